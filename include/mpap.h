@@ -1,0 +1,241 @@
+/*
+ * mpap.h -- C ABI of the GB300 (sm_103a) MPAP hot-path library (libmpap.so).
+ *
+ * MPAP is the Multiobjective Perception-Aware Planning method of Ichter, Landry,
+ * Schmerling and Pavone (arXiv 1705.02408).  Given an obstacle set X_obs, dynamics,
+ * an initial state x_init, a goal region X_goal, a cost c and a perception
+ * heuristic h with bound beta (Sec. 2, Eq. 1 and Eq. 2), the library
+ *   1. builds an r_n-disc roadmap with per-edge perception transfers
+ *      (Alg. 1 steps 1-2, Alg. 2 BuildGraph),
+ *   2. runs the wavefront multiobjective search (Alg. 1 step 3, Alg. 3 Explore),
+ *   3. certifies the returned plan by Monte Carlo rollouts (Alg. 1 step 4).
+ * Every step runs in this library's CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by all entry points
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; calls that return host results synchronise
+ *     that stream before returning.
+ *   - Host input arrays are copied; the caller keeps ownership.  Arrays flagged
+ *     MPAP_MEM_DEVICE are read in place (device pointers, 16-byte aligned) and must
+ *     stay valid until the call returns.
+ *   - Opaque handles (mpap_roadmap, mpap_workspace) own device memory and are
+ *     released by their *_free function.  A handle must not be used by two calls
+ *     that overlap in time.
+ *   - Errors are returned as negative mpap_status values; mpap_last_error() gives
+ *     a one-line description (thread-local).  Device-side failures (capacity
+ *     overflow, iteration cap) are detected on the device and returned as status
+ *     codes; no kernel traps.
+ *
+ * Units.  Costs are int64 multiples of 2^-24 (cost quantum).  Perception heuristic
+ * values are int64 multiples of 2^-24 / (M n_f) units of drift time, where M is
+ * the number of sub-steps per edge and n_f the number of features that cancels
+ * drift (Sec. 4.1).  Monte Carlo positions are integers in units of 2^-20.
+ */
+#ifndef MPAP_H_
+#define MPAP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MPAP_OK = 0,
+  MPAP_NO_SOLUTION = 1,       /* P_open became empty without a goal plan (Alg. 3) */
+  MPAP_ERR_INVALID_ARG = -1,  /* null pointer, bad size, too-small output buffer */
+  MPAP_ERR_CAPACITY = -2,     /* a front, the plan arena or a work list overflowed */
+  MPAP_ERR_TIMEOUT = -3,      /* a bounded device wait gave up */
+  MPAP_ERR_ITER_LIMIT = -4,   /* the search hit max_iters wavefronts */
+  MPAP_ERR_CUDA = -5,         /* a CUDA runtime call failed */
+  MPAP_ERR_SAMPLING = -6      /* SampleFree could not find n free samples */
+} mpap_status;
+
+typedef enum { MPAP_DIM_2D = 2, MPAP_DIM_3D = 3, MPAP_DIM_DI6 = 6 } mpap_dim_kind;
+typedef enum { MPAP_MEM_HOST = 0, MPAP_MEM_DEVICE = 1 } mpap_mem;
+
+typedef struct mpap_roadmap mpap_roadmap;
+typedef struct mpap_workspace mpap_workspace;
+
+/* The mapped environment (Sec. 2: X, X_obs; Sec. 4.1: the perception field).
+ *   dim_kind    2 (unit square, kinematic), 3 (unit cube, kinematic) or
+ *               6 (3D double integrator x'' = u with |v| <= 1, Sec. 4.1).
+ *   nb, box_lo, box_hi   axis-aligned closed boxes, float[nb][3] (z ignored in 2D);
+ *               nb may be 0 (the pointers may then be NULL).
+ *   grid_G, grid_level   perception quality levels 0..K on a G^Dp grid over the
+ *               unit square/cube (Dp = 2 or 3), uint8, x fastest; G a power of two
+ *               in [1, 1024].  A level k stands for the number of visible features
+ *               in the Sec. 4.1 heuristic.
+ *   n_f, K      features that cancel drift (the paper uses 12) and the top level.
+ *   mem         MPAP_MEM_HOST or MPAP_MEM_DEVICE for box_lo, box_hi, grid_level. */
+typedef struct {
+  int32_t dim_kind;
+  int32_t nb;
+  const float* box_lo;
+  const float* box_hi;
+  int32_t grid_G;
+  const uint8_t* grid_level;
+  int32_t n_f;
+  int32_t K;
+  int32_t mem;
+} mpap_scene;
+
+/* Roadmap construction parameters (Alg. 2).
+ *   n           free samples drawn by SampleFree; V = n + 2 nodes with
+ *               node 0 = x_init and node 1 = x_goal.
+ *   seed, query_id   key and third counter word of the Philox4x32-10 sampler.
+ *   r           connection radius r_n in cost units (Near uses Cost < r).
+ *   T_edge      duration of a double-integrator connection (ignored in 2D/3D).
+ *   M           sub-steps per connection (checkpoints for collision and heuristic).
+ *   x_init, x_goal   states (position, velocity); goal_radius defines X_goal as the
+ *               position ball around x_goal. */
+typedef struct {
+  uint32_t n;
+  uint32_t query_id;
+  uint64_t seed;
+  float r;
+  float T_edge;
+  int32_t M;
+  float x_init[6];
+  float x_goal[6];
+  float goal_radius;
+} mpap_roadmap_params;
+
+/* One search query (Alg. 3).
+ *   beta        perception-heuristic bound (plans with h > beta are cut, Eq. 2).
+ *   lambda      group cost factor in (0, 1]; groups are {p open : cost <= i lambda r_n}.
+ *   max_iters   wavefront cap (MPAP_ERR_ITER_LIMIT when reached).
+ *   flags       bit 0 MPAP_QUERY_NO_GOAL_STOP: run until P_open is empty. */
+#define MPAP_QUERY_NO_GOAL_STOP 1u
+typedef struct {
+  int64_t beta;
+  float lambda;
+  uint32_t max_iters;
+  uint32_t flags;
+} mpap_query;
+
+/* Search result.  path is a caller-owned host array of path_cap entries; on
+ * return path_len holds the number of nodes from x_init to the goal node (also
+ * when path_cap is too small, in which case the status is MPAP_ERR_INVALID_ARG). */
+typedef struct {
+  int32_t status;
+  int64_t cost;
+  int64_t h;
+  uint32_t path_len;
+  uint32_t path_cap;
+  uint32_t* path;
+  uint32_t wavefronts;     /* executed iterations of the Explore loop */
+  uint64_t expansions;     /* (p in group, edge out of p.head) pairs evaluated */
+  uint64_t plans;          /* plans that entered a stored front */
+} mpap_result;
+
+/* Monte Carlo model (integer error walk; see mpap_certify).  sigma_fx and shift
+ * are host arrays of K+1 int32 entries indexed by quality level. */
+typedef struct {
+  uint32_t rollouts;
+  uint32_t call_id;
+  uint64_t seed;
+  int64_t delta_fx;
+  const int32_t* sigma_fx;
+  const int32_t* shift;
+} mpap_mc_params;
+
+typedef struct {
+  uint32_t hits_loc;       /* rollouts whose localisation error reached delta (Eq. 1) */
+  uint32_t hits_coll;      /* rollouts whose executed state hit X_obs or left the map */
+  uint32_t hits_any;
+  uint32_t rollouts;
+} mpap_cert;
+
+const char* mpap_status_string(int32_t status);
+const char* mpap_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Roadmap (Alg. 1 steps 1-2; Alg. 2 BuildGraph; Sec. 3 primitives SampleFree,
+ * Cost, Near, Collision; Sec. 4.1 heuristic precomputed per edge).
+ * Draws V = {x_init, x_goal} + SampleFree(n), connects every ordered pair with
+ * Cost < r whose optimal connection is collision free, and stores per edge
+ * {dst, cost_q, S, C} with the heuristic transfer h -> max(C, h + S).  The handle
+ * owns all device memory.  Returns MPAP_ERR_SAMPLING if n free samples cannot be
+ * found within 64 n + 4096 candidates, MPAP_ERR_CAPACITY if an edge field
+ * overflows int32. */
+int32_t mpap_build_roadmap(const mpap_scene* scene, const mpap_roadmap_params* params,
+                           mpap_roadmap** out, void* stream);
+
+/* The same graph construction over caller-given node states x (host, float[6][V],
+ * SoA: p0, p1, p2, v0, v1, v2).  Node 0 is x_init and node 1 x_goal. */
+int32_t mpap_build_roadmap_from_points(const mpap_scene* scene, uint32_t V, const float* x,
+                                       float r, float T_edge, int32_t M, float goal_radius,
+                                       mpap_roadmap** out, void* stream);
+
+/* A roadmap given directly as a forward CSR graph (host arrays), for searches on
+ * hand-made graphs.  row_ptr[V+1], dst/cost_q/S/C[E], is_goal[V]; cost_q >= 1. */
+int32_t mpap_roadmap_from_csr(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst,
+                              const int32_t* cost_q, const int32_t* S, const int32_t* C,
+                              const uint8_t* is_goal, mpap_roadmap** out, void* stream);
+
+int32_t mpap_roadmap_info(const mpap_roadmap* rm, uint32_t* V, uint64_t* E);
+
+/* Copies the roadmap to host arrays (any pointer may be NULL): x float[6][V],
+ * is_goal[V], row_ptr[V+1], dst/cost_q/S/C[E].  Synchronises the stream. */
+int32_t mpap_roadmap_export(const mpap_roadmap* rm, float* x, uint8_t* is_goal, uint32_t* row_ptr,
+                            uint32_t* dst, int32_t* cost_q, int32_t* S, int32_t* C, void* stream);
+
+void mpap_roadmap_free(mpap_roadmap* rm);
+
+/* ---------------------------------------------------------------------------
+ * Search workspace: device memory for the per-node Pareto fronts, the plan arena
+ * and the wavefront work lists of up to `total_nodes` nodes summed over the
+ * queries of one call.  front_cap bounds every stored front (MPAP_ERR_CAPACITY
+ * when exceeded); max_plans bounds the arena and each group.  Allocates with
+ * cudaMalloc; reused by every search call. */
+int32_t mpap_workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans,
+                              mpap_workspace** out);
+void mpap_workspace_free(mpap_workspace* ws);
+
+/* Alg. 3 Explore for one query on one roadmap (the group loop runs on the
+ * device; the host waits once).  RemoveDominated uses the weak Pareto order with
+ * a total tie key (creation iteration, parent head, parent cost): an exact set
+ * function, so fronts, cost, h and path are identical to a sequential execution
+ * of Alg. 3.  Returns the result status (MPAP_OK or MPAP_NO_SOLUTION) or an
+ * error. */
+int32_t mpap_search(mpap_workspace* ws, mpap_roadmap* rm, const mpap_query* q, mpap_result* out,
+                    void* stream);
+
+/* nq independent queries in one lock-step wavefront loop (each query keeps its own
+ * iteration count, group threshold and termination).  outs[i] receives the
+ * result of qs[i] on rms[i]; the return value is MPAP_OK if every query ran to
+ * completion (individual results may still be MPAP_NO_SOLUTION) or the first
+ * error. */
+int32_t mpap_search_batch(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs,
+                          uint32_t nq, mpap_result* outs, void* stream);
+
+/* Final Pareto fronts of query `index` of the last search on `ws` (for parity
+ * checks): front_ptr[V+1] and (cost, h) pairs sorted by cost, up to cap entries;
+ * *total receives the number of entries. */
+int32_t mpap_search_fronts(mpap_workspace* ws, uint32_t index, uint32_t* front_ptr, int64_t* cost,
+                           int64_t* h, uint64_t cap, uint64_t* total, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Monte Carlo certification (Alg. 1 step 4; Sec. 3 final phase; failure events
+ * of Eq. 1 and of the robust motion planning problem).  For each rollout an
+ * integer error e (units 2^-20) walks the plan's checkpoints: at quality level k,
+ * e <- e - (e >> shift[k]) (skipped when shift[k] = 0), then
+ * e <- e + (sigma_fx[k] xi) >> 16 with xi a sum of 12 uniform 16-bit draws minus
+ * 6 * 2^16 (Philox4x32-10, counter (rollout, step, 0..4, call_id), key seed),
+ * clamped to |e_i| <= 2^30.  Localisation fails when e.e >= delta_fx^2; the
+ * executed state x_nom + e fails when it leaves the unit map or enters a closed
+ * box.  path is a host array of node indices. */
+int32_t mpap_certify(mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,
+                     const mpap_mc_params* mc, mpap_cert* out, void* stream);
+
+/* n certifications in one launch: paths[i] (host) on rms[i] with mcs[i]. */
+int32_t mpap_certify_batch(mpap_roadmap* const* rms, const uint32_t* const* paths,
+                           const uint32_t* path_lens, const mpap_mc_params* mcs, uint32_t n,
+                           mpap_cert* outs, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPAP_H_ */
