@@ -103,15 +103,20 @@ typedef struct {
 
 /* One search query (Alg. 3).
  *   beta        perception-heuristic bound (plans with h > beta are cut, Eq. 2).
- *   lambda      group cost factor in (0, 1]; groups are {p open : cost <= i lambda r_n}.
- *   max_iters   wavefront cap (MPAP_ERR_ITER_LIMIT when reached).
+ *   lambda      group cost factor in (0, 1]; groups are {p open : cost <= i Lambda}
+ *               with Lambda = round(lambda r_n 2^24) cost quanta.
+ *   group_width_q  if > 0, Lambda in cost quanta directly (lambda is then ignored;
+ *               needed for roadmaps given as plain graphs, which have no r_n).
+ *   max_iters   wavefront cap (MPAP_ERR_ITER_LIMIT when reached), > 0.
  *   flags       bit 0 MPAP_QUERY_NO_GOAL_STOP: run until P_open is empty. */
 #define MPAP_QUERY_NO_GOAL_STOP 1u
 typedef struct {
   int64_t beta;
+  int64_t group_width_q;
   float lambda;
   uint32_t max_iters;
   uint32_t flags;
+  uint32_t reserved;
 } mpap_query;
 
 /* Search result.  path is a caller-owned host array of path_cap entries; on

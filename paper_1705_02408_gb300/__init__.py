@@ -1,0 +1,381 @@
+"""Python binding of libmpap, the GB300 (sm_103a) MPAP hot-path library.
+
+Argument marshalling only: every step of roadmap construction (Alg. 2), the
+wavefront multiobjective search (Alg. 3) and Monte Carlo certification runs in
+the library's CUDA kernels.  The library must have been built
+(``paper_1705_02408_gb300.build.build()``); importing the binding without it
+raises, and there is no CPU fallback.
+
+Streams: calls take ``stream`` (a ``torch.cuda.Stream`` or a raw handle); by default
+torch's current stream on the current device is used.  Scene arrays may be numpy
+arrays (host, copied) or CUDA torch tensors (device, read in place).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpap.so")
+
+MPAP_OK, MPAP_NO_SOLUTION = 0, 1
+MPAP_ERR_INVALID_ARG, MPAP_ERR_CAPACITY, MPAP_ERR_TIMEOUT = -1, -2, -3
+MPAP_ERR_ITER_LIMIT, MPAP_ERR_CUDA, MPAP_ERR_SAMPLING = -4, -5, -6
+MPAP_MEM_HOST, MPAP_MEM_DEVICE = 0, 1
+MPAP_QUERY_NO_GOAL_STOP = 1
+
+EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap",
+           "mpap_build_roadmap_from_points", "mpap_roadmap_from_csr", "mpap_roadmap_info",
+           "mpap_roadmap_export", "mpap_roadmap_free", "mpap_workspace_create",
+           "mpap_workspace_free", "mpap_search", "mpap_search_batch", "mpap_search_fronts",
+           "mpap_certify", "mpap_certify_batch"]
+
+
+class mpap_scene(C.Structure):
+    _fields_ = [("dim_kind", C.c_int32), ("nb", C.c_int32), ("box_lo", C.c_void_p),
+                ("box_hi", C.c_void_p), ("grid_G", C.c_int32), ("grid_level", C.c_void_p),
+                ("n_f", C.c_int32), ("K", C.c_int32), ("mem", C.c_int32)]
+
+
+class mpap_roadmap_params(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("query_id", C.c_uint32), ("seed", C.c_uint64),
+                ("r", C.c_float), ("T_edge", C.c_float), ("M", C.c_int32),
+                ("x_init", C.c_float * 6), ("x_goal", C.c_float * 6), ("goal_radius", C.c_float)]
+
+
+class mpap_query(C.Structure):
+    _fields_ = [("beta", C.c_int64), ("group_width_q", C.c_int64), ("lambda_", C.c_float),
+                ("max_iters", C.c_uint32), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class mpap_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("cost", C.c_int64), ("h", C.c_int64),
+                ("path_len", C.c_uint32), ("path_cap", C.c_uint32),
+                ("path", C.POINTER(C.c_uint32)), ("wavefronts", C.c_uint32),
+                ("expansions", C.c_uint64), ("plans", C.c_uint64)]
+
+
+class mpap_mc_params(C.Structure):
+    _fields_ = [("rollouts", C.c_uint32), ("call_id", C.c_uint32), ("seed", C.c_uint64),
+                ("delta_fx", C.c_int64), ("sigma_fx", C.POINTER(C.c_int32)),
+                ("shift", C.POINTER(C.c_int32))]
+
+
+class mpap_cert(C.Structure):
+    _fields_ = [("hits_loc", C.c_uint32), ("hits_coll", C.c_uint32), ("hits_any", C.c_uint32),
+                ("rollouts", C.c_uint32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libmpap.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmpap.so not built at {LIB_PATH}: run "
+                              "paper_1705_02408_gb300.build.build() (nvcc, sm_103a)")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        i32 = C.c_int32
+        L.mpap_status_string.restype = C.c_char_p
+        L.mpap_status_string.argtypes = [i32]
+        L.mpap_last_error.restype = C.c_char_p
+        L.mpap_build_roadmap.restype = i32
+        L.mpap_build_roadmap.argtypes = [C.POINTER(mpap_scene), C.POINTER(mpap_roadmap_params),
+                                         C.POINTER(P), P]
+        L.mpap_build_roadmap_from_points.restype = i32
+        L.mpap_build_roadmap_from_points.argtypes = [C.POINTER(mpap_scene), C.c_uint32, P, C.c_float,
+                                                     C.c_float, i32, C.c_float, C.POINTER(P), P]
+        L.mpap_roadmap_from_csr.restype = i32
+        L.mpap_roadmap_from_csr.argtypes = [C.c_uint32, P, P, P, P, P, P, C.POINTER(P), P]
+        L.mpap_roadmap_info.restype = i32
+        L.mpap_roadmap_info.argtypes = [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]
+        L.mpap_roadmap_export.restype = i32
+        L.mpap_roadmap_export.argtypes = [P, P, P, P, P, P, P, P, P]
+        L.mpap_roadmap_free.argtypes = [P]
+        L.mpap_workspace_create.restype = i32
+        L.mpap_workspace_create.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.POINTER(P)]
+        L.mpap_workspace_free.argtypes = [P]
+        L.mpap_search.restype = i32
+        L.mpap_search.argtypes = [P, P, C.POINTER(mpap_query), C.POINTER(mpap_result), P]
+        L.mpap_search_batch.restype = i32
+        L.mpap_search_batch.argtypes = [P, C.POINTER(P), C.POINTER(mpap_query), C.c_uint32,
+                                        C.POINTER(mpap_result), P]
+        L.mpap_search_fronts.restype = i32
+        L.mpap_search_fronts.argtypes = [P, C.c_uint32, P, P, P, C.c_uint64,
+                                         C.POINTER(C.c_uint64), P]
+        L.mpap_certify.restype = i32
+        L.mpap_certify.argtypes = [P, P, C.c_uint32, C.POINTER(mpap_mc_params),
+                                   C.POINTER(mpap_cert), P]
+        L.mpap_certify_batch.restype = i32
+        L.mpap_certify_batch.argtypes = [C.POINTER(P), C.POINTER(P), P, C.POINTER(mpap_mc_params),
+                                         C.c_uint32, C.POINTER(mpap_cert), P]
+        _lib = L
+    return _lib
+
+
+class MpapError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        L = lib()
+        msg = L.mpap_last_error().decode(errors="replace")
+        super().__init__(f"{what}: {L.mpap_status_string(status).decode()} ({status}): {msg}")
+
+
+def _check(status, what):
+    if status < 0:
+        raise MpapError(status, what)
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(a, dtype):
+    """(pointer, keepalive, is_device) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, None, False
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr()), a, bool(a.is_cuda)
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(C.c_void_p), arr, False
+
+
+def make_scene_struct(dim_kind, box_lo, box_hi, grid, grid_G, n_f=12, K=24):
+    """An mpap_scene over numpy (host) or CUDA tensor (device) arrays."""
+    lo_p, lo_k, lo_d = _ptr(box_lo, np.float32)
+    hi_p, hi_k, hi_d = _ptr(box_hi, np.float32)
+    g_p, g_k, g_d = _ptr(grid, np.uint8)
+    nb = (lo_k.numel() if hasattr(lo_k, "numel") else lo_k.size) // 3
+    if len({lo_d, hi_d, g_d}) != 1:
+        raise ValueError("scene arrays must all be on the host or all on the device")
+    s = mpap_scene(dim_kind=dim_kind, nb=nb, box_lo=lo_p if nb else None,
+                   box_hi=hi_p if nb else None, grid_G=grid_G, grid_level=g_p, n_f=n_f, K=K,
+                   mem=MPAP_MEM_DEVICE if g_d else MPAP_MEM_HOST)
+    return s, (lo_k, hi_k, g_k)
+
+
+class Roadmap:
+    """An mpap_roadmap handle (device CSR graph with per-edge transfers)."""
+
+    def __init__(self, handle, M=16, K=24):
+        self.h = handle
+        self.M = M
+        self.K = K
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.mpap_roadmap_free(self.h)
+            self.h = None
+
+    def info(self):
+        V = C.c_uint32(); E = C.c_uint64()
+        _check(lib().mpap_roadmap_info(self.h, C.byref(V), C.byref(E)), "mpap_roadmap_info")
+        return V.value, E.value
+
+    @property
+    def V(self):
+        return self.info()[0]
+
+    @property
+    def E(self):
+        return self.info()[1]
+
+    def export(self, stream=None):
+        V, E = self.info()
+        x = np.zeros(6 * V, np.float32); g = np.zeros(V, np.uint8)
+        rp = np.zeros(V + 1, np.uint32)
+        dst = np.zeros(max(E, 1), np.uint32); cq = np.zeros(max(E, 1), np.int32)
+        S = np.zeros(max(E, 1), np.int32); Cc = np.zeros(max(E, 1), np.int32)
+        vp = lambda a: a.ctypes.data_as(C.c_void_p)
+        _check(lib().mpap_roadmap_export(self.h, vp(x), vp(g), vp(rp), vp(dst), vp(cq), vp(S), vp(Cc),
+                                         _stream(stream)), "mpap_roadmap_export")
+        return dict(V=V, E=E, x=x.reshape(6, V), is_goal=g, row_ptr=rp, dst=dst[:E], cost_q=cq[:E],
+                    S=S[:E], C=Cc[:E])
+
+
+def build_roadmap(dim_kind, box_lo, box_hi, grid, grid_G, n, seed, r, x_init, x_goal,
+                  goal_radius=0.05, T=0.25, M=16, query_id=0, n_f=12, K=24, stream=None) -> Roadmap:
+    """mpap_build_roadmap: V = {x_init, x_goal} + SampleFree(n), r-disc graph (Alg. 2)."""
+    sc, keep = make_scene_struct(dim_kind, box_lo, box_hi, grid, grid_G, n_f, K)
+    p = mpap_roadmap_params(n=n, query_id=query_id, seed=seed, r=r, T_edge=T, M=M,
+                            goal_radius=goal_radius)
+    for i in range(6):
+        p.x_init[i] = float(x_init[i]); p.x_goal[i] = float(x_goal[i])
+    h = C.c_void_p()
+    _check(lib().mpap_build_roadmap(C.byref(sc), C.byref(p), C.byref(h), _stream(stream)),
+           "mpap_build_roadmap")
+    return Roadmap(h, M, K)
+
+
+def build_roadmap_from_points(dim_kind, box_lo, box_hi, grid, grid_G, x, r, T=0.25, M=16,
+                              goal_radius=0.05, n_f=12, K=24, stream=None) -> Roadmap:
+    box_lo = np.asarray(box_lo, np.float32).reshape(-1, 3) if not hasattr(box_lo, "is_cuda") else box_lo
+    box_hi = np.asarray(box_hi, np.float32).reshape(-1, 3) if not hasattr(box_hi, "is_cuda") else box_hi
+    sc, keep = make_scene_struct(dim_kind, box_lo, box_hi, grid, grid_G, n_f, K)
+    x = np.ascontiguousarray(x, np.float32)
+    h = C.c_void_p()
+    _check(lib().mpap_build_roadmap_from_points(C.byref(sc), x.shape[1], x.ctypes.data_as(C.c_void_p), r, T,
+                                                M, goal_radius, C.byref(h), _stream(stream)),
+           "mpap_build_roadmap_from_points")
+    return Roadmap(h, M, K)
+
+
+def roadmap_from_csr(row_ptr, dst, cost_q, S, Cc, is_goal, stream=None) -> Roadmap:
+    arrs = [np.ascontiguousarray(row_ptr, np.uint32), np.ascontiguousarray(dst, np.uint32),
+            np.ascontiguousarray(cost_q, np.int32), np.ascontiguousarray(S, np.int32),
+            np.ascontiguousarray(Cc, np.int32), np.ascontiguousarray(is_goal, np.uint8)]
+    arrs = [a if a.size else np.zeros(1, a.dtype) for a in arrs]
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    h = C.c_void_p()
+    _check(lib().mpap_roadmap_from_csr(len(row_ptr) - 1, *[vp(a) for a in arrs], C.byref(h), _stream(stream)),
+           "mpap_roadmap_from_csr")
+    return Roadmap(h)
+
+
+def build_roadmap_for_scene(scene, n=None, r=None, M=None, device_inputs=False, stream=None) -> Roadmap:
+    """Convenience: build from a scenegen.Scene (host arrays, or device copies)."""
+    cfg = scene.cfg
+    lo, hi, grid = scene.box_lo, scene.box_hi, scene.grid
+    if device_inputs:
+        import torch
+        lo = torch.from_numpy(np.ascontiguousarray(lo)).cuda()
+        hi = torch.from_numpy(np.ascontiguousarray(hi)).cuda()
+        grid = torch.from_numpy(np.ascontiguousarray(grid)).cuda()
+    return build_roadmap(cfg.dim_kind, lo, hi, grid, cfg.grid_G, cfg.n if n is None else n,
+                         scene.sample_seed, cfg.r if r is None else r, scene.x_init, scene.x_goal,
+                         T=cfg.T_edge, M=cfg.M if M is None else M, query_id=scene.query_id,
+                         stream=stream)
+
+
+class Workspace:
+    """An mpap_workspace: device fronts, plan arena and work lists for searches of
+    up to ``total_nodes`` nodes (summed over one batch)."""
+
+    def __init__(self, total_nodes, front_cap=64, max_plans=1 << 24):
+        h = C.c_void_p()
+        _check(lib().mpap_workspace_create(int(total_nodes), int(front_cap), int(max_plans), C.byref(h)),
+               "mpap_workspace_create")
+        self.h = h
+        self.total_nodes = int(total_nodes)
+        self.front_cap = int(front_cap)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.mpap_workspace_free(self.h)
+            self.h = None
+
+    def fronts(self, index=0, stream=None):
+        """Final (cost, h) fronts of query `index` of the last search: (ptr, cost, h)."""
+        tot = C.c_uint64()
+        lib().mpap_search_fronts(self.h, index, None, None, None, 0, C.byref(tot), _stream(stream))
+        n = tot.value
+        # V from the last search: ask with a large pointer array
+        cost = np.zeros(max(n, 1), np.int64); hh = np.zeros(max(n, 1), np.int64)
+        ptr = np.zeros(self.total_nodes + 1, np.uint32)
+        _check(lib().mpap_search_fronts(self.h, index, ptr.ctypes.data_as(C.c_void_p),
+                                        cost.ctypes.data_as(C.c_void_p), hh.ctypes.data_as(C.c_void_p),
+                                        n, C.byref(tot), _stream(stream)), "mpap_search_fronts")
+        return ptr, cost[:n], hh[:n]
+
+
+@dataclass
+class SearchResult:
+    status: int
+    cost: int
+    h: int
+    path: np.ndarray
+    wavefronts: int
+    expansions: int
+    plans: int
+
+
+def make_query(beta, lam=0.5, group_width_q=0, max_iters=100000, goal_stop=True):
+    return mpap_query(beta=int(beta), group_width_q=int(group_width_q), lambda_=float(lam),
+                      max_iters=int(max_iters), flags=0 if goal_stop else MPAP_QUERY_NO_GOAL_STOP)
+
+
+def _result(r, buf):
+    n = r.path_len if r.status == MPAP_OK else 0
+    return SearchResult(r.status, r.cost, r.h, buf[:n].copy(), r.wavefronts, r.expansions, r.plans)
+
+
+def search(ws: Workspace, rm: Roadmap, beta, lam=0.5, group_width_q=0, max_iters=100000,
+           goal_stop=True, path_cap=4096, stream=None) -> SearchResult:
+    """mpap_search: Alg. 3 Explore for one query."""
+    q = make_query(beta, lam, group_width_q, max_iters, goal_stop)
+    buf = np.zeros(path_cap, np.uint32)
+    r = mpap_result(path_cap=path_cap, path=buf.ctypes.data_as(C.POINTER(C.c_uint32)))
+    _check(lib().mpap_search(ws.h, rm.h, C.byref(q), C.byref(r), _stream(stream)), "mpap_search")
+    return _result(r, buf)
+
+
+def search_batch(ws: Workspace, rms, queries, path_cap=4096, stream=None, check=True):
+    """mpap_search_batch: independent queries in one lock-step wavefront loop."""
+    nq = len(rms)
+    hs = (C.c_void_p * nq)(*[rm.h for rm in rms])
+    qs = (mpap_query * nq)(*queries)
+    bufs = [np.zeros(path_cap, np.uint32) for _ in range(nq)]
+    rs = (mpap_result * nq)()
+    for i in range(nq):
+        rs[i].path_cap = path_cap
+        rs[i].path = bufs[i].ctypes.data_as(C.POINTER(C.c_uint32))
+    rc = lib().mpap_search_batch(ws.h, hs, qs, nq, rs, _stream(stream))
+    if check:
+        _check(rc, "mpap_search_batch")
+    return [_result(rs[i], bufs[i]) for i in range(nq)]
+
+
+def make_mc(rollouts, seed, call_id, delta_fx, sigma_fx, shift):
+    sig = np.ascontiguousarray(sigma_fx, np.int32); sh = np.ascontiguousarray(shift, np.int32)
+    p = mpap_mc_params(rollouts=rollouts, call_id=call_id, seed=seed, delta_fx=int(delta_fx),
+                       sigma_fx=sig.ctypes.data_as(C.POINTER(C.c_int32)),
+                       shift=sh.ctypes.data_as(C.POINTER(C.c_int32)))
+    return p, (sig, sh)
+
+
+def certify(rm: Roadmap, path, rollouts, seed, call_id, delta_fx, sigma_fx, shift, stream=None):
+    """mpap_certify: Monte Carlo rollouts along a plan."""
+    p, keep = make_mc(rollouts, seed, call_id, delta_fx, sigma_fx, shift)
+    path = np.ascontiguousarray(path, np.uint32)
+    out = mpap_cert()
+    _check(lib().mpap_certify(rm.h, path.ctypes.data_as(C.c_void_p), path.size, C.byref(p), C.byref(out),
+                              _stream(stream)), "mpap_certify")
+    return dict(hits_loc=out.hits_loc, hits_coll=out.hits_coll, hits_any=out.hits_any, rollouts=out.rollouts)
+
+
+def certify_batch(rms, paths, mcs, stream=None):
+    """mpap_certify_batch. mcs: list of (rollouts, seed, call_id, delta_fx, sigma_fx, shift)."""
+    n = len(rms)
+    hs = (C.c_void_p * n)(*[rm.h for rm in rms])
+    arrs = [np.ascontiguousarray(p, np.uint32) if len(p) else np.zeros(1, np.uint32) for p in paths]
+    pp = (C.c_void_p * n)(*[a.ctypes.data for a in arrs])
+    lens = np.array([len(p) for p in paths], np.uint32)
+    keep = []
+    ms = (mpap_mc_params * n)()
+    for i, m in enumerate(mcs):
+        ms[i], k = make_mc(*m)
+        keep.append(k)
+    outs = (mpap_cert * n)()
+    _check(lib().mpap_certify_batch(hs, pp, lens.ctypes.data_as(C.c_void_p), ms, n, outs, _stream(stream)),
+           "mpap_certify_batch")
+    return [dict(hits_loc=o.hits_loc, hits_coll=o.hits_coll, hits_any=o.hits_any, rollouts=o.rollouts)
+            for o in outs]

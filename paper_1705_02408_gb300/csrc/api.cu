@@ -1,0 +1,242 @@
+// C ABI of libmpap (declared in include/mpap.h): argument validation and
+// dispatch to the roadmap, search and certification implementations.
+#include <cstring>
+
+#include "internal.h"
+
+namespace mpap {
+const char* last_error();
+int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans, uint32_t max_q,
+                         mpap_workspace** out);
+void workspace_free(mpap_workspace* ws);
+int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs, uint32_t nq,
+                          mpap_result* outs, cudaStream_t st);
+int32_t search_fronts_impl(mpap_workspace* ws, uint32_t index, uint32_t* front_ptr, int64_t* cost,
+                           int64_t* h, uint64_t cap, uint64_t* total, cudaStream_t st);
+int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,
+                           const mpap_mc_params* mcs, uint32_t n, mpap_cert* outs, cudaStream_t st);
+}  // namespace mpap
+
+using mpap::set_error;
+
+namespace {
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int32_t check_scene(const mpap_scene* sc) {
+  if (!sc) {
+    set_error("scene is null");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (sc->dim_kind != 2 && sc->dim_kind != 3 && sc->dim_kind != 6) {
+    set_error("dim_kind must be 2, 3 or 6");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (sc->nb < 0 || (sc->nb > 0 && (!sc->box_lo || !sc->box_hi))) {
+    set_error("bad obstacle arrays");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (sc->grid_G < 1 || sc->grid_G > 1024 || (sc->grid_G & (sc->grid_G - 1)) || !sc->grid_level) {
+    set_error("grid_G must be a power of two in [1, 1024] with a level array");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (sc->n_f < 0 || sc->K < 0 || sc->K > 255) {
+    set_error("bad n_f / K");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (sc->mem != MPAP_MEM_HOST && sc->mem != MPAP_MEM_DEVICE) {
+    set_error("mem must be MPAP_MEM_HOST or MPAP_MEM_DEVICE");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  // 6D boxes are staged in shared memory by the edge kernel (48 KB default)
+  if (sc->nb > 1024) {
+    set_error("at most 1024 boxes");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return MPAP_OK;
+}
+
+int32_t check_conn(float r, float T, int M, int dim) {
+  if (!(r > 0.0f) || M < 1 || M > 4096 || (dim == 6 && !(T > 0.0f))) {
+    set_error("need r > 0, 1 <= M <= 4096 and (6D) T > 0");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return MPAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mpap_status_string(int32_t s) {
+  switch (s) {
+    case MPAP_OK: return "ok";
+    case MPAP_NO_SOLUTION: return "no solution";
+    case MPAP_ERR_INVALID_ARG: return "invalid argument";
+    case MPAP_ERR_CAPACITY: return "capacity exceeded";
+    case MPAP_ERR_TIMEOUT: return "device wait timed out";
+    case MPAP_ERR_ITER_LIMIT: return "iteration limit";
+    case MPAP_ERR_CUDA: return "CUDA error";
+    case MPAP_ERR_SAMPLING: return "sampling failed";
+    default: return "unknown status";
+  }
+}
+
+const char* mpap_last_error(void) { return mpap::last_error(); }
+
+int32_t mpap_build_roadmap(const mpap_scene* scene, const mpap_roadmap_params* p, mpap_roadmap** out,
+                           void* stream) {
+  int32_t rc = check_scene(scene);
+  if (rc) return rc;
+  if (!p || !out) {
+    set_error("null params/out");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if ((rc = check_conn(p->r, p->T_edge, p->M, scene->dim_kind))) return rc;
+  if (p->n == 0 || p->n > 0x0FFFFFFFu) {
+    set_error("n must be in [1, 2^28)");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  return mpap::build_roadmap_impl(scene, p, nullptr, 0, p->r, p->T_edge, p->M, p->goal_radius, out, S(stream));
+}
+
+int32_t mpap_build_roadmap_from_points(const mpap_scene* scene, uint32_t V, const float* x, float r, float T,
+                                       int32_t M, float goal_radius, mpap_roadmap** out, void* stream) {
+  int32_t rc = check_scene(scene);
+  if (rc) return rc;
+  if (!x || !out || V < 2) {
+    set_error("need x, out and V >= 2");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if ((rc = check_conn(r, T, M, scene->dim_kind))) return rc;
+  *out = nullptr;
+  return mpap::build_roadmap_impl(scene, nullptr, x, V, r, T, M, goal_radius, out, S(stream));
+}
+
+int32_t mpap_roadmap_from_csr(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst, const int32_t* cost_q,
+                              const int32_t* Sv, const int32_t* C, const uint8_t* is_goal, mpap_roadmap** out,
+                              void* stream) {
+  if (!row_ptr || !is_goal || !out || V < 1) {
+    set_error("need row_ptr, is_goal, out and V >= 1");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  const uint32_t E = row_ptr[V];
+  if (E && (!dst || !cost_q || !Sv || !C)) {
+    set_error("null edge arrays");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  for (uint32_t v = 0; v < V; ++v)
+    if (row_ptr[v] > row_ptr[v + 1]) {
+      set_error("row_ptr not monotone");
+      return MPAP_ERR_INVALID_ARG;
+    }
+  for (uint32_t e = 0; e < E; ++e)
+    if (dst[e] >= V || cost_q[e] < 1 || C[e] < 0) {
+      set_error("edge %u: dst out of range, cost_q < 1 or C < 0", e);
+      return MPAP_ERR_INVALID_ARG;
+    }
+  *out = nullptr;
+  return mpap::roadmap_from_csr_impl(V, row_ptr, dst, cost_q, Sv, C, is_goal, out, S(stream));
+}
+
+int32_t mpap_roadmap_info(const mpap_roadmap* rm, uint32_t* V, uint64_t* E) {
+  if (!rm) {
+    set_error("null roadmap");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (V) *V = rm->V;
+  if (E) *E = rm->E;
+  return MPAP_OK;
+}
+
+int32_t mpap_roadmap_export(const mpap_roadmap* rm, float* x, uint8_t* is_goal, uint32_t* row_ptr, uint32_t* dst,
+                            int32_t* cost_q, int32_t* Sv, int32_t* C, void* stream) {
+  if (!rm) {
+    set_error("null roadmap");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = S(stream);
+  if (x) MPAP_CK(cudaMemcpyAsync(x, rm->x, sizeof(float) * 6 * (size_t)rm->V, cudaMemcpyDeviceToHost, st));
+  if (is_goal) MPAP_CK(cudaMemcpyAsync(is_goal, rm->is_goal, rm->V, cudaMemcpyDeviceToHost, st));
+  if (row_ptr)
+    MPAP_CK(cudaMemcpyAsync(row_ptr, rm->fwd_ptr, 4 * ((size_t)rm->V + 1), cudaMemcpyDeviceToHost, st));
+  if (dst || cost_q || Sv || C) {
+    int4* tmp = new int4[rm->E ? rm->E : 1];
+    if (rm->E && !mpap::cuda_ok(cudaMemcpyAsync(tmp, rm->fwd_edge, sizeof(int4) * rm->E, cudaMemcpyDeviceToHost, st),
+                                "export edges")) {
+      delete[] tmp;
+      return MPAP_ERR_CUDA;
+    }
+    if (!mpap::cuda_ok(cudaStreamSynchronize(st), "sync")) {
+      delete[] tmp;
+      return MPAP_ERR_CUDA;
+    }
+    for (uint64_t e = 0; e < rm->E; ++e) {
+      if (dst) dst[e] = (uint32_t)tmp[e].x;
+      if (cost_q) cost_q[e] = tmp[e].y;
+      if (Sv) Sv[e] = tmp[e].z;
+      if (C) C[e] = tmp[e].w;
+    }
+    delete[] tmp;
+  }
+  MPAP_CK(cudaStreamSynchronize(st));
+  return MPAP_OK;
+}
+
+void mpap_roadmap_free(mpap_roadmap* rm) { mpap::roadmap_free_impl(rm); }
+
+int32_t mpap_workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans,
+                              mpap_workspace** out) {
+  return mpap::workspace_create(total_nodes, front_cap, max_plans, 4096u, out);
+}
+
+void mpap_workspace_free(mpap_workspace* ws) { mpap::workspace_free(ws); }
+
+int32_t mpap_search(mpap_workspace* ws, mpap_roadmap* rm, const mpap_query* q, mpap_result* out, void* stream) {
+  if (!ws || !rm || !q || !out) {
+    set_error("null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  int32_t rc = mpap::search_batch_impl(ws, &rm, q, 1, out, S(stream));
+  if (rc < 0) return rc;
+  return out->status;
+}
+
+int32_t mpap_search_batch(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs, uint32_t nq,
+                          mpap_result* outs, void* stream) {
+  if (!ws || (nq && (!rms || !qs || !outs))) {
+    set_error("null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::search_batch_impl(ws, rms, qs, nq, outs, S(stream));
+}
+
+int32_t mpap_search_fronts(mpap_workspace* ws, uint32_t index, uint32_t* front_ptr, int64_t* cost, int64_t* h,
+                           uint64_t cap, uint64_t* total, void* stream) {
+  if (!ws) {
+    set_error("null workspace");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::search_fronts_impl(ws, index, front_ptr, cost, h, cap, total, S(stream));
+}
+
+int32_t mpap_certify(mpap_roadmap* rm, const uint32_t* path, uint32_t path_len, const mpap_mc_params* mc,
+                     mpap_cert* out, void* stream) {
+  if (!rm || !mc || !out || (path_len && !path)) {
+    set_error("null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::certify_batch_impl(&rm, &path, &path_len, mc, 1, out, S(stream));
+}
+
+int32_t mpap_certify_batch(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,
+                           const mpap_mc_params* mcs, uint32_t n, mpap_cert* outs, void* stream) {
+  if (n && (!rms || !paths || !path_lens || !mcs || !outs)) {
+    set_error("null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::certify_batch_impl(rms, paths, path_lens, mcs, n, outs, S(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+// Monte Carlo certification of a plan: Alg. 1 step 4 and the final phase of
+// Sec. 3 (probability of meeting the localisation bound of Eq. 1 and the
+// deviation bound of the robust motion planning problem, by rollouts).
+//
+// Two kernels per batch of plans:
+//   k_mc_checkpoints  one thread per (plan edge, sub-step): the nominal state at
+//                     the end of every sub-interval, in 2^-20 fixed point, with its
+//                     perception quality level (same connection model and
+//                     evaluation order as the roadmap build).
+//   k_mc_rollouts     one thread per rollout: an integer error random walk over the
+//                     checkpoints (relocalisation contraction, Irwin-Hall(12)
+//                     noise from Philox4x32-10), counting localisation and
+//                     collision/leave-map failures.
+#include <vector>
+
+#include "internal.h"
+
+namespace mpap {
+
+struct McJob {
+  Geom g;
+  const float* x;          // roadmap node states [6][V]
+  uint32_t V;
+  const uint32_t* path;    // device copy of the plan
+  uint32_t path_len;
+  int4* ckpt;              // [steps] {x, y, z (2^-20 units), level}
+  uint32_t steps;
+  uint32_t rollouts;
+  uint32_t call_id;
+  int K;                   // table size - 1 (levels are clamped to [0, K])
+  uint32_t key0, key1;
+  long long delta2;
+  const int32_t* sigma;    // [K+1]
+  const int32_t* shift;    // [K+1]
+  uint32_t* hits;          // [3] loc, coll, any
+};
+
+__global__ void k_mc_checkpoints(const McJob* jobs) {
+  const McJob& J = jobs[blockIdx.y];
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < J.steps; t += gridDim.x * blockDim.x) {
+    const uint32_t j = t / (uint32_t)J.g.M;
+    const int m = (int)(t % (uint32_t)J.g.M) + 1;
+    const uint32_t a = J.path[j], b = J.path[j + 1];
+    float xa[6], xb[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      xa[c] = J.x[(size_t)c * J.V + a];
+      xb[c] = J.x[(size_t)c * J.V + b];
+    }
+    Conn cn;
+    conn_setup(J.g, xa, xb, cn);
+    float p[3];
+    conn_point(J.g, cn, m, p);
+    int lev = level_at(J.g, p);
+    lev = lev > J.K ? J.K : lev;
+    J.ckpt[t] = make_int4((int)__float2ll_rn(__fmul_rn(p[0], kTwo20)), (int)__float2ll_rn(__fmul_rn(p[1], kTwo20)),
+                          (int)__float2ll_rn(__fmul_rn(p[2], kTwo20)), lev);
+  }
+}
+
+constexpr int kMcMaxBoxes = 512;
+
+__global__ void __launch_bounds__(256) k_mc_rollouts(const McJob* jobs) {
+  const McJob& J = jobs[blockIdx.y];
+  __shared__ int s_lo[3 * kMcMaxBoxes], s_hi[3 * kMcMaxBoxes];
+  const int nb = J.g.nb < kMcMaxBoxes ? J.g.nb : kMcMaxBoxes;
+  for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) {
+    s_lo[i] = (int)__float2ll_rn(__fmul_rn(J.g.box_lo[i], kTwo20));
+    s_hi[i] = (int)__float2ll_rn(__fmul_rn(J.g.box_hi[i], kTwo20));
+  }
+  __syncthreads();
+  const int dp = J.g.dp;
+  const uint32_t ro = blockIdx.x * blockDim.x + threadIdx.x;
+  bool loc = false, coll = false;
+  if (ro < J.rollouts) {
+    long long e[3] = {0, 0, 0};
+    const long long lim = 1ll << 30, one = 1ll << 20;
+    const int calls = (12 * dp + 7) / 8;   // Philox calls needed for dp axes of noise
+    for (uint32_t s = 0; s < J.steps && !(loc && coll); ++s) {
+      const int4 ck = J.ckpt[s];
+      const int k = ck.w;
+      const int sh = __ldg(J.shift + k);
+      if (sh > 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (i < dp) e[i] -= (e[i] >> sh);
+      }
+      uint32_t wd[20];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        if (c < calls) {
+          uint32_t w0 = ro, w1 = s, w2 = (uint32_t)c, w3 = J.call_id;
+          philox4x32_10(w0, w1, w2, w3, J.key0, J.key1);
+          wd[4 * c + 0] = w0;
+          wd[4 * c + 1] = w1;
+          wd[4 * c + 2] = w2;
+          wd[4 * c + 3] = w3;
+        }
+      }
+      const long long sig = (long long)__ldg(J.sigma + k);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (i < dp) {
+          long long xi = 0;
+#pragma unroll
+          for (int jj = 0; jj < 6; ++jj) {   // 12 draws = 6 words, low then high half
+            const uint32_t w = wd[6 * i + jj];
+            xi += (long long)(w & 0xFFFFu) + (long long)(w >> 16);
+          }
+          xi -= 6ll * 65536ll;
+          long long v = e[i] + ((sig * xi) >> 16);
+          v = v > lim ? lim : v;
+          v = v < -lim ? -lim : v;
+          e[i] = v;
+        }
+      }
+      long long ee = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < dp) ee += e[i] * e[i];
+      if (ee >= J.delta2) loc = true;
+      const long long qx = (long long)ck.x + e[0], qy = (long long)ck.y + e[1], qz = (long long)ck.z + e[2];
+      bool bad = qx < 0 || qx > one || qy < 0 || qy > one || (dp == 3 && (qz < 0 || qz > one));
+      for (int b = 0; b < nb && !bad; ++b) {
+        bool in = qx >= s_lo[3 * b] && qx <= s_hi[3 * b] && qy >= s_lo[3 * b + 1] && qy <= s_hi[3 * b + 1];
+        if (dp == 3) in = in && qz >= s_lo[3 * b + 2] && qz <= s_hi[3 * b + 2];
+        bad = in;
+      }
+      if (bad) coll = true;
+    }
+  }
+  const unsigned nl = __reduce_add_sync(0xFFFFFFFFu, loc ? 1u : 0u);
+  const unsigned nc = __reduce_add_sync(0xFFFFFFFFu, coll ? 1u : 0u);
+  const unsigned na = __reduce_add_sync(0xFFFFFFFFu, (loc || coll) ? 1u : 0u);
+  if ((threadIdx.x & 31) == 0) {
+    if (nl) atomicAdd(J.hits + 0, nl);
+    if (nc) atomicAdd(J.hits + 1, nc);
+    if (na) atomicAdd(J.hits + 2, na);
+  }
+}
+
+int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,
+                           const mpap_mc_params* mcs, uint32_t n, mpap_cert* outs, cudaStream_t st) {
+  if (n == 0) return MPAP_OK;
+  std::vector<McJob> jobs(n);
+  size_t total_steps = 0, total_path = 0, total_tab = 0;
+  uint32_t max_ro = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const mpap_roadmap* rm = rms[i];
+    if (!rm || !rm->has_geometry) {
+      set_error("certify: roadmap %u has no geometry", i);
+      return MPAP_ERR_INVALID_ARG;
+    }
+    if (rm->nb > kMcMaxBoxes) {
+      set_error("certify: at most %d boxes", kMcMaxBoxes);
+      return MPAP_ERR_INVALID_ARG;
+    }
+    if (!mcs[i].sigma_fx || !mcs[i].shift || (path_lens[i] && !paths[i])) {
+      set_error("certify: null table or path");
+      return MPAP_ERR_INVALID_ARG;
+    }
+    for (uint32_t j = 0; j < path_lens[i]; ++j)
+      if (paths[i][j] >= rm->V) {
+        set_error("certify: path node %u out of range", paths[i][j]);
+        return MPAP_ERR_INVALID_ARG;
+      }
+    for (int k = 0; k <= rm->K; ++k)
+      if (mcs[i].shift[k] < 0 || mcs[i].shift[k] > 62) {
+        set_error("certify: shift table entries must be in [0, 62]");
+        return MPAP_ERR_INVALID_ARG;
+      }
+    const uint32_t steps = path_lens[i] >= 2 ? (path_lens[i] - 1) * (uint32_t)rm->M : 0u;
+    McJob& J = jobs[i];
+    J.g = rm->geom;
+    J.x = rm->x;
+    J.V = rm->V;
+    J.path_len = path_lens[i];
+    J.steps = steps;
+    J.rollouts = mcs[i].rollouts;
+    J.call_id = mcs[i].call_id;
+    J.K = rm->K;
+    J.key0 = (uint32_t)mcs[i].seed;
+    J.key1 = (uint32_t)(mcs[i].seed >> 32);
+    J.delta2 = (long long)mcs[i].delta_fx * (long long)mcs[i].delta_fx;
+    total_steps += steps;
+    total_path += path_lens[i];
+    total_tab += 2 * (size_t)(rm->K + 1);
+    max_ro = max_ro > mcs[i].rollouts ? max_ro : mcs[i].rollouts;
+  }
+  // one device scratch block: jobs | hits | paths | tables | checkpoints
+  const size_t b_jobs = sizeof(McJob) * n;
+  const size_t b_hits = sizeof(uint32_t) * 3 * n;
+  const size_t b_path = sizeof(uint32_t) * (total_path + 1);
+  const size_t b_tab = sizeof(int32_t) * (total_tab + 1);
+  const size_t b_ck = sizeof(int4) * (total_steps + 1);
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t bytes = up(b_jobs) + up(b_hits) + up(b_path) + up(b_tab) + up(b_ck);
+  char* blk = nullptr;
+  MPAP_CK(cudaMallocAsync((void**)&blk, bytes, st));
+  McJob* d_jobs = (McJob*)blk;
+  uint32_t* d_hits = (uint32_t*)(blk + up(b_jobs));
+  uint32_t* d_path = (uint32_t*)(blk + up(b_jobs) + up(b_hits));
+  int32_t* d_tab = (int32_t*)(blk + up(b_jobs) + up(b_hits) + up(b_path));
+  int4* d_ck = (int4*)(blk + up(b_jobs) + up(b_hits) + up(b_path) + up(b_tab));
+  // host staging for paths and tables (one copy each)
+  std::vector<uint32_t> hpath(total_path + 1);
+  std::vector<int32_t> htab(total_tab + 1);
+  size_t po = 0, to = 0, co = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const int K1 = rms[i]->K + 1;
+    for (uint32_t j = 0; j < path_lens[i]; ++j) hpath[po + j] = paths[i][j];
+    for (int k = 0; k < K1; ++k) {
+      htab[to + k] = mcs[i].sigma_fx[k];
+      htab[to + K1 + k] = mcs[i].shift[k];
+    }
+    jobs[i].path = d_path + po;
+    jobs[i].sigma = d_tab + to;
+    jobs[i].shift = d_tab + to + K1;
+    jobs[i].ckpt = d_ck + co;
+    jobs[i].hits = d_hits + 3 * i;
+    po += path_lens[i];
+    to += 2 * (size_t)K1;
+    co += jobs[i].steps;
+  }
+  MPAP_CK(cudaMemcpyAsync(d_jobs, jobs.data(), b_jobs, cudaMemcpyHostToDevice, st));
+  MPAP_CK(cudaMemcpyAsync(d_path, hpath.data(), b_path, cudaMemcpyHostToDevice, st));
+  MPAP_CK(cudaMemcpyAsync(d_tab, htab.data(), b_tab, cudaMemcpyHostToDevice, st));
+  MPAP_CK(cudaMemsetAsync(d_hits, 0, b_hits, st));
+  uint32_t max_steps = 0;
+  for (auto& J : jobs) max_steps = max_steps > J.steps ? max_steps : J.steps;
+  if (max_steps) {
+    dim3 gck((max_steps + 255) / 256, n);
+    k_mc_checkpoints<<<gck, 256, 0, st>>>(d_jobs);
+  }
+  if (max_ro && max_steps) {
+    dim3 gro((max_ro + 255) / 256, n);
+    k_mc_rollouts<<<gro, 256, 0, st>>>(d_jobs);
+  }
+  MPAP_CK(cudaGetLastError());
+  std::vector<uint32_t> hh(3 * n);
+  MPAP_CK(cudaMemcpyAsync(hh.data(), d_hits, b_hits, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaFreeAsync(blk, st));
+  MPAP_CK(cudaStreamSynchronize(st));
+  for (uint32_t i = 0; i < n; ++i) {
+    outs[i].hits_loc = hh[3 * i];
+    outs[i].hits_coll = hh[3 * i + 1];
+    outs[i].hits_any = hh[3 * i + 2];
+    outs[i].rollouts = mcs[i].rollouts;
+  }
+  return MPAP_OK;
+}
+
+}  // namespace mpap

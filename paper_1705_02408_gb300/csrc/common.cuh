@@ -1,0 +1,263 @@
+// Device-side building blocks shared by the MPAP kernels (sm_103a).
+//
+// Floating-point convention: every geometric quantity is evaluated with explicit
+// round-to-nearest binary32 intrinsics (__fadd_rn, __fmul_rn, __fdiv_rn,
+// __fsqrt_rn) in a fixed operation order, so no multiply-add contraction can occur
+// and results are bit-reproducible against a plain IEEE-754 evaluation of the
+// same expressions.  Floats become integers only through exact power-of-two
+// scalings followed by round-half-even (__float2ll_rn) or floor.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpap {
+
+// Front entry flags, stored in the high bits of the 32-bit plan reference.
+constexpr uint32_t kOpen = 0x80000000u;     // plan is in P_open
+constexpr uint32_t kNew = 0x40000000u;      // candidate of the current wavefront
+constexpr uint32_t kPidMask = 0x3FFFFFFFu;  // arena index (or parent index if kNew)
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+// Device error bits (MPAP_ERR_CAPACITY unless noted).
+constexpr uint32_t kErrFront = 1u;
+constexpr uint32_t kErrArena = 2u;
+constexpr uint32_t kErrGroup = 4u;
+constexpr uint32_t kErrList = 8u;
+constexpr uint32_t kErrEdge = 16u;
+constexpr uint32_t kErrPath = 32u;
+
+constexpr float kTwo24 = 16777216.0f;
+constexpr float kTwo20 = 1048576.0f;
+
+// Environment and connection model, passed by value to kernels.
+struct Geom {
+  int dim;        // 2, 3, or 6 (double integrator)
+  int dp;         // position axes (2 or 3)
+  int nb;         // number of boxes
+  int G;          // grid cells per axis
+  int n_f;
+  int M;          // sub-steps per connection
+  const float* box_lo;    // [nb][3]
+  const float* box_hi;
+  const uint8_t* grid;    // [G^dp], x fastest
+  float r;
+  float T;
+  // double-integrator constants (rounded once from double on the host)
+  float c1, c2, c3, e1, e2, inv6, dtm;
+  float invM;             // 1 / M
+  int64_t Tq;             // round(T 2^24)
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// multiplies with the published multipliers, the key advanced by the published
+// Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t& x0, uint32_t& x1, uint32_t& x2,
+                                              uint32_t& x3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+    uint32_t lo_a = m0 * x0, hi_a = __umulhi(m0, x0);
+    uint32_t lo_b = m1 * x2, hi_b = __umulhi(m1, x2);
+    uint32_t y0 = hi_b ^ x1 ^ k0;
+    uint32_t y2 = hi_a ^ x3 ^ k1;
+    x0 = y0;
+    x1 = lo_b;
+    x2 = y2;
+    x3 = lo_a;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+__device__ __forceinline__ float unit24(uint32_t w) {
+  return __fmul_rn((float)(w >> 8), 5.9604644775390625e-8f);  // 2^-24, exact
+}
+
+// ---------------------------------------------------------------------------
+// Geometry
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool in_box(const float* lo, const float* hi, int dp, const float p[3]) {
+  bool in = true;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (i < dp) in = in && (p[i] >= lo[i]) && (p[i] <= hi[i]);
+  return in;
+}
+
+__device__ __forceinline__ int level_at(const Geom& g, const float p[3]) {
+  int c[3] = {0, 0, 0};
+  const float Gf = (float)g.G;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i < g.dp) {
+      int ci = (int)floorf(__fmul_rn(p[i], Gf));
+      ci = ci < 0 ? 0 : ci;
+      ci = ci > g.G - 1 ? g.G - 1 : ci;
+      c[i] = ci;
+    }
+  }
+  size_t idx = (g.dp == 2) ? ((size_t)c[1] * g.G + c[0])
+                           : (((size_t)c[2] * g.G + c[1]) * g.G + c[0]);
+  return (int)__ldg(g.grid + idx);
+}
+
+// The optimal connection from state a to state b.
+//   2D/3D: straight segment a + t d, t in [0, 1] (unit speed); cost = |d|.
+//   6D:    p(t) = p0 + t (v0 + t (a0/2 + t j/6)) with a0 = 6 dp/T^2 - 2 dv/T and
+//          j = 6 dv/T^2 - 12 dp/T^3 (dp = p1 - p0 - v0 T, dv = v1 - v0);
+//          cost = T + sum_axes (12 dp^2/T^3 - 12 dp dv/T^2 + 4 dv^2/T).
+struct Conn {
+  float p0[3], v0[3], q2[3], q3[3];   // 6D cubic (q2 = a0/2, q3 = j/6)
+  float d[3];                         // 2D/3D direction (p0 holds the start)
+  float cost;
+};
+
+__device__ __forceinline__ void conn_setup(const Geom& g, const float a[6], const float b[6], Conn& c) {
+  if (g.dim != 6) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (i < g.dp) {
+        c.p0[i] = a[i];
+        c.d[i] = __fsub_rn(b[i], a[i]);
+        float sq = __fmul_rn(c.d[i], c.d[i]);
+        s = (i == 0) ? sq : __fadd_rn(s, sq);
+      } else {
+        c.p0[i] = 0.0f;
+        c.d[i] = 0.0f;
+      }
+    }
+    c.cost = __fsqrt_rn(s);
+    return;
+  }
+  float jsum = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float dpos = __fsub_rn(__fsub_rn(b[i], a[i]), __fmul_rn(a[3 + i], g.T));
+    float dvel = __fsub_rn(b[3 + i], a[3 + i]);
+    float t1 = __fmul_rn(__fmul_rn(g.c1, dpos), dpos);
+    float t2 = __fmul_rn(__fmul_rn(g.c2, dpos), dvel);
+    float t3 = __fmul_rn(__fmul_rn(g.c3, dvel), dvel);
+    float ji = __fadd_rn(__fsub_rn(t1, t2), t3);
+    jsum = (i == 0) ? ji : __fadd_rn(jsum, ji);
+    float a0 = __fsub_rn(__fmul_rn(g.e1, dpos), __fmul_rn(g.e2, dvel));
+    float jk = __fsub_rn(__fmul_rn(g.e1, dvel), __fmul_rn(g.c1, dpos));
+    c.p0[i] = a[i];
+    c.v0[i] = a[3 + i];
+    c.q2[i] = __fmul_rn(a0, 0.5f);
+    c.q3[i] = __fmul_rn(jk, g.inv6);
+  }
+  c.cost = __fadd_rn(g.T, jsum);
+}
+
+// Position at the end of sub-interval m (m = 1..M).
+__device__ __forceinline__ void conn_point(const Geom& g, const Conn& c, int m, float p[3]) {
+  if (g.dim != 6) {
+    float t = __fmul_rn((float)m, g.invM);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) p[i] = (i < g.dp) ? __fadd_rn(c.p0[i], __fmul_rn(t, c.d[i])) : 0.0f;
+    return;
+  }
+  float t = __fmul_rn((float)m, g.dtm);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float in = __fadd_rn(c.q2[i], __fmul_rn(t, c.q3[i]));
+    float mid = __fadd_rn(c.v0[i], __fmul_rn(t, in));
+    p[i] = __fadd_rn(c.p0[i], __fmul_rn(t, mid));
+  }
+}
+
+// Closed segment (2D/3D) against one closed box: slab clipping with IEEE division.
+__device__ __forceinline__ bool seg_hits_box(int dp, const float a[3], const float d[3],
+                                             const float* lo, const float* hi) {
+  float t0 = -INFINITY, t1 = INFINITY;
+  bool miss = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i < dp) {
+      if (d[i] == 0.0f) {
+        miss = miss || (a[i] < lo[i]) || (a[i] > hi[i]);
+      } else {
+        float ta = __fdiv_rn(__fsub_rn(lo[i], a[i]), d[i]);
+        float tb = __fdiv_rn(__fsub_rn(hi[i], a[i]), d[i]);
+        t0 = fmaxf(t0, fminf(ta, tb));
+        t1 = fminf(t1, fmaxf(ta, tb));
+      }
+    }
+  }
+  return !miss && (t0 <= t1) && (t1 >= 0.0f) && (t0 <= 1.0f);
+}
+
+// Collision of a connection against the boxes (box data in shared memory):
+// 2D/3D exact slab test; 6D point tests at the M-1 interior checkpoints, where
+// leaving the unit workspace also counts.
+__device__ __forceinline__ bool conn_collides(const Geom& g, const Conn& c, const float* s_lo,
+                                              const float* s_hi) {
+  if (g.dim != 6) {
+    for (int b = 0; b < g.nb; ++b)
+      if (seg_hits_box(g.dp, c.p0, c.d, s_lo + 3 * b, s_hi + 3 * b)) return true;
+    return false;
+  }
+  for (int m = 1; m < g.M; ++m) {
+    float p[3];
+    conn_point(g, c, m, p);
+    if (p[0] < 0.0f || p[0] > 1.0f || p[1] < 0.0f || p[1] > 1.0f || p[2] < 0.0f || p[2] > 1.0f)
+      return true;
+    for (int b = 0; b < g.nb; ++b)
+      if (in_box(s_lo + 3 * b, s_hi + 3 * b, 3, p)) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int64_t quantise_cost(float cost) {
+  long long q = __float2ll_rn(__fmul_rn(cost, kTwo24));
+  return q < 1 ? 1 : (int64_t)q;
+}
+
+// Per-edge perception transfer F_e(h) = max(C, h + S) from the M sub-steps
+// (Sec. 4.1 heuristic on the quality grid): step m adds inc (n_f - k_m).
+__device__ __forceinline__ void conn_transfer(const Geom& g, const Conn& c, int64_t cost_q,
+                                              int64_t& S, int64_t& C) {
+  const int64_t inc = (g.dim == 6) ? g.Tq : cost_q;
+  int64_t s = 0, h = 0;
+  for (int m = 1; m <= g.M; ++m) {
+    float p[3];
+    conn_point(g, c, m, p);
+    int64_t dm = inc * (int64_t)(g.n_f - level_at(g, p));
+    s += dm;
+    h += dm;
+    h = h < 0 ? 0 : h;
+  }
+  S = s;
+  C = h;
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const unsigned l = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (l >= (unsigned)o) v += t;
+  }
+  return v;
+}
+
+__device__ __forceinline__ int64_t shfl_i64(int64_t v, int src) {
+  return (int64_t)__shfl_sync(0xFFFFFFFFu, (long long)v, src);
+}
+__device__ __forceinline__ int64_t shfl_xor_i64(int64_t v, int m) {
+  return (int64_t)__shfl_xor_sync(0xFFFFFFFFu, (long long)v, m);
+}
+__device__ __forceinline__ int64_t shfl_up_i64(int64_t v, int o) {
+  return (int64_t)__shfl_up_sync(0xFFFFFFFFu, (long long)v, o);
+}
+
+}  // namespace mpap

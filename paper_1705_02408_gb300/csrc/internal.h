@@ -1,0 +1,63 @@
+// Host-side internals of libmpap: handle layouts and cross-file helpers.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mpap.h"
+#include "common.cuh"
+
+struct mpap_roadmap {
+  int dim = 2;
+  uint32_t V = 0;
+  uint64_t E = 0;
+  int M = 16;
+  int n_f = 12, K = 24, G = 1, nb = 0;
+  float r = 0.0f, T = 0.25f, goal_radius = 0.0f;
+  bool has_geometry = false;
+  mpap::Geom geom{};           // device pointers below, constants filled
+  // device arrays (owned)
+  float* x = nullptr;          // [6][V]
+  uint8_t* is_goal = nullptr;  // [V]
+  uint32_t* goal_list = nullptr;
+  uint32_t n_goal = 0;
+  uint32_t* fwd_ptr = nullptr; // [V+1]
+  int4* fwd_edge = nullptr;    // [E] {dst, cost_q, S, C}
+  uint32_t* rev_ptr = nullptr; // [V+1]
+  int4* rev_edge = nullptr;    // [E] {src, cost_q, S, C}
+  float* box_lo = nullptr;     // [nb][3]
+  float* box_hi = nullptr;
+  uint8_t* grid = nullptr;
+};
+
+namespace mpap {
+
+void set_error(const char* fmt, ...);
+bool cuda_ok(cudaError_t e, const char* what);
+
+#define MPAP_CK(call)                                   \
+  do {                                                  \
+    if (!::mpap::cuda_ok((call), #call)) return MPAP_ERR_CUDA; \
+  } while (0)
+
+// Fill the double-integrator constants and scalars of g from (T, M, ...).
+void fill_geom_constants(Geom& g, int dim, int nb, int G, int n_f, int M, float r, float T);
+
+// Roadmap construction (roadmap.cu).
+int32_t build_roadmap_impl(const mpap_scene* scene, const mpap_roadmap_params* prm,
+                           const float* host_x, uint32_t V_given, float r, float T, int M,
+                           float goal_radius, mpap_roadmap** out, cudaStream_t st);
+int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst,
+                              const int32_t* cost_q, const int32_t* S, const int32_t* C,
+                              const uint8_t* is_goal, mpap_roadmap** out, cudaStream_t st);
+void roadmap_free_impl(mpap_roadmap* rm);
+
+// Single-block exclusive scan of n uint32 values into out[0..n] (out[n] = total,
+// saturating at 0xFFFFFFFF with *overflow set).
+void launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* overflow,
+                           cudaStream_t st);
+
+}  // namespace mpap

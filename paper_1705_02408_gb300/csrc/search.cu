@@ -1,0 +1,912 @@
+// Wavefront multiobjective search: Alg. 3 (Explore) of Ichter et al., with
+// RemoveDominated (Sec. 3) and the perception-heuristic cutoff h <= beta.
+//
+// Per wavefront (iteration i) three kernels run over all queries of a batch:
+//   select  one warp per node with open plans: the group B_i of that node (its
+//           open plans with cost <= i lambda r_n) is copied to the group array and
+//           closed (P_open <- P_open \ B); every out-neighbour is marked touched.
+//           A group plan at a goal node ends its query before expansion.
+//   prune   one warp per touched node x ("pull"): each in-edge u -> x whose source
+//           holds group plans yields candidates q = (cost + cost_q, max(C, h + S))
+//           (PH(x, p) of Sec. 3), cut at beta, and merged into the stored front of
+//           x.  The merge is an exact skyline under the weak Pareto order with the
+//           total tie key (creation iteration, parent head): old plans win ties,
+//           candidates tie-break by parent head.  Candidates are consumed in
+//           chunks of 32: filter against the front (binary search), warp bitonic
+//           sort, warp prefix-min, then one merge pass over the front into the
+//           other slab buffer.  Surviving candidates get arena records at the end.
+//   end     one thread per query: termination (goal in group, P_open empty,
+//           iteration cap) and counters.
+//
+// HBM layout (NV = nodes summed over the batch, F = front capacity):
+//   fronts   2 x [NV][F] of {cost i64, h i64, ref u32 (arena | open | new), aux u32}
+//   f_cnt    2 x [NV], cur [NV] (which buffer holds the live front)
+//   group    [cap] {cost, h, ref}, per node offset/count, stamps [NV]
+//   arena    [cap] {head u32, parent u32, iter u32, cost i64} for back-tracing
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace mpap {
+
+struct QueryDev {
+  const uint32_t* rev_ptr;
+  const int4* rev_edge;
+  const uint32_t* fwd_ptr;
+  const int4* fwd_edge;
+  const uint8_t* is_goal;
+  const uint32_t* goal_list;
+  uint32_t n_goal;
+  uint32_t V;
+  uint32_t base;
+  uint32_t max_iters;
+  uint32_t flags;
+  uint32_t pad;
+  int64_t beta;
+  int64_t Lambda;
+};
+
+struct QueryState {
+  long long open_cnt;
+  unsigned long long expansions;
+  unsigned long long plans;
+  uint32_t wavefronts;
+  uint32_t goal_hit;
+  uint32_t done;
+  int32_t status;
+};
+
+struct ResultDev {
+  long long cost;
+  long long h;
+  uint32_t path_len;
+  int32_t status;
+};
+
+struct Ctl {
+  uint32_t oh_n[2];
+  uint32_t t_n;
+  uint32_t g_n;
+  unsigned long long arena_n;
+  uint32_t err;
+  uint32_t n_done;
+};
+
+struct WS {
+  uint64_t NV;
+  uint32_t fcap;
+  uint64_t acap, gcap;
+  long long* f_cost;
+  long long* f_h;
+  uint32_t* f_pid;
+  uint32_t* f_aux;
+  uint32_t* f_cnt;
+  uint8_t* cur;
+  uint32_t* qid;
+  uint32_t* act_stamp;
+  uint32_t* touch_stamp;
+  uint32_t* oh_stamp;
+  uint32_t* g_off;
+  uint32_t* g_cnt;
+  long long* g_cost;
+  long long* g_h;
+  uint32_t* g_pid;
+  uint32_t* oh_list;
+  uint32_t* t_list;
+  uint32_t* a_head;
+  uint32_t* a_parent;
+  uint32_t* a_iter;
+  long long* a_cost;
+  Ctl* ctl;
+  QueryDev* qd;
+  QueryState* qs;
+  ResultDev* res;
+  uint32_t* path;
+  uint32_t path_cap;
+};
+
+}  // namespace mpap
+
+struct mpap_workspace {
+  mpap::WS w{};
+  uint32_t max_q = 0;
+  // host record of the last search (for front export)
+  std::vector<uint32_t> last_V, last_base;
+};
+
+namespace mpap {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+void workspace_free(mpap_workspace* ws);
+
+// Signed 64-bit atomic add through the unsigned overload (two's complement).
+__device__ __forceinline__ void atomic_add_i64(long long* p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+
+__device__ __forceinline__ size_t slab(const WS& w, uint32_t b, uint32_t g) {
+  return ((size_t)b * w.NV + g) * w.fcap;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_fill_qid(WS w, uint32_t nq) {
+  const QueryDev* qd = w.qd;
+  for (uint32_t q = blockIdx.y; q < nq; q += gridDim.y) {
+    const uint32_t base = qd[q].base, V = qd[q].V;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
+      w.qid[base + v] = q;
+  }
+}
+
+__global__ void k_init(WS w, uint32_t nq) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0) {
+    w.ctl->oh_n[0] = nq;
+    w.ctl->oh_n[1] = 0;
+    w.ctl->t_n = 0;
+    w.ctl->g_n = 0;
+    w.ctl->arena_n = nq;
+    w.ctl->err = 0;
+    w.ctl->n_done = 0;
+  }
+  if (q >= nq) return;
+  const uint32_t g = w.qd[q].base;   // x_init is node 0 of every roadmap
+  QueryState s;
+  s.open_cnt = 1;
+  s.expansions = 0;
+  s.plans = 0;
+  s.wavefronts = 0;
+  s.goal_hit = 0;
+  s.done = 0;
+  s.status = 0;
+  w.qs[q] = s;
+  const size_t o = slab(w, 0, g);
+  w.f_cost[o] = 0;
+  w.f_h[o] = 0;
+  w.f_pid[o] = q | kOpen;      // the root plan (x_init, {}, 0, 0) is arena record q
+  w.f_aux[o] = 0;
+  w.f_cnt[g] = 1;
+  w.a_head[q] = 0;
+  w.a_parent[q] = kNone;
+  w.a_iter[q] = 0;
+  w.a_cost[q] = 0;
+  w.oh_list[q] = g;
+  w.oh_stamp[g] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// select: group formation, closing, goal test and marking (warp per node).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w, uint32_t it) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t n_list = w.ctl->oh_n[it & 1];
+  const uint32_t* list = w.oh_list + (size_t)(it & 1) * w.NV;
+  uint32_t* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
+    const uint32_t g = list[k];
+    const uint32_t q = w.qid[g];
+    if (w.qs[q].done) continue;
+    const QueryDev& Q = w.qd[q];
+    const uint32_t b = w.cur[g];
+    const uint32_t n = w.f_cnt[(size_t)b * w.NV + g];
+    const size_t o = slab(w, b, g);
+    const long long thr = (long long)it * Q.Lambda;
+    uint32_t cnt = 0;
+    bool rest = false;
+    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      uint32_t pid = 0;
+      long long c = 0;
+      if (j < n) {
+        pid = w.f_pid[o + j];
+        c = w.f_cost[o + j];
+      }
+      const bool open = (j < n) && (pid & kOpen);
+      cnt += __popc(__ballot_sync(kFull, open && c <= thr));
+      rest = rest || __any_sync(kFull, open && c > thr);
+    }
+    if (cnt) {
+      uint32_t off = 0;
+      if (lane == 0) off = atomicAdd(&w.ctl->g_n, cnt);
+      off = __shfl_sync(kFull, off, 0);
+      const bool fits = (uint64_t)off + cnt <= w.gcap;
+      if (!fits) {
+        if (lane == 0) atomicOr(&w.ctl->err, kErrGroup);
+      } else {
+        uint32_t r0 = 0;
+        for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+          const uint32_t j = j0 + lane;
+          uint32_t pid = 0;
+          long long c = 0;
+          if (j < n) {
+            pid = w.f_pid[o + j];
+            c = w.f_cost[o + j];
+          }
+          const bool isg = (j < n) && (pid & kOpen) && c <= thr;
+          const unsigned bal = __ballot_sync(kFull, isg);
+          if (isg) {
+            const uint32_t r = off + r0 + __popc(bal & lt);
+            w.g_cost[r] = c;
+            w.g_h[r] = w.f_h[o + j];
+            w.g_pid[r] = pid & kPidMask;
+            w.f_pid[o + j] = pid & ~kOpen;
+          }
+          r0 += __popc(bal);
+        }
+        if (lane == 0) {
+          w.g_off[g] = off;
+          w.g_cnt[g] = cnt;
+          w.act_stamp[g] = it;
+          atomic_add_i64(&w.qs[q].open_cnt, -(long long)cnt);
+          if (Q.is_goal[g - Q.base]) w.qs[q].goal_hit = 1u;
+        }
+        // mark the out-neighbours of this node as touched (deduplicated by stamp)
+        const uint32_t u = g - Q.base;
+        const uint32_t e_end = Q.fwd_ptr[u + 1];
+        for (uint32_t e0 = Q.fwd_ptr[u]; e0 < e_end; e0 += 32) {
+          const uint32_t e = e0 + lane;
+          bool first = false;
+          uint32_t gx = 0;
+          if (e < e_end) {
+            gx = Q.base + (uint32_t)__ldg(&Q.fwd_edge[e].x);
+            first = atomicExch(&w.touch_stamp[gx], it) != it;
+          }
+          const unsigned bal = __ballot_sync(kFull, first);
+          if (bal) {
+            uint32_t pos = 0;
+            if (lane == 0) pos = atomicAdd(&w.ctl->t_n, __popc(bal));
+            pos = __shfl_sync(kFull, pos, 0);
+            if (first) w.t_list[pos + __popc(bal & lt)] = gx;
+          }
+        }
+      }
+    }
+    if (rest && lane == 0) {
+      if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = g;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// prune: pull candidates into the front of each touched node (warp per node).
+// ---------------------------------------------------------------------------
+struct WarpSmem {
+  long long s_cost[32];
+  long long s_h[32];
+  uint32_t s_tb[32];
+  uint32_t s_pp[32];
+  uint32_t bins[33];
+};
+
+__device__ __forceinline__ bool key_less(long long c1, long long h1, uint32_t t1, long long c2,
+                                         long long h2, uint32_t t2) {
+  if (c1 != c2) return c1 < c2;
+  if (h1 != h2) return h1 < h2;
+  return t1 < t2;
+}
+
+struct FrontCursor {
+  uint32_t b;        // live buffer
+  uint32_t n;        // live count
+  uint32_t removed_open;
+  bool any_new;
+};
+
+// Merge up to 32 candidates (one per lane, `ok` marks the real ones) into the
+// live front of node g.  Candidate tie key tb = 1 + parent head (old plans have
+// tie key 0, i.e. they win exact (cost, h) ties).
+__device__ void merge_chunk(const WS& w, uint32_t g, FrontCursor& fc, WarpSmem& sm, bool ok,
+                            long long cc, long long ch, uint32_t ctb, uint32_t cpp) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  // 1. drop candidates dominated by the live front (last entry with cost <= cc)
+  {
+    const size_t o = slab(w, fc.b, g);
+    if (ok && fc.n > 0) {
+      uint32_t L = 0, R = fc.n;
+      while (L < R) {
+        const uint32_t mid = (L + R) >> 1;
+        if (w.f_cost[o + mid] <= cc) L = mid + 1; else R = mid;
+      }
+      if (L > 0) {
+        const uint32_t j = L - 1;
+        const long long fcost = w.f_cost[o + j], fh = w.f_h[o + j];
+        const uint32_t fpid = w.f_pid[o + j];
+        const uint32_t ftb = (fpid & kNew) ? w.f_aux[o + j] : 0u;
+        if (fh <= ch && (fcost < cc || fh < ch || ftb < ctb)) ok = false;
+      }
+    }
+  }
+  if (!__any_sync(kFull, ok)) return;
+  // 2. warp bitonic sort by (cost, h, tb); padding lanes sort last
+  long long kc = ok ? cc : LLONG_MAX, kh = ok ? ch : LLONG_MAX;
+  uint32_t kt = ok ? ctb : 0xFFFFFFFFu, kp = cpp;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const long long oc = shfl_xor_i64(kc, j), oh = shfl_xor_i64(kh, j);
+      const uint32_t ot = __shfl_xor_sync(kFull, kt, j), op = __shfl_xor_sync(kFull, kp, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool o_less = key_less(oc, oh, ot, kc, kh, kt);
+      const bool m_less = key_less(kc, kh, kt, oc, oh, ot);
+      const bool take = (lower == up) ? o_less : m_less;
+      if (take) {
+        kc = oc; kh = oh; kt = ot; kp = op;
+      }
+    }
+  }
+  // exclusive prefix minimum of h in sorted order -> skyline of the chunk
+  long long pm = kh;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = shfl_up_i64(pm, o);
+    if (lane >= (unsigned)o) pm = t < pm ? t : pm;
+  }
+  long long excl = shfl_up_i64(pm, 1);
+  if (lane == 0) excl = LLONG_MAX;
+  const bool surv = (kt != 0xFFFFFFFFu) && kh < excl;
+  const unsigned sb = __ballot_sync(kFull, surv);
+  const uint32_t m = __popc(sb);
+  if (surv) {
+    const uint32_t r = __popc(sb & lt);
+    sm.s_cost[r] = kc;
+    sm.s_h[r] = kh;
+    sm.s_tb[r] = kt;
+    sm.s_pp[r] = kp;
+  }
+  sm.bins[lane] = 0;
+  if (lane == 0) sm.bins[32] = 0;
+  __syncwarp();
+  // 3. one pass over the live front: drop entries dominated by a survivor, write
+  //    the kept ones to the other buffer at (kept rank + survivors before them)
+  const uint32_t nb = fc.b ^ 1u;
+  const size_t o = slab(w, fc.b, g), on = slab(w, nb, g);
+  uint32_t kept = 0;
+  uint32_t rem_open = 0;
+  bool overflow = false;
+  for (uint32_t j0 = 0; j0 < fc.n; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    const bool valid = j < fc.n;
+    long long fcost = 0, fh = 0;
+    uint32_t fpid = 0, faux = 0;
+    if (valid) {
+      fcost = w.f_cost[o + j];
+      fh = w.f_h[o + j];
+      fpid = w.f_pid[o + j];
+      faux = w.f_aux[o + j];
+    }
+    const uint32_t ftb = (fpid & kNew) ? faux : 0u;
+    uint32_t L = 0, R = m;
+    while (L < R) {
+      const uint32_t mid = (L + R) >> 1;
+      if (sm.s_cost[mid] <= fcost) L = mid + 1; else R = mid;
+    }
+    bool dom = false;
+    if (valid && L > 0) {
+      const uint32_t s = L - 1;
+      const long long scost = sm.s_cost[s], sh = sm.s_h[s];
+      dom = sh <= fh && (scost < fcost || sh < fh || sm.s_tb[s] < ftb);
+    }
+    const bool keep = valid && !dom;
+    if (dom && (fpid & kOpen) && !(fpid & kNew)) rem_open++;
+    const unsigned kb = __ballot_sync(kFull, keep);
+    if (keep) {
+      const uint32_t pos = kept + __popc(kb & lt) + L;
+      if (pos < w.fcap) {
+        w.f_cost[on + pos] = fcost;
+        w.f_h[on + pos] = fh;
+        w.f_pid[on + pos] = fpid;
+        w.f_aux[on + pos] = faux;
+      } else {
+        overflow = true;
+      }
+      atomicAdd(&sm.bins[L], 1u);
+    }
+    kept += __popc(kb);
+  }
+  __syncwarp();
+  const uint32_t before = warp_incl_scan(lane < m ? sm.bins[lane] : 0u);
+  if (lane < m) {
+    const uint32_t pos = lane + before;
+    if (pos < w.fcap) {
+      w.f_cost[on + pos] = sm.s_cost[lane];
+      w.f_h[on + pos] = sm.s_h[lane];
+      w.f_pid[on + pos] = sm.s_pp[lane] | kNew;
+      w.f_aux[on + pos] = sm.s_tb[lane];
+    } else {
+      overflow = true;
+    }
+  }
+  uint32_t n_new = kept + m;
+  if (__any_sync(kFull, overflow) || n_new > w.fcap) {
+    if (lane == 0) atomicOr(&w.ctl->err, kErrFront);
+    n_new = n_new > w.fcap ? w.fcap : n_new;
+  }
+  for (int s = 16; s > 0; s >>= 1) rem_open += __shfl_xor_sync(kFull, rem_open, s);
+  fc.removed_open += rem_open;
+  fc.b = nb;
+  fc.n = n_new;
+  fc.any_new = true;
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prune(WS w, uint32_t it) {
+  __shared__ WarpSmem smem[kWarpsPerBlock];
+  WarpSmem& sm = smem[threadIdx.x >> 5];
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t n_list = w.ctl->t_n;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  uint32_t* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
+  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
+    const uint32_t g = w.t_list[k];
+    const uint32_t q = w.qid[g];
+    const QueryDev& Q = w.qd[q];
+    {
+      const QueryState& s = w.qs[q];
+      if (s.done || (s.goal_hit && !(Q.flags & MPAP_QUERY_NO_GOAL_STOP)) || s.wavefronts >= Q.max_iters)
+        continue;
+    }
+    const uint32_t x = g - Q.base;
+    FrontCursor fc;
+    fc.b = w.cur[g];
+    fc.n = w.f_cnt[(size_t)fc.b * w.NV + g];
+    fc.removed_open = 0;
+    fc.any_new = false;
+    unsigned long long exps = 0;
+    const uint32_t e_end = Q.rev_ptr[x + 1];
+    for (uint32_t e0 = Q.rev_ptr[x]; e0 < e_end; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      int4 ed = make_int4(0, 0, 0, 0);
+      uint32_t cnt = 0, goff = 0;
+      if (e < e_end) {
+        ed = __ldg(&Q.rev_edge[e]);
+        const uint32_t gu = Q.base + (uint32_t)ed.x;
+        if (w.act_stamp[gu] == it) {
+          cnt = w.g_cnt[gu];
+          goff = w.g_off[gu];
+        }
+      }
+      const uint32_t incl = warp_incl_scan(cnt);
+      const uint32_t total = __shfl_sync(kFull, incl, 31);
+      const uint32_t excl = incl - cnt;
+      exps += total;
+      for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+        const uint32_t c = c0 + lane;
+        // owner lane: the last lane whose exclusive offset is <= c
+        uint32_t owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t probe = owner + step;
+          const uint32_t ev = __shfl_sync(kFull, excl, probe);
+          if (ev <= c) owner = probe;
+        }
+        const uint32_t o_excl = __shfl_sync(kFull, excl, owner);
+        const uint32_t o_goff = __shfl_sync(kFull, goff, owner);
+        const int o_src = __shfl_sync(kFull, ed.x, owner);
+        const int o_cq = __shfl_sync(kFull, ed.y, owner);
+        const int o_S = __shfl_sync(kFull, ed.z, owner);
+        const int o_C = __shfl_sync(kFull, ed.w, owner);
+        bool ok = false;
+        long long cc = 0, ch = 0;
+        uint32_t pp = 0;
+        if (c < total) {
+          const uint32_t gi = o_goff + (c - o_excl);
+          cc = w.g_cost[gi] + (long long)o_cq;
+          const long long hh = w.g_h[gi] + (long long)o_S;
+          ch = hh > (long long)o_C ? hh : (long long)o_C;
+          pp = w.g_pid[gi];
+          ok = ch <= Q.beta;          // perception-heuristic cutoff
+        }
+        merge_chunk(w, g, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
+      }
+    }
+    if (fc.any_new) {
+      // give every new front entry an arena record and mark it open
+      const size_t o = slab(w, fc.b, g);
+      uint32_t n_new = 0;
+      for (uint32_t j0 = 0; j0 < fc.n; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        uint32_t pid = 0;
+        if (j < fc.n) pid = w.f_pid[o + j];
+        const bool isnew = (j < fc.n) && (pid & kNew);
+        const unsigned bal = __ballot_sync(kFull, isnew);
+        if (!bal) continue;
+        unsigned long long a0 = 0;
+        if (lane == 0) a0 = atomicAdd(&w.ctl->arena_n, (unsigned long long)__popc(bal));
+        a0 = __shfl_sync(kFull, a0, 0);
+        if (isnew) {
+          const unsigned long long a = a0 + __popc(bal & lt);
+          if (a < w.acap) {
+            w.a_head[a] = x;
+            w.a_parent[a] = pid & kPidMask;
+            w.a_iter[a] = it + 1;
+            w.a_cost[a] = w.f_cost[o + j];
+            w.f_pid[o + j] = (uint32_t)a | kOpen;
+          } else {
+            atomicOr(&w.ctl->err, kErrArena);
+            w.f_pid[o + j] = kOpen;
+          }
+          w.f_aux[o + j] = 0;
+        }
+        n_new += __popc(bal);
+      }
+      if (lane == 0) {
+        w.cur[g] = (uint8_t)fc.b;
+        w.f_cnt[(size_t)fc.b * w.NV + g] = fc.n;
+        atomic_add_i64(&w.qs[q].open_cnt, (long long)n_new - (long long)fc.removed_open);
+        atomicAdd(&w.qs[q].plans, (unsigned long long)n_new);
+        if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = g;
+      }
+    }
+    if (lane == 0 && exps) atomicAdd(&w.qs[q].expansions, exps);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// end of wavefront: termination per query (thread per query).
+// ---------------------------------------------------------------------------
+__global__ void k_end(WS w, uint32_t it, uint32_t nq) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nq) {
+    QueryState& s = w.qs[q];
+    const QueryDev& Q = w.qd[q];
+    if (!s.done) {
+      if (w.ctl->err) {
+        s.done = 1;
+        s.status = MPAP_ERR_CAPACITY;
+      } else if (s.goal_hit && !(Q.flags & MPAP_QUERY_NO_GOAL_STOP)) {
+        s.done = 1;
+      } else if (s.wavefronts >= Q.max_iters) {
+        s.done = 1;
+        s.status = MPAP_ERR_ITER_LIMIT;
+      } else {
+        s.wavefronts += 1;
+        if (s.open_cnt == 0) s.done = 1;
+      }
+      if (s.done) atomicAdd(&w.ctl->n_done, 1u);
+    }
+  }
+  if (q == 0) {
+    // the list consumed in this iteration becomes the append target of the next
+    w.ctl->oh_n[it & 1] = 0;
+    w.ctl->t_n = 0;
+    w.ctl->g_n = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Solution selection (Alg. 3 final lines) and back-tracing (block per query).
+// Among all stored plans at goal nodes: minimum cost, then h, then the tie key
+// (creation iteration, parent head, parent cost), then head index.
+// ---------------------------------------------------------------------------
+struct Best {
+  long long cost, h, pcost;
+  uint32_t iter, phead, head, ref;
+};
+
+__device__ __forceinline__ bool better(const Best& a, const Best& b) {
+  if (a.cost != b.cost) return a.cost < b.cost;
+  if (a.h != b.h) return a.h < b.h;
+  if (a.iter != b.iter) return a.iter < b.iter;
+  if (a.phead != b.phead) return a.phead < b.phead;
+  if (a.pcost != b.pcost) return a.pcost < b.pcost;
+  return a.head < b.head;
+}
+
+__global__ void k_finalize(WS w, uint32_t nq) {
+  const uint32_t q = blockIdx.x;
+  if (q >= nq) return;
+  const QueryDev& Q = w.qd[q];
+  const QueryState& s = w.qs[q];
+  __shared__ Best sb[256];
+  Best best;
+  best.cost = LLONG_MAX;
+  best.ref = kNone;
+  if (s.status == 0) {
+    for (uint32_t i = threadIdx.x; i < Q.n_goal; i += blockDim.x) {
+      const uint32_t v = Q.goal_list[i];
+      const uint32_t g = Q.base + v;
+      const uint32_t b = w.cur[g];
+      const uint32_t n = w.f_cnt[(size_t)b * w.NV + g];
+      const size_t o = slab(w, b, g);
+      for (uint32_t j = 0; j < n; ++j) {
+        Best c;
+        c.cost = w.f_cost[o + j];
+        c.h = w.f_h[o + j];
+        c.ref = w.f_pid[o + j] & kPidMask;
+        c.iter = w.a_iter[c.ref];
+        const uint32_t par = w.a_parent[c.ref];
+        c.phead = (par == kNone) ? kNone : w.a_head[par];
+        c.pcost = (par == kNone) ? 0 : w.a_cost[par];
+        c.head = v;
+        if (best.ref == kNone || better(c, best)) best = c;
+      }
+    }
+  }
+  sb[threadIdx.x] = best;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      const Best& o = sb[threadIdx.x + st];
+      if (o.ref != kNone && (sb[threadIdx.x].ref == kNone || better(o, sb[threadIdx.x]))) sb[threadIdx.x] = o;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ResultDev r;
+    r.status = s.status;
+    r.cost = 0;
+    r.h = 0;
+    r.path_len = 0;
+    if (s.status == 0) {
+      const Best b = sb[0];
+      if (b.ref == kNone) {
+        r.status = MPAP_NO_SOLUTION;
+      } else {
+        r.cost = b.cost;
+        r.h = b.h;
+        uint32_t* path = w.path + (size_t)q * w.path_cap;
+        uint32_t len = 0;
+        uint32_t a = b.ref;
+        while (a != kNone && len <= w.path_cap) {
+          if (len < w.path_cap) path[len] = w.a_head[a];
+          ++len;
+          a = w.a_parent[a];
+        }
+        if (len > w.path_cap) {
+          r.status = MPAP_ERR_CAPACITY;
+        } else {
+          for (uint32_t i = 0; i < len / 2; ++i) {
+            const uint32_t t = path[i];
+            path[i] = path[len - 1 - i];
+            path[len - 1 - i] = t;
+          }
+        }
+        r.path_len = len;
+      }
+    }
+    w.res[q] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+int sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <typename T>
+bool walloc(T** p, size_t n) {
+  return cuda_ok(cudaMalloc((void**)p, (n ? n : 1) * sizeof(T)), "cudaMalloc(workspace)");
+}
+
+}  // namespace
+
+int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans, uint32_t max_q,
+                         mpap_workspace** out) {
+  if (!out || total_nodes == 0 || total_nodes > 0xFFFFFFF0ull || front_cap == 0 || max_plans == 0 ||
+      max_plans > (uint64_t)kPidMask) {
+    set_error("mpap_workspace_create: invalid sizes");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  mpap_workspace* ws = new mpap_workspace();
+  WS& w = ws->w;
+  w.NV = total_nodes;
+  w.fcap = front_cap;
+  w.acap = max_plans;
+  w.gcap = max_plans;
+  w.path_cap = 4096;
+  ws->max_q = max_q;
+  const size_t slots = 2 * (size_t)w.NV * w.fcap;
+  bool ok = walloc(&w.f_cost, slots) && walloc(&w.f_h, slots) && walloc(&w.f_pid, slots) &&
+            walloc(&w.f_aux, slots) && walloc(&w.f_cnt, 2 * w.NV) && walloc(&w.cur, w.NV) &&
+            walloc(&w.qid, w.NV) && walloc(&w.act_stamp, w.NV) && walloc(&w.touch_stamp, w.NV) &&
+            walloc(&w.oh_stamp, w.NV) && walloc(&w.g_off, w.NV) && walloc(&w.g_cnt, w.NV) &&
+            walloc(&w.g_cost, w.gcap) && walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) &&
+            walloc(&w.oh_list, 2 * w.NV) && walloc(&w.t_list, w.NV) && walloc(&w.a_head, w.acap) &&
+            walloc(&w.a_parent, w.acap) && walloc(&w.a_iter, w.acap) && walloc(&w.a_cost, w.acap) &&
+            walloc(&w.ctl, 1) && walloc(&w.qd, max_q) && walloc(&w.qs, max_q) && walloc(&w.res, max_q) &&
+            walloc(&w.path, (size_t)max_q * w.path_cap);
+  if (!ok) {
+    workspace_free(ws);
+    return MPAP_ERR_CUDA;
+  }
+  *out = ws;
+  return MPAP_OK;
+}
+
+void workspace_free(mpap_workspace* ws) {
+  if (!ws) return;
+  WS& w = ws->w;
+  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.f_cnt, w.cur, w.qid, w.act_stamp, w.touch_stamp,
+                  w.oh_stamp, w.g_off, w.g_cnt, w.g_cost, w.g_h, w.g_pid, w.oh_list, w.t_list,
+                  w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl, w.qd, w.qs, w.res, w.path};
+  for (void* p : ptrs) cudaFree(p);
+  delete ws;
+}
+
+int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs, uint32_t nq,
+                          mpap_result* outs, cudaStream_t st) {
+  WS& w = ws->w;
+  if (nq == 0) return MPAP_OK;
+  if (nq > ws->max_q) {
+    set_error("search: %u queries exceed the workspace's %u", nq, ws->max_q);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  std::vector<QueryDev> qd(nq);
+  uint64_t total = 0;
+  uint32_t max_iters = 0;
+  for (uint32_t i = 0; i < nq; ++i) {
+    const mpap_roadmap* rm = rms[i];
+    if (!rm || rm->V < 1) {
+      set_error("search: null or empty roadmap %u", i);
+      return MPAP_ERR_INVALID_ARG;
+    }
+    if ((qs[i].group_width_q <= 0 && (!(qs[i].lambda > 0.0f) || !(qs[i].lambda <= 1.0f))) ||
+        qs[i].beta < 0 || qs[i].max_iters == 0) {
+      set_error("search: query %u needs lambda in (0, 1] (or group_width_q > 0), beta >= 0, max_iters > 0", i);
+      return MPAP_ERR_INVALID_ARG;
+    }
+    QueryDev d{};
+    d.rev_ptr = rm->rev_ptr;
+    d.rev_edge = rm->rev_edge;
+    d.fwd_ptr = rm->fwd_ptr;
+    d.fwd_edge = rm->fwd_edge;
+    d.is_goal = rm->is_goal;
+    d.goal_list = rm->goal_list;
+    d.n_goal = rm->n_goal;
+    d.V = rm->V;
+    d.base = (uint32_t)total;
+    d.max_iters = qs[i].max_iters;
+    d.flags = qs[i].flags;
+    d.beta = qs[i].beta;
+    // Lambda = round(lambda r_n 2^24), the group threshold quantum (or the
+    // caller's explicit width in cost quanta).
+    d.Lambda = qs[i].group_width_q > 0 ? qs[i].group_width_q
+                                       : (int64_t)llrint((double)qs[i].lambda * (double)rm->r * 16777216.0);
+    if (d.Lambda < 1) d.Lambda = 1;
+    total += rm->V;
+    max_iters = std::max(max_iters, qs[i].max_iters);
+    qd[i] = d;
+  }
+  if (total > w.NV) {
+    set_error("search: %llu nodes exceed the workspace's %llu", (unsigned long long)total,
+              (unsigned long long)w.NV);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  ws->last_V.resize(nq);
+  ws->last_base.resize(nq);
+  for (uint32_t i = 0; i < nq; ++i) {
+    ws->last_V[i] = qd[i].V;
+    ws->last_base[i] = qd[i].base;
+  }
+  const size_t NVu = (size_t)total;
+  MPAP_CK(cudaMemcpyAsync(w.qd, qd.data(), sizeof(QueryDev) * nq, cudaMemcpyHostToDevice, st));
+  MPAP_CK(cudaMemsetAsync(w.f_cnt, 0, sizeof(uint32_t) * NVu, st));
+  MPAP_CK(cudaMemsetAsync(w.f_cnt + w.NV, 0, sizeof(uint32_t) * NVu, st));
+  MPAP_CK(cudaMemsetAsync(w.cur, 0, NVu, st));
+  MPAP_CK(cudaMemsetAsync(w.act_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
+  MPAP_CK(cudaMemsetAsync(w.touch_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
+  MPAP_CK(cudaMemsetAsync(w.oh_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
+  dim3 fg((unsigned)std::min<uint64_t>((total / nq + 255) / 256 + 1, 64), std::min(nq, 1024u));
+  k_fill_qid<<<fg, 256, 0, st>>>(w, nq);
+  k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq);
+  MPAP_CK(cudaGetLastError());
+
+  const int blocks_sel = 16 * sms();
+  const int blocks_pr = 16 * sms();
+  uint32_t it = 0;
+  const uint32_t check_every = 2;
+  Ctl hc{};
+  while (true) {
+    for (uint32_t r = 0; r < check_every; ++r, ++it) {
+      k_select<<<blocks_sel, kWarpsPerBlock * 32, 0, st>>>(w, it);
+      k_prune<<<blocks_pr, kWarpsPerBlock * 32, 0, st>>>(w, it);
+      k_end<<<(nq + 127) / 128, 128, 0, st>>>(w, it, nq);
+    }
+    MPAP_CK(cudaGetLastError());
+    MPAP_CK(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    MPAP_CK(cudaStreamSynchronize(st));
+    if (hc.n_done >= nq) break;
+    if ((uint64_t)it > (uint64_t)max_iters + 4) {
+      set_error("search: wavefront loop did not terminate");
+      return MPAP_ERR_ITER_LIMIT;
+    }
+  }
+  k_finalize<<<nq, 256, 0, st>>>(w, nq);
+  MPAP_CK(cudaGetLastError());
+  std::vector<ResultDev> res(nq);
+  std::vector<QueryState> qsh(nq);
+  MPAP_CK(cudaMemcpyAsync(res.data(), w.res, sizeof(ResultDev) * nq, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaMemcpyAsync(qsh.data(), w.qs, sizeof(QueryState) * nq, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaStreamSynchronize(st));
+  int32_t rc = MPAP_OK;
+  for (uint32_t i = 0; i < nq; ++i) {
+    mpap_result& o = outs[i];
+    o.status = res[i].status;
+    o.cost = res[i].cost;
+    o.h = res[i].h;
+    o.wavefronts = qsh[i].wavefronts;
+    o.expansions = qsh[i].expansions;
+    o.plans = qsh[i].plans;
+    o.path_len = res[i].path_len;
+    if (o.status == MPAP_OK) {
+      if (o.path && o.path_cap >= o.path_len) {
+        MPAP_CK(cudaMemcpyAsync(o.path, w.path + (size_t)i * w.path_cap, 4 * (size_t)o.path_len,
+                                cudaMemcpyDeviceToHost, st));
+      } else if (o.path_cap < o.path_len) {
+        o.status = MPAP_ERR_INVALID_ARG;
+      }
+    }
+    if (o.status < 0 && rc == MPAP_OK) rc = o.status;
+  }
+  MPAP_CK(cudaStreamSynchronize(st));
+  if (hc.err) {
+    set_error("search: device capacity exceeded (flags 0x%x: 1 front, 2 arena, 4 group)", hc.err);
+    rc = MPAP_ERR_CAPACITY;
+  }
+  return rc;
+}
+
+int32_t search_fronts_impl(mpap_workspace* ws, uint32_t index, uint32_t* front_ptr, int64_t* cost,
+                           int64_t* h, uint64_t cap, uint64_t* total, cudaStream_t st) {
+  const WS& w = ws->w;
+  if (index >= ws->last_V.size()) {
+    set_error("search_fronts: no query %u in the last search", index);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  const uint32_t V = ws->last_V[index], base = ws->last_base[index];
+  std::vector<uint8_t> cur(V);
+  std::vector<uint32_t> cnt(2 * (size_t)V);
+  MPAP_CK(cudaMemcpyAsync(cur.data(), w.cur + base, V, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaMemcpyAsync(cnt.data(), w.f_cnt + base, 4 * (size_t)V, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaMemcpyAsync(cnt.data() + V, w.f_cnt + w.NV + base, 4 * (size_t)V, cudaMemcpyDeviceToHost, st));
+  const size_t slots = (size_t)V * w.fcap;
+  std::vector<long long> c0(slots), h0(slots), c1(slots), h1(slots);
+  MPAP_CK(cudaMemcpyAsync(c0.data(), w.f_cost + (size_t)base * w.fcap, 8 * slots, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaMemcpyAsync(h0.data(), w.f_h + (size_t)base * w.fcap, 8 * slots, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaMemcpyAsync(c1.data(), w.f_cost + ((size_t)w.NV + base) * w.fcap, 8 * slots,
+                          cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaMemcpyAsync(h1.data(), w.f_h + ((size_t)w.NV + base) * w.fcap, 8 * slots,
+                          cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaStreamSynchronize(st));
+  uint64_t t = 0;
+  for (uint32_t v = 0; v < V; ++v) {
+    if (front_ptr) front_ptr[v] = (uint32_t)t;
+    const uint32_t b = cur[v];
+    const uint32_t n = cnt[(size_t)b * V + v];
+    const long long* cs = b ? c1.data() : c0.data();
+    const long long* hs = b ? h1.data() : h0.data();
+    for (uint32_t j = 0; j < n; ++j, ++t) {
+      if (t < cap) {
+        if (cost) cost[t] = cs[(size_t)v * w.fcap + j];
+        if (h) h[t] = hs[(size_t)v * w.fcap + j];
+      }
+    }
+  }
+  if (front_ptr) front_ptr[V] = (uint32_t)t;
+  if (total) *total = t;
+  return t <= cap ? MPAP_OK : MPAP_ERR_INVALID_ARG;
+}
+
+}  // namespace mpap

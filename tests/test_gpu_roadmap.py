@@ -1,0 +1,70 @@
+"""GPU roadmap construction (Alg. 2 + per-edge transfers) vs the oracle: the
+node states and the whole CSR, bit for bit."""
+import numpy as np
+import pytest
+
+import scenegen
+from _gpu import assert_same_graph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mp():
+    from paper_1705_02408_gb300 import build
+    build.build()
+    import paper_1705_02408_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("name,seed,n,r", [
+    ("2d", 1, 1000, None), ("2d", 2, 1000, None), ("2d", 3, 257, 0.2),
+    ("3d", 1, 2000, None), ("3d", 4, 777, 0.2),
+    ("6d", 1, 2000, None), ("6d", 5, 1500, 20.0),
+])
+def test_roadmap_matches_oracle(mp, orc, name, seed, n, r):
+    sc = scenegen.make_scene(name, seed, query_id=seed)
+    rg = mp.build_roadmap_for_scene(sc, n=n, r=r)
+    ro = orc.build_roadmap(sc, n=n, r=r)
+    assert_same_graph(rg.export(), ro.graph())
+
+
+def test_roadmap_device_inputs(mp, orc):
+    sc = scenegen.make_scene("3d", 9)
+    rg = mp.build_roadmap_for_scene(sc, n=1200, device_inputs=True)
+    ro = orc.build_roadmap(sc, n=1200)
+    assert_same_graph(rg.export(), ro.graph())
+
+
+def test_roadmap_from_points(mp, orc):
+    rng = np.random.default_rng(3)
+    sc = scenegen.make_scene("2d", 4)
+    x = np.zeros((6, 300), np.float32)
+    x[:2] = rng.random((2, 300)).astype(np.float32)
+    x[:2, 0] = 0.05; x[:2, 1] = 0.95
+    ro = orc.build_roadmap_from_points(2, sc.box_lo, sc.box_hi, sc.grid, 64, x, r=0.15)
+    rg = mp.build_roadmap_from_points(2, sc.box_lo, sc.box_hi, sc.grid, 64, x, r=0.15)
+    assert_same_graph(rg.export(), ro.graph())
+
+
+def test_roadmap_edge_cases(mp, orc):
+    # no obstacles, tiny n, ragged tiles (n + 2 not a multiple of 256 or 8)
+    sc = scenegen.make_scene("2d", 1)
+    sc.box_lo = np.zeros((0, 3), np.float32); sc.box_hi = np.zeros((0, 3), np.float32)
+    sc.cfg = scenegen.config("2d", nb=0)
+    for n in (1, 7, 255, 263):
+        rg = mp.build_roadmap_for_scene(sc, n=n, r=0.3)
+        ro = orc.build_roadmap(sc, n=n, r=0.3)
+        assert_same_graph(rg.export(), ro.graph())
+    # radius too small for any edge
+    rg = mp.build_roadmap_for_scene(sc, n=50, r=1e-6)
+    assert rg.E == 0
+
+
+def test_roadmap_full_size_6d(mp, orc):
+    """The 6D double-integrator roadmap at full size (16000 samples), as timed by
+    the benchmark, compared edge for edge."""
+    sc = scenegen.make_scene("6d", 1, query_id=1)
+    rg = mp.build_roadmap_for_scene(sc)
+    ro = orc.build_roadmap(sc)
+    assert_same_graph(rg.export(), ro.graph())

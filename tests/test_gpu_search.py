@@ -1,0 +1,156 @@
+"""GPU wavefront search (Alg. 3) vs the oracle: final Pareto fronts of every node,
+solution cost, heuristic and path, wavefront and expansion counts -- bit-exact."""
+import os
+
+import numpy as np
+import pytest
+
+import scenegen
+from _gpu import BIG, assert_same_search
+from _search_ref import random_graph
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def mp():
+    from paper_1705_02408_gb300 import build
+    build.build()
+    import paper_1705_02408_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ws(mp):
+    return mp.Workspace(40000, front_cap=2048, max_plans=1 << 23)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_random_graphs(mp, orc, ws, seed):
+    rng = np.random.default_rng(500 + seed)
+    V = int(rng.integers(3, 40))
+    g = random_graph(rng, V, p_edge=float(rng.uniform(0.1, 0.5)), cmax=int(rng.integers(1, 9)),
+                     dmax=int(rng.integers(1, 6)))
+    ro = orc.roadmap_from_csr(*g)
+    rg = mp.roadmap_from_csr(*g)
+    for beta in (int(rng.integers(0, 12)), BIG):
+        for lam in (1, 2, 7, 1000):
+            for stop in (True, False):
+                a = orc.explore(ro, beta, lam, goal_termination=stop)
+                b = mp.search(ws, rg, beta, group_width_q=lam, goal_stop=stop)
+                assert_same_search(b, a, ws)
+
+
+def test_narrow_passage(mp, ws):
+    lines = [l.split() for l in open(os.path.join(GOLDEN, "narrow_passage_fig2.txt"))
+             if l.strip() and not l.startswith("#")]
+    V, beta, goal_node = map(int, lines[0])
+    edges = sorted(tuple(map(int, l)) for l in lines[1:-1])
+    exp = list(map(int, lines[-1]))
+    row_ptr = np.zeros(V + 1, np.uint32)
+    for s, *_ in edges:
+        row_ptr[s + 1:] += 1
+    cols = list(zip(*edges))
+    goal = np.zeros(V, np.uint8); goal[goal_node] = 1
+    rg = mp.roadmap_from_csr(row_ptr, cols[1], cols[2], cols[3], cols[4], goal)
+    r = mp.search(ws, rg, beta, group_width_q=1)
+    assert [r.status, r.cost, r.h] + list(r.path) == exp
+
+
+@pytest.mark.parametrize("name,seed,n,beta_mode", [
+    ("2d", 1, 1000, "pct"), ("2d", 2, 1000, "pct"), ("2d", 3, 1000, "pct"), ("2d", 4, 1000, "inf"),
+    ("2d", 5, 600, "zero"), ("3d", 1, 2500, "pct"), ("6d", 1, 3000, "pct"), ("6d", 2, 3000, "inf"),
+])
+def test_scenes(mp, orc, ws, name, seed, n, beta_mode):
+    sc = scenegen.make_scene(name, seed, query_id=seed)
+    r = sc.cfg.r if name != "6d" else 18.0
+    ro = orc.build_roadmap(sc, n=n, r=r)
+    rg = mp.build_roadmap_for_scene(sc, n=n, r=r)
+    beta = {"pct": orc.beta_percentile(ro), "inf": BIG, "zero": 0}[beta_mode]
+    lam_q = orc.group_width(0.5, r)
+    a = orc.explore(ro, beta, lam_q)
+    b = mp.search(ws, rg, beta, lam=0.5)
+    assert_same_search(b, a, ws)
+    # exhaustive variant (no goal stop)
+    a2 = orc.explore(ro, beta, lam_q, goal_termination=False)
+    b2 = mp.search(ws, rg, beta, lam=0.5, goal_stop=False)
+    assert_same_search(b2, a2, ws)
+    # a front cap below the largest oracle front is reported, not truncated
+    biggest = int(np.diff(a2.front_ptr).max())
+    if biggest > 1:
+        small = mp.Workspace(rg.V, front_cap=biggest - 1, max_plans=1 << 23)
+        with pytest.raises(mp.MpapError) as e:
+            mp.search(small, rg, beta, lam=0.5, goal_stop=False)
+        assert e.value.status == mp.MPAP_ERR_CAPACITY
+        exact = mp.Workspace(rg.V, front_cap=biggest, max_plans=1 << 23)
+        assert_same_search(mp.search(exact, rg, beta, lam=0.5, goal_stop=False), a2, exact)
+
+
+def test_batch_matches_individual(mp, orc):
+    specs = [("2d", 1, 1000), ("3d", 2, 1500), ("6d", 3, 2000), ("2d", 7, 333), ("6d", 4, 1200)]
+    rgs, ros, qs, betas = [], [], [], []
+    for name, seed, n in specs:
+        sc = scenegen.make_scene(name, seed, query_id=seed)
+        r = sc.cfg.r if name != "6d" else 18.0
+        ro = orc.build_roadmap(sc, n=n, r=r)
+        rg = mp.build_roadmap_for_scene(sc, n=n, r=r)
+        beta = orc.beta_percentile(ro)
+        ros.append((ro, r)); rgs.append(rg); betas.append(beta)
+        qs.append(mp.make_query(beta, 0.5))
+    total = sum(rg.V for rg in rgs)
+    wsb = mp.Workspace(total, front_cap=1024, max_plans=1 << 23)
+    res = mp.search_batch(wsb, rgs, qs)
+    for i, ((ro, r), beta) in enumerate(zip(ros, betas)):
+        a = orc.explore(ro, beta, orc.group_width(0.5, r))
+        assert_same_search(res[i], a, wsb, index=i)
+
+
+def test_capacity_and_iteration_limits(mp, orc):
+    sc = scenegen.make_scene("2d", 2, query_id=2)
+    ro = orc.build_roadmap(sc)
+    rg = mp.build_roadmap_for_scene(sc)
+    beta = orc.beta_percentile(ro)
+    small = mp.Workspace(rg.V, front_cap=4, max_plans=1 << 20)
+    with pytest.raises(mp.MpapError) as e:
+        mp.search(small, rg, beta)
+    assert e.value.status == mp.MPAP_ERR_CAPACITY
+    tiny_arena = mp.Workspace(rg.V, front_cap=1024, max_plans=64)
+    with pytest.raises(mp.MpapError) as e:
+        mp.search(tiny_arena, rg, beta)
+    assert e.value.status == mp.MPAP_ERR_CAPACITY
+    big = mp.Workspace(rg.V, front_cap=1024, max_plans=1 << 22)
+    a = orc.explore(ro, beta, orc.group_width(0.5, sc.cfg.r), max_iters=5)
+    assert a.status == -4
+    with pytest.raises(mp.MpapError) as e:
+        mp.search(big, rg, beta, max_iters=5)
+    assert e.value.status == mp.MPAP_ERR_ITER_LIMIT
+    # the workspace stays usable after errors
+    ok = mp.search(big, rg, beta)
+    assert_same_search(ok, orc.explore(ro, beta, orc.group_width(0.5, sc.cfg.r)), big)
+
+
+def test_start_in_goal_and_isolated_start(mp, orc, ws):
+    # x_init inside X_goal: the first group already holds a goal plan
+    g = (np.array([0, 1, 1], np.uint32), np.array([1], np.uint32), np.array([3], np.int32),
+         np.array([0], np.int32), np.array([0], np.int32), np.array([1, 0], np.uint8))
+    r = mp.search(ws, mp.roadmap_from_csr(*g), BIG, group_width_q=1)
+    assert (r.status, r.cost, list(r.path), r.wavefronts, r.expansions) == (0, 0, [0], 0, 0)
+    # no out-edges at x_init: P_open empties after one wavefront
+    g = (np.array([0, 0, 0], np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.int32),
+         np.zeros(0, np.int32), np.zeros(0, np.int32), np.array([0, 1], np.uint8))
+    r = mp.search(ws, mp.roadmap_from_csr(*g), BIG, group_width_q=1)
+    a = orc.explore(orc.roadmap_from_csr(*g), BIG, 1)
+    assert r.status == a.status == 1 and r.wavefronts == a.wavefronts
+
+
+def test_full_size_6d(mp, orc):
+    """The 6D, 16000-sample configuration the benchmark times: full comparison."""
+    sc = scenegen.make_scene("6d", 1, query_id=1)
+    ro = orc.build_roadmap(sc)
+    rg = mp.build_roadmap_for_scene(sc)
+    beta = orc.beta_percentile(ro)
+    wsf = mp.Workspace(rg.V, front_cap=64, max_plans=1 << 24)
+    a = orc.explore(ro, beta, orc.group_width(0.5, sc.cfg.r))
+    b = mp.search(wsf, rg, beta, lam=0.5)
+    assert_same_search(b, a, wsf)
