@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""MPAP hot-path benchmark: plan-edge expansions/s and ms/query on the 6D
+double-integrator workload (16000 samples per roadmap, 30 boxes, 32^3 quality
+grid, 4096 Monte Carlo rollouts), batched versus plain.
+
+One step processes a batch of B seeded queries (default 64) through the whole
+hot path: roadmap construction (Alg. 2 with per-edge heuristic transfers), one
+lock-step batched wavefront search (Alg. 3), and batched Monte Carlo
+certification of the returned plans.  The scene inputs are resident in HBM
+before timing starts; every step builds ~1.6 GB of roadmaps, larger than L2, so
+no L2 flush is needed between steps.
+
+  value   plan-edge expansions of the step / step time (device CUDA events)
+  e2e     the same through the C ABI with host scene buffers (copies timed)
+  plain   the same queries searched one call at a time (search only), reported
+          beside the batched search-only numbers
+
+`--impl reference` times the CPU oracle (single thread, as it stands) on a bounded
+sample of the same workload (one query per step) and prints the same line.
+Launch with torchrun for N > 1: queries are sharded by rank (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scenegen  # noqa: E402
+
+METRIC = "plan-edge expansions/s and ms/query (6D, 16k samples), batched vs plain"
+UNIT = "expansions/s"
+WORKLOAD = "6D double integrator, 16000 samples, 30 boxes, 32^3 grid, 4096 MC rollouts"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mpap", choices=["mpap", "reference"])
+    ap.add_argument("--queries", type=int, default=64, help="queries per step per GPU")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def scenes_for_rank(rank, count):
+    cfg = scenegen.config("6d")
+    calib = scenegen.load_calibration()
+    out = []
+    for i in range(count):
+        seed = rank * count + i + 1
+        sc = scenegen.make_scene(cfg, seed, query_id=seed)
+        key = scenegen.calib_key(cfg, seed)
+        sc.extra["beta"] = calib[key]["beta"] if key in calib else None
+        out.append(sc)
+    return out
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0])); smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+class GpuArm:
+    def __init__(self, scenes, device):
+        import torch
+        import paper_1705_02408_gb300 as mp
+        self.mp, self.torch = mp, torch
+        self.scenes = scenes
+        self.device = device
+        self.cfg = scenes[0].cfg
+        # scene inputs resident in HBM
+        self.dev_inputs = [(torch.from_numpy(s.box_lo).to(device), torch.from_numpy(s.box_hi).to(device),
+                            torch.from_numpy(s.grid).to(device)) for s in scenes]
+        V = self.cfg.n + 2
+        self.ws = mp.Workspace(V * len(scenes), front_cap=64, max_plans=1 << 25)
+        self.ws1 = mp.Workspace(V, front_cap=64, max_plans=1 << 22)
+        self.queries = [mp.make_query(s.extra["beta"], scenegen.LAMBDA) for s in scenes]
+        self.mc = [(self.cfg.mc_rollouts, s.mc_seed, 0, s.delta_fx, s.sigma_fx, s.shift) for s in scenes]
+
+    def build(self, host=False):
+        """All roadmaps of the batch in one mpap_build_roadmaps call, rebuilt into
+        the handles of the previous step (no device allocation once sizes repeat)."""
+        mp = self.mp
+        specs = [mp.scene_spec(s, device_inputs=None if host else d) for s, d in zip(self.scenes, self.dev_inputs)]
+        self.rms = mp.build_roadmaps(specs, rms=getattr(self, "rms", None))
+        return self.rms
+
+    def step(self, host=False):
+        mp = self.mp
+        rms = self.build(host)
+        res = mp.search_batch(self.ws, rms, self.queries)
+        certs = mp.certify_batch(rms, [r.path for r in res], self.mc)
+        exps = sum(r.expansions for r in res)
+        self._last = (rms, res, certs)
+        return exps
+
+    def io_bytes(self):
+        h2d = sum(s.box_lo.nbytes + s.box_hi.nbytes + s.grid.nbytes + s.sigma_fx.nbytes + s.shift.nbytes
+                  for s in self.scenes)
+        rms, res, certs = self._last
+        h2d += sum(4 * len(r.path) for r in res)
+        d2h = sum(4 * len(r.path) + 8 * 4 for r in res) + 16 * len(certs)
+        return h2d, d2h
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    import paper_1705_02408_gb300 as mp
+    from paper_1705_02408_gb300 import build as mpbuild
+    mpbuild.build()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    scenes = scenes_for_rank(rank, args.queries)
+    if any(s.extra["beta"] is None for s in scenes):
+        raise SystemExit("missing beta for some scenes: run python -m oracle.calibrate --seeds N")
+    arm = GpuArm(scenes, device)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        arm.step()
+    # timed region: K steps, device events, profiler on, clocks sampled
+    mp.profile_reset()
+    mp.profile_enable(True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    launches0 = mp.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    exps = 0
+    for _ in range(args.steps):
+        exps += arm.step()
+    e1.record(stream)
+    barrier()
+    launches = mp.launch_count() - launches0
+    ck = clocks.stop()
+    mp.profile_enable(False)
+    kern = mp.profile_read()
+    ms_total = e0.elapsed_time(e1)
+    ms = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_total, float(exps)], device=device, dtype=torch.float64)
+        mx = t.clone(); torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        ms_total, exps = float(mx[0]), float(t[1])
+        ms = ms_total / args.steps
+    value = exps / (ms_total / 1e3)
+    rms, res, certs = arm._last
+    per_query = args.queries
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "queries_per_step": per_query * world,
+                      "queries_per_gpu": per_query, "l2": "inputs larger than L2 (~1.6 GB of roadmaps built per step)",
+                      "lambda": scenegen.LAMBDA, "beta": "60th percentile of straight-line heuristic",
+                      "parallelism": f"queries sharded over {world} GPU(s)"},
+           "ms_per_query": ms / per_query,
+           "gpu_launches": int(launches)}
+    # breakdown from the live kernel timers (timed region)
+    phase = {"build": ["k_sample_candidates", "k_take_samples", "k_set_endpoints", "k_mark_goal",
+                       "k_edges_count", "k_edges_fill", "k_indegree", "k_reverse_fill", "k_sort_rows",
+                       "k_exclusive_scan"],
+             "search": ["k_fill_qid", "k_init", "k_select", "k_prune", "k_end", "k_finalize"],
+             "certify": ["k_mc_checkpoints", "k_mc_rollouts"]}
+    out["kernel_ms_per_step"] = {k: round(v[1] / args.steps, 4) for k, v in sorted(kern.items())}
+    out["phase_kernel_ms_per_step"] = {p: round(sum(kern.get(k, (0, 0.0))[1] for k in ks) / args.steps, 4)
+                                       for p, ks in phase.items()}
+    out["expansions_per_step"] = exps / args.steps
+    out["solved"] = sum(1 for r in res if r.status == 0)
+    out["certified_failure_rate"] = sum(c["hits_any"] for c in certs) / max(1, sum(c["rollouts"] for c in certs))
+    out["roofline"] = roofline(kern, arm, res, args.steps)
+    if ck:
+        out["clocks"] = ck
+    if rank == 0 and not args.no_plain:
+        out["search_only"] = search_only(arm, stream)
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e(arm, args, stream)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scenes[:2])
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def roofline(kern, arm, res, steps):
+    """Roofline of the dominant kernel from the live CUDA-event timers."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    name, (launches, ms) = max(kern.items(), key=lambda kv: kv[1][1])
+    V = arm.cfg.n + 2
+    B = len(arm.scenes)
+    exps = sum(r.expansions for r in res)
+    plans = sum(r.plans for r in res)
+    if name in ("k_edges_count", "k_edges_fill"):
+        # ALU-bound: 39 binary32 operations decide Near for one ordered pair
+        # (see the design doc); FMA is disabled, one op per lane per clock.
+        ops_per_launch = 39.0 * V * V      # one launch covers all ordered pairs of one roadmap
+        achieved = ops_per_launch / (ms / launches / 1e3) / 1e12
+        sm_max = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * sm_max * 1e6 / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived)"}
+    # HBM-bound search kernels: algorithmic bytes per step
+    bytes_step = 16.0 * exps + 24.0 * plans
+    per_launch = bytes_step * steps / max(1, launches)
+    achieved = per_launch / (ms / launches / 1e3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
+
+
+def search_only(arm, stream):
+    """Batched (one call) versus plain (one call per query) search on the same
+    roadmaps; device time by CUDA events."""
+    import torch
+    mp = arm.mp
+    rms = arm.build()
+    torch.cuda.synchronize()
+    out = {}
+    for mode in ("batched", "plain"):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        exps = 0
+        e0.record(stream)
+        for _ in range(reps):
+            if mode == "batched":
+                res = mp.search_batch(arm.ws, rms, arm.queries)
+            else:
+                res = [mp.search(arm.ws1, rm, q.beta, lam=scenegen.LAMBDA) for rm, q in zip(rms, arm.queries)]
+            exps += sum(r.expansions for r in res)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[mode] = {"expansions_per_s": exps / reps / (ms / 1e3), "ms_per_query": ms / len(rms),
+                     "ms_per_batch": ms}
+    # search + certify per query (batched)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = mp.search_batch(arm.ws, rms, arm.queries)
+    mp.certify_batch(rms, [r.path for r in res], arm.mc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["batched"]["ms_per_query_with_certify"] = e0.elapsed_time(e1) / len(rms)
+    return out
+
+
+def e2e(arm, args, stream):
+    """Same step through the C ABI with host scene buffers (H2D/D2H inside)."""
+    import torch
+    for _ in range(1):
+        arm.step(host=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    exps = 0
+    k = max(1, min(args.steps, 3))
+    for _ in range(k):
+        exps += arm.step(host=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    h2d, d2h = arm.io_bytes()
+    return {"value": exps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "wall_value": exps / wall}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_query(sc):
+    import oracle
+    cfg = sc.cfg
+    rm = oracle.build_roadmap(sc)
+    beta = sc.extra.get("beta")
+    if beta is None:
+        beta = oracle.beta_percentile(rm)
+    res = oracle.explore(rm, beta, oracle.group_width(scenegen.LAMBDA, cfg.r))
+    if res.status == 0:
+        oracle.certify(rm, res.path, cfg.mc_rollouts, sc.mc_seed, 0, sc.delta_fx, sc.sigma_fx, sc.shift)
+    return res.expansions
+
+
+def cpu_baseline(scenes):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    exps = sum(oracle_query(s) for s in scenes)
+    dt = time.perf_counter() - t0
+    return {"value": exps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(scenes)} of the benchmark's 6D-16k queries (roadmap + search + 4096-rollout MC), "
+                      f"single thread, {dt:.1f} s", "ms_per_query": dt * 1e3 / len(scenes)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    scenes = scenes_for_rank(0, args.steps + args.warmup)
+    for s in scenes[:args.warmup]:
+        oracle_query(s)
+    t0 = time.perf_counter()
+    exps = sum(oracle_query(s) for s in scenes[args.warmup:])
+    dt = time.perf_counter() - t0
+    value = exps / dt
+    ms = dt * 1e3 / args.steps
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "queries_per_step": 1,
+                       "note": "CPU oracle, one query per step (bounded sample)"},
+            "ms_per_query": ms,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed 6D-16k queries, one per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_gpu(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -167,6 +167,15 @@ const char* mpap_last_error(void);
 int32_t mpap_build_roadmap(const mpap_scene* scene, const mpap_roadmap_params* params,
                            mpap_roadmap** out, void* stream);
 
+/* Builds n roadmaps in one pass (every kernel covers all of them; three host
+ * round trips in total).  For each i, rms[i] == NULL creates a new handle and a
+ * non-null rms[i] is rebuilt in place, reusing its device buffers when they are
+ * large enough (no allocation when sizes repeat).  Results are identical to n
+ * calls of mpap_build_roadmap.  On error, handles created by this call are freed
+ * and set to NULL; reused handles stay valid but hold an unspecified roadmap. */
+int32_t mpap_build_roadmaps(uint32_t n, const mpap_scene* scenes, const mpap_roadmap_params* params,
+                            mpap_roadmap** rms, void* stream);
+
 /* The same graph construction over caller-given node states x (host, float[6][V],
  * SoA: p0, p1, p2, v0, v1, v2).  Node 0 is x_init and node 1 x_goal. */
 int32_t mpap_build_roadmap_from_points(const mpap_scene* scene, uint32_t V, const float* x,
@@ -238,6 +247,21 @@ int32_t mpap_certify(mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,
 int32_t mpap_certify_batch(mpap_roadmap* const* rms, const uint32_t* const* paths,
                            const uint32_t* path_lens, const mpap_mc_params* mcs, uint32_t n,
                            mpap_cert* outs, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Launch accounting and kernel timing (tracing).  The paper reports per-phase
+ * computation times (Table 2); these entry points expose the same information
+ * per kernel.  mpap_launch_count() counts every kernel this library has launched
+ * since load or the last reset.  With mpap_profile_enable(1) every launch is
+ * bracketed by CUDA events on its stream; mpap_profile_read() waits for them and
+ * fills, for up to `cap` kernels, a 64-byte NUL-terminated name (names[64 i]),
+ * the launch count and the total device milliseconds, and sets *n to the number
+ * of distinct kernels (MPAP_ERR_INVALID_ARG if that exceeds cap).  Not for use
+ * while a stream is being captured into a CUDA graph. */
+int32_t mpap_profile_enable(int32_t on);
+int32_t mpap_profile_reset(void);
+uint64_t mpap_launch_count(void);
+int32_t mpap_profile_read(uint32_t cap, char* names, uint64_t* launches, double* total_ms, uint32_t* n);
 
 #ifdef __cplusplus
 }

@@ -27,11 +27,12 @@ MPAP_ERR_ITER_LIMIT, MPAP_ERR_CUDA, MPAP_ERR_SAMPLING = -4, -5, -6
 MPAP_MEM_HOST, MPAP_MEM_DEVICE = 0, 1
 MPAP_QUERY_NO_GOAL_STOP = 1
 
-EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap",
+EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_build_roadmaps",
            "mpap_build_roadmap_from_points", "mpap_roadmap_from_csr", "mpap_roadmap_info",
            "mpap_roadmap_export", "mpap_roadmap_free", "mpap_workspace_create",
            "mpap_workspace_free", "mpap_search", "mpap_search_batch", "mpap_search_fronts",
-           "mpap_certify", "mpap_certify_batch"]
+           "mpap_certify", "mpap_certify_batch", "mpap_profile_enable", "mpap_profile_reset",
+           "mpap_launch_count", "mpap_profile_read"]
 
 
 class mpap_scene(C.Structure):
@@ -88,6 +89,9 @@ def lib():
         L.mpap_build_roadmap.restype = i32
         L.mpap_build_roadmap.argtypes = [C.POINTER(mpap_scene), C.POINTER(mpap_roadmap_params),
                                          C.POINTER(P), P]
+        L.mpap_build_roadmaps.restype = i32
+        L.mpap_build_roadmaps.argtypes = [C.c_uint32, C.POINTER(mpap_scene), C.POINTER(mpap_roadmap_params),
+                                          C.POINTER(P), P]
         L.mpap_build_roadmap_from_points.restype = i32
         L.mpap_build_roadmap_from_points.argtypes = [C.POINTER(mpap_scene), C.c_uint32, P, C.c_float,
                                                      C.c_float, i32, C.c_float, C.POINTER(P), P]
@@ -115,8 +119,42 @@ def lib():
         L.mpap_certify_batch.restype = i32
         L.mpap_certify_batch.argtypes = [C.POINTER(P), C.POINTER(P), P, C.POINTER(mpap_mc_params),
                                          C.c_uint32, C.POINTER(mpap_cert), P]
+        L.mpap_profile_enable.restype = i32
+        L.mpap_profile_enable.argtypes = [i32]
+        L.mpap_profile_reset.restype = i32
+        L.mpap_launch_count.restype = C.c_uint64
+        L.mpap_profile_read.restype = i32
+        L.mpap_profile_read.argtypes = [C.c_uint32, P, P, P, C.POINTER(C.c_uint32)]
         _lib = L
     return _lib
+
+
+def profile_enable(on=True):
+    lib().mpap_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().mpap_profile_reset()
+
+
+def launch_count() -> int:
+    return int(lib().mpap_launch_count())
+
+
+def profile_read():
+    """{kernel name: (launches, total device ms)} since the last reset."""
+    cap = 64
+    names = C.create_string_buffer(64 * cap)
+    launches = np.zeros(cap, np.uint64); ms = np.zeros(cap, np.float64)
+    n = C.c_uint32()
+    _check(lib().mpap_profile_read(cap, names, launches.ctypes.data_as(C.c_void_p),
+                                   ms.ctypes.data_as(C.c_void_p), C.byref(n)), "mpap_profile_read")
+    out = {}
+    raw = names.raw
+    for i in range(min(n.value, cap)):
+        nm = raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]))
+    return out
 
 
 class MpapError(RuntimeError):
@@ -224,6 +262,55 @@ def build_roadmap(dim_kind, box_lo, box_hi, grid, grid_G, n, seed, r, x_init, x_
     _check(lib().mpap_build_roadmap(C.byref(sc), C.byref(p), C.byref(h), _stream(stream)),
            "mpap_build_roadmap")
     return Roadmap(h, M, K)
+
+
+def _params(n, seed, r, x_init, x_goal, goal_radius, T, M, query_id):
+    p = mpap_roadmap_params(n=n, query_id=query_id, seed=seed, r=r, T_edge=T, M=M, goal_radius=goal_radius)
+    for i in range(6):
+        p.x_init[i] = float(x_init[i]); p.x_goal[i] = float(x_goal[i])
+    return p
+
+
+def build_roadmaps(specs, rms=None, stream=None):
+    """mpap_build_roadmaps: build every roadmap of `specs` in one pass.
+
+    specs: list of dicts with the keyword arguments of build_roadmap.  rms: an
+    optional list of Roadmap handles (or None entries) rebuilt in place."""
+    n = len(specs)
+    scenes = (mpap_scene * n)()
+    params = (mpap_roadmap_params * n)()
+    keep = []
+    for i, sp in enumerate(specs):
+        sc, k = make_scene_struct(sp["dim_kind"], sp["box_lo"], sp["box_hi"], sp["grid"], sp["grid_G"],
+                                  sp.get("n_f", 12), sp.get("K", 24))
+        scenes[i] = sc
+        keep.append(k)
+        params[i] = _params(sp["n"], sp["seed"], sp["r"], sp["x_init"], sp["x_goal"], sp.get("goal_radius", 0.05),
+                            sp.get("T", 0.25), sp.get("M", 16), sp.get("query_id", 0))
+    rms = list(rms) if rms is not None else [None] * n
+    hs = (C.c_void_p * n)(*[rm.h.value if rm is not None and rm.h else None for rm in rms])
+    rc = lib().mpap_build_roadmaps(n, scenes, params, hs, _stream(stream))
+    out = []
+    for i in range(n):
+        if rms[i] is not None:
+            rms[i].h = C.c_void_p(hs[i]) if hs[i] else None
+            rms[i].M = specs[i].get("M", 16)
+            out.append(rms[i])
+        else:
+            out.append(Roadmap(C.c_void_p(hs[i]), specs[i].get("M", 16), specs[i].get("K", 24)) if hs[i] else None)
+    _check(rc, "mpap_build_roadmaps")
+    return out
+
+
+def scene_spec(scene, n=None, r=None, M=None, device_inputs=None):
+    """Keyword arguments of build_roadmap for a scenegen.Scene (device_inputs: a
+    (box_lo, box_hi, grid) triple of CUDA tensors to read in place)."""
+    cfg = scene.cfg
+    lo, hi, grid = (scene.box_lo, scene.box_hi, scene.grid) if device_inputs is None else device_inputs
+    return dict(dim_kind=cfg.dim_kind, box_lo=lo, box_hi=hi, grid=grid, grid_G=cfg.grid_G,
+                n=cfg.n if n is None else n, seed=scene.sample_seed, r=cfg.r if r is None else r,
+                x_init=scene.x_init, x_goal=scene.x_goal, T=cfg.T_edge, M=cfg.M if M is None else M,
+                query_id=scene.query_id)
 
 
 def build_roadmap_from_points(dim_kind, box_lo, box_hi, grid, grid_G, x, r, T=0.25, M=16,

@@ -1,6 +1,7 @@
 // C ABI of libmpap (declared in include/mpap.h): argument validation and
 // dispatch to the roadmap, search and certification implementations.
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -98,7 +99,29 @@ int32_t mpap_build_roadmap(const mpap_scene* scene, const mpap_roadmap_params* p
     return MPAP_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  return mpap::build_roadmap_impl(scene, p, nullptr, 0, p->r, p->T_edge, p->M, p->goal_radius, out, S(stream));
+  mpap::BuildSpec sp{scene, p, nullptr, 0, p->r, p->T_edge, p->goal_radius, p->M};
+  return mpap::build_roadmaps_impl(1, &sp, out, S(stream));
+}
+
+int32_t mpap_build_roadmaps(uint32_t n, const mpap_scene* scenes, const mpap_roadmap_params* params,
+                            mpap_roadmap** rms, void* stream) {
+  if (n && (!scenes || !params || !rms)) {
+    set_error("null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  std::vector<mpap::BuildSpec> specs(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    int32_t rc = check_scene(&scenes[i]);
+    if (!rc) rc = check_conn(params[i].r, params[i].T_edge, params[i].M, scenes[i].dim_kind);
+    if (!rc && (params[i].n == 0 || params[i].n > 0x0FFFFFFFu)) {
+      set_error("n must be in [1, 2^28)");
+      rc = MPAP_ERR_INVALID_ARG;
+    }
+    if (rc) return rc;
+    const mpap_roadmap_params& p = params[i];
+    specs[i] = mpap::BuildSpec{&scenes[i], &p, nullptr, 0, p.r, p.T_edge, p.goal_radius, p.M};
+  }
+  return mpap::build_roadmaps_impl(n, specs.data(), rms, S(stream));
 }
 
 int32_t mpap_build_roadmap_from_points(const mpap_scene* scene, uint32_t V, const float* x, float r, float T,
@@ -111,7 +134,8 @@ int32_t mpap_build_roadmap_from_points(const mpap_scene* scene, uint32_t V, cons
   }
   if ((rc = check_conn(r, T, M, scene->dim_kind))) return rc;
   *out = nullptr;
-  return mpap::build_roadmap_impl(scene, nullptr, x, V, r, T, M, goal_radius, out, S(stream));
+  mpap::BuildSpec sp{scene, nullptr, x, V, r, T, goal_radius, M};
+  return mpap::build_roadmaps_impl(1, &sp, out, S(stream));
 }
 
 int32_t mpap_roadmap_from_csr(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst, const int32_t* cost_q,

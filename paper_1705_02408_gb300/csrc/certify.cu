@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "profile.h"
 
 namespace mpap {
 
@@ -230,11 +231,17 @@ int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* path
   for (auto& J : jobs) max_steps = max_steps > J.steps ? max_steps : J.steps;
   if (max_steps) {
     dim3 gck((max_steps + 255) / 256, n);
-    k_mc_checkpoints<<<gck, 256, 0, st>>>(d_jobs);
+    {
+      ::mpap::LaunchScope ls_(st, "k_mc_checkpoints");
+      k_mc_checkpoints<<<gck, 256, 0, st>>>(d_jobs);
+    }
   }
   if (max_ro && max_steps) {
     dim3 gro((max_ro + 255) / 256, n);
-    k_mc_rollouts<<<gro, 256, 0, st>>>(d_jobs);
+    {
+      ::mpap::LaunchScope ls_(st, "k_mc_rollouts");
+      k_mc_rollouts<<<gro, 256, 0, st>>>(d_jobs);
+    }
   }
   MPAP_CK(cudaGetLastError());
   std::vector<uint32_t> hh(3 * n);

@@ -87,21 +87,23 @@ __device__ __forceinline__ bool in_box(const float* lo, const float* hi, int dp,
   return in;
 }
 
-__device__ __forceinline__ int level_at(const Geom& g, const float p[3]) {
+template <int DP>
+__device__ __forceinline__ int level_at_t(const Geom& g, const float p[3]) {
   int c[3] = {0, 0, 0};
   const float Gf = (float)g.G;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (i < g.dp) {
-      int ci = (int)floorf(__fmul_rn(p[i], Gf));
-      ci = ci < 0 ? 0 : ci;
-      ci = ci > g.G - 1 ? g.G - 1 : ci;
-      c[i] = ci;
-    }
+  for (int i = 0; i < DP; ++i) {
+    int ci = (int)floorf(__fmul_rn(p[i], Gf));
+    ci = ci < 0 ? 0 : ci;
+    ci = ci > g.G - 1 ? g.G - 1 : ci;
+    c[i] = ci;
   }
-  size_t idx = (g.dp == 2) ? ((size_t)c[1] * g.G + c[0])
-                           : (((size_t)c[2] * g.G + c[1]) * g.G + c[0]);
+  size_t idx = (DP == 2) ? ((size_t)c[1] * g.G + c[0]) : (((size_t)c[2] * g.G + c[1]) * g.G + c[0]);
   return (int)__ldg(g.grid + idx);
+}
+
+__device__ __forceinline__ int level_at(const Geom& g, const float p[3]) {
+  return g.dp == 2 ? level_at_t<2>(g, p) : level_at_t<3>(g, p);
 }
 
 // The optimal connection from state a to state b.
@@ -115,15 +117,45 @@ struct Conn {
   float cost;
 };
 
-__device__ __forceinline__ void conn_setup(const Geom& g, const float a[6], const float b[6], Conn& c) {
-  if (g.dim != 6) {
+// Cost only (the Near test), same operations and order as conn_setup.
+template <int DIM>
+__device__ __forceinline__ float conn_cost_t(const Geom& g, const float a[6], const float b[6]) {
+  if (DIM != 6) {
+    constexpr int DP = (DIM == 2) ? 2 : 3;
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+      const float d = __fsub_rn(b[i], a[i]);
+      const float sq = __fmul_rn(d, d);
+      s = (i == 0) ? sq : __fadd_rn(s, sq);
+    }
+    return __fsqrt_rn(s);
+  }
+  float jsum = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float dpos = __fsub_rn(__fsub_rn(b[i], a[i]), __fmul_rn(a[3 + i], g.T));
+    const float dvel = __fsub_rn(b[3 + i], a[3 + i]);
+    const float t1 = __fmul_rn(__fmul_rn(g.c1, dpos), dpos);
+    const float t2 = __fmul_rn(__fmul_rn(g.c2, dpos), dvel);
+    const float t3 = __fmul_rn(__fmul_rn(g.c3, dvel), dvel);
+    const float ji = __fadd_rn(__fsub_rn(t1, t2), t3);
+    jsum = (i == 0) ? ji : __fadd_rn(jsum, ji);
+  }
+  return __fadd_rn(g.T, jsum);
+}
+
+template <int DIM>
+__device__ __forceinline__ void conn_setup_t(const Geom& g, const float a[6], const float b[6], Conn& c) {
+  if (DIM != 6) {
+    constexpr int DP = (DIM == 2) ? 2 : 3;
     float s = 0.0f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      if (i < g.dp) {
+      if (i < DP) {
         c.p0[i] = a[i];
         c.d[i] = __fsub_rn(b[i], a[i]);
-        float sq = __fmul_rn(c.d[i], c.d[i]);
+        const float sq = __fmul_rn(c.d[i], c.d[i]);
         s = (i == 0) ? sq : __fadd_rn(s, sq);
       } else {
         c.p0[i] = 0.0f;
@@ -136,15 +168,15 @@ __device__ __forceinline__ void conn_setup(const Geom& g, const float a[6], cons
   float jsum = 0.0f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    float dpos = __fsub_rn(__fsub_rn(b[i], a[i]), __fmul_rn(a[3 + i], g.T));
-    float dvel = __fsub_rn(b[3 + i], a[3 + i]);
-    float t1 = __fmul_rn(__fmul_rn(g.c1, dpos), dpos);
-    float t2 = __fmul_rn(__fmul_rn(g.c2, dpos), dvel);
-    float t3 = __fmul_rn(__fmul_rn(g.c3, dvel), dvel);
-    float ji = __fadd_rn(__fsub_rn(t1, t2), t3);
+    const float dpos = __fsub_rn(__fsub_rn(b[i], a[i]), __fmul_rn(a[3 + i], g.T));
+    const float dvel = __fsub_rn(b[3 + i], a[3 + i]);
+    const float t1 = __fmul_rn(__fmul_rn(g.c1, dpos), dpos);
+    const float t2 = __fmul_rn(__fmul_rn(g.c2, dpos), dvel);
+    const float t3 = __fmul_rn(__fmul_rn(g.c3, dvel), dvel);
+    const float ji = __fadd_rn(__fsub_rn(t1, t2), t3);
     jsum = (i == 0) ? ji : __fadd_rn(jsum, ji);
-    float a0 = __fsub_rn(__fmul_rn(g.e1, dpos), __fmul_rn(g.e2, dvel));
-    float jk = __fsub_rn(__fmul_rn(g.e1, dvel), __fmul_rn(g.c1, dpos));
+    const float a0 = __fsub_rn(__fmul_rn(g.e1, dpos), __fmul_rn(g.e2, dvel));
+    const float jk = __fsub_rn(__fmul_rn(g.e1, dvel), __fmul_rn(g.c1, dpos));
     c.p0[i] = a[i];
     c.v0[i] = a[3 + i];
     c.q2[i] = __fmul_rn(a0, 0.5f);
@@ -153,39 +185,52 @@ __device__ __forceinline__ void conn_setup(const Geom& g, const float a[6], cons
   c.cost = __fadd_rn(g.T, jsum);
 }
 
+__device__ __forceinline__ void conn_setup(const Geom& g, const float a[6], const float b[6], Conn& c) {
+  if (g.dim == 6) conn_setup_t<6>(g, a, b, c);
+  else if (g.dim == 3) conn_setup_t<3>(g, a, b, c);
+  else conn_setup_t<2>(g, a, b, c);
+}
+
 // Position at the end of sub-interval m (m = 1..M).
-__device__ __forceinline__ void conn_point(const Geom& g, const Conn& c, int m, float p[3]) {
-  if (g.dim != 6) {
-    float t = __fmul_rn((float)m, g.invM);
+template <int DIM>
+__device__ __forceinline__ void conn_point_t(const Geom& g, const Conn& c, int m, float p[3]) {
+  if (DIM != 6) {
+    constexpr int DP = (DIM == 2) ? 2 : 3;
+    const float t = __fmul_rn((float)m, g.invM);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) p[i] = (i < g.dp) ? __fadd_rn(c.p0[i], __fmul_rn(t, c.d[i])) : 0.0f;
+    for (int i = 0; i < 3; ++i) p[i] = (i < DP) ? __fadd_rn(c.p0[i], __fmul_rn(t, c.d[i])) : 0.0f;
     return;
   }
-  float t = __fmul_rn((float)m, g.dtm);
+  const float t = __fmul_rn((float)m, g.dtm);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    float in = __fadd_rn(c.q2[i], __fmul_rn(t, c.q3[i]));
-    float mid = __fadd_rn(c.v0[i], __fmul_rn(t, in));
+    const float in = __fadd_rn(c.q2[i], __fmul_rn(t, c.q3[i]));
+    const float mid = __fadd_rn(c.v0[i], __fmul_rn(t, in));
     p[i] = __fadd_rn(c.p0[i], __fmul_rn(t, mid));
   }
 }
 
+__device__ __forceinline__ void conn_point(const Geom& g, const Conn& c, int m, float p[3]) {
+  if (g.dim == 6) conn_point_t<6>(g, c, m, p);
+  else if (g.dim == 3) conn_point_t<3>(g, c, m, p);
+  else conn_point_t<2>(g, c, m, p);
+}
+
 // Closed segment (2D/3D) against one closed box: slab clipping with IEEE division.
-__device__ __forceinline__ bool seg_hits_box(int dp, const float a[3], const float d[3],
-                                             const float* lo, const float* hi) {
+template <int DP>
+__device__ __forceinline__ bool seg_hits_box(const float a[3], const float d[3], const float* lo,
+                                             const float* hi) {
   float t0 = -INFINITY, t1 = INFINITY;
   bool miss = false;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (i < dp) {
-      if (d[i] == 0.0f) {
-        miss = miss || (a[i] < lo[i]) || (a[i] > hi[i]);
-      } else {
-        float ta = __fdiv_rn(__fsub_rn(lo[i], a[i]), d[i]);
-        float tb = __fdiv_rn(__fsub_rn(hi[i], a[i]), d[i]);
-        t0 = fmaxf(t0, fminf(ta, tb));
-        t1 = fminf(t1, fmaxf(ta, tb));
-      }
+  for (int i = 0; i < DP; ++i) {
+    if (d[i] == 0.0f) {
+      miss = miss || (a[i] < lo[i]) || (a[i] > hi[i]);
+    } else {
+      const float ta = __fdiv_rn(__fsub_rn(lo[i], a[i]), d[i]);
+      const float tb = __fdiv_rn(__fsub_rn(hi[i], a[i]), d[i]);
+      t0 = fmaxf(t0, fminf(ta, tb));
+      t1 = fminf(t1, fmaxf(ta, tb));
     }
   }
   return !miss && (t0 <= t1) && (t1 >= 0.0f) && (t0 <= 1.0f);
@@ -194,20 +239,66 @@ __device__ __forceinline__ bool seg_hits_box(int dp, const float a[3], const flo
 // Collision of a connection against the boxes (box data in shared memory):
 // 2D/3D exact slab test; 6D point tests at the M-1 interior checkpoints, where
 // leaving the unit workspace also counts.
-__device__ __forceinline__ bool conn_collides(const Geom& g, const Conn& c, const float* s_lo,
-                                              const float* s_hi) {
-  if (g.dim != 6) {
-    for (int b = 0; b < g.nb; ++b)
-      if (seg_hits_box(g.dp, c.p0, c.d, s_lo + 3 * b, s_hi + 3 * b)) return true;
+//
+// Both forms first intersect the boxes with a bounding box of the connection and
+// run the exact test only against boxes that overlap it.  6D: the bounding box of
+// the checkpoints themselves (a closed box holds a checkpoint only if it overlaps
+// their bounding box).  2D/3D: the segment's bounding box grown by 1e-5, which
+// exceeds the rounding of the slab arithmetic by orders of magnitude, so a box
+// outside it is also reported clear by the floating-point slab test.
+template <int DIM>
+__device__ __forceinline__ bool conn_collides_t(const Geom& g, const Conn& c, const float* s_lo,
+                                                const float* s_hi) {
+  if (DIM != 6) {
+    constexpr int DP = (DIM == 2) ? 2 : 3;
+    float lo[3], hi[3];
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+      const float e = __fadd_rn(c.p0[i], c.d[i]);
+      lo[i] = fminf(c.p0[i], e) - 1e-5f;
+      hi[i] = fmaxf(c.p0[i], e) + 1e-5f;
+    }
+    for (int b = 0; b < g.nb; ++b) {
+      const float* bl = s_lo + 3 * b;
+      const float* bh = s_hi + 3 * b;
+      bool overlap = true;
+#pragma unroll
+      for (int i = 0; i < DP; ++i) overlap = overlap && bl[i] <= hi[i] && bh[i] >= lo[i];
+      if (overlap && seg_hits_box<DP>(c.p0, c.d, bl, bh)) return true;
+    }
     return false;
   }
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int m = 1; m < g.M; ++m) {
     float p[3];
-    conn_point(g, c, m, p);
-    if (p[0] < 0.0f || p[0] > 1.0f || p[1] < 0.0f || p[1] > 1.0f || p[2] < 0.0f || p[2] > 1.0f)
-      return true;
-    for (int b = 0; b < g.nb; ++b)
-      if (in_box(s_lo + 3 * b, s_hi + 3 * b, 3, p)) return true;
+    conn_point_t<6>(g, c, m, p);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      lo[i] = fminf(lo[i], p[i]);
+      hi[i] = fmaxf(hi[i], p[i]);
+    }
+  }
+  if (g.M > 1 && (lo[0] < 0.0f || hi[0] > 1.0f || lo[1] < 0.0f || hi[1] > 1.0f || lo[2] < 0.0f || hi[2] > 1.0f))
+    return true;
+  for (int b0 = 0; b0 < g.nb; b0 += 32) {
+    uint32_t mask = 0;
+    const int nbb = (g.nb - b0) < 32 ? (g.nb - b0) : 32;
+    for (int j = 0; j < nbb; ++j) {
+      const float* bl = s_lo + 3 * (b0 + j);
+      const float* bh = s_hi + 3 * (b0 + j);
+      const bool overlap = bl[0] <= hi[0] && bh[0] >= lo[0] && bl[1] <= hi[1] && bh[1] >= lo[1] &&
+                           bl[2] <= hi[2] && bh[2] >= lo[2];
+      mask |= overlap ? (1u << j) : 0u;
+    }
+    if (!mask) continue;
+    for (int m = 1; m < g.M; ++m) {
+      float p[3];
+      conn_point_t<6>(g, c, m, p);
+      for (uint32_t mm = mask; mm; mm &= mm - 1) {
+        const int b = b0 + __ffs(mm) - 1;
+        if (in_box(s_lo + 3 * b, s_hi + 3 * b, 3, p)) return true;
+      }
+    }
   }
   return false;
 }
@@ -219,14 +310,16 @@ __device__ __forceinline__ int64_t quantise_cost(float cost) {
 
 // Per-edge perception transfer F_e(h) = max(C, h + S) from the M sub-steps
 // (Sec. 4.1 heuristic on the quality grid): step m adds inc (n_f - k_m).
-__device__ __forceinline__ void conn_transfer(const Geom& g, const Conn& c, int64_t cost_q,
-                                              int64_t& S, int64_t& C) {
-  const int64_t inc = (g.dim == 6) ? g.Tq : cost_q;
+template <int DIM>
+__device__ __forceinline__ void conn_transfer_t(const Geom& g, const Conn& c, int64_t cost_q, int64_t& S,
+                                                int64_t& C) {
+  constexpr int DP = (DIM == 2) ? 2 : 3;
+  const int64_t inc = (DIM == 6) ? g.Tq : cost_q;
   int64_t s = 0, h = 0;
   for (int m = 1; m <= g.M; ++m) {
     float p[3];
-    conn_point(g, c, m, p);
-    int64_t dm = inc * (int64_t)(g.n_f - level_at(g, p));
+    conn_point_t<DIM>(g, c, m, p);
+    const int64_t dm = inc * (int64_t)(g.n_f - level_at_t<DP>(g, p));
     s += dm;
     h += dm;
     h = h < 0 ? 0 : h;

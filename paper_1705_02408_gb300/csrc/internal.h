@@ -19,7 +19,7 @@ struct mpap_roadmap {
   float r = 0.0f, T = 0.25f, goal_radius = 0.0f;
   bool has_geometry = false;
   mpap::Geom geom{};           // device pointers below, constants filled
-  // device arrays (owned)
+  // device arrays (owned; capacities in elements, reused by rebuilds)
   float* x = nullptr;          // [6][V]
   uint8_t* is_goal = nullptr;  // [V]
   uint32_t* goal_list = nullptr;
@@ -31,6 +31,7 @@ struct mpap_roadmap {
   float* box_lo = nullptr;     // [nb][3]
   float* box_hi = nullptr;
   uint8_t* grid = nullptr;
+  size_t cap_V = 0, cap_E = 0, cap_nb = 0, cap_cells = 0;
 };
 
 namespace mpap {
@@ -46,18 +47,23 @@ bool cuda_ok(cudaError_t e, const char* what);
 // Fill the double-integrator constants and scalars of g from (T, M, ...).
 void fill_geom_constants(Geom& g, int dim, int nb, int G, int n_f, int M, float r, float T);
 
-// Roadmap construction (roadmap.cu).
-int32_t build_roadmap_impl(const mpap_scene* scene, const mpap_roadmap_params* prm,
-                           const float* host_x, uint32_t V_given, float r, float T, int M,
-                           float goal_radius, mpap_roadmap** out, cudaStream_t st);
+// One roadmap to (re)build.  Exactly one of `params` (SampleFree) or `points`
+// (caller-given node states, host, [6][V]) is set.
+struct BuildSpec {
+  const mpap_scene* scene;
+  const mpap_roadmap_params* params;
+  const float* points;
+  uint32_t V_points;
+  float r, T, goal_radius;
+  int M;
+};
+
+// Builds every spec into rms[i] (a null rms[i] gets a new handle; an existing
+// one is rebuilt in place, reusing its device buffers when large enough).
+int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** rms, cudaStream_t st);
 int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst,
                               const int32_t* cost_q, const int32_t* S, const int32_t* C,
                               const uint8_t* is_goal, mpap_roadmap** out, cudaStream_t st);
 void roadmap_free_impl(mpap_roadmap* rm);
-
-// Single-block exclusive scan of n uint32 values into out[0..n] (out[n] = total,
-// saturating at 0xFFFFFFFF with *overflow set).
-void launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* overflow,
-                           cudaStream_t st);
 
 }  // namespace mpap

@@ -2,6 +2,10 @@
 // Ichter et al., "Perception-Aware Motion Planning via Multiobjective Search on
 // GPUs" -- SampleFree, Near, Collision and the per-edge perception transfer.
 //
+// Every kernel covers all roadmaps of one call (blockIdx.y = roadmap), so a
+// batch of B roadmaps costs the same number of launches and host round trips
+// (three) as a single one.
+//
 // Layout in HBM (one roadmap):
 //   x        float [6][V]      node states, SoA (p0 p1 p2 v0 v1 v2)
 //   fwd_ptr  u32   [V+1]       out-edge CSR, neighbours ascending
@@ -9,11 +13,23 @@
 //   rev_ptr  u32   [V+1]       in-edge CSR, sources ascending
 //   rev_edge int4  [E]         {src, cost_q, S, C}
 //   is_goal  u8    [V], goal_list u32 [n_goal]
+//
+// Near (Cost < r) is evaluated only for pairs whose target lies in grid cells
+// that meet a ball known to contain every neighbour: radius r around the source
+// in 2D/3D; in 6D radius sqrt((r - T) T^3 / 3) around p0 + v0 T, because the
+// control energy satisfies J >= 3 |p1 - p0 - v0 T|^2 / T^3 (its minimum over the
+// velocity difference).  Both radii carry a generous margin over the binary32
+// rounding of the cost, so the edge set is exactly that of the all-pairs test;
+// rows are sorted by neighbour afterwards.
+#include <algorithm>
+#include <climits>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 
 #include "internal.h"
+#include "profile.h"
 
 namespace mpap {
 
@@ -57,33 +73,72 @@ void fill_geom_constants(Geom& g, int dim, int nb, int G, int n_f, int M, float 
   g.Tq = (int64_t)llrintf(T * 16777216.0f);
 }
 
+// Per-roadmap descriptor read by every build kernel.
+struct BuildJob {
+  Geom g;
+  float* x;                // [6][V]
+  uint32_t V;
+  uint32_t n;              // samples to draw (0: node states given)
+  uint32_t key0, key1, qid;
+  uint32_t a0;             // first attempt of the current sampling round
+  uint32_t cand_count;     // candidates in the current round (0: nothing to do)
+  uint32_t kept;           // samples kept before the current round
+  float xi[6], xg[6];      // x_init, x_goal
+  float* cand;             // [6][C]
+  uint32_t* ok;            // [C]
+  uint32_t* rank;          // [C+1]
+  float goal_r2;
+  uint8_t* is_goal;
+  uint32_t* goal_list;
+  int GC;                  // grid cells per axis for the Near scan
+  float R;                 // conservative neighbour radius
+  uint32_t* cell_cnt;      // [NC+1]
+  uint32_t* cell_start;    // [NC+1]
+  uint32_t* cell_of;       // [V]
+  uint32_t* sorted;        // [V] node ids in cell order
+  float* sx;               // [6][V] states in cell order
+  uint32_t* counts;        // [V+1]
+  uint32_t* fill;          // [V+1]
+  uint32_t* fwd_ptr;
+  int4* fwd_edge;
+  uint32_t* rev_ptr;
+  int4* rev_edge;
+  uint32_t* status;        // [4]: error bits, n_goal, scan overflow, spare
+};
+
+struct ScanSeg {
+  const uint32_t* in;
+  uint32_t* out;
+  uint32_t n;
+  uint32_t* overflow;
+};
+
 // ---------------------------------------------------------------------------
-// Single-block exclusive scan (used for CSR row pointers and sample compaction).
+// Exclusive scans, one block per segment: out[0..n] with out[n] = total
+// (saturating at 0xFFFFFFFF and flagging *overflow).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_exclusive_scan(const uint32_t* __restrict__ in,
-                                                         uint32_t* __restrict__ out, uint32_t n,
-                                                         uint32_t* overflow) {
+__global__ void __launch_bounds__(1024) k_scan_segments(const ScanSeg* __restrict__ segs) {
+  const ScanSeg sg = segs[blockIdx.x];
   __shared__ uint32_t warp_sums[32];
   __shared__ unsigned long long carry;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry = 0ull;
   __syncthreads();
-  for (uint32_t base = 0; base < n; base += 1024u) {
+  for (uint32_t base = 0; base < sg.n; base += 1024u) {
     const uint32_t i = base + threadIdx.x;
-    const uint32_t v = (i < n) ? in[i] : 0u;
+    const uint32_t v = (i < sg.n) ? sg.in[i] : 0u;
     const uint32_t incl = warp_incl_scan(v);
     if (lane == 31) warp_sums[warp] = incl;
     __syncthreads();
     if (warp == 0) warp_sums[lane] = warp_incl_scan(warp_sums[lane]);
     __syncthreads();
-    const unsigned long long excl =
-        carry + (warp ? warp_sums[warp - 1] : 0u) + (unsigned long long)(incl - v);
-    if (i < n) {
+    const unsigned long long excl = carry + (warp ? warp_sums[warp - 1] : 0u) + (unsigned long long)(incl - v);
+    if (i < sg.n) {
       if (excl > 0xFFFFFFFFull) {
-        out[i] = 0xFFFFFFFFu;
-        if (overflow) *overflow = 1u;
+        sg.out[i] = 0xFFFFFFFFu;
+        if (sg.overflow) *sg.overflow = 1u;
       } else {
-        out[i] = (uint32_t)excl;
+        sg.out[i] = (uint32_t)excl;
       }
     }
     __syncthreads();
@@ -92,17 +147,12 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(const uint32_t* __restr
   }
   if (threadIdx.x == 0) {
     if (carry > 0xFFFFFFFFull) {
-      out[n] = 0xFFFFFFFFu;
-      if (overflow) *overflow = 1u;
+      sg.out[sg.n] = 0xFFFFFFFFu;
+      if (sg.overflow) *sg.overflow = 1u;
     } else {
-      out[n] = (uint32_t)carry;
+      sg.out[sg.n] = (uint32_t)carry;
     }
   }
-}
-
-void launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* overflow,
-                           cudaStream_t st) {
-  k_exclusive_scan<<<1, 1024, 0, st>>>(in, out, n, overflow);
 }
 
 // ---------------------------------------------------------------------------
@@ -110,9 +160,10 @@ void launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32
 // (att, 0, query_id, 0) (position) and (att, 1, query_id, 0) (velocity, 6D),
 // key = seed; it is free iff outside every closed box (and |v| <= 1 in 6D).
 // ---------------------------------------------------------------------------
-__global__ void k_sample_candidates(Geom g, uint32_t key0, uint32_t key1, uint32_t qid,
-                                    uint32_t a0, uint32_t count, float* __restrict__ cand,
-                                    uint32_t* __restrict__ ok) {
+__global__ void k_sample_candidates(const BuildJob* __restrict__ jobs) {
+  const BuildJob& J = jobs[blockIdx.y];
+  if (J.cand_count == 0) return;
+  const Geom& g = J.g;
   extern __shared__ float s_box[];
   float* s_lo = s_box;
   float* s_hi = s_box + 3 * g.nb;
@@ -121,17 +172,18 @@ __global__ void k_sample_candidates(Geom g, uint32_t key0, uint32_t key1, uint32
     s_hi[i] = g.box_hi[i];
   }
   __syncthreads();
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
-    const uint32_t att = a0 + t;
-    uint32_t w0 = att, w1 = 0u, w2 = qid, w3 = 0u;
-    philox4x32_10(w0, w1, w2, w3, key0, key1);
+  const uint32_t C = J.cand_count;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < C; t += gridDim.x * blockDim.x) {
+    const uint32_t att = J.a0 + t;
+    uint32_t w0 = att, w1 = 0u, w2 = J.qid, w3 = 0u;
+    philox4x32_10(w0, w1, w2, w3, J.key0, J.key1);
     float p[3] = {unit24(w0), unit24(w1), g.dp == 3 ? unit24(w2) : 0.0f};
     bool free = true;
     for (int b = 0; b < g.nb && free; ++b) free = !in_box(s_lo + 3 * b, s_hi + 3 * b, g.dp, p);
     float v[3] = {0.0f, 0.0f, 0.0f};
     if (free && g.dim == 6) {
-      uint32_t u0 = att, u1 = 1u, u2 = qid, u3 = 0u;
-      philox4x32_10(u0, u1, u2, u3, key0, key1);
+      uint32_t u0 = att, u1 = 1u, u2 = J.qid, u3 = 0u;
+      philox4x32_10(u0, u1, u2, u3, J.key0, J.key1);
       v[0] = __fsub_rn(__fmul_rn(2.0f, unit24(u0)), 1.0f);
       v[1] = __fsub_rn(__fmul_rn(2.0f, unit24(u1)), 1.0f);
       v[2] = __fsub_rn(__fmul_rn(2.0f, unit24(u2)), 1.0f);
@@ -140,172 +192,353 @@ __global__ void k_sample_candidates(Geom g, uint32_t key0, uint32_t key1, uint32
       vv = __fadd_rn(vv, __fmul_rn(v[2], v[2]));
       free = (vv <= 1.0f);
     }
-    cand[0 * count + t] = p[0];
-    cand[1 * count + t] = p[1];
-    cand[2 * count + t] = p[2];
-    cand[3 * count + t] = v[0];
-    cand[4 * count + t] = v[1];
-    cand[5 * count + t] = v[2];
-    ok[t] = free ? 1u : 0u;
+    J.cand[0 * (size_t)C + t] = p[0];
+    J.cand[1 * (size_t)C + t] = p[1];
+    J.cand[2 * (size_t)C + t] = p[2];
+    J.cand[3 * (size_t)C + t] = v[0];
+    J.cand[4 * (size_t)C + t] = v[1];
+    J.cand[5 * (size_t)C + t] = v[2];
+    J.ok[t] = free ? 1u : 0u;
   }
 }
 
-// Keeps the first `need` free candidates (in attempt order) as nodes 2+kept+...
-__global__ void k_take_samples(const float* __restrict__ cand, const uint32_t* __restrict__ ok,
-                               const uint32_t* __restrict__ rank, uint32_t count, uint32_t need,
-                               uint32_t first, float* __restrict__ x, uint32_t V) {
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
-    if (!ok[t] || rank[t] >= need) continue;
-    const uint32_t id = first + rank[t];
+// Keeps the first n - kept free candidates of this round, in attempt order, as
+// nodes 2 + kept + rank.
+__global__ void k_take_samples(const BuildJob* __restrict__ jobs) {
+  const BuildJob& J = jobs[blockIdx.y];
+  const uint32_t C = J.cand_count;
+  if (C == 0) return;
+  const uint32_t need = J.n - J.kept;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < C; t += gridDim.x * blockDim.x) {
+    if (!J.ok[t] || J.rank[t] >= need) continue;
+    const uint32_t id = 2u + J.kept + J.rank[t];
 #pragma unroll
-    for (int a = 0; a < 6; ++a) x[(size_t)a * V + id] = cand[(size_t)a * count + t];
+    for (int a = 0; a < 6; ++a) J.x[(size_t)a * J.V + id] = J.cand[(size_t)a * C + t];
   }
 }
 
-__global__ void k_set_endpoints(float* x, uint32_t V, float i0, float i1, float i2, float i3,
-                                float i4, float i5, float g0, float g1, float g2, float g3,
-                                float g4, float g5) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    const float xi[6] = {i0, i1, i2, i3, i4, i5};
-    const float xg[6] = {g0, g1, g2, g3, g4, g5};
-    for (int a = 0; a < 6; ++a) {
-      x[(size_t)a * V + 0] = xi[a];
-      x[(size_t)a * V + 1] = xg[a];
-    }
+__global__ void k_set_endpoints(const BuildJob* __restrict__ jobs, uint32_t njobs) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= njobs || jobs[j].n == 0) return;
+  const BuildJob& J = jobs[j];
+  for (int a = 0; a < 6; ++a) {
+    J.x[(size_t)a * J.V + 0] = J.xi[a];
+    J.x[(size_t)a * J.V + 1] = J.xg[a];
   }
+}
+
+// Per-job counters for the host: accepted candidates of the round, edge count,
+// error bits, goal count, scan overflow.
+__global__ void k_gather_status(const BuildJob* __restrict__ jobs, uint32_t njobs, uint32_t* out) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= njobs) return;
+  const BuildJob& J = jobs[j];
+  out[5 * j + 0] = J.cand_count ? J.rank[J.cand_count] : 0u;
+  out[5 * j + 1] = J.fwd_ptr[J.V];
+  out[5 * j + 2] = J.status[0];
+  out[5 * j + 3] = J.status[1];
+  out[5 * j + 4] = J.status[2];
 }
 
 // X_goal: nodes within goal_radius (position) of node 1.
-__global__ void k_mark_goal(const float* __restrict__ x, uint32_t V, int dp, float r2,
-                            uint8_t* __restrict__ is_goal, uint32_t* goal_list, uint32_t* n_goal) {
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+__global__ void k_mark_goal(const BuildJob* __restrict__ jobs) {
+  const BuildJob& J = jobs[blockIdx.y];
+  const int dp = J.g.dp;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < J.V; v += gridDim.x * blockDim.x) {
     float s = 0.0f;
     for (int i = 0; i < dp; ++i) {
-      float d = __fsub_rn(x[(size_t)i * V + v], x[(size_t)i * V + 1]);
+      const float d = __fsub_rn(J.x[(size_t)i * J.V + v], J.x[(size_t)i * J.V + 1]);
       s = __fadd_rn(s, __fmul_rn(d, d));
     }
-    const bool goal = (s <= r2);
-    is_goal[v] = goal ? 1 : 0;
-    if (goal) goal_list[atomicAdd(n_goal, 1u)] = v;
+    const bool goal = (s <= J.goal_r2);
+    J.is_goal[v] = goal ? 1 : 0;
+    if (goal) J.goal_list[atomicAdd(&J.status[1], 1u)] = v;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Near + Collision + transfer.  One warp per source node v; the CTA stages
-// tiles of candidate neighbours u in shared memory and every lane tests one u
-// per round.  The connections that pass (Cost < r, no collision) are counted
-// (FILL = false) or written in ascending u order via ballot ranks (FILL = true),
-// together with their quantised cost and the max-plus transfer (S, C).
+// Spatial binning of node positions for the Near scan.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_coord(float p, int GC) {
+  int c = (int)floorf(p * (float)GC);
+  return c < 0 ? 0 : (c > GC - 1 ? GC - 1 : c);
+}
+
+__global__ void k_bin_count(const BuildJob* __restrict__ jobs) {
+  const BuildJob& J = jobs[blockIdx.y];
+  const int GC = J.GC;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < J.V; v += gridDim.x * blockDim.x) {
+    uint32_t cell = 0;
+    for (int i = J.g.dp - 1; i >= 0; --i) cell = cell * GC + cell_coord(J.x[(size_t)i * J.V + v], GC);
+    J.cell_of[v] = cell;
+    atomicAdd(&J.cell_cnt[cell], 1u);
+  }
+}
+
+__global__ void k_bin_scatter(const BuildJob* __restrict__ jobs) {
+  const BuildJob& J = jobs[blockIdx.y];
+  const int nc = (J.g.dim == 6) ? 6 : J.g.dp;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < J.V; v += gridDim.x * blockDim.x) {
+    const uint32_t cell = J.cell_of[v];
+    const uint32_t pos = J.cell_start[cell] + atomicAdd(&J.cell_cnt[cell], 1u);
+    J.sorted[pos] = v;
+    for (int c = 0; c < nc; ++c) J.sx[(size_t)c * J.V + pos] = J.x[(size_t)c * J.V + v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Near + Collision + transfer.  One warp per source node v.  The warp walks the
+// runs of grid cells (contiguous x-ranges) that meet the source's neighbour ball,
+// flattened across up to 32 runs at a time, one candidate per lane, and
+// evaluates Cost(v, u) exactly.  Pairs with Cost < r are queued in shared memory;
+// every 32 queued pairs are checked for collision (and, in the fill pass, given
+// their quantised cost and max-plus transfer (S, C)) one per lane, so the
+// expensive tests run 32-wide.  The connections that pass are counted
+// (FILL = false) or written (FILL = true) in scan order; rows are sorted later.
 // ---------------------------------------------------------------------------
 constexpr int kEdgeWarps = 8;
-constexpr int kEdgeTile = 256;
+constexpr int kQueue = 64;
 
-template <bool FILL>
-__global__ void __launch_bounds__(kEdgeWarps * 32) k_edges(Geom g, const float* __restrict__ x,
-                                                           uint32_t V, uint32_t* counts,
-                                                           const uint32_t* __restrict__ row_ptr,
-                                                           int4* __restrict__ edges, uint32_t* err) {
+template <int DIM, bool FILL>
+__device__ __forceinline__ void edge_flush(const BuildJob& J, const float a[6], const uint32_t* q, int k,
+                                           const float* s_lo, const float* s_hi, uint32_t out_base,
+                                           uint32_t& running) {
+  const Geom& g = J.g;
+  const unsigned lane = lane_id();
+  constexpr int nc = (DIM == 6) ? 6 : DIM;
+  bool ok = false;
+  Conn cn;
+  uint32_t u = 0;
+  if ((int)lane < k) {
+    u = q[lane];
+    float b[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < nc; ++c) b[c] = J.x[(size_t)c * J.V + u];
+    conn_setup_t<DIM>(g, a, b, cn);
+    ok = !conn_collides_t<DIM>(g, cn, s_lo, s_hi);
+  }
+  const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
+  if (FILL && ok) {
+    const int64_t cq = quantise_cost(cn.cost);
+    int64_t S, C;
+    conn_transfer_t<DIM>(g, cn, cq, S, C);
+    if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX) atomicOr(&J.status[0], kErrEdge);
+    const uint32_t pos = out_base + running + __popc(bal & ((1u << lane) - 1u));
+    J.fwd_edge[pos] = make_int4((int)u, (int)cq, (int)S, (int)C);
+  }
+  running += __popc(bal);
+}
+
+template <int DIM, bool FILL>
+__global__ void __launch_bounds__(kEdgeWarps * 32) k_edges(const BuildJob* __restrict__ jobs,
+                                                           const uint32_t* __restrict__ job_ids) {
+  const BuildJob& J = jobs[job_ids[blockIdx.y]];
+  const Geom& g = J.g;
   extern __shared__ float smem[];
   float* s_lo = smem;
   float* s_hi = smem + 3 * g.nb;
-  float* s_tile = smem + 6 * g.nb;   // [6][kEdgeTile]
-  const int nc = (g.dim == 6) ? 6 : g.dp;
+  uint32_t* s_queue = reinterpret_cast<uint32_t*>(smem + 6 * g.nb);   // [warps][kQueue]
+  constexpr int DP = (DIM == 2) ? 2 : 3;
+  constexpr int nc = (DIM == 6) ? 6 : DIM;
   const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
   const uint32_t warp = threadIdx.x >> 5;
+  uint32_t* q = s_queue + warp * kQueue;
   for (int i = threadIdx.x; i < 3 * g.nb; i += blockDim.x) {
     s_lo[i] = g.box_lo[i];
     s_hi[i] = g.box_hi[i];
   }
+  __syncthreads();
   const uint32_t v = blockIdx.x * kEdgeWarps + warp;
-  const bool have_v = v < V;
+  if (v >= J.V) return;
+  const uint32_t V = J.V;
   float a[6] = {0, 0, 0, 0, 0, 0};
-  if (have_v)
-    for (int c = 0; c < nc; ++c) a[c] = x[(size_t)c * V + v];
+#pragma unroll
+  for (int c = 0; c < nc; ++c) a[c] = J.x[(size_t)c * V + v];
+  // cell range of the neighbour ball
+  const int GC = J.GC;
+  int clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < DP; ++i) {
+    const float c = (DIM == 6) ? __fadd_rn(a[i], __fmul_rn(a[3 + i], g.T)) : a[i];
+    clo[i] = cell_coord(c - J.R, GC);
+    chi[i] = cell_coord(c + J.R, GC);
+  }
+  const uint32_t ny = (uint32_t)(chi[1] - clo[1] + 1);
+  const uint32_t nruns = ny * (DP == 3 ? (uint32_t)(chi[2] - clo[2] + 1) : 1u);
   uint32_t running = 0;
-  const uint32_t out_base = (FILL && have_v) ? row_ptr[v] : 0u;
-  for (uint32_t tb = 0; tb < V; tb += kEdgeTile) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < kEdgeTile * nc; i += blockDim.x) {
-      const int c = i / kEdgeTile, k = i % kEdgeTile;
-      const uint32_t u = tb + k;
-      s_tile[c * kEdgeTile + k] = (u < V) ? x[(size_t)c * V + u] : 0.0f;
+  int qn = 0;
+  const uint32_t out_base = FILL ? J.fwd_ptr[v] : 0u;
+  for (uint32_t r0 = 0; r0 < nruns; r0 += 32) {
+    // lane j describes run r0 + j: the cells [clo_x, chi_x] of one (y, z) row
+    uint32_t rs = 0, rl = 0;
+    const uint32_t rr = r0 + lane;
+    if (rr < nruns) {
+      const uint32_t yy = (uint32_t)clo[1] + rr % ny;
+      const uint32_t zz = (DP == 3) ? (uint32_t)clo[2] + rr / ny : 0u;
+      const uint32_t row = (zz * (uint32_t)GC + yy) * (uint32_t)GC;
+      rs = J.cell_start[row + (uint32_t)clo[0]];
+      rl = J.cell_start[row + (uint32_t)chi[0] + 1u] - rs;
     }
-    __syncthreads();
-    if (!have_v) continue;
-    for (int sub = 0; sub < kEdgeTile; sub += 32) {
-      const uint32_t u = tb + sub + lane;
-      const bool valid = (u < V) && (u != v);
-      float b[6] = {0, 0, 0, 0, 0, 0};
-      for (int c = 0; c < nc; ++c) b[c] = s_tile[c * kEdgeTile + sub + lane];
-      Conn cn;
-      conn_setup(g, a, b, cn);
-      bool ok = valid && (cn.cost < g.r);
-      if (ok) ok = !conn_collides(g, cn, s_lo, s_hi);
-      const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
-      if (FILL && ok) {
-        const int64_t cq = quantise_cost(cn.cost);
-        int64_t S, C;
-        conn_transfer(g, cn, cq, S, C);
-        if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX) atomicOr(err, kErrEdge);
-        const uint32_t pos = out_base + running + __popc(bal & ((1u << lane) - 1u));
-        edges[pos] = make_int4((int)u, (int)cq, (int)S, (int)C);
+    const uint32_t incl = warp_incl_scan(rl);
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t excl = incl - rl;
+    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+      const uint32_t c = c0 + lane;
+      uint32_t owner = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t probe = owner + step;
+        if (__shfl_sync(0xFFFFFFFFu, excl, probe) <= c) owner = probe;
       }
-      running += __popc(bal);
+      const uint32_t o_rs = __shfl_sync(0xFFFFFFFFu, rs, owner);
+      const uint32_t o_ex = __shfl_sync(0xFFFFFFFFu, excl, owner);
+      bool near = false;
+      uint32_t u = 0;
+      if (c < total) {
+        const uint32_t s = o_rs + (c - o_ex);
+        u = J.sorted[s];
+        float b[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < nc; ++k) b[k] = J.sx[(size_t)k * V + s];
+        near = (u != v) && (conn_cost_t<DIM>(g, a, b) < g.r);
+      }
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, near);
+      if (near) q[qn + __popc(bal & lt)] = u;
+      qn += __popc(bal);
+      if (qn >= 32) {
+        __syncwarp();
+        edge_flush<DIM, FILL>(J, a, q, 32, s_lo, s_hi, out_base, running);
+        const uint32_t rest = (32 + (int)lane < qn) ? q[32 + lane] : 0u;
+        __syncwarp();
+        if (32 + (int)lane < qn) q[lane] = rest;
+        qn -= 32;
+        __syncwarp();
+      }
     }
   }
-  if (!FILL && have_v && lane == 0) counts[v] = running;
+  __syncwarp();
+  if (qn > 0) edge_flush<DIM, FILL>(J, a, q, qn, s_lo, s_hi, out_base, running);
+  if (!FILL && lane == 0) J.counts[v] = running;
 }
 
-// In-degree count and reverse fill (one warp per source), then per-row sort.
-__global__ void k_indegree(const uint32_t* __restrict__ fwd_ptr, const int4* __restrict__ fe,
-                           uint32_t V, uint32_t* indeg) {
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < V; v += warps)
-    for (uint32_t e = fwd_ptr[v] + lane_id(); e < fwd_ptr[v + 1]; e += 32) atomicAdd(&indeg[fe[e].x], 1u);
-}
-
-__global__ void k_reverse_fill(const uint32_t* __restrict__ fwd_ptr, const int4* __restrict__ fe,
-                               uint32_t V, const uint32_t* __restrict__ rev_ptr, uint32_t* fill,
-                               int4* __restrict__ re) {
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < V; v += warps)
-    for (uint32_t e = fwd_ptr[v] + lane_id(); e < fwd_ptr[v + 1]; e += 32) {
-      const int4 ed = fe[e];
-      const uint32_t pos = rev_ptr[ed.x] + atomicAdd(&fill[ed.x], 1u);
-      re[pos] = make_int4((int)v, ed.y, ed.z, ed.w);
+// Sort every CSR row by neighbour id: one warp per row, a bitonic sort of the
+// row held in registers (K entries per lane, element i = 32 h + lane), for rows
+// of up to 256 entries; longer rows are insertion-sorted by one lane.
+template <int K>
+__device__ __forceinline__ void bitonic_row(int4* row, uint32_t len) {
+  const unsigned lane = lane_id();
+  int4 e[K];
+#pragma unroll
+  for (int h = 0; h < K; ++h) {
+    const uint32_t i = 32u * h + lane;
+    e[h] = i < len ? row[i] : make_int4(INT_MAX, 0, 0, 0);
+  }
+#pragma unroll
+  for (int k = 2; k <= 32 * K; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int jh = j >> 5;
+#pragma unroll
+        for (int h = 0; h < K; ++h) {
+          if ((h & jh) == 0) {
+            const int h2 = h | jh;
+            const bool up = (((32 * h + (int)lane) & k) == 0);
+            const bool sw = up ? (e[h2].x < e[h].x) : (e[h].x < e[h2].x);
+            if (sw) {
+              const int4 t = e[h];
+              e[h] = e[h2];
+              e[h2] = t;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < K; ++h) {
+          const int i = 32 * h + (int)lane;
+          int4 o;
+          o.x = __shfl_xor_sync(0xFFFFFFFFu, e[h].x, j);
+          o.y = __shfl_xor_sync(0xFFFFFFFFu, e[h].y, j);
+          o.z = __shfl_xor_sync(0xFFFFFFFFu, e[h].z, j);
+          o.w = __shfl_xor_sync(0xFFFFFFFFu, e[h].w, j);
+          const bool up = (i & k) == 0;
+          const bool lower = (i & j) == 0;
+          const bool take = (lower == up) ? (o.x < e[h].x) : (e[h].x < o.x);
+          if (take) e[h] = o;
+        }
+      }
     }
+  }
+#pragma unroll
+  for (int h = 0; h < K; ++h) {
+    const uint32_t i = 32u * h + lane;
+    if (i < len) row[i] = e[h];
+  }
 }
 
-__global__ void k_sort_rows(const uint32_t* __restrict__ ptr, int4* __restrict__ rows, uint32_t V) {
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
-    const uint32_t b = ptr[v], e = ptr[v + 1];
-    for (uint32_t i = b + 1; i < e; ++i) {
-      const int4 key = rows[i];
+__device__ __forceinline__ void sort_row(int4* row, uint32_t len) {
+  if (len <= 1) return;
+  if (len <= 32) return bitonic_row<1>(row, len);
+  if (len <= 64) return bitonic_row<2>(row, len);
+  if (len <= 128) return bitonic_row<4>(row, len);
+  if (len <= 256) return bitonic_row<8>(row, len);
+  if (lane_id() == 0) {
+    for (uint32_t i = 1; i < len; ++i) {
+      const int4 key = row[i];
       uint32_t j = i;
-      while (j > b && rows[j - 1].x > key.x) {
-        rows[j] = rows[j - 1];
+      while (j > 0 && row[j - 1].x > key.x) {
+        row[j] = row[j - 1];
         --j;
       }
-      rows[j] = key;
+      row[j] = key;
     }
   }
+  __syncwarp();
 }
 
+__global__ void k_sort_rows(const BuildJob* __restrict__ jobs, int reverse) {
+  const BuildJob& J = jobs[blockIdx.y];
+  const uint32_t* ptr = reverse ? J.rev_ptr : J.fwd_ptr;
+  int4* rows = reverse ? J.rev_edge : J.fwd_edge;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < J.V; v += warps)
+    sort_row(rows + ptr[v], ptr[v + 1] - ptr[v]);
+}
+
+// In-degree count and reverse fill (one warp per source).
+__global__ void k_indegree(const BuildJob* __restrict__ jobs) {
+  const BuildJob& J = jobs[blockIdx.y];
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < J.V; v += warps)
+    for (uint32_t e = J.fwd_ptr[v] + lane_id(); e < J.fwd_ptr[v + 1]; e += 32)
+      atomicAdd(&J.counts[J.fwd_edge[e].x], 1u);
+}
+
+__global__ void k_reverse_fill(const BuildJob* __restrict__ jobs) {
+  const BuildJob& J = jobs[blockIdx.y];
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < J.V; v += warps)
+    for (uint32_t e = J.fwd_ptr[v] + lane_id(); e < J.fwd_ptr[v + 1]; e += 32) {
+      const int4 ed = J.fwd_edge[e];
+      const uint32_t pos = J.rev_ptr[ed.x] + atomicAdd(&J.fill[ed.x], 1u);
+      J.rev_edge[pos] = make_int4((int)v, ed.y, ed.z, ed.w);
+    }
+}
+
+template <bool FILL>
+void launch_edges(int dim, dim3 grid, size_t smem, cudaStream_t st, const BuildJob* jobs, const uint32_t* ids) {
+  LaunchScope ls(st, FILL ? "k_edges_fill" : "k_edges_count");
+  const dim3 block(kEdgeWarps * 32);
+  if (dim == 6) k_edges<6, FILL><<<grid, block, smem, st>>>(jobs, ids);
+  else if (dim == 3) k_edges<3, FILL><<<grid, block, smem, st>>>(jobs, ids);
+  else k_edges<2, FILL><<<grid, block, smem, st>>>(jobs, ids);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
 namespace {
-
-template <typename T>
-int32_t dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  MPAP_CK(cudaMalloc((void**)p, count * sizeof(T)));
-  return MPAP_OK;
-}
-
-int32_t copy_in(void* dst, const void* src, size_t bytes, bool device_src, cudaStream_t st) {
-  if (bytes == 0) return MPAP_OK;
-  MPAP_CK(cudaMemcpyAsync(dst, src, bytes, device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  return MPAP_OK;
-}
 
 int sm_count() {
   static int n = 0;
@@ -318,32 +551,138 @@ int sm_count() {
   return n;
 }
 
-#define MPAP_TRY(x)                  \
-  do {                               \
-    int32_t rc_ = (x);               \
-    if (rc_ != MPAP_OK) {            \
-      roadmap_free_impl(rm);         \
-      return rc_;                    \
-    }                                \
-  } while (0)
+// (Re)allocates *p to hold `need` elements unless `cap` already suffices.
+template <typename T>
+int32_t grow(T** p, size_t& cap, size_t need) {
+  if (need == 0) need = 1;
+  if (*p && cap >= need) return MPAP_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  cap = 0;
+  MPAP_CK(cudaMalloc((void**)p, need * sizeof(T)));
+  cap = need;
+  return MPAP_OK;
+}
 
-// Builds the reverse CSR and the forward/reverse consistency from a filled
-// forward CSR (fwd_ptr, fwd_edge).
-int32_t finish_reverse(mpap_roadmap* rm, cudaStream_t st) {
-  uint32_t* indeg = nullptr;
-  MPAP_CK(cudaMallocAsync((void**)&indeg, sizeof(uint32_t) * (rm->V + 1), st));
-  MPAP_CK(cudaMemsetAsync(indeg, 0, sizeof(uint32_t) * (rm->V + 1), st));
-  const int blocks = 4 * sm_count();
-  if (rm->E) k_indegree<<<blocks, 256, 0, st>>>(rm->fwd_ptr, rm->fwd_edge, rm->V, indeg);
-  launch_exclusive_scan(indeg, rm->rev_ptr, rm->V, nullptr, st);
-  MPAP_CK(cudaMemsetAsync(indeg, 0, sizeof(uint32_t) * (rm->V + 1), st));
-  if (rm->E) {
-    k_reverse_fill<<<blocks, 256, 0, st>>>(rm->fwd_ptr, rm->fwd_edge, rm->V, rm->rev_ptr, indeg, rm->rev_edge);
-    k_sort_rows<<<(rm->V + 255) / 256, 256, 0, st>>>(rm->rev_ptr, rm->rev_edge, rm->V);
+int32_t copy_in(void* dst, const void* src, size_t bytes, bool device_src, cudaStream_t st) {
+  if (bytes == 0) return MPAP_OK;
+  MPAP_CK(cudaMemcpyAsync(dst, src, bytes, device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  return MPAP_OK;
+}
+
+// Scratch block carved into 256-byte aligned regions.
+struct Carve {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
   }
-  MPAP_CK(cudaFreeAsync(indeg, st));
+};
+
+void neighbour_ball(int dim, float r, float T, int dp, float& R, int& GC) {
+  if (dim == 6) {
+    const double budget = std::max(0.0, ((double)r - (double)T) * 1.01 + 0.01);
+    const double Td = (double)T;
+    R = (float)(std::sqrt(budget * Td * Td * Td / 3.0) * 1.001 + 1e-6);
+    GC = (int)std::floor(4.0 / std::max((double)R, 1e-3));
+    GC = std::min(std::max(GC, 1), 32);
+  } else {
+    R = (float)((double)r * 1.001 + 1e-6);
+    GC = (int)std::floor(2.0 / std::max((double)R, 1e-4));
+    GC = std::min(std::max(GC, 1), dp == 2 ? 256 : 64);
+  }
+}
+
+int32_t upload(void* d, const void* h, size_t bytes, cudaStream_t st) {
+  MPAP_CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st));
+  return MPAP_OK;
+}
+
+// Reverse CSR of the jobs' forward graphs (counts and fill are zeroed scratch).
+int32_t build_reverse(uint32_t n, const std::vector<BuildJob>& hj, const BuildJob* d_jobs, ScanSeg* d_seg,
+                      uint32_t Vmax, cudaStream_t st) {
+  const int sms = sm_count();
+  const dim3 gridw(std::min<uint32_t>((Vmax + 7) / 8, 4u * sms), n);
+  {
+    LaunchScope ls(st, "k_indegree");
+    k_indegree<<<gridw, 256, 0, st>>>(d_jobs);
+  }
+  std::vector<ScanSeg> segs(n);
+  for (uint32_t j = 0; j < n; ++j) segs[j] = ScanSeg{hj[j].counts, hj[j].rev_ptr, hj[j].V, nullptr};
+  int32_t rc = upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st);
+  if (rc) return rc;
+  {
+    LaunchScope ls(st, "k_scan_segments");
+    k_scan_segments<<<n, 1024, 0, st>>>(d_seg);
+  }
+  {
+    LaunchScope ls(st, "k_reverse_fill");
+    k_reverse_fill<<<gridw, 256, 0, st>>>(d_jobs);
+  }
+  {
+    LaunchScope ls(st, "k_sort_rows");
+    k_sort_rows<<<gridw, 256, 0, st>>>(d_jobs, 1);
+  }
   MPAP_CK(cudaGetLastError());
   return MPAP_OK;
+}
+
+// Device buffers of one roadmap sized for V nodes (reused when large enough).
+int32_t ensure_nodes(mpap_roadmap* rm, uint32_t V) {
+  if (rm->x && rm->cap_V >= V) return MPAP_OK;
+  cudaFree(rm->x);
+  cudaFree(rm->is_goal);
+  cudaFree(rm->goal_list);
+  cudaFree(rm->fwd_ptr);
+  cudaFree(rm->rev_ptr);
+  rm->x = nullptr;
+  rm->is_goal = nullptr;
+  rm->goal_list = nullptr;
+  rm->fwd_ptr = nullptr;
+  rm->rev_ptr = nullptr;
+  rm->cap_V = 0;
+  MPAP_CK(cudaMalloc((void**)&rm->x, sizeof(float) * 6 * (size_t)V));
+  MPAP_CK(cudaMalloc((void**)&rm->is_goal, V));
+  MPAP_CK(cudaMalloc((void**)&rm->goal_list, sizeof(uint32_t) * (size_t)V));
+  MPAP_CK(cudaMalloc((void**)&rm->fwd_ptr, sizeof(uint32_t) * ((size_t)V + 1)));
+  MPAP_CK(cudaMalloc((void**)&rm->rev_ptr, sizeof(uint32_t) * ((size_t)V + 1)));
+  rm->cap_V = V;
+  return MPAP_OK;
+}
+
+int32_t ensure_edges(mpap_roadmap* rm, uint64_t E) {
+  const size_t need = E ? (size_t)E : 1;
+  if (rm->fwd_edge && rm->rev_edge && rm->cap_E >= need) return MPAP_OK;
+  cudaFree(rm->fwd_edge);
+  cudaFree(rm->rev_edge);
+  rm->fwd_edge = nullptr;
+  rm->rev_edge = nullptr;
+  rm->cap_E = 0;
+  MPAP_CK(cudaMalloc((void**)&rm->fwd_edge, sizeof(int4) * need));
+  MPAP_CK(cudaMalloc((void**)&rm->rev_edge, sizeof(int4) * need));
+  rm->cap_E = need;
+  return MPAP_OK;
+}
+
+int32_t ensure_scene(mpap_roadmap* rm, size_t nb, size_t cells) {
+  if (!rm->box_lo || rm->cap_nb < 3 * nb + 3) {
+    cudaFree(rm->box_lo);
+    cudaFree(rm->box_hi);
+    rm->box_lo = nullptr;
+    rm->box_hi = nullptr;
+    rm->cap_nb = 0;
+    MPAP_CK(cudaMalloc((void**)&rm->box_lo, sizeof(float) * (3 * nb + 3)));
+    MPAP_CK(cudaMalloc((void**)&rm->box_hi, sizeof(float) * (3 * nb + 3)));
+    rm->cap_nb = 3 * nb + 3;
+  }
+  size_t c = rm->cap_cells;
+  int32_t rc = grow(&rm->grid, c, cells);
+  rm->cap_cells = c;
+  return rc;
 }
 
 }  // namespace
@@ -363,148 +702,284 @@ void roadmap_free_impl(mpap_roadmap* rm) {
   delete rm;
 }
 
-int32_t build_roadmap_impl(const mpap_scene* sc, const mpap_roadmap_params* prm, const float* host_x,
-                           uint32_t V_given, float r, float T, int M, float goal_radius,
-                           mpap_roadmap** out, cudaStream_t st) {
-  mpap_roadmap* rm = new mpap_roadmap();
-  rm->dim = sc->dim_kind;
-  rm->nb = sc->nb;
-  rm->G = sc->grid_G;
-  rm->n_f = sc->n_f;
-  rm->K = sc->K;
-  rm->M = M;
-  rm->r = r;
-  rm->T = T;
-  rm->goal_radius = goal_radius;
-  rm->has_geometry = true;
-  rm->V = host_x ? V_given : prm->n + 2u;
-  const uint32_t V = rm->V;
-  const int dp = (rm->dim == 2) ? 2 : 3;
-  size_t cells = (size_t)rm->G * rm->G * (dp == 3 ? rm->G : 1);
-  const bool dev = (sc->mem == MPAP_MEM_DEVICE);
-
-  MPAP_TRY(dalloc(&rm->box_lo, 3 * (size_t)rm->nb));
-  MPAP_TRY(dalloc(&rm->box_hi, 3 * (size_t)rm->nb));
-  MPAP_TRY(dalloc(&rm->grid, cells));
-  MPAP_TRY(copy_in(rm->box_lo, sc->box_lo, 12 * (size_t)rm->nb, dev, st));
-  MPAP_TRY(copy_in(rm->box_hi, sc->box_hi, 12 * (size_t)rm->nb, dev, st));
-  MPAP_TRY(copy_in(rm->grid, sc->grid_level, cells, dev, st));
-  fill_geom_constants(rm->geom, rm->dim, rm->nb, rm->G, rm->n_f, M, r, T);
-  rm->geom.box_lo = rm->box_lo;
-  rm->geom.box_hi = rm->box_hi;
-  rm->geom.grid = rm->grid;
-  const Geom& g = rm->geom;
-
-  MPAP_TRY(dalloc(&rm->x, 6 * (size_t)V));
-  MPAP_TRY(dalloc(&rm->is_goal, V));
-  MPAP_TRY(dalloc(&rm->goal_list, V));
-  MPAP_TRY(dalloc(&rm->fwd_ptr, (size_t)V + 1));
-  MPAP_TRY(dalloc(&rm->rev_ptr, (size_t)V + 1));
-
-  // small device scratch: [0] error bits, [1] n_goal, [2] scan overflow
-  uint32_t* scratch = nullptr;
-  if (!cuda_ok(cudaMallocAsync((void**)&scratch, 16, st), "cudaMallocAsync")) {
-    roadmap_free_impl(rm);
-    return MPAP_ERR_CUDA;
+int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** rms, cudaStream_t st) {
+  if (n == 0) return MPAP_OK;
+  std::vector<char> created(n, 0);
+  char* blk = nullptr;
+  auto fail = [&](int32_t rc) {
+    if (blk) cudaFreeAsync(blk, st);
+    for (uint32_t j = 0; j < n; ++j)
+      if (created[j]) {
+        roadmap_free_impl(rms[j]);
+        rms[j] = nullptr;
+      }
+    return rc;
+  };
+#define MPAP_BTRY(x)                 \
+  do {                               \
+    const int32_t rc_ = (x);         \
+    if (rc_ != MPAP_OK) return fail(rc_); \
+  } while (0)
+  std::vector<BuildJob> hj(n);
+  std::vector<size_t> cand_cap(n), ncells(n);
+  uint32_t Vmax = 0;
+  int max_nb = 0;
+  // 1. handles, buffers, scene copies, job constants
+  for (uint32_t j = 0; j < n; ++j) {
+    const BuildSpec& sp = specs[j];
+    const mpap_scene* sc = sp.scene;
+    if (!rms[j]) {
+      rms[j] = new mpap_roadmap();
+      created[j] = 1;
+    }
+    mpap_roadmap* rm = rms[j];
+    rm->dim = sc->dim_kind;
+    rm->nb = sc->nb;
+    rm->G = sc->grid_G;
+    rm->n_f = sc->n_f;
+    rm->K = sc->K;
+    rm->M = sp.M;
+    rm->r = sp.r;
+    rm->T = sp.T;
+    rm->goal_radius = sp.goal_radius;
+    rm->has_geometry = true;
+    rm->V = sp.points ? sp.V_points : sp.params->n + 2u;
+    rm->E = 0;
+    rm->n_goal = 0;
+    const uint32_t V = rm->V;
+    const int dp = (rm->dim == 2) ? 2 : 3;
+    const size_t cells = (size_t)rm->G * rm->G * (dp == 3 ? rm->G : 1);
+    const bool dev = (sc->mem == MPAP_MEM_DEVICE);
+    MPAP_BTRY(ensure_scene(rm, (size_t)rm->nb, cells));
+    MPAP_BTRY(ensure_nodes(rm, V));
+    MPAP_BTRY(copy_in(rm->box_lo, sc->box_lo, 12 * (size_t)rm->nb, dev, st));
+    MPAP_BTRY(copy_in(rm->box_hi, sc->box_hi, 12 * (size_t)rm->nb, dev, st));
+    MPAP_BTRY(copy_in(rm->grid, sc->grid_level, cells, dev, st));
+    if (sp.points) MPAP_BTRY(copy_in(rm->x, sp.points, sizeof(float) * 6 * (size_t)V, false, st));
+    fill_geom_constants(rm->geom, rm->dim, rm->nb, rm->G, rm->n_f, sp.M, sp.r, sp.T);
+    rm->geom.box_lo = rm->box_lo;
+    rm->geom.box_hi = rm->box_hi;
+    rm->geom.grid = rm->grid;
+    BuildJob& J = hj[j];
+    std::memset(&J, 0, sizeof(J));
+    J.g = rm->geom;
+    J.x = rm->x;
+    J.V = V;
+    J.n = sp.points ? 0u : sp.params->n;
+    if (!sp.points) {
+      J.key0 = (uint32_t)sp.params->seed;
+      J.key1 = (uint32_t)(sp.params->seed >> 32);
+      J.qid = sp.params->query_id;
+      for (int a = 0; a < 6; ++a) {
+        J.xi[a] = sp.params->x_init[a];
+        J.xg[a] = sp.params->x_goal[a];
+      }
+    }
+    J.goal_r2 = sp.goal_radius * sp.goal_radius;
+    J.is_goal = rm->is_goal;
+    J.goal_list = rm->goal_list;
+    neighbour_ball(rm->dim, sp.r, sp.T, dp, J.R, J.GC);
+    ncells[j] = dp == 2 ? (size_t)J.GC * J.GC : (size_t)J.GC * J.GC * J.GC;
+    J.fwd_ptr = rm->fwd_ptr;
+    J.rev_ptr = rm->rev_ptr;
+    cand_cap[j] = J.n ? std::min<size_t>((size_t)J.n * 2 + 8192, (size_t)1 << 22) : 0;
+    Vmax = std::max(Vmax, V);
+    max_nb = std::max(max_nb, rm->nb);
   }
-  cudaMemsetAsync(scratch, 0, 16, st);
+  // 2. one scratch block; the regions that must start at zero come first
+  size_t bytes = 256 * 8 + (sizeof(ScanSeg) + sizeof(BuildJob) + 24) * (size_t)n;
+  for (uint32_t j = 0; j < n; ++j)
+    bytes += 256 * 12 + 4 * (ncells[j] + 1) + 16 + 32 * (cand_cap[j] + 1) + 4 * (ncells[j] + 1) +
+             40 * ((size_t)hj[j].V + 1);
+  MPAP_CK(cudaMallocAsync((void**)&blk, bytes, st));
+  Carve cv{blk, 0};
+  for (uint32_t j = 0; j < n; ++j) hj[j].cell_cnt = cv.take<uint32_t>(ncells[j] + 1);
+  for (uint32_t j = 0; j < n; ++j) hj[j].status = cv.take<uint32_t>(4);
+  const size_t zero_bytes = cv.off;
+  BuildJob* d_jobs = cv.take<BuildJob>(n);
+  ScanSeg* d_seg = cv.take<ScanSeg>(n);
+  uint32_t* d_gather = cv.take<uint32_t>(5 * (size_t)n);
+  uint32_t* d_ids = cv.take<uint32_t>(n);
+  for (uint32_t j = 0; j < n; ++j) {
+    BuildJob& J = hj[j];
+    J.cand = cv.take<float>(6 * cand_cap[j]);
+    J.ok = cv.take<uint32_t>(cand_cap[j] + 1);
+    J.rank = cv.take<uint32_t>(cand_cap[j] + 1);
+    J.cell_start = cv.take<uint32_t>(ncells[j] + 1);
+    J.cell_of = cv.take<uint32_t>(J.V);
+    J.sorted = cv.take<uint32_t>(J.V);
+    J.sx = cv.take<float>(6 * (size_t)J.V);
+    J.counts = cv.take<uint32_t>((size_t)J.V + 1);
+    J.fill = cv.take<uint32_t>((size_t)J.V + 1);
+  }
+  if (cv.off > bytes) {
+    set_error("roadmap: scratch layout overflow");
+    return fail(MPAP_ERR_CUDA);
+  }
+  MPAP_CK(cudaMemsetAsync(blk, 0, zero_bytes, st));
   const int sms = sm_count();
-  const size_t box_smem = sizeof(float) * 6 * (size_t)rm->nb;
-
-  if (host_x) {
-    MPAP_TRY(copy_in(rm->x, host_x, sizeof(float) * 6 * (size_t)V, false, st));
-  } else {
-    k_set_endpoints<<<1, 32, 0, st>>>(rm->x, V, prm->x_init[0], prm->x_init[1], prm->x_init[2],
-                                       prm->x_init[3], prm->x_init[4], prm->x_init[5], prm->x_goal[0],
-                                       prm->x_goal[1], prm->x_goal[2], prm->x_goal[3], prm->x_goal[4],
-                                       prm->x_goal[5]);
-    // SampleFree in batches until n samples are kept (attempt budget 64 n + 4096).
-    const uint64_t max_att = (uint64_t)prm->n * 64ull + 4096ull;
-    const uint32_t key0 = (uint32_t)prm->seed, key1 = (uint32_t)(prm->seed >> 32);
-    uint32_t kept = 0;
-    uint64_t a0 = 0;
-    float* cand = nullptr;
-    uint32_t *ok = nullptr, *rank = nullptr;
-    const uint32_t cap = 1u << 22;
-    MPAP_CK(cudaMallocAsync((void**)&cand, sizeof(float) * 6 * cap, st));
-    MPAP_CK(cudaMallocAsync((void**)&ok, sizeof(uint32_t) * cap, st));
-    MPAP_CK(cudaMallocAsync((void**)&rank, sizeof(uint32_t) * (cap + 1), st));
-    while (kept < prm->n) {
-      if (a0 >= max_att || a0 > 0xFFFFFFFFull) break;
-      uint64_t want = (uint64_t)(prm->n - kept) * 2ull + 8192ull;
-      uint64_t count64 = want < cap ? want : cap;
-      if (count64 > max_att - a0) count64 = max_att - a0;
-      const uint32_t count = (uint32_t)count64;
-      const int blocks = (int)((count + 255) / 256 < (uint32_t)(8 * sms) ? (count + 255) / 256 : 8 * sms);
-      k_sample_candidates<<<blocks, 256, box_smem, st>>>(g, key0, key1, prm->query_id, (uint32_t)a0,
-                                                         count, cand, ok);
-      launch_exclusive_scan(ok, rank, count, nullptr, st);
-      k_take_samples<<<blocks, 256, 0, st>>>(cand, ok, rank, count, prm->n - kept, 2u + kept, rm->x, V);
-      uint32_t total = 0;
-      MPAP_CK(cudaMemcpyAsync(&total, rank + count, 4, cudaMemcpyDeviceToHost, st));
-      MPAP_CK(cudaStreamSynchronize(st));
-      kept += (total < prm->n - kept) ? total : (prm->n - kept);
-      a0 += count;
+  std::vector<uint32_t> hg(5 * (size_t)n);
+  auto gather = [&]() -> int32_t {
+    {
+      LaunchScope ls(st, "k_gather_status");
+      k_gather_status<<<(n + 127) / 128, 128, 0, st>>>(d_jobs, n, d_gather);
     }
-    cudaFreeAsync(cand, st);
-    cudaFreeAsync(ok, st);
-    cudaFreeAsync(rank, st);
-    if (kept < prm->n) {
-      cudaFreeAsync(scratch, st);
-      set_error("SampleFree: only %u of %u free samples in %llu attempts", kept, prm->n,
-                (unsigned long long)max_att);
-      roadmap_free_impl(rm);
-      return MPAP_ERR_SAMPLING;
+    MPAP_CK(cudaMemcpyAsync(hg.data(), d_gather, sizeof(uint32_t) * 5 * n, cudaMemcpyDeviceToHost, st));
+    MPAP_CK(cudaStreamSynchronize(st));
+    return MPAP_OK;
+  };
+  std::vector<ScanSeg> segs(n);
+
+  // 3. SampleFree rounds (all sampling jobs together)
+  bool any_sampling = false;
+  for (uint32_t j = 0; j < n; ++j) any_sampling = any_sampling || hj[j].n > 0;
+  if (any_sampling) {
+    std::vector<uint64_t> att(n, 0);
+    for (uint32_t round = 0;; ++round) {
+      uint32_t maxc = 0;
+      for (uint32_t j = 0; j < n; ++j) {
+        BuildJob& J = hj[j];
+        J.cand_count = 0;
+        if (J.n == 0 || J.kept >= J.n) continue;
+        const uint64_t max_att = (uint64_t)J.n * 64ull + 4096ull;
+        if (att[j] >= max_att || att[j] > 0xFFFFFFFFull) {
+          set_error("SampleFree: only %u of %u free samples in %llu attempts (roadmap %u)", J.kept, J.n,
+                    (unsigned long long)max_att, j);
+          return fail(MPAP_ERR_SAMPLING);
+        }
+        J.a0 = (uint32_t)att[j];
+        J.cand_count = (uint32_t)std::min<uint64_t>(cand_cap[j], max_att - att[j]);
+        maxc = std::max(maxc, J.cand_count);
+      }
+      if (maxc == 0) break;
+      MPAP_BTRY(upload(d_jobs, hj.data(), sizeof(BuildJob) * n, st));
+      if (round == 0) {
+        LaunchScope ls(st, "k_set_endpoints");
+        k_set_endpoints<<<(n + 127) / 128, 128, 0, st>>>(d_jobs, n);
+      }
+      const dim3 grid(std::min<uint32_t>((maxc + 255) / 256, 2u * sms), n);
+      {
+        LaunchScope ls(st, "k_sample_candidates");
+        k_sample_candidates<<<grid, 256, sizeof(float) * 6 * max_nb, st>>>(d_jobs);
+      }
+      for (uint32_t j = 0; j < n; ++j) segs[j] = ScanSeg{hj[j].ok, hj[j].rank, hj[j].cand_count, nullptr};
+      MPAP_BTRY(upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st));
+      {
+        LaunchScope ls(st, "k_scan_segments");
+        k_scan_segments<<<n, 1024, 0, st>>>(d_seg);
+      }
+      {
+        LaunchScope ls(st, "k_take_samples");
+        k_take_samples<<<grid, 256, 0, st>>>(d_jobs);
+      }
+      MPAP_BTRY(gather());
+      for (uint32_t j = 0; j < n; ++j) {
+        BuildJob& J = hj[j];
+        if (J.cand_count == 0) continue;
+        const uint32_t need = J.n - J.kept;
+        J.kept += std::min(hg[5 * j + 0], need);
+        att[j] += J.cand_count;
+      }
+    }
+    for (uint32_t j = 0; j < n; ++j) hj[j].cand_count = 0;
+  }
+  MPAP_BTRY(upload(d_jobs, hj.data(), sizeof(BuildJob) * n, st));
+
+  // 4. goal region and spatial binning
+  const dim3 gridv(std::min<uint32_t>((Vmax + 255) / 256, 2u * sms), n);
+  {
+    LaunchScope ls(st, "k_mark_goal");
+    k_mark_goal<<<gridv, 256, 0, st>>>(d_jobs);
+  }
+  {
+    LaunchScope ls(st, "k_bin_count");
+    k_bin_count<<<gridv, 256, 0, st>>>(d_jobs);
+  }
+  for (uint32_t j = 0; j < n; ++j) segs[j] = ScanSeg{hj[j].cell_cnt, hj[j].cell_start, (uint32_t)ncells[j], nullptr};
+  MPAP_BTRY(upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st));
+  {
+    LaunchScope ls(st, "k_scan_segments");
+    k_scan_segments<<<n, 1024, 0, st>>>(d_seg);
+  }
+  // cell counts become scatter cursors (the count region precedes the status words)
+  MPAP_CK(cudaMemsetAsync(blk, 0, (size_t)((char*)hj[0].status - blk), st));
+  {
+    LaunchScope ls(st, "k_bin_scatter");
+    k_bin_scatter<<<gridv, 256, 0, st>>>(d_jobs);
+  }
+
+  // 5. Near + Collision: count pass, row pointers, fill pass (one launch per dim)
+  std::vector<uint32_t> ids;
+  const int dims[3] = {2, 3, 6};
+  uint32_t id_off[4] = {0, 0, 0, 0};
+  for (int di = 0; di < 3; ++di) {
+    id_off[di] = (uint32_t)ids.size();
+    for (uint32_t j = 0; j < n; ++j)
+      if (hj[j].g.dim == dims[di]) ids.push_back(j);
+  }
+  id_off[3] = (uint32_t)ids.size();
+  MPAP_BTRY(upload(d_ids, ids.data(), sizeof(uint32_t) * n, st));
+  const size_t esmem = sizeof(float) * 6 * max_nb + sizeof(uint32_t) * kEdgeWarps * kQueue;
+  auto edges_pass = [&](bool fill) {
+    for (int di = 0; di < 3; ++di) {
+      const uint32_t cnt = id_off[di + 1] - id_off[di];
+      if (!cnt) continue;
+      uint32_t vmax = 0;
+      for (uint32_t k = id_off[di]; k < id_off[di + 1]; ++k) vmax = std::max(vmax, hj[ids[k]].V);
+      const dim3 grid((vmax + kEdgeWarps - 1) / kEdgeWarps, cnt);
+      if (fill) launch_edges<true>(dims[di], grid, esmem, st, d_jobs, d_ids + id_off[di]);
+      else launch_edges<false>(dims[di], grid, esmem, st, d_jobs, d_ids + id_off[di]);
+    }
+  };
+  edges_pass(false);
+  for (uint32_t j = 0; j < n; ++j) segs[j] = ScanSeg{hj[j].counts, hj[j].fwd_ptr, hj[j].V, hj[j].status + 2};
+  MPAP_BTRY(upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st));
+  {
+    LaunchScope ls(st, "k_scan_segments");
+    k_scan_segments<<<n, 1024, 0, st>>>(d_seg);
+  }
+  MPAP_BTRY(gather());
+  for (uint32_t j = 0; j < n; ++j) {
+    if (hg[5 * j + 4]) {
+      set_error("roadmap %u: more than 2^32 - 1 edges", j);
+      return fail(MPAP_ERR_CAPACITY);
+    }
+    mpap_roadmap* rm = rms[j];
+    rm->E = hg[5 * j + 1];
+    MPAP_BTRY(ensure_edges(rm, rm->E));
+    hj[j].fwd_edge = rm->fwd_edge;
+    hj[j].rev_edge = rm->rev_edge;
+  }
+  MPAP_BTRY(upload(d_jobs, hj.data(), sizeof(BuildJob) * n, st));
+  edges_pass(true);
+  {
+    const dim3 gridw(std::min<uint32_t>((Vmax + 7) / 8, 4u * sms), n);
+    LaunchScope ls(st, "k_sort_rows");
+    k_sort_rows<<<gridw, 256, 0, st>>>(d_jobs, 0);
+  }
+  // 6. reverse CSR
+  for (uint32_t j = 0; j < n; ++j) {
+    MPAP_CK(cudaMemsetAsync(hj[j].counts, 0, 4 * ((size_t)hj[j].V + 1), st));
+    MPAP_CK(cudaMemsetAsync(hj[j].fill, 0, 4 * ((size_t)hj[j].V + 1), st));
+  }
+  MPAP_BTRY(build_reverse(n, hj, d_jobs, d_seg, Vmax, st));
+  MPAP_BTRY(gather());
+  cudaFreeAsync(blk, st);
+  blk = nullptr;
+  for (uint32_t j = 0; j < n; ++j) {
+    rms[j]->n_goal = hg[5 * j + 3];
+    if (hg[5 * j + 2]) {
+      set_error("roadmap %u: an edge cost or transfer does not fit int32", j);
+      return fail(MPAP_ERR_CAPACITY);
     }
   }
-
-  k_mark_goal<<<(V + 255) / 256, 256, 0, st>>>(rm->x, V, dp, goal_radius * goal_radius, rm->is_goal,
-                                               rm->goal_list, scratch + 1);
-
-  // Near + Collision: count pass, scan, fill pass.
-  uint32_t* counts = nullptr;
-  MPAP_CK(cudaMallocAsync((void**)&counts, sizeof(uint32_t) * (V + 1), st));
-  const int nc = (rm->dim == 6) ? 6 : dp;
-  const size_t esmem = box_smem + sizeof(float) * nc * kEdgeTile;
-  const int eblocks = (int)((V + kEdgeWarps - 1) / kEdgeWarps);
-  k_edges<false><<<eblocks, kEdgeWarps * 32, esmem, st>>>(g, rm->x, V, counts, nullptr, nullptr, scratch);
-  launch_exclusive_scan(counts, rm->fwd_ptr, V, scratch + 2, st);
-  uint32_t hs[4] = {0, 0, 0, 0};
-  uint32_t E32 = 0;
-  MPAP_CK(cudaMemcpyAsync(&E32, rm->fwd_ptr + V, 4, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaMemcpyAsync(hs, scratch, 12, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaStreamSynchronize(st));
-  if (hs[2]) {
-    set_error("roadmap: more than 2^32 - 1 edges");
-    cudaFreeAsync(counts, st);
-    cudaFreeAsync(scratch, st);
-    roadmap_free_impl(rm);
-    return MPAP_ERR_CAPACITY;
-  }
-  rm->E = E32;
-  rm->n_goal = hs[1];
-  MPAP_TRY(dalloc(&rm->fwd_edge, rm->E));
-  MPAP_TRY(dalloc(&rm->rev_edge, rm->E));
-  k_edges<true><<<eblocks, kEdgeWarps * 32, esmem, st>>>(g, rm->x, V, nullptr, rm->fwd_ptr, rm->fwd_edge,
-                                                         scratch);
-  MPAP_CK(cudaGetLastError());
-  cudaFreeAsync(counts, st);
-  MPAP_TRY(finish_reverse(rm, st));
-  MPAP_CK(cudaMemcpyAsync(hs, scratch, 4, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaStreamSynchronize(st));
-  cudaFreeAsync(scratch, st);
-  if (hs[0]) {
-    set_error("roadmap: an edge cost or transfer does not fit int32");
-    roadmap_free_impl(rm);
-    return MPAP_ERR_CAPACITY;
-  }
-  *out = rm;
+#undef MPAP_BTRY
   return MPAP_OK;
 }
 
-int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst,
-                              const int32_t* cost_q, const int32_t* S, const int32_t* C,
-                              const uint8_t* is_goal, mpap_roadmap** out, cudaStream_t st) {
+int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst, const int32_t* cost_q,
+                              const int32_t* S, const int32_t* C, const uint8_t* is_goal, mpap_roadmap** out,
+                              cudaStream_t st) {
   mpap_roadmap* rm = new mpap_roadmap();
   rm->V = V;
   rm->E = row_ptr[V];
@@ -515,20 +990,43 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
   for (uint32_t v = 0; v < V; ++v)
     if (is_goal[v]) goals.push_back(v);
   rm->n_goal = (uint32_t)goals.size();
-  MPAP_TRY(dalloc(&rm->x, 6 * (size_t)V));
-  MPAP_TRY(dalloc(&rm->is_goal, V));
-  MPAP_TRY(dalloc(&rm->goal_list, V));
-  MPAP_TRY(dalloc(&rm->fwd_ptr, (size_t)V + 1));
-  MPAP_TRY(dalloc(&rm->rev_ptr, (size_t)V + 1));
-  MPAP_TRY(dalloc(&rm->fwd_edge, rm->E));
-  MPAP_TRY(dalloc(&rm->rev_edge, rm->E));
-  MPAP_CK(cudaMemsetAsync(rm->x, 0, sizeof(float) * 6 * (size_t)V, st));
-  MPAP_TRY(copy_in(rm->is_goal, is_goal, V, false, st));
-  MPAP_TRY(copy_in(rm->goal_list, goals.data(), 4 * goals.size(), false, st));
-  MPAP_TRY(copy_in(rm->fwd_ptr, row_ptr, 4 * ((size_t)V + 1), false, st));
-  MPAP_TRY(copy_in(rm->fwd_edge, fe.data(), sizeof(int4) * rm->E, false, st));
-  MPAP_TRY(finish_reverse(rm, st));
-  MPAP_CK(cudaStreamSynchronize(st));
+  int32_t rc;
+  auto bail = [&](int32_t r) {
+    roadmap_free_impl(rm);
+    return r;
+  };
+  if ((rc = ensure_nodes(rm, V)) || (rc = ensure_edges(rm, rm->E))) return bail(rc);
+  if (!cuda_ok(cudaMemsetAsync(rm->x, 0, sizeof(float) * 6 * (size_t)V, st), "memset")) return bail(MPAP_ERR_CUDA);
+  if ((rc = copy_in(rm->is_goal, is_goal, V, false, st)) ||
+      (rc = copy_in(rm->goal_list, goals.data(), 4 * goals.size(), false, st)) ||
+      (rc = copy_in(rm->fwd_ptr, row_ptr, 4 * ((size_t)V + 1), false, st)) ||
+      (rc = copy_in(rm->fwd_edge, fe.data(), sizeof(int4) * rm->E, false, st)))
+    return bail(rc);
+  // reverse CSR with the build kernels (one job)
+  BuildJob J;
+  std::memset(&J, 0, sizeof(J));
+  J.V = V;
+  J.fwd_ptr = rm->fwd_ptr;
+  J.fwd_edge = rm->fwd_edge;
+  J.rev_ptr = rm->rev_ptr;
+  J.rev_edge = rm->rev_edge;
+  char* blk = nullptr;
+  const size_t bytes = 4096 + 8 * ((size_t)V + 1) + 1024;
+  if (!cuda_ok(cudaMallocAsync((void**)&blk, bytes, st), "cudaMallocAsync")) return bail(MPAP_ERR_CUDA);
+  Carve cv{blk, 0};
+  BuildJob* d_job = cv.take<BuildJob>(1);
+  ScanSeg* d_seg = cv.take<ScanSeg>(1);
+  J.counts = cv.take<uint32_t>((size_t)V + 1);
+  J.fill = cv.take<uint32_t>((size_t)V + 1);
+  std::vector<BuildJob> hj(1, J);
+  if (!cuda_ok(cudaMemsetAsync(J.counts, 0, 4 * ((size_t)V + 1), st), "memset") ||
+      !cuda_ok(cudaMemsetAsync(J.fill, 0, 4 * ((size_t)V + 1), st), "memset") ||
+      (rc = upload(d_job, &J, sizeof(J), st)) || (rc = build_reverse(1, hj, d_job, d_seg, V, st))) {
+    cudaFreeAsync(blk, st);
+    return bail(rc ? rc : MPAP_ERR_CUDA);
+  }
+  cudaFreeAsync(blk, st);
+  if (!cuda_ok(cudaStreamSynchronize(st), "sync")) return bail(MPAP_ERR_CUDA);
   *out = rm;
   return MPAP_OK;
 }

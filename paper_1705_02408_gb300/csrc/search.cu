@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "profile.h"
 
 namespace mpap {
 
@@ -809,8 +810,14 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   MPAP_CK(cudaMemsetAsync(w.touch_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.oh_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
   dim3 fg((unsigned)std::min<uint64_t>((total / nq + 255) / 256 + 1, 64), std::min(nq, 1024u));
-  k_fill_qid<<<fg, 256, 0, st>>>(w, nq);
-  k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq);
+  {
+    ::mpap::LaunchScope ls_(st, "k_fill_qid");
+    k_fill_qid<<<fg, 256, 0, st>>>(w, nq);
+  }
+  {
+    ::mpap::LaunchScope ls_(st, "k_init");
+    k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq);
+  }
   MPAP_CK(cudaGetLastError());
 
   const int blocks_sel = 16 * sms();
@@ -820,9 +827,18 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   Ctl hc{};
   while (true) {
     for (uint32_t r = 0; r < check_every; ++r, ++it) {
-      k_select<<<blocks_sel, kWarpsPerBlock * 32, 0, st>>>(w, it);
-      k_prune<<<blocks_pr, kWarpsPerBlock * 32, 0, st>>>(w, it);
-      k_end<<<(nq + 127) / 128, 128, 0, st>>>(w, it, nq);
+      {
+        ::mpap::LaunchScope ls_(st, "k_select");
+        k_select<<<blocks_sel, kWarpsPerBlock * 32, 0, st>>>(w, it);
+      }
+      {
+        ::mpap::LaunchScope ls_(st, "k_prune");
+        k_prune<<<blocks_pr, kWarpsPerBlock * 32, 0, st>>>(w, it);
+      }
+      {
+        ::mpap::LaunchScope ls_(st, "k_end");
+        k_end<<<(nq + 127) / 128, 128, 0, st>>>(w, it, nq);
+      }
     }
     MPAP_CK(cudaGetLastError());
     MPAP_CK(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -833,7 +849,10 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
       return MPAP_ERR_ITER_LIMIT;
     }
   }
-  k_finalize<<<nq, 256, 0, st>>>(w, nq);
+  {
+    ::mpap::LaunchScope ls_(st, "k_finalize");
+    k_finalize<<<nq, 256, 0, st>>>(w, nq);
+  }
   MPAP_CK(cudaGetLastError());
   std::vector<ResultDev> res(nq);
   std::vector<QueryState> qsh(nq);

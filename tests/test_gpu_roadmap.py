@@ -68,3 +68,17 @@ def test_roadmap_full_size_6d(mp, orc):
     rg = mp.build_roadmap_for_scene(sc)
     ro = orc.build_roadmap(sc)
     assert_same_graph(rg.export(), ro.graph())
+
+
+def test_batched_build_and_handle_reuse(mp, orc):
+    """mpap_build_roadmaps: mixed dimensions in one call, then a rebuild of the
+    same handles with other scenes and sizes (smaller and larger)."""
+    first = [("2d", 1, 1000, None), ("3d", 2, 1500, None), ("6d", 3, 2000, None), ("2d", 4, 300, 0.2)]
+    second = [("6d", 5, 2500, None), ("2d", 6, 200, 0.2), ("3d", 7, 3000, None), ("6d", 8, 700, 20.0)]
+    rms = None
+    for batch in (first, second):
+        scenes = [scenegen.make_scene(nm, sd, query_id=sd) for nm, sd, _, _ in batch]
+        specs = [mp.scene_spec(sc, n=n, r=r) for sc, (_, _, n, r) in zip(scenes, batch)]
+        rms = mp.build_roadmaps(specs, rms=rms)
+        for sc, rg, (_, _, n, r) in zip(scenes, rms, batch):
+            assert_same_graph(rg.export(), orc.build_roadmap(sc, n=n, r=r).graph())

@@ -76,15 +76,15 @@ def test_scenes(mp, orc, ws, name, seed, n, beta_mode):
     a2 = orc.explore(ro, beta, lam_q, goal_termination=False)
     b2 = mp.search(ws, rg, beta, lam=0.5, goal_stop=False)
     assert_same_search(b2, a2, ws)
-    # a front cap below the largest oracle front is reported, not truncated
+    # a front cap below the largest final oracle front is reported, not truncated
+    # (fronts can be larger mid-search than at the end, so only this direction
+    # is implied by the final fronts)
     biggest = int(np.diff(a2.front_ptr).max())
     if biggest > 1:
         small = mp.Workspace(rg.V, front_cap=biggest - 1, max_plans=1 << 23)
         with pytest.raises(mp.MpapError) as e:
             mp.search(small, rg, beta, lam=0.5, goal_stop=False)
         assert e.value.status == mp.MPAP_ERR_CAPACITY
-        exact = mp.Workspace(rg.V, front_cap=biggest, max_plans=1 << 23)
-        assert_same_search(mp.search(exact, rg, beta, lam=0.5, goal_stop=False), a2, exact)
 
 
 def test_batch_matches_individual(mp, orc):
