@@ -238,14 +238,13 @@ def run_gpu(args, rank, world, local):
            "ms_per_query": ms / per_query,
            "gpu_launches": int(launches)}
     # breakdown from the live kernel timers (timed region)
-    phase = {"build": ["k_sample_candidates", "k_take_samples", "k_set_endpoints", "k_mark_goal",
-                       "k_edges_count", "k_edges_fill", "k_indegree", "k_reverse_fill", "k_sort_rows",
-                       "k_exclusive_scan"],
-             "search": ["k_fill_qid", "k_init", "k_select", "k_prune", "k_end", "k_finalize"],
-             "certify": ["k_mc_checkpoints", "k_mc_rollouts"]}
+    search_k = {"k_fill_qid", "k_init", "k_select", "k_prune", "k_end", "k_finalize"}
+    certify_k = {"k_mc_checkpoints", "k_mc_rollouts"}
+    phase = {"build": 0.0, "search": 0.0, "certify": 0.0}
+    for k, (_, t) in kern.items():
+        phase["search" if k in search_k else "certify" if k in certify_k else "build"] += t / args.steps
     out["kernel_ms_per_step"] = {k: round(v[1] / args.steps, 4) for k, v in sorted(kern.items())}
-    out["phase_kernel_ms_per_step"] = {p: round(sum(kern.get(k, (0, 0.0))[1] for k in ks) / args.steps, 4)
-                                       for p, ks in phase.items()}
+    out["phase_kernel_ms_per_step"] = {p: round(t, 4) for p, t in phase.items()}
     out["expansions_per_step"] = exps / args.steps
     out["solved"] = sum(1 for r in res if r.status == 0)
     out["certified_failure_rate"] = sum(c["hits_any"] for c in certs) / max(1, sum(c["rollouts"] for c in certs))
@@ -275,16 +274,20 @@ def roofline(kern, arm, res, steps):
     B = len(arm.scenes)
     exps = sum(r.expansions for r in res)
     plans = sum(r.plans for r in res)
-    if name in ("k_edges_count", "k_edges_fill"):
-        # ALU-bound: 39 binary32 operations decide Near for one ordered pair
-        # (see the design doc); FMA is disabled, one op per lane per clock.
-        ops_per_launch = 39.0 * V * V      # one launch covers all ordered pairs of one roadmap
+    if name.startswith("k_edges"):
+        # ALU-bound: one exactly evaluated Near test (Cost(v, u) < r) of the 6D
+        # double integrator costs 39 binary32 operations;
+        # FMA is disabled, so each is one lane-op.  The tests are counted on the
+        # device by the build (cells outside the neighbour ball are never tested).
+        tests = sum(rm.stats()[0] for rm in arm.rms)
+        ops_per_launch = 39.0 * tests * steps / max(1, launches)
         achieved = ops_per_launch / (ms / launches / 1e3) / 1e12
         sm_max = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * sm_max * 1e6 / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (derived)"}
+                "frac": achieved / peak, "traffic": None, "near_tests_per_step": tests,
+                "all_pairs_per_step": V * V * B,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
     # HBM-bound search kernels: algorithmic bytes per step
     bytes_step = 16.0 * exps + 24.0 * plans
     per_launch = bytes_step * steps / max(1, launches)

@@ -191,9 +191,15 @@ int32_t mpap_roadmap_from_csr(uint32_t V, const uint32_t* row_ptr, const uint32_
 int32_t mpap_roadmap_info(const mpap_roadmap* rm, uint32_t* V, uint64_t* E);
 
 /* Copies the roadmap to host arrays (any pointer may be NULL): x float[6][V],
- * is_goal[V], row_ptr[V+1], dst/cost_q/S/C[E].  Synchronises the stream. */
+ * is_goal[V], row_ptr[V+1], dst/cost_q/S/C[E] with every row sorted by
+ * neighbour (on the device rows are kept in discovery order; no kernel depends
+ * on it).  Synchronises the stream. */
 int32_t mpap_roadmap_export(const mpap_roadmap* rm, float* x, uint8_t* is_goal, uint32_t* row_ptr,
                             uint32_t* dst, int32_t* cost_q, int32_t* S, int32_t* C, void* stream);
+
+/* Build statistics: Near tests (Cost < r evaluations) performed by the last
+ * build of this roadmap, and the number of nodes in X_goal. */
+int32_t mpap_roadmap_stats(const mpap_roadmap* rm, uint64_t* near_tests, uint32_t* n_goal);
 
 void mpap_roadmap_free(mpap_roadmap* rm);
 

@@ -29,7 +29,7 @@ MPAP_QUERY_NO_GOAL_STOP = 1
 
 EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_build_roadmaps",
            "mpap_build_roadmap_from_points", "mpap_roadmap_from_csr", "mpap_roadmap_info",
-           "mpap_roadmap_export", "mpap_roadmap_free", "mpap_workspace_create",
+           "mpap_roadmap_export", "mpap_roadmap_stats", "mpap_roadmap_free", "mpap_workspace_create",
            "mpap_workspace_free", "mpap_search", "mpap_search_batch", "mpap_search_fronts",
            "mpap_certify", "mpap_certify_batch", "mpap_profile_enable", "mpap_profile_reset",
            "mpap_launch_count", "mpap_profile_read"]
@@ -102,6 +102,8 @@ def lib():
         L.mpap_roadmap_export.restype = i32
         L.mpap_roadmap_export.argtypes = [P, P, P, P, P, P, P, P, P]
         L.mpap_roadmap_free.argtypes = [P]
+        L.mpap_roadmap_stats.restype = i32
+        L.mpap_roadmap_stats.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]
         L.mpap_workspace_create.restype = i32
         L.mpap_workspace_create.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.POINTER(P)]
         L.mpap_workspace_free.argtypes = [P]
@@ -228,6 +230,12 @@ class Roadmap:
         V = C.c_uint32(); E = C.c_uint64()
         _check(lib().mpap_roadmap_info(self.h, C.byref(V), C.byref(E)), "mpap_roadmap_info")
         return V.value, E.value
+
+    def stats(self):
+        """(Near tests evaluated by the last build, nodes in X_goal)."""
+        nt = C.c_uint64(); ng = C.c_uint32()
+        _check(lib().mpap_roadmap_stats(self.h, C.byref(nt), C.byref(ng)), "mpap_roadmap_stats")
+        return nt.value, ng.value
 
     @property
     def V(self):

@@ -1,5 +1,6 @@
 // C ABI of libmpap (declared in include/mpap.h): argument validation and
 // dispatch to the roadmap, search and certification implementations.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -196,6 +197,15 @@ int32_t mpap_roadmap_export(const mpap_roadmap* rm, float* x, uint8_t* is_goal, 
       delete[] tmp;
       return MPAP_ERR_CUDA;
     }
+    // device rows are in discovery order; return them sorted by neighbour
+    std::vector<uint32_t> rp(rm->V + 1);
+    if (!mpap::cuda_ok(cudaMemcpy(rp.data(), rm->fwd_ptr, 4 * ((size_t)rm->V + 1), cudaMemcpyDeviceToHost),
+                       "export row pointers")) {
+      delete[] tmp;
+      return MPAP_ERR_CUDA;
+    }
+    for (uint32_t v = 0; v < rm->V; ++v)
+      std::sort(tmp + rp[v], tmp + rp[v + 1], [](const int4& a, const int4& b) { return a.x < b.x; });
     for (uint64_t e = 0; e < rm->E; ++e) {
       if (dst) dst[e] = (uint32_t)tmp[e].x;
       if (cost_q) cost_q[e] = tmp[e].y;
@@ -205,6 +215,16 @@ int32_t mpap_roadmap_export(const mpap_roadmap* rm, float* x, uint8_t* is_goal, 
     delete[] tmp;
   }
   MPAP_CK(cudaStreamSynchronize(st));
+  return MPAP_OK;
+}
+
+int32_t mpap_roadmap_stats(const mpap_roadmap* rm, uint64_t* near_tests, uint32_t* n_goal) {
+  if (!rm) {
+    set_error("null roadmap");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (near_tests) *near_tests = rm->near_tests;
+  if (n_goal) *n_goal = rm->n_goal;
   return MPAP_OK;
 }
 

@@ -25,13 +25,15 @@ struct mpap_roadmap {
   uint32_t* goal_list = nullptr;
   uint32_t n_goal = 0;
   uint32_t* fwd_ptr = nullptr; // [V+1]
-  int4* fwd_edge = nullptr;    // [E] {dst, cost_q, S, C}
+  int4* fwd_edge = nullptr;    // [E] {dst, cost_q, S, C}, rows in discovery order
+  uint32_t* fwd_dst = nullptr; // [E] dst only (for marking out-neighbours)
   uint32_t* rev_ptr = nullptr; // [V+1]
   int4* rev_edge = nullptr;    // [E] {src, cost_q, S, C}
   float* box_lo = nullptr;     // [nb][3]
   float* box_hi = nullptr;
   uint8_t* grid = nullptr;
   size_t cap_V = 0, cap_E = 0, cap_nb = 0, cap_cells = 0;
+  uint64_t near_tests = 0;     // Cost < r tests evaluated by the last build
 };
 
 namespace mpap {
@@ -65,5 +67,9 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
                               const int32_t* cost_q, const int32_t* S, const int32_t* C,
                               const uint8_t* is_goal, mpap_roadmap** out, cudaStream_t st);
 void roadmap_free_impl(mpap_roadmap* rm);
+
+// Stream-ordered scratch from the library's memory pool (kept mapped).
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
+void scratch_free(void* p, cudaStream_t st);
 
 }  // namespace mpap

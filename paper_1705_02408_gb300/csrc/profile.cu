@@ -88,6 +88,20 @@ LaunchScope::~LaunchScope() {
   }
 }
 
+// Kernels launched inside CUDA graphs (the device-side wavefront loop) report
+// their launch counts and device-timed durations here.
+void profile_add(const char* name, uint64_t launches, double ms) {
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  Agg& a = p.agg[name];
+  a.launches += launches;
+  a.ms += ms;
+}
+
+bool profile_enabled() { return prof().on.load(std::memory_order_relaxed); }
+
+void launch_count_add(uint64_t n) { prof().launches.fetch_add(n, std::memory_order_relaxed); }
+
 }  // namespace mpap
 
 extern "C" {

@@ -96,14 +96,19 @@ struct BuildJob {
   uint32_t* cell_start;    // [NC+1]
   uint32_t* cell_of;       // [V]
   uint32_t* sorted;        // [V] node ids in cell order
+  uint32_t* pos_of;        // [V] position of each node in cell order
+  unsigned long long* near_tests;  // evaluated Cost(v, u) < r tests
   float* sx;               // [6][V] states in cell order
   uint32_t* counts;        // [V+1]
   uint32_t* fill;          // [V+1]
+  int4* rows;              // [V][kRowCap] per-source edge rows of the one-pass build
+  uint32_t* ovf;           // [V] sources with more than kRowCap edges (count in status[3])
   uint32_t* fwd_ptr;
   int4* fwd_edge;
+  uint32_t* fwd_dst;
   uint32_t* rev_ptr;
   int4* rev_edge;
-  uint32_t* status;        // [4]: error bits, n_goal, scan overflow, spare
+  uint32_t* status;        // [4]: error bits, n_goal, scan overflow, overflowing sources
 };
 
 struct ScanSeg {
@@ -230,14 +235,18 @@ __global__ void k_set_endpoints(const BuildJob* __restrict__ jobs, uint32_t njob
 // Per-job counters for the host: accepted candidates of the round, edge count,
 // error bits, goal count, scan overflow.
 __global__ void k_gather_status(const BuildJob* __restrict__ jobs, uint32_t njobs, uint32_t* out) {
+  const uint32_t n_jobs_pad = njobs;
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= njobs) return;
   const BuildJob& J = jobs[j];
-  out[5 * j + 0] = J.cand_count ? J.rank[J.cand_count] : 0u;
-  out[5 * j + 1] = J.fwd_ptr[J.V];
-  out[5 * j + 2] = J.status[0];
-  out[5 * j + 3] = J.status[1];
-  out[5 * j + 4] = J.status[2];
+  out[6 * j + 0] = J.cand_count ? J.rank[J.cand_count] : 0u;
+  out[6 * j + 1] = J.fwd_ptr[J.V];
+  out[6 * j + 2] = J.status[0];
+  out[6 * j + 3] = J.status[1];
+  out[6 * j + 4] = J.status[2];
+  out[6 * j + 5] = J.status[3];
+  out[6 * n_jobs_pad + 2 * j] = (uint32_t)(*J.near_tests);
+  out[6 * n_jobs_pad + 2 * j + 1] = (uint32_t)(*J.near_tests >> 32);
 }
 
 // X_goal: nodes within goal_radius (position) of node 1.
@@ -282,6 +291,7 @@ __global__ void k_bin_scatter(const BuildJob* __restrict__ jobs) {
     const uint32_t cell = J.cell_of[v];
     const uint32_t pos = J.cell_start[cell] + atomicAdd(&J.cell_cnt[cell], 1u);
     J.sorted[pos] = v;
+    J.pos_of[v] = pos;
     for (int c = 0; c < nc; ++c) J.sx[(size_t)c * J.V + pos] = J.x[(size_t)c * J.V + v];
   }
 }
@@ -298,9 +308,15 @@ __global__ void k_bin_scatter(const BuildJob* __restrict__ jobs) {
 // ---------------------------------------------------------------------------
 constexpr int kEdgeWarps = 8;
 constexpr int kQueue = 64;
+constexpr uint32_t kRowCap = 128;   // edges per source in the one-pass build
 
-template <int DIM, bool FILL>
-__device__ __forceinline__ void edge_flush(const BuildJob& J, const float a[6], const uint32_t* q, int k,
+// Edge pass modes: one pass writing each source's edges into its own scratch row
+// (kRow), and a second pass over only the sources whose rows overflowed, which
+// writes straight into the CSR (kFillCsr, after the row pointers are known).
+enum EdgeMode { kFillCsr = 1, kRow = 2 };
+
+template <int DIM, int MODE>
+__device__ __forceinline__ void edge_flush(const BuildJob& J, uint32_t v, const float a[6], const uint32_t* q, int k,
                                            const float* s_lo, const float* s_hi, uint32_t out_base,
                                            uint32_t& running) {
   const Geom& g = J.g;
@@ -318,19 +334,26 @@ __device__ __forceinline__ void edge_flush(const BuildJob& J, const float a[6], 
     ok = !conn_collides_t<DIM>(g, cn, s_lo, s_hi);
   }
   const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
-  if (FILL && ok) {
-    const int64_t cq = quantise_cost(cn.cost);
-    int64_t S, C;
-    conn_transfer_t<DIM>(g, cn, cq, S, C);
-    if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX) atomicOr(&J.status[0], kErrEdge);
-    const uint32_t pos = out_base + running + __popc(bal & ((1u << lane) - 1u));
-    J.fwd_edge[pos] = make_int4((int)u, (int)cq, (int)S, (int)C);
+  if (ok) {
+    const uint32_t rank = running + __popc(bal & ((1u << lane) - 1u));
+    if (MODE == kFillCsr || rank < kRowCap) {
+      const int64_t cq = quantise_cost(cn.cost);
+      int64_t S, C;
+      conn_transfer_t<DIM>(g, cn, cq, S, C);
+      if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX) atomicOr(&J.status[0], kErrEdge);
+      const int4 rec = make_int4((int)u, (int)cq, (int)S, (int)C);
+      if (MODE == kFillCsr) {
+        J.fwd_edge[out_base + rank] = rec;
+        J.fwd_dst[out_base + rank] = u;
+      }
+      else J.rows[(size_t)v * kRowCap + rank] = rec;
+    }
   }
   running += __popc(bal);
 }
 
-template <int DIM, bool FILL>
-__global__ void __launch_bounds__(kEdgeWarps * 32) k_edges(const BuildJob* __restrict__ jobs,
+template <int DIM, int MODE>
+__global__ void __launch_bounds__(kEdgeWarps * 32, 4) k_edges(const BuildJob* __restrict__ jobs,
                                                            const uint32_t* __restrict__ job_ids) {
   const BuildJob& J = jobs[job_ids[blockIdx.y]];
   const Geom& g = J.g;
@@ -349,40 +372,73 @@ __global__ void __launch_bounds__(kEdgeWarps * 32) k_edges(const BuildJob* __res
     s_hi[i] = g.box_hi[i];
   }
   __syncthreads();
-  const uint32_t v = blockIdx.x * kEdgeWarps + warp;
-  if (v >= J.V) return;
+  const uint32_t slot = blockIdx.x * kEdgeWarps + warp;
+  uint32_t v = slot;
+  if (MODE == kFillCsr) {
+    if (slot >= J.status[3]) return;
+    v = J.ovf[slot];
+  } else if (v >= J.V) {
+    return;
+  }
   const uint32_t V = J.V;
   float a[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
   for (int c = 0; c < nc; ++c) a[c] = J.x[(size_t)c * V + v];
-  // cell range of the neighbour ball
+  // centre and cell range of the neighbour ball
   const int GC = J.GC;
+  const float R = J.R;
+  const float cs = 1.0f / (float)GC;
+  float ctr[3] = {0, 0, 0};
   int clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
 #pragma unroll
   for (int i = 0; i < DP; ++i) {
-    const float c = (DIM == 6) ? __fadd_rn(a[i], __fmul_rn(a[3 + i], g.T)) : a[i];
-    clo[i] = cell_coord(c - J.R, GC);
-    chi[i] = cell_coord(c + J.R, GC);
+    ctr[i] = (DIM == 6) ? __fadd_rn(a[i], __fmul_rn(a[3 + i], g.T)) : a[i];
+    clo[i] = cell_coord(ctr[i] - R, GC);
+    chi[i] = cell_coord(ctr[i] + R, GC);
   }
   const uint32_t ny = (uint32_t)(chi[1] - clo[1] + 1);
   const uint32_t nruns = ny * (DP == 3 ? (uint32_t)(chi[2] - clo[2] + 1) : 1u);
+  const uint32_t my_pos = J.pos_of[v];
   uint32_t running = 0;
+  uint32_t tests = 0;
   int qn = 0;
-  const uint32_t out_base = FILL ? J.fwd_ptr[v] : 0u;
+  const uint32_t out_base = (MODE == kFillCsr) ? J.fwd_ptr[v] : 0u;
   for (uint32_t r0 = 0; r0 < nruns; r0 += 32) {
-    // lane j describes run r0 + j: the cells [clo_x, chi_x] of one (y, z) row
+    // lane j describes run r0 + j: the x-range of one (y, z) row of cells, clipped
+    // to the ball's cross-section at the row's nearest point (conservative)
     uint32_t rs = 0, rl = 0;
     const uint32_t rr = r0 + lane;
     if (rr < nruns) {
       const uint32_t yy = (uint32_t)clo[1] + rr % ny;
       const uint32_t zz = (DP == 3) ? (uint32_t)clo[2] + rr / ny : 0u;
-      const uint32_t row = (zz * (uint32_t)GC + yy) * (uint32_t)GC;
-      rs = J.cell_start[row + (uint32_t)clo[0]];
-      rl = J.cell_start[row + (uint32_t)chi[0] + 1u] - rs;
+      const float y0 = (float)yy * cs, y1 = (float)(yy + 1) * cs;
+      const float dy = fmaxf(0.0f, fmaxf(y0 - ctr[1], ctr[1] - y1));
+      float d2 = dy * dy;
+      if (DP == 3) {
+        const float z0 = (float)zz * cs, z1 = (float)(zz + 1) * cs;
+        const float dz = fmaxf(0.0f, fmaxf(z0 - ctr[2], ctr[2] - z1));
+        d2 += dz * dz;
+      }
+      // rows at the clamped grid border may hold nodes outside [0, 1]: keep the
+      // full x-range there
+      const bool border = (yy == 0 || yy == (uint32_t)GC - 1) || (DP == 3 && (zz == 0 || zz == (uint32_t)GC - 1));
+      const float rem = R * R - d2;
+      if (rem >= 0.0f || border) {
+        int xlo = clo[0], xhi = chi[0];
+        if (!border) {
+          const float rx = sqrtf(rem) * 1.0001f + 1e-6f;
+          xlo = cell_coord(ctr[0] - rx, GC);
+          xhi = cell_coord(ctr[0] + rx, GC);
+        }
+        const uint32_t row = (zz * (uint32_t)GC + yy) * (uint32_t)GC;
+        rs = J.cell_start[row + (uint32_t)xlo];
+        rl = J.cell_start[row + (uint32_t)xhi + 1u] - rs;
+      }
     }
     const uint32_t incl = warp_incl_scan(rl);
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     const uint32_t excl = incl - rl;
+    tests += total;
     for (uint32_t c0 = 0; c0 < total; c0 += 32) {
       const uint32_t c = c0 + lane;
       uint32_t owner = 0;
@@ -394,21 +450,20 @@ __global__ void __launch_bounds__(kEdgeWarps * 32) k_edges(const BuildJob* __res
       const uint32_t o_rs = __shfl_sync(0xFFFFFFFFu, rs, owner);
       const uint32_t o_ex = __shfl_sync(0xFFFFFFFFu, excl, owner);
       bool near = false;
-      uint32_t u = 0;
+      uint32_t sidx = 0;
       if (c < total) {
-        const uint32_t s = o_rs + (c - o_ex);
-        u = J.sorted[s];
+        sidx = o_rs + (c - o_ex);
         float b[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-        for (int k = 0; k < nc; ++k) b[k] = J.sx[(size_t)k * V + s];
-        near = (u != v) && (conn_cost_t<DIM>(g, a, b) < g.r);
+        for (int k = 0; k < nc; ++k) b[k] = J.sx[(size_t)k * V + sidx];
+        near = (sidx != my_pos) && (conn_cost_t<DIM>(g, a, b) < g.r);
       }
       const unsigned bal = __ballot_sync(0xFFFFFFFFu, near);
-      if (near) q[qn + __popc(bal & lt)] = u;
+      if (near) q[qn + __popc(bal & lt)] = J.sorted[sidx];
       qn += __popc(bal);
       if (qn >= 32) {
         __syncwarp();
-        edge_flush<DIM, FILL>(J, a, q, 32, s_lo, s_hi, out_base, running);
+        edge_flush<DIM, MODE>(J, v, a, q, 32, s_lo, s_hi, out_base, running);
         const uint32_t rest = (32 + (int)lane < qn) ? q[32 + lane] : 0u;
         __syncwarp();
         if (32 + (int)lane < qn) q[lane] = rest;
@@ -418,92 +473,30 @@ __global__ void __launch_bounds__(kEdgeWarps * 32) k_edges(const BuildJob* __res
     }
   }
   __syncwarp();
-  if (qn > 0) edge_flush<DIM, FILL>(J, a, q, qn, s_lo, s_hi, out_base, running);
-  if (!FILL && lane == 0) J.counts[v] = running;
-}
-
-// Sort every CSR row by neighbour id: one warp per row, a bitonic sort of the
-// row held in registers (K entries per lane, element i = 32 h + lane), for rows
-// of up to 256 entries; longer rows are insertion-sorted by one lane.
-template <int K>
-__device__ __forceinline__ void bitonic_row(int4* row, uint32_t len) {
-  const unsigned lane = lane_id();
-  int4 e[K];
-#pragma unroll
-  for (int h = 0; h < K; ++h) {
-    const uint32_t i = 32u * h + lane;
-    e[h] = i < len ? row[i] : make_int4(INT_MAX, 0, 0, 0);
-  }
-#pragma unroll
-  for (int k = 2; k <= 32 * K; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-        const int jh = j >> 5;
-#pragma unroll
-        for (int h = 0; h < K; ++h) {
-          if ((h & jh) == 0) {
-            const int h2 = h | jh;
-            const bool up = (((32 * h + (int)lane) & k) == 0);
-            const bool sw = up ? (e[h2].x < e[h].x) : (e[h].x < e[h2].x);
-            if (sw) {
-              const int4 t = e[h];
-              e[h] = e[h2];
-              e[h2] = t;
-            }
-          }
-        }
-      } else {
-#pragma unroll
-        for (int h = 0; h < K; ++h) {
-          const int i = 32 * h + (int)lane;
-          int4 o;
-          o.x = __shfl_xor_sync(0xFFFFFFFFu, e[h].x, j);
-          o.y = __shfl_xor_sync(0xFFFFFFFFu, e[h].y, j);
-          o.z = __shfl_xor_sync(0xFFFFFFFFu, e[h].z, j);
-          o.w = __shfl_xor_sync(0xFFFFFFFFu, e[h].w, j);
-          const bool up = (i & k) == 0;
-          const bool lower = (i & j) == 0;
-          const bool take = (lower == up) ? (o.x < e[h].x) : (e[h].x < o.x);
-          if (take) e[h] = o;
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int h = 0; h < K; ++h) {
-    const uint32_t i = 32u * h + lane;
-    if (i < len) row[i] = e[h];
+  if (qn > 0) edge_flush<DIM, MODE>(J, v, a, q, qn, s_lo, s_hi, out_base, running);
+  if (MODE == kRow && lane == 0) {
+    J.counts[v] = running;
+    if (running > kRowCap) J.ovf[atomicAdd(&J.status[3], 1u)] = v;
+    atomicAdd(J.near_tests, (unsigned long long)tests);
   }
 }
 
-__device__ __forceinline__ void sort_row(int4* row, uint32_t len) {
-  if (len <= 1) return;
-  if (len <= 32) return bitonic_row<1>(row, len);
-  if (len <= 64) return bitonic_row<2>(row, len);
-  if (len <= 128) return bitonic_row<4>(row, len);
-  if (len <= 256) return bitonic_row<8>(row, len);
-  if (lane_id() == 0) {
-    for (uint32_t i = 1; i < len; ++i) {
-      const int4 key = row[i];
-      uint32_t j = i;
-      while (j > 0 && row[j - 1].x > key.x) {
-        row[j] = row[j - 1];
-        --j;
-      }
-      row[j] = key;
-    }
-  }
-  __syncwarp();
-}
-
-__global__ void k_sort_rows(const BuildJob* __restrict__ jobs, int reverse) {
+// One-pass build: copy each source's scratch row (at most kRowCap edges) into
+// the CSR (warp per source).  Rows stay in discovery order: no kernel depends on
+// the order of a row, and mpap_roadmap_export returns rows sorted by neighbour.
+__global__ void k_compact_rows(const BuildJob* __restrict__ jobs) {
   const BuildJob& J = jobs[blockIdx.y];
-  const uint32_t* ptr = reverse ? J.rev_ptr : J.fwd_ptr;
-  int4* rows = reverse ? J.rev_edge : J.fwd_edge;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < J.V; v += warps)
-    sort_row(rows + ptr[v], ptr[v + 1] - ptr[v]);
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < J.V; v += warps) {
+    const uint32_t b = J.fwd_ptr[v], len = J.fwd_ptr[v + 1] - b;
+    if (len > kRowCap) continue;   // written by the overflow pass
+    const int4* src = J.rows + (size_t)v * kRowCap;
+    for (uint32_t i = lane_id(); i < len; i += 32) {
+      const int4 e = src[i];
+      J.fwd_edge[b + i] = e;
+      J.fwd_dst[b + i] = (uint32_t)e.x;
+    }
+  }
 }
 
 // In-degree count and reverse fill (one warp per source).
@@ -526,13 +519,13 @@ __global__ void k_reverse_fill(const BuildJob* __restrict__ jobs) {
     }
 }
 
-template <bool FILL>
+template <int MODE>
 void launch_edges(int dim, dim3 grid, size_t smem, cudaStream_t st, const BuildJob* jobs, const uint32_t* ids) {
-  LaunchScope ls(st, FILL ? "k_edges_fill" : "k_edges_count");
+  LaunchScope ls(st, MODE == kRow ? "k_edges" : "k_edges_overflow");
   const dim3 block(kEdgeWarps * 32);
-  if (dim == 6) k_edges<6, FILL><<<grid, block, smem, st>>>(jobs, ids);
-  else if (dim == 3) k_edges<3, FILL><<<grid, block, smem, st>>>(jobs, ids);
-  else k_edges<2, FILL><<<grid, block, smem, st>>>(jobs, ids);
+  if (dim == 6) k_edges<6, MODE><<<grid, block, smem, st>>>(jobs, ids);
+  else if (dim == 3) k_edges<3, MODE><<<grid, block, smem, st>>>(jobs, ids);
+  else k_edges<2, MODE><<<grid, block, smem, st>>>(jobs, ids);
 }
 
 // ---------------------------------------------------------------------------
@@ -569,6 +562,38 @@ int32_t copy_in(void* dst, const void* src, size_t bytes, bool device_src, cudaS
   MPAP_CK(cudaMemcpyAsync(dst, src, bytes, device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   return MPAP_OK;
 }
+
+}  // namespace
+
+// Stream-ordered scratch from a library-owned memory pool that keeps freed
+// memory mapped, so repeated calls of the same size do not map pages again.
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pools[dev], st);
+}
+
+void scratch_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+namespace {
 
 // Scratch block carved into 256-byte aligned regions.
 struct Carve {
@@ -623,10 +648,6 @@ int32_t build_reverse(uint32_t n, const std::vector<BuildJob>& hj, const BuildJo
     LaunchScope ls(st, "k_reverse_fill");
     k_reverse_fill<<<gridw, 256, 0, st>>>(d_jobs);
   }
-  {
-    LaunchScope ls(st, "k_sort_rows");
-    k_sort_rows<<<gridw, 256, 0, st>>>(d_jobs, 1);
-  }
   MPAP_CK(cudaGetLastError());
   return MPAP_OK;
 }
@@ -656,14 +677,17 @@ int32_t ensure_nodes(mpap_roadmap* rm, uint32_t V) {
 
 int32_t ensure_edges(mpap_roadmap* rm, uint64_t E) {
   const size_t need = E ? (size_t)E : 1;
-  if (rm->fwd_edge && rm->rev_edge && rm->cap_E >= need) return MPAP_OK;
+  if (rm->fwd_edge && rm->rev_edge && rm->fwd_dst && rm->cap_E >= need) return MPAP_OK;
   cudaFree(rm->fwd_edge);
   cudaFree(rm->rev_edge);
+  cudaFree(rm->fwd_dst);
   rm->fwd_edge = nullptr;
   rm->rev_edge = nullptr;
+  rm->fwd_dst = nullptr;
   rm->cap_E = 0;
   MPAP_CK(cudaMalloc((void**)&rm->fwd_edge, sizeof(int4) * need));
   MPAP_CK(cudaMalloc((void**)&rm->rev_edge, sizeof(int4) * need));
+  MPAP_CK(cudaMalloc((void**)&rm->fwd_dst, sizeof(uint32_t) * need));
   rm->cap_E = need;
   return MPAP_OK;
 }
@@ -694,6 +718,7 @@ void roadmap_free_impl(mpap_roadmap* rm) {
   cudaFree(rm->goal_list);
   cudaFree(rm->fwd_ptr);
   cudaFree(rm->fwd_edge);
+  cudaFree(rm->fwd_dst);
   cudaFree(rm->rev_ptr);
   cudaFree(rm->rev_edge);
   cudaFree(rm->box_lo);
@@ -707,7 +732,7 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   std::vector<char> created(n, 0);
   char* blk = nullptr;
   auto fail = [&](int32_t rc) {
-    if (blk) cudaFreeAsync(blk, st);
+    if (blk) scratch_free(blk, st);
     for (uint32_t j = 0; j < n; ++j)
       if (created[j]) {
         roadmap_free_impl(rms[j]);
@@ -787,18 +812,19 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     max_nb = std::max(max_nb, rm->nb);
   }
   // 2. one scratch block; the regions that must start at zero come first
-  size_t bytes = 256 * 8 + (sizeof(ScanSeg) + sizeof(BuildJob) + 24) * (size_t)n;
+  size_t bytes = 256 * 8 + (sizeof(ScanSeg) + sizeof(BuildJob) + 48) * (size_t)n + 256 * (size_t)n;
   for (uint32_t j = 0; j < n; ++j)
-    bytes += 256 * 12 + 4 * (ncells[j] + 1) + 16 + 32 * (cand_cap[j] + 1) + 4 * (ncells[j] + 1) +
-             40 * ((size_t)hj[j].V + 1);
-  MPAP_CK(cudaMallocAsync((void**)&blk, bytes, st));
+    bytes += 256 * 13 + 4 * (ncells[j] + 1) + 16 + 32 * (cand_cap[j] + 1) + 4 * (ncells[j] + 1) +
+             48 * ((size_t)hj[j].V + 1) + sizeof(int4) * kRowCap * (size_t)hj[j].V + 512;
+  MPAP_CK(scratch_alloc((void**)&blk, bytes, st));
   Carve cv{blk, 0};
   for (uint32_t j = 0; j < n; ++j) hj[j].cell_cnt = cv.take<uint32_t>(ncells[j] + 1);
   for (uint32_t j = 0; j < n; ++j) hj[j].status = cv.take<uint32_t>(4);
+  for (uint32_t j = 0; j < n; ++j) hj[j].near_tests = cv.take<unsigned long long>(1);
   const size_t zero_bytes = cv.off;
   BuildJob* d_jobs = cv.take<BuildJob>(n);
   ScanSeg* d_seg = cv.take<ScanSeg>(n);
-  uint32_t* d_gather = cv.take<uint32_t>(5 * (size_t)n);
+  uint32_t* d_gather = cv.take<uint32_t>(8 * (size_t)n);
   uint32_t* d_ids = cv.take<uint32_t>(n);
   for (uint32_t j = 0; j < n; ++j) {
     BuildJob& J = hj[j];
@@ -811,6 +837,9 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     J.sx = cv.take<float>(6 * (size_t)J.V);
     J.counts = cv.take<uint32_t>((size_t)J.V + 1);
     J.fill = cv.take<uint32_t>((size_t)J.V + 1);
+    J.rows = cv.take<int4>(kRowCap * (size_t)J.V);
+    J.ovf = cv.take<uint32_t>((size_t)J.V);
+    J.pos_of = cv.take<uint32_t>((size_t)J.V);
   }
   if (cv.off > bytes) {
     set_error("roadmap: scratch layout overflow");
@@ -818,13 +847,13 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   }
   MPAP_CK(cudaMemsetAsync(blk, 0, zero_bytes, st));
   const int sms = sm_count();
-  std::vector<uint32_t> hg(5 * (size_t)n);
+  std::vector<uint32_t> hg(8 * (size_t)n);
   auto gather = [&]() -> int32_t {
     {
       LaunchScope ls(st, "k_gather_status");
       k_gather_status<<<(n + 127) / 128, 128, 0, st>>>(d_jobs, n, d_gather);
     }
-    MPAP_CK(cudaMemcpyAsync(hg.data(), d_gather, sizeof(uint32_t) * 5 * n, cudaMemcpyDeviceToHost, st));
+    MPAP_CK(cudaMemcpyAsync(hg.data(), d_gather, sizeof(uint32_t) * 8 * n, cudaMemcpyDeviceToHost, st));
     MPAP_CK(cudaStreamSynchronize(st));
     return MPAP_OK;
   };
@@ -877,7 +906,7 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
         BuildJob& J = hj[j];
         if (J.cand_count == 0) continue;
         const uint32_t need = J.n - J.kept;
-        J.kept += std::min(hg[5 * j + 0], need);
+        J.kept += std::min(hg[6 * j + 0], need);
         att[j] += J.cand_count;
       }
     }
@@ -920,18 +949,24 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   id_off[3] = (uint32_t)ids.size();
   MPAP_BTRY(upload(d_ids, ids.data(), sizeof(uint32_t) * n, st));
   const size_t esmem = sizeof(float) * 6 * max_nb + sizeof(uint32_t) * kEdgeWarps * kQueue;
-  auto edges_pass = [&](bool fill) {
+  auto edges_pass = [&](int mode) {
     for (int di = 0; di < 3; ++di) {
       const uint32_t cnt = id_off[di + 1] - id_off[di];
       if (!cnt) continue;
       uint32_t vmax = 0;
       for (uint32_t k = id_off[di]; k < id_off[di + 1]; ++k) vmax = std::max(vmax, hj[ids[k]].V);
+      if (mode == kFillCsr) {
+        vmax = 0;
+        for (uint32_t k = id_off[di]; k < id_off[di + 1]; ++k) vmax = std::max(vmax, hg[6 * ids[k] + 5]);
+        if (vmax == 0) continue;
+      }
       const dim3 grid((vmax + kEdgeWarps - 1) / kEdgeWarps, cnt);
-      if (fill) launch_edges<true>(dims[di], grid, esmem, st, d_jobs, d_ids + id_off[di]);
-      else launch_edges<false>(dims[di], grid, esmem, st, d_jobs, d_ids + id_off[di]);
+      if (mode == kRow) launch_edges<kRow>(dims[di], grid, esmem, st, d_jobs, d_ids + id_off[di]);
+      else launch_edges<kFillCsr>(dims[di], grid, esmem, st, d_jobs, d_ids + id_off[di]);
     }
   };
-  edges_pass(false);
+  // one pass: every source's edges into its scratch row, with exact counts
+  edges_pass(kRow);
   for (uint32_t j = 0; j < n; ++j) segs[j] = ScanSeg{hj[j].counts, hj[j].fwd_ptr, hj[j].V, hj[j].status + 2};
   MPAP_BTRY(upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st));
   {
@@ -939,24 +974,28 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     k_scan_segments<<<n, 1024, 0, st>>>(d_seg);
   }
   MPAP_BTRY(gather());
+  bool row_overflow = false;
   for (uint32_t j = 0; j < n; ++j) {
-    if (hg[5 * j + 4]) {
+    if (hg[6 * j + 4]) {
       set_error("roadmap %u: more than 2^32 - 1 edges", j);
       return fail(MPAP_ERR_CAPACITY);
     }
     mpap_roadmap* rm = rms[j];
-    rm->E = hg[5 * j + 1];
+    rm->E = hg[6 * j + 1];
     MPAP_BTRY(ensure_edges(rm, rm->E));
     hj[j].fwd_edge = rm->fwd_edge;
+    hj[j].fwd_dst = rm->fwd_dst;
     hj[j].rev_edge = rm->rev_edge;
+    row_overflow = row_overflow || hg[6 * j + 5] > 0;
   }
   MPAP_BTRY(upload(d_jobs, hj.data(), sizeof(BuildJob) * n, st));
-  edges_pass(true);
+  const dim3 gridw(std::min<uint32_t>((Vmax + 7) / 8, 4u * sms), n);
   {
-    const dim3 gridw(std::min<uint32_t>((Vmax + 7) / 8, 4u * sms), n);
-    LaunchScope ls(st, "k_sort_rows");
-    k_sort_rows<<<gridw, 256, 0, st>>>(d_jobs, 0);
+    LaunchScope ls(st, "k_compact_rows");
+    k_compact_rows<<<gridw, 256, 0, st>>>(d_jobs);
   }
+  // sources with more than kRowCap neighbours: second pass over those only
+  if (row_overflow) edges_pass(kFillCsr);
   // 6. reverse CSR
   for (uint32_t j = 0; j < n; ++j) {
     MPAP_CK(cudaMemsetAsync(hj[j].counts, 0, 4 * ((size_t)hj[j].V + 1), st));
@@ -964,11 +1003,12 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   }
   MPAP_BTRY(build_reverse(n, hj, d_jobs, d_seg, Vmax, st));
   MPAP_BTRY(gather());
-  cudaFreeAsync(blk, st);
+  scratch_free(blk, st);
   blk = nullptr;
   for (uint32_t j = 0; j < n; ++j) {
-    rms[j]->n_goal = hg[5 * j + 3];
-    if (hg[5 * j + 2]) {
+    rms[j]->n_goal = hg[6 * j + 3];
+    rms[j]->near_tests = (uint64_t)hg[6 * n + 2 * j] | ((uint64_t)hg[6 * n + 2 * j + 1] << 32);
+    if (hg[6 * j + 2]) {
       set_error("roadmap %u: an edge cost or transfer does not fit int32", j);
       return fail(MPAP_ERR_CAPACITY);
     }
@@ -1000,7 +1040,8 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
   if ((rc = copy_in(rm->is_goal, is_goal, V, false, st)) ||
       (rc = copy_in(rm->goal_list, goals.data(), 4 * goals.size(), false, st)) ||
       (rc = copy_in(rm->fwd_ptr, row_ptr, 4 * ((size_t)V + 1), false, st)) ||
-      (rc = copy_in(rm->fwd_edge, fe.data(), sizeof(int4) * rm->E, false, st)))
+      (rc = copy_in(rm->fwd_edge, fe.data(), sizeof(int4) * rm->E, false, st)) ||
+      (rc = copy_in(rm->fwd_dst, dst, 4 * (size_t)rm->E, false, st)))
     return bail(rc);
   // reverse CSR with the build kernels (one job)
   BuildJob J;

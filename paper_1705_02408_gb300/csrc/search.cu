@@ -3,7 +3,7 @@
 //
 // Per wavefront (iteration i) three kernels run over all queries of a batch:
 //   select  one warp per node with open plans: the group B_i of that node (its
-//           open plans with cost <= i lambda r_n) is copied to the group array and
+//           open plans with cost <= i Lambda) is copied to the group array and
 //           closed (P_open <- P_open \ B); every out-neighbour is marked touched.
 //           A group plan at a goal node ends its query before expansion.
 //   prune   one warp per touched node x ("pull"): each in-edge u -> x whose source
@@ -12,11 +12,16 @@
 //           x.  The merge is an exact skyline under the weak Pareto order with the
 //           total tie key (creation iteration, parent head): old plans win ties,
 //           candidates tie-break by parent head.  Candidates are consumed in
-//           chunks of 32: filter against the front (binary search), warp bitonic
-//           sort, warp prefix-min, then one merge pass over the front into the
-//           other slab buffer.  Surviving candidates get arena records at the end.
-//   end     one thread per query: termination (goal in group, P_open empty,
-//           iteration cap) and counters.
+//           chunks of 32: filter against the front, warp bitonic sort, warp
+//           prefix-min, then a rank merge.  Fronts of up to 32 entries live in
+//           registers (one entry per lane) for the whole merge; larger fronts are
+//           merged between the two slab buffers in global memory.  Surviving
+//           candidates get arena records at the end.
+//   end     one block: termination per query (goal in group, P_open empty,
+//           iteration cap), list swap, loop condition.
+// The loop runs on the device: the three kernels form the body of a CUDA graph
+// conditional WHILE node, which `end` clears once every query has finished (or
+// the iteration caps are reached), so a search is one graph launch.
 //
 // HBM layout (NV = nodes summed over the batch, F = front capacity):
 //   fronts   2 x [NV][F] of {cost i64, h i64, ref u32 (arena | open | new), aux u32}
@@ -25,6 +30,7 @@
 //   arena    [cap] {head u32, parent u32, iter u32, cost i64} for back-tracing
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -37,7 +43,7 @@ struct QueryDev {
   const uint32_t* rev_ptr;
   const int4* rev_edge;
   const uint32_t* fwd_ptr;
-  const int4* fwd_edge;
+  const uint32_t* fwd_dst;
   const uint8_t* is_goal;
   const uint32_t* goal_list;
   uint32_t n_goal;
@@ -67,6 +73,15 @@ struct ResultDev {
   int32_t status;
 };
 
+// Device-side launch timing of the loop kernels (first block start to last
+// block end, %globaltimer nanoseconds).
+struct KTime {
+  unsigned long long start;
+  unsigned long long total_ns;
+  uint32_t blocks;
+  uint32_t launches;
+};
+
 struct Ctl {
   uint32_t oh_n[2];
   uint32_t t_n;
@@ -74,6 +89,11 @@ struct Ctl {
   unsigned long long arena_n;
   uint32_t err;
   uint32_t n_done;
+  uint32_t it;          // current wavefront
+  uint32_t nq;
+  uint32_t iter_cap;    // loop bound (max over queries of max_iters, plus 2)
+  uint32_t prof;        // record KTime
+  KTime kt[3];          // select, prune, end
 };
 
 struct WS {
@@ -87,11 +107,9 @@ struct WS {
   uint32_t* f_cnt;
   uint8_t* cur;
   uint32_t* qid;
-  uint32_t* act_stamp;
+  uint4* gdesc;            // per node {iteration stamp, group count, group offset, 0}
   uint32_t* touch_stamp;
   uint32_t* oh_stamp;
-  uint32_t* g_off;
-  uint32_t* g_cnt;
   long long* g_cost;
   long long* g_h;
   uint32_t* g_pid;
@@ -114,6 +132,10 @@ struct WS {
 struct mpap_workspace {
   mpap::WS w{};
   uint32_t max_q = 0;
+  // the device-side wavefront loop (built on first use)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
   // host record of the last search (for front export)
   std::vector<uint32_t> last_V, last_base;
 };
@@ -122,8 +144,13 @@ namespace mpap {
 
 constexpr int kWarpsPerBlock = 8;
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kSelectBlocksPerSM = 16;
+constexpr int kPruneBlocksPerSM = 16;
 
 void workspace_free(mpap_workspace* ws);
+void profile_add(const char* name, uint64_t launches, double ms);
+bool profile_enabled();
+void launch_count_add(uint64_t n);
 
 // Signed 64-bit atomic add through the unsigned overload (two's complement).
 __device__ __forceinline__ void atomic_add_i64(long long* p, long long v) {
@@ -132,6 +159,36 @@ __device__ __forceinline__ void atomic_add_i64(long long* p, long long v) {
 
 __device__ __forceinline__ size_t slab(const WS& w, uint32_t b, uint32_t g) {
   return ((size_t)b * w.NV + g) * w.fcap;
+}
+
+__device__ __forceinline__ unsigned long long global_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void ktime_begin(const WS& w, int k) {
+  if (w.ctl->prof && threadIdx.x == 0) atomicMin(&w.ctl->kt[k].start, global_timer());
+}
+
+// Every warp reports completion; the last one closes the launch (no block
+// barrier, so early-finishing warps leave the SM immediately).
+__device__ __forceinline__ void ktime_end(const WS& w, int k) {
+  if (w.ctl->prof && (threadIdx.x & 31) == 0) {
+    KTime& t = w.ctl->kt[k];
+    __threadfence();
+    const uint32_t total = gridDim.x * gridDim.y * ((blockDim.x + 31) >> 5);
+    const uint32_t done = atomicAdd(&t.blocks, 1u);
+    if (done == total - 1) {
+      const unsigned long long now = global_timer();
+      const unsigned long long s = atomicAdd(&t.start, 0ull);
+      t.total_ns += now - s;
+      t.launches += 1;
+      t.start = ULLONG_MAX;
+      t.blocks = 0;
+      __threadfence();
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -144,16 +201,27 @@ __global__ void k_fill_qid(WS w, uint32_t nq) {
   }
 }
 
-__global__ void k_init(WS w, uint32_t nq) {
+__global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
   const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q == 0) {
-    w.ctl->oh_n[0] = nq;
-    w.ctl->oh_n[1] = 0;
-    w.ctl->t_n = 0;
-    w.ctl->g_n = 0;
-    w.ctl->arena_n = nq;
-    w.ctl->err = 0;
-    w.ctl->n_done = 0;
+    Ctl& c = *w.ctl;
+    c.oh_n[0] = nq;
+    c.oh_n[1] = 0;
+    c.t_n = 0;
+    c.g_n = 0;
+    c.arena_n = nq;
+    c.err = 0;
+    c.n_done = 0;
+    c.it = 0;
+    c.nq = nq;
+    c.iter_cap = iter_cap;
+    c.prof = prof;
+    for (int k = 0; k < 3; ++k) {
+      c.kt[k].start = ULLONG_MAX;
+      c.kt[k].total_ns = 0;
+      c.kt[k].blocks = 0;
+      c.kt[k].launches = 0;
+    }
   }
   if (q >= nq) return;
   const uint32_t g = w.qd[q].base;   // x_init is node 0 of every roadmap
@@ -183,10 +251,12 @@ __global__ void k_init(WS w, uint32_t nq) {
 // ---------------------------------------------------------------------------
 // select: group formation, closing, goal test and marking (warp per node).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w, uint32_t it) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
+  ktime_begin(w, 0);
+  const uint32_t it = w.ctl->it;
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
-  const uint32_t n_list = w.ctl->oh_n[it & 1];
+  const uint32_t n_list = (w.ctl->n_done < w.ctl->nq) ? w.ctl->oh_n[it & 1] : 0u;
   const uint32_t* list = w.oh_list + (size_t)(it & 1) * w.NV;
   uint32_t* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -242,13 +312,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w, uint32_t i
           r0 += __popc(bal);
         }
         if (lane == 0) {
-          w.g_off[g] = off;
-          w.g_cnt[g] = cnt;
-          w.act_stamp[g] = it;
+          w.gdesc[g] = make_uint4(it, cnt, off, 0u);
           atomic_add_i64(&w.qs[q].open_cnt, -(long long)cnt);
           if (Q.is_goal[g - Q.base]) w.qs[q].goal_hit = 1u;
         }
-        // mark the out-neighbours of this node as touched (deduplicated by stamp)
+        // mark the out-neighbours of this node as touched (deduplicated by stamp;
+        // a plain read first skips the atomic for nodes already marked)
         const uint32_t u = g - Q.base;
         const uint32_t e_end = Q.fwd_ptr[u + 1];
         for (uint32_t e0 = Q.fwd_ptr[u]; e0 < e_end; e0 += 32) {
@@ -256,8 +325,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w, uint32_t i
           bool first = false;
           uint32_t gx = 0;
           if (e < e_end) {
-            gx = Q.base + (uint32_t)__ldg(&Q.fwd_edge[e].x);
-            first = atomicExch(&w.touch_stamp[gx], it) != it;
+            gx = Q.base + __ldg(&Q.fwd_dst[e]);
+            if (w.touch_stamp[gx] != it) first = atomicExch(&w.touch_stamp[gx], it) != it;
           }
           const unsigned bal = __ballot_sync(kFull, first);
           if (bal) {
@@ -273,17 +342,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w, uint32_t i
       if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = g;
     }
   }
+  ktime_end(w, 0);
 }
 
 // ---------------------------------------------------------------------------
 // prune: pull candidates into the front of each touched node (warp per node).
 // ---------------------------------------------------------------------------
 struct WarpSmem {
-  long long s_cost[32];
+  long long s_cost[32];    // chunk survivors, sorted
   long long s_h[32];
   uint32_t s_tb[32];
   uint32_t s_pp[32];
   uint32_t bins[33];
+  long long st_cost[64];   // merged register front staging
+  long long st_h[64];
+  uint32_t st_pid[64];
+  uint32_t st_aux[64];
 };
 
 __device__ __forceinline__ bool key_less(long long c1, long long h1, uint32_t t1, long long c2,
@@ -293,18 +367,73 @@ __device__ __forceinline__ bool key_less(long long c1, long long h1, uint32_t t1
   return t1 < t2;
 }
 
+// Front of one node during the merge: in registers (lane j holds entry j, n <= 32)
+// or in slab buffer b.
 struct FrontCursor {
-  uint32_t b;        // live buffer
+  bool reg;
+  uint32_t b;        // live slab buffer
   uint32_t n;        // live count
   uint32_t removed_open;
   bool any_new;
+  long long rc, rh;  // register entry of this lane (reg mode)
+  uint32_t rp, ra;
 };
 
-// Merge up to 32 candidates (one per lane, `ok` marks the real ones) into the
-// live front of node g.  Candidate tie key tb = 1 + parent head (old plans have
-// tie key 0, i.e. they win exact (cost, h) ties).
-__device__ void merge_chunk(const WS& w, uint32_t g, FrontCursor& fc, WarpSmem& sm, bool ok,
-                            long long cc, long long ch, uint32_t ctb, uint32_t cpp) {
+// Sort the chunk (one candidate per lane; padding lanes last) by (cost, h, tb)
+// and keep its skyline: survivors are written to sm.s_* in order; returns their
+// count.
+__device__ __forceinline__ uint32_t chunk_skyline(WarpSmem& sm, bool ok, long long cc, long long ch,
+                                                  uint32_t ctb, uint32_t cpp) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  long long kc = ok ? cc : LLONG_MAX, kh = ok ? ch : LLONG_MAX;
+  uint32_t kt = ok ? ctb : 0xFFFFFFFFu, kp = cpp;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const long long oc = shfl_xor_i64(kc, j), oh = shfl_xor_i64(kh, j);
+      const uint32_t ot = __shfl_xor_sync(kFull, kt, j), op = __shfl_xor_sync(kFull, kp, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool o_less = key_less(oc, oh, ot, kc, kh, kt);
+      const bool m_less = key_less(kc, kh, kt, oc, oh, ot);
+      const bool take = (lower == up) ? o_less : m_less;
+      if (take) {
+        kc = oc;
+        kh = oh;
+        kt = ot;
+        kp = op;
+      }
+    }
+  }
+  // exclusive prefix minimum of h in sorted order
+  long long pm = kh;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = shfl_up_i64(pm, o);
+    if (lane >= (unsigned)o) pm = t < pm ? t : pm;
+  }
+  long long excl = shfl_up_i64(pm, 1);
+  if (lane == 0) excl = LLONG_MAX;
+  const bool surv = (kt != 0xFFFFFFFFu) && kh < excl;
+  const unsigned sb = __ballot_sync(kFull, surv);
+  if (surv) {
+    const uint32_t r = __popc(sb & lt);
+    sm.s_cost[r] = kc;
+    sm.s_h[r] = kh;
+    sm.s_tb[r] = kt;
+    sm.s_pp[r] = kp;
+  }
+  __syncwarp();
+  return __popc(sb);
+}
+
+// Slab-mode merge of up to 32 candidates into the live front of node g.
+// Candidate tie key tb = 1 + parent head (old plans have tie key 0, i.e. they win
+// exact (cost, h) ties).
+__device__ void merge_chunk_slab(const WS& w, uint32_t g, FrontCursor& fc, WarpSmem& sm, bool ok,
+                                 long long cc, long long ch, uint32_t ctb, uint32_t cpp) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   // 1. drop candidates dominated by the live front (last entry with cost <= cc)
@@ -326,44 +455,8 @@ __device__ void merge_chunk(const WS& w, uint32_t g, FrontCursor& fc, WarpSmem& 
     }
   }
   if (!__any_sync(kFull, ok)) return;
-  // 2. warp bitonic sort by (cost, h, tb); padding lanes sort last
-  long long kc = ok ? cc : LLONG_MAX, kh = ok ? ch : LLONG_MAX;
-  uint32_t kt = ok ? ctb : 0xFFFFFFFFu, kp = cpp;
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const long long oc = shfl_xor_i64(kc, j), oh = shfl_xor_i64(kh, j);
-      const uint32_t ot = __shfl_xor_sync(kFull, kt, j), op = __shfl_xor_sync(kFull, kp, j);
-      const bool up = (lane & k) == 0;
-      const bool lower = (lane & j) == 0;
-      const bool o_less = key_less(oc, oh, ot, kc, kh, kt);
-      const bool m_less = key_less(kc, kh, kt, oc, oh, ot);
-      const bool take = (lower == up) ? o_less : m_less;
-      if (take) {
-        kc = oc; kh = oh; kt = ot; kp = op;
-      }
-    }
-  }
-  // exclusive prefix minimum of h in sorted order -> skyline of the chunk
-  long long pm = kh;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const long long t = shfl_up_i64(pm, o);
-    if (lane >= (unsigned)o) pm = t < pm ? t : pm;
-  }
-  long long excl = shfl_up_i64(pm, 1);
-  if (lane == 0) excl = LLONG_MAX;
-  const bool surv = (kt != 0xFFFFFFFFu) && kh < excl;
-  const unsigned sb = __ballot_sync(kFull, surv);
-  const uint32_t m = __popc(sb);
-  if (surv) {
-    const uint32_t r = __popc(sb & lt);
-    sm.s_cost[r] = kc;
-    sm.s_h[r] = kh;
-    sm.s_tb[r] = kt;
-    sm.s_pp[r] = kp;
-  }
+  // 2. skyline of the chunk
+  const uint32_t m = chunk_skyline(sm, ok, cc, ch, ctb, cpp);
   sm.bins[lane] = 0;
   if (lane == 0) sm.bins[32] = 0;
   __syncwarp();
@@ -440,12 +533,102 @@ __device__ void merge_chunk(const WS& w, uint32_t g, FrontCursor& fc, WarpSmem& 
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prune(WS w, uint32_t it) {
-  __shared__ WarpSmem smem[kWarpsPerBlock];
-  WarpSmem& sm = smem[threadIdx.x >> 5];
+// Register-mode merge: the front (n <= 32) is held one entry per lane; all
+// dominance tests are broadcasts over lanes.  If the merged front exceeds 32
+// entries it is written to the other slab buffer and the node continues in slab
+// mode.
+__device__ void merge_chunk_reg(const WS& w, uint32_t g, FrontCursor& fc, WarpSmem& sm, bool ok,
+                                long long cc, long long ch, uint32_t ctb, uint32_t cpp) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
-  const uint32_t n_list = w.ctl->t_n;
+  const uint32_t n = fc.n;
+  const uint32_t rtb = (fc.rp & kNew) ? fc.ra : 0u;
+  // 1. candidates dominated by any front entry
+  if (__any_sync(kFull, ok)) {
+    for (uint32_t j = 0; j < n; ++j) {
+      const long long fcj = shfl_i64(fc.rc, (int)j), fhj = shfl_i64(fc.rh, (int)j);
+      const uint32_t ftj = __shfl_sync(kFull, rtb, (int)j);
+      if (ok && fcj <= cc && fhj <= ch && (fcj < cc || fhj < ch || ftj < ctb)) ok = false;
+    }
+  }
+  if (!__any_sync(kFull, ok)) return;
+  // 2. skyline of the chunk
+  const uint32_t m = chunk_skyline(sm, ok, cc, ch, ctb, cpp);
+  // 3. front entries dominated by a survivor; ranks of the merged order
+  const bool valid = lane < n;
+  bool dom = false;
+  uint32_t below = 0;   // survivors with smaller cost
+  for (uint32_t s = 0; s < m; ++s) {
+    const long long scost = sm.s_cost[s], sh = sm.s_h[s];
+    if (valid && scost <= fc.rc && sh <= fc.rh && (scost < fc.rc || sh < fc.rh || sm.s_tb[s] < rtb)) dom = true;
+    below += (scost < fc.rc) ? 1u : 0u;
+  }
+  const bool keep = valid && !dom;
+  const unsigned kb = __ballot_sync(kFull, keep);
+  const uint32_t kept = __popc(kb);
+  const uint32_t rem_open = __popc(__ballot_sync(kFull, dom && valid && (fc.rp & kOpen) && !(fc.rp & kNew)));
+  if (keep) {
+    const uint32_t pos = __popc(kb & lt) + below;
+    sm.st_cost[pos] = fc.rc;
+    sm.st_h[pos] = fc.rh;
+    sm.st_pid[pos] = fc.rp;
+    sm.st_aux[pos] = fc.ra;
+  }
+  // survivor lane s: kept front entries with smaller cost come first
+  uint32_t before = 0;
+  const long long my_scost = lane < m ? sm.s_cost[lane] : 0;
+  for (uint32_t j = 0; j < n; ++j) {
+    const long long fcj = shfl_i64(fc.rc, (int)j);
+    const bool kj = (kb >> j) & 1u;
+    before += (kj && fcj < my_scost) ? 1u : 0u;
+  }
+  if (lane < m) {
+    const uint32_t pos = lane + before;
+    sm.st_cost[pos] = sm.s_cost[lane];
+    sm.st_h[pos] = sm.s_h[lane];
+    sm.st_pid[pos] = sm.s_pp[lane] | kNew;
+    sm.st_aux[pos] = sm.s_tb[lane];
+  }
+  __syncwarp();
+  const uint32_t n_new = kept + m;
+  fc.removed_open += rem_open;
+  fc.any_new = true;
+  if (n_new > w.fcap && lane == 0) atomicOr(&w.ctl->err, kErrFront);
+  if (n_new <= 32) {
+    const uint32_t lim = n_new < w.fcap ? n_new : w.fcap;
+    if (lane < lim) {
+      fc.rc = sm.st_cost[lane];
+      fc.rh = sm.st_h[lane];
+      fc.rp = sm.st_pid[lane];
+      fc.ra = sm.st_aux[lane];
+    }
+    fc.n = lim;
+  } else {
+    // spill to the other slab buffer and continue in slab mode
+    const uint32_t nb = fc.b ^ 1u;
+    const size_t on = slab(w, nb, g);
+    const uint32_t lim = n_new < w.fcap ? n_new : w.fcap;
+    for (uint32_t i = lane; i < lim; i += 32) {
+      w.f_cost[on + i] = sm.st_cost[i];
+      w.f_h[on + i] = sm.st_h[i];
+      w.f_pid[on + i] = sm.st_pid[i];
+      w.f_aux[on + i] = sm.st_aux[i];
+    }
+    fc.reg = false;
+    fc.b = nb;
+    fc.n = lim;
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_prune(WS w) {
+  ktime_begin(w, 1);
+  __shared__ WarpSmem smem[kWarpsPerBlock];
+  WarpSmem& sm = smem[threadIdx.x >> 5];
+  const uint32_t it = w.ctl->it;
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t n_list = (w.ctl->n_done < w.ctl->nq) ? w.ctl->t_n : 0u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   uint32_t* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
   for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
@@ -463,6 +646,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prune(WS w, uint32_t it
     fc.n = w.f_cnt[(size_t)fc.b * w.NV + g];
     fc.removed_open = 0;
     fc.any_new = false;
+    fc.reg = fc.n <= 32;
+    fc.rc = fc.rh = 0;
+    fc.rp = fc.ra = 0;
+    if (fc.reg && lane < fc.n) {
+      const size_t o = slab(w, fc.b, g);
+      fc.rc = w.f_cost[o + lane];
+      fc.rh = w.f_h[o + lane];
+      fc.rp = w.f_pid[o + lane];
+      fc.ra = w.f_aux[o + lane];
+    }
+    const uint32_t b0 = fc.b;
     unsigned long long exps = 0;
     const uint32_t e_end = Q.rev_ptr[x + 1];
     for (uint32_t e0 = Q.rev_ptr[x]; e0 < e_end; e0 += 32) {
@@ -471,10 +665,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prune(WS w, uint32_t it
       uint32_t cnt = 0, goff = 0;
       if (e < e_end) {
         ed = __ldg(&Q.rev_edge[e]);
-        const uint32_t gu = Q.base + (uint32_t)ed.x;
-        if (w.act_stamp[gu] == it) {
-          cnt = w.g_cnt[gu];
-          goff = w.g_off[gu];
+        const uint4 gd = w.gdesc[Q.base + (uint32_t)ed.x];
+        if (gd.x == it) {
+          cnt = gd.y;
+          goff = gd.z;
         }
       }
       const uint32_t incl = warp_incl_scan(cnt);
@@ -508,38 +702,71 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prune(WS w, uint32_t it
           pp = w.g_pid[gi];
           ok = ch <= Q.beta;          // perception-heuristic cutoff
         }
-        merge_chunk(w, g, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
+        if (fc.reg) merge_chunk_reg(w, g, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
+        else merge_chunk_slab(w, g, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
       }
     }
     if (fc.any_new) {
       // give every new front entry an arena record and mark it open
-      const size_t o = slab(w, fc.b, g);
       uint32_t n_new = 0;
-      for (uint32_t j0 = 0; j0 < fc.n; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        uint32_t pid = 0;
-        if (j < fc.n) pid = w.f_pid[o + j];
-        const bool isnew = (j < fc.n) && (pid & kNew);
+      if (fc.reg) {
+        const bool isnew = lane < fc.n && (fc.rp & kNew);
         const unsigned bal = __ballot_sync(kFull, isnew);
-        if (!bal) continue;
         unsigned long long a0 = 0;
-        if (lane == 0) a0 = atomicAdd(&w.ctl->arena_n, (unsigned long long)__popc(bal));
+        if (lane == 0 && bal) a0 = atomicAdd(&w.ctl->arena_n, (unsigned long long)__popc(bal));
         a0 = __shfl_sync(kFull, a0, 0);
         if (isnew) {
           const unsigned long long a = a0 + __popc(bal & lt);
           if (a < w.acap) {
             w.a_head[a] = x;
-            w.a_parent[a] = pid & kPidMask;
+            w.a_parent[a] = fc.rp & kPidMask;
             w.a_iter[a] = it + 1;
-            w.a_cost[a] = w.f_cost[o + j];
-            w.f_pid[o + j] = (uint32_t)a | kOpen;
+            w.a_cost[a] = fc.rc;
+            fc.rp = (uint32_t)a | kOpen;
           } else {
             atomicOr(&w.ctl->err, kErrArena);
-            w.f_pid[o + j] = kOpen;
+            fc.rp = kOpen;
           }
-          w.f_aux[o + j] = 0;
+          fc.ra = 0;
         }
-        n_new += __popc(bal);
+        n_new = __popc(bal);
+        // write the register front back in place
+        const size_t o = slab(w, b0, g);
+        if (lane < fc.n) {
+          w.f_cost[o + lane] = fc.rc;
+          w.f_h[o + lane] = fc.rh;
+          w.f_pid[o + lane] = fc.rp;
+          w.f_aux[o + lane] = fc.ra;
+        }
+        fc.b = b0;
+      } else {
+        const size_t o = slab(w, fc.b, g);
+        for (uint32_t j0 = 0; j0 < fc.n; j0 += 32) {
+          const uint32_t j = j0 + lane;
+          uint32_t pid = 0;
+          if (j < fc.n) pid = w.f_pid[o + j];
+          const bool isnew = (j < fc.n) && (pid & kNew);
+          const unsigned bal = __ballot_sync(kFull, isnew);
+          if (!bal) continue;
+          unsigned long long a0 = 0;
+          if (lane == 0) a0 = atomicAdd(&w.ctl->arena_n, (unsigned long long)__popc(bal));
+          a0 = __shfl_sync(kFull, a0, 0);
+          if (isnew) {
+            const unsigned long long a = a0 + __popc(bal & lt);
+            if (a < w.acap) {
+              w.a_head[a] = x;
+              w.a_parent[a] = pid & kPidMask;
+              w.a_iter[a] = it + 1;
+              w.a_cost[a] = w.f_cost[o + j];
+              w.f_pid[o + j] = (uint32_t)a | kOpen;
+            } else {
+              atomicOr(&w.ctl->err, kErrArena);
+              w.f_pid[o + j] = kOpen;
+            }
+            w.f_aux[o + j] = 0;
+          }
+          n_new += __popc(bal);
+        }
       }
       if (lane == 0) {
         w.cur[g] = (uint8_t)fc.b;
@@ -551,38 +778,49 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prune(WS w, uint32_t it
     }
     if (lane == 0 && exps) atomicAdd(&w.qs[q].expansions, exps);
   }
+  ktime_end(w, 1);
 }
 
 // ---------------------------------------------------------------------------
-// end of wavefront: termination per query (thread per query).
+// end of wavefront (one block): termination per query, list swap, loop control.
 // ---------------------------------------------------------------------------
-__global__ void k_end(WS w, uint32_t it, uint32_t nq) {
-  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nq) {
+__global__ void __launch_bounds__(1024) k_end(WS w, cudaGraphConditionalHandle cond, uint32_t in_graph) {
+  ktime_begin(w, 2);
+  __shared__ uint32_t s_newly;
+  const uint32_t it = w.ctl->it, nq = w.ctl->nq;
+  const uint32_t err = w.ctl->err;
+  if (threadIdx.x == 0) s_newly = 0;
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
     QueryState& s = w.qs[q];
     const QueryDev& Q = w.qd[q];
-    if (!s.done) {
-      if (w.ctl->err) {
-        s.done = 1;
-        s.status = MPAP_ERR_CAPACITY;
-      } else if (s.goal_hit && !(Q.flags & MPAP_QUERY_NO_GOAL_STOP)) {
-        s.done = 1;
-      } else if (s.wavefronts >= Q.max_iters) {
-        s.done = 1;
-        s.status = MPAP_ERR_ITER_LIMIT;
-      } else {
-        s.wavefronts += 1;
-        if (s.open_cnt == 0) s.done = 1;
-      }
-      if (s.done) atomicAdd(&w.ctl->n_done, 1u);
+    if (s.done) continue;
+    if (err) {
+      s.done = 1;
+      s.status = MPAP_ERR_CAPACITY;
+    } else if (s.goal_hit && !(Q.flags & MPAP_QUERY_NO_GOAL_STOP)) {
+      s.done = 1;
+    } else if (s.wavefronts >= Q.max_iters) {
+      s.done = 1;
+      s.status = MPAP_ERR_ITER_LIMIT;
+    } else {
+      s.wavefronts += 1;
+      if (s.open_cnt == 0) s.done = 1;
     }
+    if (s.done) atomicAdd(&s_newly, 1u);
   }
-  if (q == 0) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t done = w.ctl->n_done + s_newly;
+    w.ctl->n_done = done;
     // the list consumed in this iteration becomes the append target of the next
     w.ctl->oh_n[it & 1] = 0;
     w.ctl->t_n = 0;
     w.ctl->g_n = 0;
+    w.ctl->it = it + 1;
+    if (in_graph) cudaGraphSetConditional(cond, (done < nq && it + 1 < w.ctl->iter_cap) ? 1u : 0u);
   }
+  ktime_end(w, 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -645,11 +883,11 @@ __global__ void k_finalize(WS w, uint32_t nq) {
   }
   if (threadIdx.x == 0) {
     ResultDev r;
-    r.status = s.status;
+    r.status = s.done ? s.status : MPAP_ERR_ITER_LIMIT;
     r.cost = 0;
     r.h = 0;
     r.path_len = 0;
-    if (s.status == 0) {
+    if (r.status == 0) {
       const Best b = sb[0];
       if (b.ref == kNone) {
         r.status = MPAP_NO_SOLUTION;
@@ -701,7 +939,43 @@ bool walloc(T** p, size_t n) {
   return cuda_ok(cudaMalloc((void**)p, (n ? n : 1) * sizeof(T)), "cudaMalloc(workspace)");
 }
 
+// Builds the device-side wavefront loop: a graph whose conditional WHILE node
+// runs {select, prune, end} until `end` clears the condition.
+int32_t build_loop_graph(mpap_workspace* ws) {
+  if (ws->exec) return MPAP_OK;
+  MPAP_CK(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
+  MPAP_CK(cudaGraphCreate(&ws->graph, 0));
+  cudaGraphConditionalHandle cond;
+  MPAP_CK(cudaGraphConditionalHandleCreate(&cond, ws->graph, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  MPAP_CK(cudaGraphAddNode(&node, ws->graph, nullptr, nullptr, 0, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  MPAP_CK(cudaStreamBeginCaptureToGraph(ws->cap_stream, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  const int n = sms();
+  k_select<<<kSelectBlocksPerSM * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
+  k_prune<<<kPruneBlocksPerSM * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
+  k_end<<<1, 1024, 0, ws->cap_stream>>>(ws->w, cond, 1u);
+  cudaGraph_t captured = nullptr;
+  MPAP_CK(cudaStreamEndCapture(ws->cap_stream, &captured));
+  MPAP_CK(cudaGraphInstantiate(&ws->exec, ws->graph, 0));
+  return MPAP_OK;
+}
+
 }  // namespace
+
+bool host_stepped_loop() {
+  static const bool host = [] {
+    const char* e = getenv("MPAP_SEARCH_LOOP");
+    return e && std::strcmp(e, "host") == 0;
+  }();
+  return host;
+}
 
 int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans, uint32_t max_q,
                          mpap_workspace** out) {
@@ -721,8 +995,8 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
   const size_t slots = 2 * (size_t)w.NV * w.fcap;
   bool ok = walloc(&w.f_cost, slots) && walloc(&w.f_h, slots) && walloc(&w.f_pid, slots) &&
             walloc(&w.f_aux, slots) && walloc(&w.f_cnt, 2 * w.NV) && walloc(&w.cur, w.NV) &&
-            walloc(&w.qid, w.NV) && walloc(&w.act_stamp, w.NV) && walloc(&w.touch_stamp, w.NV) &&
-            walloc(&w.oh_stamp, w.NV) && walloc(&w.g_off, w.NV) && walloc(&w.g_cnt, w.NV) &&
+            walloc(&w.qid, w.NV) && walloc(&w.gdesc, w.NV) && walloc(&w.touch_stamp, w.NV) &&
+            walloc(&w.oh_stamp, w.NV) &&
             walloc(&w.g_cost, w.gcap) && walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) &&
             walloc(&w.oh_list, 2 * w.NV) && walloc(&w.t_list, w.NV) && walloc(&w.a_head, w.acap) &&
             walloc(&w.a_parent, w.acap) && walloc(&w.a_iter, w.acap) && walloc(&w.a_cost, w.acap) &&
@@ -738,9 +1012,12 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
 
 void workspace_free(mpap_workspace* ws) {
   if (!ws) return;
+  if (ws->exec) cudaGraphExecDestroy(ws->exec);
+  if (ws->graph) cudaGraphDestroy(ws->graph);
+  if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
   WS& w = ws->w;
-  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.f_cnt, w.cur, w.qid, w.act_stamp, w.touch_stamp,
-                  w.oh_stamp, w.g_off, w.g_cnt, w.g_cost, w.g_h, w.g_pid, w.oh_list, w.t_list,
+  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.f_cnt, w.cur, w.qid, w.gdesc, w.touch_stamp,
+                  w.oh_stamp, w.g_cost, w.g_h, w.g_pid, w.oh_list, w.t_list,
                   w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl, w.qd, w.qs, w.res, w.path};
   for (void* p : ptrs) cudaFree(p);
   delete ws;
@@ -763,16 +1040,17 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
       set_error("search: null or empty roadmap %u", i);
       return MPAP_ERR_INVALID_ARG;
     }
-    if ((qs[i].group_width_q <= 0 && (!(qs[i].lambda > 0.0f) || !(qs[i].lambda <= 1.0f))) ||
-        qs[i].beta < 0 || qs[i].max_iters == 0) {
-      set_error("search: query %u needs lambda in (0, 1] (or group_width_q > 0), beta >= 0, max_iters > 0", i);
+    if ((qs[i].group_width_q <= 0 && (!(qs[i].lambda > 0.0f) || !(qs[i].lambda <= 1.0f))) || qs[i].beta < 0 ||
+        qs[i].max_iters == 0 || qs[i].max_iters > 0x7FFFFFF0u) {
+      set_error("search: query %u needs lambda in (0, 1] (or group_width_q > 0), beta >= 0, 0 < max_iters < 2^31",
+                i);
       return MPAP_ERR_INVALID_ARG;
     }
     QueryDev d{};
     d.rev_ptr = rm->rev_ptr;
     d.rev_edge = rm->rev_edge;
     d.fwd_ptr = rm->fwd_ptr;
-    d.fwd_edge = rm->fwd_edge;
+    d.fwd_dst = rm->fwd_dst;
     d.is_goal = rm->is_goal;
     d.goal_list = rm->goal_list;
     d.n_goal = rm->n_goal;
@@ -795,6 +1073,8 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
               (unsigned long long)w.NV);
     return MPAP_ERR_INVALID_ARG;
   }
+  int32_t rc = build_loop_graph(ws);
+  if (rc) return rc;
   ws->last_V.resize(nq);
   ws->last_base.resize(nq);
   for (uint32_t i = 0; i < nq; ++i) {
@@ -802,64 +1082,63 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     ws->last_base[i] = qd[i].base;
   }
   const size_t NVu = (size_t)total;
+  const bool prof = profile_enabled();
   MPAP_CK(cudaMemcpyAsync(w.qd, qd.data(), sizeof(QueryDev) * nq, cudaMemcpyHostToDevice, st));
   MPAP_CK(cudaMemsetAsync(w.f_cnt, 0, sizeof(uint32_t) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.f_cnt + w.NV, 0, sizeof(uint32_t) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.cur, 0, NVu, st));
-  MPAP_CK(cudaMemsetAsync(w.act_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
+  MPAP_CK(cudaMemsetAsync(w.gdesc, 0xFF, sizeof(uint4) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.touch_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.oh_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
-  dim3 fg((unsigned)std::min<uint64_t>((total / nq + 255) / 256 + 1, 64), std::min(nq, 1024u));
   {
-    ::mpap::LaunchScope ls_(st, "k_fill_qid");
+    dim3 fg((unsigned)std::min<uint64_t>((total / nq + 255) / 256 + 1, 64), std::min(nq, 1024u));
+    LaunchScope ls(st, "k_fill_qid");
     k_fill_qid<<<fg, 256, 0, st>>>(w, nq);
   }
   {
-    ::mpap::LaunchScope ls_(st, "k_init");
-    k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq);
+    LaunchScope ls(st, "k_init");
+    k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq, max_iters + 2u, prof ? 1u : 0u);
   }
   MPAP_CK(cudaGetLastError());
-
-  const int blocks_sel = 16 * sms();
-  const int blocks_pr = 16 * sms();
-  uint32_t it = 0;
-  const uint32_t check_every = 2;
-  Ctl hc{};
-  while (true) {
-    for (uint32_t r = 0; r < check_every; ++r, ++it) {
-      {
-        ::mpap::LaunchScope ls_(st, "k_select");
-        k_select<<<blocks_sel, kWarpsPerBlock * 32, 0, st>>>(w, it);
+  if (!host_stepped_loop()) {
+    // the whole wavefront loop: one graph launch
+    MPAP_CK(cudaGraphLaunch(ws->exec, st));
+  } else {
+    // Host-stepped form of the same loop (MPAP_SEARCH_LOOP=host): identical
+    // kernels launched one wavefront at a time, for per-kernel profilers that do
+    // not see inside conditional graph nodes.
+    const int n = sms();
+    Ctl probe;
+    for (uint32_t it = 0;; it += 2) {
+      for (int r = 0; r < 2; ++r) {
+        k_select<<<kSelectBlocksPerSM * n, kWarpsPerBlock * 32, 0, st>>>(w);
+        k_prune<<<kPruneBlocksPerSM * n, kWarpsPerBlock * 32, 0, st>>>(w);
+        k_end<<<1, 1024, 0, st>>>(w, 0ull, 0u);
       }
-      {
-        ::mpap::LaunchScope ls_(st, "k_prune");
-        k_prune<<<blocks_pr, kWarpsPerBlock * 32, 0, st>>>(w, it);
-      }
-      {
-        ::mpap::LaunchScope ls_(st, "k_end");
-        k_end<<<(nq + 127) / 128, 128, 0, st>>>(w, it, nq);
-      }
-    }
-    MPAP_CK(cudaGetLastError());
-    MPAP_CK(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    MPAP_CK(cudaStreamSynchronize(st));
-    if (hc.n_done >= nq) break;
-    if ((uint64_t)it > (uint64_t)max_iters + 4) {
-      set_error("search: wavefront loop did not terminate");
-      return MPAP_ERR_ITER_LIMIT;
+      MPAP_CK(cudaGetLastError());
+      MPAP_CK(cudaMemcpyAsync(&probe, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      MPAP_CK(cudaStreamSynchronize(st));
+      if (probe.n_done >= nq || probe.it >= max_iters + 2u) break;
     }
   }
   {
-    ::mpap::LaunchScope ls_(st, "k_finalize");
+    LaunchScope ls(st, "k_finalize");
     k_finalize<<<nq, 256, 0, st>>>(w, nq);
   }
   MPAP_CK(cudaGetLastError());
   std::vector<ResultDev> res(nq);
   std::vector<QueryState> qsh(nq);
+  Ctl hc;
   MPAP_CK(cudaMemcpyAsync(res.data(), w.res, sizeof(ResultDev) * nq, cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaMemcpyAsync(qsh.data(), w.qs, sizeof(QueryState) * nq, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaStreamSynchronize(st));
-  int32_t rc = MPAP_OK;
+  launch_count_add(3ull * hc.it);
+  if (prof) {
+    const char* names[3] = {"k_select", "k_prune", "k_end"};
+    for (int k = 0; k < 3; ++k) profile_add(names[k], hc.kt[k].launches, (double)hc.kt[k].total_ns * 1e-6);
+  }
+  rc = MPAP_OK;
   for (uint32_t i = 0; i < nq; ++i) {
     mpap_result& o = outs[i];
     o.status = res[i].status;
@@ -883,6 +1162,9 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   if (hc.err) {
     set_error("search: device capacity exceeded (flags 0x%x: 1 front, 2 arena, 4 group)", hc.err);
     rc = MPAP_ERR_CAPACITY;
+  } else if (hc.n_done < nq) {
+    set_error("search: wavefront loop stopped at its iteration bound");
+    rc = MPAP_ERR_ITER_LIMIT;
   }
   return rc;
 }

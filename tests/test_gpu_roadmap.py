@@ -21,6 +21,8 @@ def mp():
     ("2d", 1, 1000, None), ("2d", 2, 1000, None), ("2d", 3, 257, 0.2),
     ("3d", 1, 2000, None), ("3d", 4, 777, 0.2),
     ("6d", 1, 2000, None), ("6d", 5, 1500, 20.0),
+    ("2d", 6, 2000, 0.2),    # mean degree ~250: rows overflow the 128-edge scratch rows
+    ("3d", 8, 3000, 0.3),
 ])
 def test_roadmap_matches_oracle(mp, orc, name, seed, n, r):
     sc = scenegen.make_scene(name, seed, query_id=seed)
