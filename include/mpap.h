@@ -254,6 +254,25 @@ int32_t mpap_certify_batch(mpap_roadmap* const* rms, const uint32_t* const* path
                            const uint32_t* path_lens, const mpap_mc_params* mcs, uint32_t n,
                            mpap_cert* outs, void* stream);
 
+/* mpap_certify without any device allocation (the paper has no counterpart;
+ * this serves deployment).  For callers that must not allocate device memory
+ * while running -- a planner inside a robot's real-time control loop, where an
+ * allocation can block or fragment a fixed memory budget, or a program whose
+ * device memory is all held by another framework's allocator.  The scratch the
+ * certification kernels need lives in one fixed device array inside the library
+ * (about 1.1 MB, held on every GPU that loads the library until the process
+ * exits); the caller passes the inputs (a built roadmap, the host plan and
+ * tables) and the output struct as for mpap_certify, and gets identical counts.
+ * Limits: path_len <= 4096 nodes, (path_len - 1) * M <= 65536 checkpoints,
+ * K + 1 <= 256 levels, at most 512 boxes; larger inputs return
+ * MPAP_ERR_INVALID_ARG with the reason in mpap_last_error().  The first call on a
+ * device looks up the array's device address (make it before any stream capture
+ * on that device).  Every call on a device shares the one array and clears the
+ * counters it needs, so calls that overlap on the GPU (other streams or threads)
+ * race: serialise them.  Calls no cudaMalloc, cudaFree or allocating routine. */
+int32_t mpap_certify_noalloc(const mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,
+                             const mpap_mc_params* mc, mpap_cert* out, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Launch accounting and kernel timing (tracing).  The paper reports per-phase
  * computation times (Table 2); these entry points expose the same information

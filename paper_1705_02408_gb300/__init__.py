@@ -31,7 +31,7 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_build_roadmap_from_points", "mpap_roadmap_from_csr", "mpap_roadmap_info",
            "mpap_roadmap_export", "mpap_roadmap_stats", "mpap_roadmap_free", "mpap_workspace_create",
            "mpap_workspace_free", "mpap_search", "mpap_search_batch", "mpap_search_fronts",
-           "mpap_certify", "mpap_certify_batch", "mpap_profile_enable", "mpap_profile_reset",
+           "mpap_certify", "mpap_certify_batch", "mpap_certify_noalloc", "mpap_profile_enable", "mpap_profile_reset",
            "mpap_launch_count", "mpap_profile_read"]
 
 
@@ -118,6 +118,9 @@ def lib():
         L.mpap_certify.restype = i32
         L.mpap_certify.argtypes = [P, P, C.c_uint32, C.POINTER(mpap_mc_params),
                                    C.POINTER(mpap_cert), P]
+        L.mpap_certify_noalloc.restype = i32
+        L.mpap_certify_noalloc.argtypes = [P, P, C.c_uint32, C.POINTER(mpap_mc_params),
+                                           C.POINTER(mpap_cert), P]
         L.mpap_certify_batch.restype = i32
         L.mpap_certify_batch.argtypes = [C.POINTER(P), C.POINTER(P), P, C.POINTER(mpap_mc_params),
                                          C.c_uint32, C.POINTER(mpap_cert), P]
@@ -454,6 +457,18 @@ def certify(rm: Roadmap, path, rollouts, seed, call_id, delta_fx, sigma_fx, shif
     out = mpap_cert()
     _check(lib().mpap_certify(rm.h, path.ctypes.data_as(C.c_void_p), path.size, C.byref(p), C.byref(out),
                               _stream(stream)), "mpap_certify")
+    return dict(hits_loc=out.hits_loc, hits_coll=out.hits_coll, hits_any=out.hits_any, rollouts=out.rollouts)
+
+
+def certify_noalloc(rm: Roadmap, path, rollouts, seed, call_id, delta_fx, sigma_fx, shift, stream=None):
+    """mpap_certify_noalloc: the same rollouts as certify() with the kernels'
+    scratch in a fixed device array inside the library (no device allocation),
+    for callers that cannot allocate while running."""
+    p, keep = make_mc(rollouts, seed, call_id, delta_fx, sigma_fx, shift)
+    path = np.ascontiguousarray(path, np.uint32)
+    out = mpap_cert()
+    _check(lib().mpap_certify_noalloc(rm.h, path.ctypes.data_as(C.c_void_p), path.size, C.byref(p),
+                                      C.byref(out), _stream(stream)), "mpap_certify_noalloc")
     return dict(hits_loc=out.hits_loc, hits_coll=out.hits_coll, hits_any=out.hits_any, rollouts=out.rollouts)
 
 

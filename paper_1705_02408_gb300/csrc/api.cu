@@ -17,6 +17,8 @@ int32_t search_fronts_impl(mpap_workspace* ws, uint32_t index, uint32_t* front_p
                            int64_t* h, uint64_t cap, uint64_t* total, cudaStream_t st);
 int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,
                            const mpap_mc_params* mcs, uint32_t n, mpap_cert* outs, cudaStream_t st);
+int32_t certify_noalloc_impl(const mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,
+                             const mpap_mc_params* mc, mpap_cert* out, cudaStream_t st);
 }  // namespace mpap
 
 using mpap::set_error;
@@ -272,6 +274,15 @@ int32_t mpap_certify(mpap_roadmap* rm, const uint32_t* path, uint32_t path_len, 
     return MPAP_ERR_INVALID_ARG;
   }
   return mpap::certify_batch_impl(&rm, &path, &path_len, mc, 1, out, S(stream));
+}
+
+int32_t mpap_certify_noalloc(const mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,
+                             const mpap_mc_params* mc, mpap_cert* out, void* stream) {
+  if (!rm || !mc || !out || (path_len && !path) || !mc->sigma_fx || !mc->shift) {
+    set_error("null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::certify_noalloc_impl(rm, path, path_len, mc, out, S(stream));
 }
 
 int32_t mpap_certify_batch(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,

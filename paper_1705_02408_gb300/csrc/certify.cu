@@ -11,6 +11,8 @@
 //                     checkpoints (relocalisation contraction, Irwin-Hall(12)
 //                     noise from Philox4x32-10), counting localisation and
 //                     collision/leave-map failures.
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -254,6 +256,145 @@ int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* path
     outs[i].hits_any = hh[3 * i + 2];
     outs[i].rollouts = mcs[i].rollouts;
   }
+  return MPAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Certification without any device allocation.
+//
+// Some callers cannot allocate device memory once they are running: a planner
+// inside a robot's real-time control loop, where an allocation may block or
+// fragment a fixed memory budget, or a host program whose device memory is all
+// reserved by another framework's caching allocator.  For them the scratch that
+// the certification kernels need (the job descriptor, a copy of the plan, the
+// noise tables, the hit counters and the per-checkpoint nominal states) lives in
+// one file-scope device array of fixed size instead of a stream-ordered
+// allocation.  The array is part of the library image: every GPU that loads the
+// library holds it (kNoAllocBytes) until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t kNoAllocMaxPath = 4096;     // plan nodes
+constexpr uint32_t kNoAllocMaxSteps = 65536;   // checkpoints, (path_len - 1) * M
+constexpr uint32_t kNoAllocMaxLevels = 256;    // quality levels K + 1
+constexpr size_t kNoAllocJob = 0;
+constexpr size_t kNoAllocHits = 1024;
+constexpr size_t kNoAllocPath = 2048;
+constexpr size_t kNoAllocTables = kNoAllocPath + 4 * (size_t)kNoAllocMaxPath;
+constexpr size_t kNoAllocCkpt = kNoAllocTables + 2 * 4 * (size_t)kNoAllocMaxLevels;
+constexpr size_t kNoAllocBytes = kNoAllocCkpt + sizeof(int4) * (size_t)kNoAllocMaxSteps;
+static_assert(sizeof(McJob) <= kNoAllocHits, "job descriptor does not fit its slot");
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_certify_scratch[kNoAllocBytes];
+
+namespace {
+
+// Device address of g_certify_scratch on the current device, looked up once
+// per device (with that device current) and cached.
+int32_t noalloc_scratch(char** out) {
+  static std::mutex mu;
+  static void* addr[64] = {};
+  int dev = 0;
+  MPAP_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("certify_noalloc: device ordinal %d out of range", dev);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> g(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    MPAP_CK(cudaGetSymbolAddress(&p, g_certify_scratch));
+    addr[dev] = p;
+  }
+  *out = static_cast<char*>(addr[dev]);
+  return MPAP_OK;
+}
+
+}  // namespace
+
+int32_t certify_noalloc_impl(const mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,
+                             const mpap_mc_params* mc, mpap_cert* out, cudaStream_t st) {
+  if (!rm->has_geometry) {
+    set_error("certify_noalloc: the roadmap has no geometry");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (rm->nb > kMcMaxBoxes) {
+    set_error("certify_noalloc: at most %d boxes", kMcMaxBoxes);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (path_len > kNoAllocMaxPath) {
+    set_error("certify_noalloc: plan of %u nodes exceeds the fixed maximum of %u", path_len, kNoAllocMaxPath);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  const uint64_t steps64 = path_len >= 2 ? (uint64_t)(path_len - 1) * (uint64_t)rm->M : 0ull;
+  if (steps64 > kNoAllocMaxSteps) {
+    set_error("certify_noalloc: %llu checkpoints exceed the fixed maximum of %u", (unsigned long long)steps64,
+              kNoAllocMaxSteps);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if ((uint32_t)rm->K + 1u > kNoAllocMaxLevels) {
+    set_error("certify_noalloc: at most %u quality levels", kNoAllocMaxLevels);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  for (uint32_t j = 0; j < path_len; ++j)
+    if (path[j] >= rm->V) {
+      set_error("certify_noalloc: path node %u out of range", path[j]);
+      return MPAP_ERR_INVALID_ARG;
+    }
+  for (int k = 0; k <= rm->K; ++k)
+    if (mc->shift[k] < 0 || mc->shift[k] > 62) {
+      set_error("certify_noalloc: shift table entries must be in [0, 62]");
+      return MPAP_ERR_INVALID_ARG;
+    }
+  char* base = nullptr;
+  int32_t rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  const int K1 = rm->K + 1;
+  McJob J;
+  std::memset(&J, 0, sizeof(J));
+  J.g = rm->geom;
+  J.x = rm->x;
+  J.V = rm->V;
+  J.path = reinterpret_cast<const uint32_t*>(base + kNoAllocPath);
+  J.path_len = path_len;
+  J.ckpt = reinterpret_cast<int4*>(base + kNoAllocCkpt);
+  J.steps = (uint32_t)steps64;
+  J.rollouts = mc->rollouts;
+  J.call_id = mc->call_id;
+  J.K = rm->K;
+  J.key0 = (uint32_t)mc->seed;
+  J.key1 = (uint32_t)(mc->seed >> 32);
+  J.delta2 = (long long)mc->delta_fx * (long long)mc->delta_fx;
+  J.sigma = reinterpret_cast<const int32_t*>(base + kNoAllocTables);
+  J.shift = reinterpret_cast<const int32_t*>(base + kNoAllocTables) + K1;
+  J.hits = reinterpret_cast<uint32_t*>(base + kNoAllocHits);
+  MPAP_CK(cudaMemcpyAsync(base + kNoAllocJob, &J, sizeof(J), cudaMemcpyHostToDevice, st));
+  if (path_len)
+    MPAP_CK(cudaMemcpyAsync(base + kNoAllocPath, path, 4 * (size_t)path_len, cudaMemcpyHostToDevice, st));
+  MPAP_CK(cudaMemcpyAsync(base + kNoAllocTables, mc->sigma_fx, 4 * (size_t)K1, cudaMemcpyHostToDevice, st));
+  MPAP_CK(cudaMemcpyAsync(base + kNoAllocTables + 4 * (size_t)K1, mc->shift, 4 * (size_t)K1,
+                          cudaMemcpyHostToDevice, st));
+  // the array keeps the previous call's contents: the counters restart at zero
+  MPAP_CK(cudaMemsetAsync(base + kNoAllocHits, 0, 3 * sizeof(uint32_t), st));
+  const McJob* d_job = reinterpret_cast<const McJob*>(base + kNoAllocJob);
+  if (J.steps) {
+    LaunchScope ls(st, "k_mc_checkpoints");
+    k_mc_checkpoints<<<dim3((J.steps + 255) / 256, 1), 256, 0, st>>>(d_job);
+  }
+  if (J.steps && J.rollouts) {
+    LaunchScope ls(st, "k_mc_rollouts");
+    k_mc_rollouts<<<dim3((J.rollouts + 255) / 256, 1), 256, 0, st>>>(d_job);
+  }
+  MPAP_CK(cudaGetLastError());
+  uint32_t hh[3] = {0, 0, 0};
+  MPAP_CK(cudaMemcpyAsync(hh, base + kNoAllocHits, sizeof(hh), cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaStreamSynchronize(st));
+  out->hits_loc = hh[0];
+  out->hits_coll = hh[1];
+  out->hits_any = hh[2];
+  out->rollouts = mc->rollouts;
   return MPAP_OK;
 }
 
