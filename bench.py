@@ -262,6 +262,27 @@ def run_gpu(args, rank, world, local):
     return out
 
 
+# DRAM traffic from ncu captures (profiles/*.md), per unit of work, valid only
+# while the kernel sources are the ones that were captured.
+NCU_TRAFFIC = {
+    "k_edges": {"bytes_per_roadmap": (8.139776e6 + 35.685376e6) / 8,
+                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "26e0e2f093e32e194704078bba025fca173c0704",
+                            "paper_1705_02408_gb300/csrc/common.cuh": "9d98f0917e0c93396e66c0986e42f7a820288d41"}},
+}
+
+
+def _traffic(kernel, units):
+    import hashlib
+    t = NCU_TRAFFIC.get(kernel)
+    if not t:
+        return None
+    for path, sha in t["sources"].items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != sha:
+                return None
+    return t["bytes_per_roadmap"] * units
+
+
 def roofline(kern, arm, res, steps):
     """Roofline of the dominant kernel from the live CUDA-event timers."""
     peaks = {}
@@ -285,7 +306,9 @@ def roofline(kern, arm, res, steps):
         sm_max = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * sm_max * 1e6 / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None, "near_tests_per_step": tests,
+                "frac": achieved / peak, "traffic": _traffic(name, B * steps / max(1, launches)),
+                "traffic_unit": "DRAM bytes per launch (ncu, scaled from an 8-roadmap capture)",
+                "near_tests_per_step": tests,
                 "all_pairs_per_step": V * V * B,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
     # HBM-bound search kernels: algorithmic bytes per step
