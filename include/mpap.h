@@ -274,6 +274,78 @@ int32_t mpap_certify_noalloc(const mpap_roadmap* rm, const uint32_t* path, uint3
                              const mpap_mc_params* mc, mpap_cert* out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Candidate plans and the certification surrogate.
+ *
+ * Alg. 3 ends by collecting P_candidates, every plan stored at a goal node, and
+ * returning the cheapest; Alg. 1 then certifies that plan by Monte Carlo and, if
+ * it fails, refines the bound and searches again.  The entry points below expose
+ * the whole candidate set and a learned screen of it, so that a caller can try
+ * the candidates in cost order but skip those a small network predicts will fail
+ * certification, and spend Monte Carlo only on likely winners.  The network is
+ * not in the paper (the paper learns nothing); Monte Carlo stays the judge of
+ * every plan returned.
+ * ------------------------------------------------------------------------- */
+
+/* Candidates of query `index` of the last search on ws (Alg. 3 final lines), in
+ * the solution order (cost, then h, then the tie key: creation wavefront, parent
+ * head, parent cost; then head index), so candidate 0 is the plan mpap_search
+ * returned.  Writes up to `cap` candidates to host arrays: cost[i], h[i] and the
+ * node sequence path[path_ptr[i] .. path_ptr[i+1]) (path_ptr has cap+1 entries,
+ * path has path_cap entries).  *n receives the number written and *total the
+ * size of P_candidates.  MPAP_ERR_CAPACITY if the paths do not fit path_cap (the
+ * counts are still set); MPAP_ERR_INVALID_ARG for a query that did not finish
+ * with MPAP_OK. */
+int32_t mpap_search_candidates(mpap_workspace* ws, uint32_t index, uint32_t cap, int64_t* cost,
+                               int64_t* h, uint32_t* path_ptr, uint32_t* path, uint32_t path_cap,
+                               uint32_t* n, uint32_t* total, void* stream);
+
+/* 48 trajectory features of each of n plans on one roadmap (input of the
+ * surrogate).  Plan i is the host node sequence path[path_ptr[i] ..
+ * path_ptr[i+1]) (at least 2 nodes).  Its Monte Carlo checkpoints (the M
+ * sub-steps of every edge, as mpap_certify uses them, s = 0 .. steps-1) are split
+ * into 16 bins, checkpoint s going to bin floor(16 s / steps).  For bin j:
+ *   feat[j]      = max quality level in the bin / K
+ *   feat[16 + j] = sum of quality levels in the bin / (64 K)
+ *   feat[32 + j] = 4 min(0.25, clearance), the clearance of a checkpoint p being
+ *                  min over boxes b of max_i max(lo_bi - p_i, p_i - hi_bi) and
+ *                  over the walls of min_i min(p_i, 1 - p_i) (negative inside)
+ * (an empty bin gives 0, 0, 1).  feat is a host array [n][48] of float. */
+#define MPAP_FEATURES 48
+int32_t mpap_plan_features(mpap_roadmap* rm, uint32_t n, const uint32_t* path_ptr,
+                           const uint32_t* path, float* feat, void* stream);
+
+/* The surrogate network: 48 -> 128 -> 128 -> 128 -> 2 with ReLU, logits of
+ * (collision, localisation) failure; bfloat16 weights and activations in every
+ * product, fp32 accumulation (tensor cores), fp32 master weights and biases,
+ * Adam.  Packed parameters (fp32, MPAP_MLP_PARAMS): W1[128][48], b1[128],
+ * W2[128][128], b2[128], W3[128][128], b3[128], W4[2][128], b4[2], W[o][i] being
+ * the weight from input i to output o.  mpap_mlp_create initialises the weights
+ * from Philox4x32-10 (uniform in +-1/sqrt(fan in)), biases zero, and sizes the
+ * activations for batches of up to max_batch rows. */
+#define MPAP_MLP_PARAMS 39554
+typedef struct mpap_mlp mpap_mlp;
+int32_t mpap_mlp_create(uint64_t seed, uint32_t max_batch, mpap_mlp** out);
+void mpap_mlp_free(mpap_mlp* net);
+int32_t mpap_mlp_get_params(mpap_mlp* net, float* params, void* stream);
+/* Sets the parameters and clears the Adam state. */
+int32_t mpap_mlp_set_params(mpap_mlp* net, const float* params, void* stream);
+
+/* prob[n][2] = sigmoid(logits) of the features x[n][48].  x and prob are host
+ * arrays, or device arrays when mem = MPAP_MEM_DEVICE.  n <= max_batch. */
+int32_t mpap_mlp_forward(mpap_mlp* net, const float* x, uint32_t n, float* prob, int32_t mem,
+                         void* stream);
+
+/* One training step on the batch (x[n][48], soft labels y[n][2] in [0, 1]):
+ * loss = mean over rows and both outputs of the binary cross-entropy of
+ * sigmoid(logit) against y; gradients by back-propagation (the bfloat16
+ * roundings of stored values pass gradients unchanged); if apply, one Adam step
+ * (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr).  *loss (host, optional)
+ * receives the loss before the step; grads (optional, MPAP_MLP_PARAMS floats,
+ * host or device per mem) the packed gradient. */
+int32_t mpap_mlp_train_step(mpap_mlp* net, const float* x, const float* y, uint32_t n, float lr,
+                            int32_t apply, float* loss, float* grads, int32_t mem, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Launch accounting and kernel timing (tracing).  The paper reports per-phase
  * computation times (Table 2); these entry points expose the same information
  * per kernel.  mpap_launch_count() counts every kernel this library has launched

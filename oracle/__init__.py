@@ -76,6 +76,10 @@ def lib():
         L.orc_certify.argtypes = [P, u32p, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32,
                                   C.c_int64, i32p, i32p, u32p]
         L.orc_straight_line_h.argtypes = [P, i64p]
+        L.orc_result_candidates.restype = C.c_int
+        L.orc_result_candidates.argtypes = [P, C.c_uint32, i64p, i64p, u32p, u32p, C.c_uint32,
+                                            C.POINTER(C.c_uint32)]
+        L.orc_plan_features.argtypes = [P, C.c_uint32, u32p, u32p, f32p]
         _lib = L
     return _lib
 
@@ -201,6 +205,8 @@ class ExploreResult:
     front_ptr: np.ndarray
     front_cost: np.ndarray
     front_h: np.ndarray
+    # P_candidates in solution order (when asked for): dict(cost, h, paths, total)
+    candidates: dict | None = None
 
     def front(self, v: int):
         a, b = int(self.front_ptr[v]), int(self.front_ptr[v + 1])
@@ -208,7 +214,8 @@ class ExploreResult:
 
 
 def explore(rm: Roadmap, beta: int, Lambda: int, max_iters: int = 1 << 20,
-            goal_termination: bool = True, max_plans: int = 1 << 28) -> ExploreResult:
+            goal_termination: bool = True, max_plans: int = 1 << 28,
+            candidates: int = 0) -> ExploreResult:
     L = lib()
     r = L.orc_explore(rm.h, int(beta), int(Lambda), int(max_iters), int(goal_termination),
                       int(max_plans))
@@ -222,8 +229,20 @@ def explore(rm: Roadmap, beta: int, Lambda: int, max_iters: int = 1 << 20,
         fc = np.zeros(max(ft.value, 1), np.int64)
         fh = np.zeros(max(ft.value, 1), np.int64)
         L.orc_result_get(r, path, fp, fc, fh)
+        cand = None
+        if candidates and st.value == 0:
+            k = C.c_uint32()
+            cc = np.zeros(candidates, np.int64); ch = np.zeros(candidates, np.int64)
+            cp = np.zeros(candidates + 1, np.uint32)
+            cap = 1 << 22
+            cpath = np.zeros(cap, np.uint32)
+            tot = L.orc_result_candidates(r, candidates, cc, ch, cp, cpath, cap, C.byref(k))
+            assert tot >= 0
+            n = k.value
+            cand = dict(cost=cc[:n], h=ch[:n], paths=[cpath[cp[i]:cp[i + 1]].copy() for i in range(n)],
+                        total=tot)
         return ExploreResult(st.value, cost.value, hv.value, path[:pl.value], wf.value, ex.value,
-                             pc.value, fp, fc[:ft.value], fh[:ft.value])
+                             pc.value, fp, fc[:ft.value], fh[:ft.value], cand)
     finally:
         L.orc_result_free(r)
 
@@ -254,3 +273,15 @@ def beta_percentile(rm: Roadmap, pct: float = 60.0) -> int:
     h = np.sort(rm.straight_line_h())
     k = int(np.ceil(pct / 100.0 * h.size)) - 1
     return int(h[max(0, min(h.size - 1, k))])
+
+
+def plan_features(rm: Roadmap, paths) -> np.ndarray:
+    """[len(paths), 48] float32 trajectory features (surrogate input)."""
+    n = len(paths)
+    ptr = np.zeros(n + 1, np.uint32)
+    ptr[1:] = np.cumsum([len(p) for p in paths])
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(p, np.uint32) for p in paths])
+                                if n else np.zeros(1, np.uint32), np.uint32)
+    out = np.zeros((max(n, 1), 48), np.float32)
+    lib().orc_plan_features(rm.h, n, ptr, flat, out)
+    return out[:n]

@@ -19,6 +19,8 @@
 //   build_graph          Alg. 2 (BuildGraph)
 //   explore              Alg. 3 (Explore), RemoveDominated (Sec. 3)
 //   certify              Monte Carlo verification (Sec. 3 final phase, Eq. 1)
+//   plan_features        trajectory features of candidate plans (the project's
+//                        certification surrogate; not in the paper)
 //
 // Parity is pinned by the -m "not gpu" tests (brute-force label enumeration,
 // Dijkstra special cases, closed forms, exact slab-test truth, 6D steering
@@ -414,6 +416,9 @@ struct ExploreOut {
   uint64_t plans_created = 0;
   std::vector<uint32_t> front_ptr;   // final per-node fronts, sorted by cost
   std::vector<int64_t> front_cost, front_h;
+  // P_candidates in solution order, with their node sequences
+  std::vector<int64_t> cand_cost, cand_h;
+  std::vector<uint32_t> cand_ptr, cand_path;
 };
 
 void explore(const Roadmap& rm, int64_t beta, int64_t Lambda, uint32_t max_iters,
@@ -533,6 +538,29 @@ void explore(const Roadmap& rm, int64_t beta, int64_t Lambda, uint32_t max_iters
     }
   }
   if (best < 0) { out.status = 1; return; }
+  // the whole candidate set, sorted by the same rule
+  std::vector<uint32_t> cand;
+  for (uint32_t v = 0; v < rm.V; ++v)
+    if (rm.is_goal[v])
+      for (uint32_t pi : P[v]) cand.push_back(pi);
+  std::sort(cand.begin(), cand.end(), [&](uint32_t ia, uint32_t ib) {
+    const Plan& a = plans[ia];
+    const Plan& b = plans[ib];
+    if (a.cost != b.cost) return a.cost < b.cost;
+    if (a.h != b.h) return a.h < b.h;
+    if (key_less(a, b)) return true;
+    if (key_less(b, a)) return false;
+    return a.head < b.head;
+  });
+  out.cand_ptr.assign(1, 0);
+  for (uint32_t pi : cand) {
+    out.cand_cost.push_back(plans[pi].cost);
+    out.cand_h.push_back(plans[pi].h);
+    std::vector<uint32_t> seq;
+    for (int64_t a = pi; a >= 0; a = plans[a].parent) seq.push_back(plans[a].head);
+    out.cand_path.insert(out.cand_path.end(), seq.rbegin(), seq.rend());
+    out.cand_ptr.push_back((uint32_t)out.cand_path.size());
+  }
   out.cost = plans[best].cost;
   out.h = plans[best].h;
   out.path.clear();
@@ -630,6 +658,59 @@ int certify(const Roadmap& rm, const uint32_t* path, uint32_t path_len, uint32_t
     out.hits_any += (loc || coll);
   }
   return 0;
+}
+
+// ----------------------------------------------------------------------------
+// Trajectory features of a plan (input of the certification surrogate, which is
+// not in the paper).  The plan's Monte Carlo checkpoints s = 0 .. steps-1 (the M
+// sub-steps of every edge, exactly as certify() visits them) are split into 16
+// bins, s going to bin floor(16 s / steps).  For bin j: the maximum quality level
+// / K, the sum of levels / (64 K), and 4 min(0.25, clearance), where the clearance
+// of p is the smallest of the signed max-norm distances to the boxes
+// (max_i max(lo_i - p_i, p_i - hi_i), negative inside) and of the distances to the
+// walls of the unit map (min_i min(p_i, 1 - p_i)).  An empty bin gives 0, 0, 1.
+// ----------------------------------------------------------------------------
+void plan_features(const Roadmap& rm, const uint32_t* path, uint32_t len, float* f) {
+  const Scene& sc = rm.sc;
+  const int dp = sc.dp();
+  std::vector<int> lev;
+  std::vector<float> clr;
+  for (uint32_t j = 0; j + 1 < len; ++j) {
+    EdgeGeom g = edge_geom(rm, path[j], path[j + 1]);
+    for (int m = 1; m <= rm.M; ++m) {
+      float p[3];
+      checkpoint(rm, g, m, p);
+      int k = level_at(sc, p);
+      lev.push_back(k > sc.K ? sc.K : k);
+      float c = INFINITY;
+      for (int i = 0; i < dp; ++i) c = std::fmin(c, std::fmin(p[i], 1.0f - p[i]));
+      for (int b = 0; b < sc.nb; ++b) {
+        float d = -INFINITY;
+        for (int i = 0; i < dp; ++i)
+          d = std::fmax(d, std::fmax(sc.lo[3 * b + i] - p[i], p[i] - sc.hi[3 * b + i]));
+        c = std::fmin(c, d);
+      }
+      clr.push_back(c);
+    }
+  }
+  const uint64_t steps = lev.size();
+  const float Kf = (float)(sc.K > 0 ? sc.K : 1);
+  for (int j = 0; j < 16; ++j) {
+    int lmax = 0;
+    uint32_t lsum = 0;
+    float cmin = INFINITY;
+    bool any = false;
+    for (uint64_t s = 0; s < steps; ++s) {
+      if ((16 * s) / steps != (uint64_t)j) continue;
+      any = true;
+      lmax = std::max(lmax, lev[s]);
+      lsum += (uint32_t)lev[s];
+      cmin = std::fmin(cmin, clr[s]);
+    }
+    f[j] = any ? (float)lmax / Kf : 0.0f;
+    f[16 + j] = any ? (float)lsum / (64.0f * Kf) : 0.0f;
+    f[32 + j] = any ? 4.0f * std::fmin(0.25f, cmin) : 1.0f;
+  }
 }
 
 Scene make_scene(int dim, int nb, const float* lo, const float* hi, int G,
@@ -795,6 +876,32 @@ void orc_result_get(const orc_result* r, uint32_t* path, uint32_t* front_ptr,
   if (front_ptr) std::memcpy(front_ptr, o.front_ptr.data(), o.front_ptr.size() * 4);
   if (front_cost) std::memcpy(front_cost, o.front_cost.data(), o.front_cost.size() * 8);
   if (front_h) std::memcpy(front_h, o.front_h.data(), o.front_h.size() * 8);
+}
+
+// P_candidates of an explore result: up to cap candidates (cost, h, node
+// sequences packed as path[ptr[i] .. ptr[i+1])); returns the total count, or -1 if
+// the paths need more than path_cap entries.
+int orc_result_candidates(const orc_result* r, uint32_t cap, int64_t* cost, int64_t* hval,
+                          uint32_t* ptr, uint32_t* path, uint32_t path_cap, uint32_t* n) {
+  const ExploreOut& o = r->out;
+  const uint32_t total = (uint32_t)o.cand_cost.size();
+  const uint32_t k = std::min(cap, total);
+  *n = k;
+  if (k == 0) return (int)total;
+  if (o.cand_ptr[k] > path_cap) return -1;
+  for (uint32_t i = 0; i < k; ++i) {
+    cost[i] = o.cand_cost[i];
+    hval[i] = o.cand_h[i];
+  }
+  std::memcpy(ptr, o.cand_ptr.data(), 4 * ((size_t)k + 1));
+  std::memcpy(path, o.cand_path.data(), 4 * (size_t)o.cand_ptr[k]);
+  return (int)total;
+}
+
+void orc_plan_features(const orc_roadmap* h, uint32_t n, const uint32_t* ptr, const uint32_t* path,
+                       float* feat) {
+  for (uint32_t i = 0; i < n; ++i)
+    plan_features(h->rm, path + ptr[i], ptr[i + 1] - ptr[i], feat + 48 * (size_t)i);
 }
 
 int orc_certify(const orc_roadmap* h, const uint32_t* path, uint32_t path_len, uint32_t rollouts,

@@ -32,7 +32,9 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_roadmap_export", "mpap_roadmap_stats", "mpap_roadmap_free", "mpap_workspace_create",
            "mpap_workspace_free", "mpap_search", "mpap_search_batch", "mpap_search_fronts",
            "mpap_certify", "mpap_certify_batch", "mpap_certify_noalloc", "mpap_profile_enable", "mpap_profile_reset",
-           "mpap_launch_count", "mpap_profile_read"]
+           "mpap_launch_count", "mpap_profile_read", "mpap_search_candidates", "mpap_plan_features",
+           "mpap_mlp_create", "mpap_mlp_free", "mpap_mlp_get_params", "mpap_mlp_set_params",
+           "mpap_mlp_forward", "mpap_mlp_train_step"]
 
 
 class mpap_scene(C.Structure):
@@ -130,6 +132,22 @@ def lib():
         L.mpap_launch_count.restype = C.c_uint64
         L.mpap_profile_read.restype = i32
         L.mpap_profile_read.argtypes = [C.c_uint32, P, P, P, C.POINTER(C.c_uint32)]
+        u32p = C.POINTER(C.c_uint32)
+        L.mpap_search_candidates.restype = i32
+        L.mpap_search_candidates.argtypes = [P, C.c_uint32, C.c_uint32, P, P, P, P, C.c_uint32, u32p, u32p, P]
+        L.mpap_plan_features.restype = i32
+        L.mpap_plan_features.argtypes = [P, C.c_uint32, P, P, P, P]
+        L.mpap_mlp_create.restype = i32
+        L.mpap_mlp_create.argtypes = [C.c_uint64, C.c_uint32, C.POINTER(P)]
+        L.mpap_mlp_free.argtypes = [P]
+        L.mpap_mlp_get_params.restype = i32
+        L.mpap_mlp_get_params.argtypes = [P, P, P]
+        L.mpap_mlp_set_params.restype = i32
+        L.mpap_mlp_set_params.argtypes = [P, P, P]
+        L.mpap_mlp_forward.restype = i32
+        L.mpap_mlp_forward.argtypes = [P, P, C.c_uint32, P, i32, P]
+        L.mpap_mlp_train_step.restype = i32
+        L.mpap_mlp_train_step.argtypes = [P, P, P, C.c_uint32, C.c_float, i32, C.POINTER(C.c_float), P, i32, P]
         _lib = L
     return _lib
 
@@ -489,3 +507,103 @@ def certify_batch(rms, paths, mcs, stream=None):
            "mpap_certify_batch")
     return [dict(hits_loc=o.hits_loc, hits_coll=o.hits_coll, hits_any=o.hits_any, rollouts=o.rollouts)
             for o in outs]
+
+
+# ---------------------------------------------------------------------------
+# Candidate plans and the certification surrogate
+# ---------------------------------------------------------------------------
+MLP_PARAMS = 39554
+N_FEATURES = 48
+
+
+def search_candidates(ws: Workspace, index=0, cap=64, path_cap=1 << 16, stream=None):
+    """P_candidates of query `index` of the last search on ws, in solution order:
+    dict(cost, h (int64 arrays), paths (list of uint32 arrays), total)."""
+    cost = np.zeros(max(cap, 1), np.int64)
+    hh = np.zeros(max(cap, 1), np.int64)
+    ptr = np.zeros(cap + 1, np.uint32)
+    path = np.zeros(max(path_cap, 1), np.uint32)
+    n = C.c_uint32()
+    tot = C.c_uint32()
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(lib().mpap_search_candidates(ws.h, index, cap, vp(cost), vp(hh), vp(ptr), vp(path), path_cap,
+                                        C.byref(n), C.byref(tot), _stream(stream)), "mpap_search_candidates")
+    k = n.value
+    paths = [path[ptr[i]:ptr[i + 1]].copy() for i in range(k)]
+    return dict(cost=cost[:k].copy(), h=hh[:k].copy(), paths=paths, total=tot.value)
+
+
+def plan_features(rm: Roadmap, paths, stream=None) -> np.ndarray:
+    """mpap_plan_features: [len(paths), 48] float32 features of node sequences on rm."""
+    n = len(paths)
+    if n == 0:
+        return np.zeros((0, N_FEATURES), np.float32)
+    ptr = np.zeros(n + 1, np.uint32)
+    ptr[1:] = np.cumsum([len(p) for p in paths])
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(p, np.uint32) for p in paths]), np.uint32)
+    out = np.zeros((n, N_FEATURES), np.float32)
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(lib().mpap_plan_features(rm.h, n, vp(ptr), vp(flat), vp(out), _stream(stream)), "mpap_plan_features")
+    return out
+
+
+class Mlp:
+    """An mpap_mlp: the 48-128-128-128-2 certification surrogate (bf16 tensor-core
+    products, fp32 master weights, Adam).  Inputs and outputs are numpy arrays
+    (host) or contiguous CUDA tensors (device, float32)."""
+
+    def __init__(self, seed=0, max_batch=4096):
+        h = C.c_void_p()
+        _check(lib().mpap_mlp_create(int(seed), int(max_batch), C.byref(h)), "mpap_mlp_create")
+        self.h = h
+        self.max_batch = int(max_batch)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.mpap_mlp_free(self.h)
+            self.h = None
+
+    def get_params(self, stream=None) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, np.float32)
+        _check(lib().mpap_mlp_get_params(self.h, out.ctypes.data_as(C.c_void_p), _stream(stream)),
+               "mpap_mlp_get_params")
+        return out
+
+    def set_params(self, params, stream=None):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == MLP_PARAMS
+        _check(lib().mpap_mlp_set_params(self.h, p.ctypes.data_as(C.c_void_p), _stream(stream)),
+               "mpap_mlp_set_params")
+
+    def forward(self, x, stream=None):
+        xp, xk, dev = _ptr(x, np.float32)
+        n = int(x.shape[0])
+        if dev:
+            import torch
+            out = torch.empty((n, 2), dtype=torch.float32, device=x.device)
+            op = C.c_void_p(out.data_ptr())
+        else:
+            out = np.zeros((n, 2), np.float32)
+            op = out.ctypes.data_as(C.c_void_p)
+        _check(lib().mpap_mlp_forward(self.h, xp, n, op, 1 if dev else 0, _stream(stream)), "mpap_mlp_forward")
+        return out
+
+    def train_step(self, x, y, lr=1e-3, apply=True, want_grads=False, stream=None):
+        """One step; returns (loss, grads or None)."""
+        xp, xk, dev = _ptr(x, np.float32)
+        yp, yk, _ = _ptr(y, np.float32)
+        n = int(x.shape[0])
+        loss = C.c_float()
+        g = None
+        gp = None
+        if want_grads:
+            if dev:
+                import torch
+                g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+                gp = C.c_void_p(g.data_ptr())
+            else:
+                g = np.zeros(MLP_PARAMS, np.float32)
+                gp = g.ctypes.data_as(C.c_void_p)
+        _check(lib().mpap_mlp_train_step(self.h, xp, yp, n, float(lr), 1 if apply else 0, C.byref(loss), gp,
+                                         1 if dev else 0, _stream(stream)), "mpap_mlp_train_step")
+        return loss.value, g

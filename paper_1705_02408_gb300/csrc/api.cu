@@ -19,6 +19,18 @@ int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* path
                            const mpap_mc_params* mcs, uint32_t n, mpap_cert* outs, cudaStream_t st);
 int32_t certify_noalloc_impl(const mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,
                              const mpap_mc_params* mc, mpap_cert* out, cudaStream_t st);
+int32_t search_candidates_impl(mpap_workspace* ws, uint32_t index, uint32_t cap, int64_t* cost, int64_t* h,
+                               uint32_t* path_ptr, uint32_t* path, uint32_t path_cap, uint32_t* n_out,
+                               uint32_t* total_out, cudaStream_t st);
+int32_t plan_features_impl(mpap_roadmap* rm, uint32_t n, const uint32_t* path_ptr, const uint32_t* path, float* feat,
+                           cudaStream_t st);
+int32_t mlp_create(uint64_t seed, uint32_t max_batch, mpap_mlp** out);
+void mlp_free(mpap_mlp* n);
+int32_t mlp_get_params(mpap_mlp* n, float* params, cudaStream_t st);
+int32_t mlp_set_params(mpap_mlp* n, const float* params, cudaStream_t st);
+int32_t mlp_forward(mpap_mlp* nt, const float* x, uint32_t n, float* prob, int32_t mem, cudaStream_t st);
+int32_t mlp_train_step(mpap_mlp* nt, const float* x, const float* y, uint32_t n, float lr, int32_t apply,
+                       float* loss_out, float* grads_out, int32_t mem, cudaStream_t st);
 }  // namespace mpap
 
 using mpap::set_error;
@@ -292,6 +304,64 @@ int32_t mpap_certify_batch(mpap_roadmap* const* rms, const uint32_t* const* path
     return MPAP_ERR_INVALID_ARG;
   }
   return mpap::certify_batch_impl(rms, paths, path_lens, mcs, n, outs, S(stream));
+}
+
+int32_t mpap_search_candidates(mpap_workspace* ws, uint32_t index, uint32_t cap, int64_t* cost, int64_t* h,
+                               uint32_t* path_ptr, uint32_t* path, uint32_t path_cap, uint32_t* n, uint32_t* total,
+                               void* stream) {
+  if (!ws || !n) {
+    set_error("search_candidates: null workspace or count");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (cap > (1u << 16)) {
+    set_error("search_candidates: cap must be at most 65536");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::search_candidates_impl(ws, index, cap, cost, h, path_ptr, path, path_cap, n, total, S(stream));
+}
+
+int32_t mpap_plan_features(mpap_roadmap* rm, uint32_t n, const uint32_t* path_ptr, const uint32_t* path, float* feat,
+                           void* stream) {
+  return mpap::plan_features_impl(rm, n, path_ptr, path, feat, S(stream));
+}
+
+int32_t mpap_mlp_create(uint64_t seed, uint32_t max_batch, mpap_mlp** out) {
+  return mpap::mlp_create(seed, max_batch, out);
+}
+
+void mpap_mlp_free(mpap_mlp* net) { mpap::mlp_free(net); }
+
+int32_t mpap_mlp_get_params(mpap_mlp* net, float* params, void* stream) {
+  if (!net || !params) {
+    set_error("mlp_get_params: null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::mlp_get_params(net, params, S(stream));
+}
+
+int32_t mpap_mlp_set_params(mpap_mlp* net, const float* params, void* stream) {
+  if (!net || !params) {
+    set_error("mlp_set_params: null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::mlp_set_params(net, params, S(stream));
+}
+
+int32_t mpap_mlp_forward(mpap_mlp* net, const float* x, uint32_t n, float* prob, int32_t mem, void* stream) {
+  if (!net || (n && (!x || !prob)) || (mem != MPAP_MEM_HOST && mem != MPAP_MEM_DEVICE)) {
+    set_error("mlp_forward: null argument or bad mem");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::mlp_forward(net, x, n, prob, mem, S(stream));
+}
+
+int32_t mpap_mlp_train_step(mpap_mlp* net, const float* x, const float* y, uint32_t n, float lr, int32_t apply,
+                            float* loss, float* grads, int32_t mem, void* stream) {
+  if (!net || !x || !y || (mem != MPAP_MEM_HOST && mem != MPAP_MEM_DEVICE) || !(lr >= 0.0f)) {
+    set_error("mlp_train_step: null argument, bad mem or negative lr");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::mlp_train_step(net, x, y, n, lr, apply, loss, grads, mem, S(stream));
 }
 
 }  // extern "C"

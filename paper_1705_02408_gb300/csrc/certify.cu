@@ -398,4 +398,136 @@ int32_t certify_noalloc_impl(const mpap_roadmap* rm, const uint32_t* path, uint3
   return MPAP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Trajectory features of candidate plans (input of the certification
+// surrogate): one thread per (plan, bin).  A plan's Monte Carlo checkpoints
+// s = 0 .. steps-1 (the M sub-steps of each edge, as k_mc_checkpoints) fall into
+// 16 bins, s going to floor(16 s / steps); per bin the maximum and the sum of the
+// quality levels and the minimum clearance (signed box distance in the max norm,
+// and the distance to the walls of the unit map).  Every float operation is one
+// IEEE operation, so the features are reproducible bit for bit.
+// ---------------------------------------------------------------------------
+struct FeatJob {
+  Geom g;
+  const float* x;
+  uint32_t V;
+  int K;
+  uint32_t n;
+  const uint32_t* ptr;     // [n + 1]
+  const uint32_t* path;
+  float* feat;             // [n][48]
+};
+
+__global__ void k_plan_features(FeatJob J) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= J.n * 16u) return;
+  const uint32_t i = t >> 4, j = t & 15u;
+  const uint32_t p0 = J.ptr[i], len = J.ptr[i + 1] - p0;
+  const uint32_t M = (uint32_t)J.g.M;
+  const uint32_t steps = len >= 2 ? (len - 1) * M : 0u;
+  const uint32_t s_lo = (j * steps + 15u) / 16u, s_hi = ((j + 1) * steps + 15u) / 16u;
+  int lmax = 0;
+  uint32_t lsum = 0;
+  float clr = INFINITY;
+  const int dp = J.g.dp;
+  uint32_t cur_e = 0xFFFFFFFFu;
+  Conn cn;
+  for (uint32_t s = s_lo; s < s_hi; ++s) {
+    const uint32_t e = s / M;
+    if (e != cur_e) {
+      cur_e = e;
+      const uint32_t a = J.path[p0 + e], b = J.path[p0 + e + 1];
+      float xa[6], xb[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        xa[c] = J.x[(size_t)c * J.V + a];
+        xb[c] = J.x[(size_t)c * J.V + b];
+      }
+      conn_setup(J.g, xa, xb, cn);
+    }
+    float p[3];
+    conn_point(J.g, cn, (int)(s % M) + 1, p);
+    int lev = level_at(J.g, p);
+    lev = lev > J.K ? J.K : lev;
+    lmax = lev > lmax ? lev : lmax;
+    lsum += (uint32_t)lev;
+    float c = INFINITY;
+    for (int k = 0; k < dp; ++k) c = fminf(c, fminf(p[k], __fsub_rn(1.0f, p[k])));
+    for (int b = 0; b < J.g.nb; ++b) {
+      float d = -INFINITY;
+      for (int k = 0; k < dp; ++k) {
+        d = fmaxf(d, fmaxf(__fsub_rn(J.g.box_lo[3 * b + k], p[k]), __fsub_rn(p[k], J.g.box_hi[3 * b + k])));
+      }
+      c = fminf(c, d);
+    }
+    clr = fminf(clr, c);
+  }
+  float* f = J.feat + (size_t)i * 48;
+  const float Kf = (float)(J.K > 0 ? J.K : 1);
+  if (s_hi > s_lo) {
+    f[j] = __fdiv_rn((float)lmax, Kf);
+    f[16 + j] = __fdiv_rn((float)lsum, __fmul_rn(64.0f, Kf));
+    f[32 + j] = __fmul_rn(4.0f, fminf(0.25f, clr));
+  } else {
+    f[j] = 0.0f;
+    f[16 + j] = 0.0f;
+    f[32 + j] = 1.0f;
+  }
+}
+
+int32_t plan_features_impl(mpap_roadmap* rm, uint32_t n, const uint32_t* path_ptr, const uint32_t* path, float* feat,
+                           cudaStream_t st) {
+  if (!rm || !rm->has_geometry) {
+    set_error("plan_features: roadmap has no geometry");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (n == 0) return MPAP_OK;
+  if (!path_ptr || !path || !feat) {
+    set_error("plan_features: null array");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  const uint32_t total = path_ptr[n] - path_ptr[0];
+  for (uint32_t i = 0; i < n; ++i) {
+    if (path_ptr[i + 1] < path_ptr[i] + 2) {
+      set_error("plan_features: plan %u has fewer than 2 nodes", i);
+      return MPAP_ERR_INVALID_ARG;
+    }
+  }
+  for (uint32_t k = 0; k < total; ++k)
+    if (path[path_ptr[0] + k] >= rm->V) {
+      set_error("plan_features: node %u out of range", path[path_ptr[0] + k]);
+      return MPAP_ERR_INVALID_ARG;
+    }
+  std::vector<uint32_t> ptr(n + 1);
+  for (uint32_t i = 0; i <= n; ++i) ptr[i] = path_ptr[i] - path_ptr[0];
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t b_ptr = up(4 * ((size_t)n + 1)), b_path = up(4 * (size_t)total), b_feat = 4 * 48 * (size_t)n;
+  char* blk = nullptr;
+  MPAP_CK(scratch_alloc((void**)&blk, b_ptr + b_path + b_feat, st));
+  FeatJob J;
+  J.g = rm->geom;
+  J.x = rm->x;
+  J.V = rm->V;
+  J.K = rm->K;
+  J.n = n;
+  J.ptr = (const uint32_t*)blk;
+  J.path = (const uint32_t*)(blk + b_ptr);
+  J.feat = (float*)(blk + b_ptr + b_path);
+  int32_t rc = MPAP_OK;
+  if (!cuda_ok(cudaMemcpyAsync(blk, ptr.data(), 4 * ((size_t)n + 1), cudaMemcpyHostToDevice, st), "features ptr") ||
+      !cuda_ok(cudaMemcpyAsync(blk + b_ptr, path + path_ptr[0], 4 * (size_t)total, cudaMemcpyHostToDevice, st),
+               "features path"))
+    rc = MPAP_ERR_CUDA;
+  if (rc == MPAP_OK) {
+    LaunchScope ls(st, "k_plan_features");
+    k_plan_features<<<(n * 16 + 255) / 256, 256, 0, st>>>(J);
+    if (!cuda_ok(cudaGetLastError(), "k_plan_features")) rc = MPAP_ERR_CUDA;
+  }
+  if (rc == MPAP_OK && !cuda_ok(cudaMemcpyAsync(feat, J.feat, b_feat, cudaMemcpyDeviceToHost, st), "features out"))
+    rc = MPAP_ERR_CUDA;
+  scratch_free(blk, st);
+  if (!cuda_ok(cudaStreamSynchronize(st), "plan_features")) rc = MPAP_ERR_CUDA;
+  return rc;
+}
+
 }  // namespace mpap

@@ -919,6 +919,108 @@ __global__ void k_finalize(WS w, uint32_t nq) {
 }
 
 // ---------------------------------------------------------------------------
+// Candidate export (Alg. 3 final lines: P_candidates, every plan stored at a goal
+// node).  One block for one query: `cap` rounds, each picking the best plan that
+// is strictly worse (in the solution order) than the previous pick, so the
+// candidates come out in the order k_finalize uses; then each thread back-traces
+// one candidate into the packed path array.
+// ---------------------------------------------------------------------------
+struct CandOut {
+  long long* cost;
+  long long* h;
+  uint32_t* ref;
+  uint32_t* ptr;       // [cap + 1]
+  uint32_t* path;      // [path_cap]
+  uint32_t path_cap;
+  uint32_t* counts;    // [0] candidates written, [1] |P_candidates|, [2] path overflow
+};
+
+__device__ __forceinline__ Best goal_plan(const WS& w, uint32_t v, uint32_t ref, long long cost, long long h) {
+  Best c;
+  c.cost = cost;
+  c.h = h;
+  c.ref = ref;
+  c.iter = w.a_iter[ref];
+  const uint32_t par = w.a_parent[ref];
+  c.phead = (par == kNone) ? kNone : w.a_head[par];
+  c.pcost = (par == kNone) ? 0 : w.a_cost[par];
+  c.head = v;
+  return c;
+}
+
+__global__ void __launch_bounds__(256) k_candidates(WS w, uint32_t q, uint32_t cap, CandOut o) {
+  const QueryDev& Q = w.qd[q];
+  __shared__ Best sb[256];
+  __shared__ Best prev;
+  __shared__ uint32_t s_total, s_n;
+  if (threadIdx.x == 0) {
+    s_total = 0;
+    s_n = 0;
+  }
+  __syncthreads();
+  uint32_t mine = 0;
+  for (uint32_t r = 0; r < cap; ++r) {
+    Best best;
+    best.cost = LLONG_MAX;
+    best.ref = kNone;
+    for (uint32_t i = threadIdx.x; i < Q.n_goal; i += blockDim.x) {
+      const uint32_t v = Q.goal_list[i];
+      const uint32_t g = Q.base + v;
+      const uint32_t b = w.cur[g];
+      const uint32_t n = w.f_cnt[(size_t)b * w.NV + g];
+      const size_t off = slab(w, b, g);
+      if (r == 0) mine += n;
+      for (uint32_t j = 0; j < n; ++j) {
+        const Best c = goal_plan(w, v, w.f_pid[off + j] & kPidMask, w.f_cost[off + j], w.f_h[off + j]);
+        if (r > 0 && !better(prev, c)) continue;
+        if (best.ref == kNone || better(c, best)) best = c;
+      }
+    }
+    sb[threadIdx.x] = best;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if ((int)threadIdx.x < st) {
+        const Best& x = sb[threadIdx.x + st];
+        if (x.ref != kNone && (sb[threadIdx.x].ref == kNone || better(x, sb[threadIdx.x]))) sb[threadIdx.x] = x;
+      }
+      __syncthreads();
+    }
+    const bool none = sb[0].ref == kNone;
+    if (threadIdx.x == 0 && !none) {
+      prev = sb[0];
+      o.cost[r] = sb[0].cost;
+      o.h[r] = sb[0].h;
+      o.ref[r] = sb[0].ref;
+      s_n = r + 1;
+    }
+    if (r == 0 && mine) atomicAdd(&s_total, mine);
+    __syncthreads();
+    if (none) break;
+  }
+  // path lengths, offsets (serial over at most cap candidates), then the paths
+  const uint32_t nc = s_n;
+  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
+    uint32_t len = 0;
+    for (uint32_t a = o.ref[i]; a != kNone; a = w.a_parent[a]) ++len;
+    o.ptr[i + 1] = len;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    o.ptr[0] = 0;
+    for (uint32_t i = 0; i < nc; ++i) o.ptr[i + 1] += o.ptr[i];
+    o.counts[0] = nc;
+    o.counts[1] = s_total;
+    o.counts[2] = o.ptr[nc] > o.path_cap ? 1u : 0u;
+  }
+  __syncthreads();
+  if (o.ptr[nc] > o.path_cap) return;
+  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
+    uint32_t k = o.ptr[i + 1];
+    for (uint32_t a = o.ref[i]; a != kNone; a = w.a_parent[a]) o.path[--k] = w.a_head[a];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -1208,6 +1310,69 @@ int32_t search_fronts_impl(mpap_workspace* ws, uint32_t index, uint32_t* front_p
   if (front_ptr) front_ptr[V] = (uint32_t)t;
   if (total) *total = t;
   return t <= cap ? MPAP_OK : MPAP_ERR_INVALID_ARG;
+}
+
+
+int32_t search_candidates_impl(mpap_workspace* ws, uint32_t index, uint32_t cap, int64_t* cost, int64_t* h,
+                               uint32_t* path_ptr, uint32_t* path, uint32_t path_cap, uint32_t* n_out,
+                               uint32_t* total_out, cudaStream_t st) {
+  const WS& w = ws->w;
+  if (index >= ws->last_V.size()) {
+    set_error("search_candidates: no query %u in the last search", index);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  ResultDev r;
+  MPAP_CK(cudaMemcpyAsync(&r, w.res + index, sizeof(ResultDev), cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaStreamSynchronize(st));
+  if (r.status != MPAP_OK) {
+    set_error("search_candidates: query %u finished with status %d", index, r.status);
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (cap == 0) {
+    if (n_out) *n_out = 0;
+    return MPAP_OK;
+  }
+  const size_t bytes = (size_t)cap * 20 + 4 * ((size_t)cap + 1) + 4 * (size_t)path_cap + 16 + 64;
+  char* buf = nullptr;
+  MPAP_CK(scratch_alloc((void**)&buf, bytes, st));
+  CandOut o;
+  o.cost = reinterpret_cast<long long*>(buf);
+  o.h = o.cost + cap;
+  o.ref = reinterpret_cast<uint32_t*>(o.h + cap);
+  o.ptr = o.ref + cap;
+  o.counts = o.ptr + cap + 1;
+  o.path = o.counts + 4;
+  o.path_cap = path_cap;
+  {
+    LaunchScope ls(st, "k_candidates");
+    k_candidates<<<1, 256, 0, st>>>(w, index, cap, o);
+  }
+  int32_t rc = cudaGetLastError() == cudaSuccess ? MPAP_OK : MPAP_ERR_CUDA;
+  uint32_t counts[3] = {0, 0, 0};
+  if (rc == MPAP_OK) {
+    cudaMemcpyAsync(counts, o.counts, 12, cudaMemcpyDeviceToHost, st);
+    rc = cuda_ok(cudaStreamSynchronize(st), "k_candidates") ? MPAP_OK : MPAP_ERR_CUDA;
+  }
+  const uint32_t nc = counts[0];
+  if (rc == MPAP_OK) {
+    if (n_out) *n_out = nc;
+    if (total_out) *total_out = counts[1];
+    if (cost) cudaMemcpyAsync(cost, o.cost, 8 * (size_t)nc, cudaMemcpyDeviceToHost, st);
+    if (h) cudaMemcpyAsync(h, o.h, 8 * (size_t)nc, cudaMemcpyDeviceToHost, st);
+    if (path_ptr) cudaMemcpyAsync(path_ptr, o.ptr, 4 * ((size_t)nc + 1), cudaMemcpyDeviceToHost, st);
+    if (counts[2]) {
+      set_error("search_candidates: paths need more than path_cap = %u entries", path_cap);
+      rc = MPAP_ERR_CAPACITY;
+    }
+    rc = cuda_ok(cudaStreamSynchronize(st), "candidates copy") ? rc : MPAP_ERR_CUDA;
+    if (rc == MPAP_OK && path && path_ptr && nc)
+      rc = cuda_ok(cudaMemcpyAsync(path, o.path, 4 * (size_t)path_ptr[nc], cudaMemcpyDeviceToHost, st), "path copy")
+               ? MPAP_OK
+               : MPAP_ERR_CUDA;
+  }
+  scratch_free(buf, st);
+  if (!cuda_ok(cudaStreamSynchronize(st), "candidates")) rc = MPAP_ERR_CUDA;
+  return rc;
 }
 
 }  // namespace mpap

@@ -1,0 +1,175 @@
+"""GPU parity of the surrogate path: candidate export (P_candidates, Alg. 3 final
+lines) and trajectory features bit-exact against the oracle; the tensor-core MLP
+forward pass, its back-propagated gradients and the Adam step against the float64
+oracle with the same bfloat16 rounding points."""
+import numpy as np
+import pytest
+
+import scenegen
+from _gpu import BIG
+from _search_ref import random_graph
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mp():
+    from paper_1705_02408_gb300 import build
+    build.build()
+    import paper_1705_02408_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ws(mp):
+    return mp.Workspace(40000, front_cap=2048, max_plans=1 << 23)
+
+
+def _same_candidates(g, o):
+    assert g["total"] == o["total"]
+    assert len(g["paths"]) == len(o["paths"])
+    np.testing.assert_array_equal(g["cost"], o["cost"])
+    np.testing.assert_array_equal(g["h"], o["h"])
+    for a, b in zip(g["paths"], o["paths"]):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_candidates_random_graphs(mp, orc, ws, seed):
+    rng = np.random.default_rng(900 + seed)
+    V = int(rng.integers(3, 30))
+    g = random_graph(rng, V, p_edge=float(rng.uniform(0.15, 0.5)), dmax=int(rng.integers(1, 5)))
+    ro = orc.roadmap_from_csr(*g)
+    rg = mp.roadmap_from_csr(*g)
+    for stop in (True, False):
+        for cap in (1, 5, 300):
+            a = orc.explore(ro, BIG, 2, goal_termination=stop, candidates=cap)
+            b = mp.search(ws, rg, BIG, group_width_q=2, goal_stop=stop)
+            assert b.status == a.status
+            if a.status != 0:
+                continue
+            _same_candidates(mp.search_candidates(ws, 0, cap=cap), a.candidates)
+
+
+@pytest.mark.parametrize("name,seed,n", [("2d", 1, 1000), ("2d", 6, 1000), ("3d", 2, 2500),
+                                         ("6d", 1, 3000), ("6d", 4, 3000)])
+def test_candidates_and_features_on_scenes(mp, orc, ws, name, seed, n):
+    sc = scenegen.make_scene(name, seed, query_id=seed)
+    r = sc.cfg.r if name != "6d" else 18.0
+    ro = orc.build_roadmap(sc, n=n, r=r)
+    rg = mp.build_roadmap_for_scene(sc, n=n, r=r)
+    beta = orc.beta_percentile(ro)
+    for stop in (True, False):
+        a = orc.explore(ro, beta, orc.group_width(0.5, r), goal_termination=stop, candidates=64)
+        b = mp.search(ws, rg, beta, lam=0.5, goal_stop=stop)
+        assert b.status == a.status == 0
+        cand = mp.search_candidates(ws, 0, cap=64)
+        _same_candidates(cand, a.candidates)
+        np.testing.assert_array_equal(cand["paths"][0], b.path)
+        fg = mp.plan_features(rg, cand["paths"])
+        fo = orc.plan_features(ro, cand["paths"])
+        assert fg.shape == (len(cand["paths"]), 48)
+        np.testing.assert_array_equal(fg, fo)
+
+
+def test_candidates_reject_unfinished_query(mp, ws):
+    g = (np.array([0, 0, 0], np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.int32),
+         np.zeros(0, np.int32), np.zeros(0, np.int32), np.array([0, 1], np.uint8))
+    rg = mp.roadmap_from_csr(*g)
+    r = mp.search(ws, rg, BIG, group_width_q=1)
+    assert r.status == 1
+    with pytest.raises(mp.MpapError) as e:
+        mp.search_candidates(ws, 0, cap=4)
+    assert e.value.status == mp.MPAP_ERR_INVALID_ARG
+
+
+def _features(rng, n):
+    x = np.empty((n, 48), np.float32)
+    x[:, :32] = rng.uniform(0, 1, (n, 32))
+    x[:, 32:] = rng.uniform(-1, 1, (n, 16))
+    return x
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 300, 1000, 4096])
+def test_mlp_forward_matches_oracle(mp, n):
+    rng = np.random.default_rng(n)
+    net = mp.Mlp(seed=11, max_batch=4096)
+    p = net.get_params().astype(np.float64)
+    # non-zero biases so that every bias path is exercised
+    d = omlp.unpack(p)
+    for b in ("b1", "b2", "b3", "b4"):
+        d[b] = rng.normal(0, 0.1, d[b].shape)
+    p = omlp.pack(d).astype(np.float32)
+    net.set_params(p)
+    x = _features(rng, n)
+    got = net.forward(x)
+    z, _ = omlp.forward(p.astype(np.float64), x, rounding=True)
+    want = omlp.sigmoid(z)
+    assert got.shape == (n, 2)
+    assert np.max(np.abs(got - want)) <= 1e-3
+
+
+def test_mlp_forward_device_arrays(mp):
+    import torch
+    rng = np.random.default_rng(3)
+    net = mp.Mlp(seed=2, max_batch=512)
+    x = _features(rng, 300)
+    a = net.forward(x)
+    b = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("n", [64, 333, 2048])
+def test_mlp_gradients_match_oracle(mp, n):
+    rng = np.random.default_rng(100 + n)
+    net = mp.Mlp(seed=5, max_batch=4096)
+    p = net.get_params().astype(np.float64)
+    x = _features(rng, n)
+    y = rng.uniform(0, 1, (n, 2)).astype(np.float32)
+    loss, g = net.train_step(x, y, lr=0.0, apply=False, want_grads=True)
+    lo, go = omlp.loss_and_grad(p, x, y, rounding=True)
+    assert loss == pytest.approx(lo, rel=1e-4, abs=1e-6)
+    gd, od = omlp.unpack(g.astype(np.float64)), omlp.unpack(go)
+    for k, _ in omlp.SHAPES:
+        err = np.linalg.norm(gd[k] - od[k])
+        assert err <= 1e-2 * np.linalg.norm(od[k]) + 1e-9, (k, err, np.linalg.norm(od[k]))
+    # apply = False leaves the parameters alone
+    np.testing.assert_array_equal(net.get_params(), p.astype(np.float32))
+
+
+def test_adam_step_matches_oracle(mp):
+    rng = np.random.default_rng(8)
+    net = mp.Mlp(seed=9, max_batch=1024)
+    p = net.get_params().astype(np.float64)
+    opt = omlp.Adam(omlp.N_PARAMS, lr=3e-3)
+    for step in range(3):
+        x = _features(rng, 500)
+        y = rng.uniform(0, 1, (500, 2)).astype(np.float32)
+        _, g = net.train_step(x, y, lr=3e-3, apply=True, want_grads=True)
+        p = opt.step(p, g.astype(np.float64))      # Adam on the device's own gradient
+        got = net.get_params().astype(np.float64)
+        assert np.max(np.abs(got - p)) <= 1e-6 + 1e-5 * np.max(np.abs(p)), step
+        p = got
+
+
+def test_mlp_learns_a_separable_rule(mp):
+    """A rule the network can represent (failure iff the mean of the first 16
+    features exceeds 0.5): the training loss falls well below log 2."""
+    rng = np.random.default_rng(21)
+    net = mp.Mlp(seed=1, max_batch=1024)
+    losses = []
+    for _ in range(300):
+        x = _features(rng, 1024)
+        t = (x[:, :16].mean(1) > 0.5).astype(np.float32)
+        y = np.stack([t, 1 - t], 1)
+        loss, _ = net.train_step(x, y, lr=3e-3)
+        losses.append(loss)
+    assert losses[0] > 0.6 and np.mean(losses[-20:]) < 0.2
+
+
+def test_mlp_rejects_oversized_batch(mp):
+    net = mp.Mlp(seed=0, max_batch=128)
+    with pytest.raises(mp.MpapError) as e:
+        net.forward(np.zeros((129, 48), np.float32))
+    assert e.value.status == mp.MPAP_ERR_INVALID_ARG
