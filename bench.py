@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-train-plans", type=int, default=200000,
+                    help="Monte Carlo-labelled candidate plans to train the surrogate on")
+    ap.add_argument("--sur-train-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -255,6 +259,8 @@ def run_gpu(args, rank, world, local):
         out["search_only"] = search_only(arm, stream)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e(arm, args, stream)
+    if rank == 0 and world == 1 and not args.no_surrogate:
+        out["surrogate"] = surrogate_report(args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scenes[:2])
     if world > 1:
@@ -376,6 +382,118 @@ def e2e(arm, args, stream):
     h2d, d2h = arm.io_bytes()
     return {"value": exps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "wall_value": exps / wall}
+
+
+# ------------------------------------------------------------------ surrogate
+SUR_N, SUR_EPS, SUR_TAU, SUR_BATCH = 32000, 0.05, 0.1, 64
+# algorithmic FLOPs per sample of one training step: forward 2 (48*128 + 2*128^2 +
+# 128*2), weight gradients the same, input gradients of layers 2..4 2 (2*128^2 + 128*2)
+MLP_TRAIN_FLOP = 2 * (48 * 128 + 2 * 128 * 128 + 128 * 2) * 2 + 2 * (2 * 128 * 128 + 128 * 2)
+
+
+def _sur_batch(mp, S, ws, cfg, seeds, call_base, rollouts=None):
+    scs = [scenegen.make_scene(cfg, s, query_id=s) for s in seeds]
+    rms = mp.build_roadmaps([mp.scene_spec(sc) for sc in scs])
+    res = mp.search_batch(ws, rms, [mp.make_query(1 << 62, scenegen.LAMBDA, goal_stop=False) for _ in scs])
+    cands = S.collect_candidates(ws, res, 64)
+    mcs = [(rollouts or cfg.mc_rollouts, sc.mc_seed, 0, sc.delta_fx, sc.sigma_fx, sc.shift) for sc in scs]
+    return rms, res, cands, mcs
+
+
+def surrogate_report(args, stream):
+    """Batched search + learned screen versus the plain GPU search on the same 64
+    queries (6D, 32000 samples, 64 candidate goal plans each, 4096-rollout Monte
+    Carlo as judge), at one certified failure bound.  The network is first trained
+    on the GPU on Monte Carlo-labelled candidates of separate training queries."""
+    import torch
+    import paper_1705_02408_gb300 as mp
+    from paper_1705_02408_gb300 import surrogate as S
+    cfg = scenegen.surrogate_config(SUR_N)
+    ws = mp.Workspace(SUR_BATCH * (SUR_N + 2), front_cap=128, max_plans=1 << 25)
+    # training set: candidates of seeds 100001.. until enough plans
+    t0 = time.perf_counter()
+    X, Y, q = [], [], 0
+    while sum(len(x) for x in X) < args.sur_train_plans:
+        seeds = range(100001 + q, 100001 + q + SUR_BATCH)
+        rms, res, cands, mcs = _sur_batch(mp, S, ws, cfg, seeds, 10000)
+        for f, r in zip(S.candidate_features(rms, cands), S.mc_rates(rms, cands, mcs, call_base=10000)):
+            X.append(f); Y.append(r[:, :2])
+        q += SUR_BATCH
+    X, Y = np.concatenate(X)[:args.sur_train_plans], np.concatenate(Y)[:args.sur_train_plans]
+    gen_s = time.perf_counter() - t0
+    net = mp.Mlp(seed=3, max_batch=4096)
+    S.train(net, X, Y, steps=20, batch=4096, lr=2e-3, seed=1)        # warm-up
+    net = mp.Mlp(seed=3, max_batch=4096)
+    mp.profile_reset(); mp.profile_enable(True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = S.train(net, X, Y, steps=args.sur_train_steps, batch=4096, lr=2e-3, seed=1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mp.profile_enable(False)
+    kern = mp.profile_read()
+    train_ms = e0.elapsed_time(e1)
+    gl, gms = kern.get("k_gemm_tc", (0, 0.0))
+    flop = MLP_TRAIN_FLOP * 4096.0 * args.sur_train_steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = peaks.get("bf16_tflops", 1900.0)
+    train = {"plans": int(len(X)), "queries": q, "label_rollouts": cfg.mc_rollouts,
+             "generate_s": round(gen_s, 2), "steps": args.sur_train_steps, "batch": 4096,
+             "loss_first": float(losses[0]), "loss_last50": float(np.mean(losses[-50:])),
+             "ms_per_step": train_ms / args.sur_train_steps,
+             "samples_per_s": 4096.0 * args.sur_train_steps / (train_ms / 1e3),
+             "kernel_ms_per_step": {k: round(v[1] / args.sur_train_steps, 4) for k, v in sorted(kern.items())},
+             "roofline": {"kernel": "k_gemm_tc", "bound": "tensor",
+                          "achieved": flop / (gms / 1e3) / 1e12 if gms else None,
+                          "peak": peak, "unit": "TFLOP/s",
+                          "frac": (flop / (gms / 1e3) / 1e12) / peak if gms else None,
+                          "launches": int(gl), "traffic": None,
+                          "note": "algorithmic bf16 FLOPs of the 11 products of a step over the tensor-core "
+                                  "kernel's time; 128-wide layers leave it latency-bound",
+                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)" if peaks else "fallback"}}
+    # evaluation: 64 held-out queries, plain vs screened; wall time from the
+    # search to the certified plan of every query (host decisions between rounds)
+    ev = {}
+    seeds = range(1, 1 + SUR_BATCH)
+    rms, res, cands, mcs = _sur_batch(mp, S, ws, cfg, seeds, 0)
+    qs = [mp.make_query(1 << 62, scenegen.LAMBDA, goal_stop=False) for _ in rms]
+    sel = {}
+    for mode in ("plain", "screened", "plain", "screened"):      # second pass is the timed one
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = mp.search_batch(ws, rms, qs)
+        cands = S.collect_candidates(ws, res, 64)
+        if mode == "plain":
+            orders = [np.arange(len(c["paths"])) if c else np.zeros(0, np.int64) for c in cands]
+        else:
+            pf = S.predicted_failure(net, S.candidate_features(rms, cands))
+            orders = [S.screened_order(p, SUR_TAU) for p in pf]
+        out = S.certify_in_order(rms, cands, mcs, orders, SUR_EPS)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        sel[mode] = out
+        ev[mode] = {"ms_per_batch": dt * 1e3, "ms_per_query": dt * 1e3 / len(rms),
+                    "mc_calls": int(out.mc_calls.sum()), "mc_rounds": out.rounds,
+                    "mc_rollouts": int(out.mc_calls.sum()) * cfg.mc_rollouts,
+                    "solved": int((out.chosen >= 0).sum())}
+    a, b = sel["plain"], sel["screened"]
+    ratios = [cands[i]["cost"][b.chosen[i]] / cands[i]["cost"][a.chosen[i]]
+              for i in range(len(rms)) if a.chosen[i] >= 0]
+    return {"workload": f"6D double integrator, {SUR_N} samples, 30 boxes, 32^3 grid, twice the 6D MC noise, "
+                        f"beta unbounded, exhaustive search (no goal stop), 64 candidates/query, "
+                        f"{cfg.mc_rollouts}-rollout MC judge",
+            "queries": len(rms), "certified_failure_bound": SUR_EPS, "screen_threshold": SUR_TAU,
+            "plain": ev["plain"], "screened": ev["screened"],
+            "mc_calls_ratio": ev["screened"]["mc_calls"] / max(1, ev["plain"]["mc_calls"]),
+            "speedup": ev["plain"]["ms_per_batch"] / ev["screened"]["ms_per_batch"],
+            "cost_ratio_mean": float(np.mean(ratios)) if ratios else None,
+            "cost_ratio_max": float(np.max(ratios)) if ratios else None,
+            "train": train}
 
 
 # ------------------------------------------------------------------ CPU oracle

@@ -216,6 +216,16 @@ def scaled_config(dim_kind: int, n: int) -> Config:
     return replace(base, name=f"{base.name}_n{n}", n=int(n), r=float(np.float32(r)))
 
 
+def surrogate_config(n: int = 32000) -> Config:
+    """Workload of the certification surrogate: the double integrator resized to
+    n samples (radius as scaled_config) with twice the 6D Monte Carlo noise, so
+    that the cheapest goal plan often fails a 5% bound and the screen has
+    alternatives to choose among; 4096 rollouts."""
+    base = scaled_config(DIM_DI6, n)
+    return replace(base, name=f"6d_sur_n{n}", sigma_max=2 * CONFIGS["6d"].sigma_max,
+                   sigma_min=2 * CONFIGS["6d"].sigma_min, mc_rollouts=4096)
+
+
 def batch_specs(count: int = 256, seed: int = 7, n_lo: int = 1000, n_hi: int = 32000):
     """(dim_kind, n, scene_seed) for the batched workload: n log-uniform in
     [n_lo, n_hi], dimension uniform over {2d, 3d, 6d}."""
