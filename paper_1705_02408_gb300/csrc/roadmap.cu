@@ -91,7 +91,10 @@ struct BuildJob {
   uint8_t* is_goal;
   uint32_t* goal_list;
   int GC;                  // grid cells per axis for the Near scan
-  float R;                 // conservative neighbour radius
+  float R;                 // conservative neighbour radius (grid units: the grid spans [0, 1))
+  // grid coordinate of a node: (p + bin_shift v - bin_lo) * bin_inv per axis (6D:
+  // the backward point p - T v / 2); a source queries around p - bin_shift v
+  float bin_shift, bin_lo, bin_inv;
   uint32_t* cell_cnt;      // [NC+1]
   uint32_t* cell_start;    // [NC+1]
   uint32_t* cell_of;       // [V]
@@ -273,12 +276,22 @@ __device__ __forceinline__ int cell_coord(float p, int GC) {
   return c < 0 ? 0 : (c > GC - 1 ? GC - 1 : c);
 }
 
+// Grid coordinate of position p with velocity w along one axis.
+__device__ __forceinline__ float bin_q(const BuildJob& J, float p, float w, float shift) {
+  if (J.g.dim == 6) p = __fadd_rn(p, __fmul_rn(shift, w));
+  return __fmul_rn(__fsub_rn(p, J.bin_lo), J.bin_inv);
+}
+
 __global__ void k_bin_count(const BuildJob* __restrict__ jobs) {
   const BuildJob& J = jobs[blockIdx.y];
   const int GC = J.GC;
+  const bool six = J.g.dim == 6;
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < J.V; v += gridDim.x * blockDim.x) {
     uint32_t cell = 0;
-    for (int i = J.g.dp - 1; i >= 0; --i) cell = cell * GC + cell_coord(J.x[(size_t)i * J.V + v], GC);
+    for (int i = J.g.dp - 1; i >= 0; --i) {
+      const float w = six ? J.x[(size_t)(3 + i) * J.V + v] : 0.0f;
+      cell = cell * GC + cell_coord(bin_q(J, J.x[(size_t)i * J.V + v], w, J.bin_shift), GC);
+    }
     J.cell_of[v] = cell;
     atomicAdd(&J.cell_cnt[cell], 1u);
   }
@@ -392,7 +405,7 @@ __global__ void __launch_bounds__(kEdgeWarps * 32, 4) k_edges(const BuildJob* __
   int clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
 #pragma unroll
   for (int i = 0; i < DP; ++i) {
-    ctr[i] = (DIM == 6) ? __fadd_rn(a[i], __fmul_rn(a[3 + i], g.T)) : a[i];
+    ctr[i] = bin_q(J, a[i], a[3 + i], -J.bin_shift);
     clo[i] = cell_coord(ctr[i] - R, GC);
     chi[i] = cell_coord(ctr[i] + R, GC);
   }
@@ -608,14 +621,30 @@ struct Carve {
   }
 };
 
-void neighbour_ball(int dim, float r, float T, int dp, float& R, int& GC) {
+// Conservative neighbour ball of the Near scan and the grid it runs on.  6D:
+// per axis the minimum control energy of the fixed-time double-integrator
+// connection splits into two non-negative parts,
+//   J = 12 |(p1 - T v1 / 2) - (p0 + T v0 / 2)|^2 / T^3 + |v1 - v0|^2 / T,
+// so Cost < r implies that the backward point p1 - T v1 / 2 of the target lies
+// within sqrt((r - T) T^3 / 12) of the forward point p0 + T v0 / 2 of the source.
+// Nodes are binned by their backward points, which lie in [-T/2, 1 + T/2] for
+// |v| <= 1 (others are clamped into the border cells); the grid spans that range.
+// The budget carries a margin far above binary32 rounding of the exact test.
+void neighbour_ball(int dim, float r, float T, int dp, float& R, int& GC, float& shift, float& lo, float& inv) {
   if (dim == 6) {
     const double budget = std::max(0.0, ((double)r - (double)T) * 1.01 + 0.01);
     const double Td = (double)T;
-    R = (float)(std::sqrt(budget * Td * Td * Td / 3.0) * 1.001 + 1e-6);
+    const double span = 1.0 + Td;
+    shift = (float)(-0.5 * Td);
+    lo = (float)(-0.5 * Td);
+    inv = (float)(1.0 / span);
+    R = (float)((std::sqrt(budget * Td * Td * Td / 12.0) * 1.001 + 1e-6) / span * 1.0001 + 1e-6);
     GC = (int)std::floor(4.0 / std::max((double)R, 1e-3));
-    GC = std::min(std::max(GC, 1), 32);
+    GC = std::min(std::max(GC, 1), 64);
   } else {
+    shift = 0.0f;
+    lo = 0.0f;
+    inv = 1.0f;
     R = (float)((double)r * 1.001 + 1e-6);
     GC = (int)std::floor(2.0 / std::max((double)R, 1e-4));
     GC = std::min(std::max(GC, 1), dp == 2 ? 256 : 64);
@@ -803,7 +832,7 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     J.goal_r2 = sp.goal_radius * sp.goal_radius;
     J.is_goal = rm->is_goal;
     J.goal_list = rm->goal_list;
-    neighbour_ball(rm->dim, sp.r, sp.T, dp, J.R, J.GC);
+    neighbour_ball(rm->dim, sp.r, sp.T, dp, J.R, J.GC, J.bin_shift, J.bin_lo, J.bin_inv);
     ncells[j] = dp == 2 ? (size_t)J.GC * J.GC : (size_t)J.GC * J.GC * J.GC;
     J.fwd_ptr = rm->fwd_ptr;
     J.rev_ptr = rm->rev_ptr;
