@@ -46,7 +46,7 @@ WORKLOAD = "6D double integrator, 16000 samples, 30 boxes, 32^3 grid, 4096 MC ro
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mpap", choices=["mpap", "reference"])
     ap.add_argument("--queries", type=int, default=64, help="queries per step per GPU")
@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--sur-train-plans", type=int, default=200000,
                     help="Monte Carlo-labelled candidate plans to train the surrogate on")
     ap.add_argument("--sur-train-steps", type=int, default=2000)
@@ -97,7 +99,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -195,6 +197,17 @@ def run_gpu(args, rank, world, local):
         raise SystemExit("missing beta for some scenes: run python -m oracle.calibrate --seeds N")
     arm = GpuArm(scenes, device)
     stream = torch.cuda.current_stream()
+    # launch shapes from the autotuner (edge block size; select/prune grids)
+    tuning = None
+    if not args.no_autotune:
+        specs = [mp.scene_spec(s, device_inputs=d) for s, d in zip(arm.scenes, arm.dev_inputs)]
+        tb, b_ms, arm.rms = mp.autotune_build(specs, reps=1)
+        ts, s_ms = mp.autotune_search(arm.ws, arm.rms, arm.queries, reps=1)
+        if ts["front_cap"] > arm.ws.front_cap:
+            arm.ws = mp.Workspace(arm.ws.total_nodes, front_cap=ts["front_cap"], max_plans=1 << 25)
+        tuning = {"edge_warps": tb["edge_warps"], "select_blocks_per_sm": ts["select_blocks_per_sm"],
+                  "prune_blocks_per_sm": ts["prune_blocks_per_sm"], "front_cap": arm.ws.front_cap,
+                  "tuned_build_ms": round(b_ms, 3), "tuned_search_ms": round(s_ms, 3)}
 
     def barrier():
         if world > 1:
@@ -240,7 +253,8 @@ def run_gpu(args, rank, world, local):
                       "lambda": scenegen.LAMBDA, "beta": "60th percentile of straight-line heuristic",
                       "parallelism": f"queries sharded over {world} GPU(s)"},
            "ms_per_query": ms / per_query,
-           "gpu_launches": int(launches)}
+           "gpu_launches": int(launches),
+           "tuning": tuning}
     # breakdown from the live kernel timers (timed region)
     search_k = {"k_fill_qid", "k_init", "k_select", "k_prune", "k_end", "k_finalize"}
     certify_k = {"k_mc_checkpoints", "k_mc_rollouts"}
@@ -259,6 +273,8 @@ def run_gpu(args, rank, world, local):
         out["search_only"] = search_only(arm, stream)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e(arm, args, stream)
+    if rank == 0 and world == 1 and not args.no_mixed:
+        out["mixed_batch"] = mixed_report(args, stream)
     if rank == 0 and world == 1 and not args.no_surrogate:
         out["surrogate"] = surrogate_report(args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -382,6 +398,81 @@ def e2e(arm, args, stream):
     h2d, d2h = arm.io_bytes()
     return {"value": exps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "wall_value": exps / wall}
+
+
+# ------------------------------------------------------------------ mixed batch
+def mixed_report(args, stream, count=256):
+    """The batched workload: 256 queries, each on its own roadmap (dimension
+    uniform over 2D/3D/6D, n log-uniform in [1000, 32000], obstacles and grids
+    seeded per query), built in one call, searched in one lock-step launch and
+    certified in one launch, with launch shapes from the autotuner."""
+    import torch
+    import paper_1705_02408_gb300 as mp
+    calib = scenegen.load_calibration()
+    scenes = []
+    for d, n, s in scenegen.batch_specs(count):
+        cfg = scenegen.scaled_config(d, n)
+        sc = scenegen.make_scene(cfg, s, query_id=s)
+        key = scenegen.calib_key(cfg, s)
+        if key not in calib:
+            return {"skipped": f"no stored beta for {key}: run python -m oracle.calibrate --batch {count}"}
+        sc.extra["beta"] = calib[key]["beta"]
+        scenes.append(sc)
+    specs = [mp.scene_spec(sc) for sc in scenes]
+    queries = [mp.make_query(sc.extra["beta"], scenegen.LAMBDA) for sc in scenes]
+    mcs = [(sc.cfg.mc_rollouts, sc.mc_seed, 0, sc.delta_fx, sc.sigma_fx, sc.shift) for sc in scenes]
+    total = sum(sc.cfg.n + 2 for sc in scenes)
+    t0 = time.perf_counter()
+    tb, build_ms, rms = mp.autotune_build(specs, reps=1)
+    ws = mp.Workspace(total, front_cap=256, max_plans=1 << 27)
+    ts, search_ms = mp.autotune_search(ws, rms, queries, reps=1)
+    tune_s = time.perf_counter() - t0
+    ws = mp.Workspace(total, front_cap=max(ts["front_cap"], 64), max_plans=1 << 27)
+
+    def step():
+        nonlocal rms
+        rms = mp.build_roadmaps(specs, rms=rms)
+        res = mp.search_batch(ws, rms, queries)
+        mp.certify_batch([rms[i] for i in range(count) if res[i].status == 0],
+                         [r.path for r in res if r.status == 0],
+                         [mcs[i] for i in range(count) if res[i].status == 0])
+        return res
+    for _ in range(2):
+        step()
+    reps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    exps = 0
+    for _ in range(reps):
+        res = step()
+        exps += sum(r.expansions for r in res)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    # search only: batched vs one call per query, same roadmaps
+    e0.record(stream)
+    resb = mp.search_batch(ws, rms, queries)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    ws1 = mp.Workspace(max(sc.cfg.n + 2 for sc in scenes), front_cap=max(ts["front_cap"], 64),
+                       max_plans=1 << 24)
+    e0.record(stream)
+    for rm, q in zip(rms, queries):
+        mp.search(ws1, rm, q.beta, lam=scenegen.LAMBDA)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    return {"workload": f"{count} queries, one roadmap each: dimension uniform over 2D/3D/6D, n log-uniform in "
+                        f"[1000, 32000] (total {total} nodes), per-query obstacles and grids, beta = stored "
+                        f"60th percentile, MC rollouts 1024 (2D/3D) / 4096 (6D)",
+            "ms_per_step": ms, "ms_per_query": ms / count, "expansions_per_s": exps / reps / (ms / 1e3),
+            "solved": sum(1 for r in res if r.status == 0),
+            "search_only": {"batched_ms_per_query": ms_b / count, "plain_ms_per_query": ms_p / count,
+                            "speedup": ms_p / ms_b},
+            "tuning": {"build": tb, "build_ms": build_ms, "search": ts, "search_ms": search_ms,
+                       "autotune_s": round(tune_s, 2)}}
 
 
 # ------------------------------------------------------------------ surrogate

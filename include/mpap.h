@@ -274,6 +274,51 @@ int32_t mpap_certify_noalloc(const mpap_roadmap* rm, const uint32_t* path, uint3
                              const mpap_mc_params* mc, mpap_cert* out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Launch-shape tuning (not in the paper; serves batched deployment).  The
+ * library keeps a table of launch shapes keyed by (dimension, node-count bucket
+ * floor(log2 V)); dim_kind 0 keys a batch that mixes dimensions, V the largest
+ * roadmap of a batch.  mpap_build_roadmaps reads edge_warps for each dimension
+ * group of its batch; mpap_search / mpap_search_batch read select and prune
+ * blocks per SM for the batch key.  Keys without an entry use the defaults
+ * (8, 16, 16).  The results of every call are identical for every valid shape;
+ * only the time changes.  The table is process-wide and guarded by a mutex.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  uint32_t edge_warps;            /* warps per block of the edge kernel: 4 or 8 */
+  uint32_t select_blocks_per_sm;  /* grid of the group-selection kernel: 1 .. 64 */
+  uint32_t prune_blocks_per_sm;   /* grid of the candidate-pull/prune kernel: 1 .. 64 */
+  uint32_t front_cap;             /* advisory front slot size for mpap_workspace_create */
+} mpap_tuning;
+
+/* The entry the library uses for (dim_kind, V): a stored one or the defaults. */
+int32_t mpap_tuning_get(int32_t dim_kind, uint32_t V, mpap_tuning* out);
+/* Stores t for the key of (dim_kind, V); MPAP_ERR_INVALID_ARG for an invalid shape. */
+int32_t mpap_tuning_set(int32_t dim_kind, uint32_t V, const mpap_tuning* t);
+int32_t mpap_tuning_clear(void);
+/* Copies up to cap stored entries (keys as dim_kind and bucket) and sets *n to
+ * the number stored (MPAP_ERR_INVALID_ARG if that exceeds cap). */
+int32_t mpap_tuning_export(uint32_t cap, int32_t* dim_kind, uint32_t* bucket, mpap_tuning* t, uint32_t* n);
+
+/* Grid search of the edge kernel's block size (4, 8 warps) on one batched build
+ * of these n roadmaps: each candidate builds into rms (handles as for
+ * mpap_build_roadmaps) `reps` times after one untimed build, timed with CUDA
+ * events on `stream`.  The fastest is stored for every (dimension, bucket) group
+ * of the batch; *best and *best_ms (per build) describe it. */
+int32_t mpap_autotune_build(uint32_t n, const mpap_scene* scenes, const mpap_roadmap_params* params,
+                            mpap_roadmap** rms, uint32_t reps, mpap_tuning* best, double* best_ms,
+                            void* stream);
+
+/* Grid search of the select and prune grids (1, 2, 4, 8, 16, 32 blocks per SM
+ * each) on one batched search of these queries, `reps` timed searches per
+ * candidate after an untimed one.  Stores the fastest for the batch key and
+ * sets best->front_cap to twice the largest front any node held during the
+ * search, rounded up to a power of two (at least 32).  Fails with MPAP_ERR_CUDA
+ * (and stores nothing) if two shapes give different results. */
+int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs,
+                             uint32_t nq, uint32_t reps, mpap_tuning* best, double* best_ms,
+                             void* stream);
+
+/* ---------------------------------------------------------------------------
  * Candidate plans and the certification surrogate.
  *
  * Alg. 3 ends by collecting P_candidates, every plan stored at a goal node, and

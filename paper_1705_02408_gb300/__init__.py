@@ -34,7 +34,8 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_certify", "mpap_certify_batch", "mpap_certify_noalloc", "mpap_profile_enable", "mpap_profile_reset",
            "mpap_launch_count", "mpap_profile_read", "mpap_search_candidates", "mpap_plan_features",
            "mpap_mlp_create", "mpap_mlp_free", "mpap_mlp_get_params", "mpap_mlp_set_params",
-           "mpap_mlp_forward", "mpap_mlp_train_step"]
+           "mpap_mlp_forward", "mpap_mlp_train_step", "mpap_tuning_get", "mpap_tuning_set",
+           "mpap_tuning_clear", "mpap_tuning_export", "mpap_autotune_build", "mpap_autotune_search"]
 
 
 class mpap_scene(C.Structure):
@@ -65,6 +66,11 @@ class mpap_mc_params(C.Structure):
     _fields_ = [("rollouts", C.c_uint32), ("call_id", C.c_uint32), ("seed", C.c_uint64),
                 ("delta_fx", C.c_int64), ("sigma_fx", C.POINTER(C.c_int32)),
                 ("shift", C.POINTER(C.c_int32))]
+
+
+class mpap_tuning(C.Structure):
+    _fields_ = [("edge_warps", C.c_uint32), ("select_blocks_per_sm", C.c_uint32),
+                ("prune_blocks_per_sm", C.c_uint32), ("front_cap", C.c_uint32)]
 
 
 class mpap_cert(C.Structure):
@@ -148,6 +154,20 @@ def lib():
         L.mpap_mlp_forward.argtypes = [P, P, C.c_uint32, P, i32, P]
         L.mpap_mlp_train_step.restype = i32
         L.mpap_mlp_train_step.argtypes = [P, P, P, C.c_uint32, C.c_float, i32, C.POINTER(C.c_float), P, i32, P]
+        TP = C.POINTER(mpap_tuning)
+        L.mpap_tuning_get.restype = i32
+        L.mpap_tuning_get.argtypes = [i32, C.c_uint32, TP]
+        L.mpap_tuning_set.restype = i32
+        L.mpap_tuning_set.argtypes = [i32, C.c_uint32, TP]
+        L.mpap_tuning_clear.restype = i32
+        L.mpap_tuning_export.restype = i32
+        L.mpap_tuning_export.argtypes = [C.c_uint32, P, P, P, C.POINTER(C.c_uint32)]
+        L.mpap_autotune_build.restype = i32
+        L.mpap_autotune_build.argtypes = [C.c_uint32, C.POINTER(mpap_scene), C.POINTER(mpap_roadmap_params),
+                                          C.POINTER(P), C.c_uint32, TP, C.POINTER(C.c_double), P]
+        L.mpap_autotune_search.restype = i32
+        L.mpap_autotune_search.argtypes = [P, C.POINTER(P), C.POINTER(mpap_query), C.c_uint32, C.c_uint32, TP,
+                                           C.POINTER(C.c_double), P]
         _lib = L
     return _lib
 
@@ -298,6 +318,33 @@ def _params(n, seed, r, x_init, x_goal, goal_radius, T, M, query_id):
     for i in range(6):
         p.x_init[i] = float(x_init[i]); p.x_goal[i] = float(x_goal[i])
     return p
+
+
+def _batch_structs(specs):
+    n = len(specs)
+    scenes = (mpap_scene * n)()
+    params = (mpap_roadmap_params * n)()
+    keep = []
+    for i, sp in enumerate(specs):
+        sc, k = make_scene_struct(sp["dim_kind"], sp["box_lo"], sp["box_hi"], sp["grid"], sp["grid_G"],
+                                  sp.get("n_f", 12), sp.get("K", 24))
+        scenes[i] = sc
+        keep.append(k)
+        params[i] = _params(sp["n"], sp["seed"], sp["r"], sp["x_init"], sp["x_goal"], sp.get("goal_radius", 0.05),
+                            sp.get("T", 0.25), sp.get("M", 16), sp.get("query_id", 0))
+    return scenes, params, keep
+
+
+def _adopt(specs, rms, hs):
+    out = []
+    for i in range(len(specs)):
+        if rms[i] is not None:
+            rms[i].h = C.c_void_p(hs[i]) if hs[i] else None
+            rms[i].M = specs[i].get("M", 16)
+            out.append(rms[i])
+        else:
+            out.append(Roadmap(C.c_void_p(hs[i]), specs[i].get("M", 16), specs[i].get("K", 24)) if hs[i] else None)
+    return out
 
 
 def build_roadmaps(specs, rms=None, stream=None):
@@ -607,3 +654,65 @@ class Mlp:
         _check(lib().mpap_mlp_train_step(self.h, xp, yp, n, float(lr), 1 if apply else 0, C.byref(loss), gp,
                                          1 if dev else 0, _stream(stream)), "mpap_mlp_train_step")
         return loss.value, g
+
+
+# ---------------------------------------------------------------------------
+# Launch-shape tuning
+# ---------------------------------------------------------------------------
+def _tuning_dict(t):
+    return dict(edge_warps=t.edge_warps, select_blocks_per_sm=t.select_blocks_per_sm,
+                prune_blocks_per_sm=t.prune_blocks_per_sm, front_cap=t.front_cap)
+
+
+def tuning_get(dim_kind, V):
+    t = mpap_tuning()
+    _check(lib().mpap_tuning_get(int(dim_kind), int(V), C.byref(t)), "mpap_tuning_get")
+    return _tuning_dict(t)
+
+
+def tuning_set(dim_kind, V, edge_warps=8, select_blocks_per_sm=16, prune_blocks_per_sm=16, front_cap=64):
+    t = mpap_tuning(edge_warps, select_blocks_per_sm, prune_blocks_per_sm, front_cap)
+    _check(lib().mpap_tuning_set(int(dim_kind), int(V), C.byref(t)), "mpap_tuning_set")
+
+
+def tuning_clear():
+    lib().mpap_tuning_clear()
+
+
+def tuning_export():
+    """[(dim_kind, bucket, tuning dict)] of the stored entries (bucket = floor(log2 V))."""
+    n = C.c_uint32()
+    lib().mpap_tuning_export(0, None, None, None, C.byref(n))
+    k = n.value
+    dims = np.zeros(max(k, 1), np.int32)
+    bks = np.zeros(max(k, 1), np.uint32)
+    ts = (mpap_tuning * max(k, 1))()
+    _check(lib().mpap_tuning_export(k, dims.ctypes.data_as(C.c_void_p), bks.ctypes.data_as(C.c_void_p),
+                                    C.cast(ts, C.c_void_p), C.byref(n)), "mpap_tuning_export")
+    return [(int(dims[i]), int(bks[i]), _tuning_dict(ts[i])) for i in range(k)]
+
+
+def autotune_build(specs, rms=None, reps=2, stream=None):
+    """mpap_autotune_build on a batch of build specs; returns (tuning, ms per build, roadmaps)."""
+    n = len(specs)
+    scenes, params, keep = _batch_structs(specs)
+    rms = list(rms) if rms is not None else [None] * n
+    hs = (C.c_void_p * n)(*[rm.h.value if rm is not None and rm.h else None for rm in rms])
+    t = mpap_tuning()
+    ms = C.c_double()
+    rc = lib().mpap_autotune_build(n, scenes, params, hs, int(reps), C.byref(t), C.byref(ms), _stream(stream))
+    out = _adopt(specs, rms, hs)
+    _check(rc, "mpap_autotune_build")
+    return _tuning_dict(t), ms.value, out
+
+
+def autotune_search(ws, rms, queries, reps=2, stream=None):
+    """mpap_autotune_search on a batch of queries; returns (tuning, ms per search)."""
+    nq = len(rms)
+    hs = (C.c_void_p * nq)(*[rm.h for rm in rms])
+    qs = (mpap_query * nq)(*queries)
+    t = mpap_tuning()
+    ms = C.c_double()
+    _check(lib().mpap_autotune_search(ws.h, hs, qs, nq, int(reps), C.byref(t), C.byref(ms), _stream(stream)),
+           "mpap_autotune_search")
+    return _tuning_dict(t), ms.value

@@ -31,6 +31,11 @@ int32_t mlp_set_params(mpap_mlp* n, const float* params, cudaStream_t st);
 int32_t mlp_forward(mpap_mlp* nt, const float* x, uint32_t n, float* prob, int32_t mem, cudaStream_t st);
 int32_t mlp_train_step(mpap_mlp* nt, const float* x, const float* y, uint32_t n, float lr, int32_t apply,
                        float* loss_out, float* grads_out, int32_t mem, cudaStream_t st);
+int32_t tuning_set(int dim, uint32_t V, const mpap_tuning& t);
+void tuning_clear();
+int32_t tuning_export(uint32_t cap, int32_t* dims, uint32_t* buckets, mpap_tuning* t, uint32_t* n);
+void batch_key(mpap_roadmap* const* rms, uint32_t nq, int& dim, uint32_t& V);
+uint32_t workspace_last_max_front(const mpap_workspace* ws);
 }  // namespace mpap
 
 using mpap::set_error;
@@ -82,6 +87,47 @@ int32_t check_conn(float r, float T, int M, int dim) {
 
 }  // namespace
 
+namespace {
+
+int32_t batch_specs(uint32_t n, const mpap_scene* scenes, const mpap_roadmap_params* params,
+                    std::vector<mpap::BuildSpec>& specs) {
+  specs.resize(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    int32_t rc = check_scene(&scenes[i]);
+    if (!rc) rc = check_conn(params[i].r, params[i].T_edge, params[i].M, scenes[i].dim_kind);
+    if (!rc && (params[i].n == 0 || params[i].n > 0x0FFFFFFFu)) {
+      set_error("n must be in [1, 2^28)");
+      rc = MPAP_ERR_INVALID_ARG;
+    }
+    if (rc) return rc;
+    const mpap_roadmap_params& p = params[i];
+    specs[i] = mpap::BuildSpec{&scenes[i], &p, nullptr, 0, p.r, p.T_edge, p.goal_radius, p.M};
+  }
+  return MPAP_OK;
+}
+
+// Device milliseconds per call of `reps` calls of f() after one untimed call.
+template <typename F>
+int32_t time_reps(cudaStream_t st, uint32_t reps, F f, double* ms) {
+  int32_t rc = f();
+  if (rc < 0) return rc;
+  cudaEvent_t e0, e1;
+  MPAP_CK(cudaEventCreate(&e0));
+  MPAP_CK(cudaEventCreate(&e1));
+  cudaEventRecord(e0, st);
+  for (uint32_t r = 0; r < reps && rc >= 0; ++r) rc = f();
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float t = 0.0f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = (double)t / (double)(reps ? reps : 1);
+  return rc < 0 ? rc : MPAP_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* mpap_status_string(int32_t s) {
@@ -118,24 +164,16 @@ int32_t mpap_build_roadmap(const mpap_scene* scene, const mpap_roadmap_params* p
   return mpap::build_roadmaps_impl(1, &sp, out, S(stream));
 }
 
+
 int32_t mpap_build_roadmaps(uint32_t n, const mpap_scene* scenes, const mpap_roadmap_params* params,
                             mpap_roadmap** rms, void* stream) {
   if (n && (!scenes || !params || !rms)) {
     set_error("null argument");
     return MPAP_ERR_INVALID_ARG;
   }
-  std::vector<mpap::BuildSpec> specs(n);
-  for (uint32_t i = 0; i < n; ++i) {
-    int32_t rc = check_scene(&scenes[i]);
-    if (!rc) rc = check_conn(params[i].r, params[i].T_edge, params[i].M, scenes[i].dim_kind);
-    if (!rc && (params[i].n == 0 || params[i].n > 0x0FFFFFFFu)) {
-      set_error("n must be in [1, 2^28)");
-      rc = MPAP_ERR_INVALID_ARG;
-    }
-    if (rc) return rc;
-    const mpap_roadmap_params& p = params[i];
-    specs[i] = mpap::BuildSpec{&scenes[i], &p, nullptr, 0, p.r, p.T_edge, p.goal_radius, p.M};
-  }
+  std::vector<mpap::BuildSpec> specs;
+  int32_t rc = batch_specs(n, scenes, params, specs);
+  if (rc) return rc;
   return mpap::build_roadmaps_impl(n, specs.data(), rms, S(stream));
 }
 
@@ -362,6 +400,144 @@ int32_t mpap_mlp_train_step(mpap_mlp* net, const float* x, const float* y, uint3
     return MPAP_ERR_INVALID_ARG;
   }
   return mpap::mlp_train_step(net, x, y, n, lr, apply, loss, grads, mem, S(stream));
+}
+
+int32_t mpap_tuning_get(int32_t dim_kind, uint32_t V, mpap_tuning* out) {
+  if (!out) {
+    set_error("tuning_get: null output");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  *out = mpap::tuning_for(dim_kind, V);
+  return MPAP_OK;
+}
+
+int32_t mpap_tuning_set(int32_t dim_kind, uint32_t V, const mpap_tuning* t) {
+  if (!t) {
+    set_error("tuning_set: null entry");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::tuning_set(dim_kind, V, *t);
+}
+
+int32_t mpap_tuning_clear(void) {
+  mpap::tuning_clear();
+  return MPAP_OK;
+}
+
+int32_t mpap_tuning_export(uint32_t cap, int32_t* dim_kind, uint32_t* bucket, mpap_tuning* t, uint32_t* n) {
+  if (!n) {
+    set_error("tuning_export: null count");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::tuning_export(cap, dim_kind, bucket, t, n);
+}
+
+int32_t mpap_autotune_build(uint32_t n, const mpap_scene* scenes, const mpap_roadmap_params* params,
+                            mpap_roadmap** rms, uint32_t reps, mpap_tuning* best, double* best_ms, void* stream) {
+  if (!n || !scenes || !params || !rms || !best || !best_ms || reps == 0) {
+    set_error("autotune_build: null argument, empty batch or zero reps");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  std::vector<mpap::BuildSpec> specs;
+  int32_t rc = batch_specs(n, scenes, params, specs);
+  if (rc) return rc;
+  // the (dimension, largest V) key of every dimension group of the batch
+  std::vector<std::pair<int, uint32_t>> keys;
+  for (int d : {2, 3, 6}) {
+    uint32_t vmax = 0;
+    for (uint32_t i = 0; i < n; ++i)
+      if (scenes[i].dim_kind == d) vmax = std::max(vmax, params[i].n + 2u);
+    if (vmax) keys.push_back({d, vmax});
+  }
+  const cudaStream_t st = S(stream);
+  double best_t = 1e300;
+  uint32_t best_w = 8;
+  for (uint32_t warps : {4u, 8u}) {
+    for (const auto& k : keys) {
+      mpap_tuning t = mpap::tuning_for(k.first, k.second);
+      t.edge_warps = warps;
+      mpap::tuning_set(k.first, k.second, t);
+    }
+    double ms = 0.0;
+    rc = time_reps(st, reps, [&] { return mpap::build_roadmaps_impl(n, specs.data(), rms, st); }, &ms);
+    if (rc) return rc;
+    if (ms < best_t) {
+      best_t = ms;
+      best_w = warps;
+    }
+  }
+  for (const auto& k : keys) {
+    mpap_tuning t = mpap::tuning_for(k.first, k.second);
+    t.edge_warps = best_w;
+    mpap::tuning_set(k.first, k.second, t);
+  }
+  *best = mpap::tuning_for(keys[0].first, keys[0].second);
+  *best_ms = best_t;
+  return MPAP_OK;
+}
+
+int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs, uint32_t nq,
+                             uint32_t reps, mpap_tuning* best, double* best_ms, void* stream) {
+  if (!ws || !nq || !rms || !qs || !best || !best_ms || reps == 0) {
+    set_error("autotune_search: null argument, empty batch or zero reps");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  int kdim = 0;
+  uint32_t kV = 0;
+  mpap::batch_key(rms, nq, kdim, kV);
+  const mpap_tuning base = mpap::tuning_for(kdim, kV);
+  const cudaStream_t st = S(stream);
+  std::vector<std::vector<uint32_t>> paths(nq, std::vector<uint32_t>(4096));
+  std::vector<mpap_result> outs(nq), ref;
+  auto run = [&] {
+    for (uint32_t i = 0; i < nq; ++i) {
+      outs[i] = mpap_result{};
+      outs[i].path = paths[i].data();
+      outs[i].path_cap = 4096;
+    }
+    return mpap::search_batch_impl(ws, rms, qs, nq, outs.data(), st);
+  };
+  double best_t = 1e300;
+  mpap_tuning bt = base;
+  uint32_t max_front = 1;
+  const uint32_t grids[] = {1, 2, 4, 8, 16, 32};
+  for (uint32_t sel : grids) {
+    for (uint32_t pru : grids) {
+      mpap_tuning t = base;
+      t.select_blocks_per_sm = sel;
+      t.prune_blocks_per_sm = pru;
+      mpap::tuning_set(kdim, kV, t);
+      double ms = 0.0;
+      const int32_t rc = time_reps(st, reps, run, &ms);
+      if (rc < 0) {
+        mpap::tuning_set(kdim, kV, base);
+        return rc;
+      }
+      if (ref.empty()) {
+        ref = outs;
+      } else {
+        for (uint32_t i = 0; i < nq; ++i)
+          if (outs[i].status != ref[i].status || outs[i].cost != ref[i].cost || outs[i].h != ref[i].h ||
+              outs[i].expansions != ref[i].expansions) {
+            mpap::tuning_set(kdim, kV, base);
+            set_error("autotune_search: query %u differs between launch shapes", i);
+            return MPAP_ERR_CUDA;
+          }
+      }
+      max_front = std::max(max_front, mpap::workspace_last_max_front(ws));
+      if (ms < best_t) {
+        best_t = ms;
+        bt = t;
+      }
+    }
+  }
+  uint32_t fc = 32;
+  while (fc < 2 * max_front) fc <<= 1;
+  bt.front_cap = fc;
+  mpap::tuning_set(kdim, kV, bt);
+  *best = bt;
+  *best_ms = best_t;
+  return MPAP_OK;
 }
 
 }  // extern "C"

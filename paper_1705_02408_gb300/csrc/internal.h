@@ -68,6 +68,12 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
                               const uint8_t* is_goal, mpap_roadmap** out, cudaStream_t st);
 void roadmap_free_impl(mpap_roadmap* rm);
 
+// Launch shapes from the tuning table (tune.cu), keyed by (dimension, node-count
+// bucket floor(log2 V)); dimension 0 stands for a batch mixing dimensions.
+// Entries absent from the table give the defaults.
+mpap_tuning tuning_for(int dim, uint32_t V);
+bool tuning_valid(const mpap_tuning& t);
+
 // Stream-ordered scratch from the library's memory pool (kept mapped).
 cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
 void scratch_free(void* p, cudaStream_t st);

@@ -319,7 +319,6 @@ __global__ void k_bin_scatter(const BuildJob* __restrict__ jobs) {
 // expensive tests run 32-wide.  The connections that pass are counted
 // (FILL = false) or written (FILL = true) in scan order; rows are sorted later.
 // ---------------------------------------------------------------------------
-constexpr int kEdgeWarps = 8;
 constexpr int kQueue = 64;
 constexpr uint32_t kRowCap = 128;   // edges per source in the one-pass build
 
@@ -365,9 +364,9 @@ __device__ __forceinline__ void edge_flush(const BuildJob& J, uint32_t v, const 
   running += __popc(bal);
 }
 
-template <int DIM, int MODE>
-__global__ void __launch_bounds__(kEdgeWarps * 32, 4) k_edges(const BuildJob* __restrict__ jobs,
-                                                           const uint32_t* __restrict__ job_ids) {
+template <int DIM, int MODE, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges(const BuildJob* __restrict__ jobs,
+                                                               const uint32_t* __restrict__ job_ids) {
   const BuildJob& J = jobs[job_ids[blockIdx.y]];
   const Geom& g = J.g;
   extern __shared__ float smem[];
@@ -385,7 +384,7 @@ __global__ void __launch_bounds__(kEdgeWarps * 32, 4) k_edges(const BuildJob* __
     s_hi[i] = g.box_hi[i];
   }
   __syncthreads();
-  const uint32_t slot = blockIdx.x * kEdgeWarps + warp;
+  const uint32_t slot = blockIdx.x * WARPS + warp;
   uint32_t v = slot;
   if (MODE == kFillCsr) {
     if (slot >= J.status[3]) return;
@@ -532,13 +531,24 @@ __global__ void k_reverse_fill(const BuildJob* __restrict__ jobs) {
     }
 }
 
+template <int MODE, int WARPS>
+void launch_edges_w(int dim, dim3 grid, size_t smem, cudaStream_t st, const BuildJob* jobs, const uint32_t* ids) {
+  const dim3 block(WARPS * 32);
+  if (dim == 6) k_edges<6, MODE, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+  else if (dim == 3) k_edges<3, MODE, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+  else k_edges<2, MODE, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+}
+
+// One launch per dimension group; `warps` (4 or 8 warps per block) comes from
+// the tuning table.
 template <int MODE>
-void launch_edges(int dim, dim3 grid, size_t smem, cudaStream_t st, const BuildJob* jobs, const uint32_t* ids) {
+void launch_edges(int dim, uint32_t warps, uint32_t vmax, uint32_t njobs, size_t box_smem, cudaStream_t st,
+                  const BuildJob* jobs, const uint32_t* ids) {
   LaunchScope ls(st, MODE == kRow ? "k_edges" : "k_edges_overflow");
-  const dim3 block(kEdgeWarps * 32);
-  if (dim == 6) k_edges<6, MODE><<<grid, block, smem, st>>>(jobs, ids);
-  else if (dim == 3) k_edges<3, MODE><<<grid, block, smem, st>>>(jobs, ids);
-  else k_edges<2, MODE><<<grid, block, smem, st>>>(jobs, ids);
+  const dim3 grid((vmax + warps - 1) / warps, njobs);
+  const size_t smem = box_smem + sizeof(uint32_t) * warps * kQueue;
+  if (warps == 4) launch_edges_w<MODE, 4>(dim, grid, smem, st, jobs, ids);
+  else launch_edges_w<MODE, 8>(dim, grid, smem, st, jobs, ids);
 }
 
 // ---------------------------------------------------------------------------
@@ -977,21 +987,21 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   }
   id_off[3] = (uint32_t)ids.size();
   MPAP_BTRY(upload(d_ids, ids.data(), sizeof(uint32_t) * n, st));
-  const size_t esmem = sizeof(float) * 6 * max_nb + sizeof(uint32_t) * kEdgeWarps * kQueue;
+  const size_t box_smem = sizeof(float) * 6 * max_nb;
   auto edges_pass = [&](int mode) {
     for (int di = 0; di < 3; ++di) {
       const uint32_t cnt = id_off[di + 1] - id_off[di];
       if (!cnt) continue;
       uint32_t vmax = 0;
       for (uint32_t k = id_off[di]; k < id_off[di + 1]; ++k) vmax = std::max(vmax, hj[ids[k]].V);
+      const uint32_t warps = tuning_for(dims[di], vmax).edge_warps;
       if (mode == kFillCsr) {
         vmax = 0;
         for (uint32_t k = id_off[di]; k < id_off[di + 1]; ++k) vmax = std::max(vmax, hg[6 * ids[k] + 5]);
         if (vmax == 0) continue;
       }
-      const dim3 grid((vmax + kEdgeWarps - 1) / kEdgeWarps, cnt);
-      if (mode == kRow) launch_edges<kRow>(dims[di], grid, esmem, st, d_jobs, d_ids + id_off[di]);
-      else launch_edges<kFillCsr>(dims[di], grid, esmem, st, d_jobs, d_ids + id_off[di]);
+      if (mode == kRow) launch_edges<kRow>(dims[di], warps, vmax, cnt, box_smem, st, d_jobs, d_ids + id_off[di]);
+      else launch_edges<kFillCsr>(dims[di], warps, vmax, cnt, box_smem, st, d_jobs, d_ids + id_off[di]);
     }
   };
   // one pass: every source's edges into its scratch row, with exact counts

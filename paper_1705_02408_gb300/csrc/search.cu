@@ -93,6 +93,7 @@ struct Ctl {
   uint32_t nq;
   uint32_t iter_cap;    // loop bound (max over queries of max_iters, plus 2)
   uint32_t prof;        // record KTime
+  uint32_t max_front;   // largest front committed by any node
   KTime kt[3];          // select, prune, end
 };
 
@@ -136,16 +137,16 @@ struct mpap_workspace {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap_stream = nullptr;
-  // host record of the last search (for front export)
+  uint32_t graph_sel = 0, graph_pru = 0;   // grids captured in the graph (blocks per SM)
+  // host record of the last search (for front export and tuning)
   std::vector<uint32_t> last_V, last_base;
+  uint32_t last_max_front = 0;
 };
 
 namespace mpap {
 
 constexpr int kWarpsPerBlock = 8;
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kSelectBlocksPerSM = 16;
-constexpr int kPruneBlocksPerSM = 16;
 
 void workspace_free(mpap_workspace* ws);
 void profile_add(const char* name, uint64_t launches, double ms);
@@ -216,6 +217,7 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
     c.nq = nq;
     c.iter_cap = iter_cap;
     c.prof = prof;
+    c.max_front = 1;
     for (int k = 0; k < 3; ++k) {
       c.kt[k].start = ULLONG_MAX;
       c.kt[k].total_ns = 0;
@@ -773,6 +775,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_prune(WS w) {
         w.f_cnt[(size_t)fc.b * w.NV + g] = fc.n;
         atomic_add_i64(&w.qs[q].open_cnt, (long long)n_new - (long long)fc.removed_open);
         atomicAdd(&w.qs[q].plans, (unsigned long long)n_new);
+        atomicMax(&w.ctl->max_front, fc.n);
         if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = g;
       }
     }
@@ -1043,9 +1046,17 @@ bool walloc(T** p, size_t n) {
 
 // Builds the device-side wavefront loop: a graph whose conditional WHILE node
 // runs {select, prune, end} until `end` clears the condition.
-int32_t build_loop_graph(mpap_workspace* ws) {
-  if (ws->exec) return MPAP_OK;
-  MPAP_CK(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
+int32_t build_loop_graph(mpap_workspace* ws, uint32_t sel, uint32_t pru) {
+  if (ws->exec && ws->graph_sel == sel && ws->graph_pru == pru) return MPAP_OK;
+  if (ws->exec) {
+    cudaGraphExecDestroy(ws->exec);
+    ws->exec = nullptr;
+  }
+  if (ws->graph) {
+    cudaGraphDestroy(ws->graph);
+    ws->graph = nullptr;
+  }
+  if (!ws->cap_stream) MPAP_CK(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
   MPAP_CK(cudaGraphCreate(&ws->graph, 0));
   cudaGraphConditionalHandle cond;
   MPAP_CK(cudaGraphConditionalHandleCreate(&cond, ws->graph, 1u, cudaGraphCondAssignDefault));
@@ -1060,12 +1071,14 @@ int32_t build_loop_graph(mpap_workspace* ws) {
   MPAP_CK(cudaStreamBeginCaptureToGraph(ws->cap_stream, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
   const int n = sms();
-  k_select<<<kSelectBlocksPerSM * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
-  k_prune<<<kPruneBlocksPerSM * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
+  k_select<<<sel * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
+  k_prune<<<pru * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
   k_end<<<1, 1024, 0, ws->cap_stream>>>(ws->w, cond, 1u);
   cudaGraph_t captured = nullptr;
   MPAP_CK(cudaStreamEndCapture(ws->cap_stream, &captured));
   MPAP_CK(cudaGraphInstantiate(&ws->exec, ws->graph, 0));
+  ws->graph_sel = sel;
+  ws->graph_pru = pru;
   return MPAP_OK;
 }
 
@@ -1125,6 +1138,20 @@ void workspace_free(mpap_workspace* ws) {
   delete ws;
 }
 
+// Tuning key of a batch: the common dimension (0 if mixed) and the largest V.
+void batch_key(mpap_roadmap* const* rms, uint32_t nq, int& dim, uint32_t& V) {
+  dim = -1;
+  V = 0;
+  for (uint32_t i = 0; i < nq; ++i) {
+    if (!rms[i]) continue;
+    dim = (dim < 0 || dim == rms[i]->dim) ? rms[i]->dim : 0;
+    V = std::max(V, rms[i]->V);
+  }
+  if (dim < 0) dim = 0;
+}
+
+uint32_t workspace_last_max_front(const mpap_workspace* ws) { return ws->last_max_front; }
+
 int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs, uint32_t nq,
                           mpap_result* outs, cudaStream_t st) {
   WS& w = ws->w;
@@ -1175,7 +1202,11 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
               (unsigned long long)w.NV);
     return MPAP_ERR_INVALID_ARG;
   }
-  int32_t rc = build_loop_graph(ws);
+  int kdim = -1;
+  uint32_t kV = 0;
+  batch_key(rms, nq, kdim, kV);
+  const mpap_tuning tun = tuning_for(kdim, kV);
+  int32_t rc = build_loop_graph(ws, tun.select_blocks_per_sm, tun.prune_blocks_per_sm);
   if (rc) return rc;
   ws->last_V.resize(nq);
   ws->last_base.resize(nq);
@@ -1213,8 +1244,8 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     Ctl probe;
     for (uint32_t it = 0;; it += 2) {
       for (int r = 0; r < 2; ++r) {
-        k_select<<<kSelectBlocksPerSM * n, kWarpsPerBlock * 32, 0, st>>>(w);
-        k_prune<<<kPruneBlocksPerSM * n, kWarpsPerBlock * 32, 0, st>>>(w);
+        k_select<<<tun.select_blocks_per_sm * n, kWarpsPerBlock * 32, 0, st>>>(w);
+        k_prune<<<tun.prune_blocks_per_sm * n, kWarpsPerBlock * 32, 0, st>>>(w);
         k_end<<<1, 1024, 0, st>>>(w, 0ull, 0u);
       }
       MPAP_CK(cudaGetLastError());
@@ -1235,6 +1266,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   MPAP_CK(cudaMemcpyAsync(qsh.data(), w.qs, sizeof(QueryState) * nq, cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaStreamSynchronize(st));
+  ws->last_max_front = hc.max_front;
   launch_count_add(3ull * hc.it);
   if (prof) {
     const char* names[3] = {"k_select", "k_prune", "k_end"};
