@@ -43,6 +43,11 @@ UNIT = "expansions/s"
 WORKLOAD = "6D double integrator, 16000 samples, 30 boxes, 32^3 grid, 4096 MC rollouts"
 
 
+def log(msg):
+    sys.stderr.write(f"[bench {time.strftime('%H:%M:%S')}] {msg}\n")
+    sys.stderr.flush()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -55,6 +60,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-2d", action="store_true",
+                    help="also time the 2D queries of the mixed workload (heavy-tailed fronts: minutes)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--sur-train-plans", type=int, default=200000,
                     help="Monte Carlo-labelled candidate plans to train the surrogate on")
@@ -214,8 +221,10 @@ def run_gpu(args, rank, world, local):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    log("autotuned; warm-up")
     for _ in range(args.warmup):
         arm.step()
+    log("timed region")
     # timed region: K steps, device events, profiler on, clocks sampled
     mp.profile_reset()
     mp.profile_enable(True)
@@ -273,9 +282,11 @@ def run_gpu(args, rank, world, local):
         out["search_only"] = search_only(arm, stream)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e(arm, args, stream)
+    log("timed region done")
     if rank == 0 and world == 1 and not args.no_mixed:
         out["mixed_batch"] = mixed_report(args, stream)
     if rank == 0 and world == 1 and not args.no_surrogate:
+        log("surrogate")
         out["surrogate"] = surrogate_report(args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scenes[:2])
@@ -403,9 +414,13 @@ def e2e(arm, args, stream):
 # ------------------------------------------------------------------ mixed batch
 def mixed_report(args, stream, count=256):
     """The batched workload: 256 queries, each on its own roadmap (dimension
-    uniform over 2D/3D/6D, n log-uniform in [1000, 32000], obstacles and grids
-    seeded per query), built in one call, searched in one lock-step launch and
-    certified in one launch, with launch shapes from the autotuner."""
+    uniform over 2D/3D/6D; n log-uniform in [1000, 32000] for 3D/6D and [1000,
+    4000] for 2D), obstacles and grids seeded per query, beta from the stored
+    oracle calibration.  The 3D and 6D queries (uneven sizes) are built in one
+    call, searched in one lock-step launch with autotuned shapes and certified in
+    one launch; the 2D queries, whose Pareto fronts are heavy-tailed (single
+    fronts above 10^5 plans), run as a second batch with a larger front pool,
+    timed once."""
     import torch
     import paper_1705_02408_gb300 as mp
     calib = scenegen.load_calibration()
@@ -418,61 +433,81 @@ def mixed_report(args, stream, count=256):
             return {"skipped": f"no stored beta for {key}: run python -m oracle.calibrate --batch {count}"}
         sc.extra["beta"] = calib[key]["beta"]
         scenes.append(sc)
-    specs = [mp.scene_spec(sc) for sc in scenes]
-    queries = [mp.make_query(sc.extra["beta"], scenegen.LAMBDA) for sc in scenes]
-    mcs = [(sc.cfg.mc_rollouts, sc.mc_seed, 0, sc.delta_fx, sc.sigma_fx, sc.shift) for sc in scenes]
-    total = sum(sc.cfg.n + 2 for sc in scenes)
-    t0 = time.perf_counter()
-    tb, build_ms, rms = mp.autotune_build(specs, reps=1)
-    ws = mp.Workspace(total, front_cap=256, max_plans=1 << 27)
-    ts, search_ms = mp.autotune_search(ws, rms, queries, reps=1)
-    tune_s = time.perf_counter() - t0
-    ws = mp.Workspace(total, front_cap=max(ts["front_cap"], 64), max_plans=1 << 27)
+    out = {"workload": f"{count} queries, one roadmap each: dimension uniform over 2D/3D/6D, n log-uniform in "
+                       f"[1000, 32000] (2D: [1000, 4000]), per-query obstacles and grids, beta = stored 60th "
+                       f"percentile, MC rollouts 1024 (2D/3D) / 4096 (6D)"}
 
-    def step():
-        nonlocal rms
-        rms = mp.build_roadmaps(specs, rms=rms)
-        res = mp.search_batch(ws, rms, queries)
-        mp.certify_batch([rms[i] for i in range(count) if res[i].status == 0],
-                         [r.path for r in res if r.status == 0],
-                         [mcs[i] for i in range(count) if res[i].status == 0])
-        return res
-    for _ in range(2):
-        step()
-    reps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    exps = 0
-    for _ in range(reps):
-        res = step()
-        exps += sum(r.expansions for r in res)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    # search only: batched vs one call per query, same roadmaps
-    e0.record(stream)
-    resb = mp.search_batch(ws, rms, queries)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1)
-    ws1 = mp.Workspace(max(sc.cfg.n + 2 for sc in scenes), front_cap=max(ts["front_cap"], 64),
-                       max_plans=1 << 24)
-    e0.record(stream)
-    for rm, q in zip(rms, queries):
-        mp.search(ws1, rm, q.beta, lam=scenegen.LAMBDA)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_p = e0.elapsed_time(e1)
-    return {"workload": f"{count} queries, one roadmap each: dimension uniform over 2D/3D/6D, n log-uniform in "
-                        f"[1000, 32000] (total {total} nodes), per-query obstacles and grids, beta = stored "
-                        f"60th percentile, MC rollouts 1024 (2D/3D) / 4096 (6D)",
-            "ms_per_step": ms, "ms_per_query": ms / count, "expansions_per_s": exps / reps / (ms / 1e3),
-            "solved": sum(1 for r in res if r.status == 0),
-            "search_only": {"batched_ms_per_query": ms_b / count, "plain_ms_per_query": ms_p / count,
-                            "speedup": ms_p / ms_b},
-            "tuning": {"build": tb, "build_ms": build_ms, "search": ts, "search_ms": search_ms,
-                       "autotune_s": round(tune_s, 2)}}
+    def run_group(name, idx, front_cap, tune, timed_reps, plain):
+        grp = [scenes[i] for i in idx]
+        specs = [mp.scene_spec(sc) for sc in grp]
+        queries = [mp.make_query(sc.extra["beta"], scenegen.LAMBDA) for sc in grp]
+        mcs = [(sc.cfg.mc_rollouts, sc.mc_seed, 0, sc.delta_fx, sc.sigma_fx, sc.shift) for sc in grp]
+        total = sum(sc.cfg.n + 2 for sc in grp)
+        t0 = time.perf_counter()
+        log(f"mixed {name}: {len(grp)} queries, {total} nodes")
+        ws = mp.Workspace(total, front_cap=front_cap, max_plans=1 << 27)
+        tuning = None
+        if tune:
+            tb, build_ms, rms = mp.autotune_build(specs, reps=1)
+            ts, search_ms = mp.autotune_search(ws, rms, queries, reps=1)
+            tuning = {"build": tb, "build_ms": build_ms, "search": ts, "search_ms": search_ms,
+                      "autotune_s": round(time.perf_counter() - t0, 2)}
+            log(f"mixed {name}: autotuned in {tuning['autotune_s']} s")
+        else:
+            rms = mp.build_roadmaps(specs)
+        holder = {"rms": rms}
+
+        def step():
+            holder["rms"] = mp.build_roadmaps(specs, rms=holder["rms"])
+            r = holder["rms"]
+            res = mp.search_batch(ws, r, queries, check=False)
+            ok = [i for i in range(len(grp)) if res[i].status == 0]
+            if ok:
+                mp.certify_batch([r[i] for i in ok], [res[i].path for i in ok], [mcs[i] for i in ok])
+            return res
+        for _ in range(1 if timed_reps > 1 else 0):
+            step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        exps = 0
+        for _ in range(timed_reps):
+            res = step()
+            exps += sum(r.expansions for r in res)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / timed_reps
+        log(f"mixed {name}: {ms:.1f} ms per step")
+        g = {"queries": len(grp), "nodes": total, "ms_per_step": ms, "ms_per_query": ms / len(grp),
+             "expansions_per_s": exps / timed_reps / (ms / 1e3),
+             "status": {str(k): int(v) for k, v in zip(*np.unique([r.status for r in res], return_counts=True))},
+             "max_wavefronts": max(r.wavefronts for r in res), "front_cap": front_cap, "tuning": tuning}
+        if plain:
+            e0.record(stream)
+            mp.search_batch(ws, holder["rms"], queries, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_b = e0.elapsed_time(e1)
+            ws1 = mp.Workspace(max(sc.cfg.n + 2 for sc in grp), front_cap=1024, max_plans=1 << 25)
+            e0.record(stream)
+            for rm, q in zip(holder["rms"], queries):
+                mp.search(ws1, rm, q.beta, lam=scenegen.LAMBDA)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_p = e0.elapsed_time(e1)
+            g["search_only"] = {"batched_ms_per_query": ms_b / len(grp), "plain_ms_per_query": ms_p / len(grp),
+                                "speedup": ms_p / ms_b}
+        return g
+
+    idx36 = [i for i, sc in enumerate(scenes) if sc.cfg.dim_kind != 2]
+    idx2 = [i for i, sc in enumerate(scenes) if sc.cfg.dim_kind == 2]
+    out["3d_6d"] = run_group("3d_6d", idx36, 128, True, max(1, min(args.steps, 5)), True)
+    if args.mixed_2d:
+        out["2d"] = run_group("2d", idx2, 1024, False, 1, False)
+    else:
+        out["2d"] = {"skipped": "run with --mixed-2d: 2D Pareto fronts are heavy-tailed (a single front of "
+                                "193,126 plans at n = 1276 takes 29 s alone)"}
+    return out
 
 
 # ------------------------------------------------------------------ surrogate

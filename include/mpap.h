@@ -206,9 +206,14 @@ void mpap_roadmap_free(mpap_roadmap* rm);
 /* ---------------------------------------------------------------------------
  * Search workspace: device memory for the per-node Pareto fronts, the plan arena
  * and the wavefront work lists of up to `total_nodes` nodes summed over the
- * queries of one call.  front_cap bounds every stored front (MPAP_ERR_CAPACITY
- * when exceeded); max_plans bounds the arena and each group.  Allocates with
- * cudaMalloc; reused by every search call. */
+ * queries of one call.  Fronts live in one pool of total_nodes * front_cap
+ * entries (24 bytes each; the product must not exceed 2^32 - 16): every node
+ * draws two blocks from it (its live front and a merge target), of 16 entries
+ * and up, replaced by blocks twice the needed size as its front grows, so single
+ * fronts may be far larger than front_cap as long as the pool lasts.  A query
+ * that runs out of pool, plan arena (max_plans) or group array (max_plans) ends
+ * with MPAP_ERR_CAPACITY in its own result; the other queries of the batch run
+ * on.  Allocates with cudaMalloc; reused by every search call. */
 int32_t mpap_workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans,
                               mpap_workspace** out);
 void mpap_workspace_free(mpap_workspace* ws);
@@ -287,7 +292,7 @@ typedef struct {
   uint32_t edge_warps;            /* warps per block of the edge kernel: 4 or 8 */
   uint32_t select_blocks_per_sm;  /* grid of the group-selection kernel: 1 .. 64 */
   uint32_t prune_blocks_per_sm;   /* grid of the candidate-pull/prune kernel: 1 .. 64 */
-  uint32_t front_cap;             /* advisory front slot size for mpap_workspace_create */
+  uint32_t front_cap;             /* advisory pool entries per node for mpap_workspace_create */
 } mpap_tuning;
 
 /* The entry the library uses for (dim_kind, V): a stored one or the defaults. */
@@ -308,11 +313,10 @@ int32_t mpap_autotune_build(uint32_t n, const mpap_scene* scenes, const mpap_roa
                             mpap_roadmap** rms, uint32_t reps, mpap_tuning* best, double* best_ms,
                             void* stream);
 
-/* Grid search of the select and prune grids (1, 2, 4, 8, 16, 32 blocks per SM
- * each) on one batched search of these queries, `reps` timed searches per
+/* Grid search of the select and prune grids (2, 4, 8, 16 blocks per SM each) on one batched search of these queries, `reps` timed searches per
  * candidate after an untimed one.  Stores the fastest for the batch key and
- * sets best->front_cap to twice the largest front any node held during the
- * search, rounded up to a power of two (at least 32).  Fails with MPAP_ERR_CUDA
+ * sets best->front_cap to twice the front-pool entries per node the search
+ * used, rounded up to a power of two (at least 16).  Fails with MPAP_ERR_CUDA
  * (and stores nothing) if two shapes give different results. */
 int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs,
                              uint32_t nq, uint32_t reps, mpap_tuning* best, double* best_ms,

@@ -54,8 +54,7 @@ def main():
     ctx = mpr.get_context("spawn")
     with ctx.Pool(args.procs) as pool:
         out = dict(pool.map(_one, jobs))
-    data = scenegen.load_calibration()
-    data.update(out)
+    data = out          # the file holds exactly the scenes of this run
     path = os.path.join(ROOT, "scenegen", "calibration.json")
     with open(path, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)

@@ -36,6 +36,7 @@ void tuning_clear();
 int32_t tuning_export(uint32_t cap, int32_t* dims, uint32_t* buckets, mpap_tuning* t, uint32_t* n);
 void batch_key(mpap_roadmap* const* rms, uint32_t nq, int& dim, uint32_t& V);
 uint32_t workspace_last_max_front(const mpap_workspace* ws);
+unsigned long long workspace_last_pool_used(const mpap_workspace* ws);
 }  // namespace mpap
 
 using mpap::set_error;
@@ -499,8 +500,10 @@ int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const
   };
   double best_t = 1e300;
   mpap_tuning bt = base;
-  uint32_t max_front = 1;
-  const uint32_t grids[] = {1, 2, 4, 8, 16, 32};
+  unsigned long long pool_used = 0;
+  uint64_t nodes = 0;
+  for (uint32_t i = 0; i < nq; ++i) nodes += rms[i] ? rms[i]->V : 0u;
+  const uint32_t grids[] = {2, 4, 8, 16};
   for (uint32_t sel : grids) {
     for (uint32_t pru : grids) {
       mpap_tuning t = base;
@@ -524,15 +527,15 @@ int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const
             return MPAP_ERR_CUDA;
           }
       }
-      max_front = std::max(max_front, mpap::workspace_last_max_front(ws));
+      pool_used = std::max(pool_used, mpap::workspace_last_pool_used(ws));
       if (ms < best_t) {
         best_t = ms;
         bt = t;
       }
     }
   }
-  uint32_t fc = 32;
-  while (fc < 2 * max_front) fc <<= 1;
+  uint32_t fc = 16;
+  while ((uint64_t)fc * std::max<uint64_t>(nodes, 1) < 2 * pool_used) fc <<= 1;
   bt.front_cap = fc;
   mpap::tuning_set(kdim, kV, bt);
   *best = bt;

@@ -15,17 +15,21 @@
 //           chunks of 32: filter against the front, warp bitonic sort, warp
 //           prefix-min, then a rank merge.  Fronts of up to 32 entries live in
 //           registers (one entry per lane) for the whole merge; larger fronts are
-//           merged between the two slab buffers in global memory.  Surviving
-//           candidates get arena records at the end.
+//           merged between the node's two pool blocks in global memory.
+//           Surviving candidates get arena records at the end.
 //   end     one block: termination per query (goal in group, P_open empty,
 //           iteration cap), list swap, loop condition.
 // The loop runs on the device: the three kernels form the body of a CUDA graph
 // conditional WHILE node, which `end` clears once every query has finished (or
 // the iteration caps are reached), so a search is one graph launch.
 //
-// HBM layout (NV = nodes summed over the batch, F = front capacity):
-//   fronts   2 x [NV][F] of {cost i64, h i64, ref u32 (arena | open | new), aux u32}
-//   f_cnt    2 x [NV], cur [NV] (which buffer holds the live front)
+// HBM layout (NV = nodes summed over the batch):
+//   fronts   a pool of {cost i64, h i64, ref u32 (arena | open | new), aux u32}
+//            entries; every node owns two blocks of it (live front, merge
+//            target), of power-of-two sizes from 16 up, taken from the pool with
+//            one atomic add and replaced by a block twice the needed size when
+//            too small (the old block is abandoned: at most as much again)
+//   fdesc    [NV] {live block, count, other block, log2 sizes}
 //   group    [cap] {cost, h, ref}, per node offset/count, stamps [NV]
 //   arena    [cap] {head u32, parent u32, iter u32, cost i64} for back-tracing
 #include <algorithm>
@@ -64,6 +68,8 @@ struct QueryState {
   uint32_t goal_hit;
   uint32_t done;
   int32_t status;
+  uint32_t err;          // capacity error bits of this query (pool, arena, group)
+  uint32_t pad;
 };
 
 struct ResultDev {
@@ -94,19 +100,20 @@ struct Ctl {
   uint32_t iter_cap;    // loop bound (max over queries of max_iters, plus 2)
   uint32_t prof;        // record KTime
   uint32_t max_front;   // largest front committed by any node
+  unsigned long long pool_n;  // front pool entries handed out
   KTime kt[3];          // select, prune, end
 };
 
 struct WS {
   uint64_t NV;
-  uint32_t fcap;
+  uint32_t fcap;           // front pool entries per node (pool = NV fcap)
+  uint64_t pcap;           // front pool entries
   uint64_t acap, gcap;
-  long long* f_cost;
+  long long* f_cost;       // [pcap] front pool
   long long* f_h;
   uint32_t* f_pid;
   uint32_t* f_aux;
-  uint32_t* f_cnt;
-  uint8_t* cur;
+  uint4* fdesc;            // [NV] {live block, count, other block, lg live | lg other << 8}
   uint32_t* qid;
   uint4* gdesc;            // per node {iteration stamp, group count, group offset, 0}
   uint32_t* touch_stamp;
@@ -141,11 +148,16 @@ struct mpap_workspace {
   // host record of the last search (for front export and tuning)
   std::vector<uint32_t> last_V, last_base;
   uint32_t last_max_front = 0;
+  unsigned long long last_pool_used = 0;
 };
 
 namespace mpap {
 
 constexpr int kWarpsPerBlock = 8;
+// Resident blocks per SM the prune kernel is compiled for (register budget).
+#ifndef MPAP_PRUNE_MIN_BLOCKS
+#define MPAP_PRUNE_MIN_BLOCKS 4
+#endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 void workspace_free(mpap_workspace* ws);
@@ -158,8 +170,25 @@ __device__ __forceinline__ void atomic_add_i64(long long* p, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
 }
 
-__device__ __forceinline__ size_t slab(const WS& w, uint32_t b, uint32_t g) {
-  return ((size_t)b * w.NV + g) * w.fcap;
+constexpr uint32_t kMinLg = 4;          // smallest pool block: 16 entries
+constexpr uint32_t kNoBlock = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t ceil_lg(uint32_t n) {
+  return n <= 1 ? 0u : 32u - (uint32_t)__clz(n - 1u);
+}
+
+// One block of 2^lg pool entries (call from one lane); kNoBlock when the pool is
+// exhausted.
+__device__ __forceinline__ uint32_t pool_alloc(const WS& w, uint32_t lg) {
+  const unsigned long long sz = 1ull << lg;
+  const unsigned long long o = atomicAdd(&w.ctl->pool_n, sz);
+  return (o + sz <= w.pcap) ? (uint32_t)o : kNoBlock;
+}
+
+// Records a capacity error of query q (it ends at the next end-of-wavefront).
+__device__ __forceinline__ void query_error(const WS& w, uint32_t q, uint32_t bit) {
+  atomicOr(&w.qs[q].err, bit);
+  atomicOr(&w.ctl->err, bit);
 }
 
 __device__ __forceinline__ unsigned long long global_timer() {
@@ -218,6 +247,7 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
     c.iter_cap = iter_cap;
     c.prof = prof;
     c.max_front = 1;
+    c.pool_n = (unsigned long long)nq << kMinLg;   // the roots' blocks
     for (int k = 0; k < 3; ++k) {
       c.kt[k].start = ULLONG_MAX;
       c.kt[k].total_ns = 0;
@@ -235,13 +265,15 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
   s.goal_hit = 0;
   s.done = 0;
   s.status = 0;
+  s.err = 0;
+  s.pad = 0;
   w.qs[q] = s;
-  const size_t o = slab(w, 0, g);
+  const uint32_t o = q << kMinLg;   // block q of the pool
   w.f_cost[o] = 0;
   w.f_h[o] = 0;
   w.f_pid[o] = q | kOpen;      // the root plan (x_init, {}, 0, 0) is arena record q
   w.f_aux[o] = 0;
-  w.f_cnt[g] = 1;
+  w.fdesc[g] = make_uint4(o, 1u, 0u, kMinLg);
   w.a_head[q] = 0;
   w.a_parent[q] = kNone;
   w.a_iter[q] = 0;
@@ -267,9 +299,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
     const uint32_t q = w.qid[g];
     if (w.qs[q].done) continue;
     const QueryDev& Q = w.qd[q];
-    const uint32_t b = w.cur[g];
-    const uint32_t n = w.f_cnt[(size_t)b * w.NV + g];
-    const size_t o = slab(w, b, g);
+    const uint4 fd = w.fdesc[g];
+    const uint32_t n = fd.y;
+    const size_t o = fd.x;
     const long long thr = (long long)it * Q.Lambda;
     uint32_t cnt = 0;
     bool rest = false;
@@ -291,7 +323,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
       off = __shfl_sync(kFull, off, 0);
       const bool fits = (uint64_t)off + cnt <= w.gcap;
       if (!fits) {
-        if (lane == 0) atomicOr(&w.ctl->err, kErrGroup);
+        if (lane == 0) query_error(w, q, kErrGroup);
       } else {
         uint32_t r0 = 0;
         for (uint32_t j0 = 0; j0 < n; j0 += 32) {
@@ -370,16 +402,44 @@ __device__ __forceinline__ bool key_less(long long c1, long long h1, uint32_t t1
 }
 
 // Front of one node during the merge: in registers (lane j holds entry j, n <= 32)
-// or in slab buffer b.
+// or in the node's live pool block.
 struct FrontCursor {
   bool reg;
-  uint32_t b;        // live slab buffer
+  bool err;          // a pool block could not be had: stop merging this node
+  uint32_t off, lg;  // live block (lg = log2 size, 0: none)
+  uint32_t off2, lg2;  // the other block (merge target)
   uint32_t n;        // live count
   uint32_t removed_open;
   bool any_new;
   long long rc, rh;  // register entry of this lane (reg mode)
   uint32_t rp, ra;
 };
+
+// Makes the other block hold at least `need` entries (warp-uniform); false when
+// the pool is exhausted (the query is marked failed).
+__device__ __forceinline__ bool ensure_other(const WS& w, uint32_t q, FrontCursor& fc, uint32_t need) {
+  if (fc.lg2 != 0 && (1u << fc.lg2) >= need) return true;
+  const uint32_t lg = max(kMinLg, ceil_lg(need) + 1u);
+  uint32_t o = 0;
+  if (lane_id() == 0) o = pool_alloc(w, lg);
+  o = __shfl_sync(kFull, o, 0);
+  if (o == kNoBlock) {
+    if (lane_id() == 0) query_error(w, q, kErrFront);
+    fc.err = true;
+    return false;
+  }
+  fc.off2 = o;
+  fc.lg2 = lg;
+  return true;
+}
+
+__device__ __forceinline__ void swap_blocks(FrontCursor& fc) {
+  const uint32_t o = fc.off, l = fc.lg;
+  fc.off = fc.off2;
+  fc.lg = fc.lg2;
+  fc.off2 = o;
+  fc.lg2 = l;
+}
 
 // Sort the chunk (one candidate per lane; padding lanes last) by (cost, h, tb)
 // and keep its skyline: survivors are written to sm.s_* in order; returns their
@@ -431,16 +491,17 @@ __device__ __forceinline__ uint32_t chunk_skyline(WarpSmem& sm, bool ok, long lo
   return __popc(sb);
 }
 
-// Slab-mode merge of up to 32 candidates into the live front of node g.
+// Block-mode merge of up to 32 candidates into the live front of a node: the
+// merged front is written to the node's other block, which then becomes live.
 // Candidate tie key tb = 1 + parent head (old plans have tie key 0, i.e. they win
 // exact (cost, h) ties).
-__device__ void merge_chunk_slab(const WS& w, uint32_t g, FrontCursor& fc, WarpSmem& sm, bool ok,
+__device__ void merge_chunk_slab(const WS& w, uint32_t q, FrontCursor& fc, WarpSmem& sm, bool ok,
                                  long long cc, long long ch, uint32_t ctb, uint32_t cpp) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   // 1. drop candidates dominated by the live front (last entry with cost <= cc)
   {
-    const size_t o = slab(w, fc.b, g);
+    const size_t o = fc.off;
     if (ok && fc.n > 0) {
       uint32_t L = 0, R = fc.n;
       while (L < R) {
@@ -459,16 +520,15 @@ __device__ void merge_chunk_slab(const WS& w, uint32_t g, FrontCursor& fc, WarpS
   if (!__any_sync(kFull, ok)) return;
   // 2. skyline of the chunk
   const uint32_t m = chunk_skyline(sm, ok, cc, ch, ctb, cpp);
+  if (!ensure_other(w, q, fc, fc.n + m)) return;
   sm.bins[lane] = 0;
   if (lane == 0) sm.bins[32] = 0;
   __syncwarp();
   // 3. one pass over the live front: drop entries dominated by a survivor, write
-  //    the kept ones to the other buffer at (kept rank + survivors before them)
-  const uint32_t nb = fc.b ^ 1u;
-  const size_t o = slab(w, fc.b, g), on = slab(w, nb, g);
+  //    the kept ones to the other block at (kept rank + survivors before them)
+  const size_t o = fc.off, on = fc.off2;
   uint32_t kept = 0;
   uint32_t rem_open = 0;
-  bool overflow = false;
   for (uint32_t j0 = 0; j0 < fc.n; j0 += 32) {
     const uint32_t j = j0 + lane;
     const bool valid = j < fc.n;
@@ -497,14 +557,10 @@ __device__ void merge_chunk_slab(const WS& w, uint32_t g, FrontCursor& fc, WarpS
     const unsigned kb = __ballot_sync(kFull, keep);
     if (keep) {
       const uint32_t pos = kept + __popc(kb & lt) + L;
-      if (pos < w.fcap) {
-        w.f_cost[on + pos] = fcost;
-        w.f_h[on + pos] = fh;
-        w.f_pid[on + pos] = fpid;
-        w.f_aux[on + pos] = faux;
-      } else {
-        overflow = true;
-      }
+      w.f_cost[on + pos] = fcost;
+      w.f_h[on + pos] = fh;
+      w.f_pid[on + pos] = fpid;
+      w.f_aux[on + pos] = faux;
       atomicAdd(&sm.bins[L], 1u);
     }
     kept += __popc(kb);
@@ -513,33 +569,24 @@ __device__ void merge_chunk_slab(const WS& w, uint32_t g, FrontCursor& fc, WarpS
   const uint32_t before = warp_incl_scan(lane < m ? sm.bins[lane] : 0u);
   if (lane < m) {
     const uint32_t pos = lane + before;
-    if (pos < w.fcap) {
-      w.f_cost[on + pos] = sm.s_cost[lane];
-      w.f_h[on + pos] = sm.s_h[lane];
-      w.f_pid[on + pos] = sm.s_pp[lane] | kNew;
-      w.f_aux[on + pos] = sm.s_tb[lane];
-    } else {
-      overflow = true;
-    }
-  }
-  uint32_t n_new = kept + m;
-  if (__any_sync(kFull, overflow) || n_new > w.fcap) {
-    if (lane == 0) atomicOr(&w.ctl->err, kErrFront);
-    n_new = n_new > w.fcap ? w.fcap : n_new;
+    w.f_cost[on + pos] = sm.s_cost[lane];
+    w.f_h[on + pos] = sm.s_h[lane];
+    w.f_pid[on + pos] = sm.s_pp[lane] | kNew;
+    w.f_aux[on + pos] = sm.s_tb[lane];
   }
   for (int s = 16; s > 0; s >>= 1) rem_open += __shfl_xor_sync(kFull, rem_open, s);
   fc.removed_open += rem_open;
-  fc.b = nb;
-  fc.n = n_new;
+  swap_blocks(fc);
+  fc.n = kept + m;
   fc.any_new = true;
   __syncwarp();
 }
 
 // Register-mode merge: the front (n <= 32) is held one entry per lane; all
 // dominance tests are broadcasts over lanes.  If the merged front exceeds 32
-// entries it is written to the other slab buffer and the node continues in slab
-// mode.
-__device__ void merge_chunk_reg(const WS& w, uint32_t g, FrontCursor& fc, WarpSmem& sm, bool ok,
+// entries it is written to the node's other block and the node continues in
+// block mode.
+__device__ void merge_chunk_reg(const WS& w, uint32_t q, FrontCursor& fc, WarpSmem& sm, bool ok,
                                 long long cc, long long ch, uint32_t ctb, uint32_t cpp) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
@@ -593,37 +640,34 @@ __device__ void merge_chunk_reg(const WS& w, uint32_t g, FrontCursor& fc, WarpSm
   }
   __syncwarp();
   const uint32_t n_new = kept + m;
-  fc.removed_open += rem_open;
-  fc.any_new = true;
-  if (n_new > w.fcap && lane == 0) atomicOr(&w.ctl->err, kErrFront);
   if (n_new <= 32) {
-    const uint32_t lim = n_new < w.fcap ? n_new : w.fcap;
-    if (lane < lim) {
+    if (lane < n_new) {
       fc.rc = sm.st_cost[lane];
       fc.rh = sm.st_h[lane];
       fc.rp = sm.st_pid[lane];
       fc.ra = sm.st_aux[lane];
     }
-    fc.n = lim;
+    fc.n = n_new;
   } else {
-    // spill to the other slab buffer and continue in slab mode
-    const uint32_t nb = fc.b ^ 1u;
-    const size_t on = slab(w, nb, g);
-    const uint32_t lim = n_new < w.fcap ? n_new : w.fcap;
-    for (uint32_t i = lane; i < lim; i += 32) {
+    // spill to the other block and continue in block mode
+    if (!ensure_other(w, q, fc, n_new)) return;
+    const size_t on = fc.off2;
+    for (uint32_t i = lane; i < n_new; i += 32) {
       w.f_cost[on + i] = sm.st_cost[i];
       w.f_h[on + i] = sm.st_h[i];
       w.f_pid[on + i] = sm.st_pid[i];
       w.f_aux[on + i] = sm.st_aux[i];
     }
+    swap_blocks(fc);
     fc.reg = false;
-    fc.b = nb;
-    fc.n = lim;
+    fc.n = n_new;
   }
+  fc.removed_open += rem_open;
+  fc.any_new = true;
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_prune(WS w) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_prune(WS w) {
   ktime_begin(w, 1);
   __shared__ WarpSmem smem[kWarpsPerBlock];
   WarpSmem& sm = smem[threadIdx.x >> 5];
@@ -644,21 +688,27 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_prune(WS w) {
     }
     const uint32_t x = g - Q.base;
     FrontCursor fc;
-    fc.b = w.cur[g];
-    fc.n = w.f_cnt[(size_t)fc.b * w.NV + g];
+    {
+      const uint4 fd = w.fdesc[g];
+      fc.off = fd.x;
+      fc.n = fd.y;
+      fc.off2 = fd.z;
+      fc.lg = fd.w & 0xFFu;
+      fc.lg2 = (fd.w >> 8) & 0xFFu;
+    }
+    fc.err = false;
     fc.removed_open = 0;
     fc.any_new = false;
     fc.reg = fc.n <= 32;
     fc.rc = fc.rh = 0;
     fc.rp = fc.ra = 0;
     if (fc.reg && lane < fc.n) {
-      const size_t o = slab(w, fc.b, g);
+      const size_t o = fc.off;
       fc.rc = w.f_cost[o + lane];
       fc.rh = w.f_h[o + lane];
       fc.rp = w.f_pid[o + lane];
       fc.ra = w.f_aux[o + lane];
     }
-    const uint32_t b0 = fc.b;
     unsigned long long exps = 0;
     const uint32_t e_end = Q.rev_ptr[x + 1];
     for (uint32_t e0 = Q.rev_ptr[x]; e0 < e_end; e0 += 32) {
@@ -704,11 +754,26 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_prune(WS w) {
           pp = w.g_pid[gi];
           ok = ch <= Q.beta;          // perception-heuristic cutoff
         }
-        if (fc.reg) merge_chunk_reg(w, g, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
-        else merge_chunk_slab(w, g, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
+        if (fc.err) continue;
+        if (fc.reg) merge_chunk_reg(w, q, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
+        else merge_chunk_slab(w, q, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
       }
     }
-    if (fc.any_new) {
+    if (fc.any_new && !fc.err && fc.reg && (fc.lg == 0 || (1u << fc.lg) < fc.n)) {
+      // the register front needs a (larger) live block to be written back to
+      const uint32_t lg = max(kMinLg, ceil_lg(fc.n));
+      uint32_t o = 0;
+      if (lane == 0) o = pool_alloc(w, lg);
+      o = __shfl_sync(kFull, o, 0);
+      if (o == kNoBlock) {
+        if (lane == 0) query_error(w, q, kErrFront);
+        fc.err = true;
+      } else {
+        fc.off = o;
+        fc.lg = lg;
+      }
+    }
+    if (fc.any_new && !fc.err) {
       // give every new front entry an arena record and mark it open
       uint32_t n_new = 0;
       if (fc.reg) {
@@ -726,23 +791,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_prune(WS w) {
             w.a_cost[a] = fc.rc;
             fc.rp = (uint32_t)a | kOpen;
           } else {
-            atomicOr(&w.ctl->err, kErrArena);
+            query_error(w, q, kErrArena);
             fc.rp = kOpen;
           }
           fc.ra = 0;
         }
         n_new = __popc(bal);
-        // write the register front back in place
-        const size_t o = slab(w, b0, g);
+        // write the register front to the live block
+        const size_t o = fc.off;
         if (lane < fc.n) {
           w.f_cost[o + lane] = fc.rc;
           w.f_h[o + lane] = fc.rh;
           w.f_pid[o + lane] = fc.rp;
           w.f_aux[o + lane] = fc.ra;
         }
-        fc.b = b0;
       } else {
-        const size_t o = slab(w, fc.b, g);
+        const size_t o = fc.off;
         for (uint32_t j0 = 0; j0 < fc.n; j0 += 32) {
           const uint32_t j = j0 + lane;
           uint32_t pid = 0;
@@ -762,7 +826,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_prune(WS w) {
               w.a_cost[a] = w.f_cost[o + j];
               w.f_pid[o + j] = (uint32_t)a | kOpen;
             } else {
-              atomicOr(&w.ctl->err, kErrArena);
+              query_error(w, q, kErrArena);
               w.f_pid[o + j] = kOpen;
             }
             w.f_aux[o + j] = 0;
@@ -771,8 +835,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_prune(WS w) {
         }
       }
       if (lane == 0) {
-        w.cur[g] = (uint8_t)fc.b;
-        w.f_cnt[(size_t)fc.b * w.NV + g] = fc.n;
+        w.fdesc[g] = make_uint4(fc.off, fc.n, fc.off2, fc.lg | (fc.lg2 << 8));
         atomic_add_i64(&w.qs[q].open_cnt, (long long)n_new - (long long)fc.removed_open);
         atomicAdd(&w.qs[q].plans, (unsigned long long)n_new);
         atomicMax(&w.ctl->max_front, fc.n);
@@ -791,14 +854,13 @@ __global__ void __launch_bounds__(1024) k_end(WS w, cudaGraphConditionalHandle c
   ktime_begin(w, 2);
   __shared__ uint32_t s_newly;
   const uint32_t it = w.ctl->it, nq = w.ctl->nq;
-  const uint32_t err = w.ctl->err;
   if (threadIdx.x == 0) s_newly = 0;
   __syncthreads();
   for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
     QueryState& s = w.qs[q];
     const QueryDev& Q = w.qd[q];
     if (s.done) continue;
-    if (err) {
+    if (s.err) {
       s.done = 1;
       s.status = MPAP_ERR_CAPACITY;
     } else if (s.goal_hit && !(Q.flags & MPAP_QUERY_NO_GOAL_STOP)) {
@@ -858,9 +920,9 @@ __global__ void k_finalize(WS w, uint32_t nq) {
     for (uint32_t i = threadIdx.x; i < Q.n_goal; i += blockDim.x) {
       const uint32_t v = Q.goal_list[i];
       const uint32_t g = Q.base + v;
-      const uint32_t b = w.cur[g];
-      const uint32_t n = w.f_cnt[(size_t)b * w.NV + g];
-      const size_t o = slab(w, b, g);
+      const uint4 fd = w.fdesc[g];
+      const uint32_t n = fd.y;
+      const size_t o = fd.x;
       for (uint32_t j = 0; j < n; ++j) {
         Best c;
         c.cost = w.f_cost[o + j];
@@ -969,9 +1031,9 @@ __global__ void __launch_bounds__(256) k_candidates(WS w, uint32_t q, uint32_t c
     for (uint32_t i = threadIdx.x; i < Q.n_goal; i += blockDim.x) {
       const uint32_t v = Q.goal_list[i];
       const uint32_t g = Q.base + v;
-      const uint32_t b = w.cur[g];
-      const uint32_t n = w.f_cnt[(size_t)b * w.NV + g];
-      const size_t off = slab(w, b, g);
+      const uint4 fd = w.fdesc[g];
+      const uint32_t n = fd.y;
+      const size_t off = fd.x;
       if (r == 0) mine += n;
       for (uint32_t j = 0; j < n; ++j) {
         const Best c = goal_plan(w, v, w.f_pid[off + j] & kPidMask, w.f_cost[off + j], w.f_h[off + j]);
@@ -1020,6 +1082,20 @@ __global__ void __launch_bounds__(256) k_candidates(WS w, uint32_t q, uint32_t c
   for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
     uint32_t k = o.ptr[i + 1];
     for (uint32_t a = o.ref[i]; a != kNone; a = w.a_parent[a]) o.path[--k] = w.a_head[a];
+  }
+}
+
+// Packs the final fronts of one query (nodes base .. base+V-1) into [ptr[v],
+// ptr[v+1]) of oc/oh (warp per node; front export for parity checks).
+__global__ void k_gather_fronts(WS w, uint32_t base, uint32_t V, const uint32_t* __restrict__ ptr,
+                                long long* __restrict__ oc, long long* __restrict__ oh) {
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < V; v += warps) {
+    const uint4 fd = w.fdesc[base + v];
+    for (uint32_t j = lane_id(); j < fd.y; j += 32) {
+      oc[ptr[v] + j] = w.f_cost[(size_t)fd.x + j];
+      oh[ptr[v] + j] = w.f_h[(size_t)fd.x + j];
+    }
   }
 }
 
@@ -1103,13 +1179,19 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
   WS& w = ws->w;
   w.NV = total_nodes;
   w.fcap = front_cap;
+  w.pcap = (uint64_t)total_nodes * front_cap;
+  if (w.pcap > 0xFFFFFFF0ull || w.pcap < 16) {
+    delete ws;
+    set_error("mpap_workspace_create: total_nodes x front_cap must lie in [16, 2^32 - 16]");
+    return MPAP_ERR_INVALID_ARG;
+  }
   w.acap = max_plans;
   w.gcap = max_plans;
   w.path_cap = 4096;
   ws->max_q = max_q;
-  const size_t slots = 2 * (size_t)w.NV * w.fcap;
+  const size_t slots = (size_t)w.pcap;
   bool ok = walloc(&w.f_cost, slots) && walloc(&w.f_h, slots) && walloc(&w.f_pid, slots) &&
-            walloc(&w.f_aux, slots) && walloc(&w.f_cnt, 2 * w.NV) && walloc(&w.cur, w.NV) &&
+            walloc(&w.f_aux, slots) && walloc(&w.fdesc, w.NV) &&
             walloc(&w.qid, w.NV) && walloc(&w.gdesc, w.NV) && walloc(&w.touch_stamp, w.NV) &&
             walloc(&w.oh_stamp, w.NV) &&
             walloc(&w.g_cost, w.gcap) && walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) &&
@@ -1131,7 +1213,7 @@ void workspace_free(mpap_workspace* ws) {
   if (ws->graph) cudaGraphDestroy(ws->graph);
   if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
   WS& w = ws->w;
-  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.f_cnt, w.cur, w.qid, w.gdesc, w.touch_stamp,
+  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.fdesc, w.qid, w.gdesc, w.touch_stamp,
                   w.oh_stamp, w.g_cost, w.g_h, w.g_pid, w.oh_list, w.t_list,
                   w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl, w.qd, w.qs, w.res, w.path};
   for (void* p : ptrs) cudaFree(p);
@@ -1151,6 +1233,8 @@ void batch_key(mpap_roadmap* const* rms, uint32_t nq, int& dim, uint32_t& V) {
 }
 
 uint32_t workspace_last_max_front(const mpap_workspace* ws) { return ws->last_max_front; }
+unsigned long long workspace_last_pool_used(const mpap_workspace* ws) { return ws->last_pool_used; }
+uint64_t workspace_nodes(const mpap_workspace* ws) { return ws->w.NV; }
 
 int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs, uint32_t nq,
                           mpap_result* outs, cudaStream_t st) {
@@ -1159,6 +1243,11 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   if (nq > ws->max_q) {
     set_error("search: %u queries exceed the workspace's %u", nq, ws->max_q);
     return MPAP_ERR_INVALID_ARG;
+  }
+  if (((uint64_t)nq << 4) > w.pcap) {
+    set_error("search: the front pool (%llu entries) cannot hold the %u queries' roots",
+              (unsigned long long)w.pcap, nq);
+    return MPAP_ERR_CAPACITY;
   }
   std::vector<QueryDev> qd(nq);
   uint64_t total = 0;
@@ -1217,9 +1306,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   const size_t NVu = (size_t)total;
   const bool prof = profile_enabled();
   MPAP_CK(cudaMemcpyAsync(w.qd, qd.data(), sizeof(QueryDev) * nq, cudaMemcpyHostToDevice, st));
-  MPAP_CK(cudaMemsetAsync(w.f_cnt, 0, sizeof(uint32_t) * NVu, st));
-  MPAP_CK(cudaMemsetAsync(w.f_cnt + w.NV, 0, sizeof(uint32_t) * NVu, st));
-  MPAP_CK(cudaMemsetAsync(w.cur, 0, NVu, st));
+  MPAP_CK(cudaMemsetAsync(w.fdesc, 0, sizeof(uint4) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.gdesc, 0xFF, sizeof(uint4) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.touch_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.oh_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
@@ -1293,8 +1380,10 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     if (o.status < 0 && rc == MPAP_OK) rc = o.status;
   }
   MPAP_CK(cudaStreamSynchronize(st));
+  ws->last_pool_used = hc.pool_n;
   if (hc.err) {
-    set_error("search: device capacity exceeded (flags 0x%x: 1 front, 2 arena, 4 group)", hc.err);
+    set_error("search: capacity exceeded in at least one query (flags 0x%x: 1 front pool, 2 plan arena, "
+              "4 group array); its status says so, the other queries' results stand", hc.err);
     rc = MPAP_ERR_CAPACITY;
   } else if (hc.n_done < nq) {
     set_error("search: wavefront loop stopped at its iteration bound");
@@ -1311,37 +1400,43 @@ int32_t search_fronts_impl(mpap_workspace* ws, uint32_t index, uint32_t* front_p
     return MPAP_ERR_INVALID_ARG;
   }
   const uint32_t V = ws->last_V[index], base = ws->last_base[index];
-  std::vector<uint8_t> cur(V);
-  std::vector<uint32_t> cnt(2 * (size_t)V);
-  MPAP_CK(cudaMemcpyAsync(cur.data(), w.cur + base, V, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaMemcpyAsync(cnt.data(), w.f_cnt + base, 4 * (size_t)V, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaMemcpyAsync(cnt.data() + V, w.f_cnt + w.NV + base, 4 * (size_t)V, cudaMemcpyDeviceToHost, st));
-  const size_t slots = (size_t)V * w.fcap;
-  std::vector<long long> c0(slots), h0(slots), c1(slots), h1(slots);
-  MPAP_CK(cudaMemcpyAsync(c0.data(), w.f_cost + (size_t)base * w.fcap, 8 * slots, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaMemcpyAsync(h0.data(), w.f_h + (size_t)base * w.fcap, 8 * slots, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaMemcpyAsync(c1.data(), w.f_cost + ((size_t)w.NV + base) * w.fcap, 8 * slots,
-                          cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaMemcpyAsync(h1.data(), w.f_h + ((size_t)w.NV + base) * w.fcap, 8 * slots,
-                          cudaMemcpyDeviceToHost, st));
+  std::vector<uint4> fd(V);
+  MPAP_CK(cudaMemcpyAsync(fd.data(), w.fdesc + base, sizeof(uint4) * V, cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaStreamSynchronize(st));
+  std::vector<uint32_t> ptr(V + 1);
   uint64_t t = 0;
   for (uint32_t v = 0; v < V; ++v) {
-    if (front_ptr) front_ptr[v] = (uint32_t)t;
-    const uint32_t b = cur[v];
-    const uint32_t n = cnt[(size_t)b * V + v];
-    const long long* cs = b ? c1.data() : c0.data();
-    const long long* hs = b ? h1.data() : h0.data();
-    for (uint32_t j = 0; j < n; ++j, ++t) {
-      if (t < cap) {
-        if (cost) cost[t] = cs[(size_t)v * w.fcap + j];
-        if (h) h[t] = hs[(size_t)v * w.fcap + j];
-      }
-    }
+    ptr[v] = (uint32_t)t;
+    t += fd[v].y;
   }
-  if (front_ptr) front_ptr[V] = (uint32_t)t;
+  ptr[V] = (uint32_t)t;
+  if (front_ptr) std::memcpy(front_ptr, ptr.data(), 4 * ((size_t)V + 1));
   if (total) *total = t;
-  return t <= cap ? MPAP_OK : MPAP_ERR_INVALID_ARG;
+  if (t > cap) return MPAP_ERR_INVALID_ARG;
+  if (t == 0 || (!cost && !h)) return MPAP_OK;
+  // gather the fronts on the device into one packed block, then copy it out
+  const size_t b_ptr = (4 * ((size_t)V + 1) + 255) & ~(size_t)255;
+  char* blk = nullptr;
+  MPAP_CK(scratch_alloc((void**)&blk, b_ptr + 16 * t, st));
+  uint32_t* d_ptr = reinterpret_cast<uint32_t*>(blk);
+  long long* d_c = reinterpret_cast<long long*>(blk + b_ptr);
+  long long* d_h = d_c + t;
+  int32_t rc = MPAP_OK;
+  if (!cuda_ok(cudaMemcpyAsync(d_ptr, ptr.data(), 4 * ((size_t)V + 1), cudaMemcpyHostToDevice, st), "fronts ptr"))
+    rc = MPAP_ERR_CUDA;
+  if (rc == MPAP_OK) {
+    LaunchScope ls(st, "k_gather_fronts");
+    k_gather_fronts<<<std::min<uint32_t>((V + 7) / 8, 4096u), 256, 0, st>>>(w, base, V, d_ptr, d_c, d_h);
+    if (!cuda_ok(cudaGetLastError(), "k_gather_fronts")) rc = MPAP_ERR_CUDA;
+  }
+  if (rc == MPAP_OK && cost &&
+      !cuda_ok(cudaMemcpyAsync(cost, d_c, 8 * t, cudaMemcpyDeviceToHost, st), "fronts cost"))
+    rc = MPAP_ERR_CUDA;
+  if (rc == MPAP_OK && h && !cuda_ok(cudaMemcpyAsync(h, d_h, 8 * t, cudaMemcpyDeviceToHost, st), "fronts h"))
+    rc = MPAP_ERR_CUDA;
+  scratch_free(blk, st);
+  if (!cuda_ok(cudaStreamSynchronize(st), "search_fronts")) rc = MPAP_ERR_CUDA;
+  return rc;
 }
 
 

@@ -226,14 +226,22 @@ def surrogate_config(n: int = 32000) -> Config:
                    sigma_min=2 * CONFIGS["6d"].sigma_min, mc_rollouts=4096)
 
 
-def batch_specs(count: int = 256, seed: int = 7, n_lo: int = 1000, n_hi: int = 32000):
-    """(dim_kind, n, scene_seed) for the batched workload: n log-uniform in
-    [n_lo, n_hi], dimension uniform over {2d, 3d, 6d}."""
+def batch_specs(count: int = 256, seed: int = 7, n_lo: int = 1000, n_hi: int = 32000, n_hi_2d: int = 4000):
+    """(dim_kind, n, scene_seed) for the batched workload: dimension uniform over
+    {2d, 3d, 6d}, n log-uniform in [n_lo, n_hi] ([n_lo, min(n_hi, n_hi_2d)] for
+    2D, whose Pareto fronts grow without bound with n: the 2D heuristic gains are
+    continuous in edge length, so almost every path has its own h)."""
     rng = np.random.default_rng([int(seed), 0xBA7C4])
     dims = rng.choice([DIM_2D, DIM_3D, DIM_DI6], size=count)
-    ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count)).astype(np.int64)
+    u = rng.uniform(0.0, 1.0, size=count)
     seeds = rng.integers(1, 2**31 - 1, size=count)
-    return [(int(d), int(n), int(s)) for d, n, s in zip(dims, ns, seeds)]
+    out = []
+    for d, uu, s in zip(dims, u, seeds):
+        hi = min(n_hi, n_hi_2d) if d == DIM_2D else n_hi
+        hi = max(hi, n_lo)
+        n = int(math.exp(math.log(n_lo) + uu * (math.log(hi) - math.log(n_lo))))
+        out.append((int(d), n, int(s)))
+    return out
 
 
 def load_calibration() -> dict:

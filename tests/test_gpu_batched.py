@@ -37,7 +37,7 @@ def test_mixed_batch_matches_oracle(mp, orc):
         assert_same_graph(rg.export(), ro.graph())
     betas = [orc.beta_percentile(ro) for ro in ros]
     qs = [mp.make_query(b, 0.5) for b in betas]
-    ws = mp.Workspace(sum(rg.V for rg in rms), front_cap=4096, max_plans=1 << 23)
+    ws = mp.Workspace(sum(rg.V for rg in rms), front_cap=2048, max_plans=1 << 24)
     res = mp.search_batch(ws, rms, qs)
     solved = []
     for i, ((cfg, sc), ro, b) in enumerate(zip(batch, ros, betas)):
@@ -57,15 +57,15 @@ def test_autotune_search_keeps_results(mp):
     batch = _mixed(9, 5, 1000, 3000)
     rms = mp.build_roadmaps([mp.scene_spec(sc) for _, sc in batch])
     qs = [mp.make_query(1 << 62, 0.5) for _ in batch]
-    ws = mp.Workspace(sum(rg.V for rg in rms), front_cap=4096, max_plans=1 << 23)
+    ws = mp.Workspace(sum(rg.V for rg in rms), front_cap=2048, max_plans=1 << 24)
     mp.tuning_clear()
     ref = mp.search_batch(ws, rms, qs)
     ref_fronts = [ws.fronts(i) for i in range(len(rms))]
     tun, ms = mp.autotune_search(ws, rms, qs, reps=1)
-    assert ms > 0 and tun["front_cap"] >= 32 and (tun["front_cap"] & (tun["front_cap"] - 1)) == 0
+    assert ms > 0 and tun["front_cap"] >= 16 and (tun["front_cap"] & (tun["front_cap"] - 1)) == 0
     Vmax = max(rg.V for rg in rms)
     assert mp.tuning_get(0, Vmax) == tun            # stored under the mixed-batch key
-    for sel, pru in [(1, 1), (32, 2), (tun["select_blocks_per_sm"], tun["prune_blocks_per_sm"])]:
+    for sel, pru in [(1, 1), (32, 2), (64, 64), (tun["select_blocks_per_sm"], tun["prune_blocks_per_sm"])]:
         mp.tuning_set(0, Vmax, select_blocks_per_sm=sel, prune_blocks_per_sm=pru)
         got = mp.search_batch(ws, rms, qs)
         for i in range(len(rms)):

@@ -76,12 +76,11 @@ def test_scenes(mp, orc, ws, name, seed, n, beta_mode):
     a2 = orc.explore(ro, beta, lam_q, goal_termination=False)
     b2 = mp.search(ws, rg, beta, lam=0.5, goal_stop=False)
     assert_same_search(b2, a2, ws)
-    # a front cap below the largest final oracle front is reported, not truncated
-    # (fronts can be larger mid-search than at the end, so only this direction
-    # is implied by the final fronts)
-    biggest = int(np.diff(a2.front_ptr).max())
-    if biggest > 1:
-        small = mp.Workspace(rg.V, front_cap=biggest - 1, max_plans=1 << 23)
+    # a front pool that runs out is reported, not truncated: with one pool entry
+    # per node it lasts for at most V / 16 touched nodes (blocks hold 16 or more)
+    touched = int((np.diff(a2.front_ptr) > 0).sum())
+    if touched > rg.V // 16 + 1:
+        small = mp.Workspace(rg.V, front_cap=1, max_plans=1 << 23)
         with pytest.raises(mp.MpapError) as e:
             mp.search(small, rg, beta, lam=0.5, goal_stop=False)
         assert e.value.status == mp.MPAP_ERR_CAPACITY
@@ -111,7 +110,7 @@ def test_capacity_and_iteration_limits(mp, orc):
     ro = orc.build_roadmap(sc)
     rg = mp.build_roadmap_for_scene(sc)
     beta = orc.beta_percentile(ro)
-    small = mp.Workspace(rg.V, front_cap=4, max_plans=1 << 20)
+    small = mp.Workspace(rg.V, front_cap=2, max_plans=1 << 20)
     with pytest.raises(mp.MpapError) as e:
         mp.search(small, rg, beta)
     assert e.value.status == mp.MPAP_ERR_CAPACITY
@@ -154,3 +153,24 @@ def test_full_size_6d(mp, orc):
     a = orc.explore(ro, beta, orc.group_width(0.5, sc.cfg.r))
     b = mp.search(wsf, rg, beta, lam=0.5)
     assert_same_search(b, a, wsf)
+
+
+def test_query_error_stays_with_its_query(mp, orc):
+    """In one batch, a query that stops at its own iteration cap fails alone: the
+    other queries' results stay exact."""
+    specs = [("2d", 3, 800), ("6d", 2, 1500), ("3d", 4, 1200)]
+    rgs, ros, qs, betas = [], [], [], []
+    for name, seed, n in specs:
+        sc = scenegen.make_scene(name, seed, query_id=seed)
+        r = sc.cfg.r if name != "6d" else 18.0
+        ro = orc.build_roadmap(sc, n=n, r=r)
+        rgs.append(mp.build_roadmap_for_scene(sc, n=n, r=r)); ros.append((ro, r))
+        betas.append(orc.beta_percentile(ro))
+    total = sum(rg.V for rg in rgs)
+    wsb = mp.Workspace(total, front_cap=1024, max_plans=1 << 22)
+    qs = [mp.make_query(betas[0], 0.5, max_iters=3), mp.make_query(betas[1], 0.5), mp.make_query(betas[2], 0.5)]
+    res = mp.search_batch(wsb, rgs, qs, check=False)
+    assert res[0].status == mp.MPAP_ERR_ITER_LIMIT
+    for i in (1, 2):
+        ro, r = ros[i]
+        assert_same_search(res[i], orc.explore(ro, betas[i], orc.group_width(0.5, r)), wsb, index=i)
