@@ -298,22 +298,26 @@ def run_gpu(args, rank, world, local):
 # DRAM traffic from ncu captures (profiles/*.md), per unit of work, valid only
 # while the kernel sources are the ones that were captured.
 NCU_TRAFFIC = {
-    "k_edges": {"bytes_per_roadmap": (8.139776e6 + 35.685376e6) / 8,
-                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "26e0e2f093e32e194704078bba025fca173c0704",
+    "k_edges": {"bytes_per_roadmap": (10.0928e6 + 36.237056e6) / 8,
+                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "3232646ccb709cf0e592f862f18b2f772fe002a1",
                             "paper_1705_02408_gb300/csrc/common.cuh": "9d98f0917e0c93396e66c0986e42f7a820288d41"}},
+    # every k_prune launch of the 8-query, 2-step capture: 895.66 MB of DRAM reads +
+    # writes over 2 x 12,658,585 expansions (profiles/k_prune_6d16k.md)
+    "k_prune": {"bytes_per_expansion": 895661824.0 / (2 * 12658585.0),
+                "sources": {"paper_1705_02408_gb300/csrc/search.cu": "14f3fffca7c67ccece6091241c159a1d533ca532"}},
 }
 
 
-def _traffic(kernel, units):
+def _traffic(kernel, units, key="bytes_per_roadmap"):
     import hashlib
     t = NCU_TRAFFIC.get(kernel)
-    if not t:
+    if not t or key not in t:
         return None
     for path, sha in t["sources"].items():
         with open(os.path.join(ROOT, path), "rb") as f:
             if hashlib.sha1(f.read()).hexdigest() != sha:
                 return None
-    return t["bytes_per_roadmap"] * units
+    return t[key] * units
 
 
 def roofline(kern, arm, res, steps):
@@ -349,8 +353,14 @@ def roofline(kern, arm, res, steps):
     per_launch = bytes_step * steps / max(1, launches)
     achieved = per_launch / (ms / launches / 1e3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
+    # DRAM traffic: bytes per plan-edge expansion from an ncu capture of every
+    # launch of a smaller batch, times the expansions of one launch here
+    traffic = None
+    if name == "k_prune":
+        traffic = _traffic(name, exps * steps / max(1, launches), "bytes_per_expansion")
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_unit": "DRAM bytes per launch (ncu, per expansion of an 8-query capture)",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
 
 
@@ -594,16 +604,21 @@ def surrogate_report(args, stream):
         t = time.perf_counter()
         res = mp.search_batch(ws, rms, qs)
         cands = S.collect_candidates(ws, res, 64)
+        t1 = time.perf_counter()
         if mode == "plain":
             orders = [np.arange(len(c["paths"])) if c else np.zeros(0, np.int64) for c in cands]
         else:
             pf = S.predicted_failure(net, S.candidate_features(rms, cands))
             orders = [S.screened_order(p, SUR_TAU) for p in pf]
+        t2 = time.perf_counter()
         out = S.certify_in_order(rms, cands, mcs, orders, SUR_EPS)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t
+        t3 = time.perf_counter()
+        dt = t3 - t
         sel[mode] = out
         ev[mode] = {"ms_per_batch": dt * 1e3, "ms_per_query": dt * 1e3 / len(rms),
+                    "phase_ms": {"search_and_candidates": (t1 - t) * 1e3, "screen": (t2 - t1) * 1e3,
+                                 "certify_rounds": (t3 - t2) * 1e3},
                     "mc_calls": int(out.mc_calls.sum()), "mc_rounds": out.rounds,
                     "mc_rollouts": int(out.mc_calls.sum()) * cfg.mc_rollouts,
                     "solved": int((out.chosen >= 0).sum())}

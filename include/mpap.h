@@ -348,6 +348,16 @@ int32_t mpap_search_candidates(mpap_workspace* ws, uint32_t index, uint32_t cap,
                                int64_t* h, uint32_t* path_ptr, uint32_t* path, uint32_t path_cap,
                                uint32_t* n, uint32_t* total, void* stream);
 
+/* mpap_search_candidates for queries 0 .. nq-1 of the last search on ws in one
+ * launch (one block per query).  Host outputs in slices: query i writes up to cap
+ * candidates to cost[i cap ..], h[i cap ..], offsets path_ptr[i (cap+1) ..] into
+ * its path slice path[i path_cap ..], and n[i], total[i]; a query that did not
+ * finish with MPAP_OK gets n[i] = total[i] = 0.  MPAP_ERR_CAPACITY if a query's
+ * paths exceed path_cap. */
+int32_t mpap_search_candidates_batch(mpap_workspace* ws, uint32_t nq, uint32_t cap, int64_t* cost,
+                                     int64_t* h, uint32_t* path_ptr, uint32_t* path,
+                                     uint32_t path_cap, uint32_t* n, uint32_t* total, void* stream);
+
 /* 48 trajectory features of each of n plans on one roadmap (input of the
  * surrogate).  Plan i is the host node sequence path[path_ptr[i] ..
  * path_ptr[i+1]) (at least 2 nodes).  Its Monte Carlo checkpoints (the M
@@ -362,6 +372,13 @@ int32_t mpap_search_candidates(mpap_workspace* ws, uint32_t index, uint32_t cap,
 #define MPAP_FEATURES 48
 int32_t mpap_plan_features(mpap_roadmap* rm, uint32_t n, const uint32_t* path_ptr,
                            const uint32_t* path, float* feat, void* stream);
+
+/* mpap_plan_features for plans on several roadmaps in one launch: the plans of
+ * rms[r] are plan_ptr[r] .. plan_ptr[r+1]-1 (plan_ptr has n_rm + 1 entries), plan
+ * i is path[path_ptr[i] .. path_ptr[i+1]) and gets feat[48 (i - plan_ptr[0]) ..]. */
+int32_t mpap_plan_features_batch(mpap_roadmap* const* rms, uint32_t n_rm, const uint32_t* plan_ptr,
+                                 const uint32_t* path_ptr, const uint32_t* path, float* feat,
+                                 void* stream);
 
 /* The surrogate network: 48 -> 128 -> 128 -> 128 -> 2 with ReLU, logits of
  * (collision, localisation) failure; bfloat16 weights and activations in every

@@ -35,7 +35,8 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_launch_count", "mpap_profile_read", "mpap_search_candidates", "mpap_plan_features",
            "mpap_mlp_create", "mpap_mlp_free", "mpap_mlp_get_params", "mpap_mlp_set_params",
            "mpap_mlp_forward", "mpap_mlp_train_step", "mpap_tuning_get", "mpap_tuning_set",
-           "mpap_tuning_clear", "mpap_tuning_export", "mpap_autotune_build", "mpap_autotune_search"]
+           "mpap_tuning_clear", "mpap_tuning_export", "mpap_autotune_build", "mpap_autotune_search",
+           "mpap_search_candidates_batch", "mpap_plan_features_batch"]
 
 
 class mpap_scene(C.Structure):
@@ -141,6 +142,10 @@ def lib():
         u32p = C.POINTER(C.c_uint32)
         L.mpap_search_candidates.restype = i32
         L.mpap_search_candidates.argtypes = [P, C.c_uint32, C.c_uint32, P, P, P, P, C.c_uint32, u32p, u32p, P]
+        L.mpap_search_candidates_batch.restype = i32
+        L.mpap_search_candidates_batch.argtypes = [P, C.c_uint32, C.c_uint32, P, P, P, P, C.c_uint32, P, P, P]
+        L.mpap_plan_features_batch.restype = i32
+        L.mpap_plan_features_batch.argtypes = [C.POINTER(P), C.c_uint32, P, P, P, P, P]
         L.mpap_plan_features.restype = i32
         L.mpap_plan_features.argtypes = [P, C.c_uint32, P, P, P, P]
         L.mpap_mlp_create.restype = i32
@@ -716,3 +721,48 @@ def autotune_search(ws, rms, queries, reps=2, stream=None):
     _check(lib().mpap_autotune_search(ws.h, hs, qs, nq, int(reps), C.byref(t), C.byref(ms), _stream(stream)),
            "mpap_autotune_search")
     return _tuning_dict(t), ms.value
+
+
+def search_candidates_batch(ws: Workspace, nq, cap=64, path_cap=1 << 14, stream=None):
+    """mpap_search_candidates_batch: candidates of queries 0..nq-1 of the last search
+    (one launch); a list of dicts as search_candidates, None for unsolved queries."""
+    cost = np.zeros((max(nq, 1), cap), np.int64)
+    hh = np.zeros((max(nq, 1), cap), np.int64)
+    ptr = np.zeros((max(nq, 1), cap + 1), np.uint32)
+    path = np.zeros((max(nq, 1), path_cap), np.uint32)
+    n = np.zeros(max(nq, 1), np.uint32)
+    tot = np.zeros(max(nq, 1), np.uint32)
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(lib().mpap_search_candidates_batch(ws.h, nq, cap, vp(cost), vp(hh), vp(ptr), vp(path), path_cap,
+                                              vp(n), vp(tot), _stream(stream)), "mpap_search_candidates_batch")
+    out = []
+    for i in range(nq):
+        k = int(n[i])
+        if k == 0:
+            out.append(None)
+            continue
+        out.append(dict(cost=cost[i, :k].copy(), h=hh[i, :k].copy(), total=int(tot[i]),
+                        paths=[path[i, ptr[i, j]:ptr[i, j + 1]].copy() for j in range(k)]))
+    return out
+
+
+def plan_features_batch(rms, paths_per_rm, stream=None):
+    """mpap_plan_features_batch: features of the plans of several roadmaps in one
+    launch; returns one [k_r, 48] array per roadmap."""
+    n_rm = len(rms)
+    counts = [len(p) for p in paths_per_rm]
+    plan_ptr = np.zeros(n_rm + 1, np.uint32)
+    plan_ptr[1:] = np.cumsum(counts)
+    flat_paths = [np.asarray(p, np.uint32) for ps in paths_per_rm for p in ps]
+    n = len(flat_paths)
+    if n == 0:
+        return [np.zeros((0, N_FEATURES), np.float32) for _ in rms]
+    path_ptr = np.zeros(n + 1, np.uint32)
+    path_ptr[1:] = np.cumsum([len(p) for p in flat_paths])
+    flat = np.ascontiguousarray(np.concatenate(flat_paths), np.uint32)
+    feat = np.zeros((n, N_FEATURES), np.float32)
+    hs = (C.c_void_p * n_rm)(*[rm.h for rm in rms])
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(lib().mpap_plan_features_batch(hs, n_rm, vp(plan_ptr), vp(path_ptr), vp(flat), vp(feat),
+                                          _stream(stream)), "mpap_plan_features_batch")
+    return [feat[plan_ptr[r]:plan_ptr[r + 1]] for r in range(n_rm)]

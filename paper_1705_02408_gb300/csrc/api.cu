@@ -24,6 +24,11 @@ int32_t search_candidates_impl(mpap_workspace* ws, uint32_t index, uint32_t cap,
                                uint32_t* total_out, cudaStream_t st);
 int32_t plan_features_impl(mpap_roadmap* rm, uint32_t n, const uint32_t* path_ptr, const uint32_t* path, float* feat,
                            cudaStream_t st);
+int32_t plan_features_batch_impl(mpap_roadmap* const* rms, uint32_t n_rm, const uint32_t* plan_ptr,
+                                 const uint32_t* path_ptr, const uint32_t* path, float* feat, cudaStream_t st);
+int32_t search_candidates_batch_impl(mpap_workspace* ws, uint32_t nq, uint32_t cap, int64_t* cost, int64_t* h,
+                                     uint32_t* path_ptr, uint32_t* path, uint32_t path_cap, uint32_t* n_out,
+                                     uint32_t* total_out, cudaStream_t st);
 int32_t mlp_create(uint64_t seed, uint32_t max_batch, mpap_mlp** out);
 void mlp_free(mpap_mlp* n);
 int32_t mlp_get_params(mpap_mlp* n, float* params, cudaStream_t st);
@@ -362,6 +367,25 @@ int32_t mpap_search_candidates(mpap_workspace* ws, uint32_t index, uint32_t cap,
 int32_t mpap_plan_features(mpap_roadmap* rm, uint32_t n, const uint32_t* path_ptr, const uint32_t* path, float* feat,
                            void* stream) {
   return mpap::plan_features_impl(rm, n, path_ptr, path, feat, S(stream));
+}
+
+int32_t mpap_plan_features_batch(mpap_roadmap* const* rms, uint32_t n_rm, const uint32_t* plan_ptr,
+                                 const uint32_t* path_ptr, const uint32_t* path, float* feat, void* stream) {
+  return mpap::plan_features_batch_impl(rms, n_rm, plan_ptr, path_ptr, path, feat, S(stream));
+}
+
+int32_t mpap_search_candidates_batch(mpap_workspace* ws, uint32_t nq, uint32_t cap, int64_t* cost, int64_t* h,
+                                     uint32_t* path_ptr, uint32_t* path, uint32_t path_cap, uint32_t* n,
+                                     uint32_t* total, void* stream) {
+  if (!ws || (nq && (!n || !cost || !h || !path_ptr || !path))) {
+    set_error("search_candidates_batch: null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (cap > (1u << 16)) {
+    set_error("search_candidates_batch: cap must be at most 65536");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::search_candidates_batch_impl(ws, nq, cap, cost, h, path_ptr, path, path_cap, n, total, S(stream));
 }
 
 int32_t mpap_mlp_create(uint64_t seed, uint32_t max_batch, mpap_mlp** out) {

@@ -11,6 +11,7 @@
 //                     checkpoints (relocalisation contraction, Irwin-Hall(12)
 //                     noise from Philox4x32-10), counting localisation and
 //                     collision/leave-map failures.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -412,16 +413,17 @@ struct FeatJob {
   const float* x;
   uint32_t V;
   int K;
-  uint32_t n;
-  const uint32_t* ptr;     // [n + 1]
+  uint32_t p0, n;          // plans p0 .. p0 + n - 1 lie on this roadmap
+  const uint32_t* ptr;     // [plans + 1] offsets into path
   const uint32_t* path;
-  float* feat;             // [n][48]
+  float* feat;             // [plans][48]
 };
 
-__global__ void k_plan_features(FeatJob J) {
+__global__ void k_plan_features(const FeatJob* __restrict__ jobs) {
+  const FeatJob& J = jobs[blockIdx.y];
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= J.n * 16u) return;
-  const uint32_t i = t >> 4, j = t & 15u;
+  const uint32_t i = J.p0 + (t >> 4), j = t & 15u;
   const uint32_t p0 = J.ptr[i], len = J.ptr[i + 1] - p0;
   const uint32_t M = (uint32_t)J.g.M;
   const uint32_t steps = len >= 2 ? (len - 1) * M : 0u;
@@ -475,59 +477,96 @@ __global__ void k_plan_features(FeatJob J) {
   }
 }
 
+// Features of plans on n_rm roadmaps in one launch: the plans of roadmap r are
+// plan_ptr[r] .. plan_ptr[r+1] - 1, plan i is path[path_ptr[i] .. path_ptr[i+1]).
+int32_t plan_features_batch_impl(mpap_roadmap* const* rms, uint32_t n_rm, const uint32_t* plan_ptr,
+                                 const uint32_t* path_ptr, const uint32_t* path, float* feat, cudaStream_t st) {
+  if (!rms || !plan_ptr || (plan_ptr[n_rm] > plan_ptr[0] && (!path_ptr || !path || !feat))) {
+    set_error("plan_features: null array");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  const uint32_t P0 = plan_ptr[0], n = plan_ptr[n_rm] - P0;
+  if (n == 0) return MPAP_OK;
+  uint32_t max_plans = 0;
+  for (uint32_t r = 0; r < n_rm; ++r) {
+    const mpap_roadmap* rm = rms[r];
+    if (plan_ptr[r + 1] < plan_ptr[r]) {
+      set_error("plan_features: plan_ptr must not decrease");
+      return MPAP_ERR_INVALID_ARG;
+    }
+    if (plan_ptr[r + 1] == plan_ptr[r]) continue;
+    if (!rm || !rm->has_geometry) {
+      set_error("plan_features: roadmap %u has no geometry", r);
+      return MPAP_ERR_INVALID_ARG;
+    }
+    max_plans = std::max(max_plans, plan_ptr[r + 1] - plan_ptr[r]);
+    for (uint32_t i = plan_ptr[r]; i < plan_ptr[r + 1]; ++i) {
+      if (path_ptr[i + 1] < path_ptr[i] + 2) {
+        set_error("plan_features: plan %u has fewer than 2 nodes", i);
+        return MPAP_ERR_INVALID_ARG;
+      }
+      for (uint32_t k = path_ptr[i]; k < path_ptr[i + 1]; ++k)
+        if (path[k] >= rm->V) {
+          set_error("plan_features: node %u out of range on roadmap %u", path[k], r);
+          return MPAP_ERR_INVALID_ARG;
+        }
+    }
+  }
+  const uint32_t base = path_ptr[P0], total = path_ptr[P0 + n] - base;
+  std::vector<uint32_t> ptr(n + 1);
+  for (uint32_t i = 0; i <= n; ++i) ptr[i] = path_ptr[P0 + i] - base;
+  std::vector<FeatJob> jobs;
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t b_jobs = up(sizeof(FeatJob) * n_rm), b_ptr = up(4 * ((size_t)n + 1)), b_path = up(4 * (size_t)total),
+               b_feat = 4 * 48 * (size_t)n;
+  char* blk = nullptr;
+  MPAP_CK(scratch_alloc((void**)&blk, b_jobs + b_ptr + b_path + b_feat, st));
+  const uint32_t* d_ptr = (const uint32_t*)(blk + b_jobs);
+  const uint32_t* d_path = (const uint32_t*)(blk + b_jobs + b_ptr);
+  float* d_feat = (float*)(blk + b_jobs + b_ptr + b_path);
+  for (uint32_t r = 0; r < n_rm; ++r) {
+    if (plan_ptr[r + 1] == plan_ptr[r]) continue;
+    FeatJob J;
+    J.g = rms[r]->geom;
+    J.x = rms[r]->x;
+    J.V = rms[r]->V;
+    J.K = rms[r]->K;
+    J.p0 = plan_ptr[r] - P0;
+    J.n = plan_ptr[r + 1] - plan_ptr[r];
+    J.ptr = d_ptr;
+    J.path = d_path;
+    J.feat = d_feat;
+    jobs.push_back(J);
+  }
+  int32_t rc = MPAP_OK;
+  if (!cuda_ok(cudaMemcpyAsync(blk, jobs.data(), sizeof(FeatJob) * jobs.size(), cudaMemcpyHostToDevice, st),
+               "features jobs") ||
+      !cuda_ok(cudaMemcpyAsync((void*)d_ptr, ptr.data(), 4 * ((size_t)n + 1), cudaMemcpyHostToDevice, st),
+               "features ptr") ||
+      !cuda_ok(cudaMemcpyAsync((void*)d_path, path + base, 4 * (size_t)total, cudaMemcpyHostToDevice, st),
+               "features path"))
+    rc = MPAP_ERR_CUDA;
+  if (rc == MPAP_OK) {
+    LaunchScope ls(st, "k_plan_features");
+    const dim3 grid((max_plans * 16 + 255) / 256, (uint32_t)jobs.size());
+    k_plan_features<<<grid, 256, 0, st>>>((const FeatJob*)blk);
+    if (!cuda_ok(cudaGetLastError(), "k_plan_features")) rc = MPAP_ERR_CUDA;
+  }
+  if (rc == MPAP_OK && !cuda_ok(cudaMemcpyAsync(feat, d_feat, b_feat, cudaMemcpyDeviceToHost, st), "features out"))
+    rc = MPAP_ERR_CUDA;
+  scratch_free(blk, st);
+  if (!cuda_ok(cudaStreamSynchronize(st), "plan_features")) rc = MPAP_ERR_CUDA;
+  return rc;
+}
+
 int32_t plan_features_impl(mpap_roadmap* rm, uint32_t n, const uint32_t* path_ptr, const uint32_t* path, float* feat,
                            cudaStream_t st) {
   if (!rm || !rm->has_geometry) {
     set_error("plan_features: roadmap has no geometry");
     return MPAP_ERR_INVALID_ARG;
   }
-  if (n == 0) return MPAP_OK;
-  if (!path_ptr || !path || !feat) {
-    set_error("plan_features: null array");
-    return MPAP_ERR_INVALID_ARG;
-  }
-  const uint32_t total = path_ptr[n] - path_ptr[0];
-  for (uint32_t i = 0; i < n; ++i) {
-    if (path_ptr[i + 1] < path_ptr[i] + 2) {
-      set_error("plan_features: plan %u has fewer than 2 nodes", i);
-      return MPAP_ERR_INVALID_ARG;
-    }
-  }
-  for (uint32_t k = 0; k < total; ++k)
-    if (path[path_ptr[0] + k] >= rm->V) {
-      set_error("plan_features: node %u out of range", path[path_ptr[0] + k]);
-      return MPAP_ERR_INVALID_ARG;
-    }
-  std::vector<uint32_t> ptr(n + 1);
-  for (uint32_t i = 0; i <= n; ++i) ptr[i] = path_ptr[i] - path_ptr[0];
-  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const size_t b_ptr = up(4 * ((size_t)n + 1)), b_path = up(4 * (size_t)total), b_feat = 4 * 48 * (size_t)n;
-  char* blk = nullptr;
-  MPAP_CK(scratch_alloc((void**)&blk, b_ptr + b_path + b_feat, st));
-  FeatJob J;
-  J.g = rm->geom;
-  J.x = rm->x;
-  J.V = rm->V;
-  J.K = rm->K;
-  J.n = n;
-  J.ptr = (const uint32_t*)blk;
-  J.path = (const uint32_t*)(blk + b_ptr);
-  J.feat = (float*)(blk + b_ptr + b_path);
-  int32_t rc = MPAP_OK;
-  if (!cuda_ok(cudaMemcpyAsync(blk, ptr.data(), 4 * ((size_t)n + 1), cudaMemcpyHostToDevice, st), "features ptr") ||
-      !cuda_ok(cudaMemcpyAsync(blk + b_ptr, path + path_ptr[0], 4 * (size_t)total, cudaMemcpyHostToDevice, st),
-               "features path"))
-    rc = MPAP_ERR_CUDA;
-  if (rc == MPAP_OK) {
-    LaunchScope ls(st, "k_plan_features");
-    k_plan_features<<<(n * 16 + 255) / 256, 256, 0, st>>>(J);
-    if (!cuda_ok(cudaGetLastError(), "k_plan_features")) rc = MPAP_ERR_CUDA;
-  }
-  if (rc == MPAP_OK && !cuda_ok(cudaMemcpyAsync(feat, J.feat, b_feat, cudaMemcpyDeviceToHost, st), "features out"))
-    rc = MPAP_ERR_CUDA;
-  scratch_free(blk, st);
-  if (!cuda_ok(cudaStreamSynchronize(st), "plan_features")) rc = MPAP_ERR_CUDA;
-  return rc;
+  const uint32_t plan_ptr[2] = {0, n};
+  return plan_features_batch_impl(&rm, 1, plan_ptr, path_ptr, path, feat, st);
 }
 
 }  // namespace mpap

@@ -1013,7 +1013,25 @@ __device__ __forceinline__ Best goal_plan(const WS& w, uint32_t v, uint32_t ref,
   return c;
 }
 
-__global__ void __launch_bounds__(256) k_candidates(WS w, uint32_t q, uint32_t cap, CandOut o) {
+// One block per query q0 + blockIdx.x; block b writes slice b of every output
+// (cap candidates, cap + 1 offsets, path_cap path entries, 4 counters).  A query
+// that did not finish with MPAP_OK gets zero counts.
+__global__ void __launch_bounds__(256) k_candidates(WS w, uint32_t q0, uint32_t cap, CandOut ob) {
+  const uint32_t b = blockIdx.x, q = q0 + b;
+  CandOut o = ob;
+  o.cost += (size_t)b * cap;
+  o.h += (size_t)b * cap;
+  o.ref += (size_t)b * cap;
+  o.ptr += (size_t)b * (cap + 1);
+  o.path += (size_t)b * o.path_cap;
+  o.counts += (size_t)b * 4;
+  if (w.res[q].status != MPAP_OK) {
+    if (threadIdx.x == 0) {
+      o.ptr[0] = 0;
+      o.counts[0] = o.counts[1] = o.counts[2] = 0;
+    }
+    return;
+  }
   const QueryDev& Q = w.qd[q];
   __shared__ Best sb[256];
   __shared__ Best prev;
@@ -1440,6 +1458,57 @@ int32_t search_fronts_impl(mpap_workspace* ws, uint32_t index, uint32_t* front_p
 }
 
 
+namespace {
+
+// Candidates of queries q0 .. q0 + nq - 1 into host arrays laid out in slices:
+// cost/h [nq][cap], path_ptr [nq][cap + 1], path [nq][path_cap], n/total/ovf [nq].
+int32_t candidates_run(mpap_workspace* ws, uint32_t q0, uint32_t nq, uint32_t cap, uint32_t path_cap,
+                       int64_t* cost, int64_t* h, uint32_t* path_ptr, uint32_t* path, uint32_t* n_out,
+                       uint32_t* total_out, uint32_t* ovf_out, cudaStream_t st) {
+  const WS& w = ws->w;
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t b_cost = up(8 * (size_t)nq * cap), b_ref = up(4 * (size_t)nq * cap),
+               b_ptr = up(4 * (size_t)nq * (cap + 1)), b_cnt = up(16 * (size_t)nq),
+               b_path = up(4 * (size_t)nq * path_cap + 4);
+  char* buf = nullptr;
+  MPAP_CK(scratch_alloc((void**)&buf, 2 * b_cost + b_ref + b_ptr + b_cnt + b_path, st));
+  CandOut o;
+  o.cost = reinterpret_cast<long long*>(buf);
+  o.h = reinterpret_cast<long long*>(buf + b_cost);
+  o.ref = reinterpret_cast<uint32_t*>(buf + 2 * b_cost);
+  o.ptr = reinterpret_cast<uint32_t*>(buf + 2 * b_cost + b_ref);
+  o.counts = reinterpret_cast<uint32_t*>(buf + 2 * b_cost + b_ref + b_ptr);
+  o.path = reinterpret_cast<uint32_t*>(buf + 2 * b_cost + b_ref + b_ptr + b_cnt);
+  o.path_cap = path_cap;
+  {
+    LaunchScope ls(st, "k_candidates");
+    k_candidates<<<nq, 256, 0, st>>>(w, q0, cap, o);
+  }
+  int32_t rc = cuda_ok(cudaGetLastError(), "k_candidates") ? MPAP_OK : MPAP_ERR_CUDA;
+  std::vector<uint32_t> counts(4 * (size_t)nq);
+  if (rc == MPAP_OK &&
+      (!cuda_ok(cudaMemcpyAsync(counts.data(), o.counts, 16 * (size_t)nq, cudaMemcpyDeviceToHost, st), "counts") ||
+       (cost && !cuda_ok(cudaMemcpyAsync(cost, o.cost, 8 * (size_t)nq * cap, cudaMemcpyDeviceToHost, st), "cost")) ||
+       (h && !cuda_ok(cudaMemcpyAsync(h, o.h, 8 * (size_t)nq * cap, cudaMemcpyDeviceToHost, st), "h")) ||
+       (path_ptr && !cuda_ok(cudaMemcpyAsync(path_ptr, o.ptr, 4 * (size_t)nq * (cap + 1), cudaMemcpyDeviceToHost, st),
+                             "path_ptr")) ||
+       (path && !cuda_ok(cudaMemcpyAsync(path, o.path, 4 * (size_t)nq * path_cap, cudaMemcpyDeviceToHost, st),
+                         "path"))))
+    rc = MPAP_ERR_CUDA;
+  scratch_free(buf, st);
+  if (!cuda_ok(cudaStreamSynchronize(st), "candidates")) rc = MPAP_ERR_CUDA;
+  if (rc == MPAP_OK) {
+    for (uint32_t i = 0; i < nq; ++i) {
+      if (n_out) n_out[i] = counts[4 * i];
+      if (total_out) total_out[i] = counts[4 * i + 1];
+      if (ovf_out) ovf_out[i] = counts[4 * i + 2];
+    }
+  }
+  return rc;
+}
+
+}  // namespace
+
 int32_t search_candidates_impl(mpap_workspace* ws, uint32_t index, uint32_t cap, int64_t* cost, int64_t* h,
                                uint32_t* path_ptr, uint32_t* path, uint32_t path_cap, uint32_t* n_out,
                                uint32_t* total_out, cudaStream_t st) {
@@ -1459,47 +1528,49 @@ int32_t search_candidates_impl(mpap_workspace* ws, uint32_t index, uint32_t cap,
     if (n_out) *n_out = 0;
     return MPAP_OK;
   }
-  const size_t bytes = (size_t)cap * 20 + 4 * ((size_t)cap + 1) + 4 * (size_t)path_cap + 16 + 64;
-  char* buf = nullptr;
-  MPAP_CK(scratch_alloc((void**)&buf, bytes, st));
-  CandOut o;
-  o.cost = reinterpret_cast<long long*>(buf);
-  o.h = o.cost + cap;
-  o.ref = reinterpret_cast<uint32_t*>(o.h + cap);
-  o.ptr = o.ref + cap;
-  o.counts = o.ptr + cap + 1;
-  o.path = o.counts + 4;
-  o.path_cap = path_cap;
-  {
-    LaunchScope ls(st, "k_candidates");
-    k_candidates<<<1, 256, 0, st>>>(w, index, cap, o);
+  std::vector<int64_t> c(cap), hh(cap);
+  std::vector<uint32_t> p(cap + 1), pa(path_cap ? path_cap : 1);
+  uint32_t n = 0, total = 0, ovf = 0;
+  int32_t rc = candidates_run(ws, index, 1, cap, path_cap, c.data(), hh.data(), p.data(), pa.data(), &n, &total,
+                              &ovf, st);
+  if (rc) return rc;
+  if (n_out) *n_out = n;
+  if (total_out) *total_out = total;
+  if (ovf) {
+    set_error("search_candidates: paths need more than path_cap = %u entries", path_cap);
+    return MPAP_ERR_CAPACITY;
   }
-  int32_t rc = cudaGetLastError() == cudaSuccess ? MPAP_OK : MPAP_ERR_CUDA;
-  uint32_t counts[3] = {0, 0, 0};
-  if (rc == MPAP_OK) {
-    cudaMemcpyAsync(counts, o.counts, 12, cudaMemcpyDeviceToHost, st);
-    rc = cuda_ok(cudaStreamSynchronize(st), "k_candidates") ? MPAP_OK : MPAP_ERR_CUDA;
-  }
-  const uint32_t nc = counts[0];
-  if (rc == MPAP_OK) {
-    if (n_out) *n_out = nc;
-    if (total_out) *total_out = counts[1];
-    if (cost) cudaMemcpyAsync(cost, o.cost, 8 * (size_t)nc, cudaMemcpyDeviceToHost, st);
-    if (h) cudaMemcpyAsync(h, o.h, 8 * (size_t)nc, cudaMemcpyDeviceToHost, st);
-    if (path_ptr) cudaMemcpyAsync(path_ptr, o.ptr, 4 * ((size_t)nc + 1), cudaMemcpyDeviceToHost, st);
-    if (counts[2]) {
-      set_error("search_candidates: paths need more than path_cap = %u entries", path_cap);
-      rc = MPAP_ERR_CAPACITY;
-    }
-    rc = cuda_ok(cudaStreamSynchronize(st), "candidates copy") ? rc : MPAP_ERR_CUDA;
-    if (rc == MPAP_OK && path && path_ptr && nc)
-      rc = cuda_ok(cudaMemcpyAsync(path, o.path, 4 * (size_t)path_ptr[nc], cudaMemcpyDeviceToHost, st), "path copy")
-               ? MPAP_OK
-               : MPAP_ERR_CUDA;
-  }
-  scratch_free(buf, st);
-  if (!cuda_ok(cudaStreamSynchronize(st), "candidates")) rc = MPAP_ERR_CUDA;
-  return rc;
+  if (cost) std::memcpy(cost, c.data(), 8 * (size_t)n);
+  if (h) std::memcpy(h, hh.data(), 8 * (size_t)n);
+  if (path_ptr) std::memcpy(path_ptr, p.data(), 4 * ((size_t)n + 1));
+  if (path && n) std::memcpy(path, pa.data(), 4 * (size_t)p[n]);
+  return MPAP_OK;
 }
+
+int32_t search_candidates_batch_impl(mpap_workspace* ws, uint32_t nq, uint32_t cap, int64_t* cost, int64_t* h,
+                                     uint32_t* path_ptr, uint32_t* path, uint32_t path_cap, uint32_t* n_out,
+                                     uint32_t* total_out, cudaStream_t st) {
+  if (nq > ws->last_V.size()) {
+    set_error("search_candidates_batch: the last search had %zu queries", ws->last_V.size());
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (nq == 0 || cap == 0) {
+    for (uint32_t i = 0; i < nq; ++i) {
+      if (n_out) n_out[i] = 0;
+      if (total_out) total_out[i] = 0;
+    }
+    return MPAP_OK;
+  }
+  std::vector<uint32_t> ovf(nq);
+  int32_t rc = candidates_run(ws, 0, nq, cap, path_cap, cost, h, path_ptr, path, n_out, total_out, ovf.data(), st);
+  if (rc) return rc;
+  for (uint32_t i = 0; i < nq; ++i)
+    if (ovf[i]) {
+      set_error("search_candidates_batch: query %u needs more than path_cap = %u path entries", i, path_cap);
+      return MPAP_ERR_CAPACITY;
+    }
+  return MPAP_OK;
+}
+
 
 }  // namespace mpap

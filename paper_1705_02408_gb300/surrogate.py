@@ -20,18 +20,18 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import Mlp, certify_batch, plan_features, search_candidates
+from . import Mlp, certify_batch, plan_features_batch, search_candidates_batch
 
 
-def collect_candidates(ws, results, cap=64):
+def collect_candidates(ws, results, cap=64, path_cap=1 << 14):
     """P_candidates (up to cap, in solution order) of every query of the last
-    mpap_search_batch on ws; None for a query without a solution."""
-    return [search_candidates(ws, i, cap=cap) if r.status == 0 else None for i, r in enumerate(results)]
+    mpap_search_batch on ws, in one launch; None for a query without a solution."""
+    return search_candidates_batch(ws, len(results), cap=cap, path_cap=path_cap)
 
 
 def candidate_features(rms, cands):
-    """[k_i, 48] float32 features per query (k_i = number of candidates)."""
-    return [plan_features(rm, c["paths"]) if c else np.zeros((0, 48), np.float32) for rm, c in zip(rms, cands)]
+    """[k_i, 48] float32 features per query (k_i = number of candidates), in one launch."""
+    return plan_features_batch(rms, [c["paths"] if c else [] for c in cands])
 
 
 def mc_rates(rms, cands, mcs, call_base=0):

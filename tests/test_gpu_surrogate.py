@@ -173,3 +173,31 @@ def test_mlp_rejects_oversized_batch(mp):
     with pytest.raises(mp.MpapError) as e:
         net.forward(np.zeros((129, 48), np.float32))
     assert e.value.status == mp.MPAP_ERR_INVALID_ARG
+
+
+def test_batched_candidates_and_features_match_single_calls(mp, orc):
+    """mpap_search_candidates_batch / mpap_plan_features_batch (one launch for a
+    whole batch) give exactly what the per-query calls give."""
+    specs = [("2d", 2, 600), ("6d", 1, 2500), ("2d", 1, 600), ("3d", 2, 1500), ("6d", 4, 2500)]
+    rms, qs = [], []
+    for name, seed, n in specs:
+        sc = scenegen.make_scene(name, seed, query_id=seed)
+        r = sc.cfg.r if name != "6d" else 18.0
+        ro = orc.build_roadmap(sc, n=n, r=r)
+        rms.append(mp.build_roadmap_for_scene(sc, n=n, r=r))
+        qs.append(mp.make_query(orc.beta_percentile(ro), 0.5, goal_stop=False))
+    wsb = mp.Workspace(sum(rg.V for rg in rms), front_cap=1024, max_plans=1 << 23)
+    res = mp.search_batch(wsb, rms, qs)
+    batch = mp.search_candidates_batch(wsb, len(rms), cap=40)
+    assert any(c is None for c in batch) or all(r.status == 0 for r in res)
+    for i, (r, c) in enumerate(zip(res, batch)):
+        if r.status != 0:
+            assert c is None
+            continue
+        _same_candidates(c, mp.search_candidates(wsb, i, cap=40))
+    feats = mp.plan_features_batch(rms, [c["paths"] if c else [] for c in batch])
+    for rg, c, f in zip(rms, batch, feats):
+        if c:
+            np.testing.assert_array_equal(f, mp.plan_features(rg, c["paths"]))
+        else:
+            assert f.shape == (0, 48)
