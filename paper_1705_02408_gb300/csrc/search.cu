@@ -448,24 +448,54 @@ __device__ __forceinline__ uint32_t chunk_skyline(WarpSmem& sm, bool ok, long lo
                                                   uint32_t ctb, uint32_t cpp) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
-  long long kc = ok ? cc : LLONG_MAX, kh = ok ? ch : LLONG_MAX;
-  uint32_t kt = ok ? ctb : 0xFFFFFFFFu, kp = cpp;
+  const long long vh = ok ? ch : LLONG_MAX;
+  const uint32_t vt = ok ? ctb : 0xFFFFFFFFu;
+  // 1. sort (cost, source lane) only -- two shuffles of key and index per
+  //    step -- then gather the rest of each candidate from its source lane
+  long long kc = ok ? cc : LLONG_MAX;
+  uint32_t ks = lane;
 #pragma unroll
   for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      const long long oc = shfl_xor_i64(kc, j), oh = shfl_xor_i64(kh, j);
-      const uint32_t ot = __shfl_xor_sync(kFull, kt, j), op = __shfl_xor_sync(kFull, kp, j);
+      const long long oc = shfl_xor_i64(kc, j);
+      const uint32_t os = __shfl_xor_sync(kFull, ks, j);
       const bool up = (lane & k) == 0;
       const bool lower = (lane & j) == 0;
-      const bool o_less = key_less(oc, oh, ot, kc, kh, kt);
-      const bool m_less = key_less(kc, kh, kt, oc, oh, ot);
-      const bool take = (lower == up) ? o_less : m_less;
+      const bool o_less = oc < kc || (oc == kc && os < ks);
+      const bool take = (lower == up) ? o_less : !o_less;
       if (take) {
         kc = oc;
-        kh = oh;
-        kt = ot;
-        kp = op;
+        ks = os;
+      }
+    }
+  }
+  long long kh = shfl_i64(vh, (int)ks);
+  uint32_t kt = __shfl_sync(kFull, vt, (int)ks), kp = __shfl_sync(kFull, cpp, (int)ks);
+  // 2. equal costs among real candidates must be ordered by (h, tie key) too:
+  //    then sort the chunk again on the full key (rare)
+  {
+    const long long pc = shfl_up_i64(kc, 1);
+    const bool tie = lane > 0 && kt != 0xFFFFFFFFu && pc == kc;
+    if (__any_sync(kFull, tie)) {
+#pragma unroll
+      for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const long long oc = shfl_xor_i64(kc, j), oh = shfl_xor_i64(kh, j);
+          const uint32_t ot = __shfl_xor_sync(kFull, kt, j), op = __shfl_xor_sync(kFull, kp, j);
+          const bool up = (lane & k) == 0;
+          const bool lower = (lane & j) == 0;
+          const bool o_less = key_less(oc, oh, ot, kc, kh, kt);
+          const bool m_less = key_less(kc, kh, kt, oc, oh, ot);
+          const bool take = (lower == up) ? o_less : m_less;
+          if (take) {
+            kc = oc;
+            kh = oh;
+            kt = ot;
+            kp = op;
+          }
+        }
       }
     }
   }
