@@ -108,8 +108,13 @@ typedef struct {
  *   group_width_q  if > 0, Lambda in cost quanta directly (lambda is then ignored;
  *               needed for roadmaps given as plain graphs, which have no r_n).
  *   max_iters   wavefront cap (MPAP_ERR_ITER_LIMIT when reached), > 0.
- *   flags       bit 0 MPAP_QUERY_NO_GOAL_STOP: run until P_open is empty. */
+ *   flags       bit 0 MPAP_QUERY_NO_GOAL_STOP: run until P_open is empty.
+ *               bit 1 MPAP_QUERY_CHECK_INTERIOR: the perception constraint of
+ *               Eq. 2 for all t: a candidate is cut when the heuristic exceeds
+ *               beta at any sub-step of its last edge (max(Cmax, h + Smax) >
+ *               beta), not only at its head (Alg. 3). */
 #define MPAP_QUERY_NO_GOAL_STOP 1u
+#define MPAP_QUERY_CHECK_INTERIOR 2u
 typedef struct {
   int64_t beta;
   int64_t group_width_q;
@@ -183,10 +188,20 @@ int32_t mpap_build_roadmap_from_points(const mpap_scene* scene, uint32_t V, cons
                                        mpap_roadmap** out, void* stream);
 
 /* A roadmap given directly as a forward CSR graph (host arrays), for searches on
- * hand-made graphs.  row_ptr[V+1], dst/cost_q/S/C[E], is_goal[V]; cost_q >= 1. */
+ * hand-made graphs.  row_ptr[V+1], dst/cost_q/S/C[E], is_goal[V]; cost_q >= 1.
+ * Every edge is then a single step for the interior check (its peak is its end
+ * value); mpap_roadmap_from_csr_peaks gives the peaks explicitly. */
 int32_t mpap_roadmap_from_csr(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst,
                               const int32_t* cost_q, const int32_t* S, const int32_t* C,
                               const uint8_t* is_goal, mpap_roadmap** out, void* stream);
+
+/* mpap_roadmap_from_csr with the per-edge transfer peaks Smax/Cmax[E]: the
+ * heuristic along edge e, entered with h, never exceeds max(Cmax, h + Smax)
+ * (Smax >= S, Cmax >= C >= 0). */
+int32_t mpap_roadmap_from_csr_peaks(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst,
+                                    const int32_t* cost_q, const int32_t* S, const int32_t* C,
+                                    const int32_t* Smax, const int32_t* Cmax, const uint8_t* is_goal,
+                                    mpap_roadmap** out, void* stream);
 
 int32_t mpap_roadmap_info(const mpap_roadmap* rm, uint32_t* V, uint64_t* E);
 
@@ -196,6 +211,12 @@ int32_t mpap_roadmap_info(const mpap_roadmap* rm, uint32_t* V, uint64_t* E);
  * on it).  Synchronises the stream. */
 int32_t mpap_roadmap_export(const mpap_roadmap* rm, float* x, uint8_t* is_goal, uint32_t* row_ptr,
                             uint32_t* dst, int32_t* cost_q, int32_t* S, int32_t* C, void* stream);
+
+/* Per-edge transfer peaks (Smax, Cmax)[E] in the order of mpap_roadmap_export:
+ * entering edge e with heuristic h, the heuristic after each of its M sub-steps
+ * is at most max(Cmax, h + Smax), with equality at some sub-step (Sec. 4.1
+ * heuristic; used by the interior check of Eq. 2). */
+int32_t mpap_roadmap_export_peaks(const mpap_roadmap* rm, int32_t* Smax, int32_t* Cmax, void* stream);
 
 /* Build statistics: Near tests (Cost < r evaluations) performed by the last
  * build of this roadmap, and the number of nodes in X_goal. */

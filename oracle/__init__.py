@@ -68,7 +68,10 @@ def lib():
         L.orc_segment_hits_box.restype = C.c_int
         L.orc_segment_hits_box.argtypes = [C.c_int, f32p, f32p, f32p, f32p]
         L.orc_explore.restype = P
-        L.orc_explore.argtypes = [P, C.c_int64, C.c_int64, C.c_uint32, C.c_int, C.c_uint64]
+        L.orc_explore.argtypes = [P, C.c_int64, C.c_int64, C.c_uint32, C.c_int, C.c_uint64, C.c_int]
+        L.orc_roadmap_from_csr_peaks.restype = P
+        L.orc_roadmap_from_csr_peaks.argtypes = [C.c_uint32, u32p, u32p, i32p, i32p, i32p, i32p, i32p, u8p]
+        L.orc_roadmap_get_peaks.argtypes = [P, i32p, i32p]
         L.orc_result_free.argtypes = [P]
         L.orc_result_summary.argtypes = [P] + [C.c_void_p] * 8
         L.orc_result_get.argtypes = [P, u32p, u32p, i64p, i64p]
@@ -100,6 +103,8 @@ class Graph:
     C: np.ndarray
     is_goal: np.ndarray
     x: np.ndarray           # [6, V]
+    Smax: np.ndarray = None  # per-edge peaks of the transfers (interior check)
+    Cmax: np.ndarray = None
 
 
 class Roadmap:
@@ -135,7 +140,10 @@ class Roadmap:
         S = np.zeros(max(E, 1), np.int32)
         Cc = np.zeros(max(E, 1), np.int32)
         lib().orc_roadmap_get(self.h, x, g, rp, dst, cq, S, Cc)
-        return Graph(V, rp, dst[:E], cq[:E], S[:E], Cc[:E], g, x.reshape(6, V))
+        Sm = np.zeros(max(E, 1), np.int32)
+        Cm = np.zeros(max(E, 1), np.int32)
+        lib().orc_roadmap_get_peaks(self.h, Sm, Cm)
+        return Graph(V, rp, dst[:E], cq[:E], S[:E], Cc[:E], g, x.reshape(6, V), Sm[:E], Cm[:E])
 
     def edge_eval(self, u: int, v: int):
         M = self.M
@@ -182,14 +190,21 @@ def build_roadmap_from_points(dim, box_lo, box_hi, grid, G, x, r, T=0.25, M=16,
     return Roadmap(h, dim, M)
 
 
-def roadmap_from_csr(row_ptr, dst, cost_q, S, Cc, is_goal) -> Roadmap:
+def roadmap_from_csr(row_ptr, dst, cost_q, S, Cc, is_goal, Smax=None, Cmax=None) -> Roadmap:
+    """A roadmap given as a CSR graph; without Smax/Cmax every edge is one step
+    (its peak is its end value)."""
     row_ptr = np.ascontiguousarray(row_ptr, np.uint32)
     V = row_ptr.size - 1
     E = int(row_ptr[-1])
     pad = lambda a, t: np.ascontiguousarray(a if E else np.zeros(1), t)
-    h = lib().orc_roadmap_from_csr(V, row_ptr, pad(dst, np.uint32), pad(cost_q, np.int32),
-                                   pad(S, np.int32), pad(Cc, np.int32),
-                                   np.ascontiguousarray(is_goal, np.uint8))
+    if Smax is None:
+        h = lib().orc_roadmap_from_csr(V, row_ptr, pad(dst, np.uint32), pad(cost_q, np.int32),
+                                       pad(S, np.int32), pad(Cc, np.int32),
+                                       np.ascontiguousarray(is_goal, np.uint8))
+    else:
+        h = lib().orc_roadmap_from_csr_peaks(V, row_ptr, pad(dst, np.uint32), pad(cost_q, np.int32),
+                                             pad(S, np.int32), pad(Cc, np.int32), pad(Smax, np.int32),
+                                             pad(Cmax, np.int32), np.ascontiguousarray(is_goal, np.uint8))
     return Roadmap(h, 0, 16)
 
 
@@ -215,10 +230,10 @@ class ExploreResult:
 
 def explore(rm: Roadmap, beta: int, Lambda: int, max_iters: int = 1 << 20,
             goal_termination: bool = True, max_plans: int = 1 << 28,
-            candidates: int = 0) -> ExploreResult:
+            candidates: int = 0, check_interior: bool = False) -> ExploreResult:
     L = lib()
     r = L.orc_explore(rm.h, int(beta), int(Lambda), int(max_iters), int(goal_termination),
-                      int(max_plans))
+                      int(max_plans), int(check_interior))
     try:
         st = C.c_int(); cost = C.c_int64(); hv = C.c_int64(); pl = C.c_uint32()
         wf = C.c_uint32(); ex = C.c_uint64(); pc = C.c_uint64(); ft = C.c_uint32()

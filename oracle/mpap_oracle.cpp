@@ -94,6 +94,7 @@ struct Roadmap {
   std::vector<uint32_t> row_ptr;      // forward CSR, neighbours in ascending order
   std::vector<uint32_t> dst;
   std::vector<int32_t> cost_q, S, C;  // per edge: quantised cost, max-plus transfer
+  std::vector<int32_t> Smax, Cmax;    // per edge: peak of the transfer over its sub-steps
   // 6D steering constants, computed once in double and rounded to float.
   float c1 = 0, c2 = 0, c3 = 0, e1 = 0, e2 = 0, inv6 = 0, dtm = 0, Tq_f = 0;
   int64_t Tq = 0;
@@ -334,15 +335,29 @@ void edge_steps(const Roadmap& rm, const EdgeGeom& g, int64_t cost_q, std::vecto
 // Each step maps h to max(0, h + d_m) (drift is clamped at zero: fully localised).
 // Composing the M steps gives F_e(h) = max(C_e, h + S_e) for h >= 0, where
 // S_e = sum d_m and C_e = F_e(0).  C_e is obtained here by literally stepping h = 0.
-void transfer_from_steps(const std::vector<int64_t>& d, int64_t& S, int64_t& Cv) {
+// After m steps the heuristic is max(C_m, h + S_m) with the partial sums S_m and
+// the stepped C_m, so its largest value along the edge (the "for all t" form of
+// Eq. 2) is max(Cmax, h + Smax) with Smax = max_m S_m and Cmax = max_m C_m.
+void transfer_from_steps(const std::vector<int64_t>& d, int64_t& S, int64_t& Cv, int64_t& Smax,
+                         int64_t& Cmax) {
   S = 0;
   int64_t h = 0;
+  Smax = INT64_MIN;
+  Cmax = 0;
   for (int64_t dm : d) {
     S += dm;
     h = h + dm;
     if (h < 0) h = 0;
+    Smax = std::max(Smax, S);
+    Cmax = std::max(Cmax, h);
   }
   Cv = h;
+  if (d.empty()) Smax = 0;
+}
+
+void transfer_from_steps(const std::vector<int64_t>& d, int64_t& S, int64_t& Cv) {
+  int64_t a, b;
+  transfer_from_steps(d, S, Cv, a, b);
 }
 
 // ----------------------------------------------------------------------------
@@ -352,7 +367,7 @@ void transfer_from_steps(const std::vector<int64_t>& d, int64_t& S, int64_t& Cv)
 // ----------------------------------------------------------------------------
 bool build_graph(Roadmap& rm) {
   rm.row_ptr.assign(rm.V + 1, 0);
-  rm.dst.clear(); rm.cost_q.clear(); rm.S.clear(); rm.C.clear();
+  rm.dst.clear(); rm.cost_q.clear(); rm.S.clear(); rm.C.clear(); rm.Smax.clear(); rm.Cmax.clear();
   std::vector<int64_t> d;
   for (uint32_t v = 0; v < rm.V; ++v) {
     for (uint32_t u = 0; u < rm.V; ++u) {
@@ -362,13 +377,17 @@ bool build_graph(Roadmap& rm) {
       if (edge_collides(rm, g)) continue;
       int64_t cq = quantise_cost(g.cost);
       edge_steps(rm, g, cq, d);
-      int64_t S, Cv;
-      transfer_from_steps(d, S, Cv);
-      if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || Cv > INT32_MAX) return false;
+      int64_t S, Cv, Smax, Cmax;
+      transfer_from_steps(d, S, Cv, Smax, Cmax);
+      if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || Cv > INT32_MAX || Smax > INT32_MAX ||
+          Cmax > INT32_MAX)
+        return false;
       rm.dst.push_back(u);
       rm.cost_q.push_back((int32_t)cq);
       rm.S.push_back((int32_t)S);
       rm.C.push_back((int32_t)Cv);
+      rm.Smax.push_back((int32_t)Smax);
+      rm.Cmax.push_back((int32_t)Cmax);
     }
     rm.row_ptr[v + 1] = (uint32_t)rm.dst.size();
   }
@@ -422,7 +441,7 @@ struct ExploreOut {
 };
 
 void explore(const Roadmap& rm, int64_t beta, int64_t Lambda, uint32_t max_iters,
-             bool goal_termination, uint64_t max_plans, ExploreOut& out) {
+             bool goal_termination, uint64_t max_plans, bool check_interior, ExploreOut& out) {
   std::vector<Plan> plans;
   std::vector<std::vector<uint32_t>> P(rm.V);     // P(v): plans with head v
   std::set<uint32_t> open;                        // P_open (arena indices)
@@ -455,7 +474,10 @@ void explore(const Roadmap& rm, int64_t beta, int64_t Lambda, uint32_t max_iters
         int64_t qcost = p.cost + (int64_t)rm.cost_q[e];
         // PH(x, p): the transfer of edge p.head -> x applied to p.h.
         int64_t qh = std::max((int64_t)rm.C[e], p.h + (int64_t)rm.S[e]);
-        if (qh <= beta) {                         // perception-heuristic cutoff
+        // perception-heuristic cutoff at the new head (Alg. 3), or at every
+        // sub-step of the edge (the "for all t" form of Eq. 2)
+        const int64_t peak = check_interior ? std::max((int64_t)rm.Cmax[e], p.h + (int64_t)rm.Smax[e]) : qh;
+        if (peak <= beta) {
           if (plans.size() >= max_plans) { out.status = -2; return; }
           Plan q{x, (int64_t)gi, qcost, qh, (uint32_t)out.wavefronts, p.head, p.cost,
                  true, true};
@@ -790,9 +812,29 @@ orc_roadmap* orc_roadmap_from_csr(uint32_t V, const uint32_t* row_ptr, const uin
   rm.cost_q.assign(cost_q, cost_q + E);
   rm.S.assign(S, S + E);
   rm.C.assign(C, C + E);
+  // without peaks an edge is one step: its peak is its end value
+  rm.Smax.assign(S, S + E);
+  rm.Cmax.assign(C, C + E);
   rm.is_goal.assign(is_goal, is_goal + V);
   for (int a = 0; a < 6; ++a) rm.x[a].assign(V, 0.0f);
   return h;
+}
+
+// The same with the per-edge peaks (Smax, Cmax) of the transfers.
+orc_roadmap* orc_roadmap_from_csr_peaks(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst,
+                                        const int32_t* cost_q, const int32_t* S, const int32_t* C,
+                                        const int32_t* Smax, const int32_t* Cmax, const uint8_t* is_goal) {
+  orc_roadmap* h = orc_roadmap_from_csr(V, row_ptr, dst, cost_q, S, C, is_goal);
+  const uint32_t E = row_ptr[V];
+  h->rm.Smax.assign(Smax, Smax + E);
+  h->rm.Cmax.assign(Cmax, Cmax + E);
+  return h;
+}
+
+void orc_roadmap_get_peaks(const orc_roadmap* h, int32_t* Smax, int32_t* Cmax) {
+  const Roadmap& rm = h->rm;
+  if (Smax) std::memcpy(Smax, rm.Smax.data(), rm.Smax.size() * 4);
+  if (Cmax) std::memcpy(Cmax, rm.Cmax.data(), rm.Cmax.size() * 4);
 }
 
 void orc_roadmap_free(orc_roadmap* h) { delete h; }
@@ -847,9 +889,9 @@ int orc_segment_hits_box(int dp, const float* a, const float* b, const float* lo
 }
 
 orc_result* orc_explore(const orc_roadmap* h, int64_t beta, int64_t Lambda, uint32_t max_iters,
-                        int goal_termination, uint64_t max_plans) {
+                        int goal_termination, uint64_t max_plans, int check_interior) {
   orc_result* r = new orc_result();
-  explore(h->rm, beta, Lambda, max_iters, goal_termination != 0, max_plans, r->out);
+  explore(h->rm, beta, Lambda, max_iters, goal_termination != 0, max_plans, check_interior != 0, r->out);
   return r;
 }
 

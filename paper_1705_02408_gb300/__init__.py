@@ -26,6 +26,7 @@ MPAP_ERR_INVALID_ARG, MPAP_ERR_CAPACITY, MPAP_ERR_TIMEOUT = -1, -2, -3
 MPAP_ERR_ITER_LIMIT, MPAP_ERR_CUDA, MPAP_ERR_SAMPLING = -4, -5, -6
 MPAP_MEM_HOST, MPAP_MEM_DEVICE = 0, 1
 MPAP_QUERY_NO_GOAL_STOP = 1
+MPAP_QUERY_CHECK_INTERIOR = 2
 
 EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_build_roadmaps",
            "mpap_build_roadmap_from_points", "mpap_roadmap_from_csr", "mpap_roadmap_info",
@@ -36,7 +37,8 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_mlp_create", "mpap_mlp_free", "mpap_mlp_get_params", "mpap_mlp_set_params",
            "mpap_mlp_forward", "mpap_mlp_train_step", "mpap_tuning_get", "mpap_tuning_set",
            "mpap_tuning_clear", "mpap_tuning_export", "mpap_autotune_build", "mpap_autotune_search",
-           "mpap_search_candidates_batch", "mpap_plan_features_batch"]
+           "mpap_search_candidates_batch", "mpap_plan_features_batch", "mpap_roadmap_from_csr_peaks",
+           "mpap_roadmap_export_peaks"]
 
 
 class mpap_scene(C.Structure):
@@ -142,6 +144,10 @@ def lib():
         u32p = C.POINTER(C.c_uint32)
         L.mpap_search_candidates.restype = i32
         L.mpap_search_candidates.argtypes = [P, C.c_uint32, C.c_uint32, P, P, P, P, C.c_uint32, u32p, u32p, P]
+        L.mpap_roadmap_from_csr_peaks.restype = i32
+        L.mpap_roadmap_from_csr_peaks.argtypes = [C.c_uint32, P, P, P, P, P, P, P, P, C.POINTER(P), P]
+        L.mpap_roadmap_export_peaks.restype = i32
+        L.mpap_roadmap_export_peaks.argtypes = [P, P, P, P]
         L.mpap_search_candidates_batch.restype = i32
         L.mpap_search_candidates_batch.argtypes = [P, C.c_uint32, C.c_uint32, P, P, P, P, C.c_uint32, P, P, P]
         L.mpap_plan_features_batch.restype = i32
@@ -303,6 +309,15 @@ class Roadmap:
         return dict(V=V, E=E, x=x.reshape(6, V), is_goal=g, row_ptr=rp, dst=dst[:E], cost_q=cq[:E],
                     S=S[:E], C=Cc[:E])
 
+    def peaks(self, stream=None):
+        """(Smax, Cmax) per edge, in the order of export()."""
+        E = self.info()[1]
+        Sm = np.zeros(max(E, 1), np.int32); Cm = np.zeros(max(E, 1), np.int32)
+        _check(lib().mpap_roadmap_export_peaks(self.h, Sm.ctypes.data_as(C.c_void_p),
+                                               Cm.ctypes.data_as(C.c_void_p), _stream(stream)),
+               "mpap_roadmap_export_peaks")
+        return Sm[:E], Cm[:E]
+
 
 def build_roadmap(dim_kind, box_lo, box_hi, grid, grid_G, n, seed, r, x_init, x_goal,
                   goal_radius=0.05, T=0.25, M=16, query_id=0, n_f=12, K=24, stream=None) -> Roadmap:
@@ -407,15 +422,23 @@ def build_roadmap_from_points(dim_kind, box_lo, box_hi, grid, grid_G, x, r, T=0.
     return Roadmap(h, M, K)
 
 
-def roadmap_from_csr(row_ptr, dst, cost_q, S, Cc, is_goal, stream=None) -> Roadmap:
+def roadmap_from_csr(row_ptr, dst, cost_q, S, Cc, is_goal, Smax=None, Cmax=None, stream=None) -> Roadmap:
+    """mpap_roadmap_from_csr (or _peaks when Smax/Cmax are given)."""
     arrs = [np.ascontiguousarray(row_ptr, np.uint32), np.ascontiguousarray(dst, np.uint32),
             np.ascontiguousarray(cost_q, np.int32), np.ascontiguousarray(S, np.int32),
-            np.ascontiguousarray(Cc, np.int32), np.ascontiguousarray(is_goal, np.uint8)]
+            np.ascontiguousarray(Cc, np.int32)]
+    goal = np.ascontiguousarray(is_goal, np.uint8)
     arrs = [a if a.size else np.zeros(1, a.dtype) for a in arrs]
     vp = lambda a: a.ctypes.data_as(C.c_void_p)
     h = C.c_void_p()
-    _check(lib().mpap_roadmap_from_csr(len(row_ptr) - 1, *[vp(a) for a in arrs], C.byref(h), _stream(stream)),
-           "mpap_roadmap_from_csr")
+    if Smax is None:
+        _check(lib().mpap_roadmap_from_csr(len(row_ptr) - 1, *[vp(a) for a in arrs], vp(goal), C.byref(h),
+                                           _stream(stream)), "mpap_roadmap_from_csr")
+    else:
+        pk = [np.ascontiguousarray(Smax, np.int32), np.ascontiguousarray(Cmax, np.int32)]
+        pk = [a if a.size else np.zeros(1, a.dtype) for a in pk]
+        _check(lib().mpap_roadmap_from_csr_peaks(len(row_ptr) - 1, *[vp(a) for a in arrs + pk], vp(goal),
+                                                 C.byref(h), _stream(stream)), "mpap_roadmap_from_csr_peaks")
     return Roadmap(h)
 
 
@@ -476,9 +499,10 @@ class SearchResult:
     plans: int
 
 
-def make_query(beta, lam=0.5, group_width_q=0, max_iters=100000, goal_stop=True):
+def make_query(beta, lam=0.5, group_width_q=0, max_iters=100000, goal_stop=True, interior=False):
+    flags = (0 if goal_stop else MPAP_QUERY_NO_GOAL_STOP) | (MPAP_QUERY_CHECK_INTERIOR if interior else 0)
     return mpap_query(beta=int(beta), group_width_q=int(group_width_q), lambda_=float(lam),
-                      max_iters=int(max_iters), flags=0 if goal_stop else MPAP_QUERY_NO_GOAL_STOP)
+                      max_iters=int(max_iters), flags=flags)
 
 
 def _result(r, buf):
@@ -487,9 +511,9 @@ def _result(r, buf):
 
 
 def search(ws: Workspace, rm: Roadmap, beta, lam=0.5, group_width_q=0, max_iters=100000,
-           goal_stop=True, path_cap=4096, stream=None) -> SearchResult:
+           goal_stop=True, path_cap=4096, stream=None, interior=False) -> SearchResult:
     """mpap_search: Alg. 3 Explore for one query."""
-    q = make_query(beta, lam, group_width_q, max_iters, goal_stop)
+    q = make_query(beta, lam, group_width_q, max_iters, goal_stop, interior)
     buf = np.zeros(path_cap, np.uint32)
     r = mpap_result(path_cap=path_cap, path=buf.ctypes.data_as(C.POINTER(C.c_uint32)))
     _check(lib().mpap_search(ws.h, rm.h, C.byref(q), C.byref(r), _stream(stream)), "mpap_search")

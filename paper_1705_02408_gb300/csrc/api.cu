@@ -200,6 +200,13 @@ int32_t mpap_build_roadmap_from_points(const mpap_scene* scene, uint32_t V, cons
 int32_t mpap_roadmap_from_csr(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst, const int32_t* cost_q,
                               const int32_t* Sv, const int32_t* C, const uint8_t* is_goal, mpap_roadmap** out,
                               void* stream) {
+  return mpap_roadmap_from_csr_peaks(V, row_ptr, dst, cost_q, Sv, C, nullptr, nullptr, is_goal, out, stream);
+}
+
+int32_t mpap_roadmap_from_csr_peaks(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst,
+                                    const int32_t* cost_q, const int32_t* Sv, const int32_t* C,
+                                    const int32_t* Smax, const int32_t* Cmax, const uint8_t* is_goal,
+                                    mpap_roadmap** out, void* stream) {
   if (!row_ptr || !is_goal || !out || V < 1) {
     set_error("need row_ptr, is_goal, out and V >= 1");
     return MPAP_ERR_INVALID_ARG;
@@ -209,18 +216,56 @@ int32_t mpap_roadmap_from_csr(uint32_t V, const uint32_t* row_ptr, const uint32_
     set_error("null edge arrays");
     return MPAP_ERR_INVALID_ARG;
   }
+  if ((Smax == nullptr) != (Cmax == nullptr)) {
+    set_error("give both Smax and Cmax or neither");
+    return MPAP_ERR_INVALID_ARG;
+  }
   for (uint32_t v = 0; v < V; ++v)
     if (row_ptr[v] > row_ptr[v + 1]) {
       set_error("row_ptr not monotone");
       return MPAP_ERR_INVALID_ARG;
     }
-  for (uint32_t e = 0; e < E; ++e)
+  for (uint32_t e = 0; e < E; ++e) {
     if (dst[e] >= V || cost_q[e] < 1 || C[e] < 0) {
       set_error("edge %u: dst out of range, cost_q < 1 or C < 0", e);
       return MPAP_ERR_INVALID_ARG;
     }
+    if (Smax && (Smax[e] < Sv[e] || Cmax[e] < C[e])) {
+      set_error("edge %u: need Smax >= S and Cmax >= C", e);
+      return MPAP_ERR_INVALID_ARG;
+    }
+  }
   *out = nullptr;
-  return mpap::roadmap_from_csr_impl(V, row_ptr, dst, cost_q, Sv, C, is_goal, out, S(stream));
+  return mpap::roadmap_from_csr_impl(V, row_ptr, dst, cost_q, Sv, C, Smax, Cmax, is_goal, out, S(stream));
+}
+
+int32_t mpap_roadmap_export_peaks(const mpap_roadmap* rm, int32_t* Smax, int32_t* Cmax, void* stream) {
+  if (!rm) {
+    set_error("null roadmap");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = S(stream);
+  const size_t E = (size_t)rm->E;
+  std::vector<int4> ed(E ? E : 1);
+  std::vector<int2> pk(E ? E : 1);
+  std::vector<uint32_t> rp((size_t)rm->V + 1);
+  if (E) {
+    MPAP_CK(cudaMemcpyAsync(ed.data(), rm->fwd_edge, sizeof(int4) * E, cudaMemcpyDeviceToHost, st));
+    MPAP_CK(cudaMemcpyAsync(pk.data(), rm->fwd_peak, sizeof(int2) * E, cudaMemcpyDeviceToHost, st));
+  }
+  MPAP_CK(cudaMemcpyAsync(rp.data(), rm->fwd_ptr, 4 * ((size_t)rm->V + 1), cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaStreamSynchronize(st));
+  // the export's order: every row sorted by neighbour
+  std::vector<uint32_t> idx(E ? E : 1);
+  for (size_t e = 0; e < E; ++e) idx[e] = (uint32_t)e;
+  for (uint32_t v = 0; v < rm->V; ++v)
+    std::sort(idx.begin() + rp[v], idx.begin() + rp[v + 1],
+              [&](uint32_t a, uint32_t b) { return ed[a].x < ed[b].x; });
+  for (size_t e = 0; e < E; ++e) {
+    if (Smax) Smax[e] = pk[idx[e]].x;
+    if (Cmax) Cmax[e] = pk[idx[e]].y;
+  }
+  return MPAP_OK;
 }
 
 int32_t mpap_roadmap_info(const mpap_roadmap* rm, uint32_t* V, uint64_t* E) {

@@ -309,13 +309,16 @@ __device__ __forceinline__ int64_t quantise_cost(float cost) {
 }
 
 // Per-edge perception transfer F_e(h) = max(C, h + S) from the M sub-steps
-// (Sec. 4.1 heuristic on the quality grid): step m adds inc (n_f - k_m).
+// (Sec. 4.1 heuristic on the quality grid): step m adds inc (n_f - k_m).  After m
+// steps the heuristic is max(C_m, h + S_m), so its peak along the edge (the "for
+// all t" form of Eq. 2) is max(Cmax, h + Smax) with Smax = max_m S_m and
+// Cmax = max_m C_m.
 template <int DIM>
 __device__ __forceinline__ void conn_transfer_t(const Geom& g, const Conn& c, int64_t cost_q, int64_t& S,
-                                                int64_t& C) {
+                                                int64_t& C, int64_t& Smax, int64_t& Cmax) {
   constexpr int DP = (DIM == 2) ? 2 : 3;
   const int64_t inc = (DIM == 6) ? g.Tq : cost_q;
-  int64_t s = 0, h = 0;
+  int64_t s = 0, h = 0, smax = INT64_MIN, cmax = 0;
   for (int m = 1; m <= g.M; ++m) {
     float p[3];
     conn_point_t<DIM>(g, c, m, p);
@@ -323,9 +326,13 @@ __device__ __forceinline__ void conn_transfer_t(const Geom& g, const Conn& c, in
     s += dm;
     h += dm;
     h = h < 0 ? 0 : h;
+    smax = s > smax ? s : smax;
+    cmax = h > cmax ? h : cmax;
   }
   S = s;
   C = h;
+  Smax = g.M > 0 ? smax : 0;
+  Cmax = cmax;
 }
 
 // ---------------------------------------------------------------------------

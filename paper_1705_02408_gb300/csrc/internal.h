@@ -29,6 +29,8 @@ struct mpap_roadmap {
   uint32_t* fwd_dst = nullptr; // [E] dst only (for marking out-neighbours)
   uint32_t* rev_ptr = nullptr; // [V+1]
   int4* rev_edge = nullptr;    // [E] {src, cost_q, S, C}
+  int2* fwd_peak = nullptr;    // [E] {Smax, Cmax}: peak of the transfer over the edge
+  int2* rev_peak = nullptr;    // [E] the same in reverse-CSR order
   float* box_lo = nullptr;     // [nb][3]
   float* box_hi = nullptr;
   uint8_t* grid = nullptr;
@@ -63,8 +65,10 @@ struct BuildSpec {
 // Builds every spec into rms[i] (a null rms[i] gets a new handle; an existing
 // one is rebuilt in place, reusing its device buffers when large enough).
 int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** rms, cudaStream_t st);
+// Smax/Cmax may be null: every edge is then one step (its peak is its end value).
 int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst,
                               const int32_t* cost_q, const int32_t* S, const int32_t* C,
+                              const int32_t* Smax, const int32_t* Cmax,
                               const uint8_t* is_goal, mpap_roadmap** out, cudaStream_t st);
 void roadmap_free_impl(mpap_roadmap* rm);
 

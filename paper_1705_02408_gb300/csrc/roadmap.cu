@@ -105,12 +105,15 @@ struct BuildJob {
   uint32_t* counts;        // [V+1]
   uint32_t* fill;          // [V+1]
   int4* rows;              // [V][kRowCap] per-source edge rows of the one-pass build
+  int2* rows_peak;         // [V][kRowCap] their transfer peaks {Smax, Cmax}
   uint32_t* ovf;           // [V] sources with more than kRowCap edges (count in status[3])
   uint32_t* fwd_ptr;
   int4* fwd_edge;
   uint32_t* fwd_dst;
   uint32_t* rev_ptr;
   int4* rev_edge;
+  int2* fwd_peak;
+  int2* rev_peak;
   uint32_t* status;        // [4]: error bits, n_goal, scan overflow, overflowing sources
 };
 
@@ -350,15 +353,20 @@ __device__ __forceinline__ void edge_flush(const BuildJob& J, uint32_t v, const 
     const uint32_t rank = running + __popc(bal & ((1u << lane) - 1u));
     if (MODE == kFillCsr || rank < kRowCap) {
       const int64_t cq = quantise_cost(cn.cost);
-      int64_t S, C;
-      conn_transfer_t<DIM>(g, cn, cq, S, C);
-      if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX) atomicOr(&J.status[0], kErrEdge);
+      int64_t S, C, Smax, Cmax;
+      conn_transfer_t<DIM>(g, cn, cq, S, C, Smax, Cmax);
+      if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX || Smax > INT32_MAX || Cmax > INT32_MAX)
+        atomicOr(&J.status[0], kErrEdge);
       const int4 rec = make_int4((int)u, (int)cq, (int)S, (int)C);
+      const int2 pk = make_int2((int)Smax, (int)Cmax);
       if (MODE == kFillCsr) {
         J.fwd_edge[out_base + rank] = rec;
         J.fwd_dst[out_base + rank] = u;
+        J.fwd_peak[out_base + rank] = pk;
+      } else {
+        J.rows[(size_t)v * kRowCap + rank] = rec;
+        J.rows_peak[(size_t)v * kRowCap + rank] = pk;
       }
-      else J.rows[(size_t)v * kRowCap + rank] = rec;
     }
   }
   running += __popc(bal);
@@ -503,10 +511,12 @@ __global__ void k_compact_rows(const BuildJob* __restrict__ jobs) {
     const uint32_t b = J.fwd_ptr[v], len = J.fwd_ptr[v + 1] - b;
     if (len > kRowCap) continue;   // written by the overflow pass
     const int4* src = J.rows + (size_t)v * kRowCap;
+    const int2* srcp = J.rows_peak + (size_t)v * kRowCap;
     for (uint32_t i = lane_id(); i < len; i += 32) {
       const int4 e = src[i];
       J.fwd_edge[b + i] = e;
       J.fwd_dst[b + i] = (uint32_t)e.x;
+      J.fwd_peak[b + i] = srcp[i];
     }
   }
 }
@@ -528,6 +538,7 @@ __global__ void k_reverse_fill(const BuildJob* __restrict__ jobs) {
       const int4 ed = J.fwd_edge[e];
       const uint32_t pos = J.rev_ptr[ed.x] + atomicAdd(&J.fill[ed.x], 1u);
       J.rev_edge[pos] = make_int4((int)v, ed.y, ed.z, ed.w);
+      J.rev_peak[pos] = J.fwd_peak[e];
     }
 }
 
@@ -716,17 +727,24 @@ int32_t ensure_nodes(mpap_roadmap* rm, uint32_t V) {
 
 int32_t ensure_edges(mpap_roadmap* rm, uint64_t E) {
   const size_t need = E ? (size_t)E : 1;
-  if (rm->fwd_edge && rm->rev_edge && rm->fwd_dst && rm->cap_E >= need) return MPAP_OK;
+  if (rm->fwd_edge && rm->rev_edge && rm->fwd_dst && rm->fwd_peak && rm->rev_peak && rm->cap_E >= need)
+    return MPAP_OK;
   cudaFree(rm->fwd_edge);
   cudaFree(rm->rev_edge);
   cudaFree(rm->fwd_dst);
+  cudaFree(rm->fwd_peak);
+  cudaFree(rm->rev_peak);
   rm->fwd_edge = nullptr;
   rm->rev_edge = nullptr;
   rm->fwd_dst = nullptr;
+  rm->fwd_peak = nullptr;
+  rm->rev_peak = nullptr;
   rm->cap_E = 0;
   MPAP_CK(cudaMalloc((void**)&rm->fwd_edge, sizeof(int4) * need));
   MPAP_CK(cudaMalloc((void**)&rm->rev_edge, sizeof(int4) * need));
   MPAP_CK(cudaMalloc((void**)&rm->fwd_dst, sizeof(uint32_t) * need));
+  MPAP_CK(cudaMalloc((void**)&rm->fwd_peak, sizeof(int2) * need));
+  MPAP_CK(cudaMalloc((void**)&rm->rev_peak, sizeof(int2) * need));
   rm->cap_E = need;
   return MPAP_OK;
 }
@@ -758,6 +776,8 @@ void roadmap_free_impl(mpap_roadmap* rm) {
   cudaFree(rm->fwd_ptr);
   cudaFree(rm->fwd_edge);
   cudaFree(rm->fwd_dst);
+  cudaFree(rm->fwd_peak);
+  cudaFree(rm->rev_peak);
   cudaFree(rm->rev_ptr);
   cudaFree(rm->rev_edge);
   cudaFree(rm->box_lo);
@@ -854,7 +874,7 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   size_t bytes = 256 * 8 + (sizeof(ScanSeg) + sizeof(BuildJob) + 48) * (size_t)n + 256 * (size_t)n;
   for (uint32_t j = 0; j < n; ++j)
     bytes += 256 * 13 + 4 * (ncells[j] + 1) + 16 + 32 * (cand_cap[j] + 1) + 4 * (ncells[j] + 1) +
-             48 * ((size_t)hj[j].V + 1) + sizeof(int4) * kRowCap * (size_t)hj[j].V + 512;
+             48 * ((size_t)hj[j].V + 1) + (sizeof(int4) + sizeof(int2)) * kRowCap * (size_t)hj[j].V + 768;
   MPAP_CK(scratch_alloc((void**)&blk, bytes, st));
   Carve cv{blk, 0};
   for (uint32_t j = 0; j < n; ++j) hj[j].cell_cnt = cv.take<uint32_t>(ncells[j] + 1);
@@ -877,6 +897,7 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     J.counts = cv.take<uint32_t>((size_t)J.V + 1);
     J.fill = cv.take<uint32_t>((size_t)J.V + 1);
     J.rows = cv.take<int4>(kRowCap * (size_t)J.V);
+    J.rows_peak = cv.take<int2>(kRowCap * (size_t)J.V);
     J.ovf = cv.take<uint32_t>((size_t)J.V);
     J.pos_of = cv.take<uint32_t>((size_t)J.V);
   }
@@ -1025,6 +1046,8 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     hj[j].fwd_edge = rm->fwd_edge;
     hj[j].fwd_dst = rm->fwd_dst;
     hj[j].rev_edge = rm->rev_edge;
+    hj[j].fwd_peak = rm->fwd_peak;
+    hj[j].rev_peak = rm->rev_peak;
     row_overflow = row_overflow || hg[6 * j + 5] > 0;
   }
   MPAP_BTRY(upload(d_jobs, hj.data(), sizeof(BuildJob) * n, st));
@@ -1057,14 +1080,18 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
 }
 
 int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_t* dst, const int32_t* cost_q,
-                              const int32_t* S, const int32_t* C, const uint8_t* is_goal, mpap_roadmap** out,
-                              cudaStream_t st) {
+                              const int32_t* S, const int32_t* C, const int32_t* Smax, const int32_t* Cmax,
+                              const uint8_t* is_goal, mpap_roadmap** out, cudaStream_t st) {
   mpap_roadmap* rm = new mpap_roadmap();
   rm->V = V;
   rm->E = row_ptr[V];
   rm->has_geometry = false;
   std::vector<int4> fe(rm->E);
-  for (uint64_t e = 0; e < rm->E; ++e) fe[e] = make_int4((int)dst[e], cost_q[e], S[e], C[e]);
+  std::vector<int2> fp(rm->E);
+  for (uint64_t e = 0; e < rm->E; ++e) {
+    fe[e] = make_int4((int)dst[e], cost_q[e], S[e], C[e]);
+    fp[e] = (Smax && Cmax) ? make_int2(Smax[e], Cmax[e]) : make_int2(S[e], C[e]);
+  }
   std::vector<uint32_t> goals;
   for (uint32_t v = 0; v < V; ++v)
     if (is_goal[v]) goals.push_back(v);
@@ -1080,7 +1107,8 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
       (rc = copy_in(rm->goal_list, goals.data(), 4 * goals.size(), false, st)) ||
       (rc = copy_in(rm->fwd_ptr, row_ptr, 4 * ((size_t)V + 1), false, st)) ||
       (rc = copy_in(rm->fwd_edge, fe.data(), sizeof(int4) * rm->E, false, st)) ||
-      (rc = copy_in(rm->fwd_dst, dst, 4 * (size_t)rm->E, false, st)))
+      (rc = copy_in(rm->fwd_dst, dst, 4 * (size_t)rm->E, false, st)) ||
+      (rc = copy_in(rm->fwd_peak, fp.data(), sizeof(int2) * rm->E, false, st)))
     return bail(rc);
   // reverse CSR with the build kernels (one job)
   BuildJob J;
@@ -1090,6 +1118,8 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
   J.fwd_edge = rm->fwd_edge;
   J.rev_ptr = rm->rev_ptr;
   J.rev_edge = rm->rev_edge;
+  J.fwd_peak = rm->fwd_peak;
+  J.rev_peak = rm->rev_peak;
   char* blk = nullptr;
   const size_t bytes = 4096 + 8 * ((size_t)V + 1) + 1024;
   if (!cuda_ok(cudaMallocAsync((void**)&blk, bytes, st), "cudaMallocAsync")) return bail(MPAP_ERR_CUDA);

@@ -46,6 +46,7 @@ namespace mpap {
 struct QueryDev {
   const uint32_t* rev_ptr;
   const int4* rev_edge;
+  const int2* rev_peak;     // per reverse edge {Smax, Cmax} (interior check)
   const uint32_t* fwd_ptr;
   const uint32_t* fwd_dst;
   const uint8_t* is_goal;
@@ -741,12 +742,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
     }
     unsigned long long exps = 0;
     const uint32_t e_end = Q.rev_ptr[x + 1];
+    const bool interior = (Q.flags & MPAP_QUERY_CHECK_INTERIOR) != 0;
     for (uint32_t e0 = Q.rev_ptr[x]; e0 < e_end; e0 += 32) {
       const uint32_t e = e0 + lane;
       int4 ed = make_int4(0, 0, 0, 0);
+      int2 pk = make_int2(0, 0);
       uint32_t cnt = 0, goff = 0;
       if (e < e_end) {
         ed = __ldg(&Q.rev_edge[e]);
+        if (interior) pk = __ldg(&Q.rev_peak[e]);
         const uint4 gd = w.gdesc[Q.base + (uint32_t)ed.x];
         if (gd.x == it) {
           cnt = gd.y;
@@ -773,6 +777,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
         const int o_cq = __shfl_sync(kFull, ed.y, owner);
         const int o_S = __shfl_sync(kFull, ed.z, owner);
         const int o_C = __shfl_sync(kFull, ed.w, owner);
+        const int o_Sm = __shfl_sync(kFull, pk.x, owner);
+        const int o_Cm = __shfl_sync(kFull, pk.y, owner);
         bool ok = false;
         long long cc = 0, ch = 0;
         uint32_t pp = 0;
@@ -782,7 +788,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
           const long long hh = w.g_h[gi] + (long long)o_S;
           ch = hh > (long long)o_C ? hh : (long long)o_C;
           pp = w.g_pid[gi];
-          ok = ch <= Q.beta;          // perception-heuristic cutoff
+          // perception-heuristic cutoff: at the new head (Alg. 3), or at every
+          // sub-step of the edge (Eq. 2 for all t)
+          long long peak = ch;
+          if (interior) {
+            const long long hp = w.g_h[gi] + (long long)o_Sm;
+            peak = hp > (long long)o_Cm ? hp : (long long)o_Cm;
+          }
+          ok = peak <= Q.beta;
         }
         if (fc.err) continue;
         if (fc.reg) merge_chunk_reg(w, q, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
@@ -1325,6 +1338,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     d.max_iters = qs[i].max_iters;
     d.flags = qs[i].flags;
     d.beta = qs[i].beta;
+    d.rev_peak = rm->rev_peak;
     // Lambda = round(lambda r_n 2^24), the group threshold quantum (or the
     // caller's explicit width in cost quanta).
     d.Lambda = qs[i].group_width_q > 0 ? qs[i].group_width_q
