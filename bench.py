@@ -76,12 +76,31 @@ def dist_env():
     return rank, world, local
 
 
+def shard_seeds(rank, count):
+    """Scene seeds of one rank: every rank takes its own `count` queries (weak
+    scaling; the queries are independent, so no data-path collective)."""
+    return [rank * count + i + 1 for i in range(count)]
+
+
+def reduce_over_ranks(ms_total, exps, device=None):
+    """(max over ranks of the timed region, sum over ranks of the expansions):
+    the only collectives of a multi-GPU run, and only for reporting."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_total, exps
+    t = torch.tensor([float(ms_total)], dtype=torch.float64, device=device)
+    e = torch.tensor([float(exps)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(e[0])
+
+
 def scenes_for_rank(rank, count):
     cfg = scenegen.config("6d")
     calib = scenegen.load_calibration()
     out = []
-    for i in range(count):
-        seed = rank * count + i + 1
+    for seed in shard_seeds(rank, count):
         sc = scenegen.make_scene(cfg, seed, query_id=seed)
         key = scenegen.calib_key(cfg, seed)
         sc.extra["beta"] = calib[key]["beta"] if key in calib else None
@@ -246,10 +265,7 @@ def run_gpu(args, rank, world, local):
     ms_total = e0.elapsed_time(e1)
     ms = ms_total / args.steps
     if world > 1:
-        t = torch.tensor([ms_total, float(exps)], device=device, dtype=torch.float64)
-        mx = t.clone(); torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        ms_total, exps = float(mx[0]), float(t[1])
+        ms_total, exps = reduce_over_ranks(ms_total, exps, device)
         ms = ms_total / args.steps
     value = exps / (ms_total / 1e3)
     rms, res, certs = arm._last
@@ -265,7 +281,7 @@ def run_gpu(args, rank, world, local):
            "gpu_launches": int(launches),
            "tuning": tuning}
     # breakdown from the live kernel timers (timed region)
-    search_k = {"k_fill_qid", "k_init", "k_select", "k_prune", "k_end", "k_finalize"}
+    search_k = {"k_init", "k_select", "k_prune", "k_end", "k_finalize", "k_candidates"}
     certify_k = {"k_mc_checkpoints", "k_mc_rollouts"}
     phase = {"build": 0.0, "search": 0.0, "certify": 0.0}
     for k, (_, t) in kern.items():

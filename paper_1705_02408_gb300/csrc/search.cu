@@ -115,15 +115,14 @@ struct WS {
   uint32_t* f_pid;
   uint32_t* f_aux;
   uint4* fdesc;            // [NV] {live block, count, other block, lg live | lg other << 8}
-  uint32_t* qid;
   uint4* gdesc;            // per node {iteration stamp, group count, group offset, 0}
   uint32_t* touch_stamp;
   uint32_t* oh_stamp;
   long long* g_cost;
   long long* g_h;
   uint32_t* g_pid;
-  uint32_t* oh_list;
-  uint32_t* t_list;
+  uint2* oh_list;           // [2][NV] {node, query} with open plans (this / next wavefront)
+  uint2* t_list;            // [NV] {node, query} touched this wavefront
   uint32_t* a_head;
   uint32_t* a_parent;
   uint32_t* a_iter;
@@ -223,15 +222,6 @@ __device__ __forceinline__ void ktime_end(const WS& w, int k) {
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_fill_qid(WS w, uint32_t nq) {
-  const QueryDev* qd = w.qd;
-  for (uint32_t q = blockIdx.y; q < nq; q += gridDim.y) {
-    const uint32_t base = qd[q].base, V = qd[q].V;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
-      w.qid[base + v] = q;
-  }
-}
-
 __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
   const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q == 0) {
@@ -279,7 +269,7 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
   w.a_parent[q] = kNone;
   w.a_iter[q] = 0;
   w.a_cost[q] = 0;
-  w.oh_list[q] = g;
+  w.oh_list[q] = make_uint2(g, q);
   w.oh_stamp[g] = 0;
 }
 
@@ -292,12 +282,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t n_list = (w.ctl->n_done < w.ctl->nq) ? w.ctl->oh_n[it & 1] : 0u;
-  const uint32_t* list = w.oh_list + (size_t)(it & 1) * w.NV;
-  uint32_t* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
+  const uint2* list = w.oh_list + (size_t)(it & 1) * w.NV;
+  uint2* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
-    const uint32_t g = list[k];
-    const uint32_t q = w.qid[g];
+    const uint2 gq = list[k];
+    const uint32_t g = gq.x, q = gq.y;
     if (w.qs[q].done) continue;
     const QueryDev& Q = w.qd[q];
     const uint4 fd = w.fdesc[g];
@@ -368,13 +358,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
             uint32_t pos = 0;
             if (lane == 0) pos = atomicAdd(&w.ctl->t_n, __popc(bal));
             pos = __shfl_sync(kFull, pos, 0);
-            if (first) w.t_list[pos + __popc(bal & lt)] = gx;
+            if (first) w.t_list[pos + __popc(bal & lt)] = make_uint2(gx, q);
           }
         }
       }
     }
     if (rest && lane == 0) {
-      if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = g;
+      if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = make_uint2(g, q);
     }
   }
   ktime_end(w, 0);
@@ -707,10 +697,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t n_list = (w.ctl->n_done < w.ctl->nq) ? w.ctl->t_n : 0u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  uint32_t* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
+  uint2* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
   for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
-    const uint32_t g = w.t_list[k];
-    const uint32_t q = w.qid[g];
+    const uint2 gq = w.t_list[k];
+    const uint32_t g = gq.x, q = gq.y;
     const QueryDev& Q = w.qd[q];
     {
       const QueryState& s = w.qs[q];
@@ -882,7 +872,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
         atomic_add_i64(&w.qs[q].open_cnt, (long long)n_new - (long long)fc.removed_open);
         atomicAdd(&w.qs[q].plans, (unsigned long long)n_new);
         atomicMax(&w.ctl->max_front, fc.n);
-        if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = g;
+        if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = make_uint2(g, q);
       }
     }
     if (lane == 0 && exps) atomicAdd(&w.qs[q].expansions, exps);
@@ -1253,7 +1243,7 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
   const size_t slots = (size_t)w.pcap;
   bool ok = walloc(&w.f_cost, slots) && walloc(&w.f_h, slots) && walloc(&w.f_pid, slots) &&
             walloc(&w.f_aux, slots) && walloc(&w.fdesc, w.NV) &&
-            walloc(&w.qid, w.NV) && walloc(&w.gdesc, w.NV) && walloc(&w.touch_stamp, w.NV) &&
+            walloc(&w.gdesc, w.NV) && walloc(&w.touch_stamp, w.NV) &&
             walloc(&w.oh_stamp, w.NV) &&
             walloc(&w.g_cost, w.gcap) && walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) &&
             walloc(&w.oh_list, 2 * w.NV) && walloc(&w.t_list, w.NV) && walloc(&w.a_head, w.acap) &&
@@ -1274,7 +1264,7 @@ void workspace_free(mpap_workspace* ws) {
   if (ws->graph) cudaGraphDestroy(ws->graph);
   if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
   WS& w = ws->w;
-  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.fdesc, w.qid, w.gdesc, w.touch_stamp,
+  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.fdesc, w.gdesc, w.touch_stamp,
                   w.oh_stamp, w.g_cost, w.g_h, w.g_pid, w.oh_list, w.t_list,
                   w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl, w.qd, w.qs, w.res, w.path};
   for (void* p : ptrs) cudaFree(p);
@@ -1372,11 +1362,6 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   MPAP_CK(cudaMemsetAsync(w.gdesc, 0xFF, sizeof(uint4) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.touch_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.oh_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
-  {
-    dim3 fg((unsigned)std::min<uint64_t>((total / nq + 255) / 256 + 1, 64), std::min(nq, 1024u));
-    LaunchScope ls(st, "k_fill_qid");
-    k_fill_qid<<<fg, 256, 0, st>>>(w, nq);
-  }
   {
     LaunchScope ls(st, "k_init");
     k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq, max_iters + 2u, prof ? 1u : 0u);
