@@ -102,7 +102,9 @@ struct Ctl {
   uint32_t prof;        // record KTime
   uint32_t max_front;   // largest front committed by any node
   unsigned long long pool_n;  // front pool entries handed out
-  KTime kt[3];          // select, prune, end
+  unsigned long long tmp_n;   // bulk-merge scratch entries handed out this wavefront
+  uint32_t b_n;         // nodes queued for the bulk prune this wavefront
+  KTime kt[4];          // select, prune, bulk prune, end
 };
 
 struct WS {
@@ -115,6 +117,11 @@ struct WS {
   uint32_t* f_pid;
   uint32_t* f_aux;
   uint4* fdesc;            // [NV] {live block, count, other block, lg live | lg other << 8}
+  uint64_t tcap;           // bulk-merge scratch entries (reused every wavefront)
+  long long* t_cost;       // [tcap] survivors of one run: cost, h, parent ref, insertion index
+  long long* t_h;
+  uint32_t* t_pp;
+  uint32_t* t_m;
   uint4* gdesc;            // per node {iteration stamp, group count, group offset, 0}
   uint32_t* touch_stamp;
   uint32_t* oh_stamp;
@@ -123,6 +130,7 @@ struct WS {
   uint32_t* g_pid;
   uint2* oh_list;           // [2][NV] {node, query} with open plans (this / next wavefront)
   uint2* t_list;            // [NV] {node, query} touched this wavefront
+  uint2* b_list;            // [NV] {node, query} left to the bulk prune this wavefront
   uint32_t* a_head;
   uint32_t* a_parent;
   uint32_t* a_iter;
@@ -239,7 +247,9 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
     c.prof = prof;
     c.max_front = 1;
     c.pool_n = (unsigned long long)nq << kMinLg;   // the roots' blocks
-    for (int k = 0; k < 3; ++k) {
+    c.tmp_n = 0;
+    c.b_n = 0;
+    for (int k = 0; k < 4; ++k) {
       c.kt[k].start = ULLONG_MAX;
       c.kt[k].total_ns = 0;
       c.kt[k].blocks = 0;
@@ -516,7 +526,7 @@ __device__ __forceinline__ uint32_t chunk_skyline(WarpSmem& sm, bool ok, long lo
 // merged front is written to the node's other block, which then becomes live.
 // Candidate tie key tb = 1 + parent head (old plans have tie key 0, i.e. they win
 // exact (cost, h) ties).
-__device__ void merge_chunk_slab(const WS& w, uint32_t q, FrontCursor& fc, WarpSmem& sm, bool ok,
+__device__ __forceinline__ void merge_chunk_slab(const WS& w, uint32_t q, FrontCursor& fc, WarpSmem& sm, bool ok,
                                  long long cc, long long ch, uint32_t ctb, uint32_t cpp) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
@@ -603,11 +613,170 @@ __device__ void merge_chunk_slab(const WS& w, uint32_t q, FrontCursor& fc, WarpS
   __syncwarp();
 }
 
+// Bulk merge of one in-edge's candidate run into a block-mode front.  The run is
+// the source's group (a contiguous part of its front: costs increasing, h
+// decreasing) shifted along one edge, so its costs increase and its h do not
+// increase: it is its own skyline once entries whose h equals their
+// predecessor's are dropped.  Pass 1 keeps the run entries that pass the beta
+// cutoff and survive the live front, compacting them into a temporary pool block
+// with their insertion index m (front entries of lower or equal cost); pass 2
+// sweeps the front once, dropping the entries a survivor dominates and
+// interleaving the survivors.  O(n/32 + L log n / 32) warp steps per run, against
+// O(L/32 * n/32) for chunked merging.
+// Returns false (and changes nothing) when this wavefront's scratch is used up;
+// the caller then merges the run in chunks.
+__device__ __forceinline__ bool merge_run_bulk(const WS& w, uint32_t q, FrontCursor& fc, long long beta, uint32_t goff,
+                                               uint32_t L, int cq, int S, int C, int Sm, int Cm, bool interior,
+                                               uint32_t tb) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long T = 0;
+  if (lane == 0) T = atomicAdd(&w.ctl->tmp_n, (unsigned long long)L);
+  T = __shfl_sync(kFull, T, 0);
+  if (T + L > w.tcap) return false;
+  const size_t o = fc.off;
+  const uint32_t n = fc.n;
+  // pass 1: survivors of the run, in run order, with their insertion index m
+  uint32_t ns = 0;
+  for (uint32_t r0 = 0; r0 < L; r0 += 32) {
+    const uint32_t r = r0 + lane;
+    bool ok = false;
+    long long cc = 0, ch = 0;
+    uint32_t pp = 0, m = 0;
+    if (r < L) {
+      const uint32_t gi = goff + r;
+      const long long gh = w.g_h[gi];
+      cc = w.g_cost[gi] + (long long)cq;
+      const long long hh = gh + (long long)S;
+      ch = hh > (long long)C ? hh : (long long)C;
+      pp = w.g_pid[gi];
+      long long peak = ch;
+      if (interior) {
+        const long long hp = gh + (long long)Sm;
+        peak = hp > (long long)Cm ? hp : (long long)Cm;
+      }
+      ok = peak <= beta;
+      if (ok && r > 0) {
+        // the run predecessor (lower cost, h never lower) dominates iff its h is equal
+        const long long ph = w.g_h[gi - 1] + (long long)S;
+        const long long pch = ph > (long long)C ? ph : (long long)C;
+        if (pch <= ch) ok = false;
+      }
+      if (ok) {
+        uint32_t lo = 0, hi = n;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (w.f_cost[o + mid] <= cc) lo = mid + 1; else hi = mid;
+        }
+        if (lo > 0) {
+          const uint32_t j = lo - 1;
+          const long long fcost = w.f_cost[o + j], fh = w.f_h[o + j];
+          const uint32_t fpid = w.f_pid[o + j];
+          const uint32_t ftb = (fpid & kNew) ? w.f_aux[o + j] : 0u;
+          if (fh <= ch && (fcost < cc || fh < ch || ftb < tb)) ok = false;
+        }
+        m = lo;
+      }
+    }
+    const unsigned sb = __ballot_sync(kFull, ok);
+    if (ok) {
+      const size_t t = (size_t)T + ns + __popc(sb & lt);
+      w.t_cost[t] = cc;
+      w.t_h[t] = ch;
+      w.t_pp[t] = pp;
+      w.t_m[t] = m;
+    }
+    ns += __popc(sb);
+  }
+  if (ns == 0) return true;
+  if (!ensure_other(w, q, fc, n + ns)) return true;
+  __syncwarp();
+  // pass 2: one sweep over the front
+  const size_t on = fc.off2;
+  uint32_t K = 0, sp = 0, rem_open = 0;
+  for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    const bool valid = j < n;
+    long long fcost = 0, fh = 0;
+    uint32_t fpid = 0, faux = 0;
+    if (valid) {
+      fcost = w.f_cost[o + j];
+      fh = w.f_h[o + j];
+      fpid = w.f_pid[o + j];
+      faux = w.f_aux[o + j];
+    }
+    const uint32_t ftb = (fpid & kNew) ? faux : 0u;
+    // survivors of lower or equal cost; the last of them is the only one that can dominate
+    uint32_t lo = 0, hi = ns;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (w.t_cost[(size_t)T + mid] <= fcost) lo = mid + 1; else hi = mid;
+    }
+    bool dom = false;
+    if (valid && lo > 0) {
+      const long long sc = w.t_cost[(size_t)T + lo - 1], sh = w.t_h[(size_t)T + lo - 1];
+      dom = sh <= fh && (sc < fcost || sh < fh || tb < ftb);
+    }
+    const bool keep = valid && !dom;
+    if (dom && (fpid & kOpen) && !(fpid & kNew)) rem_open++;
+    const unsigned kb = __ballot_sync(kFull, keep);
+    if (keep) {
+      const size_t pos = on + K + __popc(kb & lt) + lo;
+      w.f_cost[pos] = fcost;
+      w.f_h[pos] = fh;
+      w.f_pid[pos] = fpid;
+      w.f_aux[pos] = faux;
+    }
+    // survivors inserted before a front entry of this chunk (m < end of chunk)
+    const uint32_t jend = min(j0 + 32u, n);
+    for (;;) {
+      const uint32_t s = sp + lane;
+      bool emit = false;
+      uint32_t m = 0;
+      if (s < ns) {
+        m = w.t_m[(size_t)T + s];
+        emit = m < jend;
+      }
+      const unsigned eb = __ballot_sync(kFull, emit);
+      if (emit) {
+        const uint32_t d = m - j0;   // 0 .. 31: earlier chunks emitted every m < j0
+        const size_t pos = on + s + K + __popc(kb & ((1u << d) - 1u));
+        w.f_cost[pos] = w.t_cost[(size_t)T + s];
+        w.f_h[pos] = w.t_h[(size_t)T + s];
+        w.f_pid[pos] = w.t_pp[(size_t)T + s] | kNew;
+        w.f_aux[pos] = tb;
+      }
+      const uint32_t c = __popc(eb);
+      sp += c;
+      if (c < 32) break;
+    }
+    K += __popc(kb);
+  }
+  // survivors after every front entry
+  for (uint32_t s0 = sp; s0 < ns; s0 += 32) {
+    const uint32_t s = s0 + lane;
+    if (s < ns) {
+      const size_t pos = on + s + K;
+      w.f_cost[pos] = w.t_cost[(size_t)T + s];
+      w.f_h[pos] = w.t_h[(size_t)T + s];
+      w.f_pid[pos] = w.t_pp[(size_t)T + s] | kNew;
+      w.f_aux[pos] = tb;
+    }
+  }
+  for (int sft = 16; sft > 0; sft >>= 1) rem_open += __shfl_xor_sync(kFull, rem_open, sft);
+  fc.removed_open += rem_open;
+  swap_blocks(fc);
+  fc.n = K + ns;
+  fc.any_new = true;
+  __syncwarp();
+  return true;
+}
+
 // Register-mode merge: the front (n <= 32) is held one entry per lane; all
 // dominance tests are broadcasts over lanes.  If the merged front exceeds 32
 // entries it is written to the node's other block and the node continues in
 // block mode.
-__device__ void merge_chunk_reg(const WS& w, uint32_t q, FrontCursor& fc, WarpSmem& sm, bool ok,
+__device__ __forceinline__ void merge_chunk_reg(const WS& w, uint32_t q, FrontCursor& fc, WarpSmem& sm, bool ok,
                                 long long cc, long long ch, uint32_t ctb, uint32_t cpp) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
@@ -688,6 +857,183 @@ __device__ void merge_chunk_reg(const WS& w, uint32_t q, FrontCursor& fc, WarpSm
   __syncwarp();
 }
 
+// Arena records for the new entries of a block-mode front (marked open);
+// returns their number.
+__device__ __forceinline__ uint32_t arena_block(const WS& w, uint32_t q, uint32_t x, uint32_t it,
+                                                const FrontCursor& fc) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t n_new = 0;
+  const size_t o = fc.off;
+  for (uint32_t j0 = 0; j0 < fc.n; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    uint32_t pid = 0;
+    if (j < fc.n) pid = w.f_pid[o + j];
+    const bool isnew = (j < fc.n) && (pid & kNew);
+    const unsigned bal = __ballot_sync(kFull, isnew);
+    if (!bal) continue;
+    unsigned long long a0 = 0;
+    if (lane == 0) a0 = atomicAdd(&w.ctl->arena_n, (unsigned long long)__popc(bal));
+    a0 = __shfl_sync(kFull, a0, 0);
+    if (isnew) {
+      const unsigned long long a = a0 + __popc(bal & lt);
+      if (a < w.acap) {
+        w.a_head[a] = x;
+        w.a_parent[a] = pid & kPidMask;
+        w.a_iter[a] = it + 1;
+        w.a_cost[a] = w.f_cost[o + j];
+        w.f_pid[o + j] = (uint32_t)a | kOpen;
+      } else {
+        query_error(w, q, kErrArena);
+        w.f_pid[o + j] = kOpen;
+      }
+      w.f_aux[o + j] = 0;
+    }
+    n_new += __popc(bal);
+  }
+  return n_new;
+}
+
+// The node's new descriptor and counters, and its place in the next open list.
+__device__ __forceinline__ void commit_tail(const WS& w, uint32_t q, uint32_t g, uint32_t it, const FrontCursor& fc,
+                                            uint32_t n_new, uint2* next) {
+  if (lane_id() == 0) {
+    w.fdesc[g] = make_uint4(fc.off, fc.n, fc.off2, fc.lg | (fc.lg2 << 8));
+    atomic_add_i64(&w.qs[q].open_cnt, (long long)n_new - (long long)fc.removed_open);
+    atomicAdd(&w.qs[q].plans, (unsigned long long)n_new);
+    atomicMax(&w.ctl->max_front, fc.n);
+    if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = make_uint2(g, q);
+  }
+}
+
+// One node whose front is in block mode (more than 32 plans) at the start of the
+// wavefront: if its in-edge runs are long on average every run is merged in
+// bulk, otherwise its candidates are merged in chunks of 32; then the front is
+// committed.
+__device__ __forceinline__ void prune_node_bulk(const WS& w, WarpSmem& sm, uint32_t q, uint32_t g, uint32_t x,
+                                             const QueryDev& Q, uint32_t it, uint32_t e_beg, uint32_t e_end,
+                                             bool interior, uint2* next) {
+  const unsigned lane = lane_id();
+  FrontCursor fc;
+  {
+    const uint4 fd = w.fdesc[g];
+    fc.off = fd.x;
+    fc.n = fd.y;
+    fc.off2 = fd.z;
+    fc.lg = fd.w & 0xFFu;
+    fc.lg2 = (fd.w >> 8) & 0xFFu;
+  }
+  fc.reg = false;
+  fc.err = false;
+  fc.removed_open = 0;
+  fc.any_new = false;
+  fc.rc = fc.rh = 0;
+  fc.rp = fc.ra = 0;
+  unsigned long long exps = 0;
+  // runs long on average (more than 32 candidates per run): bulk merges; else
+  // all candidates in chunks of 32
+  uint32_t ctot = 0, runs = 0;
+  for (uint32_t e0 = e_beg; e0 < e_end; e0 += 32) {
+    const uint32_t e = e0 + lane;
+    uint32_t cnt = 0;
+    if (e < e_end) {
+      const uint4 gd = w.gdesc[Q.base + (uint32_t)__ldg(&Q.rev_edge[e]).x];
+      if (gd.x == it) cnt = gd.y;
+    }
+    ctot += __reduce_add_sync(kFull, cnt);
+    runs += __popc(__ballot_sync(kFull, cnt > 0));
+  }
+  const bool bulk = ctot > 32u * runs;
+  for (uint32_t e0 = e_beg; e0 < e_end; e0 += 32) {
+    const uint32_t e = e0 + lane;
+    int4 ed = make_int4(0, 0, 0, 0);
+    int2 pk = make_int2(0, 0);
+    uint32_t cnt = 0, goff = 0;
+    if (e < e_end) {
+      ed = __ldg(&Q.rev_edge[e]);
+      if (interior) pk = __ldg(&Q.rev_peak[e]);
+      const uint4 gd = w.gdesc[Q.base + (uint32_t)ed.x];
+      if (gd.x == it) {
+        cnt = gd.y;
+        goff = gd.z;
+      }
+    }
+    exps += __reduce_add_sync(kFull, cnt);
+    if (!bulk) {
+      // chunked: candidates of all runs of this chunk of in-edges, 32 at a time
+      const uint32_t incl = warp_incl_scan(cnt);
+      const uint32_t total = __shfl_sync(kFull, incl, 31);
+      const uint32_t excl = incl - cnt;
+      for (uint32_t c0 = 0; c0 < total && !fc.err; c0 += 32) {
+        const uint32_t c = c0 + lane;
+        uint32_t owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t probe = owner + step;
+          if (__shfl_sync(kFull, excl, probe) <= c) owner = probe;
+        }
+        const uint32_t o_excl = __shfl_sync(kFull, excl, owner), o_goff = __shfl_sync(kFull, goff, owner);
+        const int o_src = __shfl_sync(kFull, ed.x, owner), o_cq = __shfl_sync(kFull, ed.y, owner);
+        const int o_S = __shfl_sync(kFull, ed.z, owner), o_C = __shfl_sync(kFull, ed.w, owner);
+        const int o_Sm = __shfl_sync(kFull, pk.x, owner), o_Cm = __shfl_sync(kFull, pk.y, owner);
+        bool ok = false;
+        long long cc = 0, ch = 0;
+        uint32_t pp = 0;
+        if (c < total) {
+          const uint32_t gi = o_goff + (c - o_excl);
+          const long long gh = w.g_h[gi];
+          cc = w.g_cost[gi] + (long long)o_cq;
+          const long long hh = gh + (long long)o_S;
+          ch = hh > (long long)o_C ? hh : (long long)o_C;
+          pp = w.g_pid[gi];
+          long long peak = ch;
+          if (interior) {
+            const long long hp = gh + (long long)o_Sm;
+            peak = hp > (long long)o_Cm ? hp : (long long)o_Cm;
+          }
+          ok = peak <= Q.beta;
+        }
+        merge_chunk_slab(w, q, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
+      }
+      continue;
+    }
+    for (unsigned rb = __ballot_sync(kFull, cnt > 0); rb; rb &= rb - 1) {
+      const int l = __ffs(rb) - 1;
+      const uint32_t r_goff = __shfl_sync(kFull, goff, l), r_cnt = __shfl_sync(kFull, cnt, l);
+      const int r_src = __shfl_sync(kFull, ed.x, l), r_cq = __shfl_sync(kFull, ed.y, l);
+      const int r_S = __shfl_sync(kFull, ed.z, l), r_C = __shfl_sync(kFull, ed.w, l);
+      const int r_Sm = __shfl_sync(kFull, pk.x, l), r_Cm = __shfl_sync(kFull, pk.y, l);
+      if (fc.err) continue;
+      if (merge_run_bulk(w, q, fc, Q.beta, r_goff, r_cnt, r_cq, r_S, r_C, r_Sm, r_Cm, interior, 1u + (uint32_t)r_src))
+        continue;
+      // scratch used up this wavefront: merge the run in chunks of 32
+      for (uint32_t r0 = 0; r0 < r_cnt && !fc.err; r0 += 32) {
+        const uint32_t r = r0 + lane;
+        bool ok = false;
+        long long cc = 0, ch = 0;
+        uint32_t pp = 0;
+        if (r < r_cnt) {
+          const uint32_t gi = r_goff + r;
+          const long long gh = w.g_h[gi];
+          cc = w.g_cost[gi] + (long long)r_cq;
+          const long long hh = gh + (long long)r_S;
+          ch = hh > (long long)r_C ? hh : (long long)r_C;
+          pp = w.g_pid[gi];
+          long long peak = ch;
+          if (interior) {
+            const long long hp = gh + (long long)r_Sm;
+            peak = hp > (long long)r_Cm ? hp : (long long)r_Cm;
+          }
+          ok = peak <= Q.beta;
+        }
+        merge_chunk_slab(w, q, fc, sm, ok, cc, ch, 1u + (uint32_t)r_src, pp);
+      }
+    }
+  }
+  if (fc.any_new && !fc.err) commit_tail(w, q, g, it, fc, arena_block(w, q, x, it, fc), next);
+  if (lane == 0 && exps) atomicAdd(&w.qs[q].expansions, exps);
+}
+
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_prune(WS w) {
   ktime_begin(w, 1);
   __shared__ WarpSmem smem[kWarpsPerBlock];
@@ -733,7 +1079,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
     unsigned long long exps = 0;
     const uint32_t e_end = Q.rev_ptr[x + 1];
     const bool interior = (Q.flags & MPAP_QUERY_CHECK_INTERIOR) != 0;
-    for (uint32_t e0 = Q.rev_ptr[x]; e0 < e_end; e0 += 32) {
+    // a front in block mode from the start goes to the bulk prune kernel
+    const bool to_bulk = !fc.reg;
+    for (uint32_t e0 = to_bulk ? e_end : Q.rev_ptr[x]; e0 < e_end; e0 += 32) {
       const uint32_t e = e0 + lane;
       int4 ed = make_int4(0, 0, 0, 0);
       int2 pk = make_int2(0, 0);
@@ -839,52 +1187,45 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
           w.f_aux[o + lane] = fc.ra;
         }
       } else {
-        const size_t o = fc.off;
-        for (uint32_t j0 = 0; j0 < fc.n; j0 += 32) {
-          const uint32_t j = j0 + lane;
-          uint32_t pid = 0;
-          if (j < fc.n) pid = w.f_pid[o + j];
-          const bool isnew = (j < fc.n) && (pid & kNew);
-          const unsigned bal = __ballot_sync(kFull, isnew);
-          if (!bal) continue;
-          unsigned long long a0 = 0;
-          if (lane == 0) a0 = atomicAdd(&w.ctl->arena_n, (unsigned long long)__popc(bal));
-          a0 = __shfl_sync(kFull, a0, 0);
-          if (isnew) {
-            const unsigned long long a = a0 + __popc(bal & lt);
-            if (a < w.acap) {
-              w.a_head[a] = x;
-              w.a_parent[a] = pid & kPidMask;
-              w.a_iter[a] = it + 1;
-              w.a_cost[a] = w.f_cost[o + j];
-              w.f_pid[o + j] = (uint32_t)a | kOpen;
-            } else {
-              query_error(w, q, kErrArena);
-              w.f_pid[o + j] = kOpen;
-            }
-            w.f_aux[o + j] = 0;
-          }
-          n_new += __popc(bal);
-        }
+        n_new = arena_block(w, q, x, it, fc);
       }
-      if (lane == 0) {
-        w.fdesc[g] = make_uint4(fc.off, fc.n, fc.off2, fc.lg | (fc.lg2 << 8));
-        atomic_add_i64(&w.qs[q].open_cnt, (long long)n_new - (long long)fc.removed_open);
-        atomicAdd(&w.qs[q].plans, (unsigned long long)n_new);
-        atomicMax(&w.ctl->max_front, fc.n);
-        if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = make_uint2(g, q);
-      }
+      commit_tail(w, q, g, it, fc, n_new, next);
     }
     if (lane == 0 && exps) atomicAdd(&w.qs[q].expansions, exps);
+    if (to_bulk && lane == 0) w.b_list[atomicAdd(&w.ctl->b_n, 1u)] = make_uint2(g, q);
   }
   ktime_end(w, 1);
+}
+
+// ---------------------------------------------------------------------------
+// bulk prune: the nodes k_prune queued (fronts in block mode at the start of
+// the wavefront), warp per node.  A kernel of its own, so that the
+// register-mode path of k_prune keeps its registers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prune_bulk(WS w) {
+  ktime_begin(w, 2);
+  __shared__ WarpSmem smem[kWarpsPerBlock];
+  WarpSmem& sm = smem[threadIdx.x >> 5];
+  const uint32_t it = w.ctl->it;
+  const uint32_t n_list = (w.ctl->n_done < w.ctl->nq) ? w.ctl->b_n : 0u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  uint2* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
+  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
+    const uint2 gq = w.b_list[k];
+    const uint32_t g = gq.x, q = gq.y;
+    const QueryDev& Q = w.qd[q];
+    const uint32_t x = g - Q.base;
+    prune_node_bulk(w, sm, q, g, x, Q, it, Q.rev_ptr[x], Q.rev_ptr[x + 1], (Q.flags & MPAP_QUERY_CHECK_INTERIOR) != 0,
+                    next);
+  }
+  ktime_end(w, 2);
 }
 
 // ---------------------------------------------------------------------------
 // end of wavefront (one block): termination per query, list swap, loop control.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_end(WS w, cudaGraphConditionalHandle cond, uint32_t in_graph) {
-  ktime_begin(w, 2);
+  ktime_begin(w, 3);
   __shared__ uint32_t s_newly;
   const uint32_t it = w.ctl->it, nq = w.ctl->nq;
   if (threadIdx.x == 0) s_newly = 0;
@@ -915,10 +1256,12 @@ __global__ void __launch_bounds__(1024) k_end(WS w, cudaGraphConditionalHandle c
     w.ctl->oh_n[it & 1] = 0;
     w.ctl->t_n = 0;
     w.ctl->g_n = 0;
+    w.ctl->tmp_n = 0;
+    w.ctl->b_n = 0;
     w.ctl->it = it + 1;
     if (in_graph) cudaGraphSetConditional(cond, (done < nq && it + 1 < w.ctl->iter_cap) ? 1u : 0u);
   }
-  ktime_end(w, 2);
+  ktime_end(w, 3);
 }
 
 // ---------------------------------------------------------------------------
@@ -1200,6 +1543,7 @@ int32_t build_loop_graph(mpap_workspace* ws, uint32_t sel, uint32_t pru) {
   const int n = sms();
   k_select<<<sel * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
   k_prune<<<pru * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
+  k_prune_bulk<<<2 * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
   k_end<<<1, 1024, 0, ws->cap_stream>>>(ws->w, cond, 1u);
   cudaGraph_t captured = nullptr;
   MPAP_CK(cudaStreamEndCapture(ws->cap_stream, &captured));
@@ -1238,15 +1582,17 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
   }
   w.acap = max_plans;
   w.gcap = max_plans;
+  w.tcap = max_plans;
   w.path_cap = 4096;
   ws->max_q = max_q;
   const size_t slots = (size_t)w.pcap;
   bool ok = walloc(&w.f_cost, slots) && walloc(&w.f_h, slots) && walloc(&w.f_pid, slots) &&
-            walloc(&w.f_aux, slots) && walloc(&w.fdesc, w.NV) &&
+            walloc(&w.f_aux, slots) && walloc(&w.fdesc, w.NV) && walloc(&w.t_cost, w.tcap) && walloc(&w.t_h, w.tcap) &&
+            walloc(&w.t_pp, w.tcap) && walloc(&w.t_m, w.tcap) &&
             walloc(&w.gdesc, w.NV) && walloc(&w.touch_stamp, w.NV) &&
             walloc(&w.oh_stamp, w.NV) &&
             walloc(&w.g_cost, w.gcap) && walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) &&
-            walloc(&w.oh_list, 2 * w.NV) && walloc(&w.t_list, w.NV) && walloc(&w.a_head, w.acap) &&
+            walloc(&w.oh_list, 2 * w.NV) && walloc(&w.t_list, w.NV) && walloc(&w.b_list, w.NV) && walloc(&w.a_head, w.acap) &&
             walloc(&w.a_parent, w.acap) && walloc(&w.a_iter, w.acap) && walloc(&w.a_cost, w.acap) &&
             walloc(&w.ctl, 1) && walloc(&w.qd, max_q) && walloc(&w.qs, max_q) && walloc(&w.res, max_q) &&
             walloc(&w.path, (size_t)max_q * w.path_cap);
@@ -1264,8 +1610,8 @@ void workspace_free(mpap_workspace* ws) {
   if (ws->graph) cudaGraphDestroy(ws->graph);
   if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
   WS& w = ws->w;
-  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.fdesc, w.gdesc, w.touch_stamp,
-                  w.oh_stamp, w.g_cost, w.g_h, w.g_pid, w.oh_list, w.t_list,
+  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.fdesc, w.t_cost, w.t_h, w.t_pp, w.t_m, w.gdesc, w.touch_stamp,
+                  w.oh_stamp, w.g_cost, w.g_h, w.g_pid, w.oh_list, w.t_list, w.b_list,
                   w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl, w.qd, w.qs, w.res, w.path};
   for (void* p : ptrs) cudaFree(p);
   delete ws;
@@ -1380,6 +1726,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
       for (int r = 0; r < 2; ++r) {
         k_select<<<tun.select_blocks_per_sm * n, kWarpsPerBlock * 32, 0, st>>>(w);
         k_prune<<<tun.prune_blocks_per_sm * n, kWarpsPerBlock * 32, 0, st>>>(w);
+        k_prune_bulk<<<2 * n, kWarpsPerBlock * 32, 0, st>>>(w);
         k_end<<<1, 1024, 0, st>>>(w, 0ull, 0u);
       }
       MPAP_CK(cudaGetLastError());
@@ -1401,10 +1748,10 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   MPAP_CK(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaStreamSynchronize(st));
   ws->last_max_front = hc.max_front;
-  launch_count_add(3ull * hc.it);
+  launch_count_add(4ull * hc.it);
   if (prof) {
-    const char* names[3] = {"k_select", "k_prune", "k_end"};
-    for (int k = 0; k < 3; ++k) profile_add(names[k], hc.kt[k].launches, (double)hc.kt[k].total_ns * 1e-6);
+    const char* names[4] = {"k_select", "k_prune", "k_prune_bulk", "k_end"};
+    for (int k = 0; k < 4; ++k) profile_add(names[k], hc.kt[k].launches, (double)hc.kt[k].total_ns * 1e-6);
   }
   rc = MPAP_OK;
   for (uint32_t i = 0; i < nq; ++i) {
