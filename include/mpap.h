@@ -231,10 +231,12 @@ void mpap_roadmap_free(mpap_roadmap* rm);
  * entries (24 bytes each; the product must not exceed 2^32 - 16): every node
  * draws two blocks from it (its live front and a merge target), of 16 entries
  * and up, replaced by blocks twice the needed size as its front grows, so single
- * fronts may be far larger than front_cap as long as the pool lasts.  A query
- * that runs out of pool, plan arena (max_plans) or group array (max_plans) ends
- * with MPAP_ERR_CAPACITY in its own result; the other queries of the batch run
- * on.  Allocates with cudaMalloc; reused by every search call. */
+ * fronts may be far larger than front_cap as long as the pool lasts.  Each
+ * query of a call gets its own share of the pool, in proportion to its nodes,
+ * so a query that runs out of its share fails alone whatever the others do.  A
+ * query that runs out of pool, plan arena (max_plans) or group array (max_plans)
+ * ends with MPAP_ERR_CAPACITY in its own result; the other queries of the batch
+ * run on.  Allocates with cudaMalloc; reused by every search call. */
 int32_t mpap_workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans,
                               mpap_workspace** out);
 void mpap_workspace_free(mpap_workspace* ws);
@@ -337,8 +339,9 @@ int32_t mpap_autotune_build(uint32_t n, const mpap_scene* scenes, const mpap_roa
 /* Grid search of the select and prune grids (2, 4, 8, 16 blocks per SM each) on one batched search of these queries, `reps` timed searches per
  * candidate after an untimed one.  Stores the fastest for the batch key and
  * sets best->front_cap to twice the front-pool entries per node the search
- * used, rounded up to a power of two (at least 16).  Fails with MPAP_ERR_CUDA
- * (and stores nothing) if two shapes give different results. */
+ * used, rounded up to a power of two (at least 16).  Queries that run out of
+ * their pool share keep that status (it is part of the compared results).  Fails
+ * with MPAP_ERR_CUDA (and stores nothing) if two shapes give different results. */
 int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs,
                              uint32_t nq, uint32_t reps, mpap_tuning* best, double* best_ms,
                              void* stream);

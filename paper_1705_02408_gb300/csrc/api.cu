@@ -565,7 +565,10 @@ int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const
       outs[i].path = paths[i].data();
       outs[i].path_cap = 4096;
     }
-    return mpap::search_batch_impl(ws, rms, qs, nq, outs.data(), st);
+    // a query out of its own pool share reports it in its status, which is
+    // compared across shapes like every other result
+    const int32_t rc = mpap::search_batch_impl(ws, rms, qs, nq, outs.data(), st);
+    return rc == MPAP_ERR_CAPACITY ? MPAP_OK : rc;
   };
   double best_t = 1e300;
   mpap_tuning bt = base;

@@ -59,6 +59,8 @@ struct QueryDev {
   uint32_t pad;
   int64_t beta;
   int64_t Lambda;
+  uint64_t pool_base;       // this query's share of the front pool: [base, base + cap)
+  uint64_t pool_cap;
 };
 
 struct QueryState {
@@ -71,6 +73,7 @@ struct QueryState {
   int32_t status;
   uint32_t err;          // capacity error bits of this query (pool, arena, group)
   uint32_t pad;
+  unsigned long long pool_n;  // entries of its pool share handed out
 };
 
 struct ResultDev {
@@ -185,12 +188,14 @@ __device__ __forceinline__ uint32_t ceil_lg(uint32_t n) {
   return n <= 1 ? 0u : 32u - (uint32_t)__clz(n - 1u);
 }
 
-// One block of 2^lg pool entries (call from one lane); kNoBlock when the pool is
-// exhausted.
-__device__ __forceinline__ uint32_t pool_alloc(const WS& w, uint32_t lg) {
+// One block of 2^lg entries of query q's pool share (call from one lane);
+// kNoBlock when the share is used up.  Shares are disjoint, so a query that
+// runs out fails alone, whatever the others do.
+__device__ __forceinline__ uint32_t pool_alloc(const WS& w, uint32_t q, uint32_t lg) {
   const unsigned long long sz = 1ull << lg;
-  const unsigned long long o = atomicAdd(&w.ctl->pool_n, sz);
-  return (o + sz <= w.pcap) ? (uint32_t)o : kNoBlock;
+  const unsigned long long o = atomicAdd(&w.qs[q].pool_n, sz);
+  const QueryDev& Q = w.qd[q];
+  return (o + sz <= Q.pool_cap) ? (uint32_t)(Q.pool_base + o) : kNoBlock;
 }
 
 // Records a capacity error of query q (it ends at the next end-of-wavefront).
@@ -246,7 +251,7 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
     c.iter_cap = iter_cap;
     c.prof = prof;
     c.max_front = 1;
-    c.pool_n = (unsigned long long)nq << kMinLg;   // the roots' blocks
+    c.pool_n = 0;
     c.tmp_n = 0;
     c.b_n = 0;
     for (int k = 0; k < 4; ++k) {
@@ -268,8 +273,9 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
   s.status = 0;
   s.err = 0;
   s.pad = 0;
+  s.pool_n = 1u << kMinLg;          // the root's block opens the query's share
   w.qs[q] = s;
-  const uint32_t o = q << kMinLg;   // block q of the pool
+  const uint32_t o = (uint32_t)w.qd[q].pool_base;
   w.f_cost[o] = 0;
   w.f_h[o] = 0;
   w.f_pid[o] = q | kOpen;      // the root plan (x_init, {}, 0, 0) is arena record q
@@ -422,7 +428,7 @@ __device__ __forceinline__ bool ensure_other(const WS& w, uint32_t q, FrontCurso
   if (fc.lg2 != 0 && (1u << fc.lg2) >= need) return true;
   const uint32_t lg = max(kMinLg, ceil_lg(need) + 1u);
   uint32_t o = 0;
-  if (lane_id() == 0) o = pool_alloc(w, lg);
+  if (lane_id() == 0) o = pool_alloc(w, q, lg);
   o = __shfl_sync(kFull, o, 0);
   if (o == kNoBlock) {
     if (lane_id() == 0) query_error(w, q, kErrFront);
@@ -630,65 +636,74 @@ __device__ __forceinline__ bool merge_run_bulk(const WS& w, uint32_t q, FrontCur
                                                uint32_t tb) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
-  unsigned long long T = 0;
-  if (lane == 0) T = atomicAdd(&w.ctl->tmp_n, (unsigned long long)L);
-  T = __shfl_sync(kFull, T, 0);
-  if (T + L > w.tcap) return false;
   const size_t o = fc.off;
   const uint32_t n = fc.n;
-  // pass 1: survivors of the run, in run order, with their insertion index m
+  // run entry r: candidate, and whether it passes the cutoff, its run
+  // predecessor and the live front (m = front entries of lower or equal cost)
+  auto entry = [&](uint32_t r, long long& cc, long long& ch, uint32_t& pp, uint32_t& m) -> bool {
+    const uint32_t gi = goff + r;
+    const long long gh = w.g_h[gi];
+    cc = w.g_cost[gi] + (long long)cq;
+    const long long hh = gh + (long long)S;
+    ch = hh > (long long)C ? hh : (long long)C;
+    pp = w.g_pid[gi];
+    long long peak = ch;
+    if (interior) {
+      const long long hp = gh + (long long)Sm;
+      peak = hp > (long long)Cm ? hp : (long long)Cm;
+    }
+    if (peak > beta) return false;
+    if (r > 0) {
+      // the run predecessor (lower cost, h never lower) dominates iff its h is equal
+      const long long ph = w.g_h[gi - 1] + (long long)S;
+      const long long pch = ph > (long long)C ? ph : (long long)C;
+      if (pch <= ch) return false;
+    }
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (w.f_cost[o + mid] <= cc) lo = mid + 1; else hi = mid;
+    }
+    m = lo;
+    if (lo > 0) {
+      const uint32_t j = lo - 1;
+      const long long fcost = w.f_cost[o + j], fh = w.f_h[o + j];
+      const uint32_t fpid = w.f_pid[o + j];
+      const uint32_t ftb = (fpid & kNew) ? w.f_aux[o + j] : 0u;
+      if (fh <= ch && (fcost < cc || fh < ch || ftb < tb)) return false;
+    }
+    return true;
+  };
+  // pass 1a: count the survivors, then take exactly that much scratch
   uint32_t ns = 0;
   for (uint32_t r0 = 0; r0 < L; r0 += 32) {
     const uint32_t r = r0 + lane;
-    bool ok = false;
+    long long cc, ch;
+    uint32_t pp, m;
+    ns += __popc(__ballot_sync(kFull, r < L && entry(r, cc, ch, pp, m)));
+  }
+  if (ns == 0) return true;
+  unsigned long long T = 0;
+  if (lane == 0) T = atomicAdd(&w.ctl->tmp_n, (unsigned long long)ns);
+  T = __shfl_sync(kFull, T, 0);
+  if (T + ns > w.tcap) return false;
+  // pass 1b: the survivors, in run order, with their insertion index m
+  uint32_t k = 0;
+  for (uint32_t r0 = 0; r0 < L; r0 += 32) {
+    const uint32_t r = r0 + lane;
     long long cc = 0, ch = 0;
     uint32_t pp = 0, m = 0;
-    if (r < L) {
-      const uint32_t gi = goff + r;
-      const long long gh = w.g_h[gi];
-      cc = w.g_cost[gi] + (long long)cq;
-      const long long hh = gh + (long long)S;
-      ch = hh > (long long)C ? hh : (long long)C;
-      pp = w.g_pid[gi];
-      long long peak = ch;
-      if (interior) {
-        const long long hp = gh + (long long)Sm;
-        peak = hp > (long long)Cm ? hp : (long long)Cm;
-      }
-      ok = peak <= beta;
-      if (ok && r > 0) {
-        // the run predecessor (lower cost, h never lower) dominates iff its h is equal
-        const long long ph = w.g_h[gi - 1] + (long long)S;
-        const long long pch = ph > (long long)C ? ph : (long long)C;
-        if (pch <= ch) ok = false;
-      }
-      if (ok) {
-        uint32_t lo = 0, hi = n;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (w.f_cost[o + mid] <= cc) lo = mid + 1; else hi = mid;
-        }
-        if (lo > 0) {
-          const uint32_t j = lo - 1;
-          const long long fcost = w.f_cost[o + j], fh = w.f_h[o + j];
-          const uint32_t fpid = w.f_pid[o + j];
-          const uint32_t ftb = (fpid & kNew) ? w.f_aux[o + j] : 0u;
-          if (fh <= ch && (fcost < cc || fh < ch || ftb < tb)) ok = false;
-        }
-        m = lo;
-      }
-    }
+    const bool ok = r < L && entry(r, cc, ch, pp, m);
     const unsigned sb = __ballot_sync(kFull, ok);
     if (ok) {
-      const size_t t = (size_t)T + ns + __popc(sb & lt);
+      const size_t t = (size_t)T + k + __popc(sb & lt);
       w.t_cost[t] = cc;
       w.t_h[t] = ch;
       w.t_pp[t] = pp;
       w.t_m[t] = m;
     }
-    ns += __popc(sb);
+    k += __popc(sb);
   }
-  if (ns == 0) return true;
   if (!ensure_other(w, q, fc, n + ns)) return true;
   __syncwarp();
   // pass 2: one sweep over the front
@@ -1144,7 +1159,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
       // the register front needs a (larger) live block to be written back to
       const uint32_t lg = max(kMinLg, ceil_lg(fc.n));
       uint32_t o = 0;
-      if (lane == 0) o = pool_alloc(w, lg);
+      if (lane == 0) o = pool_alloc(w, q, lg);
       o = __shfl_sync(kFull, o, 0);
       if (o == kNoBlock) {
         if (lane == 0) query_error(w, q, kErrFront);
@@ -1202,7 +1217,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
 // the wavefront), warp per node.  A kernel of its own, so that the
 // register-mode path of k_prune keeps its registers.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_prune_bulk(WS w) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) k_prune_bulk(WS w) {
   ktime_begin(w, 2);
   __shared__ WarpSmem smem[kWarpsPerBlock];
   WarpSmem& sm = smem[threadIdx.x >> 5];
@@ -1641,11 +1656,6 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     set_error("search: %u queries exceed the workspace's %u", nq, ws->max_q);
     return MPAP_ERR_INVALID_ARG;
   }
-  if (((uint64_t)nq << 4) > w.pcap) {
-    set_error("search: the front pool (%llu entries) cannot hold the %u queries' roots",
-              (unsigned long long)w.pcap, nq);
-    return MPAP_ERR_CAPACITY;
-  }
   std::vector<QueryDev> qd(nq);
   uint64_t total = 0;
   uint32_t max_iters = 0;
@@ -1688,6 +1698,20 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     set_error("search: %llu nodes exceed the workspace's %llu", (unsigned long long)total,
               (unsigned long long)w.NV);
     return MPAP_ERR_INVALID_ARG;
+  }
+  // every query gets a share of the front pool in proportion to its nodes
+  {
+    uint64_t acc = 0;
+    for (uint32_t i = 0; i < nq; ++i) {
+      const uint64_t cap = (i + 1 == nq) ? w.pcap - acc : (uint64_t)((double)w.pcap * qd[i].V / (double)total);
+      if (cap < 16) {
+        set_error("search: query %u's share of the front pool is below 16 entries", i);
+        return MPAP_ERR_CAPACITY;
+      }
+      qd[i].pool_base = acc;
+      qd[i].pool_cap = cap;
+      acc += cap;
+    }
   }
   int kdim = -1;
   uint32_t kV = 0;
@@ -1774,7 +1798,11 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     if (o.status < 0 && rc == MPAP_OK) rc = o.status;
   }
   MPAP_CK(cudaStreamSynchronize(st));
-  ws->last_pool_used = hc.pool_n;
+  {
+    unsigned long long used = 0;
+    for (uint32_t i = 0; i < nq; ++i) used += std::min<unsigned long long>(qsh[i].pool_n, qd[i].pool_cap);
+    ws->last_pool_used = used;
+  }
   if (hc.err) {
     set_error("search: capacity exceeded in at least one query (flags 0x%x: 1 front pool, 2 plan arena, "
               "4 group array); its status says so, the other queries' results stand", hc.err);

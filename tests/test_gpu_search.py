@@ -174,3 +174,22 @@ def test_query_error_stays_with_its_query(mp, orc):
     for i in (1, 2):
         ro, r = ros[i]
         assert_same_search(res[i], orc.explore(ro, betas[i], orc.group_width(0.5, r)), wsb, index=i)
+
+
+def test_pool_share_exhaustion_stays_with_its_query(mp, orc):
+    """Every query of a batch owns a share of the front pool in proportion to its
+    nodes: a 2D query whose fronts outgrow its share fails, deterministically and
+    alone, and the 6D query beside it is still exact."""
+    s2 = scenegen.make_scene("2d", 2, query_id=2)
+    s6 = scenegen.make_scene("6d", 3, query_id=3)
+    r2 = mp.build_roadmap_for_scene(s2)
+    o6 = orc.build_roadmap(s6, n=1500, r=18.0)
+    r6 = mp.build_roadmap_for_scene(s6, n=1500, r=18.0)
+    b2 = orc.beta_percentile(orc.build_roadmap(s2))
+    b6 = orc.beta_percentile(o6)
+    wsb = mp.Workspace(r2.V + r6.V, front_cap=64, max_plans=1 << 22)
+    qs = [mp.make_query(b2, 0.5, goal_stop=False), mp.make_query(b6, 0.5)]
+    for _ in range(2):
+        res = mp.search_batch(wsb, [r2, r6], qs, check=False)
+        assert res[0].status == mp.MPAP_ERR_CAPACITY
+        assert_same_search(res[1], orc.explore(o6, b6, orc.group_width(0.5, 18.0)), wsb, index=1)
