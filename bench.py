@@ -312,13 +312,14 @@ def run_gpu(args, rank, world, local):
 # DRAM traffic from ncu captures (profiles/*.md), per unit of work, valid only
 # while the kernel sources are the ones that were captured.
 NCU_TRAFFIC = {
-    "k_edges": {"bytes_per_roadmap": (10.0928e6 + 36.237056e6) / 8,
-                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "3232646ccb709cf0e592f862f18b2f772fe002a1",
-                            "paper_1705_02408_gb300/csrc/common.cuh": "9d98f0917e0c93396e66c0986e42f7a820288d41"}},
-    # every k_prune launch of the 8-query, 2-step capture: 895.66 MB of DRAM reads +
-    # writes over 2 x 12,658,585 expansions (profiles/k_prune_6d16k.md)
-    "k_prune": {"bytes_per_expansion": 895661824.0 / (2 * 12658585.0),
-                "sources": {"paper_1705_02408_gb300/csrc/search.cu": "14f3fffca7c67ccece6091241c159a1d533ca532"}},
+    # one launch over 8 roadmaps: 12.44 MB read + 86.04 MB written (profiles/k_edges_6d16k.md)
+    "k_edges": {"bytes_per_roadmap": (12.438272e6 + 86.0416e6) / 8,
+                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "edea94b00aac4b0887c7d958b143b388e7f81245",
+                            "paper_1705_02408_gb300/csrc/common.cuh": "19791654a222d66c59cbf8d9ec58a96651c214e4"}},
+    # every k_prune (and empty k_prune_bulk) launch of the 8-query, 2-step capture:
+    # 889.10 MB of DRAM reads + writes over 2 x 12,658,585 expansions (profiles/k_prune_6d16k.md)
+    "k_prune": {"bytes_per_expansion": 889103104.0 / (2 * 12658585.0),
+                "sources": {"paper_1705_02408_gb300/csrc/search.cu": "ae56e781b445877c7f53644a9a0674fc854e7212"}},
 }
 
 
