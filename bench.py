@@ -348,19 +348,27 @@ def roofline(kern, arm, res, steps):
     exps = sum(r.expansions for r in res)
     plans = sum(r.plans for r in res)
     if name.startswith("k_edges"):
-        # ALU-bound: one exactly evaluated Near test (Cost(v, u) < r) of the 6D
-        # double integrator costs 39 binary32 operations;
-        # FMA is disabled, so each is one lane-op.  The tests are counted on the
-        # device by the build (cells outside the neighbour ball are never tested).
+        # ALU-bound binary32 work the method requires of the edge build (FMA is
+        # disabled, so every operation is one lane-op):
+        #  - one exactly evaluated Near test Cost(v, u) < r of the 6D double
+        #    integrator: 39 operations, for every pair the build tests (counted
+        #    on the device; cells outside the neighbour ball are never tested);
+        #  - per connection kept (a lower bound on the connections that pass
+        #    Near): steering setup 40, collision at the 15 interior checkpoints
+        #    15 x 19 (time and a 3-axis Horner step) plus their bounding box 90,
+        #    and the perception transfer at the 16 checkpoints 16 x 33 (Horner 19,
+        #    grid index 14): 943 operations.
         tests = sum(rm.stats()[0] for rm in arm.rms)
-        ops_per_launch = 39.0 * tests * steps / max(1, launches)
+        edges = sum(rm.E for rm in arm.rms)
+        ops_per_launch = (39.0 * tests + 943.0 * edges) * steps / max(1, launches)
         achieved = ops_per_launch / (ms / launches / 1e3) / 1e12
         sm_max = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * sm_max * 1e6 / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": _traffic(name, B * steps / max(1, launches)),
                 "traffic_unit": "DRAM bytes per launch (ncu, scaled from an 8-roadmap capture)",
-                "near_tests_per_step": tests,
+                "near_tests_per_step": tests, "edges_per_step": edges,
+                "ops_per_step": 39.0 * tests + 943.0 * edges,
                 "all_pairs_per_step": V * V * B,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
     # HBM-bound search kernels: algorithmic bytes per step
