@@ -81,6 +81,39 @@ class mpap_cert(C.Structure):
                 ("rollouts", C.c_uint32)]
 
 
+_NP_SCALAR = {C.c_int32: "i4", C.c_uint32: "u4", C.c_int64: "i8", C.c_uint64: "u8", C.c_float: "f4"}
+
+
+def _np_dtype(cls):
+    """numpy structured dtype with the byte layout of the ctypes struct `cls`
+    (pointers as uint64 addresses), so that a whole batch of structs is filled
+    column by column and handed to the library as one array."""
+    assert C.sizeof(C.c_void_p) == 8
+    names, formats, offsets = [], [], []
+    for name, ct in cls._fields_:
+        if ct in _NP_SCALAR:
+            fmt = _NP_SCALAR[ct]
+        elif issubclass(ct, C.Array):
+            fmt = (_NP_SCALAR[ct._type_], (ct._length_,))
+        else:                                   # c_void_p and POINTER(...)
+            fmt = "u8"
+        names.append(name)
+        formats.append(fmt)
+        offsets.append(getattr(cls, name).offset)
+    dt = np.dtype({"names": names, "formats": formats, "offsets": offsets, "itemsize": C.sizeof(cls)})
+    assert dt.itemsize == C.sizeof(cls)
+    return dt
+
+
+SCENE_DT, PARAMS_DT, QUERY_DT, RESULT_DT, MC_DT, CERT_DT = (
+    _np_dtype(t) for t in (mpap_scene, mpap_roadmap_params, mpap_query, mpap_result, mpap_mc_params, mpap_cert))
+
+
+def _as(a, cls):
+    """A numpy struct array as a ctypes pointer to `cls`."""
+    return a.ctypes.data_as(C.POINTER(cls))
+
+
 _lib = None
 
 
@@ -251,6 +284,16 @@ def _ptr(a, dtype):
     return arr.ctypes.data_as(C.c_void_p), arr, False
 
 
+def _addr(a, dtype):
+    """(address, keepalive, is_device, element count) for a numpy array or a torch tensor."""
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), a, bool(a.is_cuda), a.numel()
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.__array_interface__["data"][0], arr, False, arr.size
+
+
 def make_scene_struct(dim_kind, box_lo, box_hi, grid, grid_G, n_f=12, K=24):
     """An mpap_scene over numpy (host) or CUDA tensor (device) arrays."""
     lo_p, lo_k, lo_d = _ptr(box_lo, np.float32)
@@ -341,17 +384,44 @@ def _params(n, seed, r, x_init, x_goal, goal_radius, T, M, query_id):
 
 
 def _batch_structs(specs):
+    """mpap_scene and mpap_roadmap_params arrays (numpy, C layout) for a list of
+    build_roadmap keyword dicts, plus the arrays they point into."""
     n = len(specs)
-    scenes = (mpap_scene * n)()
-    params = (mpap_roadmap_params * n)()
+    scenes = np.zeros(n, SCENE_DT)
+    params = np.zeros(n, PARAMS_DT)
     keep = []
-    for i, sp in enumerate(specs):
-        sc, k = make_scene_struct(sp["dim_kind"], sp["box_lo"], sp["box_hi"], sp["grid"], sp["grid_G"],
-                                  sp.get("n_f", 12), sp.get("K", 24))
-        scenes[i] = sc
-        keep.append(k)
-        params[i] = _params(sp["n"], sp["seed"], sp["r"], sp["x_init"], sp["x_goal"], sp.get("goal_radius", 0.05),
-                            sp.get("T", 0.25), sp.get("M", 16), sp.get("query_id", 0))
+    lo, hi, gl, nb, mem = [], [], [], [], []
+    for sp in specs:
+        a_lo, k_lo, d_lo, n_lo = _addr(sp["box_lo"], np.float32)
+        a_hi, k_hi, d_hi, _ = _addr(sp["box_hi"], np.float32)
+        a_g, k_g, d_g, _ = _addr(sp["grid"], np.uint8)
+        if not (d_lo == d_hi == d_g):
+            raise ValueError("scene arrays must all be on the host or all on the device")
+        keep.append((k_lo, k_hi, k_g))
+        nb.append(n_lo // 3)
+        lo.append(a_lo if n_lo else 0)
+        hi.append(a_hi if n_lo else 0)
+        gl.append(a_g)
+        mem.append(MPAP_MEM_DEVICE if d_g else MPAP_MEM_HOST)
+    g = lambda k, d: [sp.get(k, d) for sp in specs]
+    scenes["dim_kind"] = [sp["dim_kind"] for sp in specs]
+    scenes["nb"] = nb
+    scenes["box_lo"] = lo
+    scenes["box_hi"] = hi
+    scenes["grid_G"] = [sp["grid_G"] for sp in specs]
+    scenes["grid_level"] = gl
+    scenes["n_f"] = g("n_f", 12)
+    scenes["K"] = g("K", 24)
+    scenes["mem"] = mem
+    params["n"] = [sp["n"] for sp in specs]
+    params["query_id"] = g("query_id", 0)
+    params["seed"] = [sp["seed"] for sp in specs]
+    params["r"] = [sp["r"] for sp in specs]
+    params["T_edge"] = g("T", 0.25)
+    params["M"] = g("M", 16)
+    params["x_init"] = np.asarray([sp["x_init"] for sp in specs], np.float32).reshape(n, 6)
+    params["x_goal"] = np.asarray([sp["x_goal"] for sp in specs], np.float32).reshape(n, 6)
+    params["goal_radius"] = g("goal_radius", 0.05)
     return scenes, params, keep
 
 
@@ -373,27 +443,12 @@ def build_roadmaps(specs, rms=None, stream=None):
     specs: list of dicts with the keyword arguments of build_roadmap.  rms: an
     optional list of Roadmap handles (or None entries) rebuilt in place."""
     n = len(specs)
-    scenes = (mpap_scene * n)()
-    params = (mpap_roadmap_params * n)()
-    keep = []
-    for i, sp in enumerate(specs):
-        sc, k = make_scene_struct(sp["dim_kind"], sp["box_lo"], sp["box_hi"], sp["grid"], sp["grid_G"],
-                                  sp.get("n_f", 12), sp.get("K", 24))
-        scenes[i] = sc
-        keep.append(k)
-        params[i] = _params(sp["n"], sp["seed"], sp["r"], sp["x_init"], sp["x_goal"], sp.get("goal_radius", 0.05),
-                            sp.get("T", 0.25), sp.get("M", 16), sp.get("query_id", 0))
+    scenes, params, keep = _batch_structs(specs)
     rms = list(rms) if rms is not None else [None] * n
     hs = (C.c_void_p * n)(*[rm.h.value if rm is not None and rm.h else None for rm in rms])
-    rc = lib().mpap_build_roadmaps(n, scenes, params, hs, _stream(stream))
-    out = []
-    for i in range(n):
-        if rms[i] is not None:
-            rms[i].h = C.c_void_p(hs[i]) if hs[i] else None
-            rms[i].M = specs[i].get("M", 16)
-            out.append(rms[i])
-        else:
-            out.append(Roadmap(C.c_void_p(hs[i]), specs[i].get("M", 16), specs[i].get("K", 24)) if hs[i] else None)
+    rc = lib().mpap_build_roadmaps(n, _as(scenes, mpap_scene), _as(params, mpap_roadmap_params), hs,
+                                   _stream(stream))
+    out = _adopt(specs, rms, hs)
     _check(rc, "mpap_build_roadmaps")
     return out
 
@@ -520,20 +575,28 @@ def search(ws: Workspace, rm: Roadmap, beta, lam=0.5, group_width_q=0, max_iters
     return _result(r, buf)
 
 
+def _result_array(nq, path_cap):
+    """mpap_result array (numpy, C layout) whose path pointers tile one
+    [nq, path_cap] uint32 buffer (row i receives query i's plan)."""
+    bufs = np.zeros((nq, path_cap), np.uint32)
+    rs = np.zeros(nq, RESULT_DT)
+    rs["path_cap"] = path_cap
+    rs["path"] = bufs.__array_interface__["data"][0] + 4 * path_cap * np.arange(nq, dtype=np.uint64)
+    return rs, bufs
+
+
 def search_batch(ws: Workspace, rms, queries, path_cap=4096, stream=None, check=True):
     """mpap_search_batch: independent queries in one lock-step wavefront loop."""
     nq = len(rms)
     hs = (C.c_void_p * nq)(*[rm.h for rm in rms])
     qs = (mpap_query * nq)(*queries)
-    bufs = [np.zeros(path_cap, np.uint32) for _ in range(nq)]
-    rs = (mpap_result * nq)()
-    for i in range(nq):
-        rs[i].path_cap = path_cap
-        rs[i].path = bufs[i].ctypes.data_as(C.POINTER(C.c_uint32))
-    rc = lib().mpap_search_batch(ws.h, hs, qs, nq, rs, _stream(stream))
+    rs, bufs = _result_array(nq, path_cap)
+    rc = lib().mpap_search_batch(ws.h, hs, qs, nq, _as(rs, mpap_result), _stream(stream))
     if check:
         _check(rc, "mpap_search_batch")
-    return [_result(rs[i], bufs[i]) for i in range(nq)]
+    cols = [rs[k].tolist() for k in ("status", "cost", "h", "path_len", "wavefronts", "expansions", "plans")]
+    return [SearchResult(st, c, h, bufs[i, :n].copy() if st == MPAP_OK else bufs[i, :0].copy(), w, e, pl)
+            for i, (st, c, h, n, w, e, pl) in enumerate(zip(*cols))]
 
 
 def make_mc(rollouts, seed, call_id, delta_fx, sigma_fx, shift):
@@ -566,23 +629,34 @@ def certify_noalloc(rm: Roadmap, path, rollouts, seed, call_id, delta_fx, sigma_
     return dict(hits_loc=out.hits_loc, hits_coll=out.hits_coll, hits_any=out.hits_any, rollouts=out.rollouts)
 
 
+def _mc_array(mcs):
+    """mpap_mc_params array (numpy, C layout) for (rollouts, seed, call_id,
+    delta_fx, sigma_fx, shift) tuples, plus the arrays it points into."""
+    ms = np.zeros(len(mcs), MC_DT)
+    keep = [(np.ascontiguousarray(m[4], np.int32), np.ascontiguousarray(m[5], np.int32)) for m in mcs]
+    ms["rollouts"] = [m[0] for m in mcs]
+    ms["seed"] = [m[1] for m in mcs]
+    ms["call_id"] = [m[2] for m in mcs]
+    ms["delta_fx"] = [int(m[3]) for m in mcs]
+    ms["sigma_fx"] = [k[0].__array_interface__["data"][0] for k in keep]
+    ms["shift"] = [k[1].__array_interface__["data"][0] for k in keep]
+    return ms, keep
+
+
 def certify_batch(rms, paths, mcs, stream=None):
     """mpap_certify_batch. mcs: list of (rollouts, seed, call_id, delta_fx, sigma_fx, shift)."""
     n = len(rms)
     hs = (C.c_void_p * n)(*[rm.h for rm in rms])
     arrs = [np.ascontiguousarray(p, np.uint32) if len(p) else np.zeros(1, np.uint32) for p in paths]
-    pp = (C.c_void_p * n)(*[a.ctypes.data for a in arrs])
+    pp = np.array([a.__array_interface__["data"][0] for a in arrs], np.uint64)
     lens = np.array([len(p) for p in paths], np.uint32)
-    keep = []
-    ms = (mpap_mc_params * n)()
-    for i, m in enumerate(mcs):
-        ms[i], k = make_mc(*m)
-        keep.append(k)
-    outs = (mpap_cert * n)()
-    _check(lib().mpap_certify_batch(hs, pp, lens.ctypes.data_as(C.c_void_p), ms, n, outs, _stream(stream)),
+    ms, keep = _mc_array(mcs)
+    outs = np.zeros(n, CERT_DT)
+    _check(lib().mpap_certify_batch(hs, pp.ctypes.data_as(C.POINTER(C.c_void_p)), lens.ctypes.data_as(C.c_void_p),
+                                    _as(ms, mpap_mc_params), n, _as(outs, mpap_cert), _stream(stream)),
            "mpap_certify_batch")
-    return [dict(hits_loc=o.hits_loc, hits_coll=o.hits_coll, hits_any=o.hits_any, rollouts=o.rollouts)
-            for o in outs]
+    cols = [outs[k].tolist() for k in ("hits_loc", "hits_coll", "hits_any", "rollouts")]
+    return [dict(hits_loc=a, hits_coll=b, hits_any=c, rollouts=d) for a, b, c, d in zip(*cols)]
 
 
 # ---------------------------------------------------------------------------
@@ -729,7 +803,8 @@ def autotune_build(specs, rms=None, reps=2, stream=None):
     hs = (C.c_void_p * n)(*[rm.h.value if rm is not None and rm.h else None for rm in rms])
     t = mpap_tuning()
     ms = C.c_double()
-    rc = lib().mpap_autotune_build(n, scenes, params, hs, int(reps), C.byref(t), C.byref(ms), _stream(stream))
+    rc = lib().mpap_autotune_build(n, _as(scenes, mpap_scene), _as(params, mpap_roadmap_params), hs, int(reps),
+                                   C.byref(t), C.byref(ms), _stream(stream))
     out = _adopt(specs, rms, hs)
     _check(rc, "mpap_autotune_build")
     return _tuning_dict(t), ms.value, out

@@ -200,15 +200,18 @@ int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* path
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const size_t bytes = up(b_jobs) + up(b_hits) + up(b_path) + up(b_tab) + up(b_ck);
   char* blk = nullptr;
-  MPAP_CK(cudaMallocAsync((void**)&blk, bytes, st));
+  MPAP_CK(scratch_alloc((void**)&blk, bytes, st));
+  const size_t o_hits = up(b_jobs), o_path = o_hits + up(b_hits), o_tab = o_path + up(b_path);
+  const size_t o_ck = o_tab + up(b_tab);
   McJob* d_jobs = (McJob*)blk;
-  uint32_t* d_hits = (uint32_t*)(blk + up(b_jobs));
-  uint32_t* d_path = (uint32_t*)(blk + up(b_jobs) + up(b_hits));
-  int32_t* d_tab = (int32_t*)(blk + up(b_jobs) + up(b_hits) + up(b_path));
-  int4* d_ck = (int4*)(blk + up(b_jobs) + up(b_hits) + up(b_path) + up(b_tab));
-  // host staging for paths and tables (one copy each)
-  std::vector<uint32_t> hpath(total_path + 1);
-  std::vector<int32_t> htab(total_tab + 1);
+  uint32_t* d_hits = (uint32_t*)(blk + o_hits);
+  uint32_t* d_path = (uint32_t*)(blk + o_path);
+  int32_t* d_tab = (int32_t*)(blk + o_tab);
+  int4* d_ck = (int4*)(blk + o_ck);
+  // host image of jobs | zeroed hit counters | paths | tables: one upload
+  std::vector<char> himg(o_ck, 0);
+  uint32_t* hpath = (uint32_t*)(himg.data() + o_path);
+  int32_t* htab = (int32_t*)(himg.data() + o_tab);
   size_t po = 0, to = 0, co = 0;
   for (uint32_t i = 0; i < n; ++i) {
     const int K1 = rms[i]->K + 1;
@@ -226,10 +229,8 @@ int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* path
     to += 2 * (size_t)K1;
     co += jobs[i].steps;
   }
-  MPAP_CK(cudaMemcpyAsync(d_jobs, jobs.data(), b_jobs, cudaMemcpyHostToDevice, st));
-  MPAP_CK(cudaMemcpyAsync(d_path, hpath.data(), b_path, cudaMemcpyHostToDevice, st));
-  MPAP_CK(cudaMemcpyAsync(d_tab, htab.data(), b_tab, cudaMemcpyHostToDevice, st));
-  MPAP_CK(cudaMemsetAsync(d_hits, 0, b_hits, st));
+  std::memcpy(himg.data(), jobs.data(), b_jobs);
+  MPAP_CK(cudaMemcpyAsync(blk, himg.data(), o_ck, cudaMemcpyHostToDevice, st));
   uint32_t max_steps = 0;
   for (auto& J : jobs) max_steps = max_steps > J.steps ? max_steps : J.steps;
   if (max_steps) {
@@ -249,7 +250,7 @@ int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* path
   MPAP_CK(cudaGetLastError());
   std::vector<uint32_t> hh(3 * n);
   MPAP_CK(cudaMemcpyAsync(hh.data(), d_hits, b_hits, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaFreeAsync(blk, st));
+  scratch_free(blk, st);
   MPAP_CK(cudaStreamSynchronize(st));
   for (uint32_t i = 0; i < n; ++i) {
     outs[i].hits_loc = hh[3 * i];

@@ -27,6 +27,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 #include "profile.h"
@@ -603,10 +604,12 @@ int32_t copy_in(void* dst, const void* src, size_t bytes, bool device_src, cudaS
 // memory mapped, so repeated calls of the same size do not map pages again.
 cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
   static cudaMemPool_t pools[64] = {};
+  static std::mutex mu;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+  std::lock_guard<std::mutex> g(mu);
   if (!pools[dev]) {
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
@@ -1122,7 +1125,7 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
   J.rev_peak = rm->rev_peak;
   char* blk = nullptr;
   const size_t bytes = 4096 + 8 * ((size_t)V + 1) + 1024;
-  if (!cuda_ok(cudaMallocAsync((void**)&blk, bytes, st), "cudaMallocAsync")) return bail(MPAP_ERR_CUDA);
+  if (!cuda_ok(scratch_alloc((void**)&blk, bytes, st), "scratch_alloc")) return bail(MPAP_ERR_CUDA);
   Carve cv{blk, 0};
   BuildJob* d_job = cv.take<BuildJob>(1);
   ScanSeg* d_seg = cv.take<ScanSeg>(1);
@@ -1132,10 +1135,10 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
   if (!cuda_ok(cudaMemsetAsync(J.counts, 0, 4 * ((size_t)V + 1), st), "memset") ||
       !cuda_ok(cudaMemsetAsync(J.fill, 0, 4 * ((size_t)V + 1), st), "memset") ||
       (rc = upload(d_job, &J, sizeof(J), st)) || (rc = build_reverse(1, hj, d_job, d_seg, V, st))) {
-    cudaFreeAsync(blk, st);
+    scratch_free(blk, st);
     return bail(rc ? rc : MPAP_ERR_CUDA);
   }
-  cudaFreeAsync(blk, st);
+  scratch_free(blk, st);
   if (!cuda_ok(cudaStreamSynchronize(st), "sync")) return bail(MPAP_ERR_CUDA);
   *out = rm;
   return MPAP_OK;

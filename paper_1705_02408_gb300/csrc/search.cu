@@ -160,6 +160,12 @@ struct mpap_workspace {
   std::vector<uint32_t> last_V, last_base;
   uint32_t last_max_front = 0;
   unsigned long long last_pool_used = 0;
+  // pinned host staging of the results (grown on demand): per-query results,
+  // states and the loop control block; the plans' node lists
+  char* h_hdr = nullptr;
+  size_t h_hdr_bytes = 0;
+  char* h_path = nullptr;
+  size_t h_path_bytes = 0;
 };
 
 namespace mpap {
@@ -1629,8 +1635,32 @@ void workspace_free(mpap_workspace* ws) {
                   w.oh_stamp, w.g_cost, w.g_h, w.g_pid, w.oh_list, w.t_list, w.b_list,
                   w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl, w.qd, w.qs, w.res, w.path};
   for (void* p : ptrs) cudaFree(p);
+  if (ws->h_hdr) cudaFreeHost(ws->h_hdr);
+  if (ws->h_path) cudaFreeHost(ws->h_path);
   delete ws;
 }
+
+namespace {
+
+// Pinned host buffer of at least `bytes`, reallocated (contents dropped) when it
+// is too small.  Called only when no copy into it is in flight.
+int32_t host_stage(char** buf, size_t* have, size_t bytes) {
+  if (*have >= bytes) return MPAP_OK;
+  if (*buf) cudaFreeHost(*buf);
+  *buf = nullptr;
+  *have = 0;
+  const size_t want = std::max<size_t>(bytes, 64u << 10);
+  if (!cuda_ok(cudaMallocHost(reinterpret_cast<void**>(buf), want), "cudaMallocHost")) {
+    *buf = nullptr;
+    return MPAP_ERR_CUDA;
+  }
+  *have = want;
+  return MPAP_OK;
+}
+
+constexpr size_t align64(size_t b) { return (b + 63) & ~(size_t)63; }
+
+}  // namespace
 
 // Tuning key of a batch: the common dimension (0 if mixed) and the largest V.
 void batch_key(mpap_roadmap* const* rms, uint32_t nq, int& dim, uint32_t& V) {
@@ -1764,12 +1794,16 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     k_finalize<<<nq, 256, 0, st>>>(w, nq);
   }
   MPAP_CK(cudaGetLastError());
-  std::vector<ResultDev> res(nq);
-  std::vector<QueryState> qsh(nq);
-  Ctl hc;
-  MPAP_CK(cudaMemcpyAsync(res.data(), w.res, sizeof(ResultDev) * nq, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaMemcpyAsync(qsh.data(), w.qs, sizeof(QueryState) * nq, cudaMemcpyDeviceToHost, st));
-  MPAP_CK(cudaMemcpyAsync(&hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  // results, query states and the control block: three copies into pinned staging
+  const size_t o_qs = align64(sizeof(ResultDev) * nq), o_ctl = o_qs + align64(sizeof(QueryState) * nq);
+  rc = host_stage(&ws->h_hdr, &ws->h_hdr_bytes, o_ctl + sizeof(Ctl));
+  if (rc) return rc;
+  const ResultDev* res = reinterpret_cast<const ResultDev*>(ws->h_hdr);
+  const QueryState* qsh = reinterpret_cast<const QueryState*>(ws->h_hdr + o_qs);
+  const Ctl& hc = *reinterpret_cast<const Ctl*>(ws->h_hdr + o_ctl);
+  MPAP_CK(cudaMemcpyAsync(ws->h_hdr, w.res, sizeof(ResultDev) * nq, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaMemcpyAsync(ws->h_hdr + o_qs, w.qs, sizeof(QueryState) * nq, cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaMemcpyAsync(ws->h_hdr + o_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaStreamSynchronize(st));
   ws->last_max_front = hc.max_front;
   launch_count_add(4ull * hc.it);
@@ -1778,6 +1812,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     for (int k = 0; k < 4; ++k) profile_add(names[k], hc.kt[k].launches, (double)hc.kt[k].total_ns * 1e-6);
   }
   rc = MPAP_OK;
+  uint32_t lmax = 0;     // longest plan to return
   for (uint32_t i = 0; i < nq; ++i) {
     mpap_result& o = outs[i];
     o.status = res[i].status;
@@ -1789,15 +1824,27 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     o.path_len = res[i].path_len;
     if (o.status == MPAP_OK) {
       if (o.path && o.path_cap >= o.path_len) {
-        MPAP_CK(cudaMemcpyAsync(o.path, w.path + (size_t)i * w.path_cap, 4 * (size_t)o.path_len,
-                                cudaMemcpyDeviceToHost, st));
+        lmax = std::max(lmax, o.path_len);
       } else if (o.path_cap < o.path_len) {
         o.status = MPAP_ERR_INVALID_ARG;
       }
     }
     if (o.status < 0 && rc == MPAP_OK) rc = o.status;
   }
-  MPAP_CK(cudaStreamSynchronize(st));
+  if (lmax) {
+    // the first lmax entries of every query's plan row in one strided copy
+    const int32_t r2 = host_stage(&ws->h_path, &ws->h_path_bytes, 4 * (size_t)nq * lmax);
+    if (r2) return r2;
+    MPAP_CK(cudaMemcpy2DAsync(ws->h_path, 4 * (size_t)lmax, w.path, 4 * (size_t)w.path_cap, 4 * (size_t)lmax, nq,
+                              cudaMemcpyDeviceToHost, st));
+    MPAP_CK(cudaStreamSynchronize(st));
+    const uint32_t* hp = reinterpret_cast<const uint32_t*>(ws->h_path);
+    for (uint32_t i = 0; i < nq; ++i) {
+      mpap_result& o = outs[i];
+      if (o.status == MPAP_OK && o.path && o.path_len)
+        std::memcpy(o.path, hp + (size_t)i * lmax, 4 * (size_t)o.path_len);
+    }
+  }
   {
     unsigned long long used = 0;
     for (uint32_t i = 0; i < nq; ++i) used += std::min<unsigned long long>(qsh[i].pool_n, qd[i].pool_cap);
