@@ -218,6 +218,14 @@ int32_t mpap_roadmap_export(const mpap_roadmap* rm, float* x, uint8_t* is_goal, 
  * heuristic; used by the interior check of Eq. 2). */
 int32_t mpap_roadmap_export_peaks(const mpap_roadmap* rm, int32_t* Smax, int32_t* Cmax, void* stream);
 
+/* Copies the reverse CSR the search reads (in-edges of every node, Alg. 3's
+ * predecessor sets) to host arrays (any pointer may be NULL): rev_ptr[V+1];
+ * src, cost_q, S, C, Smax, Cmax [E] with every row sorted by source.  Row u
+ * holds one record per forward edge (v -> u) with that edge's fields, so it is
+ * the transpose of mpap_roadmap_export.  Synchronises the stream. */
+int32_t mpap_roadmap_export_reverse(const mpap_roadmap* rm, uint32_t* rev_ptr, uint32_t* src, int32_t* cost_q,
+                                    int32_t* S, int32_t* C, int32_t* Smax, int32_t* Cmax, void* stream);
+
 /* Build statistics: Near tests (Cost < r evaluations) performed by the last
  * build of this roadmap, and the number of nodes in X_goal. */
 int32_t mpap_roadmap_stats(const mpap_roadmap* rm, uint64_t* near_tests, uint32_t* n_goal);

@@ -38,7 +38,7 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_mlp_forward", "mpap_mlp_train_step", "mpap_tuning_get", "mpap_tuning_set",
            "mpap_tuning_clear", "mpap_tuning_export", "mpap_autotune_build", "mpap_autotune_search",
            "mpap_search_candidates_batch", "mpap_plan_features_batch", "mpap_roadmap_from_csr_peaks",
-           "mpap_roadmap_export_peaks"]
+           "mpap_roadmap_export_peaks", "mpap_roadmap_export_reverse"]
 
 
 class mpap_scene(C.Structure):
@@ -181,6 +181,8 @@ def lib():
         L.mpap_roadmap_from_csr_peaks.argtypes = [C.c_uint32, P, P, P, P, P, P, P, P, C.POINTER(P), P]
         L.mpap_roadmap_export_peaks.restype = i32
         L.mpap_roadmap_export_peaks.argtypes = [P, P, P, P]
+        L.mpap_roadmap_export_reverse.restype = i32
+        L.mpap_roadmap_export_reverse.argtypes = [P, P, P, P, P, P, P, P, P]
         L.mpap_search_candidates_batch.restype = i32
         L.mpap_search_candidates_batch.argtypes = [P, C.c_uint32, C.c_uint32, P, P, P, P, C.c_uint32, P, P, P]
         L.mpap_plan_features_batch.restype = i32
@@ -351,6 +353,17 @@ class Roadmap:
                                          _stream(stream)), "mpap_roadmap_export")
         return dict(V=V, E=E, x=x.reshape(6, V), is_goal=g, row_ptr=rp, dst=dst[:E], cost_q=cq[:E],
                     S=S[:E], C=Cc[:E])
+
+    def export_reverse(self, stream=None):
+        """mpap_roadmap_export_reverse: the in-edge CSR, rows sorted by source."""
+        V, E = self.info()
+        rp = np.zeros(V + 1, np.uint32)
+        cols = [np.zeros(max(E, 1), t) for t in (np.uint32, np.int32, np.int32, np.int32, np.int32, np.int32)]
+        vp = lambda a: a.ctypes.data_as(C.c_void_p)
+        _check(lib().mpap_roadmap_export_reverse(self.h, vp(rp), *[vp(c) for c in cols], _stream(stream)),
+               "mpap_roadmap_export_reverse")
+        src, cq, S, Cc, Sm, Cm = (c[:E] for c in cols)
+        return dict(V=V, E=E, rev_ptr=rp, src=src, cost_q=cq, S=S, C=Cc, Smax=Sm, Cmax=Cm)
 
     def peaks(self, stream=None):
         """(Smax, Cmax) per edge, in the order of export()."""

@@ -268,6 +268,42 @@ int32_t mpap_roadmap_export_peaks(const mpap_roadmap* rm, int32_t* Smax, int32_t
   return MPAP_OK;
 }
 
+int32_t mpap_roadmap_export_reverse(const mpap_roadmap* rm, uint32_t* rev_ptr, uint32_t* src, int32_t* cost_q,
+                                    int32_t* Sv, int32_t* C, int32_t* Smax, int32_t* Cmax, void* stream) {
+  if (!rm) {
+    set_error("null roadmap");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = S(stream);
+  const size_t E = (size_t)rm->E;
+  std::vector<int4> ed(E ? E : 1);
+  std::vector<int2> pk(E ? E : 1);
+  std::vector<uint32_t> rp((size_t)rm->V + 1);
+  if (E) {
+    MPAP_CK(cudaMemcpyAsync(ed.data(), rm->rev_edge, sizeof(int4) * E, cudaMemcpyDeviceToHost, st));
+    MPAP_CK(cudaMemcpyAsync(pk.data(), rm->rev_peak, sizeof(int2) * E, cudaMemcpyDeviceToHost, st));
+  }
+  MPAP_CK(cudaMemcpyAsync(rp.data(), rm->rev_ptr, 4 * ((size_t)rm->V + 1), cudaMemcpyDeviceToHost, st));
+  MPAP_CK(cudaStreamSynchronize(st));
+  // device rows are in arrival order; return them sorted by source
+  std::vector<uint32_t> idx(E ? E : 1);
+  for (size_t e = 0; e < E; ++e) idx[e] = (uint32_t)e;
+  for (uint32_t v = 0; v < rm->V; ++v)
+    std::sort(idx.begin() + rp[v], idx.begin() + rp[v + 1],
+              [&](uint32_t a, uint32_t b) { return ed[a].x < ed[b].x; });
+  if (rev_ptr) std::memcpy(rev_ptr, rp.data(), 4 * ((size_t)rm->V + 1));
+  for (size_t e = 0; e < E; ++e) {
+    const int4& r = ed[idx[e]];
+    if (src) src[e] = (uint32_t)r.x;
+    if (cost_q) cost_q[e] = r.y;
+    if (Sv) Sv[e] = r.z;
+    if (C) C[e] = r.w;
+    if (Smax) Smax[e] = pk[idx[e]].x;
+    if (Cmax) Cmax[e] = pk[idx[e]].y;
+  }
+  return MPAP_OK;
+}
+
 int32_t mpap_roadmap_info(const mpap_roadmap* rm, uint32_t* V, uint64_t* E) {
   if (!rm) {
     set_error("null roadmap");

@@ -104,7 +104,8 @@ struct BuildJob {
   unsigned long long* near_tests;  // evaluated Cost(v, u) < r tests
   float* sx;               // [6][V] states in cell order
   uint32_t* counts;        // [V+1]
-  uint32_t* fill;          // [V+1]
+  uint32_t* indeg;         // [V+1] in-degrees, counted by the one-pass edge build
+  uint32_t* fill;          // [V+1] reverse-row cursors
   int4* rows;              // [V][kRowCap] per-source edge rows of the one-pass build
   int2* rows_peak;         // [V][kRowCap] their transfer peaks {Smax, Cmax}
   uint32_t* ovf;           // [V] sources with more than kRowCap edges (count in status[3])
@@ -350,6 +351,7 @@ __device__ __forceinline__ void edge_flush(const BuildJob& J, uint32_t v, const 
     ok = !conn_collides_t<DIM>(g, cn, s_lo, s_hi);
   }
   const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
+  if (MODE == kRow && ok) atomicAdd(&J.indeg[u], 1u);
   if (ok) {
     const uint32_t rank = running + __popc(bal & ((1u << lane) - 1u));
     if (MODE == kFillCsr || rank < kRowCap) {
@@ -364,6 +366,9 @@ __device__ __forceinline__ void edge_flush(const BuildJob& J, uint32_t v, const 
         J.fwd_edge[out_base + rank] = rec;
         J.fwd_dst[out_base + rank] = u;
         J.fwd_peak[out_base + rank] = pk;
+        const uint32_t pos = J.rev_ptr[u] + atomicAdd(&J.fill[u], 1u);
+        J.rev_edge[pos] = make_int4((int)v, rec.y, rec.z, rec.w);
+        J.rev_peak[pos] = pk;
       } else {
         J.rows[(size_t)v * kRowCap + rank] = rec;
         J.rows_peak[(size_t)v * kRowCap + rank] = pk;
@@ -503,8 +508,10 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges(const BuildJob
 }
 
 // One-pass build: copy each source's scratch row (at most kRowCap edges) into
-// the CSR (warp per source).  Rows stay in discovery order: no kernel depends on
-// the order of a row, and mpap_roadmap_export returns rows sorted by neighbour.
+// the forward CSR and scatter its edges into the reverse CSR (row pointers from
+// the in-degrees the edge pass counted), one warp per source.  Rows stay in
+// discovery (forward) or arrival (reverse) order: no kernel depends on the order
+// of a row, and mpap_roadmap_export returns rows sorted by neighbour.
 __global__ void k_compact_rows(const BuildJob* __restrict__ jobs) {
   const BuildJob& J = jobs[blockIdx.y];
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -515,9 +522,13 @@ __global__ void k_compact_rows(const BuildJob* __restrict__ jobs) {
     const int2* srcp = J.rows_peak + (size_t)v * kRowCap;
     for (uint32_t i = lane_id(); i < len; i += 32) {
       const int4 e = src[i];
+      const int2 pk = srcp[i];
       J.fwd_edge[b + i] = e;
       J.fwd_dst[b + i] = (uint32_t)e.x;
-      J.fwd_peak[b + i] = srcp[i];
+      J.fwd_peak[b + i] = pk;
+      const uint32_t pos = J.rev_ptr[e.x] + atomicAdd(&J.fill[e.x], 1u);
+      J.rev_edge[pos] = make_int4((int)v, e.y, e.z, e.w);
+      J.rev_peak[pos] = pk;
     }
   }
 }
@@ -874,18 +885,22 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     max_nb = std::max(max_nb, rm->nb);
   }
   // 2. one scratch block; the regions that must start at zero come first
-  size_t bytes = 256 * 8 + (sizeof(ScanSeg) + sizeof(BuildJob) + 48) * (size_t)n + 256 * (size_t)n;
+  size_t bytes = 256 * 8 + (2 * sizeof(ScanSeg) + sizeof(BuildJob) + 48) * (size_t)n + 256 * (size_t)n;
   for (uint32_t j = 0; j < n; ++j)
     bytes += 256 * 13 + 4 * (ncells[j] + 1) + 16 + 32 * (cand_cap[j] + 1) + 4 * (ncells[j] + 1) +
-             48 * ((size_t)hj[j].V + 1) + (sizeof(int4) + sizeof(int2)) * kRowCap * (size_t)hj[j].V + 768;
+             52 * ((size_t)hj[j].V + 1) + (sizeof(int4) + sizeof(int2)) * kRowCap * (size_t)hj[j].V + 1024;
   MPAP_CK(scratch_alloc((void**)&blk, bytes, st));
   Carve cv{blk, 0};
   for (uint32_t j = 0; j < n; ++j) hj[j].cell_cnt = cv.take<uint32_t>(ncells[j] + 1);
   for (uint32_t j = 0; j < n; ++j) hj[j].status = cv.take<uint32_t>(4);
   for (uint32_t j = 0; j < n; ++j) hj[j].near_tests = cv.take<unsigned long long>(1);
+  for (uint32_t j = 0; j < n; ++j) {
+    hj[j].indeg = cv.take<uint32_t>((size_t)hj[j].V + 1);
+    hj[j].fill = cv.take<uint32_t>((size_t)hj[j].V + 1);
+  }
   const size_t zero_bytes = cv.off;
   BuildJob* d_jobs = cv.take<BuildJob>(n);
-  ScanSeg* d_seg = cv.take<ScanSeg>(n);
+  ScanSeg* d_seg = cv.take<ScanSeg>(2 * (size_t)n);
   uint32_t* d_gather = cv.take<uint32_t>(8 * (size_t)n);
   uint32_t* d_ids = cv.take<uint32_t>(n);
   for (uint32_t j = 0; j < n; ++j) {
@@ -898,7 +913,6 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     J.sorted = cv.take<uint32_t>(J.V);
     J.sx = cv.take<float>(6 * (size_t)J.V);
     J.counts = cv.take<uint32_t>((size_t)J.V + 1);
-    J.fill = cv.take<uint32_t>((size_t)J.V + 1);
     J.rows = cv.take<int4>(kRowCap * (size_t)J.V);
     J.rows_peak = cv.take<int2>(kRowCap * (size_t)J.V);
     J.ovf = cv.take<uint32_t>((size_t)J.V);
@@ -1028,13 +1042,18 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
       else launch_edges<kFillCsr>(dims[di], warps, vmax, cnt, box_smem, st, d_jobs, d_ids + id_off[di]);
     }
   };
-  // one pass: every source's edges into its scratch row, with exact counts
+  // one pass: every source's edges into its scratch row, with exact out- and
+  // in-degrees; forward and reverse row pointers in one scan launch
   edges_pass(kRow);
-  for (uint32_t j = 0; j < n; ++j) segs[j] = ScanSeg{hj[j].counts, hj[j].fwd_ptr, hj[j].V, hj[j].status + 2};
-  MPAP_BTRY(upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st));
+  segs.resize(2 * (size_t)n);
+  for (uint32_t j = 0; j < n; ++j) {
+    segs[j] = ScanSeg{hj[j].counts, hj[j].fwd_ptr, hj[j].V, hj[j].status + 2};
+    segs[n + j] = ScanSeg{hj[j].indeg, hj[j].rev_ptr, hj[j].V, hj[j].status + 2};
+  }
+  MPAP_BTRY(upload(d_seg, segs.data(), sizeof(ScanSeg) * 2 * n, st));
   {
     LaunchScope ls(st, "k_scan_segments");
-    k_scan_segments<<<n, 1024, 0, st>>>(d_seg);
+    k_scan_segments<<<2 * n, 1024, 0, st>>>(d_seg);
   }
   MPAP_BTRY(gather());
   bool row_overflow = false;
@@ -1060,13 +1079,8 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     k_compact_rows<<<gridw, 256, 0, st>>>(d_jobs);
   }
   // sources with more than kRowCap neighbours: second pass over those only
+  // (forward and reverse records)
   if (row_overflow) edges_pass(kFillCsr);
-  // 6. reverse CSR
-  for (uint32_t j = 0; j < n; ++j) {
-    MPAP_CK(cudaMemsetAsync(hj[j].counts, 0, 4 * ((size_t)hj[j].V + 1), st));
-    MPAP_CK(cudaMemsetAsync(hj[j].fill, 0, 4 * ((size_t)hj[j].V + 1), st));
-  }
-  MPAP_BTRY(build_reverse(n, hj, d_jobs, d_seg, Vmax, st));
   MPAP_BTRY(gather());
   scratch_free(blk, st);
   blk = nullptr;

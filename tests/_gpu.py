@@ -39,3 +39,23 @@ def assert_same_search(res_gpu, res_orc, ws=None, index=0, fronts=True):
 
 def scene_beta(orc, rm_orc):
     return orc.beta_percentile(rm_orc)
+
+
+def assert_reverse_is_transpose(rm):
+    """The reverse CSR on the device (in-edges, read by the search's pull step)
+    holds exactly one record per forward edge, with its fields: the transpose of
+    the forward CSR."""
+    f = rm.export()
+    Smax, Cmax = rm.peaks()
+    r = rm.export_reverse()
+    V, E = f["V"], f["E"]
+    assert r["E"] == E
+    src = np.repeat(np.arange(V, dtype=np.uint32), np.diff(f["row_ptr"]).astype(np.int64))
+    dst = f["dst"]
+    order = np.lexsort((src, dst))
+    want_ptr = np.zeros(V + 1, np.uint32)
+    np.cumsum(np.bincount(dst, minlength=V), out=want_ptr[1:])
+    np.testing.assert_array_equal(r["rev_ptr"], want_ptr)
+    np.testing.assert_array_equal(r["src"], src[order])
+    for k, a in (("cost_q", f["cost_q"]), ("S", f["S"]), ("C", f["C"]), ("Smax", Smax), ("Cmax", Cmax)):
+        np.testing.assert_array_equal(r[k], a[order], err_msg=k)

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import scenegen
-from _gpu import assert_same_graph
+from _gpu import assert_reverse_is_transpose, assert_same_graph
 
 pytestmark = pytest.mark.gpu
 
@@ -29,6 +29,7 @@ def test_roadmap_matches_oracle(mp, orc, name, seed, n, r):
     rg = mp.build_roadmap_for_scene(sc, n=n, r=r)
     ro = orc.build_roadmap(sc, n=n, r=r)
     assert_same_graph(rg.export(), ro.graph())
+    assert_reverse_is_transpose(rg)
 
 
 def test_roadmap_device_inputs(mp, orc):
@@ -58,9 +59,11 @@ def test_roadmap_edge_cases(mp, orc):
         rg = mp.build_roadmap_for_scene(sc, n=n, r=0.3)
         ro = orc.build_roadmap(sc, n=n, r=0.3)
         assert_same_graph(rg.export(), ro.graph())
+        assert_reverse_is_transpose(rg)
     # radius too small for any edge
     rg = mp.build_roadmap_for_scene(sc, n=50, r=1e-6)
     assert rg.E == 0
+    assert_reverse_is_transpose(rg)
 
 
 def test_roadmap_full_size_6d(mp, orc):
@@ -70,6 +73,7 @@ def test_roadmap_full_size_6d(mp, orc):
     rg = mp.build_roadmap_for_scene(sc)
     ro = orc.build_roadmap(sc)
     assert_same_graph(rg.export(), ro.graph())
+    assert_reverse_is_transpose(rg)
 
 
 def test_batched_build_and_handle_reuse(mp, orc):
@@ -84,3 +88,14 @@ def test_batched_build_and_handle_reuse(mp, orc):
         rms = mp.build_roadmaps(specs, rms=rms)
         for sc, rg, (_, _, n, r) in zip(scenes, rms, batch):
             assert_same_graph(rg.export(), orc.build_roadmap(sc, n=n, r=r).graph())
+            assert_reverse_is_transpose(rg)
+
+
+def test_reverse_csr_of_a_given_graph(mp, orc):
+    """mpap_roadmap_from_csr derives the reverse CSR with its own kernels
+    (in-degree count, scan, fill): also the exact transpose."""
+    from _search_ref import random_graph
+    rng = np.random.default_rng(77)
+    for V in (1, 5, 40, 300):
+        g = random_graph(rng, V, p_edge=0.3 if V < 100 else 0.05, dmax=4)
+        assert_reverse_is_transpose(mp.roadmap_from_csr(*g))
