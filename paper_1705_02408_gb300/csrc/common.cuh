@@ -26,6 +26,7 @@ constexpr uint32_t kErrGroup = 4u;
 constexpr uint32_t kErrList = 8u;
 constexpr uint32_t kErrEdge = 16u;
 constexpr uint32_t kErrPath = 32u;
+constexpr uint32_t kErrLevel = 64u;     // a quality level above K (MPAP_ERR_INVALID_ARG)
 
 constexpr float kTwo24 = 16777216.0f;
 constexpr float kTwo20 = 1048576.0f;
@@ -47,6 +48,9 @@ struct Geom {
   float c1, c2, c3, e1, e2, inv6, dtm;
   float invM;             // 1 / M
   int64_t Tq;             // round(T 2^24)
+  // 1 when M inc max(n_f, K - n_f) < 2^31 for every edge's increment inc (levels
+  // 0..K): the transfer's partial sums then fit 32-bit integers exactly
+  int narrow;
 };
 
 // ---------------------------------------------------------------------------
@@ -313,16 +317,16 @@ __device__ __forceinline__ int64_t quantise_cost(float cost) {
 // steps the heuristic is max(C_m, h + S_m), so its peak along the edge (the "for
 // all t" form of Eq. 2) is max(Cmax, h + Smax) with Smax = max_m S_m and
 // Cmax = max_m C_m.
-template <int DIM>
-__device__ __forceinline__ void conn_transfer_t(const Geom& g, const Conn& c, int64_t cost_q, int64_t& S,
+template <typename I, int DIM>
+__device__ __forceinline__ void conn_transfer_i(const Geom& g, const Conn& c, int64_t cost_q, int64_t& S,
                                                 int64_t& C, int64_t& Smax, int64_t& Cmax) {
   constexpr int DP = (DIM == 2) ? 2 : 3;
-  const int64_t inc = (DIM == 6) ? g.Tq : cost_q;
-  int64_t s = 0, h = 0, smax = INT64_MIN, cmax = 0;
+  const I inc = (I)((DIM == 6) ? g.Tq : cost_q);
+  I s = 0, h = 0, smax = (sizeof(I) == 4) ? (I)INT32_MIN : (I)INT64_MIN, cmax = 0;
   for (int m = 1; m <= g.M; ++m) {
     float p[3];
     conn_point_t<DIM>(g, c, m, p);
-    const int64_t dm = inc * (int64_t)(g.n_f - level_at_t<DP>(g, p));
+    const I dm = inc * (I)(g.n_f - level_at_t<DP>(g, p));
     s += dm;
     h += dm;
     h = h < 0 ? 0 : h;
@@ -331,8 +335,17 @@ __device__ __forceinline__ void conn_transfer_t(const Geom& g, const Conn& c, in
   }
   S = s;
   C = h;
-  Smax = g.M > 0 ? smax : 0;
+  Smax = g.M > 0 ? (int64_t)smax : 0;
   Cmax = cmax;
+}
+
+// 32-bit partial sums where Geom::narrow proves them exact, 64-bit otherwise
+// (the same values either way).
+template <int DIM>
+__device__ __forceinline__ void conn_transfer_t(const Geom& g, const Conn& c, int64_t cost_q, int64_t& S,
+                                                int64_t& C, int64_t& Smax, int64_t& Cmax) {
+  if (g.narrow) conn_transfer_i<int32_t, DIM>(g, c, cost_q, S, C, Smax, Cmax);
+  else conn_transfer_i<int64_t, DIM>(g, c, cost_q, S, C, Smax, Cmax);
 }
 
 // ---------------------------------------------------------------------------

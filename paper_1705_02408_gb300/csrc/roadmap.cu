@@ -117,6 +117,7 @@ struct BuildJob {
   int2* fwd_peak;
   int2* rev_peak;
   uint32_t* status;        // [4]: error bits, n_goal, scan overflow, overflowing sources
+  int K;                   // top quality level
 };
 
 struct ScanSeg {
@@ -255,6 +256,18 @@ __global__ void k_gather_status(const BuildJob* __restrict__ jobs, uint32_t njob
   out[6 * j + 5] = J.status[3];
   out[6 * n_jobs_pad + 2 * j] = (uint32_t)(*J.near_tests);
   out[6 * n_jobs_pad + 2 * j + 1] = (uint32_t)(*J.near_tests >> 32);
+}
+
+// Quality levels must lie in 0..K (Sec. 4.1 heuristic; the certification tables
+// have K + 1 entries): a larger level sets an error bit.
+__global__ void k_check_levels(const BuildJob* __restrict__ jobs) {
+  const BuildJob& J = jobs[blockIdx.y];
+  const uint32_t G = (uint32_t)J.g.G;
+  const uint32_t cells = (J.g.dp == 2) ? G * G : G * G * G;
+  bool bad = false;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += gridDim.x * blockDim.x)
+    bad = bad || (int)J.g.grid[i] > J.K;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&J.status[0], kErrLevel);
 }
 
 // X_goal: nodes within goal_radius (position) of node 1.
@@ -405,6 +418,9 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges(const BuildJob
     v = J.ovf[slot];
   } else if (v >= J.V) {
     return;
+  } else {
+    // sources in cell order: the warps of a block scan overlapping neighbourhoods
+    v = J.sorted[slot];
   }
   const uint32_t V = J.V;
   float a[6] = {0, 0, 0, 0, 0, 0};
@@ -822,6 +838,7 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   std::vector<size_t> cand_cap(n), ncells(n);
   uint32_t Vmax = 0;
   int max_nb = 0;
+  size_t max_qcells = 0;
   // 1. handles, buffers, scene copies, job constants
   for (uint32_t j = 0; j < n; ++j) {
     const BuildSpec& sp = specs[j];
@@ -858,9 +875,18 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     rm->geom.box_lo = rm->box_lo;
     rm->geom.box_hi = rm->box_hi;
     rm->geom.grid = rm->grid;
+    {
+      // 32-bit transfer sums are exact when M inc max(n_f, K - n_f) < 2^31, inc
+      // = Tq (6D) or an edge's quantised cost (< r 2^24, 2D/3D)
+      const double lmax = std::max((double)rm->n_f, (double)rm->K - (double)rm->n_f);
+      const double inc_max = (rm->dim == 6) ? (double)rm->geom.Tq : std::ceil((double)sp.r * 16777216.0) + 1.0;
+      rm->geom.narrow = ((double)sp.M * inc_max * lmax < 2147483647.0) ? 1 : 0;
+    }
+    max_qcells = std::max(max_qcells, cells);
     BuildJob& J = hj[j];
     std::memset(&J, 0, sizeof(J));
     J.g = rm->geom;
+    J.K = rm->K;
     J.x = rm->x;
     J.V = V;
     J.n = sp.points ? 0u : sp.params->n;
@@ -991,7 +1017,11 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   }
   MPAP_BTRY(upload(d_jobs, hj.data(), sizeof(BuildJob) * n, st));
 
-  // 4. goal region and spatial binning
+  // 4. level check, goal region and spatial binning
+  {
+    LaunchScope ls(st, "k_check_levels");
+    k_check_levels<<<dim3((uint32_t)std::min<size_t>((max_qcells + 255) / 256, 2u * sms), n), 256, 0, st>>>(d_jobs);
+  }
   const dim3 gridv(std::min<uint32_t>((Vmax + 255) / 256, 2u * sms), n);
   {
     LaunchScope ls(st, "k_mark_goal");
@@ -1087,6 +1117,10 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   for (uint32_t j = 0; j < n; ++j) {
     rms[j]->n_goal = hg[6 * j + 3];
     rms[j]->near_tests = (uint64_t)hg[6 * n + 2 * j] | ((uint64_t)hg[6 * n + 2 * j + 1] << 32);
+    if (hg[6 * j + 2] & kErrLevel) {
+      set_error("roadmap %u: a quality level of the grid exceeds K = %d", j, rms[j]->K);
+      return fail(MPAP_ERR_INVALID_ARG);
+    }
     if (hg[6 * j + 2]) {
       set_error("roadmap %u: an edge cost or transfer does not fit int32", j);
       return fail(MPAP_ERR_CAPACITY);

@@ -99,3 +99,49 @@ def test_reverse_csr_of_a_given_graph(mp, orc):
     for V in (1, 5, 40, 300):
         g = random_graph(rng, V, p_edge=0.3 if V < 100 else 0.05, dmax=4)
         assert_reverse_is_transpose(mp.roadmap_from_csr(*g))
+
+
+@pytest.mark.parametrize("name,seed,n,r,M", [
+    # M inc max(n_f, K - n_f) >= 2^31: 64-bit transfer sums
+    ("6d", 1, 1200, None, 44),    # one edge's S is exactly -2^31
+    ("6d", 2, 1200, None, 44),
+    ("2d", 2, 800, 0.3, 40),      # transfers up to 2.04e9
+    # below the bound: 32-bit sums
+    ("3d", 3, 1200, None, 8),
+    ("6d", 3, 1200, None, 16),
+])
+def test_transfer_sums_both_widths(mp, orc, name, seed, n, r, M):
+    """The per-edge transfer runs in 32-bit integers only where its partial sums
+    provably fit; either width gives the oracle's 64-bit values, up to the int32
+    limits of the stored fields."""
+    sc = scenegen.make_scene(name, seed, query_id=seed)
+    rg = mp.build_roadmap_for_scene(sc, n=n, r=r, M=M)
+    g = orc.build_roadmap(sc, n=n, r=r, M=M).graph()
+    assert_same_graph(rg.export(), g)
+    np.testing.assert_array_equal(np.stack(rg.peaks()), np.stack([g.Smax, g.Cmax]))
+
+
+@pytest.mark.parametrize("name,seed,n,r,M", [("6d", 4, 1200, None, 44), ("2d", 2, 800, 0.3, 64)])
+def test_transfer_beyond_int32_fails_like_the_oracle(mp, orc, name, seed, n, r, M):
+    """An edge whose transfer does not fit the int32 fields fails the build
+    (MPAP_ERR_CAPACITY) exactly where the oracle's construction fails."""
+    sc = scenegen.make_scene(name, seed, query_id=seed)
+    with pytest.raises(RuntimeError):
+        orc.build_roadmap(sc, n=n, r=r, M=M)
+    with pytest.raises(mp.MpapError) as e:
+        mp.build_roadmap_for_scene(sc, n=n, r=r, M=M)
+    assert e.value.status == mp.MPAP_ERR_CAPACITY
+
+
+def test_level_above_K_is_rejected(mp):
+    """Quality levels lie in 0..K: a grid cell at K + 1 fails the build with
+    MPAP_ERR_INVALID_ARG; the top level K itself is accepted."""
+    sc = scenegen.make_scene("6d", 3, query_id=3)
+    K = 24
+    sc.grid = sc.grid.copy()
+    sc.grid.reshape(-1)[777] = K
+    mp.build_roadmap_for_scene(sc, n=300)
+    sc.grid.reshape(-1)[777] = K + 1
+    with pytest.raises(mp.MpapError) as e:
+        mp.build_roadmap_for_scene(sc, n=300)
+    assert e.value.status == mp.MPAP_ERR_INVALID_ARG
