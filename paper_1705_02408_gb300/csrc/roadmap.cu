@@ -103,7 +103,7 @@ struct BuildJob {
   uint32_t* pos_of;        // [V] position of each node in cell order
   unsigned long long* near_tests;  // evaluated Cost(v, u) < r tests
   float* sx;               // [6][V] states in cell order
-  uint32_t* counts;        // [V+1]
+  uint32_t* counts;        // [V+1] out-degrees, counted by the row pass
   uint32_t* indeg;         // [V+1] in-degrees, counted by the one-pass edge build
   uint32_t* fill;          // [V+1] reverse-row cursors
   int4* rows;              // [V][kRowCap] per-source edge rows of the one-pass build
@@ -328,14 +328,12 @@ __global__ void k_bin_scatter(const BuildJob* __restrict__ jobs) {
 }
 
 // ---------------------------------------------------------------------------
-// Near + Collision + transfer.  One warp per source node v.  The warp walks the
-// runs of grid cells (contiguous x-ranges) that meet the source's neighbour ball,
-// flattened across up to 32 runs at a time, one candidate per lane, and
-// evaluates Cost(v, u) exactly.  Pairs with Cost < r are queued in shared memory;
-// every 32 queued pairs are checked for collision (and, in the fill pass, given
-// their quantised cost and max-plus transfer (S, C)) one per lane, so the
-// expensive tests run 32-wide.  The connections that pass are counted
-// (FILL = false) or written (FILL = true) in scan order; rows are sorted later.
+// Near + Collision + transfer.  For a source node v a warp walks the runs of grid
+// cells (contiguous x-ranges) that meet the source's neighbour ball, flattened
+// across up to 32 runs at a time, one candidate per lane, and evaluates
+// Cost(v, u) exactly.  Pairs with Cost < r are queued in shared memory; every 32
+// queued pairs are checked for collision and given their quantised cost and
+// max-plus transfer (S, C) one per lane, so the expensive tests run 32-wide.
 // ---------------------------------------------------------------------------
 constexpr int kQueue = 64;
 constexpr uint32_t kRowCap = 128;   // edges per source in the one-pass build
@@ -345,10 +343,12 @@ constexpr uint32_t kRowCap = 128;   // edges per source in the one-pass build
 // writes straight into the CSR (kFillCsr, after the row pointers are known).
 enum EdgeMode { kFillCsr = 1, kRow = 2 };
 
-template <int DIM, int MODE>
-__device__ __forceinline__ void edge_flush(const BuildJob& J, uint32_t v, const float a[6], const uint32_t* q, int k,
-                                           const float* s_lo, const float* s_hi, uint32_t out_base,
-                                           uint32_t& running) {
+// Overflow pass: one flush of source v's queue, written straight into the CSR
+// (forward row from out_base in discovery order, reverse records by cursor).
+template <int DIM>
+__device__ __forceinline__ void edge_flush_csr(const BuildJob& J, uint32_t v, const float a[6], const uint32_t* q,
+                                               int k, const float* s_lo, const float* s_hi, uint32_t out_base,
+                                               uint32_t& running) {
   const Geom& g = J.g;
   const unsigned lane = lane_id();
   constexpr int nc = (DIM == 6) ? 6 : DIM;
@@ -364,36 +364,226 @@ __device__ __forceinline__ void edge_flush(const BuildJob& J, uint32_t v, const 
     ok = !conn_collides_t<DIM>(g, cn, s_lo, s_hi);
   }
   const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
-  if (MODE == kRow && ok) atomicAdd(&J.indeg[u], 1u);
   if (ok) {
     const uint32_t rank = running + __popc(bal & ((1u << lane) - 1u));
-    if (MODE == kFillCsr || rank < kRowCap) {
+    const int64_t cq = quantise_cost(cn.cost);
+    int64_t S, C, Smax, Cmax;
+    conn_transfer_t<DIM>(g, cn, cq, S, C, Smax, Cmax);
+    if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX || Smax > INT32_MAX || Cmax > INT32_MAX)
+      atomicOr(&J.status[0], kErrEdge);
+    const int4 rec = make_int4((int)u, (int)cq, (int)S, (int)C);
+    const int2 pk = make_int2((int)Smax, (int)Cmax);
+    J.fwd_edge[out_base + rank] = rec;
+    J.fwd_dst[out_base + rank] = u;
+    J.fwd_peak[out_base + rank] = pk;
+    const uint32_t pos = J.rev_ptr[u] + atomicAdd(&J.fill[u], 1u);
+    J.rev_edge[pos] = make_int4((int)v, rec.y, rec.z, rec.w);
+    J.rev_peak[pos] = pk;
+  }
+  running += __popc(bal);
+}
+
+// Run rr of a source's neighbour ball: the x-range of one (y, z) row of cells,
+// clipped to the ball's cross-section at the row's nearest point (conservative),
+// as a range [rs, rs + rl) of cell-ordered nodes.
+template <int DP>
+__device__ __forceinline__ void neighbour_run(const BuildJob& J, uint32_t rr, uint32_t ny, const int clo[3],
+                                              const int chi[3], const float ctr[3], float R, float cs, int GC,
+                                              uint32_t& rs, uint32_t& rl) {
+  const uint32_t yy = (uint32_t)clo[1] + rr % ny;
+  const uint32_t zz = (DP == 3) ? (uint32_t)clo[2] + rr / ny : 0u;
+  const float y0 = (float)yy * cs, y1 = (float)(yy + 1) * cs;
+  const float dy = fmaxf(0.0f, fmaxf(y0 - ctr[1], ctr[1] - y1));
+  float d2 = dy * dy;
+  if (DP == 3) {
+    const float z0 = (float)zz * cs, z1 = (float)(zz + 1) * cs;
+    const float dz = fmaxf(0.0f, fmaxf(z0 - ctr[2], ctr[2] - z1));
+    d2 += dz * dz;
+  }
+  // rows at the clamped grid border may hold nodes outside [0, 1]: keep the
+  // full x-range there
+  const bool border = (yy == 0 || yy == (uint32_t)GC - 1) || (DP == 3 && (zz == 0 || zz == (uint32_t)GC - 1));
+  const float rem = R * R - d2;
+  rs = 0;
+  rl = 0;
+  if (rem >= 0.0f || border) {
+    int xlo = clo[0], xhi = chi[0];
+    if (!border) {
+      const float rx = sqrtf(rem) * 1.0001f + 1e-6f;
+      xlo = cell_coord(ctr[0] - rx, GC);
+      xhi = cell_coord(ctr[0] + rx, GC);
+    }
+    const uint32_t row = (zz * (uint32_t)GC + yy) * (uint32_t)GC;
+    rs = J.cell_start[row + (uint32_t)xlo];
+    rl = J.cell_start[row + (uint32_t)xhi + 1u] - rs;
+  }
+}
+
+// Row pass: collision test, ranks and transfers of one queue flush whose lanes
+// may belong to different sources (each lane carries its own source v).  The
+// lanes of one source are contiguous and in discovery order, so one atomic add on
+// the source's edge count per group hands out its ranks; the group that carries
+// the count past kRowCap puts the source on the overflow list.
+template <int DIM>
+__device__ __forceinline__ void edge_flush_rows(const BuildJob& J, const uint32_t* qu, const uint32_t* qv, int k,
+                                                const float* s_lo, const float* s_hi) {
+  const Geom& g = J.g;
+  const unsigned lane = lane_id();
+  constexpr int nc = (DIM == 6) ? 6 : DIM;
+  bool ok = false;
+  Conn cn;
+  uint32_t u = 0, v = 0xFFFFFFFFu;
+  if ((int)lane < k) {
+    u = qu[lane];
+    v = qv[lane];
+    float a[6] = {0, 0, 0, 0, 0, 0}, b[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < nc; ++c) {
+      a[c] = J.x[(size_t)c * J.V + v];
+      b[c] = J.x[(size_t)c * J.V + u];
+    }
+    conn_setup_t<DIM>(g, a, b, cn);
+    ok = !conn_collides_t<DIM>(g, cn, s_lo, s_hi);
+  }
+  const unsigned okb = __ballot_sync(0xFFFFFFFFu, ok);
+  const unsigned same = __match_any_sync(0xFFFFFFFFu, v);
+  const unsigned grp_ok = same & okb;
+  const int leader = __ffs(same) - 1;
+  uint32_t base = 0;
+  if ((int)lane == leader && (int)lane < k && grp_ok) {
+    const uint32_t n = (uint32_t)__popc(grp_ok);
+    base = atomicAdd(&J.counts[v], n);
+    if (base <= kRowCap && base + n > kRowCap) J.ovf[atomicAdd(&J.status[3], 1u)] = v;
+  }
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (ok) {
+    atomicAdd(&J.indeg[u], 1u);
+    const uint32_t rank = base + (uint32_t)__popc(grp_ok & ((1u << lane) - 1u));
+    if (rank < kRowCap) {
       const int64_t cq = quantise_cost(cn.cost);
       int64_t S, C, Smax, Cmax;
       conn_transfer_t<DIM>(g, cn, cq, S, C, Smax, Cmax);
       if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX || Smax > INT32_MAX || Cmax > INT32_MAX)
         atomicOr(&J.status[0], kErrEdge);
-      const int4 rec = make_int4((int)u, (int)cq, (int)S, (int)C);
-      const int2 pk = make_int2((int)Smax, (int)Cmax);
-      if (MODE == kFillCsr) {
-        J.fwd_edge[out_base + rank] = rec;
-        J.fwd_dst[out_base + rank] = u;
-        J.fwd_peak[out_base + rank] = pk;
-        const uint32_t pos = J.rev_ptr[u] + atomicAdd(&J.fill[u], 1u);
-        J.rev_edge[pos] = make_int4((int)v, rec.y, rec.z, rec.w);
-        J.rev_peak[pos] = pk;
-      } else {
-        J.rows[(size_t)v * kRowCap + rank] = rec;
-        J.rows_peak[(size_t)v * kRowCap + rank] = pk;
+      J.rows[(size_t)v * kRowCap + rank] = make_int4((int)u, (int)cq, (int)S, (int)C);
+      J.rows_peak[(size_t)v * kRowCap + rank] = make_int2((int)Smax, (int)Cmax);
+    }
+  }
+}
+
+constexpr uint32_t kSourcesPerWarp = 8;
+
+// Near + CollisionFree for every source, writing each source's edges to its
+// scratch row with exact counts (sources beyond kRowCap edges go to the overflow
+// pass).  A warp takes kSourcesPerWarp consecutive sources in cell order and
+// feeds their Near candidates through one queue, so collision tests and
+// transfers run on full warps across source boundaries.
+template <int DIM, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_rows(const BuildJob* __restrict__ jobs,
+                                                                    const uint32_t* __restrict__ job_ids) {
+  const BuildJob& J = jobs[job_ids[blockIdx.y]];
+  const Geom& g = J.g;
+  extern __shared__ float smem[];
+  float* s_lo = smem;
+  float* s_hi = smem + 3 * g.nb;
+  uint32_t* s_queue = reinterpret_cast<uint32_t*>(smem + 6 * g.nb);   // [warps][2][kQueue]
+  constexpr int DP = (DIM == 2) ? 2 : 3;
+  constexpr int nc = (DIM == 6) ? 6 : DIM;
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t warp = threadIdx.x >> 5;
+  uint32_t* qu = s_queue + warp * 2 * kQueue;
+  uint32_t* qv = qu + kQueue;
+  for (int i = threadIdx.x; i < 3 * g.nb; i += blockDim.x) {
+    s_lo[i] = g.box_lo[i];
+    s_hi[i] = g.box_hi[i];
+  }
+  __syncthreads();
+  const uint32_t V = J.V;
+  const uint32_t first = (blockIdx.x * WARPS + warp) * kSourcesPerWarp;
+  if (first >= V) return;
+  const uint32_t last = min(first + kSourcesPerWarp, V);
+  const int GC = J.GC;
+  const float R = J.R;
+  const float cs = 1.0f / (float)GC;
+  uint32_t tests = 0;
+  int qn = 0;
+  for (uint32_t my_pos = first; my_pos < last; ++my_pos) {
+    const uint32_t v = J.sorted[my_pos];
+    float a[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < nc; ++c) a[c] = J.sx[(size_t)c * V + my_pos];
+    // centre and cell range of the neighbour ball
+    float ctr[3] = {0, 0, 0};
+    int clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+      ctr[i] = bin_q(J, a[i], a[3 + i], -J.bin_shift);
+      clo[i] = cell_coord(ctr[i] - R, GC);
+      chi[i] = cell_coord(ctr[i] + R, GC);
+    }
+    const uint32_t ny = (uint32_t)(chi[1] - clo[1] + 1);
+    const uint32_t nruns = ny * (DP == 3 ? (uint32_t)(chi[2] - clo[2] + 1) : 1u);
+    for (uint32_t r0 = 0; r0 < nruns; r0 += 32) {
+      uint32_t rs = 0, rl = 0;
+      const uint32_t rr = r0 + lane;
+      if (rr < nruns) neighbour_run<DP>(J, rr, ny, clo, chi, ctr, R, cs, GC, rs, rl);
+      const uint32_t incl = warp_incl_scan(rl);
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      const uint32_t excl = incl - rl;
+      tests += total;
+      for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+        const uint32_t c = c0 + lane;
+        uint32_t owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t probe = owner + step;
+          if (__shfl_sync(0xFFFFFFFFu, excl, probe) <= c) owner = probe;
+        }
+        const uint32_t o_rs = __shfl_sync(0xFFFFFFFFu, rs, owner);
+        const uint32_t o_ex = __shfl_sync(0xFFFFFFFFu, excl, owner);
+        bool near = false;
+        uint32_t sidx = 0;
+        if (c < total) {
+          sidx = o_rs + (c - o_ex);
+          float b[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+          for (int k = 0; k < nc; ++k) b[k] = J.sx[(size_t)k * V + sidx];
+          near = (sidx != my_pos) && (conn_cost_t<DIM>(g, a, b) < g.r);
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, near);
+        if (near) {
+          const int at = qn + __popc(bal & lt);
+          qu[at] = J.sorted[sidx];
+          qv[at] = v;
+        }
+        qn += __popc(bal);
+        if (qn >= 32) {
+          __syncwarp();
+          edge_flush_rows<DIM>(J, qu, qv, 32, s_lo, s_hi);
+          const bool mv = 32 + (int)lane < qn;
+          const uint32_t ru = mv ? qu[32 + lane] : 0u, rv = mv ? qv[32 + lane] : 0u;
+          __syncwarp();
+          if (mv) {
+            qu[lane] = ru;
+            qv[lane] = rv;
+          }
+          qn -= 32;
+          __syncwarp();
+        }
       }
     }
   }
-  running += __popc(bal);
+  __syncwarp();
+  if (qn > 0) edge_flush_rows<DIM>(J, qu, qv, qn, s_lo, s_hi);
+  if (lane == 0) atomicAdd(J.near_tests, (unsigned long long)tests);
 }
 
-template <int DIM, int MODE, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges(const BuildJob* __restrict__ jobs,
-                                                               const uint32_t* __restrict__ job_ids) {
+// Overflow pass: the sources whose rows outgrew kRowCap, one warp per source,
+// edges written straight into the CSR at the source's row pointer.
+template <int DIM, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_csr(const BuildJob* __restrict__ jobs,
+                                                                   const uint32_t* __restrict__ job_ids) {
   const BuildJob& J = jobs[job_ids[blockIdx.y]];
   const Geom& g = J.g;
   extern __shared__ float smem[];
@@ -412,16 +602,8 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges(const BuildJob
   }
   __syncthreads();
   const uint32_t slot = blockIdx.x * WARPS + warp;
-  uint32_t v = slot;
-  if (MODE == kFillCsr) {
-    if (slot >= J.status[3]) return;
-    v = J.ovf[slot];
-  } else if (v >= J.V) {
-    return;
-  } else {
-    // sources in cell order: the warps of a block scan overlapping neighbourhoods
-    v = J.sorted[slot];
-  }
+  if (slot >= J.status[3]) return;
+  const uint32_t v = J.ovf[slot];
   const uint32_t V = J.V;
   float a[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
@@ -444,39 +626,13 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges(const BuildJob
   uint32_t running = 0;
   uint32_t tests = 0;
   int qn = 0;
-  const uint32_t out_base = (MODE == kFillCsr) ? J.fwd_ptr[v] : 0u;
+  const uint32_t out_base = J.fwd_ptr[v];
   for (uint32_t r0 = 0; r0 < nruns; r0 += 32) {
     // lane j describes run r0 + j: the x-range of one (y, z) row of cells, clipped
     // to the ball's cross-section at the row's nearest point (conservative)
     uint32_t rs = 0, rl = 0;
     const uint32_t rr = r0 + lane;
-    if (rr < nruns) {
-      const uint32_t yy = (uint32_t)clo[1] + rr % ny;
-      const uint32_t zz = (DP == 3) ? (uint32_t)clo[2] + rr / ny : 0u;
-      const float y0 = (float)yy * cs, y1 = (float)(yy + 1) * cs;
-      const float dy = fmaxf(0.0f, fmaxf(y0 - ctr[1], ctr[1] - y1));
-      float d2 = dy * dy;
-      if (DP == 3) {
-        const float z0 = (float)zz * cs, z1 = (float)(zz + 1) * cs;
-        const float dz = fmaxf(0.0f, fmaxf(z0 - ctr[2], ctr[2] - z1));
-        d2 += dz * dz;
-      }
-      // rows at the clamped grid border may hold nodes outside [0, 1]: keep the
-      // full x-range there
-      const bool border = (yy == 0 || yy == (uint32_t)GC - 1) || (DP == 3 && (zz == 0 || zz == (uint32_t)GC - 1));
-      const float rem = R * R - d2;
-      if (rem >= 0.0f || border) {
-        int xlo = clo[0], xhi = chi[0];
-        if (!border) {
-          const float rx = sqrtf(rem) * 1.0001f + 1e-6f;
-          xlo = cell_coord(ctr[0] - rx, GC);
-          xhi = cell_coord(ctr[0] + rx, GC);
-        }
-        const uint32_t row = (zz * (uint32_t)GC + yy) * (uint32_t)GC;
-        rs = J.cell_start[row + (uint32_t)xlo];
-        rl = J.cell_start[row + (uint32_t)xhi + 1u] - rs;
-      }
-    }
+    if (rr < nruns) neighbour_run<DP>(J, rr, ny, clo, chi, ctr, R, cs, GC, rs, rl);
     const uint32_t incl = warp_incl_scan(rl);
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     const uint32_t excl = incl - rl;
@@ -505,7 +661,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges(const BuildJob
       qn += __popc(bal);
       if (qn >= 32) {
         __syncwarp();
-        edge_flush<DIM, MODE>(J, v, a, q, 32, s_lo, s_hi, out_base, running);
+        edge_flush_csr<DIM>(J, v, a, q, 32, s_lo, s_hi, out_base, running);
         const uint32_t rest = (32 + (int)lane < qn) ? q[32 + lane] : 0u;
         __syncwarp();
         if (32 + (int)lane < qn) q[lane] = rest;
@@ -515,12 +671,8 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges(const BuildJob
     }
   }
   __syncwarp();
-  if (qn > 0) edge_flush<DIM, MODE>(J, v, a, q, qn, s_lo, s_hi, out_base, running);
-  if (MODE == kRow && lane == 0) {
-    J.counts[v] = running;
-    if (running > kRowCap) J.ovf[atomicAdd(&J.status[3], 1u)] = v;
-    atomicAdd(J.near_tests, (unsigned long long)tests);
-  }
+  if (qn > 0) edge_flush_csr<DIM>(J, v, a, q, qn, s_lo, s_hi, out_base, running);
+  (void)tests;   // counted by the row pass
 }
 
 // One-pass build: copy each source's scratch row (at most kRowCap edges) into
@@ -573,9 +725,15 @@ __global__ void k_reverse_fill(const BuildJob* __restrict__ jobs) {
 template <int MODE, int WARPS>
 void launch_edges_w(int dim, dim3 grid, size_t smem, cudaStream_t st, const BuildJob* jobs, const uint32_t* ids) {
   const dim3 block(WARPS * 32);
-  if (dim == 6) k_edges<6, MODE, WARPS><<<grid, block, smem, st>>>(jobs, ids);
-  else if (dim == 3) k_edges<3, MODE, WARPS><<<grid, block, smem, st>>>(jobs, ids);
-  else k_edges<2, MODE, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+  if (MODE == kRow) {
+    if (dim == 6) k_edges_rows<6, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+    else if (dim == 3) k_edges_rows<3, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+    else k_edges_rows<2, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+  } else {
+    if (dim == 6) k_edges_csr<6, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+    else if (dim == 3) k_edges_csr<3, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+    else k_edges_csr<2, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+  }
 }
 
 // One launch per dimension group; `warps` (4 or 8 warps per block) comes from
@@ -584,8 +742,11 @@ template <int MODE>
 void launch_edges(int dim, uint32_t warps, uint32_t vmax, uint32_t njobs, size_t box_smem, cudaStream_t st,
                   const BuildJob* jobs, const uint32_t* ids) {
   LaunchScope ls(st, MODE == kRow ? "k_edges" : "k_edges_overflow");
-  const dim3 grid((vmax + warps - 1) / warps, njobs);
-  const size_t smem = box_smem + sizeof(uint32_t) * warps * kQueue;
+  // row pass: kSourcesPerWarp sources per warp, queue of (target, source) pairs;
+  // overflow pass: one source per warp
+  const uint32_t per_block = (MODE == kRow) ? warps * kSourcesPerWarp : warps;
+  const dim3 grid((vmax + per_block - 1) / per_block, njobs);
+  const size_t smem = box_smem + sizeof(uint32_t) * warps * kQueue * (MODE == kRow ? 2 : 1);
   if (warps == 4) launch_edges_w<MODE, 4>(dim, grid, smem, st, jobs, ids);
   else launch_edges_w<MODE, 8>(dim, grid, smem, st, jobs, ids);
 }
@@ -921,6 +1082,7 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   for (uint32_t j = 0; j < n; ++j) hj[j].status = cv.take<uint32_t>(4);
   for (uint32_t j = 0; j < n; ++j) hj[j].near_tests = cv.take<unsigned long long>(1);
   for (uint32_t j = 0; j < n; ++j) {
+    hj[j].counts = cv.take<uint32_t>((size_t)hj[j].V + 1);
     hj[j].indeg = cv.take<uint32_t>((size_t)hj[j].V + 1);
     hj[j].fill = cv.take<uint32_t>((size_t)hj[j].V + 1);
   }
@@ -938,7 +1100,6 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     J.cell_of = cv.take<uint32_t>(J.V);
     J.sorted = cv.take<uint32_t>(J.V);
     J.sx = cv.take<float>(6 * (size_t)J.V);
-    J.counts = cv.take<uint32_t>((size_t)J.V + 1);
     J.rows = cv.take<int4>(kRowCap * (size_t)J.V);
     J.rows_peak = cv.take<int2>(kRowCap * (size_t)J.V);
     J.ovf = cv.take<uint32_t>((size_t)J.V);
