@@ -240,6 +240,60 @@ __device__ __forceinline__ bool seg_hits_box(const float a[3], const float d[3],
   return !miss && (t0 <= t1) && (t1 >= 0.0f) && (t0 <= 1.0f);
 }
 
+// Box prefilter for scenes of at most 32 boxes: per axis a and bin i of a
+// 64-bin grid over [0, 1), bins[(2a) 64 + i] holds the boxes whose low face lies
+// below the top of bin i (every box at the last bin) and bins[(2a + 1) 64 + i]
+// the boxes whose high face lies at or above the bottom of bin i (every box at
+// bin 0).  A box meets the interval [l, h] on axis a only if it is in both
+// bins[(2a) 64 + bin(h)] and bins[(2a + 1) 64 + bin(l)] (bins clamped to the
+// grid; the 64x scaling is exact), so the AND over the axes is a superset of the
+// boxes that a bounding box overlaps.
+constexpr int kBoxBins = 64;
+constexpr int kBinMaxBoxes = 32;
+
+__device__ __forceinline__ int box_bin(float x) {
+  const float f = floorf(x * (float)kBoxBins);
+  return (f >= 0.0f) ? (f <= (float)(kBoxBins - 1) ? (int)f : kBoxBins - 1) : 0;
+}
+
+// Fills the prefilter table (dp axes) from the boxes in shared memory; all
+// threads of the block take part.
+__device__ __forceinline__ void build_box_bins(int nb, int dp, const float* s_lo, const float* s_hi,
+                                               uint32_t* s_bins) {
+  for (int t = threadIdx.x; t < dp * 2 * kBoxBins; t += blockDim.x) {
+    const int a = t / (2 * kBoxBins), side = (t / kBoxBins) & 1, i = t % kBoxBins;
+    uint32_t m = 0;
+    for (int b = 0; b < nb; ++b) {
+      const bool in = (side == 0) ? (i == kBoxBins - 1 || s_lo[3 * b + a] < (float)(i + 1) / (float)kBoxBins)
+                                  : (i == 0 || s_hi[3 * b + a] >= (float)i / (float)kBoxBins);
+      m |= in ? (1u << b) : 0u;
+    }
+    s_bins[t] = m;
+  }
+}
+
+// Boxes (bit b = box b) that the bounding box [lo, hi] overlaps, exactly: the
+// prefilter's candidates checked face by face.
+template <int DP>
+__device__ __forceinline__ uint32_t boxes_overlapping(const float lo[3], const float hi[3], const float* s_lo,
+                                                      const float* s_hi, const uint32_t* s_bins) {
+  uint32_t cand = 0xFFFFFFFFu;
+#pragma unroll
+  for (int a = 0; a < DP; ++a)
+    cand &= s_bins[(2 * a) * kBoxBins + box_bin(hi[a])] & s_bins[(2 * a + 1) * kBoxBins + box_bin(lo[a])];
+  uint32_t mask = 0;
+  for (uint32_t mm = cand; mm; mm &= mm - 1) {
+    const int b = __ffs(mm) - 1;
+    const float* bl = s_lo + 3 * b;
+    const float* bh = s_hi + 3 * b;
+    bool overlap = true;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) overlap = overlap && bl[i] <= hi[i] && bh[i] >= lo[i];
+    mask |= overlap ? (1u << b) : 0u;
+  }
+  return mask;
+}
+
 // Collision of a connection against the boxes (box data in shared memory):
 // 2D/3D exact slab test; 6D point tests at the M-1 interior checkpoints, where
 // leaving the unit workspace also counts.
@@ -249,18 +303,27 @@ __device__ __forceinline__ bool seg_hits_box(const float a[3], const float d[3],
 // the checkpoints themselves (a closed box holds a checkpoint only if it overlaps
 // their bounding box).  2D/3D: the segment's bounding box grown by 1e-5, which
 // exceeds the rounding of the slab arithmetic by orders of magnitude, so a box
-// outside it is also reported clear by the floating-point slab test.
+// outside it is also reported clear by the floating-point slab test.  With
+// s_bins (at most 32 boxes) the overlapping boxes come from the prefilter table
+// instead of a pass over every box; the set is the same.
 template <int DIM>
 __device__ __forceinline__ bool conn_collides_t(const Geom& g, const Conn& c, const float* s_lo,
-                                                const float* s_hi) {
+                                                const float* s_hi, const uint32_t* s_bins) {
   if (DIM != 6) {
     constexpr int DP = (DIM == 2) ? 2 : 3;
-    float lo[3], hi[3];
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < DP; ++i) {
       const float e = __fadd_rn(c.p0[i], c.d[i]);
       lo[i] = fminf(c.p0[i], e) - 1e-5f;
       hi[i] = fmaxf(c.p0[i], e) + 1e-5f;
+    }
+    if (s_bins) {
+      for (uint32_t mm = boxes_overlapping<DP>(lo, hi, s_lo, s_hi, s_bins); mm; mm &= mm - 1) {
+        const int b = __ffs(mm) - 1;
+        if (seg_hits_box<DP>(c.p0, c.d, s_lo + 3 * b, s_hi + 3 * b)) return true;
+      }
+      return false;
     }
     for (int b = 0; b < g.nb; ++b) {
       const float* bl = s_lo + 3 * b;
@@ -286,13 +349,17 @@ __device__ __forceinline__ bool conn_collides_t(const Geom& g, const Conn& c, co
     return true;
   for (int b0 = 0; b0 < g.nb; b0 += 32) {
     uint32_t mask = 0;
-    const int nbb = (g.nb - b0) < 32 ? (g.nb - b0) : 32;
-    for (int j = 0; j < nbb; ++j) {
-      const float* bl = s_lo + 3 * (b0 + j);
-      const float* bh = s_hi + 3 * (b0 + j);
-      const bool overlap = bl[0] <= hi[0] && bh[0] >= lo[0] && bl[1] <= hi[1] && bh[1] >= lo[1] &&
-                           bl[2] <= hi[2] && bh[2] >= lo[2];
-      mask |= overlap ? (1u << j) : 0u;
+    if (s_bins) {
+      mask = boxes_overlapping<3>(lo, hi, s_lo, s_hi, s_bins);
+    } else {
+      const int nbb = (g.nb - b0) < 32 ? (g.nb - b0) : 32;
+      for (int j = 0; j < nbb; ++j) {
+        const float* bl = s_lo + 3 * (b0 + j);
+        const float* bh = s_hi + 3 * (b0 + j);
+        const bool overlap = bl[0] <= hi[0] && bh[0] >= lo[0] && bl[1] <= hi[1] && bh[1] >= lo[1] &&
+                             bl[2] <= hi[2] && bh[2] >= lo[2];
+        mask |= overlap ? (1u << j) : 0u;
+      }
     }
     if (!mask) continue;
     for (int m = 1; m < g.M; ++m) {

@@ -347,8 +347,8 @@ enum EdgeMode { kFillCsr = 1, kRow = 2 };
 // (forward row from out_base in discovery order, reverse records by cursor).
 template <int DIM>
 __device__ __forceinline__ void edge_flush_csr(const BuildJob& J, uint32_t v, const float a[6], const uint32_t* q,
-                                               int k, const float* s_lo, const float* s_hi, uint32_t out_base,
-                                               uint32_t& running) {
+                                               int k, const float* s_lo, const float* s_hi, const uint32_t* s_bins,
+                                               uint32_t out_base, uint32_t& running) {
   const Geom& g = J.g;
   const unsigned lane = lane_id();
   constexpr int nc = (DIM == 6) ? 6 : DIM;
@@ -361,7 +361,7 @@ __device__ __forceinline__ void edge_flush_csr(const BuildJob& J, uint32_t v, co
 #pragma unroll
     for (int c = 0; c < nc; ++c) b[c] = J.x[(size_t)c * J.V + u];
     conn_setup_t<DIM>(g, a, b, cn);
-    ok = !conn_collides_t<DIM>(g, cn, s_lo, s_hi);
+    ok = !conn_collides_t<DIM>(g, cn, s_lo, s_hi, s_bins);
   }
   const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
   if (ok) {
@@ -426,7 +426,7 @@ __device__ __forceinline__ void neighbour_run(const BuildJob& J, uint32_t rr, ui
 // the count past kRowCap puts the source on the overflow list.
 template <int DIM>
 __device__ __forceinline__ void edge_flush_rows(const BuildJob& J, const uint32_t* qu, const uint32_t* qv, int k,
-                                                const float* s_lo, const float* s_hi) {
+                                                const float* s_lo, const float* s_hi, const uint32_t* s_bins) {
   const Geom& g = J.g;
   const unsigned lane = lane_id();
   constexpr int nc = (DIM == 6) ? 6 : DIM;
@@ -443,7 +443,7 @@ __device__ __forceinline__ void edge_flush_rows(const BuildJob& J, const uint32_
       b[c] = J.x[(size_t)c * J.V + u];
     }
     conn_setup_t<DIM>(g, a, b, cn);
-    ok = !conn_collides_t<DIM>(g, cn, s_lo, s_hi);
+    ok = !conn_collides_t<DIM>(g, cn, s_lo, s_hi, s_bins);
   }
   const unsigned okb = __ballot_sync(0xFFFFFFFFu, ok);
   const unsigned same = __match_any_sync(0xFFFFFFFFu, v);
@@ -486,7 +486,8 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_rows(const Bui
   extern __shared__ float smem[];
   float* s_lo = smem;
   float* s_hi = smem + 3 * g.nb;
-  uint32_t* s_queue = reinterpret_cast<uint32_t*>(smem + 6 * g.nb);   // [warps][2][kQueue]
+  uint32_t* s_bins = reinterpret_cast<uint32_t*>(smem + 6 * g.nb);            // [dp][2][kBoxBins]
+  uint32_t* s_queue = s_bins + 6 * kBoxBins;   // [warps][2][kQueue]
   constexpr int DP = (DIM == 2) ? 2 : 3;
   constexpr int nc = (DIM == 6) ? 6 : DIM;
   const unsigned lane = lane_id();
@@ -499,6 +500,11 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_rows(const Bui
     s_hi[i] = g.box_hi[i];
   }
   __syncthreads();
+  const bool binned = g.nb <= kBinMaxBoxes;
+  if (binned) {
+    build_box_bins(g.nb, DP, s_lo, s_hi, s_bins);
+    __syncthreads();
+  }
   const uint32_t V = J.V;
   const uint32_t first = (blockIdx.x * WARPS + warp) * kSourcesPerWarp;
   if (first >= V) return;
@@ -560,7 +566,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_rows(const Bui
         qn += __popc(bal);
         if (qn >= 32) {
           __syncwarp();
-          edge_flush_rows<DIM>(J, qu, qv, 32, s_lo, s_hi);
+          edge_flush_rows<DIM>(J, qu, qv, 32, s_lo, s_hi, binned ? s_bins : nullptr);
           const bool mv = 32 + (int)lane < qn;
           const uint32_t ru = mv ? qu[32 + lane] : 0u, rv = mv ? qv[32 + lane] : 0u;
           __syncwarp();
@@ -575,7 +581,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_rows(const Bui
     }
   }
   __syncwarp();
-  if (qn > 0) edge_flush_rows<DIM>(J, qu, qv, qn, s_lo, s_hi);
+  if (qn > 0) edge_flush_rows<DIM>(J, qu, qv, qn, s_lo, s_hi, binned ? s_bins : nullptr);
   if (lane == 0) atomicAdd(J.near_tests, (unsigned long long)tests);
 }
 
@@ -589,7 +595,8 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_csr(const Buil
   extern __shared__ float smem[];
   float* s_lo = smem;
   float* s_hi = smem + 3 * g.nb;
-  uint32_t* s_queue = reinterpret_cast<uint32_t*>(smem + 6 * g.nb);   // [warps][kQueue]
+  uint32_t* s_bins = reinterpret_cast<uint32_t*>(smem + 6 * g.nb);            // [dp][2][kBoxBins]
+  uint32_t* s_queue = s_bins + 6 * kBoxBins;   // [warps][kQueue]
   constexpr int DP = (DIM == 2) ? 2 : 3;
   constexpr int nc = (DIM == 6) ? 6 : DIM;
   const unsigned lane = lane_id();
@@ -601,6 +608,11 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_csr(const Buil
     s_hi[i] = g.box_hi[i];
   }
   __syncthreads();
+  const bool binned = g.nb <= kBinMaxBoxes;
+  if (binned) {
+    build_box_bins(g.nb, DP, s_lo, s_hi, s_bins);
+    __syncthreads();
+  }
   const uint32_t slot = blockIdx.x * WARPS + warp;
   if (slot >= J.status[3]) return;
   const uint32_t v = J.ovf[slot];
@@ -661,7 +673,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_csr(const Buil
       qn += __popc(bal);
       if (qn >= 32) {
         __syncwarp();
-        edge_flush_csr<DIM>(J, v, a, q, 32, s_lo, s_hi, out_base, running);
+        edge_flush_csr<DIM>(J, v, a, q, 32, s_lo, s_hi, binned ? s_bins : nullptr, out_base, running);
         const uint32_t rest = (32 + (int)lane < qn) ? q[32 + lane] : 0u;
         __syncwarp();
         if (32 + (int)lane < qn) q[lane] = rest;
@@ -671,7 +683,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_csr(const Buil
     }
   }
   __syncwarp();
-  if (qn > 0) edge_flush_csr<DIM>(J, v, a, q, qn, s_lo, s_hi, out_base, running);
+  if (qn > 0) edge_flush_csr<DIM>(J, v, a, q, qn, s_lo, s_hi, binned ? s_bins : nullptr, out_base, running);
   (void)tests;   // counted by the row pass
 }
 
@@ -746,7 +758,8 @@ void launch_edges(int dim, uint32_t warps, uint32_t vmax, uint32_t njobs, size_t
   // overflow pass: one source per warp
   const uint32_t per_block = (MODE == kRow) ? warps * kSourcesPerWarp : warps;
   const dim3 grid((vmax + per_block - 1) / per_block, njobs);
-  const size_t smem = box_smem + sizeof(uint32_t) * warps * kQueue * (MODE == kRow ? 2 : 1);
+  const size_t smem = box_smem + sizeof(uint32_t) * 6 * kBoxBins +
+                      sizeof(uint32_t) * warps * kQueue * (MODE == kRow ? 2 : 1);
   if (warps == 4) launch_edges_w<MODE, 4>(dim, grid, smem, st, jobs, ids);
   else launch_edges_w<MODE, 8>(dim, grid, smem, st, jobs, ids);
 }

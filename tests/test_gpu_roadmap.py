@@ -145,3 +145,15 @@ def test_level_above_K_is_rejected(mp):
     with pytest.raises(mp.MpapError) as e:
         mp.build_roadmap_for_scene(sc, n=300)
     assert e.value.status == mp.MPAP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name,nb,seed,n", [("2d", 33, 3, 900), ("3d", 40, 5, 1500), ("6d", 48, 6, 1500),
+                                            ("6d", 32, 7, 1500), ("3d", 1, 8, 1200)])
+def test_box_counts_around_the_prefilter_limit(mp, orc, name, nb, seed, n):
+    """Scenes of at most 32 boxes take the collision prefilter table, larger ones
+    the pass over every box: the edge set is the oracle's either way."""
+    sc = scenegen.make_scene(scenegen.config(name, nb=nb), seed, query_id=seed)
+    assert len(sc.box_lo) == nb
+    rg = mp.build_roadmap_for_scene(sc, n=n)
+    assert_same_graph(rg.export(), orc.build_roadmap(sc, n=n).graph())
+    assert_reverse_is_transpose(rg)
