@@ -109,6 +109,10 @@ def test_reverse_csr_of_a_given_graph(mp, orc):
     # below the bound: 32-bit sums
     ("3d", 3, 1200, None, 8),
     ("6d", 3, 1200, None, 16),
+    # 6D checkpoint levels packed by the collision test (m = 1..16 below M)
+    ("6d", 3, 1200, None, 1),     # no interior checkpoint
+    ("6d", 3, 1200, None, 5),
+    ("6d", 3, 1200, None, 17),    # all 16 packed, the endpoint computed
 ])
 def test_transfer_sums_both_widths(mp, orc, name, seed, n, r, M):
     """The per-edge transfer runs in 32-bit integers only where its partial sums
