@@ -313,11 +313,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
     if (w.qs[q].done) continue;
     const QueryDev& Q = w.qd[q];
     const uint4 fd = w.fdesc[g];
+    // the out-edge range does not depend on the front: its loads go out now
+    const uint32_t u = g - Q.base;
+    const uint32_t e_beg = Q.fwd_ptr[u], e_end = Q.fwd_ptr[u + 1];
     const uint32_t n = fd.y;
     const size_t o = fd.x;
     const long long thr = (long long)it * Q.Lambda;
     uint32_t cnt = 0;
     bool rest = false;
+    // a front of at most 32 entries stays in registers for the second pass
+    uint32_t pid0 = 0;
+    long long c0 = 0;
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {
       const uint32_t j = j0 + lane;
       uint32_t pid = 0;
@@ -325,6 +331,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
       if (j < n) {
         pid = w.f_pid[o + j];
         c = w.f_cost[o + j];
+      }
+      if (j0 == 0) {
+        pid0 = pid;
+        c0 = c;
       }
       const bool open = (j < n) && (pid & kOpen);
       cnt += __popc(__ballot_sync(kFull, open && c <= thr));
@@ -341,9 +351,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
         uint32_t r0 = 0;
         for (uint32_t j0 = 0; j0 < n; j0 += 32) {
           const uint32_t j = j0 + lane;
-          uint32_t pid = 0;
-          long long c = 0;
-          if (j < n) {
+          uint32_t pid = pid0;
+          long long c = c0;
+          if (j0 > 0 && j < n) {
             pid = w.f_pid[o + j];
             c = w.f_cost[o + j];
           }
@@ -361,26 +371,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
         if (lane == 0) {
           w.gdesc[g] = make_uint4(it, cnt, off, 0u);
           atomic_add_i64(&w.qs[q].open_cnt, -(long long)cnt);
-          if (Q.is_goal[g - Q.base]) w.qs[q].goal_hit = 1u;
+          if (Q.is_goal[u]) w.qs[q].goal_hit = 1u;
         }
         // mark the out-neighbours of this node as touched (deduplicated by stamp;
-        // a plain read first skips the atomic for nodes already marked)
-        const uint32_t u = g - Q.base;
-        const uint32_t e_end = Q.fwd_ptr[u + 1];
-        for (uint32_t e0 = Q.fwd_ptr[u]; e0 < e_end; e0 += 32) {
-          const uint32_t e = e0 + lane;
-          bool first = false;
-          uint32_t gx = 0;
-          if (e < e_end) {
-            gx = Q.base + __ldg(&Q.fwd_dst[e]);
-            if (w.touch_stamp[gx] != it) first = atomicExch(&w.touch_stamp[gx], it) != it;
-          }
-          const unsigned bal = __ballot_sync(kFull, first);
-          if (bal) {
+        // a plain read first skips the atomic for nodes already marked), 64 edges
+        // per step with the loads of both halves in flight together
+        for (uint32_t e0 = e_beg; e0 < e_end; e0 += 64) {
+          const uint32_t ea = e0 + lane, eb = e0 + 32 + lane;
+          const bool va = ea < e_end, vb = eb < e_end;
+          const uint32_t ga = va ? Q.base + __ldg(&Q.fwd_dst[ea]) : 0u;
+          const uint32_t gb = vb ? Q.base + __ldg(&Q.fwd_dst[eb]) : 0u;
+          const uint32_t sa = va ? w.touch_stamp[ga] : it;
+          const uint32_t sb = vb ? w.touch_stamp[gb] : it;
+          bool fa = false, fb = false;
+          if (sa != it) fa = atomicExch(&w.touch_stamp[ga], it) != it;
+          if (sb != it) fb = atomicExch(&w.touch_stamp[gb], it) != it;
+          const unsigned bala = __ballot_sync(kFull, fa), balb = __ballot_sync(kFull, fb);
+          if (bala | balb) {
             uint32_t pos = 0;
-            if (lane == 0) pos = atomicAdd(&w.ctl->t_n, __popc(bal));
+            if (lane == 0) pos = atomicAdd(&w.ctl->t_n, __popc(bala) + __popc(balb));
             pos = __shfl_sync(kFull, pos, 0);
-            if (first) w.t_list[pos + __popc(bal & lt)] = make_uint2(gx, q);
+            if (fa) w.t_list[pos + __popc(bala & lt)] = make_uint2(ga, q);
+            if (fb) w.t_list[pos + __popc(bala) + __popc(balb & lt)] = make_uint2(gb, q);
           }
         }
       }
