@@ -64,15 +64,40 @@ __global__ void k_mc_checkpoints(const McJob* jobs) {
 
 constexpr int kMcMaxBoxes = 512;
 
+// Point-in-box prefilter of the rollouts (scenes of at most 32 boxes): the unit
+// interval in 2^-20 units is cut into 64 bins of 2^14; per axis a and bin i,
+// bins[(2a) 64 + i] holds the boxes whose low face is at most the bin's largest
+// coordinate and bins[(2a + 1) 64 + i] those whose high face is at least its
+// smallest, so a box holding a point of bin i is in both: their AND over the
+// axes is a superset of the boxes holding the point, checked exactly after.
+constexpr int kMcBins = 64;
+constexpr int kMcBinShift = 14;
+
 __global__ void __launch_bounds__(256) k_mc_rollouts(const McJob* jobs) {
   const McJob& J = jobs[blockIdx.y];
   __shared__ int s_lo[3 * kMcMaxBoxes], s_hi[3 * kMcMaxBoxes];
+  __shared__ uint32_t s_bins[6 * kMcBins];
   const int nb = J.g.nb < kMcMaxBoxes ? J.g.nb : kMcMaxBoxes;
   for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) {
     s_lo[i] = (int)__float2ll_rn(__fmul_rn(J.g.box_lo[i], kTwo20));
     s_hi[i] = (int)__float2ll_rn(__fmul_rn(J.g.box_hi[i], kTwo20));
   }
   __syncthreads();
+  const bool binned = nb <= 32;
+  if (binned) {
+    for (int t = threadIdx.x; t < 6 * kMcBins; t += blockDim.x) {
+      const int a = t / (2 * kMcBins), side = (t / kMcBins) & 1, i = t % kMcBins;
+      const int bmin = i << kMcBinShift;
+      const int bmax = (i == kMcBins - 1) ? (1 << 20) : ((i + 1) << kMcBinShift) - 1;
+      uint32_t m = 0;
+      for (int b = 0; b < nb; ++b) {
+        const bool in = (side == 0) ? (s_lo[3 * b + a] <= bmax) : (s_hi[3 * b + a] >= bmin);
+        m |= in ? (1u << b) : 0u;
+      }
+      s_bins[t] = m;
+    }
+    __syncthreads();
+  }
   const int dp = J.g.dp;
   const uint32_t ro = blockIdx.x * blockDim.x + threadIdx.x;
   bool loc = false, coll = false;
@@ -125,7 +150,23 @@ __global__ void __launch_bounds__(256) k_mc_rollouts(const McJob* jobs) {
       if (ee >= J.delta2) loc = true;
       const long long qx = (long long)ck.x + e[0], qy = (long long)ck.y + e[1], qz = (long long)ck.z + e[2];
       bool bad = qx < 0 || qx > one || qy < 0 || qy > one || (dp == 3 && (qz < 0 || qz > one));
-      for (int b = 0; b < nb && !bad; ++b) {
+      if (!bad && binned) {
+        // inside the unit box: every coordinate lies in [0, 2^20]
+        const int bx = min((int)(qx >> kMcBinShift), kMcBins - 1);
+        const int by = min((int)(qy >> kMcBinShift), kMcBins - 1);
+        uint32_t cand = s_bins[bx] & s_bins[kMcBins + bx] & s_bins[2 * kMcBins + by] & s_bins[3 * kMcBins + by];
+        if (dp == 3) {
+          const int bz = min((int)(qz >> kMcBinShift), kMcBins - 1);
+          cand &= s_bins[4 * kMcBins + bz] & s_bins[5 * kMcBins + bz];
+        }
+        for (uint32_t mm = cand; mm && !bad; mm &= mm - 1) {
+          const int b = __ffs(mm) - 1;
+          bool in = qx >= s_lo[3 * b] && qx <= s_hi[3 * b] && qy >= s_lo[3 * b + 1] && qy <= s_hi[3 * b + 1];
+          if (dp == 3) in = in && qz >= s_lo[3 * b + 2] && qz <= s_hi[3 * b + 2];
+          bad = in;
+        }
+      }
+      for (int b = 0; b < nb && !bad && !binned; ++b) {
         bool in = qx >= s_lo[3 * b] && qx <= s_hi[3 * b] && qy >= s_lo[3 * b + 1] && qy <= s_hi[3 * b + 1];
         if (dp == 3) in = in && qz >= s_lo[3 * b + 2] && qz <= s_hi[3 * b + 2];
         bad = in;

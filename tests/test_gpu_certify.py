@@ -54,3 +54,21 @@ def test_certify_batch_and_edge_cases(mp, orc):
     sc, ro, rg, path = jobs[0]
     assert mp.certify(rg, path[:1], 100, 1, 0, sc.delta_fx, sc.sigma_fx, sc.shift)["hits_any"] == 0
     assert mp.certify(rg, path, 0, 1, 0, sc.delta_fx, sc.sigma_fx, sc.shift)["rollouts"] == 0
+
+
+@pytest.mark.parametrize("name,nb,seed,n", [("3d", 32, 4, 1500), ("3d", 40, 4, 1500), ("6d", 33, 5, 2500),
+                                            ("2d", 36, 6, 800)])
+def test_certify_around_the_box_prefilter_limit(mp, orc, name, nb, seed, n):
+    """Rollouts of scenes with at most 32 boxes take the point-in-box prefilter
+    table, larger scenes the pass over every box: the hit counts are the
+    oracle's either way, with collisions among them."""
+    sc = scenegen.make_scene(scenegen.config(name, nb=nb), seed, query_id=seed)
+    r = sc.cfg.r if name != "6d" else 18.0
+    ro, path = _plan(orc, sc, n, r)
+    rg = mp.build_roadmap_for_scene(sc, n=n, r=r)
+    for call_id, scale in ((1, 1), (1, 4)):
+        sig = sc.sigma_fx * scale
+        a = orc.certify(ro, path, 1024, sc.mc_seed, call_id, sc.delta_fx, sig, sc.shift)
+        b = mp.certify(rg, path, 1024, sc.mc_seed, call_id, sc.delta_fx, sig, sc.shift)
+        assert a == b
+    assert b["hits_coll"] > 0
