@@ -290,6 +290,9 @@ def run_gpu(args, rank, world, local):
     out["solved"] = sum(1 for r in res if r.status == 0)
     out["certified_failure_rate"] = sum(c["hits_any"] for c in certs) / max(1, sum(c["rollouts"] for c in certs))
     out["roofline"] = roofline(kern, arm, res, args.steps)
+    # the two kernels that share most of the step, each against its own bound
+    out["roofline_by_kernel"] = [roofline(kern, arm, res, args.steps, name=k) for k in ("k_prune", "k_edges")
+                                 if k in kern]
     if ck:
         out["clocks"] = ck
     if rank == 0 and not args.no_plain:
@@ -309,17 +312,17 @@ def run_gpu(args, rank, world, local):
     return out
 
 
-# DRAM traffic from ncu captures (profiles/*.md), per unit of work, valid only
-# while the kernel sources are the ones that were captured.
+# DRAM traffic from ncu captures, per unit of work, valid only while the kernel
+# sources are the ones that were captured.
 NCU_TRAFFIC = {
-    # one launch over 8 roadmaps: 12.44 MB read + 86.04 MB written (profiles/k_edges_6d16k.md)
-    "k_edges": {"bytes_per_roadmap": (12.438272e6 + 86.0416e6) / 8,
-                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "edea94b00aac4b0887c7d958b143b388e7f81245",
-                            "paper_1705_02408_gb300/csrc/common.cuh": "19791654a222d66c59cbf8d9ec58a96651c214e4"}},
-    # every k_prune (and empty k_prune_bulk) launch of the 8-query, 2-step capture:
-    # 889.10 MB of DRAM reads + writes over 2 x 12,658,585 expansions (profiles/k_prune_6d16k.md)
-    "k_prune": {"bytes_per_expansion": 889103104.0 / (2 * 12658585.0),
-                "sources": {"paper_1705_02408_gb300/csrc/search.cu": "ae56e781b445877c7f53644a9a0674fc854e7212"}},
+    # one row-pass launch over 8 roadmaps: 13.24 MB read + 90.36 MB written
+    "k_edges": {"bytes_per_roadmap": (13.236736e6 + 90.364672e6) / 8,
+                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "6b1b6e4b3bc3003eda3bf08dd80c10ae0f680e46",
+                            "paper_1705_02408_gb300/csrc/common.cuh": "f42dfc54d3c1a7692a7b0b6e1943805b4fb67da4"}},
+    # every k_prune and k_prune_bulk launch of the 8-query, 2-step capture:
+    # 888.84 MB of DRAM reads + writes over 2 x 12,658,585 expansions
+    "k_prune": {"bytes_per_expansion": 888836864.0 / (2 * 12658585.0),
+                "sources": {"paper_1705_02408_gb300/csrc/search.cu": "4cd7bfa51c4a0d8e8fa94bec80c11c0425eb23a5"}},
 }
 
 
@@ -335,14 +338,17 @@ def _traffic(kernel, units, key="bytes_per_roadmap"):
     return t[key] * units
 
 
-def roofline(kern, arm, res, steps):
-    """Roofline of the dominant kernel from the live CUDA-event timers."""
+def roofline(kern, arm, res, steps, name=None):
+    """Roofline of one kernel (default: the dominant one) from the live
+    CUDA-event timers."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    name, (launches, ms) = max(kern.items(), key=lambda kv: kv[1][1])
+    if name is None:
+        name = max(kern.items(), key=lambda kv: kv[1][1])[0]
+    launches, ms = kern[name]
     V = arm.cfg.n + 2
     B = len(arm.scenes)
     exps = sum(r.expansions for r in res)
@@ -371,7 +377,8 @@ def roofline(kern, arm, res, steps):
                 "ops_per_step": 39.0 * tests + 943.0 * edges,
                 "all_pairs_per_step": V * V * B,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
-    # HBM-bound search kernels: algorithmic bytes per step
+    # HBM-bound search kernels: algorithmic bytes per step, the 16-byte reverse edge
+    # record per plan-edge expansion and a 24-byte front entry per plan
     bytes_step = 16.0 * exps + 24.0 * plans
     per_launch = bytes_step * steps / max(1, launches)
     achieved = per_launch / (ms / launches / 1e3) / 1e9
