@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--sur-train-plans", type=int, default=200000,
                     help="Monte Carlo-labelled candidate plans to train the surrogate on")
     ap.add_argument("--sur-train-steps", type=int, default=2000)
@@ -300,6 +301,8 @@ def run_gpu(args, rank, world, local):
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e(arm, args, stream)
     log("timed region done")
+    if rank == 0 and not args.no_refine:
+        out["refine"] = refine_report(arm)
     if rank == 0 and world == 1 and not args.no_mixed:
         out["mixed_batch"] = mixed_report(args, stream)
     if rank == 0 and world == 1 and not args.no_surrogate:
@@ -452,6 +455,40 @@ def e2e(arm, args, stream):
 
 
 # ------------------------------------------------------------------ mixed batch
+def refine_report(arm, eps=0.05, rounds=8):
+    """Perception-bound refinement (Alg. 1 step 4) of the benchmark's queries on
+    their roadmaps: lock-step rounds of one batched search and one batched
+    certification; device time by CUDA events around the whole refinement."""
+    import collections
+    import torch
+    from paper_1705_02408_gb300.refine import refine_batch
+    rms = arm.build()
+    beta0 = [q.beta for q in arm.queries]
+    max_hits = [int(np.floor(eps * m[0])) for m in arm.mc]
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = refine_batch(arm.ws, rms, beta0, arm.mc, max_hits, max_rounds=rounds)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    first = [r.history[0] for r in res]
+    passed0 = [i for i, f in enumerate(first) if f[1] == "pass"]
+    ratios = [res[i].cost / first[i][2] for i in passed0 if res[i].certified]
+    return {"workload": f"the {len(res)} benchmark queries on their roadmaps, failure bound {eps} "
+                        f"(hits <= {max_hits[0]} of {arm.mc[0][0]}), at most {rounds} rounds",
+            "ms_per_batch": ms, "ms_per_query": ms / len(res),
+            "certified": sum(r.certified for r in res), "queries": len(res),
+            "rounds_mean": float(np.mean([r.rounds for r in res])), "rounds_max": max(r.rounds for r in res),
+            "searches": sum(r.rounds for r in res),
+            "mc_calls": sum(1 for r in res for h in r.history if h[1] in ("pass", "fail")),
+            "search_errors": sum(1 for r in res for h in r.history if h[1] == "error"),
+            "outcome_at_beta0": dict(collections.Counter(f[1] for f in first)),
+            "rescued_by_tightening": sum(1 for r, f in zip(res, first) if f[1] != "pass" and r.certified),
+            "cheaper_by_loosening": sum(1 for i in passed0 if res[i].cost < first[i][2]),
+            "cost_ratio_mean_vs_beta0": float(np.mean(ratios)) if ratios else None}
+
+
 def mixed_report(args, stream, count=256):
     """The batched workload: 256 queries, each on its own roadmap (dimension
     uniform over 2D/3D/6D; n log-uniform in [1000, 32000] for 3D/6D and [1000,
