@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
+    ap.add_argument("--no-perception", action="store_true")
     ap.add_argument("--sur-train-plans", type=int, default=200000,
                     help="Monte Carlo-labelled candidate plans to train the surrogate on")
     ap.add_argument("--sur-train-steps", type=int, default=2000)
@@ -303,6 +304,8 @@ def run_gpu(args, rank, world, local):
     log("timed region done")
     if rank == 0 and not args.no_refine:
         out["refine"] = refine_report(arm)
+    if rank == 0 and not args.no_perception:
+        out["perception_levels"] = perception_report(arm)
     if rank == 0 and world == 1 and not args.no_mixed:
         out["mixed_batch"] = mixed_report(args, stream)
     if rank == 0 and world == 1 and not args.no_surrogate:
@@ -455,6 +458,37 @@ def e2e(arm, args, stream):
 
 
 # ------------------------------------------------------------------ mixed batch
+def perception_report(arm, features=256, reps=10):
+    """Visible-feature perception levels (mpap_feature_levels) for the first
+    benchmark scene's 32^3 quality grid: eight yaw headings with a 45-degree
+    half field of view and range 0.5, and the all-direction table (range 2);
+    device arrays, CUDA events around `reps` launches."""
+    import torch
+    mp = arm.mp
+    sc = arm.scenes[0]
+    G = sc.cfg.grid_G
+    f = torch.from_numpy(scenegen.feature_points(sc, features)).cuda()
+    lo, hi = (torch.from_numpy(a).cuda() for a in (sc.box_lo, sc.box_hi))
+    out = {"workload": f"{features} features, {len(sc.box_lo)} boxes, {G}^3 cells"}
+    for key, Y, ch, rng in (("yaw8_fov45_range0.5", 8, float(np.float32(np.cos(np.pi / 4))), 0.5),
+                            ("all_direction_range2", 1, -2.0, 2.0)):
+        heads = torch.from_numpy(scenegen.yaw_headings(Y)).cuda()
+        for _ in range(2):
+            mp.feature_levels(3, lo, hi, f, G, heads, ch, rng)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            lv = mp.feature_levels(3, lo, hi, f, G, heads, ch, rng)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        pairs = Y * G ** 3 * features
+        out[key] = {"ms_per_table": ms, "cell_feature_pairs_per_s": pairs / (ms / 1e3),
+                    "mean_level": float(lv.float().mean().item())}
+    return out
+
+
 def refine_report(arm, eps=0.05, rounds=8):
     """Perception-bound refinement (Alg. 1 step 4) of the benchmark's queries on
     their roadmaps: lock-step rounds of one batched search and one batched

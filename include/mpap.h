@@ -390,6 +390,31 @@ int32_t mpap_search_candidates_batch(mpap_workspace* ws, uint32_t nq, uint32_t c
                                      int64_t* h, uint32_t* path_ptr, uint32_t* path,
                                      uint32_t path_cap, uint32_t* n, uint32_t* total, void* stream);
 
+/* Perception quality levels from mapped features: the visible-feature count of
+ * the Sec. 4.1 heuristic at the centre c = ((2i + 1) / (2G), ...) of every cell of
+ * a G^Dp grid (Dp = 2 for dim_kind 2, else 3), for each of Y = yaw_bins camera
+ * headings.  A feature f (d = f - c) counts when
+ *   |d|^2 <= range^2,
+ *   hx dx + hy dy >= cos_half_fov sqrt(dx^2 + dy^2)   (horizontal field of view of
+ *                                                      heading (hx, hy)), and
+ *   the closed segment c -> f meets no closed box;
+ * the level is min(count, K).  cos_half_fov <= -1 turns the field-of-view test
+ * off, which with one heading gives a scene's all-direction quality grid.  Every
+ * float operation is one IEEE operation in the order written.
+ *   box_lo, box_hi   float[nb][3] (z ignored in 2D), nb in [0, 1024]
+ *   features         float[n_features][3]
+ *   headings         float[yaw_bins][2], unit vectors chosen by the caller
+ *   levels           uint8[yaw_bins][G^Dp], x fastest (written)
+ *   mem              MPAP_MEM_HOST (copies in and out, synchronises the stream) or
+ *                    MPAP_MEM_DEVICE for all five arrays (asynchronous on stream).
+ * Returns MPAP_ERR_INVALID_ARG for a bad dimension, grid size (G a power of two
+ * in [1, 1024]), K outside [0, 255], null arrays, more than 2^22 features or
+ * yaw_bins G^Dp above 2^31. */
+int32_t mpap_feature_levels(int32_t dim_kind, int32_t nb, const float* box_lo, const float* box_hi,
+                            uint32_t n_features, const float* features, int32_t grid_G, uint32_t yaw_bins,
+                            const float* headings, float cos_half_fov, float range, int32_t K,
+                            uint8_t* levels, int32_t mem, void* stream);
+
 /* 48 trajectory features of each of n plans on one roadmap (input of the
  * surrogate).  Plan i is the host node sequence path[path_ptr[i] ..
  * path_ptr[i+1]) (at least 2 nodes).  Its Monte Carlo checkpoints (the M

@@ -67,6 +67,9 @@ def lib():
         L.orc_edge_eval.argtypes = [P, C.c_uint32, C.c_uint32, f32p, f32p, f32p, i64p, f32p, f32p]
         L.orc_segment_hits_box.restype = C.c_int
         L.orc_segment_hits_box.argtypes = [C.c_int, f32p, f32p, f32p, f32p]
+        L.orc_feature_levels.restype = None
+        L.orc_feature_levels.argtypes = [C.c_int, C.c_int, f32p, f32p, C.c_int, f32p, C.c_int, C.c_int, f32p,
+                                         C.c_float, C.c_float, C.c_int, u8p]
         L.orc_explore.restype = P
         L.orc_explore.argtypes = [P, C.c_int64, C.c_int64, C.c_uint32, C.c_int, C.c_uint64, C.c_int]
         L.orc_roadmap_from_csr_peaks.restype = P
@@ -275,6 +278,30 @@ def certify(rm: Roadmap, path, rollouts: int, seed: int, call_id: int, delta_fx:
                       hits)
     return dict(hits_loc=int(hits[0]), hits_coll=int(hits[1]), hits_any=int(hits[2]),
                 rollouts=int(hits[3]))
+
+
+def feature_levels(dp: int, box_lo, box_hi, features, G: int, headings=None, cos_half: float = -2.0,
+                   range_: float = 2.0, K: int = 24) -> np.ndarray:
+    """Perception levels [Y, G^dp] from mapped features: per yaw heading and grid
+    cell centre, the features in range, inside the horizontal field of view and
+    not occluded by a box, capped at K.  headings: [Y, 2] float32 unit vectors
+    (default one bin, (1, 0)); cos_half = -2 disables the field-of-view test."""
+    lo = np.ascontiguousarray(box_lo, np.float32).reshape(-1)
+    hi = np.ascontiguousarray(box_hi, np.float32).reshape(-1)
+    nb = lo.size // 3
+    if nb == 0:
+        lo = np.zeros(3, np.float32); hi = np.zeros(3, np.float32)
+    feat = np.ascontiguousarray(features, np.float32).reshape(-1)
+    nf = feat.size // 3
+    if nf == 0:
+        feat = np.zeros(3, np.float32)
+    head = np.ascontiguousarray([[1.0, 0.0]] if headings is None else headings, np.float32).reshape(-1)
+    Y = head.size // 2
+    cells = G ** dp
+    out = np.zeros(Y * cells, np.uint8)
+    lib().orc_feature_levels(int(dp), int(nb), lo, hi, int(nf), feat, int(G), int(Y), head,
+                             float(cos_half), float(range_), int(K), out)
+    return out.reshape(Y, cells)
 
 
 def group_width(lam: float, r: float) -> int:

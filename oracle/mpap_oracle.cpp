@@ -888,6 +888,55 @@ int orc_segment_hits_box(int dp, const float* a, const float* b, const float* lo
   return segment_hits_box(sc, 0, aa, d) ? 1 : 0;
 }
 
+// Perception levels from mapped features (the visible-feature count behind the
+// Sec. 4.1 heuristic).  For yaw bin y with horizontal heading (hx, hy) and the
+// centre c = ((2i + 1) / (2G), ...) of grid cell (i, j[, k]), the level is the
+// number of features f, capped at K, with
+//   |f - c|^2 <= range^2                      (in range),
+//   hx dx + hy dy >= cos_half sqrt(dx^2 + dy^2)   (inside the horizontal field of
+//                                              view; d = f - c),
+//   and the closed segment c -> f meeting no closed box (unoccluded).
+// Every float operation is written out in order; division and square root are
+// the IEEE ones.  out: [Y][G^Dp] (x fastest).
+void orc_feature_levels(int dp, int nb, const float* lo, const float* hi, int nf, const float* feat, int G,
+                        int Y, const float* head, float cos_half, float range, int K, uint8_t* out) {
+  Scene sc;
+  sc.dim = dp;
+  sc.nb = nb;
+  sc.lo.assign(lo, lo + 3 * nb);
+  sc.hi.assign(hi, hi + 3 * nb);
+  const float half = 0.5f / (float)G;
+  const float range2 = range * range;
+  const size_t cells = (size_t)G * G * (dp == 3 ? G : 1);
+  for (int y = 0; y < Y; ++y) {
+    const float hx = head[2 * y], hy = head[2 * y + 1];
+    for (size_t cell = 0; cell < cells; ++cell) {
+      const size_t i = cell % G, j = (cell / G) % G, k = (dp == 3) ? cell / ((size_t)G * G) : 0;
+      const float c[3] = {(float)(2 * i + 1) * half, (float)(2 * j + 1) * half,
+                          dp == 3 ? (float)(2 * k + 1) * half : 0.0f};
+      int count = 0;
+      for (int f = 0; f < nf; ++f) {
+        float d[3];
+        d[0] = feat[3 * f] - c[0];
+        d[1] = feat[3 * f + 1] - c[1];
+        d[2] = (dp == 3) ? feat[3 * f + 2] - c[2] : 0.0f;
+        float dxy2 = d[0] * d[0];
+        dxy2 = dxy2 + d[1] * d[1];
+        float r2 = dxy2;
+        if (dp == 3) r2 = r2 + d[2] * d[2];
+        if (r2 > range2) continue;
+        float dot = hx * d[0];
+        dot = dot + hy * d[1];
+        if (dot < cos_half * std::sqrt(dxy2)) continue;
+        bool blocked = false;
+        for (int b = 0; b < nb && !blocked; ++b) blocked = segment_hits_box(sc, b, c, d);
+        if (!blocked) ++count;
+      }
+      out[(size_t)y * cells + cell] = (uint8_t)(count < K ? count : K);
+    }
+  }
+}
+
 orc_result* orc_explore(const orc_roadmap* h, int64_t beta, int64_t Lambda, uint32_t max_iters,
                         int goal_termination, uint64_t max_plans, int check_interior) {
   orc_result* r = new orc_result();

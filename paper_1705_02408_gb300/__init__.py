@@ -38,7 +38,7 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_mlp_forward", "mpap_mlp_train_step", "mpap_tuning_get", "mpap_tuning_set",
            "mpap_tuning_clear", "mpap_tuning_export", "mpap_autotune_build", "mpap_autotune_search",
            "mpap_search_candidates_batch", "mpap_plan_features_batch", "mpap_roadmap_from_csr_peaks",
-           "mpap_roadmap_export_peaks", "mpap_roadmap_export_reverse"]
+           "mpap_roadmap_export_peaks", "mpap_roadmap_export_reverse", "mpap_feature_levels"]
 
 
 class mpap_scene(C.Structure):
@@ -183,6 +183,9 @@ def lib():
         L.mpap_roadmap_export_peaks.argtypes = [P, P, P, P]
         L.mpap_roadmap_export_reverse.restype = i32
         L.mpap_roadmap_export_reverse.argtypes = [P, P, P, P, P, P, P, P, P]
+        L.mpap_feature_levels.restype = i32
+        L.mpap_feature_levels.argtypes = [i32, i32, P, P, C.c_uint32, P, i32, C.c_uint32, P, C.c_float,
+                                          C.c_float, i32, P, i32, P]
         L.mpap_search_candidates_batch.restype = i32
         L.mpap_search_candidates_batch.argtypes = [P, C.c_uint32, C.c_uint32, P, P, P, P, C.c_uint32, P, P, P]
         L.mpap_plan_features_batch.restype = i32
@@ -463,6 +466,41 @@ def build_roadmaps(specs, rms=None, stream=None):
                                    _stream(stream))
     out = _adopt(specs, rms, hs)
     _check(rc, "mpap_build_roadmaps")
+    return out
+
+
+def feature_levels(dim_kind, box_lo, box_hi, features, grid_G, headings=None, cos_half_fov=-2.0, range_=2.0,
+                   K=24, stream=None):
+    """mpap_feature_levels: perception levels [Y, G^Dp] (uint8) from mapped features
+    for Y camera headings (default one, (1, 0)); numpy in and out, or CUDA tensors
+    (all arrays on the device; levels returned as a uint8 tensor)."""
+    dp = 2 if dim_kind == 2 else 3
+    cells = int(grid_G) ** dp
+    dev = hasattr(features, "is_cuda") and features.is_cuda
+    if dev:
+        import torch
+        head = headings if headings is not None else torch.tensor([[1.0, 0.0]], device=features.device)
+        Y = head.numel() // 2
+        out = torch.empty((Y, cells), dtype=torch.uint8, device=features.device)
+        nb = box_lo.numel() // 3
+        nf = features.numel() // 3
+        ptr = lambda a: C.c_void_p(a.data_ptr()) if a.numel() else None
+        _check(lib().mpap_feature_levels(int(dim_kind), nb, ptr(box_lo), ptr(box_hi), nf, ptr(features),
+                                         int(grid_G), Y, ptr(head), float(cos_half_fov), float(range_), int(K),
+                                         C.c_void_p(out.data_ptr()), MPAP_MEM_DEVICE, _stream(stream)),
+               "mpap_feature_levels")
+        return out
+    lo = np.ascontiguousarray(box_lo, np.float32).reshape(-1)
+    hi = np.ascontiguousarray(box_hi, np.float32).reshape(-1)
+    f = np.ascontiguousarray(features, np.float32).reshape(-1)
+    head = np.ascontiguousarray([[1.0, 0.0]] if headings is None else headings, np.float32).reshape(-1)
+    Y = head.size // 2
+    out = np.zeros((Y, cells), np.uint8)
+    vp = lambda a: a.ctypes.data_as(C.c_void_p) if a.size else None
+    _check(lib().mpap_feature_levels(int(dim_kind), lo.size // 3, vp(lo), vp(hi), f.size // 3, vp(f), int(grid_G),
+                                     Y, vp(head), float(cos_half_fov), float(range_), int(K),
+                                     out.ctypes.data_as(C.c_void_p), MPAP_MEM_HOST, _stream(stream)),
+           "mpap_feature_levels")
     return out
 
 

@@ -1,6 +1,7 @@
 // C ABI of libmpap (declared in include/mpap.h): argument validation and
 // dispatch to the roadmap, search and certification implementations.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -15,6 +16,9 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
                           mpap_result* outs, cudaStream_t st);
 int32_t search_fronts_impl(mpap_workspace* ws, uint32_t index, uint32_t* front_ptr, int64_t* cost,
                            int64_t* h, uint64_t cap, uint64_t* total, cudaStream_t st);
+int32_t feature_levels_impl(int dp, int nb, const float* lo, const float* hi, uint32_t nf, const float* feat,
+                            uint32_t G, uint32_t Y, const float* head, float cos_half, float range, int K,
+                            uint8_t* out, bool device, cudaStream_t st);
 int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,
                            const mpap_mc_params* mcs, uint32_t n, mpap_cert* outs, cudaStream_t st);
 int32_t certify_noalloc_impl(const mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,
@@ -448,6 +452,39 @@ int32_t mpap_search_candidates(mpap_workspace* ws, uint32_t index, uint32_t cap,
 int32_t mpap_plan_features(mpap_roadmap* rm, uint32_t n, const uint32_t* path_ptr, const uint32_t* path, float* feat,
                            void* stream) {
   return mpap::plan_features_impl(rm, n, path_ptr, path, feat, S(stream));
+}
+
+int32_t mpap_feature_levels(int32_t dim_kind, int32_t nb, const float* box_lo, const float* box_hi,
+                            uint32_t n_features, const float* features, int32_t grid_G, uint32_t yaw_bins,
+                            const float* headings, float cos_half_fov, float range, int32_t K,
+                            uint8_t* levels, int32_t mem, void* stream) {
+  if (dim_kind != 2 && dim_kind != 3 && dim_kind != 6) {
+    set_error("feature_levels: dim_kind must be 2, 3 or 6");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (grid_G < 1 || grid_G > 1024 || (grid_G & (grid_G - 1)) || K < 0 || K > 255 || yaw_bins < 1 ||
+      nb < 0 || nb > 1024 || n_features > (1u << 22) || !(range >= 0.0f) || std::isinf(range) ||
+      std::isnan(cos_half_fov)) {
+    set_error("feature_levels: need G a power of two in [1, 1024], K in [0, 255], yaw_bins >= 1, "
+              "0 <= nb <= 1024, at most 2^22 features, a finite range >= 0");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (mem != MPAP_MEM_HOST && mem != MPAP_MEM_DEVICE) {
+    set_error("feature_levels: mem must be MPAP_MEM_HOST or MPAP_MEM_DEVICE");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (!levels || !headings || (nb > 0 && (!box_lo || !box_hi)) || (n_features > 0 && !features)) {
+    set_error("feature_levels: null array");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  const int dp = dim_kind == 2 ? 2 : 3;
+  const unsigned long long cells = (unsigned long long)grid_G * grid_G * (dp == 3 ? grid_G : 1);
+  if ((unsigned long long)yaw_bins * cells > (1ull << 31)) {
+    set_error("feature_levels: yaw_bins x G^Dp above 2^31");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::feature_levels_impl(dp, nb, box_lo, box_hi, n_features, features, (uint32_t)grid_G, yaw_bins,
+                                   headings, cos_half_fov, range, K, levels, mem == MPAP_MEM_DEVICE, S(stream));
 }
 
 int32_t mpap_plan_features_batch(mpap_roadmap* const* rms, uint32_t n_rm, const uint32_t* plan_ptr,

@@ -200,6 +200,55 @@ def make_scene(name_or_cfg, seed: int, query_id: int = 0, **overrides) -> Scene:
                  sigma_fx=sigma_fx, shift=shift, delta_fx=delta_fx)
 
 
+FEATURE_OFFSET = 0.004   # features sit this far off the surface they mark
+
+
+def feature_points(scene: Scene, count: int = 256) -> np.ndarray:
+    """Mapped visual features for the visible-feature perception levels: ``count``
+    points, float32 [count, 3] (z = 0 in 2D), drawn alternately on the faces of
+    the scene's boxes and on the walls of the unit square/cube, each moved
+    FEATURE_OFFSET off its surface into free space (outward from a box, inward
+    from a wall); a point inside or on another box is drawn again.
+    Deterministic in the scene's seed."""
+    dp = pos_dims(scene.cfg.dim_kind)
+    rng = np.random.default_rng([int(scene.seed), int(scene.cfg.dim_kind), 0x46454154])
+    nb = len(scene.box_lo)
+    blo = scene.box_lo.astype(np.float64)[:, :dp]
+    bhi = scene.box_hi.astype(np.float64)[:, :dp]
+    out = np.zeros((count, 3))
+    k = 0
+    for attempt in range(64 * count + 64):
+        if k == count:
+            break
+        on_box = nb > 0 and attempt % 2 == 0
+        axis = int(rng.integers(0, dp))
+        side = int(rng.integers(0, 2))
+        u = rng.random(3)
+        if on_box:
+            b = int(rng.integers(0, nb))
+            lo, hi = scene.box_lo[b].astype(np.float64), scene.box_hi[b].astype(np.float64)
+            p = lo + u * (hi - lo)
+            p[axis] = (hi[axis] + FEATURE_OFFSET) if side else (lo[axis] - FEATURE_OFFSET)
+        else:
+            p = u.copy()
+            p[axis] = (1.0 - FEATURE_OFFSET) if side else FEATURE_OFFSET
+        p = np.clip(p, 0.0, 1.0)
+        if dp == 2:
+            p[2] = 0.0
+        if nb and ((p[None, :dp] >= blo) & (p[None, :dp] <= bhi)).all(1).any():
+            continue           # inside (or on) another box: draw again
+        out[k] = p
+        k += 1
+    return out[:k].astype(np.float32)
+
+
+def yaw_headings(bins: int) -> np.ndarray:
+    """Unit camera headings (cos, sin) of ``bins`` evenly spaced yaw angles
+    2 pi b / bins, float32 [bins, 2] (rounded once from double)."""
+    a = 2.0 * np.pi * np.arange(bins) / bins
+    return np.stack([np.cos(a), np.sin(a)], 1).astype(np.float32)
+
+
 def scaled_config(dim_kind: int, n: int) -> Config:
     """A configuration of dimension ``dim_kind`` resized to ``n`` samples with the
     connection radius rescaled so that the mean out-degree stays near that of the

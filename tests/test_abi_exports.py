@@ -71,3 +71,18 @@ def test_host_side_argument_checks(libpath):
     with pytest.raises(mp.MpapError) as e:
         mp.Workspace(0)
     assert e.value.status == mp.MPAP_ERR_INVALID_ARG
+
+
+def test_feature_levels_argument_checks(libpath):
+    """Invalid sizes are rejected on the host before any device work."""
+    import numpy as np
+    import paper_1705_02408_gb300 as mp
+    nob = np.zeros((0, 3), np.float32)
+    f = np.zeros((4, 3), np.float32)
+    for kw in (dict(grid_G=6), dict(grid_G=2048), dict(K=256), dict(range_=-1.0), dict(dim_kind=4),
+               dict(headings=np.zeros((0, 2), np.float32))):
+        args = dict(dim_kind=2, box_lo=nob, box_hi=nob, features=f, grid_G=4)
+        args.update(kw)
+        with pytest.raises(mp.MpapError) as e:
+            mp.feature_levels(**args)
+        assert e.value.status == mp.MPAP_ERR_INVALID_ARG
