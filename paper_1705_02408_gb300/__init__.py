@@ -480,6 +480,9 @@ def feature_levels(dim_kind, box_lo, box_hi, features, grid_G, headings=None, co
     if dev:
         import torch
         head = headings if headings is not None else torch.tensor([[1.0, 0.0]], device=features.device)
+        for a in (box_lo, box_hi, features, head):
+            if a.dtype != torch.float32 or not a.is_cuda or not a.is_contiguous():
+                raise ValueError("feature_levels: device arrays must be contiguous float32 CUDA tensors")
         Y = head.numel() // 2
         out = torch.empty((Y, cells), dtype=torch.uint8, device=features.device)
         nb = box_lo.numel() // 3
