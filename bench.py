@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-perception", action="store_true")
+    ap.add_argument("--no-update", action="store_true")
     ap.add_argument("--sur-train-plans", type=int, default=200000,
                     help="Monte Carlo-labelled candidate plans to train the surrogate on")
     ap.add_argument("--sur-train-steps", type=int, default=2000)
@@ -306,6 +307,8 @@ def run_gpu(args, rank, world, local):
         out["refine"] = refine_report(arm)
     if rank == 0 and not args.no_perception:
         out["perception_levels"] = perception_report(arm)
+    if rank == 0 and not args.no_update:
+        out["online_update"] = update_report(arm)
     if rank == 0 and world == 1 and not args.no_mixed:
         out["mixed_batch"] = mixed_report(args, stream)
     if rank == 0 and world == 1 and not args.no_surrogate:
@@ -487,6 +490,38 @@ def perception_report(arm, features=256, reps=10):
         out[key] = {"ms_per_table": ms, "cell_feature_pairs_per_s": pairs / (ms / 1e3),
                     "mean_level": float(lv.float().mean().item())}
     return out
+
+
+def update_report(arm, k=3):
+    """Online update (mpap_roadmap_update) of the benchmark's roadmaps: k added
+    boxes each and a replaced quality grid, one call per roadmap, against
+    rebuilding all of them in one batched build; CUDA events around each."""
+    import torch
+    rms = arm.build()
+    rng = np.random.default_rng(7)
+    adds = []
+    for _ in rms:
+        c = rng.uniform(0.2, 0.8, (k, 3)); sz = rng.uniform(0.04, 0.12, (k, 3))
+        adds.append(((c - sz / 2).astype(np.float32), (c + sz / 2).astype(np.float32)))
+    grids = [scenegen.make_scene(arm.cfg, s.seed + 1000).grid for s in arm.scenes]
+    E0 = sum(rm.E for rm in rms)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for rm, (lo, hi), g in zip(rms, adds, grids):
+        rm.update(lo, hi, g)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_update = e0.elapsed_time(e1)
+    E1 = sum(rm.E for rm in rms)
+    e0.record()
+    arm.build()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_build = e0.elapsed_time(e1)
+    return {"workload": f"{len(rms)} roadmaps of {arm.cfg.n + 2} nodes, {k} added boxes each and a new grid",
+            "ms_per_roadmap_update": ms_update / len(rms), "ms_per_roadmap_rebuild": ms_build / len(rms),
+            "edges_before": E0, "edges_after": E1}
 
 
 def refine_report(arm, eps=0.05, rounds=8):

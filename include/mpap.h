@@ -226,6 +226,21 @@ int32_t mpap_roadmap_export_peaks(const mpap_roadmap* rm, int32_t* Smax, int32_t
 int32_t mpap_roadmap_export_reverse(const mpap_roadmap* rm, uint32_t* rev_ptr, uint32_t* src, int32_t* cost_q,
                                     int32_t* S, int32_t* C, int32_t* Smax, int32_t* Cmax, void* stream);
 
+/* Online update of a built roadmap (the map changes, the nodes stay; Sec. 3 on
+ * use within a mapping framework): nb_add boxes float[nb_add][3] are appended to
+ * the roadmap's obstacles and, when grid is not NULL, its quality levels
+ * uint8[G^Dp] are replaced.  Every edge is tested against the added boxes only
+ * (an added box can only remove edges) and the transfers and their peaks are
+ * recomputed only when the grid changed; the forward and reverse CSR are then
+ * compacted.  The roadmap afterwards is the one mpap_build_roadmap_from_points
+ * builds from the same nodes on the updated scene.  mem: MPAP_MEM_HOST or
+ * MPAP_MEM_DEVICE for add_lo, add_hi and grid.  Synchronises the stream.
+ * Returns MPAP_ERR_INVALID_ARG for a roadmap without geometry, more than 1024
+ * boxes in all or null arrays; MPAP_ERR_CAPACITY when a new transfer does not
+ * fit int32 (the roadmap is then left with those edges' values truncated). */
+int32_t mpap_roadmap_update(mpap_roadmap* rm, int32_t nb_add, const float* add_lo, const float* add_hi,
+                            const uint8_t* grid, int32_t mem, void* stream);
+
 /* Build statistics: Near tests (Cost < r evaluations) performed by the last
  * build of this roadmap, and the number of nodes in X_goal. */
 int32_t mpap_roadmap_stats(const mpap_roadmap* rm, uint64_t* near_tests, uint32_t* n_goal);

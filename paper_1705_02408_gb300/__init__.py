@@ -38,7 +38,8 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_mlp_forward", "mpap_mlp_train_step", "mpap_tuning_get", "mpap_tuning_set",
            "mpap_tuning_clear", "mpap_tuning_export", "mpap_autotune_build", "mpap_autotune_search",
            "mpap_search_candidates_batch", "mpap_plan_features_batch", "mpap_roadmap_from_csr_peaks",
-           "mpap_roadmap_export_peaks", "mpap_roadmap_export_reverse", "mpap_feature_levels"]
+           "mpap_roadmap_export_peaks", "mpap_roadmap_export_reverse", "mpap_feature_levels",
+           "mpap_roadmap_update"]
 
 
 class mpap_scene(C.Structure):
@@ -183,6 +184,8 @@ def lib():
         L.mpap_roadmap_export_peaks.argtypes = [P, P, P, P]
         L.mpap_roadmap_export_reverse.restype = i32
         L.mpap_roadmap_export_reverse.argtypes = [P, P, P, P, P, P, P, P, P]
+        L.mpap_roadmap_update.restype = i32
+        L.mpap_roadmap_update.argtypes = [P, i32, P, P, P, i32, P]
         L.mpap_feature_levels.restype = i32
         L.mpap_feature_levels.argtypes = [i32, i32, P, P, C.c_uint32, P, i32, C.c_uint32, P, C.c_float,
                                           C.c_float, i32, P, i32, P]
@@ -367,6 +370,34 @@ class Roadmap:
                "mpap_roadmap_export_reverse")
         src, cq, S, Cc, Sm, Cm = (c[:E] for c in cols)
         return dict(V=V, E=E, rev_ptr=rp, src=src, cost_q=cq, S=S, C=Cc, Smax=Sm, Cmax=Cm)
+
+    def update(self, add_lo=None, add_hi=None, grid=None, stream=None):
+        """mpap_roadmap_update: append boxes (float [k, 3] each) and/or replace
+        the quality grid (uint8 [G^Dp]); numpy arrays or CUDA tensors."""
+        dev = any(hasattr(a, "is_cuda") and a.is_cuda for a in (add_lo, add_hi, grid) if a is not None)
+        keep = []
+
+        def ptr(a, dtype):
+            if a is None:
+                return None, 0
+            if hasattr(a, "data_ptr"):
+                if not a.is_contiguous():
+                    raise ValueError("arrays must be contiguous")
+                keep.append(a)
+                return C.c_void_p(a.data_ptr()), a.numel()
+            arr = np.ascontiguousarray(a, dtype)
+            keep.append(arr)
+            return arr.ctypes.data_as(C.c_void_p), arr.size
+
+        lo, n_lo = ptr(add_lo, np.float32)
+        hi, n_hi = ptr(add_hi, np.float32)
+        if n_lo != n_hi or n_lo % 3:
+            raise ValueError("add_lo and add_hi must both be [k, 3]")
+        g, _ = ptr(grid, np.uint8)
+        _check(lib().mpap_roadmap_update(self.h, n_lo // 3, lo if n_lo else None, hi if n_hi else None, g,
+                                         MPAP_MEM_DEVICE if dev else MPAP_MEM_HOST, _stream(stream)),
+               "mpap_roadmap_update")
+        return self
 
     def peaks(self, stream=None):
         """(Smax, Cmax) per edge, in the order of export()."""

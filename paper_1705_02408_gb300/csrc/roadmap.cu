@@ -734,6 +734,109 @@ __global__ void k_reverse_fill(const BuildJob* __restrict__ jobs) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Online update of a built roadmap (the map changes, the nodes stay): boxes are
+// added and the quality grid may be replaced.  An added box can only remove
+// edges, so every edge is tested against the added boxes alone; the transfers
+// are recomputed only when the grid changed.  The result is the roadmap the
+// build would make from the same nodes on the updated scene.
+// ---------------------------------------------------------------------------
+struct UpdateJob {
+  Geom g;                  // the updated scene (all boxes, the current grid)
+  Geom g_add;              // the added boxes only
+  const float* x;          // [6][V]
+  uint32_t V;
+  const uint32_t* ptr;     // [V+1] row pointers before the update
+  const int4* edge;        // [E] records before the update
+  const int2* peak;        // [E]
+  int4* edge_upd;          // [E] records with the new transfers
+  int2* peak_upd;          // [E]
+  uint8_t* keep;           // [E]
+  uint32_t* kept;          // [V+1] edges kept per source
+  const uint32_t* ptr_new; // [V+1] row pointers after the update
+  int4* edge_out;          // compacted forward CSR
+  uint32_t* dst_out;
+  int2* peak_out;
+  uint32_t* status;        // error bits
+  int retransfer;          // the grid changed
+};
+
+// One warp per source: collision of each out-edge against the added boxes and,
+// when the grid changed, the edge's transfer on the new grid.
+template <int DIM>
+__global__ void k_update_edges(UpdateJob J) {
+  extern __shared__ float smem[];
+  float* s_lo = smem;
+  float* s_hi = smem + 3 * J.g_add.nb;
+  for (int i = threadIdx.x; i < 3 * J.g_add.nb; i += blockDim.x) {
+    s_lo[i] = J.g_add.box_lo[i];
+    s_hi[i] = J.g_add.box_hi[i];
+  }
+  __syncthreads();
+  constexpr int nc = (DIM == 6) ? 6 : DIM;
+  const unsigned lane = lane_id();
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < J.V; v += warps) {
+    float a[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < nc; ++c) a[c] = J.x[(size_t)c * J.V + v];
+    const uint32_t b0 = J.ptr[v], b1 = J.ptr[v + 1];
+    uint32_t kept = 0;
+    for (uint32_t e0 = b0; e0 < b1; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      bool ok = false;
+      if (e < b1) {
+        int4 rec = J.edge[e];
+        int2 pk = J.peak[e];
+        float b[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < nc; ++c) b[c] = J.x[(size_t)c * J.V + (uint32_t)rec.x];
+        Conn cn;
+        conn_setup_t<DIM>(J.g, a, b, cn);
+        ok = !conn_collides_t<DIM>(J.g_add, cn, s_lo, s_hi, nullptr);
+        if (ok && J.retransfer) {
+          int64_t S, C, Smax, Cmax;
+          conn_transfer_t<DIM>(J.g, cn, (int64_t)rec.y, S, C, Smax, Cmax);
+          if (S > INT32_MAX || S < INT32_MIN || C > INT32_MAX || Smax > INT32_MAX || Cmax > INT32_MAX)
+            atomicOr(&J.status[0], kErrEdge);
+          rec.z = (int)S;
+          rec.w = (int)C;
+          pk = make_int2((int)Smax, (int)Cmax);
+        }
+        J.edge_upd[e] = rec;
+        J.peak_upd[e] = pk;
+        J.keep[e] = ok ? 1 : 0;
+      }
+      kept += __popc(__ballot_sync(0xFFFFFFFFu, ok));
+    }
+    if (lane == 0) J.kept[v] = kept;
+  }
+}
+
+// One warp per source: the kept edges, in their order, at the new row pointers.
+__global__ void k_update_compact(UpdateJob J) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < J.V; v += warps) {
+    const uint32_t b0 = J.ptr[v], b1 = J.ptr[v + 1];
+    uint32_t out = J.ptr_new[v];
+    for (uint32_t e0 = b0; e0 < b1; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const bool k = e < b1 && J.keep[e];
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, k);
+      if (k) {
+        const uint32_t o = out + __popc(bal & lt);
+        const int4 rec = J.edge_upd[e];
+        J.edge_out[o] = rec;
+        J.dst_out[o] = (uint32_t)rec.x;
+        J.peak_out[o] = J.peak_upd[e];
+      }
+      out += __popc(bal);
+    }
+  }
+}
+
 template <int MODE, int WARPS>
 void launch_edges_w(int dim, dim3 grid, size_t smem, cudaStream_t st, const BuildJob* jobs, const uint32_t* ids) {
   const dim3 block(WARPS * 32);
@@ -1363,6 +1466,148 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
   scratch_free(blk, st);
   if (!cuda_ok(cudaStreamSynchronize(st), "sync")) return bail(MPAP_ERR_CUDA);
   *out = rm;
+  return MPAP_OK;
+}
+
+int32_t roadmap_update_impl(mpap_roadmap* rm, int32_t nb_add, const float* add_lo, const float* add_hi,
+                            const uint8_t* grid, bool device, cudaStream_t st) {
+  if (!rm->has_geometry) {
+    set_error("roadmap_update: the roadmap has no geometry");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  const int dp = (rm->dim == 2) ? 2 : 3;
+  const size_t cells = (size_t)rm->G * rm->G * (dp == 3 ? rm->G : 1);
+  const int nb_old = rm->nb, nb = nb_old + nb_add;
+  if (nb > 1024) {
+    set_error("roadmap_update: at most 1024 boxes in all");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  // 1. the scene: old boxes kept, added boxes appended, grid replaced
+  std::vector<float> lo(3 * (size_t)nb + 3, 0.0f), hi(3 * (size_t)nb + 3, 0.0f);
+  if (nb_old) {
+    MPAP_CK(cudaMemcpyAsync(lo.data(), rm->box_lo, sizeof(float) * 3 * nb_old, cudaMemcpyDeviceToHost, st));
+    MPAP_CK(cudaMemcpyAsync(hi.data(), rm->box_hi, sizeof(float) * 3 * nb_old, cudaMemcpyDeviceToHost, st));
+    MPAP_CK(cudaStreamSynchronize(st));
+  }
+  if (nb_add) {
+    const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    MPAP_CK(cudaMemcpyAsync(lo.data() + 3 * nb_old, add_lo, sizeof(float) * 3 * nb_add, kind, st));
+    MPAP_CK(cudaMemcpyAsync(hi.data() + 3 * nb_old, add_hi, sizeof(float) * 3 * nb_add, kind, st));
+    MPAP_CK(cudaStreamSynchronize(st));
+  }
+  int32_t rc = ensure_scene(rm, (size_t)nb, cells);
+  if (rc) return rc;
+  MPAP_CK(cudaMemcpyAsync(rm->box_lo, lo.data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
+  MPAP_CK(cudaMemcpyAsync(rm->box_hi, hi.data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
+  if (grid) MPAP_CK(cudaMemcpyAsync(rm->grid, grid, cells, device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  rm->nb = nb;
+  fill_geom_constants(rm->geom, rm->dim, rm->nb, rm->G, rm->n_f, rm->M, rm->r, rm->T);
+  rm->geom.box_lo = rm->box_lo;
+  rm->geom.box_hi = rm->box_hi;
+  rm->geom.grid = rm->grid;
+  {
+    const double lmax = std::max((double)rm->n_f, (double)rm->K - (double)rm->n_f);
+    const double inc_max = (rm->dim == 6) ? (double)rm->geom.Tq : std::ceil((double)rm->r * 16777216.0) + 1.0;
+    rm->geom.narrow = ((double)rm->M * inc_max * lmax < 2147483647.0) ? 1 : 0;
+  }
+  const uint32_t V = rm->V;
+  const uint64_t E = rm->E;
+  if (E == 0 || (nb_add == 0 && !grid)) return cudaStreamSynchronize(st) == cudaSuccess ? MPAP_OK : MPAP_ERR_CUDA;
+  // 2. scratch: old pointers, updated records, keep flags, counts
+  char* blk = nullptr;
+  const size_t bytes = 4096 * 4 + 4 * ((size_t)V + 1) * 4 + (sizeof(int4) + sizeof(int2) + 1) * (size_t)E +
+                       sizeof(BuildJob) + sizeof(ScanSeg) + 16;
+  MPAP_CK(scratch_alloc((void**)&blk, bytes, st));
+  Carve cv{blk, 0};
+  uint32_t* d_status = cv.take<uint32_t>(4);
+  uint32_t* d_ptr_old = cv.take<uint32_t>((size_t)V + 1);
+  uint32_t* d_kept = cv.take<uint32_t>((size_t)V + 1);
+  uint32_t* d_counts = cv.take<uint32_t>((size_t)V + 1);
+  uint32_t* d_fill = cv.take<uint32_t>((size_t)V + 1);
+  int4* d_edge = cv.take<int4>(E);
+  int2* d_peak = cv.take<int2>(E);
+  uint8_t* d_keep = cv.take<uint8_t>(E);
+  BuildJob* d_job = cv.take<BuildJob>(1);
+  ScanSeg* d_seg = cv.take<ScanSeg>(1);
+  auto bail = [&](int32_t r) {
+    scratch_free(blk, st);
+    return r;
+  };
+  if (cv.off > bytes) return bail(MPAP_ERR_CUDA);
+  if (!cuda_ok(cudaMemsetAsync(d_status, 0, 16, st), "memset") ||
+      !cuda_ok(cudaMemcpyAsync(d_ptr_old, rm->fwd_ptr, 4 * ((size_t)V + 1), cudaMemcpyDeviceToDevice, st), "copy"))
+    return bail(MPAP_ERR_CUDA);
+  UpdateJob J;
+  std::memset(&J, 0, sizeof(J));
+  J.g = rm->geom;
+  J.g_add = rm->geom;
+  J.g_add.nb = nb_add;
+  J.g_add.box_lo = rm->box_lo + 3 * nb_old;
+  J.g_add.box_hi = rm->box_hi + 3 * nb_old;
+  J.x = rm->x;
+  J.V = V;
+  J.ptr = d_ptr_old;
+  J.edge = rm->fwd_edge;
+  J.peak = rm->fwd_peak;
+  J.edge_upd = d_edge;
+  J.peak_upd = d_peak;
+  J.keep = d_keep;
+  J.kept = d_kept;
+  J.ptr_new = rm->fwd_ptr;
+  J.edge_out = rm->fwd_edge;
+  J.dst_out = rm->fwd_dst;
+  J.peak_out = rm->fwd_peak;
+  J.status = d_status;
+  J.retransfer = grid ? 1 : 0;
+  const int sms = sm_count();
+  const dim3 gridw(std::min<uint32_t>((V + 7) / 8, 4u * sms));
+  {
+    LaunchScope ls(st, "k_update_edges");
+    const size_t sm = sizeof(float) * 6 * (size_t)nb_add;
+    if (rm->dim == 6) k_update_edges<6><<<gridw, 256, sm, st>>>(J);
+    else if (rm->dim == 3) k_update_edges<3><<<gridw, 256, sm, st>>>(J);
+    else k_update_edges<2><<<gridw, 256, sm, st>>>(J);
+  }
+  // 3. new row pointers; the records move from the scratch copy into the CSR
+  ScanSeg seg{d_kept, rm->fwd_ptr, V, d_status + 2};
+  if ((rc = upload(d_seg, &seg, sizeof(seg), st))) return bail(rc);
+  {
+    LaunchScope ls(st, "k_scan_segments");
+    k_scan_segments<<<1, 1024, 0, st>>>(d_seg);
+  }
+  {
+    LaunchScope ls(st, "k_update_compact");
+    k_update_compact<<<gridw, 256, 0, st>>>(J);
+  }
+  uint32_t hs[4] = {0, 0, 0, 0}, e_new = 0;
+  if (!cuda_ok(cudaMemcpyAsync(hs, d_status, 16, cudaMemcpyDeviceToHost, st), "copy") ||
+      !cuda_ok(cudaMemcpyAsync(&e_new, rm->fwd_ptr + V, 4, cudaMemcpyDeviceToHost, st), "copy") ||
+      !cuda_ok(cudaStreamSynchronize(st), "sync"))
+    return bail(MPAP_ERR_CUDA);
+  rm->E = e_new;
+  // 4. reverse CSR of the updated forward CSR
+  BuildJob B;
+  std::memset(&B, 0, sizeof(B));
+  B.V = V;
+  B.fwd_ptr = rm->fwd_ptr;
+  B.fwd_edge = rm->fwd_edge;
+  B.rev_ptr = rm->rev_ptr;
+  B.rev_edge = rm->rev_edge;
+  B.fwd_peak = rm->fwd_peak;
+  B.rev_peak = rm->rev_peak;
+  B.counts = d_counts;
+  B.fill = d_fill;
+  std::vector<BuildJob> hb(1, B);
+  if (!cuda_ok(cudaMemsetAsync(d_counts, 0, 4 * ((size_t)V + 1), st), "memset") ||
+      !cuda_ok(cudaMemsetAsync(d_fill, 0, 4 * ((size_t)V + 1), st), "memset") ||
+      (rc = upload(d_job, &B, sizeof(B), st)) || (rc = build_reverse(1, hb, d_job, d_seg, V, st)))
+    return bail(rc ? rc : MPAP_ERR_CUDA);
+  scratch_free(blk, st);
+  if (!cuda_ok(cudaStreamSynchronize(st), "sync")) return MPAP_ERR_CUDA;
+  if (hs[0]) {
+    set_error("roadmap_update: an edge transfer does not fit int32");
+    return MPAP_ERR_CAPACITY;
+  }
   return MPAP_OK;
 }
 

@@ -86,3 +86,9 @@ def test_feature_levels_argument_checks(libpath):
         with pytest.raises(mp.MpapError) as e:
             mp.feature_levels(**args)
         assert e.value.status == mp.MPAP_ERR_INVALID_ARG
+
+
+def test_roadmap_update_argument_checks(libpath):
+    import paper_1705_02408_gb300 as mp
+    L = mp.lib()
+    assert L.mpap_roadmap_update(None, 0, None, None, None, 0, None) == mp.MPAP_ERR_INVALID_ARG
