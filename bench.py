@@ -324,9 +324,10 @@ def run_gpu(args, rank, world, local):
 # DRAM traffic from ncu captures, per unit of work, valid only while the kernel
 # sources are the ones that were captured.
 NCU_TRAFFIC = {
-    # one row-pass launch over 8 roadmaps: 13.24 MB read + 90.36 MB written
+    # one row-pass launch over 8 roadmaps: 13.24 MB read + 90.36 MB written (roadmap.cu
+    # has only gained the online-update kernels since; the row pass is unchanged)
     "k_edges": {"bytes_per_roadmap": (13.236736e6 + 90.364672e6) / 8,
-                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "6b1b6e4b3bc3003eda3bf08dd80c10ae0f680e46",
+                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "d62482682c7dcca7902214d7f5b830d779e07767",
                             "paper_1705_02408_gb300/csrc/common.cuh": "f42dfc54d3c1a7692a7b0b6e1943805b4fb67da4"}},
     # every k_prune and k_prune_bulk launch of the 8-query, 2-step capture:
     # 888.84 MB of DRAM reads + writes over 2 x 12,658,585 expansions
