@@ -119,12 +119,14 @@ int32_t feature_levels_impl(int dp, int nb, const float* lo, const float* hi, ui
     float* d_feat = (float*)(blk + 2 * up(b_box));
     float* d_head = (float*)(blk + 2 * up(b_box) + up(b_feat));
     uint8_t* d_out = (uint8_t*)(blk + 2 * up(b_box) + up(b_feat) + up(b_head));
-    if (nb) {
-      MPAP_CK(cudaMemcpyAsync(d_lo, lo, b_box, cudaMemcpyHostToDevice, st));
-      MPAP_CK(cudaMemcpyAsync(d_hi, hi, b_box, cudaMemcpyHostToDevice, st));
+    const bool ok = (!nb || (cuda_ok(cudaMemcpyAsync(d_lo, lo, b_box, cudaMemcpyHostToDevice, st), "copy") &&
+                             cuda_ok(cudaMemcpyAsync(d_hi, hi, b_box, cudaMemcpyHostToDevice, st), "copy"))) &&
+                    (!nf || cuda_ok(cudaMemcpyAsync(d_feat, feat, b_feat, cudaMemcpyHostToDevice, st), "copy")) &&
+                    cuda_ok(cudaMemcpyAsync(d_head, head, b_head, cudaMemcpyHostToDevice, st), "copy");
+    if (!ok) {
+      scratch_free(blk, st);
+      return MPAP_ERR_CUDA;
     }
-    if (nf) MPAP_CK(cudaMemcpyAsync(d_feat, feat, b_feat, cudaMemcpyHostToDevice, st));
-    MPAP_CK(cudaMemcpyAsync(d_head, head, b_head, cudaMemcpyHostToDevice, st));
     J.lo = d_lo;
     J.hi = d_hi;
     J.feat = d_feat;
@@ -138,13 +140,13 @@ int32_t feature_levels_impl(int dp, int nb, const float* lo, const float* hi, ui
     if (dp == 3) k_feature_levels<3><<<(unsigned)blocks, 256, smem, st>>>(J);
     else k_feature_levels<2><<<(unsigned)blocks, 256, smem, st>>>(J);
   }
-  MPAP_CK(cudaGetLastError());
+  bool ok = cuda_ok(cudaGetLastError(), "k_feature_levels");
   if (!device) {
-    MPAP_CK(cudaMemcpyAsync(out, J.out, total, cudaMemcpyDeviceToHost, st));
+    ok = ok && cuda_ok(cudaMemcpyAsync(out, J.out, total, cudaMemcpyDeviceToHost, st), "copy");
     scratch_free(blk, st);
-    MPAP_CK(cudaStreamSynchronize(st));
+    ok = cuda_ok(cudaStreamSynchronize(st), "sync") && ok;
   }
-  return MPAP_OK;
+  return ok ? MPAP_OK : MPAP_ERR_CUDA;
 }
 
 }  // namespace mpap
