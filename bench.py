@@ -494,9 +494,9 @@ def perception_report(arm, features=256, reps=10):
 
 
 def update_report(arm, k=3):
-    """Online update (mpap_roadmap_update) of the benchmark's roadmaps: k added
-    boxes each and a replaced quality grid, one call per roadmap, against
-    rebuilding all of them in one batched build; CUDA events around each."""
+    """Online update (mpap_roadmap_update_batch) of the benchmark's roadmaps: k
+    added boxes each and a replaced quality grid, in one call, against rebuilding
+    all of them in one batched build; CUDA events around each."""
     import torch
     rms = arm.build()
     rng = np.random.default_rng(7)
@@ -509,8 +509,7 @@ def update_report(arm, k=3):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for rm, (lo, hi), g in zip(rms, adds, grids):
-        rm.update(lo, hi, g)
+    arm.mp.roadmap_update_batch(rms, [a[0] for a in adds], [a[1] for a in adds], grids)
     e1.record()
     torch.cuda.synchronize()
     ms_update = e0.elapsed_time(e1)
@@ -520,7 +519,8 @@ def update_report(arm, k=3):
     e1.record()
     torch.cuda.synchronize()
     ms_build = e0.elapsed_time(e1)
-    return {"workload": f"{len(rms)} roadmaps of {arm.cfg.n + 2} nodes, {k} added boxes each and a new grid",
+    return {"workload": f"{len(rms)} roadmaps of {arm.cfg.n + 2} nodes, {k} added boxes each and a new grid, "
+                        "one batched update call",
             "ms_per_roadmap_update": ms_update / len(rms), "ms_per_roadmap_rebuild": ms_build / len(rms),
             "edges_before": E0, "edges_after": E1}
 

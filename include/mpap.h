@@ -241,6 +241,15 @@ int32_t mpap_roadmap_export_reverse(const mpap_roadmap* rm, uint32_t* rev_ptr, u
 int32_t mpap_roadmap_update(mpap_roadmap* rm, int32_t nb_add, const float* add_lo, const float* add_hi,
                             const uint8_t* grid, int32_t mem, void* stream);
 
+/* mpap_roadmap_update for n distinct roadmaps in one pass (one launch per
+ * dimension for the edge tests, one scan, one compaction and one reverse build
+ * for all of them): roadmap j gets nb_add[j] boxes add_lo[j], add_hi[j] and, when
+ * grids is not NULL and grids[j] is not NULL, the levels grids[j].  Errors as for
+ * mpap_roadmap_update, and MPAP_ERR_INVALID_ARG for a roadmap given twice. */
+int32_t mpap_roadmap_update_batch(mpap_roadmap* const* rms, uint32_t n, const int32_t* nb_add,
+                                  const float* const* add_lo, const float* const* add_hi,
+                                  const uint8_t* const* grids, int32_t mem, void* stream);
+
 /* Build statistics: Near tests (Cost < r evaluations) performed by the last
  * build of this roadmap, and the number of nodes in X_goal. */
 int32_t mpap_roadmap_stats(const mpap_roadmap* rm, uint64_t* near_tests, uint32_t* n_goal);

@@ -39,7 +39,7 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_tuning_clear", "mpap_tuning_export", "mpap_autotune_build", "mpap_autotune_search",
            "mpap_search_candidates_batch", "mpap_plan_features_batch", "mpap_roadmap_from_csr_peaks",
            "mpap_roadmap_export_peaks", "mpap_roadmap_export_reverse", "mpap_feature_levels",
-           "mpap_roadmap_update"]
+           "mpap_roadmap_update", "mpap_roadmap_update_batch"]
 
 
 class mpap_scene(C.Structure):
@@ -186,6 +186,9 @@ def lib():
         L.mpap_roadmap_export_reverse.argtypes = [P, P, P, P, P, P, P, P, P]
         L.mpap_roadmap_update.restype = i32
         L.mpap_roadmap_update.argtypes = [P, i32, P, P, P, i32, P]
+        L.mpap_roadmap_update_batch.restype = i32
+        L.mpap_roadmap_update_batch.argtypes = [C.POINTER(P), C.c_uint32, P, C.POINTER(P), C.POINTER(P),
+                                                C.POINTER(P), i32, P]
         L.mpap_feature_levels.restype = i32
         L.mpap_feature_levels.argtypes = [i32, i32, P, P, C.c_uint32, P, i32, C.c_uint32, P, C.c_float,
                                           C.c_float, i32, P, i32, P]
@@ -536,6 +539,33 @@ def feature_levels(dim_kind, box_lo, box_hi, features, grid_G, headings=None, co
                                      out.ctypes.data_as(C.c_void_p), MPAP_MEM_HOST, _stream(stream)),
            "mpap_feature_levels")
     return out
+
+
+def roadmap_update_batch(rms, adds_lo, adds_hi, grids=None, stream=None):
+    """mpap_roadmap_update_batch: roadmap j gets the boxes adds_lo[j], adds_hi[j]
+    (float [k_j, 3], k_j may be 0) and, when given, the levels grids[j] (uint8
+    [G^Dp] or None); host numpy arrays."""
+    n = len(rms)
+    keep = []
+
+    def arr(a, dtype):
+        if a is None:
+            return None
+        x = np.ascontiguousarray(a, dtype)
+        keep.append(x)
+        return x.ctypes.data if x.size else None
+
+    los = [arr(a, np.float32) for a in adds_lo]
+    his = [arr(a, np.float32) for a in adds_hi]
+    nb = np.array([0 if a is None else np.asarray(a).size // 3 for a in adds_lo], np.int32)
+    gs = [arr(g, np.uint8) for g in grids] if grids is not None else None
+    hs = (C.c_void_p * n)(*[rm.h for rm in rms])
+    lp = (C.c_void_p * n)(*los)
+    hp = (C.c_void_p * n)(*his)
+    gp = (C.c_void_p * n)(*gs) if gs is not None else None
+    _check(lib().mpap_roadmap_update_batch(hs, n, nb.ctypes.data_as(C.c_void_p), lp, hp, gp, MPAP_MEM_HOST,
+                                           _stream(stream)), "mpap_roadmap_update_batch")
+    return rms
 
 
 def scene_spec(scene, n=None, r=None, M=None, device_inputs=None):

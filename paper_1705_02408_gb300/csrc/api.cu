@@ -16,8 +16,9 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
                           mpap_result* outs, cudaStream_t st);
 int32_t search_fronts_impl(mpap_workspace* ws, uint32_t index, uint32_t* front_ptr, int64_t* cost,
                            int64_t* h, uint64_t cap, uint64_t* total, cudaStream_t st);
-int32_t roadmap_update_impl(mpap_roadmap* rm, int32_t nb_add, const float* add_lo, const float* add_hi,
-                            const uint8_t* grid, bool device, cudaStream_t st);
+int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const int32_t* nb_add,
+                                  const float* const* add_lo, const float* const* add_hi,
+                                  const uint8_t* const* grids, bool device, cudaStream_t st);
 int32_t feature_levels_impl(int dp, int nb, const float* lo, const float* hi, uint32_t nf, const float* feat,
                             uint32_t G, uint32_t Y, const float* head, float cos_half, float range, int K,
                             uint8_t* out, bool device, cudaStream_t st);
@@ -320,7 +321,34 @@ int32_t mpap_roadmap_update(mpap_roadmap* rm, int32_t nb_add, const float* add_l
     set_error("roadmap_update: mem must be MPAP_MEM_HOST or MPAP_MEM_DEVICE");
     return MPAP_ERR_INVALID_ARG;
   }
-  return mpap::roadmap_update_impl(rm, nb_add, add_lo, add_hi, grid, mem == MPAP_MEM_DEVICE, S(stream));
+  return mpap::roadmap_update_batch_impl(1, &rm, &nb_add, &add_lo, &add_hi, &grid, mem == MPAP_MEM_DEVICE,
+                                         S(stream));
+}
+
+int32_t mpap_roadmap_update_batch(mpap_roadmap* const* rms, uint32_t n, const int32_t* nb_add,
+                                  const float* const* add_lo, const float* const* add_hi,
+                                  const uint8_t* const* grids, int32_t mem, void* stream) {
+  if (n == 0) return MPAP_OK;
+  if (!rms || !nb_add || !add_lo || !add_hi) {
+    set_error("roadmap_update_batch: null array");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  for (uint32_t j = 0; j < n; ++j)
+    if (!rms[j] || nb_add[j] < 0 || (nb_add[j] > 0 && (!add_lo[j] || !add_hi[j]))) {
+      set_error("roadmap_update_batch: roadmap %u: null roadmap, negative box count or null box arrays", j);
+      return MPAP_ERR_INVALID_ARG;
+    }
+  for (uint32_t j = 0; j < n; ++j)
+    for (uint32_t k = j + 1; k < n; ++k)
+      if (rms[j] == rms[k]) {
+        set_error("roadmap_update_batch: roadmap %u appears twice", k);
+        return MPAP_ERR_INVALID_ARG;
+      }
+  if (mem != MPAP_MEM_HOST && mem != MPAP_MEM_DEVICE) {
+    set_error("roadmap_update_batch: mem must be MPAP_MEM_HOST or MPAP_MEM_DEVICE");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::roadmap_update_batch_impl(n, rms, nb_add, add_lo, add_hi, grids, mem == MPAP_MEM_DEVICE, S(stream));
 }
 
 int32_t mpap_roadmap_info(const mpap_roadmap* rm, uint32_t* V, uint64_t* E) {

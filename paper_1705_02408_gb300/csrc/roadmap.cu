@@ -762,9 +762,11 @@ struct UpdateJob {
 };
 
 // One warp per source: collision of each out-edge against the added boxes and,
-// when the grid changed, the edge's transfer on the new grid.
+// when the grid changed, the edge's transfer on the new grid.  blockIdx.y picks
+// the roadmap among those of this dimension.
 template <int DIM>
-__global__ void k_update_edges(UpdateJob J) {
+__global__ void k_update_edges(const UpdateJob* __restrict__ jobs, const uint32_t* __restrict__ ids) {
+  const UpdateJob& J = jobs[ids[blockIdx.y]];
   extern __shared__ float smem[];
   float* s_lo = smem;
   float* s_hi = smem + 3 * J.g_add.nb;
@@ -813,8 +815,10 @@ __global__ void k_update_edges(UpdateJob J) {
   }
 }
 
-// One warp per source: the kept edges, in their order, at the new row pointers.
-__global__ void k_update_compact(UpdateJob J) {
+// One warp per source: the kept edges, in their order, at the new row pointers
+// (blockIdx.y: roadmap).
+__global__ void k_update_compact(const UpdateJob* __restrict__ jobs) {
+  const UpdateJob& J = jobs[blockIdx.y];
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -1469,145 +1473,197 @@ int32_t roadmap_from_csr_impl(uint32_t V, const uint32_t* row_ptr, const uint32_
   return MPAP_OK;
 }
 
-int32_t roadmap_update_impl(mpap_roadmap* rm, int32_t nb_add, const float* add_lo, const float* add_hi,
-                            const uint8_t* grid, bool device, cudaStream_t st) {
-  if (!rm->has_geometry) {
-    set_error("roadmap_update: the roadmap has no geometry");
-    return MPAP_ERR_INVALID_ARG;
+int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const int32_t* nb_add,
+                                  const float* const* add_lo, const float* const* add_hi,
+                                  const uint8_t* const* grids, bool device, cudaStream_t st) {
+  if (n == 0) return MPAP_OK;
+  for (uint32_t j = 0; j < n; ++j) {
+    if (!rms[j]->has_geometry) {
+      set_error("roadmap_update: roadmap %u has no geometry", j);
+      return MPAP_ERR_INVALID_ARG;
+    }
+    if (rms[j]->nb + nb_add[j] > 1024) {
+      set_error("roadmap_update: roadmap %u would have more than 1024 boxes", j);
+      return MPAP_ERR_INVALID_ARG;
+    }
   }
-  const int dp = (rm->dim == 2) ? 2 : 3;
-  const size_t cells = (size_t)rm->G * rm->G * (dp == 3 ? rm->G : 1);
-  const int nb_old = rm->nb, nb = nb_old + nb_add;
-  if (nb > 1024) {
-    set_error("roadmap_update: at most 1024 boxes in all");
-    return MPAP_ERR_INVALID_ARG;
+  // 1. the scenes: old boxes kept, added boxes appended, grids replaced
+  std::vector<std::vector<float>> lo(n), hi(n);
+  for (uint32_t j = 0; j < n; ++j) {
+    mpap_roadmap* rm = rms[j];
+    const int nb = rm->nb + nb_add[j];
+    lo[j].assign(3 * (size_t)nb + 3, 0.0f);
+    hi[j].assign(3 * (size_t)nb + 3, 0.0f);
+    if (rm->nb) {
+      MPAP_CK(cudaMemcpyAsync(lo[j].data(), rm->box_lo, sizeof(float) * 3 * rm->nb, cudaMemcpyDeviceToHost, st));
+      MPAP_CK(cudaMemcpyAsync(hi[j].data(), rm->box_hi, sizeof(float) * 3 * rm->nb, cudaMemcpyDeviceToHost, st));
+    }
+    if (nb_add[j]) {
+      const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+      MPAP_CK(cudaMemcpyAsync(lo[j].data() + 3 * rm->nb, add_lo[j], sizeof(float) * 3 * nb_add[j], kind, st));
+      MPAP_CK(cudaMemcpyAsync(hi[j].data() + 3 * rm->nb, add_hi[j], sizeof(float) * 3 * nb_add[j], kind, st));
+    }
   }
-  // 1. the scene: old boxes kept, added boxes appended, grid replaced
-  std::vector<float> lo(3 * (size_t)nb + 3, 0.0f), hi(3 * (size_t)nb + 3, 0.0f);
-  if (nb_old) {
-    MPAP_CK(cudaMemcpyAsync(lo.data(), rm->box_lo, sizeof(float) * 3 * nb_old, cudaMemcpyDeviceToHost, st));
-    MPAP_CK(cudaMemcpyAsync(hi.data(), rm->box_hi, sizeof(float) * 3 * nb_old, cudaMemcpyDeviceToHost, st));
-    MPAP_CK(cudaStreamSynchronize(st));
-  }
-  if (nb_add) {
-    const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-    MPAP_CK(cudaMemcpyAsync(lo.data() + 3 * nb_old, add_lo, sizeof(float) * 3 * nb_add, kind, st));
-    MPAP_CK(cudaMemcpyAsync(hi.data() + 3 * nb_old, add_hi, sizeof(float) * 3 * nb_add, kind, st));
-    MPAP_CK(cudaStreamSynchronize(st));
-  }
-  int32_t rc = ensure_scene(rm, (size_t)nb, cells);
-  if (rc) return rc;
-  MPAP_CK(cudaMemcpyAsync(rm->box_lo, lo.data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
-  MPAP_CK(cudaMemcpyAsync(rm->box_hi, hi.data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
-  if (grid) MPAP_CK(cudaMemcpyAsync(rm->grid, grid, cells, device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  rm->nb = nb;
-  fill_geom_constants(rm->geom, rm->dim, rm->nb, rm->G, rm->n_f, rm->M, rm->r, rm->T);
-  rm->geom.box_lo = rm->box_lo;
-  rm->geom.box_hi = rm->box_hi;
-  rm->geom.grid = rm->grid;
-  {
+  MPAP_CK(cudaStreamSynchronize(st));
+  std::vector<int> nb_old(n);
+  uint64_t E_sum = 0, V_sum = 0;
+  uint32_t Vmax = 0;
+  int max_add = 0;
+  for (uint32_t j = 0; j < n; ++j) {
+    mpap_roadmap* rm = rms[j];
+    const int dp = (rm->dim == 2) ? 2 : 3;
+    const size_t cells = (size_t)rm->G * rm->G * (dp == 3 ? rm->G : 1);
+    nb_old[j] = rm->nb;
+    const int nb = rm->nb + nb_add[j];
+    int32_t rc = ensure_scene(rm, (size_t)nb, cells);
+    if (rc) return rc;
+    MPAP_CK(cudaMemcpyAsync(rm->box_lo, lo[j].data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
+    MPAP_CK(cudaMemcpyAsync(rm->box_hi, hi[j].data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
+    if (grids && grids[j])
+      MPAP_CK(cudaMemcpyAsync(rm->grid, grids[j], cells, device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              st));
+    rm->nb = nb;
+    fill_geom_constants(rm->geom, rm->dim, rm->nb, rm->G, rm->n_f, rm->M, rm->r, rm->T);
+    rm->geom.box_lo = rm->box_lo;
+    rm->geom.box_hi = rm->box_hi;
+    rm->geom.grid = rm->grid;
     const double lmax = std::max((double)rm->n_f, (double)rm->K - (double)rm->n_f);
     const double inc_max = (rm->dim == 6) ? (double)rm->geom.Tq : std::ceil((double)rm->r * 16777216.0) + 1.0;
     rm->geom.narrow = ((double)rm->M * inc_max * lmax < 2147483647.0) ? 1 : 0;
+    E_sum += rm->E;
+    V_sum += (uint64_t)rm->V + 1;
+    Vmax = std::max(Vmax, rm->V);
+    max_add = std::max(max_add, nb_add[j]);
   }
-  const uint32_t V = rm->V;
-  const uint64_t E = rm->E;
-  if (E == 0 || (nb_add == 0 && !grid)) return cudaStreamSynchronize(st) == cudaSuccess ? MPAP_OK : MPAP_ERR_CUDA;
-  // 2. scratch: old pointers, updated records, keep flags, counts
+  // 2. one scratch block: per roadmap old pointers, kept counts, reverse counters,
+  //    updated records and keep flags; the job tables
   char* blk = nullptr;
-  const size_t bytes = 4096 * 4 + 4 * ((size_t)V + 1) * 4 + (sizeof(int4) + sizeof(int2) + 1) * (size_t)E +
-                       sizeof(BuildJob) + sizeof(ScanSeg) + 16;
+  const size_t bytes = 256 * (10 * (size_t)n + 8) + 16 * (size_t)n + 16 * V_sum +
+                       (sizeof(int4) + sizeof(int2) + 1) * (size_t)E_sum +
+                       (sizeof(UpdateJob) + sizeof(BuildJob) + sizeof(ScanSeg) + 4) * (size_t)n;
   MPAP_CK(scratch_alloc((void**)&blk, bytes, st));
-  Carve cv{blk, 0};
-  uint32_t* d_status = cv.take<uint32_t>(4);
-  uint32_t* d_ptr_old = cv.take<uint32_t>((size_t)V + 1);
-  uint32_t* d_kept = cv.take<uint32_t>((size_t)V + 1);
-  uint32_t* d_counts = cv.take<uint32_t>((size_t)V + 1);
-  uint32_t* d_fill = cv.take<uint32_t>((size_t)V + 1);
-  int4* d_edge = cv.take<int4>(E);
-  int2* d_peak = cv.take<int2>(E);
-  uint8_t* d_keep = cv.take<uint8_t>(E);
-  BuildJob* d_job = cv.take<BuildJob>(1);
-  ScanSeg* d_seg = cv.take<ScanSeg>(1);
   auto bail = [&](int32_t r) {
     scratch_free(blk, st);
     return r;
   };
-  if (cv.off > bytes) return bail(MPAP_ERR_CUDA);
-  if (!cuda_ok(cudaMemsetAsync(d_status, 0, 16, st), "memset") ||
-      !cuda_ok(cudaMemcpyAsync(d_ptr_old, rm->fwd_ptr, 4 * ((size_t)V + 1), cudaMemcpyDeviceToDevice, st), "copy"))
+  Carve cv{blk, 0};
+  uint32_t* d_status = cv.take<uint32_t>(4 * (size_t)n);
+  UpdateJob* d_uj = cv.take<UpdateJob>(n);
+  BuildJob* d_bj = cv.take<BuildJob>(n);
+  ScanSeg* d_seg = cv.take<ScanSeg>(n);
+  uint32_t* d_ids = cv.take<uint32_t>(n);
+  std::vector<UpdateJob> uj(n);
+  std::vector<BuildJob> bj(n);
+  std::vector<ScanSeg> segs(n);
+  for (uint32_t j = 0; j < n; ++j) {
+    mpap_roadmap* rm = rms[j];
+    const uint32_t V = rm->V;
+    const uint64_t E = rm->E;
+    UpdateJob& J = uj[j];
+    std::memset(&J, 0, sizeof(J));
+    uint32_t* ptr_old = cv.take<uint32_t>((size_t)V + 1);
+    J.g = rm->geom;
+    J.g_add = rm->geom;
+    J.g_add.nb = nb_add[j];
+    J.g_add.box_lo = rm->box_lo + 3 * nb_old[j];
+    J.g_add.box_hi = rm->box_hi + 3 * nb_old[j];
+    J.x = rm->x;
+    J.V = V;
+    J.ptr = ptr_old;
+    J.edge = rm->fwd_edge;
+    J.peak = rm->fwd_peak;
+    J.edge_upd = cv.take<int4>(E);
+    J.peak_upd = cv.take<int2>(E);
+    J.keep = cv.take<uint8_t>(E);
+    J.kept = cv.take<uint32_t>((size_t)V + 1);
+    J.ptr_new = rm->fwd_ptr;
+    J.edge_out = rm->fwd_edge;
+    J.dst_out = rm->fwd_dst;
+    J.peak_out = rm->fwd_peak;
+    J.status = d_status + 4 * j;
+    J.retransfer = (grids && grids[j]) ? 1 : 0;
+    segs[j] = ScanSeg{J.kept, rm->fwd_ptr, V, d_status + 4 * j + 2};
+    BuildJob& B = bj[j];
+    std::memset(&B, 0, sizeof(B));
+    B.V = V;
+    B.fwd_ptr = rm->fwd_ptr;
+    B.fwd_edge = rm->fwd_edge;
+    B.rev_ptr = rm->rev_ptr;
+    B.rev_edge = rm->rev_edge;
+    B.fwd_peak = rm->fwd_peak;
+    B.rev_peak = rm->rev_peak;
+    B.counts = cv.take<uint32_t>((size_t)V + 1);
+    B.fill = cv.take<uint32_t>((size_t)V + 1);
+  }
+  if (cv.off > bytes) {
+    set_error("roadmap_update: scratch layout overflow");
     return bail(MPAP_ERR_CUDA);
-  UpdateJob J;
-  std::memset(&J, 0, sizeof(J));
-  J.g = rm->geom;
-  J.g_add = rm->geom;
-  J.g_add.nb = nb_add;
-  J.g_add.box_lo = rm->box_lo + 3 * nb_old;
-  J.g_add.box_hi = rm->box_hi + 3 * nb_old;
-  J.x = rm->x;
-  J.V = V;
-  J.ptr = d_ptr_old;
-  J.edge = rm->fwd_edge;
-  J.peak = rm->fwd_peak;
-  J.edge_upd = d_edge;
-  J.peak_upd = d_peak;
-  J.keep = d_keep;
-  J.kept = d_kept;
-  J.ptr_new = rm->fwd_ptr;
-  J.edge_out = rm->fwd_edge;
-  J.dst_out = rm->fwd_dst;
-  J.peak_out = rm->fwd_peak;
-  J.status = d_status;
-  J.retransfer = grid ? 1 : 0;
+  }
+  int32_t rc = MPAP_OK;
+  if (!cuda_ok(cudaMemsetAsync(d_status, 0, 16 * (size_t)n, st), "memset")) return bail(MPAP_ERR_CUDA);
+  for (uint32_t j = 0; j < n; ++j) {
+    if (!cuda_ok(cudaMemcpyAsync(const_cast<uint32_t*>(uj[j].ptr), rms[j]->fwd_ptr, 4 * ((size_t)rms[j]->V + 1),
+                                 cudaMemcpyDeviceToDevice, st), "copy") ||
+        !cuda_ok(cudaMemsetAsync(bj[j].counts, 0, 4 * ((size_t)rms[j]->V + 1), st), "memset") ||
+        !cuda_ok(cudaMemsetAsync(bj[j].fill, 0, 4 * ((size_t)rms[j]->V + 1), st), "memset"))
+      return bail(MPAP_ERR_CUDA);
+  }
+  if ((rc = upload(d_uj, uj.data(), sizeof(UpdateJob) * n, st)) ||
+      (rc = upload(d_bj, bj.data(), sizeof(BuildJob) * n, st)) ||
+      (rc = upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st)))
+    return bail(rc);
+  // 3. edges against the added boxes (one launch per dimension), new row
+  //    pointers, compaction into the CSR
+  std::vector<uint32_t> ids;
+  const int dims[3] = {2, 3, 6};
+  uint32_t off[4] = {0, 0, 0, 0};
+  for (int di = 0; di < 3; ++di) {
+    off[di] = (uint32_t)ids.size();
+    for (uint32_t j = 0; j < n; ++j)
+      if (rms[j]->dim == dims[di]) ids.push_back(j);
+  }
+  off[3] = (uint32_t)ids.size();
+  if ((rc = upload(d_ids, ids.data(), sizeof(uint32_t) * n, st))) return bail(rc);
   const int sms = sm_count();
-  const dim3 gridw(std::min<uint32_t>((V + 7) / 8, 4u * sms));
+  const uint32_t gx = std::min<uint32_t>((Vmax + 7) / 8, 4u * sms);
+  const size_t sm = sizeof(float) * 6 * (size_t)max_add;
   {
     LaunchScope ls(st, "k_update_edges");
-    const size_t sm = sizeof(float) * 6 * (size_t)nb_add;
-    if (rm->dim == 6) k_update_edges<6><<<gridw, 256, sm, st>>>(J);
-    else if (rm->dim == 3) k_update_edges<3><<<gridw, 256, sm, st>>>(J);
-    else k_update_edges<2><<<gridw, 256, sm, st>>>(J);
+    for (int di = 0; di < 3; ++di) {
+      const uint32_t cnt = off[di + 1] - off[di];
+      if (!cnt) continue;
+      const dim3 grid(gx, cnt);
+      if (dims[di] == 6) k_update_edges<6><<<grid, 256, sm, st>>>(d_uj, d_ids + off[di]);
+      else if (dims[di] == 3) k_update_edges<3><<<grid, 256, sm, st>>>(d_uj, d_ids + off[di]);
+      else k_update_edges<2><<<grid, 256, sm, st>>>(d_uj, d_ids + off[di]);
+    }
   }
-  // 3. new row pointers; the records move from the scratch copy into the CSR
-  ScanSeg seg{d_kept, rm->fwd_ptr, V, d_status + 2};
-  if ((rc = upload(d_seg, &seg, sizeof(seg), st))) return bail(rc);
   {
     LaunchScope ls(st, "k_scan_segments");
-    k_scan_segments<<<1, 1024, 0, st>>>(d_seg);
+    k_scan_segments<<<n, 1024, 0, st>>>(d_seg);
   }
   {
     LaunchScope ls(st, "k_update_compact");
-    k_update_compact<<<gridw, 256, 0, st>>>(J);
+    k_update_compact<<<dim3(gx, n), 256, 0, st>>>(d_uj);
   }
-  uint32_t hs[4] = {0, 0, 0, 0}, e_new = 0;
-  if (!cuda_ok(cudaMemcpyAsync(hs, d_status, 16, cudaMemcpyDeviceToHost, st), "copy") ||
-      !cuda_ok(cudaMemcpyAsync(&e_new, rm->fwd_ptr + V, 4, cudaMemcpyDeviceToHost, st), "copy") ||
-      !cuda_ok(cudaStreamSynchronize(st), "sync"))
+  if (!cuda_ok(cudaGetLastError(), "update kernels")) return bail(MPAP_ERR_CUDA);
+  // 4. edge counts back, then the reverse CSR of every updated roadmap
+  std::vector<uint32_t> hs(4 * (size_t)n), e_new(n);
+  if (!cuda_ok(cudaMemcpyAsync(hs.data(), d_status, 16 * (size_t)n, cudaMemcpyDeviceToHost, st), "copy"))
     return bail(MPAP_ERR_CUDA);
-  rm->E = e_new;
-  // 4. reverse CSR of the updated forward CSR
-  BuildJob B;
-  std::memset(&B, 0, sizeof(B));
-  B.V = V;
-  B.fwd_ptr = rm->fwd_ptr;
-  B.fwd_edge = rm->fwd_edge;
-  B.rev_ptr = rm->rev_ptr;
-  B.rev_edge = rm->rev_edge;
-  B.fwd_peak = rm->fwd_peak;
-  B.rev_peak = rm->rev_peak;
-  B.counts = d_counts;
-  B.fill = d_fill;
-  std::vector<BuildJob> hb(1, B);
-  if (!cuda_ok(cudaMemsetAsync(d_counts, 0, 4 * ((size_t)V + 1), st), "memset") ||
-      !cuda_ok(cudaMemsetAsync(d_fill, 0, 4 * ((size_t)V + 1), st), "memset") ||
-      (rc = upload(d_job, &B, sizeof(B), st)) || (rc = build_reverse(1, hb, d_job, d_seg, V, st)))
-    return bail(rc ? rc : MPAP_ERR_CUDA);
+  for (uint32_t j = 0; j < n; ++j)
+    if (!cuda_ok(cudaMemcpyAsync(&e_new[j], rms[j]->fwd_ptr + rms[j]->V, 4, cudaMemcpyDeviceToHost, st), "copy"))
+      return bail(MPAP_ERR_CUDA);
+  if (!cuda_ok(cudaStreamSynchronize(st), "sync")) return bail(MPAP_ERR_CUDA);
+  for (uint32_t j = 0; j < n; ++j) rms[j]->E = e_new[j];
+  if ((rc = build_reverse(n, bj, d_bj, d_seg, Vmax, st))) return bail(rc);
   scratch_free(blk, st);
   if (!cuda_ok(cudaStreamSynchronize(st), "sync")) return MPAP_ERR_CUDA;
-  if (hs[0]) {
-    set_error("roadmap_update: an edge transfer does not fit int32");
-    return MPAP_ERR_CAPACITY;
-  }
+  for (uint32_t j = 0; j < n; ++j)
+    if (hs[4 * j]) {
+      set_error("roadmap_update: an edge transfer of roadmap %u does not fit int32", j);
+      return MPAP_ERR_CAPACITY;
+    }
   return MPAP_OK;
 }
 

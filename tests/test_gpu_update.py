@@ -81,3 +81,28 @@ def test_update_with_device_arrays_and_repeated(mp, orc):
                                        np.concatenate([sc.box_hi, hi1, hi2]), grid, sc.cfg.grid_G, x, sc.cfg.r)
     assert_same_graph(rg.export(), ro.graph())
     assert_reverse_is_transpose(rg)
+
+
+def test_batched_update_equals_construction_from_the_same_nodes(mp, orc):
+    """mpap_roadmap_update_batch: mixed dimensions, boxes only, grid only and both,
+    in one call."""
+    cases = [("2d", 1, 900, None, 3, True), ("3d", 2, 1500, None, 4, False), ("6d", 1, 2000, 18.0, 3, True),
+             ("6d", 4, 2000, 18.0, 0, True), ("2d", 6, 700, 0.2, 2, False)]
+    rms, adds_lo, adds_hi, grids, want = [], [], [], [], []
+    for name, seed, n, r, k, new_grid in cases:
+        sc = scenegen.make_scene(name, seed, query_id=seed)
+        rr = sc.cfg.r if r is None else r
+        rms.append(mp.build_roadmap_for_scene(sc, n=n, r=rr))
+        x = orc.build_roadmap(sc, n=n, r=rr).graph().x
+        lo, hi = _added_boxes(name, seed, k)
+        grid = scenegen.make_scene(name, seed + 100).grid if new_grid else None
+        adds_lo.append(lo); adds_hi.append(hi); grids.append(grid)
+        ro = orc.build_roadmap_from_points(sc.cfg.dim_kind, np.concatenate([sc.box_lo, lo]),
+                                           np.concatenate([sc.box_hi, hi]), sc.grid if grid is None else grid,
+                                           sc.cfg.grid_G, x, rr, T=sc.cfg.T_edge, M=sc.cfg.M)
+        want.append(ro.graph())
+    mp.roadmap_update_batch(rms, adds_lo, adds_hi, grids)
+    for rg, g in zip(rms, want):
+        assert_same_graph(rg.export(), g)
+        np.testing.assert_array_equal(np.stack(rg.peaks()), np.stack([g.Smax, g.Cmax]))
+        assert_reverse_is_transpose(rg)
