@@ -62,3 +62,22 @@ def test_features_sit_off_their_surfaces(orc):
     np.testing.assert_array_equal(f, scenegen.feature_points(sc, 200))     # seeded
     h = scenegen.yaw_headings(8)
     np.testing.assert_allclose((h.astype(np.float64) ** 2).sum(1), 1.0, atol=1e-6)
+
+
+def test_field_of_view_in_3d_is_horizontal(orc):
+    """The field of view is a horizontal cone: a feature straight above a cell
+    centre (no horizontal offset) passes every heading; one off to the side counts
+    only for headings within the half-angle of its horizontal direction, whatever
+    its height; range uses the full 3D distance."""
+    import oracle
+    heads = np.array([[1, 0], [0, 1], [-1, 0], [0, -1]], np.float32)
+    narrow = np.float32(np.cos(np.radians(10)))
+    above = np.array([[0.25, 0.25, 0.95]], np.float32)       # over cell (0.25, 0.25, 0.25)
+    lv = oracle.feature_levels(3, NOBOX, NOBOX, above, 2, heads, narrow, 2.0)
+    assert (lv[:, 0] == 1).all()
+    side = np.array([[0.95, 0.25, 0.75]], np.float32)        # +x of cell 0, 45 deg up
+    lv = oracle.feature_levels(3, NOBOX, NOBOX, side, 2, heads, narrow, 2.0)
+    np.testing.assert_array_equal(lv[:, 0], [1, 0, 0, 0])
+    # |d| = sqrt(0.7^2 + 0.5^2) = 0.86: out at range 0.8, in at range 0.9
+    assert oracle.feature_levels(3, NOBOX, NOBOX, side, 2, heads[:1], narrow, 0.8)[0, 0] == 0
+    assert oracle.feature_levels(3, NOBOX, NOBOX, side, 2, heads[:1], narrow, 0.9)[0, 0] == 1
