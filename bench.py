@@ -232,8 +232,8 @@ def run_gpu(args, rank, world, local):
         ts, s_ms = mp.autotune_search(arm.ws, arm.rms, arm.queries, reps=1)
         if ts["front_cap"] > arm.ws.front_cap:
             arm.ws = mp.Workspace(arm.ws.total_nodes, front_cap=ts["front_cap"], max_plans=1 << 25)
-        tuning = {"edge_warps": tb["edge_warps"], "select_blocks_per_sm": ts["select_blocks_per_sm"],
-                  "prune_blocks_per_sm": ts["prune_blocks_per_sm"], "front_cap": arm.ws.front_cap,
+        tuning = {"edge_warps": tb["edge_warps"], "wave_blocks_per_sm": ts["wave_blocks_per_sm"],
+                  "plan_lanes_from": ts["plan_lanes_from"], "front_cap": arm.ws.front_cap,
                   "tuned_build_ms": round(b_ms, 3), "tuned_search_ms": round(s_ms, 3)}
 
     def barrier():
@@ -282,10 +282,12 @@ def run_gpu(args, rank, world, local):
            "gpu_launches": int(launches),
            "tuning": tuning}
     # breakdown from the live kernel timers (timed region)
-    search_k = {"k_init", "k_select", "k_prune", "k_end", "k_finalize", "k_candidates"}
+    search_k = {"k_init", "k_wave", "k_finalize", "k_candidates"}
     certify_k = {"k_mc_checkpoints", "k_mc_rollouts"}
     phase = {"build": 0.0, "search": 0.0, "certify": 0.0}
     for k, (_, t) in kern.items():
+        if "." in k:
+            continue    # a phase inside a kernel (k_wave.expand, ...), already in the kernel's time
         phase["search" if k in search_k else "certify" if k in certify_k else "build"] += t / args.steps
     out["kernel_ms_per_step"] = {k: round(v[1] / args.steps, 4) for k, v in sorted(kern.items())}
     out["phase_kernel_ms_per_step"] = {p: round(t, 4) for p, t in phase.items()}
@@ -294,7 +296,7 @@ def run_gpu(args, rank, world, local):
     out["certified_failure_rate"] = sum(c["hits_any"] for c in certs) / max(1, sum(c["rollouts"] for c in certs))
     out["roofline"] = roofline(kern, arm, res, args.steps)
     # the two kernels that share most of the step, each against its own bound
-    out["roofline_by_kernel"] = [roofline(kern, arm, res, args.steps, name=k) for k in ("k_prune", "k_edges")
+    out["roofline_by_kernel"] = [roofline(kern, arm, res, args.steps, name=k) for k in ("k_wave", "k_edges")
                                  if k in kern]
     if ck:
         out["clocks"] = ck
@@ -329,10 +331,6 @@ NCU_TRAFFIC = {
     "k_edges": {"bytes_per_roadmap": (13.236736e6 + 90.364672e6) / 8,
                 "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "d62482682c7dcca7902214d7f5b830d779e07767",
                             "paper_1705_02408_gb300/csrc/common.cuh": "f42dfc54d3c1a7692a7b0b6e1943805b4fb67da4"}},
-    # every k_prune and k_prune_bulk launch of the 8-query, 2-step capture:
-    # 888.84 MB of DRAM reads + writes over 2 x 12,658,585 expansions
-    "k_prune": {"bytes_per_expansion": 888836864.0 / (2 * 12658585.0),
-                "sources": {"paper_1705_02408_gb300/csrc/search.cu": "4cd7bfa51c4a0d8e8fa94bec80c11c0425eb23a5"}},
 }
 
 
@@ -357,7 +355,7 @@ def roofline(kern, arm, res, steps, name=None):
     except OSError:
         pass
     if name is None:
-        name = max(kern.items(), key=lambda kv: kv[1][1])[0]
+        name = max(((k, v) for k, v in kern.items() if "." not in k), key=lambda kv: kv[1][1])[0]
     launches, ms = kern[name]
     V = arm.cfg.n + 2
     B = len(arm.scenes)
@@ -396,7 +394,7 @@ def roofline(kern, arm, res, steps, name=None):
     # DRAM traffic: bytes per plan-edge expansion from an ncu capture of every
     # launch of a smaller batch, times the expansions of one launch here
     traffic = None
-    if name == "k_prune":
+    if name == "k_wave":
         traffic = _traffic(name, exps * steps / max(1, launches), "bytes_per_expansion")
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,

@@ -24,7 +24,8 @@
  *   - Errors are returned as negative mpap_status values; mpap_last_error() gives
  *     a one-line description (thread-local).  Device-side failures (capacity
  *     overflow, iteration cap) are detected on the device and returned as status
- *     codes; no kernel traps.
+ *     codes; no kernel traps.  The search loop's grid barriers wait a bounded
+ *     time (mpap_query.wait_us) and report MPAP_ERR_TIMEOUT when it runs out.
  *
  * Units.  Costs are int64 multiples of 2^-24 (cost quantum).  Perception heuristic
  * values are int64 multiples of 2^-24 / (M n_f) units of drift time, where M is
@@ -112,7 +113,12 @@ typedef struct {
  *               bit 1 MPAP_QUERY_CHECK_INTERIOR: the perception constraint of
  *               Eq. 2 for all t: a candidate is cut when the heuristic exceeds
  *               beta at any sub-step of its last edge (max(Cmax, h + Smax) >
- *               beta), not only at its head (Alg. 3). */
+ *               beta), not only at its head (Alg. 3).
+ *   wait_us     limit of one grid-barrier wait of the device wavefront loop, in
+ *               microseconds of GPU timer time (0: 20 s).  A batch uses the
+ *               smallest non-zero value of its queries.  A wait that runs out
+ *               ends the loop: unfinished queries report MPAP_ERR_TIMEOUT and
+ *               the call returns it; the workspace stays usable. */
 #define MPAP_QUERY_NO_GOAL_STOP 1u
 #define MPAP_QUERY_CHECK_INTERIOR 2u
 typedef struct {
@@ -121,7 +127,7 @@ typedef struct {
   float lambda;
   uint32_t max_iters;
   uint32_t flags;
-  uint32_t reserved;
+  uint32_t wait_us;
 } mpap_query;
 
 /* Search result.  path is a caller-owned host array of path_cap entries; on
@@ -268,13 +274,17 @@ void mpap_roadmap_free(mpap_roadmap* rm);
  * so a query that runs out of its share fails alone whatever the others do.  A
  * query that runs out of pool, plan arena (max_plans) or group array (max_plans)
  * ends with MPAP_ERR_CAPACITY in its own result; the other queries of the batch
- * run on.  Allocates with cudaMalloc; reused by every search call. */
+ * run on.  Candidates of one wavefront wait in 32 slots of 32 bytes per node
+ * (1 KiB per node); a node's candidates beyond 32 go to two overflow areas of
+ * max_plans records, shared out among the queries of a call like the pool.
+ * Allocates with cudaMalloc; reused by every search call. */
 int32_t mpap_workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans,
                               mpap_workspace** out);
 void mpap_workspace_free(mpap_workspace* ws);
 
-/* Alg. 3 Explore for one query on one roadmap (the group loop runs on the
- * device; the host waits once).  RemoveDominated uses the weak Pareto order with
+/* Alg. 3 Explore for one query on one roadmap.  The whole group loop is one
+ * persistent kernel (cooperative launch, grid barriers between the expansion
+ * and the merge of every wavefront); the host waits once.  RemoveDominated uses the weak Pareto order with
  * a total tie key (creation iteration, parent head, parent cost): an exact set
  * function, so fronts, cost, h and path are identical to a sequential execution
  * of Alg. 3.  Returns the result status (MPAP_OK or MPAP_NO_SOLUTION) or an
@@ -338,15 +348,19 @@ int32_t mpap_certify_noalloc(const mpap_roadmap* rm, const uint32_t* path, uint3
  * library keeps a table of launch shapes keyed by (dimension, node-count bucket
  * floor(log2 V)); dim_kind 0 keys a batch that mixes dimensions, V the largest
  * roadmap of a batch.  mpap_build_roadmaps reads edge_warps for each dimension
- * group of its batch; mpap_search / mpap_search_batch read select and prune
- * blocks per SM for the batch key.  Keys without an entry use the defaults
- * (8, 16, 16).  The results of every call are identical for every valid shape;
- * only the time changes.  The table is process-wide and guarded by a mutex.
+ * group of its batch; mpap_search / mpap_search_batch read the wavefront
+ * kernel's blocks per SM and the group size from which its expansion runs its
+ * lanes over a node's group plans instead of its out-edges.  Keys without an
+ * entry use the defaults (8, 8, 8, 64).  The results of every call are
+ * identical for every valid shape; only the time changes.  The table is
+ * process-wide and guarded by a mutex.
  * ------------------------------------------------------------------------- */
 typedef struct {
   uint32_t edge_warps;            /* warps per block of the edge kernel: 4 or 8 */
-  uint32_t select_blocks_per_sm;  /* grid of the group-selection kernel: 1 .. 64 */
-  uint32_t prune_blocks_per_sm;   /* grid of the candidate-pull/prune kernel: 1 .. 64 */
+  uint32_t wave_blocks_per_sm;    /* blocks per SM of the persistent wavefront kernel:
+                                     1 .. 64, capped at the number that fits */
+  uint32_t plan_lanes_from;       /* group size from which the expansion puts its
+                                     lanes on the group plans: 1 .. 64 */
   uint32_t front_cap;             /* advisory pool entries per node for mpap_workspace_create */
 } mpap_tuning;
 
@@ -368,8 +382,10 @@ int32_t mpap_autotune_build(uint32_t n, const mpap_scene* scenes, const mpap_roa
                             mpap_roadmap** rms, uint32_t reps, mpap_tuning* best, double* best_ms,
                             void* stream);
 
-/* Grid search of the select and prune grids (2, 4, 8, 16 blocks per SM each) on one batched search of these queries, `reps` timed searches per
- * candidate after an untimed one.  Stores the fastest for the batch key and
+/* Grid search of the wavefront kernel's blocks per SM (1, 2, 4, 8; capped at
+ * the number that fits) and of plan_lanes_from (4, 8, 16, 32) on one batched
+ * search of these queries, `reps` timed searches per candidate after an
+ * untimed one.  Stores the fastest for the batch key and
  * sets best->front_cap to twice the front-pool entries per node the search
  * used, rounded up to a power of two (at least 16).  Queries that run out of
  * their pool share keep that status (it is part of the compared results).  Fails

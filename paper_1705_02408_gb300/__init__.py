@@ -56,7 +56,7 @@ class mpap_roadmap_params(C.Structure):
 
 class mpap_query(C.Structure):
     _fields_ = [("beta", C.c_int64), ("group_width_q", C.c_int64), ("lambda_", C.c_float),
-                ("max_iters", C.c_uint32), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
+                ("max_iters", C.c_uint32), ("flags", C.c_uint32), ("wait_us", C.c_uint32)]
 
 
 class mpap_result(C.Structure):
@@ -73,8 +73,8 @@ class mpap_mc_params(C.Structure):
 
 
 class mpap_tuning(C.Structure):
-    _fields_ = [("edge_warps", C.c_uint32), ("select_blocks_per_sm", C.c_uint32),
-                ("prune_blocks_per_sm", C.c_uint32), ("front_cap", C.c_uint32)]
+    _fields_ = [("edge_warps", C.c_uint32), ("wave_blocks_per_sm", C.c_uint32),
+                ("plan_lanes_from", C.c_uint32), ("front_cap", C.c_uint32)]
 
 
 class mpap_cert(C.Structure):
@@ -669,10 +669,10 @@ class SearchResult:
     plans: int
 
 
-def make_query(beta, lam=0.5, group_width_q=0, max_iters=100000, goal_stop=True, interior=False):
+def make_query(beta, lam=0.5, group_width_q=0, max_iters=100000, goal_stop=True, interior=False, wait_us=0):
     flags = (0 if goal_stop else MPAP_QUERY_NO_GOAL_STOP) | (MPAP_QUERY_CHECK_INTERIOR if interior else 0)
     return mpap_query(beta=int(beta), group_width_q=int(group_width_q), lambda_=float(lam),
-                      max_iters=int(max_iters), flags=flags)
+                      max_iters=int(max_iters), flags=flags, wait_us=int(wait_us))
 
 
 def _result(r, buf):
@@ -681,9 +681,9 @@ def _result(r, buf):
 
 
 def search(ws: Workspace, rm: Roadmap, beta, lam=0.5, group_width_q=0, max_iters=100000,
-           goal_stop=True, path_cap=4096, stream=None, interior=False) -> SearchResult:
+           goal_stop=True, path_cap=4096, stream=None, interior=False, wait_us=0) -> SearchResult:
     """mpap_search: Alg. 3 Explore for one query."""
-    q = make_query(beta, lam, group_width_q, max_iters, goal_stop, interior)
+    q = make_query(beta, lam, group_width_q, max_iters, goal_stop, interior, wait_us)
     buf = np.zeros(path_cap, np.uint32)
     r = mpap_result(path_cap=path_cap, path=buf.ctypes.data_as(C.POINTER(C.c_uint32)))
     _check(lib().mpap_search(ws.h, rm.h, C.byref(q), C.byref(r), _stream(stream)), "mpap_search")
@@ -878,8 +878,8 @@ class Mlp:
 # Launch-shape tuning
 # ---------------------------------------------------------------------------
 def _tuning_dict(t):
-    return dict(edge_warps=t.edge_warps, select_blocks_per_sm=t.select_blocks_per_sm,
-                prune_blocks_per_sm=t.prune_blocks_per_sm, front_cap=t.front_cap)
+    return dict(edge_warps=t.edge_warps, wave_blocks_per_sm=t.wave_blocks_per_sm,
+                plan_lanes_from=t.plan_lanes_from, front_cap=t.front_cap)
 
 
 def tuning_get(dim_kind, V):
@@ -888,8 +888,8 @@ def tuning_get(dim_kind, V):
     return _tuning_dict(t)
 
 
-def tuning_set(dim_kind, V, edge_warps=8, select_blocks_per_sm=16, prune_blocks_per_sm=16, front_cap=64):
-    t = mpap_tuning(edge_warps, select_blocks_per_sm, prune_blocks_per_sm, front_cap)
+def tuning_set(dim_kind, V, edge_warps=8, wave_blocks_per_sm=8, plan_lanes_from=8, front_cap=64):
+    t = mpap_tuning(edge_warps, wave_blocks_per_sm, plan_lanes_from, front_cap)
     _check(lib().mpap_tuning_set(int(dim_kind), int(V), C.byref(t)), "mpap_tuning_set")
 
 

@@ -691,12 +691,13 @@ int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const
   unsigned long long pool_used = 0;
   uint64_t nodes = 0;
   for (uint32_t i = 0; i < nq; ++i) nodes += rms[i] ? rms[i]->V : 0u;
-  const uint32_t grids[] = {2, 4, 8, 16};
-  for (uint32_t sel : grids) {
-    for (uint32_t pru : grids) {
+  const uint32_t blocks[] = {1, 2, 4, 8};
+  const uint32_t lanes[] = {4, 8, 16, 32};
+  for (uint32_t bps : blocks) {
+    for (uint32_t lf : lanes) {
       mpap_tuning t = base;
-      t.select_blocks_per_sm = sel;
-      t.prune_blocks_per_sm = pru;
+      t.wave_blocks_per_sm = bps;
+      t.plan_lanes_from = lf;
       mpap::tuning_set(kdim, kV, t);
       double ms = 0.0;
       const int32_t rc = time_reps(st, reps, run, &ms);

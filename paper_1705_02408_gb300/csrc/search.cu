@@ -1,27 +1,30 @@
 // Wavefront multiobjective search: Alg. 3 (Explore) of Ichter et al., with
 // RemoveDominated (Sec. 3) and the perception-heuristic cutoff h <= beta.
 //
-// Per wavefront (iteration i) three kernels run over all queries of a batch:
-//   select  one warp per node with open plans: the group B_i of that node (its
-//           open plans with cost <= i Lambda) is copied to the group array and
-//           closed (P_open <- P_open \ B); every out-neighbour is marked touched.
-//           A group plan at a goal node ends its query before expansion.
-//   prune   one warp per touched node x ("pull"): each in-edge u -> x whose source
-//           holds group plans yields candidates q = (cost + cost_q, max(C, h + S))
-//           (PH(x, p) of Sec. 3), cut at beta, and merged into the stored front of
-//           x.  The merge is an exact skyline under the weak Pareto order with the
-//           total tie key (creation iteration, parent head): old plans win ties,
-//           candidates tie-break by parent head.  Candidates are consumed in
-//           chunks of 32: filter against the front, warp bitonic sort, warp
-//           prefix-min, then a rank merge.  Fronts of up to 32 entries live in
-//           registers (one entry per lane) for the whole merge; larger fronts are
-//           merged between the node's two pool blocks in global memory.
-//           Surviving candidates get arena records at the end.
-//   end     one block: termination per query (goal in group, P_open empty,
-//           iteration cap), list swap, loop condition.
-// The loop runs on the device: the three kernels form the body of a CUDA graph
-// conditional WHILE node, which `end` clears once every query has finished (or
-// the iteration caps are reached), so a search is one graph launch.
+// The whole loop of Alg. 3 is one persistent kernel, k_wave, launched
+// cooperatively (every block resident) over all queries of a batch.  Per
+// wavefront i it runs two phases separated by grid barriers:
+//   expand  one warp per node u with open plans: the group B_i of u (its open
+//           plans with cost <= i Lambda, a cost-ordered part of its front) is
+//           closed (P_open <- P_open \ B) and expanded along every out-edge
+//           u -> x: q = (cost + cost_q, max(C, h + S)) (PH(x, p) of Sec. 3), cut
+//           at beta.  A candidate that the stored front of x, or the previous
+//           candidate of the same source along the same edge, already dominates
+//           is dropped here (the front of x does not change during this phase);
+//           the rest go to the candidate slots of x.  Small groups put the lanes
+//           on the out-edges, large ones on the group plans.
+//   merge   one warp per node x that received candidates: an exact skyline merge
+//           of the candidates into the stored front under the weak Pareto order
+//           with the total tie key (creation iteration, parent head): old plans
+//           win ties, candidates tie-break by parent head.  Candidates are merged
+//           in chunks of 32 (warp bitonic sort, prefix minimum, rank merge);
+//           fronts of up to 32 entries stay in registers, larger ones are merged
+//           between the node's two pool blocks.  New plans get arena records.
+// The last block to reach the barrier after the merge ends the wavefront: per
+// query it applies the loop condition of Alg. 3 (a goal plan in the next group,
+// P_open empty, the iteration cap) and advances the iteration.  Every barrier
+// wait is bounded in %globaltimer time; a wait that runs out ends the kernel
+// with MPAP_ERR_TIMEOUT instead of hanging.
 //
 // HBM layout (NV = nodes summed over the batch):
 //   fronts   a pool of {cost i64, h i64, ref u32 (arena | open | new), aux u32}
@@ -30,7 +33,10 @@
 //            one atomic add and replaced by a block twice the needed size when
 //            too small (the old block is abandoned: at most as much again)
 //   fdesc    [NV] {live block, count, other block, log2 sizes}
-//   group    [cap] {cost, h, ref}, per node offset/count, stamps [NV]
+//   slots    [NV][32] candidates of the current wavefront {cost, h, parent, tie}
+//            (32 B), count per node; more than 32 go to an overflow area in
+//            arrival order and are regrouped per node before the merge
+//   group    [cap] {cost, h, ref}: groups of more than 32 plans
 //   arena    [cap] {head u32, parent u32, iter u32, cost i64} for back-tracing
 #include <algorithm>
 #include <climits>
@@ -43,12 +49,13 @@
 
 namespace mpap {
 
+constexpr uint32_t kSlots = 32;          // inline candidate slots per node and wavefront
+constexpr uint32_t kDefaultWaitUs = 20000000;  // barrier wait limit when no query sets one
+
 struct QueryDev {
-  const uint32_t* rev_ptr;
-  const int4* rev_edge;
-  const int2* rev_peak;     // per reverse edge {Smax, Cmax} (interior check)
   const uint32_t* fwd_ptr;
-  const uint32_t* fwd_dst;
+  const int4* fwd_edge;     // per out-edge {dst, cost_q, S, C}
+  const int2* fwd_peak;     // per out-edge {Smax, Cmax} (interior check)
   const uint8_t* is_goal;
   const uint32_t* goal_list;
   uint32_t n_goal;
@@ -61,6 +68,10 @@ struct QueryDev {
   int64_t Lambda;
   uint64_t pool_base;       // this query's share of the front pool: [base, base + cap)
   uint64_t pool_cap;
+  uint64_t ov_base;         // and of the candidate overflow areas
+  uint64_t ov_cap;
+  uint64_t arena_base;      // and of the plan arena
+  uint64_t arena_cap;
 };
 
 struct QueryState {
@@ -71,9 +82,12 @@ struct QueryState {
   uint32_t goal_hit;
   uint32_t done;
   int32_t status;
-  uint32_t err;          // capacity error bits of this query (pool, arena, group)
-  uint32_t pad;
+  uint32_t err;          // capacity error bits of this query (pool, arena, group, overflow)
+  uint32_t goal_next;    // a goal node holds an open plan of the next group
   unsigned long long pool_n;  // entries of its pool share handed out
+  uint32_t ov_n;         // candidates in its overflow share this wavefront
+  uint32_t seg_n;        // entries of its regrouped overflow share handed out
+  unsigned long long arena_n;  // records of its arena share handed out
 };
 
 struct ResultDev {
@@ -83,57 +97,62 @@ struct ResultDev {
   int32_t status;
 };
 
-// Device-side launch timing of the loop kernels (first block start to last
-// block end, %globaltimer nanoseconds).
-struct KTime {
-  unsigned long long start;
-  unsigned long long total_ns;
-  uint32_t blocks;
-  uint32_t launches;
+// A candidate in a slot (32 B): the plan it would be and, in the overflow area,
+// its node and its index among the node's candidates.
+struct __align__(16) Cand {
+  long long cost;
+  long long h;
+  uint32_t pp;    // parent plan (arena index)
+  uint32_t tb;    // tie key: 1 + parent head
+  uint32_t g;     // node (overflow records)
+  uint32_t i;     // index - kSlots among the node's candidates (overflow records)
 };
 
 struct Ctl {
   uint32_t oh_n[2];
-  uint32_t t_n;
-  uint32_t g_n;
-  unsigned long long arena_n;
+  uint32_t m_n;          // nodes with candidates this wavefront
+  uint32_t g_n;          // group array entries handed out this wavefront
   uint32_t err;
   uint32_t n_done;
-  uint32_t it;          // current wavefront
+  uint32_t it;           // current wavefront
   uint32_t nq;
-  uint32_t iter_cap;    // loop bound (max over queries of max_iters, plus 2)
-  uint32_t prof;        // record KTime
-  uint32_t max_front;   // largest front committed by any node
-  unsigned long long pool_n;  // front pool entries handed out
-  unsigned long long tmp_n;   // bulk-merge scratch entries handed out this wavefront
-  uint32_t b_n;         // nodes queued for the bulk prune this wavefront
-  KTime kt[4];          // select, prune, bulk prune, end
+  uint32_t iter_cap;     // loop bound (max over queries of max_iters, plus 2)
+  uint32_t max_front;    // largest front committed by any node
+  uint32_t lanes_from;   // group size from which the expansion puts lanes on plans
+  uint32_t ov_any;       // some query overflowed its slots this wavefront
+  // grid barrier
+  uint32_t bar_count;
+  uint32_t bar_gen;
+  uint32_t timeout;      // a barrier wait ran out
+  uint32_t pad;
+  unsigned long long wait_ns;  // limit of one barrier wait
+  unsigned long long t_mark;   // %globaltimer at the last barrier release
+  unsigned long long ph_ns[4]; // expand, overflow regrouping, merge, end of wavefront
+  uint32_t waves;
+  uint32_t pad2;
 };
 
 struct WS {
   uint64_t NV;
   uint32_t fcap;           // front pool entries per node (pool = NV fcap)
   uint64_t pcap;           // front pool entries
-  uint64_t acap, gcap;
+  uint64_t acap, gcap, ocap;
   long long* f_cost;       // [pcap] front pool
   long long* f_h;
   uint32_t* f_pid;
   uint32_t* f_aux;
   uint4* fdesc;            // [NV] {live block, count, other block, lg live | lg other << 8}
-  uint64_t tcap;           // bulk-merge scratch entries (reused every wavefront)
-  long long* t_cost;       // [tcap] survivors of one run: cost, h, parent ref, insertion index
-  long long* t_h;
-  uint32_t* t_pp;
-  uint32_t* t_m;
-  uint4* gdesc;            // per node {iteration stamp, group count, group offset, 0}
-  uint32_t* touch_stamp;
+  Cand* slot;              // [NV * kSlots] candidates of this wavefront
+  uint32_t* cand_n;        // [NV] candidates per node this wavefront (0 between wavefronts)
+  Cand* ov;                // [ocap] overflow candidates in arrival order (per-query shares)
+  Cand* ov2;               // [ocap] the same regrouped per node
+  uint32_t* segoff;        // [NV] start of a node's regrouped overflow
   uint32_t* oh_stamp;
-  long long* g_cost;
+  long long* g_cost;       // [gcap] groups of more than 32 plans
   long long* g_h;
   uint32_t* g_pid;
-  uint2* oh_list;           // [2][NV] {node, query} with open plans (this / next wavefront)
-  uint2* t_list;            // [NV] {node, query} touched this wavefront
-  uint2* b_list;            // [NV] {node, query} left to the bulk prune this wavefront
+  uint2* oh_list;          // [2][NV] {node, query} with open plans (this / next wavefront)
+  uint2* m_list;           // [NV] {node, query} with candidates this wavefront
   uint32_t* a_head;
   uint32_t* a_parent;
   uint32_t* a_iter;
@@ -151,11 +170,6 @@ struct WS {
 struct mpap_workspace {
   mpap::WS w{};
   uint32_t max_q = 0;
-  // the device-side wavefront loop (built on first use)
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  uint32_t graph_sel = 0, graph_pru = 0;   // grids captured in the graph (blocks per SM)
   // host record of the last search (for front export and tuning)
   std::vector<uint32_t> last_V, last_base;
   uint32_t last_max_front = 0;
@@ -171,10 +185,6 @@ struct mpap_workspace {
 namespace mpap {
 
 constexpr int kWarpsPerBlock = 8;
-// Resident blocks per SM the prune kernel is compiled for (register budget).
-#ifndef MPAP_PRUNE_MIN_BLOCKS
-#define MPAP_PRUNE_MIN_BLOCKS 4
-#endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 void workspace_free(mpap_workspace* ws);
@@ -204,7 +214,7 @@ __device__ __forceinline__ uint32_t pool_alloc(const WS& w, uint32_t q, uint32_t
   return (o + sz <= Q.pool_cap) ? (uint32_t)(Q.pool_base + o) : kNoBlock;
 }
 
-// Records a capacity error of query q (it ends at the next end-of-wavefront).
+// Records a capacity error of query q (it ends at the end of the wavefront).
 __device__ __forceinline__ void query_error(const WS& w, uint32_t q, uint32_t bit) {
   atomicOr(&w.qs[q].err, bit);
   atomicOr(&w.ctl->err, bit);
@@ -216,59 +226,91 @@ __device__ __forceinline__ unsigned long long global_timer() {
   return t;
 }
 
-__device__ __forceinline__ void ktime_begin(const WS& w, int k) {
-  if (w.ctl->prof && threadIdx.x == 0) atomicMin(&w.ctl->kt[k].start, global_timer());
+__device__ __forceinline__ uint32_t ld_vol(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+
+// ---------------------------------------------------------------------------
+// Grid barrier of the persistent loop.  The launch is cooperative, so every
+// block is resident and the barrier cannot deadlock on scheduling.  Arrival is
+// an atomic count behind a fence; the last block to arrive runs `epi` with all
+// its threads, then releases the others by advancing the generation.  A block
+// that waits longer than ctl->wait_ns (%globaltimer time), or sees that another
+// block gave up, sets ctl->timeout and returns false: its caller leaves the
+// kernel, and so, within one wait limit, does every other block.
+// ---------------------------------------------------------------------------
+template <class Epi>
+__device__ __forceinline__ bool grid_barrier(const WS& w, Epi epi) {
+  __shared__ uint32_t s_last, s_ok;
+  Ctl* c = w.ctl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t gen = ld_vol(&c->bar_gen);
+    __threadfence();
+    const uint32_t arrived = atomicAdd(&c->bar_count, 1u) + 1u;
+    s_last = arrived == gridDim.x ? 1u : 0u;
+    s_ok = 1u;
+    if (!s_last) {
+      const unsigned long long t0 = global_timer();
+      const unsigned long long lim = c->wait_ns;
+      while (ld_vol(&c->bar_gen) == gen) {
+        if (ld_vol(&c->timeout) || global_timer() - t0 > lim) {
+          atomicExch(&c->timeout, 1u);
+          s_ok = 0u;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (s_last) {
+    epi();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      c->bar_count = 0;
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    }
+  }
+  return s_ok != 0u;
 }
 
-// Every warp reports completion; the last one closes the launch (no block
-// barrier, so early-finishing warps leave the SM immediately).
-__device__ __forceinline__ void ktime_end(const WS& w, int k) {
-  if (w.ctl->prof && (threadIdx.x & 31) == 0) {
-    KTime& t = w.ctl->kt[k];
-    __threadfence();
-    const uint32_t total = gridDim.x * gridDim.y * ((blockDim.x + 31) >> 5);
-    const uint32_t done = atomicAdd(&t.blocks, 1u);
-    if (done == total - 1) {
-      const unsigned long long now = global_timer();
-      const unsigned long long s = atomicAdd(&t.start, 0ull);
-      t.total_ns += now - s;
-      t.launches += 1;
-      t.start = ULLONG_MAX;
-      t.blocks = 0;
-      __threadfence();
-    }
+// Phase time between the last release and now, charged to slot k (last block).
+__device__ __forceinline__ void phase_mark(const WS& w, int k) {
+  if (threadIdx.x == 0) {
+    const unsigned long long now = global_timer();
+    w.ctl->ph_ns[k] += now - w.ctl->t_mark;
+    w.ctl->t_mark = now;
   }
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
+__global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from, unsigned long long wait_ns) {
   const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q == 0) {
     Ctl& c = *w.ctl;
     c.oh_n[0] = nq;
     c.oh_n[1] = 0;
-    c.t_n = 0;
+    c.m_n = 0;
     c.g_n = 0;
-    c.arena_n = nq;
     c.err = 0;
-    c.n_done = 0;
     c.it = 0;
     c.nq = nq;
     c.iter_cap = iter_cap;
-    c.prof = prof;
     c.max_front = 1;
-    c.pool_n = 0;
-    c.tmp_n = 0;
-    c.b_n = 0;
-    for (int k = 0; k < 4; ++k) {
-      c.kt[k].start = ULLONG_MAX;
-      c.kt[k].total_ns = 0;
-      c.kt[k].blocks = 0;
-      c.kt[k].launches = 0;
-    }
+    c.lanes_from = lanes_from;
+    c.ov_any = 0;
+    c.bar_count = 0;
+    c.bar_gen = 0;
+    c.timeout = 0;
+    c.wait_ns = wait_ns;
+    c.t_mark = 0;
+    for (int k = 0; k < 4; ++k) c.ph_ns[k] = 0;
+    c.waves = 0;
   }
   if (q >= nq) return;
-  const uint32_t g = w.qd[q].base;   // x_init is node 0 of every roadmap
+  const QueryDev& Q = w.qd[q];
+  const uint32_t g = Q.base;   // x_init is node 0 of every roadmap
   QueryState s;
   s.open_cnt = 1;
   s.expansions = 0;
@@ -278,134 +320,46 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t prof) {
   s.done = 0;
   s.status = 0;
   s.err = 0;
-  s.pad = 0;
+  s.goal_next = 0;
   s.pool_n = 1u << kMinLg;          // the root's block opens the query's share
+  s.ov_n = 0;
+  s.seg_n = 0;
+  s.arena_n = 1;                     // the root plan opens the query's arena share
+  // the first group is {root}: a root inside X_goal ends the query before any
+  // expansion (the loop condition of Alg. 3 is tested first)
+  if (Q.is_goal[0] && !(Q.flags & MPAP_QUERY_NO_GOAL_STOP)) {
+    s.done = 1;
+    s.goal_hit = 1;
+  }
   w.qs[q] = s;
-  const uint32_t o = (uint32_t)w.qd[q].pool_base;
+  const uint32_t o = (uint32_t)Q.pool_base;
+  const uint32_t a = (uint32_t)Q.arena_base;
   w.f_cost[o] = 0;
   w.f_h[o] = 0;
-  w.f_pid[o] = q | kOpen;      // the root plan (x_init, {}, 0, 0) is arena record q
+  w.f_pid[o] = a | kOpen;      // the root plan (x_init, {}, 0, 0) opens the arena share
   w.f_aux[o] = 0;
   w.fdesc[g] = make_uint4(o, 1u, 0u, kMinLg);
-  w.a_head[q] = 0;
-  w.a_parent[q] = kNone;
-  w.a_iter[q] = 0;
-  w.a_cost[q] = 0;
+  w.a_head[a] = 0;
+  w.a_parent[a] = kNone;
+  w.a_iter[a] = 0;
+  w.a_cost[a] = 0;
   w.oh_list[q] = make_uint2(g, q);
   w.oh_stamp[g] = 0;
 }
 
-// ---------------------------------------------------------------------------
-// select: group formation, closing, goal test and marking (warp per node).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_select(WS w) {
-  ktime_begin(w, 0);
-  const uint32_t it = w.ctl->it;
-  const unsigned lane = lane_id();
-  const unsigned lt = (1u << lane) - 1u;
-  const uint32_t n_list = (w.ctl->n_done < w.ctl->nq) ? w.ctl->oh_n[it & 1] : 0u;
-  const uint2* list = w.oh_list + (size_t)(it & 1) * w.NV;
-  uint2* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
-    const uint2 gq = list[k];
-    const uint32_t g = gq.x, q = gq.y;
-    if (w.qs[q].done) continue;
-    const QueryDev& Q = w.qd[q];
-    const uint4 fd = w.fdesc[g];
-    // the out-edge range does not depend on the front: its loads go out now
-    const uint32_t u = g - Q.base;
-    const uint32_t e_beg = Q.fwd_ptr[u], e_end = Q.fwd_ptr[u + 1];
-    const uint32_t n = fd.y;
-    const size_t o = fd.x;
-    const long long thr = (long long)it * Q.Lambda;
-    uint32_t cnt = 0;
-    bool rest = false;
-    // a front of at most 32 entries stays in registers for the second pass
-    uint32_t pid0 = 0;
-    long long c0 = 0;
-    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
-      const uint32_t j = j0 + lane;
-      uint32_t pid = 0;
-      long long c = 0;
-      if (j < n) {
-        pid = w.f_pid[o + j];
-        c = w.f_cost[o + j];
-      }
-      if (j0 == 0) {
-        pid0 = pid;
-        c0 = c;
-      }
-      const bool open = (j < n) && (pid & kOpen);
-      cnt += __popc(__ballot_sync(kFull, open && c <= thr));
-      rest = rest || __any_sync(kFull, open && c > thr);
-    }
-    if (cnt) {
-      uint32_t off = 0;
-      if (lane == 0) off = atomicAdd(&w.ctl->g_n, cnt);
-      off = __shfl_sync(kFull, off, 0);
-      const bool fits = (uint64_t)off + cnt <= w.gcap;
-      if (!fits) {
-        if (lane == 0) query_error(w, q, kErrGroup);
-      } else {
-        uint32_t r0 = 0;
-        for (uint32_t j0 = 0; j0 < n; j0 += 32) {
-          const uint32_t j = j0 + lane;
-          uint32_t pid = pid0;
-          long long c = c0;
-          if (j0 > 0 && j < n) {
-            pid = w.f_pid[o + j];
-            c = w.f_cost[o + j];
-          }
-          const bool isg = (j < n) && (pid & kOpen) && c <= thr;
-          const unsigned bal = __ballot_sync(kFull, isg);
-          if (isg) {
-            const uint32_t r = off + r0 + __popc(bal & lt);
-            w.g_cost[r] = c;
-            w.g_h[r] = w.f_h[o + j];
-            w.g_pid[r] = pid & kPidMask;
-            w.f_pid[o + j] = pid & ~kOpen;
-          }
-          r0 += __popc(bal);
-        }
-        if (lane == 0) {
-          w.gdesc[g] = make_uint4(it, cnt, off, 0u);
-          atomic_add_i64(&w.qs[q].open_cnt, -(long long)cnt);
-          if (Q.is_goal[u]) w.qs[q].goal_hit = 1u;
-        }
-        // mark the out-neighbours of this node as touched (deduplicated by stamp;
-        // a plain read first skips the atomic for nodes already marked), 64 edges
-        // per step with the loads of both halves in flight together
-        for (uint32_t e0 = e_beg; e0 < e_end; e0 += 64) {
-          const uint32_t ea = e0 + lane, eb = e0 + 32 + lane;
-          const bool va = ea < e_end, vb = eb < e_end;
-          const uint32_t ga = va ? Q.base + __ldg(&Q.fwd_dst[ea]) : 0u;
-          const uint32_t gb = vb ? Q.base + __ldg(&Q.fwd_dst[eb]) : 0u;
-          const uint32_t sa = va ? w.touch_stamp[ga] : it;
-          const uint32_t sb = vb ? w.touch_stamp[gb] : it;
-          bool fa = false, fb = false;
-          if (sa != it) fa = atomicExch(&w.touch_stamp[ga], it) != it;
-          if (sb != it) fb = atomicExch(&w.touch_stamp[gb], it) != it;
-          const unsigned bala = __ballot_sync(kFull, fa), balb = __ballot_sync(kFull, fb);
-          if (bala | balb) {
-            uint32_t pos = 0;
-            if (lane == 0) pos = atomicAdd(&w.ctl->t_n, __popc(bala) + __popc(balb));
-            pos = __shfl_sync(kFull, pos, 0);
-            if (fa) w.t_list[pos + __popc(bala & lt)] = make_uint2(ga, q);
-            if (fb) w.t_list[pos + __popc(bala) + __popc(balb & lt)] = make_uint2(gb, q);
-          }
-        }
-      }
-    }
-    if (rest && lane == 0) {
-      if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = make_uint2(g, q);
-    }
-  }
-  ktime_end(w, 0);
+// Counts the queries k_init ended at once (root in X_goal).
+__global__ void k_init_done(WS w, uint32_t nq) {
+  __shared__ uint32_t s_n;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x)
+    if (w.qs[q].done) atomicAdd(&s_n, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) w.ctl->n_done = s_n;
 }
-
 // ---------------------------------------------------------------------------
-// prune: pull candidates into the front of each touched node (warp per node).
+// Skyline merge of candidates into a front, 32 candidates at a time (warp per
+// node).
 // ---------------------------------------------------------------------------
 struct WarpSmem {
   long long s_cost[32];    // chunk survivors, sorted
@@ -636,175 +590,6 @@ __device__ __forceinline__ void merge_chunk_slab(const WS& w, uint32_t q, FrontC
   fc.any_new = true;
   __syncwarp();
 }
-
-// Bulk merge of one in-edge's candidate run into a block-mode front.  The run is
-// the source's group (a contiguous part of its front: costs increasing, h
-// decreasing) shifted along one edge, so its costs increase and its h do not
-// increase: it is its own skyline once entries whose h equals their
-// predecessor's are dropped.  Pass 1 keeps the run entries that pass the beta
-// cutoff and survive the live front, compacting them into a temporary pool block
-// with their insertion index m (front entries of lower or equal cost); pass 2
-// sweeps the front once, dropping the entries a survivor dominates and
-// interleaving the survivors.  O(n/32 + L log n / 32) warp steps per run, against
-// O(L/32 * n/32) for chunked merging.
-// Returns false (and changes nothing) when this wavefront's scratch is used up;
-// the caller then merges the run in chunks.
-__device__ __forceinline__ bool merge_run_bulk(const WS& w, uint32_t q, FrontCursor& fc, long long beta, uint32_t goff,
-                                               uint32_t L, int cq, int S, int C, int Sm, int Cm, bool interior,
-                                               uint32_t tb) {
-  const unsigned lane = lane_id();
-  const unsigned lt = (1u << lane) - 1u;
-  const size_t o = fc.off;
-  const uint32_t n = fc.n;
-  // run entry r: candidate, and whether it passes the cutoff, its run
-  // predecessor and the live front (m = front entries of lower or equal cost)
-  auto entry = [&](uint32_t r, long long& cc, long long& ch, uint32_t& pp, uint32_t& m) -> bool {
-    const uint32_t gi = goff + r;
-    const long long gh = w.g_h[gi];
-    cc = w.g_cost[gi] + (long long)cq;
-    const long long hh = gh + (long long)S;
-    ch = hh > (long long)C ? hh : (long long)C;
-    pp = w.g_pid[gi];
-    long long peak = ch;
-    if (interior) {
-      const long long hp = gh + (long long)Sm;
-      peak = hp > (long long)Cm ? hp : (long long)Cm;
-    }
-    if (peak > beta) return false;
-    if (r > 0) {
-      // the run predecessor (lower cost, h never lower) dominates iff its h is equal
-      const long long ph = w.g_h[gi - 1] + (long long)S;
-      const long long pch = ph > (long long)C ? ph : (long long)C;
-      if (pch <= ch) return false;
-    }
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (w.f_cost[o + mid] <= cc) lo = mid + 1; else hi = mid;
-    }
-    m = lo;
-    if (lo > 0) {
-      const uint32_t j = lo - 1;
-      const long long fcost = w.f_cost[o + j], fh = w.f_h[o + j];
-      const uint32_t fpid = w.f_pid[o + j];
-      const uint32_t ftb = (fpid & kNew) ? w.f_aux[o + j] : 0u;
-      if (fh <= ch && (fcost < cc || fh < ch || ftb < tb)) return false;
-    }
-    return true;
-  };
-  // pass 1a: count the survivors, then take exactly that much scratch
-  uint32_t ns = 0;
-  for (uint32_t r0 = 0; r0 < L; r0 += 32) {
-    const uint32_t r = r0 + lane;
-    long long cc, ch;
-    uint32_t pp, m;
-    ns += __popc(__ballot_sync(kFull, r < L && entry(r, cc, ch, pp, m)));
-  }
-  if (ns == 0) return true;
-  unsigned long long T = 0;
-  if (lane == 0) T = atomicAdd(&w.ctl->tmp_n, (unsigned long long)ns);
-  T = __shfl_sync(kFull, T, 0);
-  if (T + ns > w.tcap) return false;
-  // pass 1b: the survivors, in run order, with their insertion index m
-  uint32_t k = 0;
-  for (uint32_t r0 = 0; r0 < L; r0 += 32) {
-    const uint32_t r = r0 + lane;
-    long long cc = 0, ch = 0;
-    uint32_t pp = 0, m = 0;
-    const bool ok = r < L && entry(r, cc, ch, pp, m);
-    const unsigned sb = __ballot_sync(kFull, ok);
-    if (ok) {
-      const size_t t = (size_t)T + k + __popc(sb & lt);
-      w.t_cost[t] = cc;
-      w.t_h[t] = ch;
-      w.t_pp[t] = pp;
-      w.t_m[t] = m;
-    }
-    k += __popc(sb);
-  }
-  if (!ensure_other(w, q, fc, n + ns)) return true;
-  __syncwarp();
-  // pass 2: one sweep over the front
-  const size_t on = fc.off2;
-  uint32_t K = 0, sp = 0, rem_open = 0;
-  for (uint32_t j0 = 0; j0 < n; j0 += 32) {
-    const uint32_t j = j0 + lane;
-    const bool valid = j < n;
-    long long fcost = 0, fh = 0;
-    uint32_t fpid = 0, faux = 0;
-    if (valid) {
-      fcost = w.f_cost[o + j];
-      fh = w.f_h[o + j];
-      fpid = w.f_pid[o + j];
-      faux = w.f_aux[o + j];
-    }
-    const uint32_t ftb = (fpid & kNew) ? faux : 0u;
-    // survivors of lower or equal cost; the last of them is the only one that can dominate
-    uint32_t lo = 0, hi = ns;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (w.t_cost[(size_t)T + mid] <= fcost) lo = mid + 1; else hi = mid;
-    }
-    bool dom = false;
-    if (valid && lo > 0) {
-      const long long sc = w.t_cost[(size_t)T + lo - 1], sh = w.t_h[(size_t)T + lo - 1];
-      dom = sh <= fh && (sc < fcost || sh < fh || tb < ftb);
-    }
-    const bool keep = valid && !dom;
-    if (dom && (fpid & kOpen) && !(fpid & kNew)) rem_open++;
-    const unsigned kb = __ballot_sync(kFull, keep);
-    if (keep) {
-      const size_t pos = on + K + __popc(kb & lt) + lo;
-      w.f_cost[pos] = fcost;
-      w.f_h[pos] = fh;
-      w.f_pid[pos] = fpid;
-      w.f_aux[pos] = faux;
-    }
-    // survivors inserted before a front entry of this chunk (m < end of chunk)
-    const uint32_t jend = min(j0 + 32u, n);
-    for (;;) {
-      const uint32_t s = sp + lane;
-      bool emit = false;
-      uint32_t m = 0;
-      if (s < ns) {
-        m = w.t_m[(size_t)T + s];
-        emit = m < jend;
-      }
-      const unsigned eb = __ballot_sync(kFull, emit);
-      if (emit) {
-        const uint32_t d = m - j0;   // 0 .. 31: earlier chunks emitted every m < j0
-        const size_t pos = on + s + K + __popc(kb & ((1u << d) - 1u));
-        w.f_cost[pos] = w.t_cost[(size_t)T + s];
-        w.f_h[pos] = w.t_h[(size_t)T + s];
-        w.f_pid[pos] = w.t_pp[(size_t)T + s] | kNew;
-        w.f_aux[pos] = tb;
-      }
-      const uint32_t c = __popc(eb);
-      sp += c;
-      if (c < 32) break;
-    }
-    K += __popc(kb);
-  }
-  // survivors after every front entry
-  for (uint32_t s0 = sp; s0 < ns; s0 += 32) {
-    const uint32_t s = s0 + lane;
-    if (s < ns) {
-      const size_t pos = on + s + K;
-      w.f_cost[pos] = w.t_cost[(size_t)T + s];
-      w.f_h[pos] = w.t_h[(size_t)T + s];
-      w.f_pid[pos] = w.t_pp[(size_t)T + s] | kNew;
-      w.f_aux[pos] = tb;
-    }
-  }
-  for (int sft = 16; sft > 0; sft >>= 1) rem_open += __shfl_xor_sync(kFull, rem_open, sft);
-  fc.removed_open += rem_open;
-  swap_blocks(fc);
-  fc.n = K + ns;
-  fc.any_new = true;
-  __syncwarp();
-  return true;
-}
-
 // Register-mode merge: the front (n <= 32) is held one entry per lane; all
 // dominance tests are broadcasts over lanes.  If the merged front exceeds 32
 // entries it is written to the node's other block and the node continues in
@@ -890,6 +675,95 @@ __device__ __forceinline__ void merge_chunk_reg(const WS& w, uint32_t q, FrontCu
   __syncwarp();
 }
 
+// r arena records of query q's share (call from one lane); kNone when the share
+// is used up (the query then fails alone).
+__device__ __forceinline__ uint32_t arena_take(const WS& w, uint32_t q, uint32_t r) {
+  const unsigned long long o = atomicAdd(&w.qs[q].arena_n, (unsigned long long)r);
+  const QueryDev& Q = w.qd[q];
+  if (o + r > Q.arena_cap) {
+    query_error(w, q, kErrArena);
+    return kNone;
+  }
+  return (uint32_t)(Q.arena_base + o);
+}
+
+// Per-block shared state of the wavefront kernel: per-query counter
+// increments accumulated in shared memory (flushed to the query states once per
+// phase, so the per-node updates never contend on one global address; batches
+// of more than kAccQ queries add to the states directly), and per-warp buffers
+// of nodes bound for the next open list.
+constexpr uint32_t kAccQ = 256;
+struct WaveSmem {
+  long long open[kAccQ];
+  unsigned long long plans[kAccQ];
+  unsigned long long exps[kAccQ];
+  uint2 lbuf[kWarpsPerBlock][32];
+};
+
+struct WarpCtx {
+  WaveSmem* s;
+  uint2* next;        // open list of the next wavefront
+  uint32_t lb_n;      // nodes in this warp's buffer (warp-uniform)
+  uint32_t nq;
+  uint32_t it;
+};
+
+__device__ __forceinline__ void acc_open(const WS& w, WarpCtx& cx, uint32_t q, long long v) {
+  if (!v) return;
+  if (cx.nq <= kAccQ) atomicAdd(reinterpret_cast<unsigned long long*>(&cx.s->open[q]), (unsigned long long)v);
+  else atomic_add_i64(&w.qs[q].open_cnt, v);
+}
+__device__ __forceinline__ void acc_plans(const WS& w, WarpCtx& cx, uint32_t q, unsigned long long v) {
+  if (!v) return;
+  if (cx.nq <= kAccQ) atomicAdd(&cx.s->plans[q], v);
+  else atomicAdd(&w.qs[q].plans, v);
+}
+__device__ __forceinline__ void acc_exps(const WS& w, WarpCtx& cx, uint32_t q, unsigned long long v) {
+  if (!v) return;
+  if (cx.nq <= kAccQ) atomicAdd(&cx.s->exps[q], v);
+  else atomicAdd(&w.qs[q].expansions, v);
+}
+
+// Adds the block's accumulated increments to the query states (whole block).
+__device__ __forceinline__ void flush_acc(const WS& w, WaveSmem& s, uint32_t nq) {
+  __syncthreads();
+  if (nq <= kAccQ) {
+    for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+      if (s.open[q]) atomic_add_i64(&w.qs[q].open_cnt, s.open[q]);
+      if (s.plans[q]) atomicAdd(&w.qs[q].plans, s.plans[q]);
+      if (s.exps[q]) atomicAdd(&w.qs[q].expansions, s.exps[q]);
+      s.open[q] = 0;
+      s.plans[q] = 0;
+      s.exps[q] = 0;
+    }
+  }
+}
+
+// Moves this warp's buffered nodes to the next open list (one atomic).
+__device__ __forceinline__ void flush_next(const WS& w, WarpCtx& cx) {
+  if (!cx.lb_n) return;
+  const unsigned lane = lane_id();
+  __syncwarp();
+  uint32_t b = 0;
+  if (lane == 0) b = atomicAdd(&w.ctl->oh_n[(cx.it + 1) & 1], cx.lb_n);
+  b = __shfl_sync(kFull, b, 0);
+  if (lane < cx.lb_n) cx.next[b + lane] = cx.s->lbuf[threadIdx.x >> 5][lane];
+  __syncwarp();
+  cx.lb_n = 0;
+}
+
+// Puts node g of query q on the next open list unless it is there already
+// (its stamp); warp-uniform arguments.
+__device__ __forceinline__ void push_next(const WS& w, WarpCtx& cx, uint32_t g, uint32_t q) {
+  const unsigned lane = lane_id();
+  uint32_t fresh = 0;
+  if (lane == 0) fresh = atomicExch(&w.oh_stamp[g], cx.it + 1) != cx.it + 1 ? 1u : 0u;
+  fresh = __shfl_sync(kFull, fresh, 0);
+  if (!fresh) return;
+  if (lane == 0) cx.s->lbuf[threadIdx.x >> 5][cx.lb_n] = make_uint2(g, q);
+  if (++cx.lb_n == 32) flush_next(w, cx);
+}
+
 // Arena records for the new entries of a block-mode front (marked open);
 // returns their number.
 __device__ __forceinline__ uint32_t arena_block(const WS& w, uint32_t q, uint32_t x, uint32_t it,
@@ -905,19 +779,18 @@ __device__ __forceinline__ uint32_t arena_block(const WS& w, uint32_t q, uint32_
     const bool isnew = (j < fc.n) && (pid & kNew);
     const unsigned bal = __ballot_sync(kFull, isnew);
     if (!bal) continue;
-    unsigned long long a0 = 0;
-    if (lane == 0) a0 = atomicAdd(&w.ctl->arena_n, (unsigned long long)__popc(bal));
+    uint32_t a0 = 0;
+    if (lane == 0) a0 = arena_take(w, q, (uint32_t)__popc(bal));
     a0 = __shfl_sync(kFull, a0, 0);
     if (isnew) {
-      const unsigned long long a = a0 + __popc(bal & lt);
-      if (a < w.acap) {
+      if (a0 != kNone) {
+        const uint32_t a = a0 + (uint32_t)__popc(bal & lt);
         w.a_head[a] = x;
         w.a_parent[a] = pid & kPidMask;
         w.a_iter[a] = it + 1;
         w.a_cost[a] = w.f_cost[o + j];
-        w.f_pid[o + j] = (uint32_t)a | kOpen;
+        w.f_pid[o + j] = a | kOpen;
       } else {
-        query_error(w, q, kErrArena);
         w.f_pid[o + j] = kOpen;
       }
       w.f_aux[o + j] = 0;
@@ -928,165 +801,491 @@ __device__ __forceinline__ uint32_t arena_block(const WS& w, uint32_t q, uint32_
 }
 
 // The node's new descriptor and counters, and its place in the next open list.
-__device__ __forceinline__ void commit_tail(const WS& w, uint32_t q, uint32_t g, uint32_t it, const FrontCursor& fc,
-                                            uint32_t n_new, uint2* next) {
+__device__ __forceinline__ void commit_tail(const WS& w, WarpCtx& cx, uint32_t q, uint32_t g, const FrontCursor& fc,
+                                            uint32_t n_new) {
   if (lane_id() == 0) {
     w.fdesc[g] = make_uint4(fc.off, fc.n, fc.off2, fc.lg | (fc.lg2 << 8));
-    atomic_add_i64(&w.qs[q].open_cnt, (long long)n_new - (long long)fc.removed_open);
-    atomicAdd(&w.qs[q].plans, (unsigned long long)n_new);
-    atomicMax(&w.ctl->max_front, fc.n);
-    if (atomicExch(&w.oh_stamp[g], it + 1) != it + 1) next[atomicAdd(&w.ctl->oh_n[(it + 1) & 1], 1u)] = make_uint2(g, q);
+    acc_open(w, cx, q, (long long)n_new - (long long)fc.removed_open);
+    acc_plans(w, cx, q, n_new);
+    if (fc.n > ld_vol(&w.ctl->max_front)) atomicMax(&w.ctl->max_front, fc.n);
   }
+  push_next(w, cx, g, q);
 }
 
-// One node whose front is in block mode (more than 32 plans) at the start of the
-// wavefront: if its in-edge runs are long on average every run is merged in
-// bulk, otherwise its candidates are merged in chunks of 32; then the front is
-// committed.
-__device__ __forceinline__ void prune_node_bulk(const WS& w, WarpSmem& sm, uint32_t q, uint32_t g, uint32_t x,
-                                             const QueryDev& Q, uint32_t it, uint32_t e_beg, uint32_t e_end,
-                                             bool interior, uint2* next) {
-  const unsigned lane = lane_id();
-  FrontCursor fc;
-  {
-    const uint4 fd = w.fdesc[g];
-    fc.off = fd.x;
-    fc.n = fd.y;
-    fc.off2 = fd.z;
-    fc.lg = fd.w & 0xFFu;
-    fc.lg2 = (fd.w >> 8) & 0xFFu;
+// ---------------------------------------------------------------------------
+// Expansion (Alg. 3: every group plan along every out-edge of its head, the
+// beta cutoff, and the part of RemoveDominated that the stored front of the
+// target decides on its own).
+// ---------------------------------------------------------------------------
+
+// Group plans of one node staged per warp (groups of at most 32 plans).
+struct GroupSmem {
+  long long c[32];
+  long long h[32];
+  uint32_t p[32];
+};
+
+// First index in the cost-sorted front [o, o + n) whose cost exceeds c,
+// searching from index i (fronts are strictly increasing in cost).
+__device__ __forceinline__ uint32_t front_upper(const WS& w, size_t o, uint32_t n, uint32_t i, long long c) {
+  if (n - i > 16) {
+    uint32_t lo = i, hi = n;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (w.f_cost[o + mid] <= c) lo = mid + 1; else hi = mid;
+    }
+    return lo;
   }
-  fc.reg = false;
-  fc.err = false;
-  fc.removed_open = 0;
-  fc.any_new = false;
-  fc.rc = fc.rh = 0;
-  fc.rp = fc.ra = 0;
-  unsigned long long exps = 0;
-  // runs long on average (more than 32 candidates per run): bulk merges; else
-  // all candidates in chunks of 32
-  uint32_t ctot = 0, runs = 0;
-  for (uint32_t e0 = e_beg; e0 < e_end; e0 += 32) {
-    const uint32_t e = e0 + lane;
-    uint32_t cnt = 0;
-    if (e < e_end) {
-      const uint4 gd = w.gdesc[Q.base + (uint32_t)__ldg(&Q.rev_edge[e]).x];
-      if (gd.x == it) cnt = gd.y;
-    }
-    ctot += __reduce_add_sync(kFull, cnt);
-    runs += __popc(__ballot_sync(kFull, cnt > 0));
-  }
-  const bool bulk = ctot > 32u * runs;
-  for (uint32_t e0 = e_beg; e0 < e_end; e0 += 32) {
-    const uint32_t e = e0 + lane;
-    int4 ed = make_int4(0, 0, 0, 0);
-    int2 pk = make_int2(0, 0);
-    uint32_t cnt = 0, goff = 0;
-    if (e < e_end) {
-      ed = __ldg(&Q.rev_edge[e]);
-      if (interior) pk = __ldg(&Q.rev_peak[e]);
-      const uint4 gd = w.gdesc[Q.base + (uint32_t)ed.x];
-      if (gd.x == it) {
-        cnt = gd.y;
-        goff = gd.z;
-      }
-    }
-    exps += __reduce_add_sync(kFull, cnt);
-    if (!bulk) {
-      // chunked: candidates of all runs of this chunk of in-edges, 32 at a time
-      const uint32_t incl = warp_incl_scan(cnt);
-      const uint32_t total = __shfl_sync(kFull, incl, 31);
-      const uint32_t excl = incl - cnt;
-      for (uint32_t c0 = 0; c0 < total && !fc.err; c0 += 32) {
-        const uint32_t c = c0 + lane;
-        uint32_t owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const uint32_t probe = owner + step;
-          if (__shfl_sync(kFull, excl, probe) <= c) owner = probe;
-        }
-        const uint32_t o_excl = __shfl_sync(kFull, excl, owner), o_goff = __shfl_sync(kFull, goff, owner);
-        const int o_src = __shfl_sync(kFull, ed.x, owner), o_cq = __shfl_sync(kFull, ed.y, owner);
-        const int o_S = __shfl_sync(kFull, ed.z, owner), o_C = __shfl_sync(kFull, ed.w, owner);
-        const int o_Sm = __shfl_sync(kFull, pk.x, owner), o_Cm = __shfl_sync(kFull, pk.y, owner);
-        bool ok = false;
-        long long cc = 0, ch = 0;
-        uint32_t pp = 0;
-        if (c < total) {
-          const uint32_t gi = o_goff + (c - o_excl);
-          const long long gh = w.g_h[gi];
-          cc = w.g_cost[gi] + (long long)o_cq;
-          const long long hh = gh + (long long)o_S;
-          ch = hh > (long long)o_C ? hh : (long long)o_C;
-          pp = w.g_pid[gi];
-          long long peak = ch;
-          if (interior) {
-            const long long hp = gh + (long long)o_Sm;
-            peak = hp > (long long)o_Cm ? hp : (long long)o_Cm;
-          }
-          ok = peak <= Q.beta;
-        }
-        merge_chunk_slab(w, q, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
-      }
-      continue;
-    }
-    for (unsigned rb = __ballot_sync(kFull, cnt > 0); rb; rb &= rb - 1) {
-      const int l = __ffs(rb) - 1;
-      const uint32_t r_goff = __shfl_sync(kFull, goff, l), r_cnt = __shfl_sync(kFull, cnt, l);
-      const int r_src = __shfl_sync(kFull, ed.x, l), r_cq = __shfl_sync(kFull, ed.y, l);
-      const int r_S = __shfl_sync(kFull, ed.z, l), r_C = __shfl_sync(kFull, ed.w, l);
-      const int r_Sm = __shfl_sync(kFull, pk.x, l), r_Cm = __shfl_sync(kFull, pk.y, l);
-      if (fc.err) continue;
-      if (merge_run_bulk(w, q, fc, Q.beta, r_goff, r_cnt, r_cq, r_S, r_C, r_Sm, r_Cm, interior, 1u + (uint32_t)r_src))
-        continue;
-      // scratch used up this wavefront: merge the run in chunks of 32
-      for (uint32_t r0 = 0; r0 < r_cnt && !fc.err; r0 += 32) {
-        const uint32_t r = r0 + lane;
-        bool ok = false;
-        long long cc = 0, ch = 0;
-        uint32_t pp = 0;
-        if (r < r_cnt) {
-          const uint32_t gi = r_goff + r;
-          const long long gh = w.g_h[gi];
-          cc = w.g_cost[gi] + (long long)r_cq;
-          const long long hh = gh + (long long)r_S;
-          ch = hh > (long long)r_C ? hh : (long long)r_C;
-          pp = w.g_pid[gi];
-          long long peak = ch;
-          if (interior) {
-            const long long hp = gh + (long long)r_Sm;
-            peak = hp > (long long)r_Cm ? hp : (long long)r_Cm;
-          }
-          ok = peak <= Q.beta;
-        }
-        merge_chunk_slab(w, q, fc, sm, ok, cc, ch, 1u + (uint32_t)r_src, pp);
-      }
-    }
-  }
-  if (fc.any_new && !fc.err) commit_tail(w, q, g, it, fc, arena_block(w, q, x, it, fc), next);
-  if (lane == 0 && exps) atomicAdd(&w.qs[q].expansions, exps);
+  while (i < n && w.f_cost[o + i] <= c) ++i;
+  return i;
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_prune(WS w) {
-  ktime_begin(w, 1);
-  __shared__ WarpSmem smem[kWarpsPerBlock];
-  WarpSmem& sm = smem[threadIdx.x >> 5];
-  const uint32_t it = w.ctl->it;
+// Slots for r new candidates of node gx, taken by several lanes of one warp:
+// returns each lane's first slot; the first lane to reach gx this wavefront
+// puts it on the merge list; slots from kSlots on are overflow records, whose
+// indices in query q's overflow share come back in *ov (warp-aggregated).
+__device__ __forceinline__ uint32_t take_slots(const WS& w, uint32_t q, uint32_t gx, uint32_t r, uint32_t* ov) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
-  const uint32_t n_list = (w.ctl->n_done < w.ctl->nq) ? w.ctl->t_n : 0u;
+  uint32_t s = 0;
+  if (r) s = atomicAdd(&w.cand_n[gx], r);
+  const bool first = r && s == 0;
+  const unsigned fb = __ballot_sync(kFull, first);
+  if (fb) {
+    uint32_t b = 0;
+    if (lane == 0) b = atomicAdd(&w.ctl->m_n, (uint32_t)__popc(fb));
+    b = __shfl_sync(kFull, b, 0);
+    if (first) w.m_list[b + __popc(fb & lt)] = make_uint2(gx, q);
+  }
+  const uint32_t nov = (s + r > kSlots) ? s + r - max(s, kSlots) : 0u;
+  const uint32_t incl = warp_incl_scan(nov);
+  const uint32_t tot = __shfl_sync(kFull, incl, 31);
+  uint32_t b = 0;
+  if (tot) {
+    if (lane == 0) b = atomicAdd(&w.qs[q].ov_n, tot);
+    b = __shfl_sync(kFull, b, 0);
+  }
+  *ov = b + incl - nov;
+  return s;
+}
+
+// Stores candidate cd as candidate s of node gx (a slot, or overflow record oi
+// of query q's share).
+__device__ __forceinline__ void put_cand(const WS& w, const QueryDev& Q, uint32_t q, uint32_t gx, uint32_t s,
+                                         uint32_t& oi, Cand cd) {
+  if (s < kSlots) {
+    w.slot[(size_t)gx * kSlots + s] = cd;
+  } else {
+    if (oi < Q.ov_cap) {
+      cd.g = gx;
+      cd.i = s - kSlots;
+      w.ov[Q.ov_base + oi] = cd;
+    } else {
+      query_error(w, q, kErrList);
+    }
+    ++oi;
+  }
+}
+
+// Small groups: lanes on the out-edges of u, each lane walking the group plans
+// (cost order) and the target's front together.
+__device__ __forceinline__ void expand_edges(const WS& w, const QueryDev& Q, uint32_t q, uint32_t u, uint32_t e_beg,
+                                             uint32_t e_end, const GroupSmem& gs, uint32_t cnt, bool interior) {
+  const unsigned lane = lane_id();
+  for (uint32_t e0 = e_beg; e0 < e_end; e0 += 32) {
+    const uint32_t e = e0 + lane;
+    uint32_t mask = 0, gx = 0;
+    int4 ed = make_int4(0, 0, 0, 0);
+    if (e < e_end) {
+      ed = __ldg(&Q.fwd_edge[e]);
+      int2 pk = make_int2(0, 0);
+      if (interior) pk = __ldg(&Q.fwd_peak[e]);
+      gx = Q.base + (uint32_t)ed.x;
+      const uint4 xd = w.fdesc[gx];
+      const size_t xo = xd.x;
+      const uint32_t xn = xd.y;
+      uint32_t i = 0;
+      long long prev_h = LLONG_MAX;
+      for (uint32_t j = 0; j < cnt; ++j) {
+        const long long gh = gs.h[j];
+        const long long c = gs.c[j] + (long long)ed.y;
+        const long long hh = gh + (long long)ed.z;
+        const long long h = hh > (long long)ed.w ? hh : (long long)ed.w;
+        long long peak = h;
+        if (interior) {
+          const long long hp = gh + (long long)pk.x;
+          peak = hp > (long long)pk.y ? hp : (long long)pk.y;
+        }
+        if (peak > Q.beta) continue;
+        // the previous plan of the run (lower cost) dominates unless h drops
+        if (h >= prev_h) continue;
+        prev_h = h;
+        i = front_upper(w, xo, xn, i, c);
+        if (i > 0 && w.f_h[xo + i - 1] <= h) continue;   // an old plan wins every tie
+        mask |= 1u << j;
+      }
+    }
+    uint32_t oi = 0;
+    uint32_t s = take_slots(w, q, gx, (uint32_t)__popc(mask), &oi);
+    for (uint32_t m = mask; m; m &= m - 1u) {
+      const uint32_t j = (uint32_t)__ffs(m) - 1u;
+      Cand cd;
+      cd.cost = gs.c[j] + (long long)ed.y;
+      const long long hh = gs.h[j] + (long long)ed.z;
+      cd.h = hh > (long long)ed.w ? hh : (long long)ed.w;
+      cd.pp = gs.p[j];
+      cd.tb = 1u + u;
+      cd.g = 0;
+      cd.i = 0;
+      put_cand(w, Q, q, gx, s++, oi, cd);
+    }
+  }
+}
+
+// Large groups: one out-edge at a time, lanes on the group plans (a cost-sorted
+// run of candidates per edge).
+__device__ __forceinline__ void expand_plans(const WS& w, const QueryDev& Q, uint32_t q, uint32_t u, uint32_t e_beg,
+                                             uint32_t e_end, const long long* gc, const long long* gh,
+                                             const uint32_t* gp, uint32_t cnt, bool interior) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  for (uint32_t e = e_beg; e < e_end; ++e) {
+    const int4 ed = __ldg(&Q.fwd_edge[e]);
+    int2 pk = make_int2(0, 0);
+    if (interior) pk = __ldg(&Q.fwd_peak[e]);
+    const uint32_t gx = Q.base + (uint32_t)ed.x;
+    const uint4 xd = w.fdesc[gx];
+    const size_t xo = xd.x;
+    const uint32_t xn = xd.y;
+    long long carry_h = 0;
+    bool carry_ok = false;
+    for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      bool ok = false;
+      long long c = 0, h = 0;
+      uint32_t pp = 0;
+      if (j < cnt) {
+        const long long ghj = gh[j];
+        c = gc[j] + (long long)ed.y;
+        const long long hh = ghj + (long long)ed.z;
+        h = hh > (long long)ed.w ? hh : (long long)ed.w;
+        pp = gp[j];
+        long long peak = h;
+        if (interior) {
+          const long long hp = ghj + (long long)pk.x;
+          peak = hp > (long long)pk.y ? hp : (long long)pk.y;
+        }
+        ok = peak <= Q.beta;
+      }
+      // run predecessor (the previous plan of the group along this edge)
+      long long ph = shfl_up_i64(h, 1);
+      bool pok = __shfl_up_sync(kFull, ok, 1);
+      if (lane == 0) {
+        ph = carry_h;
+        pok = carry_ok;
+      }
+      carry_h = shfl_i64(h, 31);
+      carry_ok = __shfl_sync(kFull, ok, 31);
+      if (ok && pok && ph <= h) ok = false;
+      if (ok) {
+        const uint32_t L = front_upper(w, xo, xn, 0, c);
+        if (L > 0 && w.f_h[xo + L - 1] <= h) ok = false;
+      }
+      const unsigned bal = __ballot_sync(kFull, ok);
+      if (!bal) continue;
+      const uint32_t r = (uint32_t)__popc(bal);
+      // one lane takes the run's slots; the others follow it
+      uint32_t oi = 0;
+      uint32_t s = take_slots(w, q, gx, lane == 0 ? r : 0u, &oi);
+      s = __shfl_sync(kFull, s, 0);
+      oi = __shfl_sync(kFull, oi, 0);
+      if (ok) {
+        const uint32_t k = (uint32_t)__popc(bal & lt);
+        const uint32_t sk = s + k;
+        // overflow indices: records before this one in the run that overflowed
+        uint32_t ok_i = oi + (sk >= kSlots ? sk - max(s, kSlots) : 0u);
+        Cand cd;
+        cd.cost = c;
+        cd.h = h;
+        cd.pp = pp;
+        cd.tb = 1u + u;
+        cd.g = 0;
+        cd.i = 0;
+        put_cand(w, Q, q, gx, sk, ok_i, cd);
+      }
+    }
+  }
+}
+
+__device__ void phase_expand(const WS& w, WarpCtx& cx, GroupSmem& gs) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t it = cx.it;
+  const uint32_t n_list = ld_vol(&w.ctl->oh_n[it & 1]);
+  const uint32_t lanes_from = w.ctl->lanes_from;
+  const uint2* list = w.oh_list + (size_t)(it & 1) * w.NV;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  uint2* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
   for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
-    const uint2 gq = w.t_list[k];
+    const uint2 gq = list[k];
+    const uint32_t g = gq.x, q = gq.y;
+    if (w.qs[q].done) continue;
+    const QueryDev& Q = w.qd[q];
+    const uint32_t u = g - Q.base;
+    const uint32_t e_beg = __ldg(&Q.fwd_ptr[u]), e_end = __ldg(&Q.fwd_ptr[u + 1]);
+    const uint4 fd = w.fdesc[g];
+    const uint32_t n = fd.y;
+    const size_t o = fd.x;
+    const long long thr = (long long)it * Q.Lambda, thr2 = thr + Q.Lambda;
+    uint32_t cnt = 0;
+    bool rest = false, rgoal = false, global_group = false;
+    uint32_t goff = 0;
+    if (n <= 32) {
+      uint32_t pid = 0;
+      long long c = 0;
+      if (lane < n) {
+        pid = w.f_pid[o + lane];
+        c = w.f_cost[o + lane];
+      }
+      const bool open = lane < n && (pid & kOpen);
+      const bool isg = open && c <= thr;
+      const unsigned gb = __ballot_sync(kFull, isg);
+      cnt = (uint32_t)__popc(gb);
+      rest = __any_sync(kFull, open && !isg);
+      rgoal = __any_sync(kFull, open && !isg && c <= thr2);
+      if (isg) {
+        const uint32_t r = (uint32_t)__popc(gb & lt);
+        gs.c[r] = c;
+        gs.h[r] = w.f_h[o + lane];
+        gs.p[r] = pid & kPidMask;
+        w.f_pid[o + lane] = pid & ~kOpen;
+      }
+    } else {
+      for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        uint32_t pid = 0;
+        long long c = 0;
+        if (j < n) {
+          pid = w.f_pid[o + j];
+          c = w.f_cost[o + j];
+        }
+        const bool open = j < n && (pid & kOpen);
+        cnt += (uint32_t)__popc(__ballot_sync(kFull, open && c <= thr));
+        rest = rest || __any_sync(kFull, open && c > thr);
+        rgoal = rgoal || __any_sync(kFull, open && c > thr && c <= thr2);
+      }
+      if (cnt > 32) {
+        if (lane == 0) goff = atomicAdd(&w.ctl->g_n, cnt);
+        goff = __shfl_sync(kFull, goff, 0);
+        global_group = true;
+        if ((uint64_t)goff + cnt > w.gcap) {
+          if (lane == 0) query_error(w, q, kErrGroup);
+          cnt = 0;
+        }
+      }
+      if (cnt) {
+        uint32_t r0 = 0;
+        for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+          const uint32_t j = j0 + lane;
+          uint32_t pid = 0;
+          long long c = 0;
+          if (j < n) {
+            pid = w.f_pid[o + j];
+            c = w.f_cost[o + j];
+          }
+          const bool isg = j < n && (pid & kOpen) && c <= thr;
+          const unsigned gb = __ballot_sync(kFull, isg);
+          if (isg) {
+            const uint32_t r = r0 + (uint32_t)__popc(gb & lt);
+            if (global_group) {
+              w.g_cost[goff + r] = c;
+              w.g_h[goff + r] = w.f_h[o + j];
+              w.g_pid[goff + r] = pid & kPidMask;
+            } else {
+              gs.c[r] = c;
+              gs.h[r] = w.f_h[o + j];
+              gs.p[r] = pid & kPidMask;
+            }
+            w.f_pid[o + j] = pid & ~kOpen;
+          }
+          r0 += (uint32_t)__popc(gb);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      acc_open(w, cx, q, -(long long)cnt);
+      acc_exps(w, cx, q, (unsigned long long)cnt * (e_end - e_beg));
+      // one of the plans left open may be in the next group at a goal node
+      // (the loop condition of the next iteration)
+      if (rgoal && Q.is_goal[u]) w.qs[q].goal_next = 1u;
+    }
+    // plans left open keep the node on the open list
+    if (rest) push_next(w, cx, g, q);
+    if (cnt) {
+      const bool interior = (Q.flags & MPAP_QUERY_CHECK_INTERIOR) != 0;
+      if (!global_group && cnt < lanes_from)
+        expand_edges(w, Q, q, u, e_beg, e_end, gs, cnt, interior);
+      else if (global_group)
+        expand_plans(w, Q, q, u, e_beg, e_end, w.g_cost + goff, w.g_h + goff, w.g_pid + goff, cnt, interior);
+      else
+        expand_plans(w, Q, q, u, e_beg, e_end, gs.c, gs.h, gs.p, cnt, interior);
+    }
+    __syncwarp();
+  }
+  flush_next(w, cx);
+}
+
+// ---------------------------------------------------------------------------
+// Overflow regrouping (only in wavefronts where a node got more than kSlots
+// candidates): every such node takes a contiguous segment of its query's
+// second overflow share, then every overflow record moves to its node's
+// segment.  The order inside a segment does not matter: the merge is a set
+// function.
+// ---------------------------------------------------------------------------
+__device__ void phase_segments(const WS& w) {
+  const uint32_t n_m = ld_vol(&w.ctl->m_n);
+  const uint32_t nt = gridDim.x * blockDim.x;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_m; k += nt) {
+    const uint2 gq = w.m_list[k];
+    const uint32_t nc = w.cand_n[gq.x];
+    if (nc <= kSlots) continue;
+    const QueryDev& Q = w.qd[gq.y];
+    const uint32_t need = nc - kSlots;
+    const uint32_t off = atomicAdd(&w.qs[gq.y].seg_n, need);
+    if ((uint64_t)off + need > Q.ov_cap) {
+      w.segoff[gq.x] = kNone;
+      query_error(w, gq.y, kErrList);
+    } else {
+      w.segoff[gq.x] = (uint32_t)(Q.ov_base + off);
+    }
+  }
+}
+
+__device__ void phase_scatter(const WS& w) {
+  const uint32_t nq = w.ctl->nq;
+  const uint32_t nt = gridDim.x * blockDim.x;
+  const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint32_t q = 0; q < nq; ++q) {
+    const QueryDev& Q = w.qd[q];
+    const uint32_t cnt = (uint32_t)min((uint64_t)w.qs[q].ov_n, Q.ov_cap);
+    for (uint32_t r = t0; r < cnt; r += nt) {
+      const Cand cd = w.ov[Q.ov_base + r];
+      const uint32_t so = w.segoff[cd.g];
+      if (so != kNone) w.ov2[(size_t)so + cd.i] = cd;
+    }
+  }
+}
+
+// One-pass merge of a register front with few candidates (front + candidates
+// <= 32): the front's entries (lanes 0..n-1, tie key 0: older than any
+// candidate) and the candidates (lanes n..n+nc-1, cc/ch/ctb/cpp of this lane)
+// are sorted together by (cost, h, tie key) over the smallest power-of-two
+// width that holds them; an item survives iff its h is below every h before it
+// (the weak Pareto order with the tie key).  The new front is left in
+// registers, lane j holding entry j.
+__device__ __forceinline__ void merge_small(FrontCursor& fc, WarpSmem& sm, uint32_t nc, long long cc, long long ch,
+                                            uint32_t ctb, uint32_t cpp) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t n = fc.n, t = n + nc;
+  const bool isf = lane < n, isc = lane >= n && lane < t;
+  long long kc = isf ? fc.rc : (isc ? cc : LLONG_MAX);
+  const long long vh = isf ? fc.rh : (isc ? ch : LLONG_MAX);
+  const uint32_t vt = isf ? 0u : (isc ? ctb : 0xFFFFFFFFu);
+  const uint32_t vp = isf ? fc.rp : (isc ? (cpp | kNew) : 0u);
+  const uint32_t va = isf ? fc.ra : (isc ? ctb : 0u);
+  uint32_t W = 2;
+  while (W < t) W <<= 1;
+  // 1. sort on (cost, source lane) within segments of W lanes
+  uint32_t ks = lane;
+  for (uint32_t k = 2; k <= W; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      const long long oc = shfl_xor_i64(kc, (int)j);
+      const uint32_t os = __shfl_xor_sync(kFull, ks, (int)j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool o_less = oc < kc || (oc == kc && os < ks);
+      if ((lower == up) ? o_less : !o_less) {
+        kc = oc;
+        ks = os;
+      }
+    }
+  }
+  long long kh = shfl_i64(vh, (int)ks);
+  uint32_t kt = __shfl_sync(kFull, vt, (int)ks);
+  uint32_t kp = __shfl_sync(kFull, vp, (int)ks);
+  uint32_t ka = __shfl_sync(kFull, va, (int)ks);
+  // 2. equal costs must be ordered by (h, tie key) too (rare): sort again on the full key
+  {
+    const long long pc = shfl_up_i64(kc, 1);
+    if (__any_sync(kFull, lane > 0 && kt != 0xFFFFFFFFu && pc == kc)) {
+      for (uint32_t k = 2; k <= W; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+          const long long oc = shfl_xor_i64(kc, (int)j), oh = shfl_xor_i64(kh, (int)j);
+          const uint32_t ot = __shfl_xor_sync(kFull, kt, (int)j), op = __shfl_xor_sync(kFull, kp, (int)j);
+          const uint32_t oa = __shfl_xor_sync(kFull, ka, (int)j);
+          const bool up = (lane & k) == 0;
+          const bool lower = (lane & j) == 0;
+          const bool o_less = key_less(oc, oh, ot, kc, kh, kt);
+          const bool m_less = key_less(kc, kh, kt, oc, oh, ot);
+          if ((lower == up) ? o_less : m_less) {
+            kc = oc;
+            kh = oh;
+            kt = ot;
+            kp = op;
+            ka = oa;
+          }
+        }
+      }
+    }
+  }
+  // 3. skyline: exclusive prefix minimum of h in sorted order
+  long long pm = kh;
+  for (uint32_t o = 1; o < W; o <<= 1) {
+    const long long x = shfl_up_i64(pm, (int)o);
+    if (lane >= o && x < pm) pm = x;
+  }
+  long long excl = shfl_up_i64(pm, 1);
+  if (lane == 0) excl = LLONG_MAX;
+  const bool valid = lane < W && kt != 0xFFFFFFFFu;
+  const bool surv = valid && kh < excl;
+  const unsigned sb = __ballot_sync(kFull, surv);
+  fc.removed_open += (uint32_t)__popc(__ballot_sync(kFull, valid && !surv && kt == 0u && (kp & kOpen)));
+  fc.any_new = fc.any_new || __any_sync(kFull, surv && (kp & kNew));
+  if (surv) {
+    const uint32_t r = (uint32_t)__popc(sb & lt);
+    sm.st_cost[r] = kc;
+    sm.st_h[r] = kh;
+    sm.st_pid[r] = kp;
+    sm.st_aux[r] = ka;
+  }
+  __syncwarp();
+  fc.n = (uint32_t)__popc(sb);
+  if (lane < fc.n) {
+    fc.rc = sm.st_cost[lane];
+    fc.rh = sm.st_h[lane];
+    fc.rp = sm.st_pid[lane];
+    fc.ra = sm.st_aux[lane];
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Merge (RemoveDominated, Sec. 3, for every node that received candidates).
+// ---------------------------------------------------------------------------
+__device__ void phase_merge(const WS& w, WarpCtx& cx, WarpSmem& sm) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t it = cx.it;
+  const uint32_t n_m = ld_vol(&w.ctl->m_n);
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_m; k += warps) {
+    const uint2 gq = w.m_list[k];
     const uint32_t g = gq.x, q = gq.y;
     const QueryDev& Q = w.qd[q];
-    {
-      const QueryState& s = w.qs[q];
-      if (s.done || (s.goal_hit && !(Q.flags & MPAP_QUERY_NO_GOAL_STOP)) || s.wavefronts >= Q.max_iters)
-        continue;
-    }
     const uint32_t x = g - Q.base;
+    const uint32_t nc = w.cand_n[g];
+    const uint32_t so = nc > kSlots ? w.segoff[g] : 0u;
     FrontCursor fc;
     {
       const uint4 fd = w.fdesc[g];
@@ -1109,68 +1308,33 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
       fc.rp = w.f_pid[o + lane];
       fc.ra = w.f_aux[o + lane];
     }
-    unsigned long long exps = 0;
-    const uint32_t e_end = Q.rev_ptr[x + 1];
-    const bool interior = (Q.flags & MPAP_QUERY_CHECK_INTERIOR) != 0;
-    // a front in block mode from the start goes to the bulk prune kernel
-    const bool to_bulk = !fc.reg;
-    for (uint32_t e0 = to_bulk ? e_end : Q.rev_ptr[x]; e0 < e_end; e0 += 32) {
-      const uint32_t e = e0 + lane;
-      int4 ed = make_int4(0, 0, 0, 0);
-      int2 pk = make_int2(0, 0);
-      uint32_t cnt = 0, goff = 0;
-      if (e < e_end) {
-        ed = __ldg(&Q.rev_edge[e]);
-        if (interior) pk = __ldg(&Q.rev_peak[e]);
-        const uint4 gd = w.gdesc[Q.base + (uint32_t)ed.x];
-        if (gd.x == it) {
-          cnt = gd.y;
-          goff = gd.z;
-        }
-      }
-      const uint32_t incl = warp_incl_scan(cnt);
-      const uint32_t total = __shfl_sync(kFull, incl, 31);
-      const uint32_t excl = incl - cnt;
-      exps += total;
-      for (uint32_t c0 = 0; c0 < total; c0 += 32) {
-        const uint32_t c = c0 + lane;
-        // owner lane: the last lane whose exclusive offset is <= c
-        uint32_t owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const uint32_t probe = owner + step;
-          const uint32_t ev = __shfl_sync(kFull, excl, probe);
-          if (ev <= c) owner = probe;
-        }
-        const uint32_t o_excl = __shfl_sync(kFull, excl, owner);
-        const uint32_t o_goff = __shfl_sync(kFull, goff, owner);
-        const int o_src = __shfl_sync(kFull, ed.x, owner);
-        const int o_cq = __shfl_sync(kFull, ed.y, owner);
-        const int o_S = __shfl_sync(kFull, ed.z, owner);
-        const int o_C = __shfl_sync(kFull, ed.w, owner);
-        const int o_Sm = __shfl_sync(kFull, pk.x, owner);
-        const int o_Cm = __shfl_sync(kFull, pk.y, owner);
+    // candidate i of this node: an inline slot or its regrouped overflow
+    auto load = [&](uint32_t i, long long& cc, long long& ch, uint32_t& tb, uint32_t& pp) -> bool {
+      const Cand* src = nullptr;
+      if (i < kSlots) src = &w.slot[(size_t)g * kSlots + i];
+      else if (so != kNone) src = &w.ov2[(size_t)so + (i - kSlots)];
+      if (!src) return false;
+      const Cand cd = *src;
+      cc = cd.cost;
+      ch = cd.h;
+      tb = cd.tb;
+      pp = cd.pp;
+      return true;
+    };
+    if (fc.reg && fc.n + nc <= 32) {
+      long long cc = 0, ch = 0;
+      uint32_t tb = 0, pp = 0;
+      if (lane >= fc.n && lane < fc.n + nc) load(lane - fc.n, cc, ch, tb, pp);
+      merge_small(fc, sm, nc, cc, ch, tb, pp);
+    } else {
+      for (uint32_t c0 = 0; c0 < nc && !fc.err; c0 += 32) {
+        const uint32_t i = c0 + lane;
         bool ok = false;
         long long cc = 0, ch = 0;
-        uint32_t pp = 0;
-        if (c < total) {
-          const uint32_t gi = o_goff + (c - o_excl);
-          cc = w.g_cost[gi] + (long long)o_cq;
-          const long long hh = w.g_h[gi] + (long long)o_S;
-          ch = hh > (long long)o_C ? hh : (long long)o_C;
-          pp = w.g_pid[gi];
-          // perception-heuristic cutoff: at the new head (Alg. 3), or at every
-          // sub-step of the edge (Eq. 2 for all t)
-          long long peak = ch;
-          if (interior) {
-            const long long hp = w.g_h[gi] + (long long)o_Sm;
-            peak = hp > (long long)o_Cm ? hp : (long long)o_Cm;
-          }
-          ok = peak <= Q.beta;
-        }
-        if (fc.err) continue;
-        if (fc.reg) merge_chunk_reg(w, q, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
-        else merge_chunk_slab(w, q, fc, sm, ok, cc, ch, 1u + (uint32_t)o_src, pp);
+        uint32_t tb = 0, pp = 0;
+        if (i < nc) ok = load(i, cc, ch, tb, pp);
+        if (fc.reg) merge_chunk_reg(w, q, fc, sm, ok, cc, ch, tb, pp);
+        else merge_chunk_slab(w, q, fc, sm, ok, cc, ch, tb, pp);
       }
     }
     if (fc.any_new && !fc.err && fc.reg && (fc.lg == 0 || (1u << fc.lg) < fc.n)) {
@@ -1190,27 +1354,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
     if (fc.any_new && !fc.err) {
       // give every new front entry an arena record and mark it open
       uint32_t n_new = 0;
+      const long long thr2 = (long long)(it + 1) * Q.Lambda;
+      bool gnext = false;
       if (fc.reg) {
         const bool isnew = lane < fc.n && (fc.rp & kNew);
         const unsigned bal = __ballot_sync(kFull, isnew);
-        unsigned long long a0 = 0;
-        if (lane == 0 && bal) a0 = atomicAdd(&w.ctl->arena_n, (unsigned long long)__popc(bal));
+        uint32_t a0 = kNone;
+        if (lane == 0 && bal) a0 = arena_take(w, q, (uint32_t)__popc(bal));
         a0 = __shfl_sync(kFull, a0, 0);
         if (isnew) {
-          const unsigned long long a = a0 + __popc(bal & lt);
-          if (a < w.acap) {
+          if (a0 != kNone) {
+            const uint32_t a = a0 + (uint32_t)__popc(bal & lt);
             w.a_head[a] = x;
             w.a_parent[a] = fc.rp & kPidMask;
             w.a_iter[a] = it + 1;
             w.a_cost[a] = fc.rc;
-            fc.rp = (uint32_t)a | kOpen;
+            fc.rp = a | kOpen;
           } else {
-            query_error(w, q, kErrArena);
             fc.rp = kOpen;
           }
           fc.ra = 0;
         }
-        n_new = __popc(bal);
+        n_new = (uint32_t)__popc(bal);
         // write the register front to the live block
         const size_t o = fc.off;
         if (lane < fc.n) {
@@ -1219,50 +1384,50 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MPAP_PRUNE_MIN_BLOCKS) k_
           w.f_pid[o + lane] = fc.rp;
           w.f_aux[o + lane] = fc.ra;
         }
+        gnext = __any_sync(kFull, lane < fc.n && (fc.rp & kOpen) && fc.rc <= thr2);
       } else {
         n_new = arena_block(w, q, x, it, fc);
+        for (uint32_t j0 = 0; j0 < fc.n; j0 += 32) {
+          const uint32_t j = j0 + lane;
+          const bool hit = j < fc.n && (w.f_pid[(size_t)fc.off + j] & kOpen) && w.f_cost[(size_t)fc.off + j] <= thr2;
+          gnext = gnext || __any_sync(kFull, hit);
+        }
       }
-      commit_tail(w, q, g, it, fc, n_new, next);
+      commit_tail(w, cx, q, g, fc, n_new);
+      // an open plan of the next group at a goal node ends the query at the
+      // top of the next iteration (the loop condition of Alg. 3)
+      if (lane == 0 && gnext && Q.is_goal[x]) w.qs[q].goal_next = 1u;
     }
-    if (lane == 0 && exps) atomicAdd(&w.qs[q].expansions, exps);
-    if (to_bulk && lane == 0) w.b_list[atomicAdd(&w.ctl->b_n, 1u)] = make_uint2(g, q);
+    if (lane == 0) w.cand_n[g] = 0;
   }
-  ktime_end(w, 1);
+  flush_next(w, cx);
 }
 
 // ---------------------------------------------------------------------------
-// bulk prune: the nodes k_prune queued (fronts in block mode at the start of
-// the wavefront), warp per node.  A kernel of its own, so that the
-// register-mode path of k_prune keeps its registers.
+// Work of the last block at the barriers.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) k_prune_bulk(WS w) {
-  ktime_begin(w, 2);
-  __shared__ WarpSmem smem[kWarpsPerBlock];
-  WarpSmem& sm = smem[threadIdx.x >> 5];
-  const uint32_t it = w.ctl->it;
-  const uint32_t n_list = (w.ctl->n_done < w.ctl->nq) ? w.ctl->b_n : 0u;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  uint2* next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
-  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
-    const uint2 gq = w.b_list[k];
-    const uint32_t g = gq.x, q = gq.y;
-    const QueryDev& Q = w.qd[q];
-    const uint32_t x = g - Q.base;
-    prune_node_bulk(w, sm, q, g, x, Q, it, Q.rev_ptr[x], Q.rev_ptr[x + 1], (Q.flags & MPAP_QUERY_CHECK_INTERIOR) != 0,
-                    next);
-  }
-  ktime_end(w, 2);
+// After the expansion: does any query need its overflow regrouped?
+__device__ void epi_mid(const WS& w) {
+  __shared__ uint32_t s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  const uint32_t nq = w.ctl->nq;
+  for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x)
+    if (w.qs[q].ov_n) s_any = 1u;
+  __syncthreads();
+  if (threadIdx.x == 0) w.ctl->ov_any = s_any;
+  phase_mark(w, 0);
 }
 
-// ---------------------------------------------------------------------------
-// end of wavefront (one block): termination per query, list swap, loop control.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_end(WS w, cudaGraphConditionalHandle cond, uint32_t in_graph) {
-  ktime_begin(w, 3);
+// End of wavefront i: the loop condition of Alg. 3 per query (tested in the
+// order of the algorithm: P_open empty, a goal plan in the next group, then the
+// iteration cap), then the next iteration.
+__device__ void epi_end(const WS& w) {
   __shared__ uint32_t s_newly;
-  const uint32_t it = w.ctl->it, nq = w.ctl->nq;
   if (threadIdx.x == 0) s_newly = 0;
   __syncthreads();
+  Ctl* c = w.ctl;
+  const uint32_t it = c->it, nq = c->nq;
   for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
     QueryState& s = w.qs[q];
     const QueryDev& Q = w.qd[q];
@@ -1270,31 +1435,78 @@ __global__ void __launch_bounds__(1024) k_end(WS w, cudaGraphConditionalHandle c
     if (s.err) {
       s.done = 1;
       s.status = MPAP_ERR_CAPACITY;
-    } else if (s.goal_hit && !(Q.flags & MPAP_QUERY_NO_GOAL_STOP)) {
-      s.done = 1;
-    } else if (s.wavefronts >= Q.max_iters) {
-      s.done = 1;
-      s.status = MPAP_ERR_ITER_LIMIT;
     } else {
       s.wavefronts += 1;
-      if (s.open_cnt == 0) s.done = 1;
+      if (s.open_cnt == 0) {
+        s.done = 1;
+      } else if (s.goal_next && !(Q.flags & MPAP_QUERY_NO_GOAL_STOP)) {
+        s.done = 1;
+        s.goal_hit = 1;
+      } else if (s.wavefronts >= Q.max_iters) {
+        s.done = 1;
+        s.status = MPAP_ERR_ITER_LIMIT;
+      }
     }
+    s.goal_next = 0;
+    s.ov_n = 0;
+    s.seg_n = 0;
     if (s.done) atomicAdd(&s_newly, 1u);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const uint32_t done = w.ctl->n_done + s_newly;
-    w.ctl->n_done = done;
+    c->n_done += s_newly;
     // the list consumed in this iteration becomes the append target of the next
-    w.ctl->oh_n[it & 1] = 0;
-    w.ctl->t_n = 0;
-    w.ctl->g_n = 0;
-    w.ctl->tmp_n = 0;
-    w.ctl->b_n = 0;
-    w.ctl->it = it + 1;
-    if (in_graph) cudaGraphSetConditional(cond, (done < nq && it + 1 < w.ctl->iter_cap) ? 1u : 0u);
+    c->oh_n[it & 1] = 0;
+    c->m_n = 0;
+    c->g_n = 0;
+    c->ov_any = 0;
+    c->it = it + 1;
+    c->waves += 1;
   }
-  ktime_end(w, 3);
+  phase_mark(w, 3);
+}
+
+// The persistent wavefront loop (Alg. 3): one cooperative launch per search.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_wave(WS w) {
+  __shared__ WarpSmem smem[kWarpsPerBlock];
+  __shared__ GroupSmem gsm[kWarpsPerBlock];
+  __shared__ WaveSmem ws;
+  WarpSmem& sm = smem[threadIdx.x >> 5];
+  GroupSmem& gs = gsm[threadIdx.x >> 5];
+  const uint32_t nq = w.ctl->nq;
+  for (uint32_t q = threadIdx.x; q < kAccQ; q += blockDim.x) {
+    ws.open[q] = 0;
+    ws.plans[q] = 0;
+    ws.exps[q] = 0;
+  }
+  __syncthreads();
+  WarpCtx cx;
+  cx.s = &ws;
+  cx.lb_n = 0;
+  cx.nq = nq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) w.ctl->t_mark = global_timer();
+  for (;;) {
+    const uint32_t it = ld_vol(&w.ctl->it);
+    if (ld_vol(&w.ctl->n_done) >= nq || it >= w.ctl->iter_cap) break;
+    cx.it = it;
+    cx.next = w.oh_list + (size_t)((it + 1) & 1) * w.NV;
+    phase_expand(w, cx, gs);
+    flush_acc(w, ws, nq);
+    if (!grid_barrier(w, [&] { epi_mid(w); })) return;
+    if (ld_vol(&w.ctl->ov_any)) {
+      phase_segments(w);
+      if (!grid_barrier(w, [] {})) return;
+      phase_scatter(w);
+      if (!grid_barrier(w, [&] { phase_mark(w, 1); })) return;
+    }
+    phase_merge(w, cx, sm);
+    flush_acc(w, ws, nq);
+    if (!grid_barrier(w, [&] {
+          phase_mark(w, 2);
+          epi_end(w);
+        }))
+      return;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1357,7 +1569,7 @@ __global__ void k_finalize(WS w, uint32_t nq) {
   }
   if (threadIdx.x == 0) {
     ResultDev r;
-    r.status = s.done ? s.status : MPAP_ERR_ITER_LIMIT;
+    r.status = s.done ? s.status : (w.ctl->timeout ? MPAP_ERR_TIMEOUT : MPAP_ERR_ITER_LIMIT);
     r.cost = 0;
     r.h = 0;
     r.path_len = 0;
@@ -1542,65 +1754,35 @@ int sms() {
   return n;
 }
 
+// Resident blocks per SM of k_wave (all of them must fit: cooperative launch).
+int wave_occupancy() {
+  static int occ = 0;
+  if (!occ) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wave, kWarpsPerBlock * 32, 0) != cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+  }
+  return occ;
+}
+
 template <typename T>
 bool walloc(T** p, size_t n) {
   return cuda_ok(cudaMalloc((void**)p, (n ? n : 1) * sizeof(T)), "cudaMalloc(workspace)");
 }
 
-// Builds the device-side wavefront loop: a graph whose conditional WHILE node
-// runs {select, prune, end} until `end` clears the condition.
-int32_t build_loop_graph(mpap_workspace* ws, uint32_t sel, uint32_t pru) {
-  if (ws->exec && ws->graph_sel == sel && ws->graph_pru == pru) return MPAP_OK;
-  if (ws->exec) {
-    cudaGraphExecDestroy(ws->exec);
-    ws->exec = nullptr;
-  }
-  if (ws->graph) {
-    cudaGraphDestroy(ws->graph);
-    ws->graph = nullptr;
-  }
-  if (!ws->cap_stream) MPAP_CK(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
-  MPAP_CK(cudaGraphCreate(&ws->graph, 0));
-  cudaGraphConditionalHandle cond;
-  MPAP_CK(cudaGraphConditionalHandleCreate(&cond, ws->graph, 1u, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams p = {};
-  p.type = cudaGraphNodeTypeConditional;
-  p.conditional.handle = cond;
-  p.conditional.type = cudaGraphCondTypeWhile;
-  p.conditional.size = 1;
-  cudaGraphNode_t node;
-  MPAP_CK(cudaGraphAddNode(&node, ws->graph, nullptr, nullptr, 0, &p));
-  cudaGraph_t body = p.conditional.phGraph_out[0];
-  MPAP_CK(cudaStreamBeginCaptureToGraph(ws->cap_stream, body, nullptr, nullptr, 0,
-                                        cudaStreamCaptureModeThreadLocal));
-  const int n = sms();
-  k_select<<<sel * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
-  k_prune<<<pru * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
-  k_prune_bulk<<<2 * n, kWarpsPerBlock * 32, 0, ws->cap_stream>>>(ws->w);
-  k_end<<<1, 1024, 0, ws->cap_stream>>>(ws->w, cond, 1u);
-  cudaGraph_t captured = nullptr;
-  MPAP_CK(cudaStreamEndCapture(ws->cap_stream, &captured));
-  MPAP_CK(cudaGraphInstantiate(&ws->exec, ws->graph, 0));
-  ws->graph_sel = sel;
-  ws->graph_pru = pru;
-  return MPAP_OK;
-}
-
 }  // namespace
-
-bool host_stepped_loop() {
-  static const bool host = [] {
-    const char* e = getenv("MPAP_SEARCH_LOOP");
-    return e && std::strcmp(e, "host") == 0;
-  }();
-  return host;
-}
 
 int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans, uint32_t max_q,
                          mpap_workspace** out) {
   if (!out || total_nodes == 0 || total_nodes > 0xFFFFFFF0ull || front_cap == 0 || max_plans == 0 ||
       max_plans > (uint64_t)kPidMask) {
     set_error("mpap_workspace_create: invalid sizes");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (total_nodes * kSlots > 0xFFFFFFFFFFull) {
+    set_error("mpap_workspace_create: too many nodes");
     return MPAP_ERR_INVALID_ARG;
   }
   mpap_workspace* ws = new mpap_workspace();
@@ -1615,20 +1797,18 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
   }
   w.acap = max_plans;
   w.gcap = max_plans;
-  w.tcap = max_plans;
+  w.ocap = max_plans;
   w.path_cap = 4096;
   ws->max_q = max_q;
   const size_t slots = (size_t)w.pcap;
   bool ok = walloc(&w.f_cost, slots) && walloc(&w.f_h, slots) && walloc(&w.f_pid, slots) &&
-            walloc(&w.f_aux, slots) && walloc(&w.fdesc, w.NV) && walloc(&w.t_cost, w.tcap) && walloc(&w.t_h, w.tcap) &&
-            walloc(&w.t_pp, w.tcap) && walloc(&w.t_m, w.tcap) &&
-            walloc(&w.gdesc, w.NV) && walloc(&w.touch_stamp, w.NV) &&
-            walloc(&w.oh_stamp, w.NV) &&
-            walloc(&w.g_cost, w.gcap) && walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) &&
-            walloc(&w.oh_list, 2 * w.NV) && walloc(&w.t_list, w.NV) && walloc(&w.b_list, w.NV) && walloc(&w.a_head, w.acap) &&
-            walloc(&w.a_parent, w.acap) && walloc(&w.a_iter, w.acap) && walloc(&w.a_cost, w.acap) &&
-            walloc(&w.ctl, 1) && walloc(&w.qd, max_q) && walloc(&w.qs, max_q) && walloc(&w.res, max_q) &&
-            walloc(&w.path, (size_t)max_q * w.path_cap);
+            walloc(&w.f_aux, slots) && walloc(&w.fdesc, w.NV) && walloc(&w.slot, w.NV * kSlots) &&
+            walloc(&w.cand_n, w.NV) && walloc(&w.ov, w.ocap) && walloc(&w.ov2, w.ocap) &&
+            walloc(&w.segoff, w.NV) && walloc(&w.oh_stamp, w.NV) && walloc(&w.g_cost, w.gcap) &&
+            walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) && walloc(&w.oh_list, 2 * w.NV) &&
+            walloc(&w.m_list, w.NV) && walloc(&w.a_head, w.acap) && walloc(&w.a_parent, w.acap) &&
+            walloc(&w.a_iter, w.acap) && walloc(&w.a_cost, w.acap) && walloc(&w.ctl, 1) && walloc(&w.qd, max_q) &&
+            walloc(&w.qs, max_q) && walloc(&w.res, max_q) && walloc(&w.path, (size_t)max_q * w.path_cap);
   if (!ok) {
     workspace_free(ws);
     return MPAP_ERR_CUDA;
@@ -1639,13 +1819,11 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
 
 void workspace_free(mpap_workspace* ws) {
   if (!ws) return;
-  if (ws->exec) cudaGraphExecDestroy(ws->exec);
-  if (ws->graph) cudaGraphDestroy(ws->graph);
-  if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
   WS& w = ws->w;
-  void* ptrs[] = {w.f_cost, w.f_h, w.f_pid, w.f_aux, w.fdesc, w.t_cost, w.t_h, w.t_pp, w.t_m, w.gdesc, w.touch_stamp,
-                  w.oh_stamp, w.g_cost, w.g_h, w.g_pid, w.oh_list, w.t_list, w.b_list,
-                  w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl, w.qd, w.qs, w.res, w.path};
+  void* ptrs[] = {w.f_cost, w.f_h,     w.f_pid,  w.f_aux,  w.fdesc,  w.slot,     w.cand_n, w.ov,
+                  w.ov2,    w.segoff,  w.oh_stamp, w.g_cost, w.g_h,  w.g_pid,    w.oh_list, w.m_list,
+                  w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl,    w.qd,       w.qs,     w.res,
+                  w.path};
   for (void* p : ptrs) cudaFree(p);
   if (ws->h_hdr) cudaFreeHost(ws->h_hdr);
   if (ws->h_path) cudaFreeHost(ws->h_path);
@@ -1701,6 +1879,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   std::vector<QueryDev> qd(nq);
   uint64_t total = 0;
   uint32_t max_iters = 0;
+  uint32_t wait_us = 0;
   for (uint32_t i = 0; i < nq; ++i) {
     const mpap_roadmap* rm = rms[i];
     if (!rm || rm->V < 1) {
@@ -1714,10 +1893,9 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
       return MPAP_ERR_INVALID_ARG;
     }
     QueryDev d{};
-    d.rev_ptr = rm->rev_ptr;
-    d.rev_edge = rm->rev_edge;
     d.fwd_ptr = rm->fwd_ptr;
-    d.fwd_dst = rm->fwd_dst;
+    d.fwd_edge = rm->fwd_edge;
+    d.fwd_peak = rm->fwd_peak;
     d.is_goal = rm->is_goal;
     d.goal_list = rm->goal_list;
     d.n_goal = rm->n_goal;
@@ -1726,7 +1904,6 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     d.max_iters = qs[i].max_iters;
     d.flags = qs[i].flags;
     d.beta = qs[i].beta;
-    d.rev_peak = rm->rev_peak;
     // Lambda = round(lambda r_n 2^24), the group threshold quantum (or the
     // caller's explicit width in cost quanta).
     d.Lambda = qs[i].group_width_q > 0 ? qs[i].group_width_q
@@ -1734,6 +1911,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     if (d.Lambda < 1) d.Lambda = 1;
     total += rm->V;
     max_iters = std::max(max_iters, qs[i].max_iters);
+    if (qs[i].wait_us && (wait_us == 0 || qs[i].wait_us < wait_us)) wait_us = qs[i].wait_us;
     qd[i] = d;
   }
   if (total > w.NV) {
@@ -1741,26 +1919,36 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
               (unsigned long long)w.NV);
     return MPAP_ERR_INVALID_ARG;
   }
-  // every query gets a share of the front pool in proportion to its nodes
+  // every query gets a share of the front pool, of the candidate overflow
+  // areas and of the plan arena in proportion to its nodes
   {
-    uint64_t acc = 0;
+    uint64_t acc = 0, acc_o = 0, acc_a = 0;
     for (uint32_t i = 0; i < nq; ++i) {
-      const uint64_t cap = (i + 1 == nq) ? w.pcap - acc : (uint64_t)((double)w.pcap * qd[i].V / (double)total);
-      if (cap < 16) {
-        set_error("search: query %u's share of the front pool is below 16 entries", i);
+      const bool last = i + 1 == nq;
+      const double f = (double)qd[i].V / (double)total;
+      const uint64_t cap = last ? w.pcap - acc : (uint64_t)((double)w.pcap * f);
+      const uint64_t ocap = last ? w.ocap - acc_o : (uint64_t)((double)w.ocap * f);
+      const uint64_t acap = last ? w.acap - acc_a : (uint64_t)((double)w.acap * f);
+      if (cap < 16 || acap < 1) {
+        set_error("search: query %u's share of the front pool (below 16 entries) or of the plan arena is too small",
+                  i);
         return MPAP_ERR_CAPACITY;
       }
       qd[i].pool_base = acc;
       qd[i].pool_cap = cap;
+      qd[i].ov_base = acc_o;
+      qd[i].ov_cap = ocap;
+      qd[i].arena_base = acc_a;
+      qd[i].arena_cap = acap;
       acc += cap;
+      acc_o += ocap;
+      acc_a += acap;
     }
   }
   int kdim = -1;
   uint32_t kV = 0;
   batch_key(rms, nq, kdim, kV);
   const mpap_tuning tun = tuning_for(kdim, kV);
-  int32_t rc = build_loop_graph(ws, tun.select_blocks_per_sm, tun.prune_blocks_per_sm);
-  if (rc) return rc;
   ws->last_V.resize(nq);
   ws->last_base.resize(nq);
   for (uint32_t i = 0; i < nq; ++i) {
@@ -1769,37 +1957,24 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   }
   const size_t NVu = (size_t)total;
   const bool prof = profile_enabled();
+  const unsigned long long wait_ns = (unsigned long long)(wait_us ? wait_us : kDefaultWaitUs) * 1000ull;
   MPAP_CK(cudaMemcpyAsync(w.qd, qd.data(), sizeof(QueryDev) * nq, cudaMemcpyHostToDevice, st));
   MPAP_CK(cudaMemsetAsync(w.fdesc, 0, sizeof(uint4) * NVu, st));
-  MPAP_CK(cudaMemsetAsync(w.gdesc, 0xFF, sizeof(uint4) * NVu, st));
-  MPAP_CK(cudaMemsetAsync(w.touch_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
+  MPAP_CK(cudaMemsetAsync(w.cand_n, 0, sizeof(uint32_t) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.oh_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
   {
     LaunchScope ls(st, "k_init");
-    k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq, max_iters + 2u, prof ? 1u : 0u);
+    k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq, max_iters + 2u, tun.plan_lanes_from, wait_ns);
+    k_init_done<<<1, 256, 0, st>>>(w, nq);
   }
   MPAP_CK(cudaGetLastError());
-  if (!host_stepped_loop()) {
-    // the whole wavefront loop: one graph launch
-    MPAP_CK(cudaGraphLaunch(ws->exec, st));
-  } else {
-    // Host-stepped form of the same loop (MPAP_SEARCH_LOOP=host): identical
-    // kernels launched one wavefront at a time, for per-kernel profilers that do
-    // not see inside conditional graph nodes.
-    const int n = sms();
-    Ctl probe;
-    for (uint32_t it = 0;; it += 2) {
-      for (int r = 0; r < 2; ++r) {
-        k_select<<<tun.select_blocks_per_sm * n, kWarpsPerBlock * 32, 0, st>>>(w);
-        k_prune<<<tun.prune_blocks_per_sm * n, kWarpsPerBlock * 32, 0, st>>>(w);
-        k_prune_bulk<<<2 * n, kWarpsPerBlock * 32, 0, st>>>(w);
-        k_end<<<1, 1024, 0, st>>>(w, 0ull, 0u);
-      }
-      MPAP_CK(cudaGetLastError());
-      MPAP_CK(cudaMemcpyAsync(&probe, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-      MPAP_CK(cudaStreamSynchronize(st));
-      if (probe.n_done >= nq || probe.it >= max_iters + 2u) break;
-    }
+  {
+    // the whole wavefront loop: one cooperative launch, every block resident
+    const int per_sm = std::max(1, std::min<int>((int)tun.wave_blocks_per_sm, wave_occupancy()));
+    void* args[] = {&w};
+    LaunchScope ls(st, "k_wave");
+    MPAP_CK(cudaLaunchCooperativeKernel((const void*)k_wave, dim3(per_sm * sms()), dim3(kWarpsPerBlock * 32), args, 0,
+                                        st));
   }
   {
     LaunchScope ls(st, "k_finalize");
@@ -1808,7 +1983,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   MPAP_CK(cudaGetLastError());
   // results, query states and the control block: three copies into pinned staging
   const size_t o_qs = align64(sizeof(ResultDev) * nq), o_ctl = o_qs + align64(sizeof(QueryState) * nq);
-  rc = host_stage(&ws->h_hdr, &ws->h_hdr_bytes, o_ctl + sizeof(Ctl));
+  int32_t rc = host_stage(&ws->h_hdr, &ws->h_hdr_bytes, o_ctl + sizeof(Ctl));
   if (rc) return rc;
   const ResultDev* res = reinterpret_cast<const ResultDev*>(ws->h_hdr);
   const QueryState* qsh = reinterpret_cast<const QueryState*>(ws->h_hdr + o_qs);
@@ -1818,10 +1993,10 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   MPAP_CK(cudaMemcpyAsync(ws->h_hdr + o_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaStreamSynchronize(st));
   ws->last_max_front = hc.max_front;
-  launch_count_add(4ull * hc.it);
+  launch_count_add(3);
   if (prof) {
-    const char* names[4] = {"k_select", "k_prune", "k_prune_bulk", "k_end"};
-    for (int k = 0; k < 4; ++k) profile_add(names[k], hc.kt[k].launches, (double)hc.kt[k].total_ns * 1e-6);
+    const char* names[4] = {"k_wave.expand", "k_wave.regroup", "k_wave.merge", "k_wave.end"};
+    for (int k = 0; k < 4; ++k) profile_add(names[k], hc.waves, (double)hc.ph_ns[k] * 1e-6);
   }
   rc = MPAP_OK;
   uint32_t lmax = 0;     // longest plan to return
@@ -1862,9 +2037,13 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     for (uint32_t i = 0; i < nq; ++i) used += std::min<unsigned long long>(qsh[i].pool_n, qd[i].pool_cap);
     ws->last_pool_used = used;
   }
-  if (hc.err) {
+  if (hc.timeout) {
+    set_error("search: a grid barrier wait of the wavefront loop ran past its limit (%u us); unfinished queries "
+              "report MPAP_ERR_TIMEOUT", wait_us ? wait_us : kDefaultWaitUs);
+    rc = MPAP_ERR_TIMEOUT;
+  } else if (hc.err) {
     set_error("search: capacity exceeded in at least one query (flags 0x%x: 1 front pool, 2 plan arena, "
-              "4 group array); its status says so, the other queries' results stand", hc.err);
+              "4 group array, 8 candidate overflow); its status says so, the other queries' results stand", hc.err);
     rc = MPAP_ERR_CAPACITY;
   } else if (hc.n_done < nq) {
     set_error("search: wavefront loop stopped at its iteration bound");

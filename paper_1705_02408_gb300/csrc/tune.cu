@@ -30,15 +30,15 @@ uint32_t bucket_of(uint32_t V) {
 mpap_tuning default_tuning() {
   mpap_tuning t;
   t.edge_warps = 8;
-  t.select_blocks_per_sm = 16;
-  t.prune_blocks_per_sm = 16;
+  t.wave_blocks_per_sm = 8;
+  t.plan_lanes_from = 8;
   t.front_cap = 64;
   return t;
 }
 
 bool tuning_valid(const mpap_tuning& t) {
-  return (t.edge_warps == 4 || t.edge_warps == 8) && t.select_blocks_per_sm >= 1 && t.select_blocks_per_sm <= 64 &&
-         t.prune_blocks_per_sm >= 1 && t.prune_blocks_per_sm <= 64 && t.front_cap >= 1;
+  return (t.edge_warps == 4 || t.edge_warps == 8) && t.wave_blocks_per_sm >= 1 && t.wave_blocks_per_sm <= 64 &&
+         t.plan_lanes_from >= 1 && t.plan_lanes_from <= 64 && t.front_cap >= 1;
 }
 
 mpap_tuning tuning_for(int dim, uint32_t V) {

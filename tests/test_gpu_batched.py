@@ -65,8 +65,8 @@ def test_autotune_search_keeps_results(mp):
     assert ms > 0 and tun["front_cap"] >= 16 and (tun["front_cap"] & (tun["front_cap"] - 1)) == 0
     Vmax = max(rg.V for rg in rms)
     assert mp.tuning_get(0, Vmax) == tun            # stored under the mixed-batch key
-    for sel, pru in [(1, 1), (32, 2), (64, 64), (tun["select_blocks_per_sm"], tun["prune_blocks_per_sm"])]:
-        mp.tuning_set(0, Vmax, select_blocks_per_sm=sel, prune_blocks_per_sm=pru)
+    for bps, lf in [(1, 1), (32, 2), (64, 64), (2, 33), (tun["wave_blocks_per_sm"], tun["plan_lanes_from"])]:
+        mp.tuning_set(0, Vmax, wave_blocks_per_sm=bps, plan_lanes_from=lf)
         got = mp.search_batch(ws, rms, qs)
         for i in range(len(rms)):
             assert (got[i].status, got[i].cost, got[i].h, got[i].expansions, got[i].wavefronts) == \

@@ -193,3 +193,20 @@ def test_pool_share_exhaustion_stays_with_its_query(mp, orc):
         res = mp.search_batch(wsb, [r2, r6], qs, check=False)
         assert res[0].status == mp.MPAP_ERR_CAPACITY
         assert_same_search(res[1], orc.explore(o6, b6, orc.group_width(0.5, 18.0)), wsb, index=1)
+
+
+def test_barrier_timeout_is_reported(mp, orc, ws):
+    """A grid-barrier wait of the device wavefront loop that runs past its limit
+    ends the search with MPAP_ERR_TIMEOUT instead of hanging, and the workspace
+    stays usable.  With a 1 us limit on a grid of hundreds of blocks some wait
+    runs out (the first block at a barrier waits for all the others); the
+    barrier itself never waits unbounded, so nothing on the GPU hangs."""
+    sc = scenegen.make_scene("2d", 1, query_id=1)
+    ro = orc.build_roadmap(sc, n=600)
+    rg = mp.build_roadmap_for_scene(sc, n=600)
+    beta = orc.beta_percentile(ro)
+    with pytest.raises(mp.MpapError) as e:
+        mp.search(ws, rg, beta, lam=0.5, wait_us=1)
+    assert e.value.status == mp.MPAP_ERR_TIMEOUT
+    ok = mp.search(ws, rg, beta, lam=0.5)
+    assert_same_search(ok, orc.explore(ro, beta, orc.group_width(0.5, sc.cfg.r)), ws)
