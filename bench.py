@@ -178,7 +178,9 @@ class GpuArm:
         self.dev_inputs = [(torch.from_numpy(s.box_lo).to(device), torch.from_numpy(s.box_hi).to(device),
                             torch.from_numpy(s.grid).to(device)) for s in scenes]
         V = self.cfg.n + 2
-        self.ws = mp.Workspace(V * len(scenes), front_cap=64, max_plans=1 << 25)
+        # plan arena, group array and candidate overflow areas: 2^19 records per query
+        self.max_plans = len(scenes) << 19
+        self.ws = mp.Workspace(V * len(scenes), front_cap=64, max_plans=self.max_plans)
         self.ws1 = mp.Workspace(V, front_cap=64, max_plans=1 << 22)
         self.queries = [mp.make_query(s.extra["beta"], scenegen.LAMBDA) for s in scenes]
         self.mc = [(self.cfg.mc_rollouts, s.mc_seed, 0, s.delta_fx, s.sigma_fx, s.shift) for s in scenes]
@@ -231,7 +233,7 @@ def run_gpu(args, rank, world, local):
         tb, b_ms, arm.rms = mp.autotune_build(specs, reps=1)
         ts, s_ms = mp.autotune_search(arm.ws, arm.rms, arm.queries, reps=1)
         if ts["front_cap"] > arm.ws.front_cap:
-            arm.ws = mp.Workspace(arm.ws.total_nodes, front_cap=ts["front_cap"], max_plans=1 << 25)
+            arm.ws = mp.Workspace(arm.ws.total_nodes, front_cap=ts["front_cap"], max_plans=arm.max_plans)
         tuning = {"edge_warps": tb["edge_warps"], "wave_blocks_per_sm": ts["wave_blocks_per_sm"],
                   "plan_lanes_from": ts["plan_lanes_from"], "front_cap": arm.ws.front_cap,
                   "tuned_build_ms": round(b_ms, 3), "tuned_search_ms": round(s_ms, 3)}

@@ -108,6 +108,14 @@ struct __align__(16) Cand {
   uint32_t i;     // index - kSlots among the node's candidates (overflow records)
 };
 
+// A node's front descriptor (32 B, one sector): its live block, count, other
+// block and block sizes, and a copy of its last entry (highest cost, lowest h),
+// which alone dominates most candidates that reach the node.
+struct __align__(32) FDesc {
+  uint4 d;          // {live block, count, other block, lg live | lg other << 8}
+  longlong2 last;   // {cost, h} of entry count - 1 (count > 0)
+};
+
 struct Ctl {
   uint32_t oh_n[2];
   uint32_t m_n;          // nodes with candidates this wavefront
@@ -128,8 +136,9 @@ struct Ctl {
   unsigned long long wait_ns;  // limit of one barrier wait
   unsigned long long t_mark;   // %globaltimer at the last barrier release
   unsigned long long ph_ns[4]; // expand, overflow regrouping, merge, end of wavefront
+  unsigned long long idle_ns;  // block time spent waiting at grid barriers, summed over blocks
   uint32_t waves;
-  uint32_t pad2;
+  uint32_t grab[2];      // work counters of the expansion and the merge (nodes handed out)
 };
 
 struct WS {
@@ -141,7 +150,7 @@ struct WS {
   long long* f_h;
   uint32_t* f_pid;
   uint32_t* f_aux;
-  uint4* fdesc;            // [NV] {live block, count, other block, lg live | lg other << 8}
+  FDesc* fdesc;            // [NV]
   Cand* slot;              // [NV * kSlots] candidates of this wavefront
   uint32_t* cand_n;        // [NV] candidates per node this wavefront (0 between wavefronts)
   Cand* ov;                // [ocap] overflow candidates in arrival order (per-query shares)
@@ -251,14 +260,17 @@ __device__ __forceinline__ bool grid_barrier(const WS& w, Epi epi) {
     if (!s_last) {
       const unsigned long long t0 = global_timer();
       const unsigned long long lim = c->wait_ns;
+      unsigned long long t = t0;
       while (ld_vol(&c->bar_gen) == gen) {
-        if (ld_vol(&c->timeout) || global_timer() - t0 > lim) {
+        t = global_timer();
+        if (ld_vol(&c->timeout) || t - t0 > lim) {
           atomicExch(&c->timeout, 1u);
           s_ok = 0u;
           break;
         }
-        __nanosleep(100);
+        __nanosleep(64);
       }
+      atomicAdd(&c->idle_ns, t - t0);
     }
     __threadfence();
   }
@@ -306,7 +318,10 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from
     c.wait_ns = wait_ns;
     c.t_mark = 0;
     for (int k = 0; k < 4; ++k) c.ph_ns[k] = 0;
+    c.idle_ns = 0;
     c.waves = 0;
+    c.grab[0] = 0;
+    c.grab[1] = 0;
   }
   if (q >= nq) return;
   const QueryDev& Q = w.qd[q];
@@ -338,7 +353,10 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from
   w.f_h[o] = 0;
   w.f_pid[o] = a | kOpen;      // the root plan (x_init, {}, 0, 0) opens the arena share
   w.f_aux[o] = 0;
-  w.fdesc[g] = make_uint4(o, 1u, 0u, kMinLg);
+  FDesc fd0;
+  fd0.d = make_uint4(o, 1u, 0u, kMinLg);
+  fd0.last = make_longlong2(0, 0);
+  w.fdesc[g] = fd0;
   w.a_head[a] = 0;
   w.a_parent[a] = kNone;
   w.a_iter[a] = 0;
@@ -802,9 +820,12 @@ __device__ __forceinline__ uint32_t arena_block(const WS& w, uint32_t q, uint32_
 
 // The node's new descriptor and counters, and its place in the next open list.
 __device__ __forceinline__ void commit_tail(const WS& w, WarpCtx& cx, uint32_t q, uint32_t g, const FrontCursor& fc,
-                                            uint32_t n_new) {
+                                            uint32_t n_new, long long last_c, long long last_h) {
   if (lane_id() == 0) {
-    w.fdesc[g] = make_uint4(fc.off, fc.n, fc.off2, fc.lg | (fc.lg2 << 8));
+    FDesc fd;
+    fd.d = make_uint4(fc.off, fc.n, fc.off2, fc.lg | (fc.lg2 << 8));
+    fd.last = make_longlong2(last_c, last_h);
+    w.fdesc[g] = fd;
     acc_open(w, cx, q, (long long)n_new - (long long)fc.removed_open);
     acc_plans(w, cx, q, n_new);
     if (fc.n > ld_vol(&w.ctl->max_front)) atomicMax(&w.ctl->max_front, fc.n);
@@ -840,15 +861,13 @@ __device__ __forceinline__ uint32_t front_upper(const WS& w, size_t o, uint32_t 
   return i;
 }
 
-// Slots for r new candidates of node gx, taken by several lanes of one warp:
-// returns each lane's first slot; the first lane to reach gx this wavefront
-// puts it on the merge list; slots from kSlots on are overflow records, whose
-// indices in query q's overflow share come back in *ov (warp-aggregated).
-__device__ __forceinline__ uint32_t take_slots(const WS& w, uint32_t q, uint32_t gx, uint32_t r, uint32_t* ov) {
+// Slot bookkeeping after the atomic add that gave a lane its first slot s for r
+// new candidates of node gx: the lane that opened gx this wavefront puts it on
+// the merge list; slots from kSlots on are overflow records, whose indices in
+// query q's overflow share come back in *ov (warp-aggregated).  Warp-collective.
+__device__ __forceinline__ void slot_book(const WS& w, uint32_t q, uint32_t gx, uint32_t r, uint32_t s, uint32_t* ov) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
-  uint32_t s = 0;
-  if (r) s = atomicAdd(&w.cand_n[gx], r);
   const bool first = r && s == 0;
   const unsigned fb = __ballot_sync(kFull, first);
   if (fb) {
@@ -866,7 +885,6 @@ __device__ __forceinline__ uint32_t take_slots(const WS& w, uint32_t q, uint32_t
     b = __shfl_sync(kFull, b, 0);
   }
   *ov = b + incl - nov;
-  return s;
 }
 
 // Stores candidate cd as candidate s of node gx (a slot, or overflow record oi
@@ -887,58 +905,94 @@ __device__ __forceinline__ void put_cand(const WS& w, const QueryDev& Q, uint32_
   }
 }
 
-// Small groups: lanes on the out-edges of u, each lane walking the group plans
-// (cost order) and the target's front together.
+// Is candidate (c, h) dominated by the stored front of a node (descriptor xd)?
+// The last entry decides most cases; otherwise the last entry of cost <= c (the
+// one of lowest h among them: fronts are strictly monotone), found from index *i
+// on (candidates of one run come in increasing cost).  Old plans win ties.
+__device__ __forceinline__ bool front_dominates(const WS& w, const FDesc& xd, uint32_t* i, long long c, long long h) {
+  const uint32_t n = xd.d.y;
+  if (n == 0) return false;
+  if (c >= xd.last.x && h >= xd.last.y) return true;
+  *i = front_upper(w, xd.d.x, n, *i, c);
+  return *i > 0 && w.f_h[(size_t)xd.d.x + *i - 1] <= h;
+}
+
+// Bit j set: group plan j extended along edge ed survives the beta cutoff, its
+// run predecessor and the target's stored front.
+__device__ __forceinline__ uint32_t filter_run(const WS& w, const QueryDev& Q, const GroupSmem& gs, uint32_t cnt,
+                                               const int4& ed, const int2& pk, bool interior, const FDesc& xd) {
+  uint32_t mask = 0, i = 0;
+  long long prev_h = LLONG_MAX;
+  for (uint32_t j = 0; j < cnt; ++j) {
+    const long long gh = gs.h[j];
+    const long long c = gs.c[j] + (long long)ed.y;
+    const long long hh = gh + (long long)ed.z;
+    const long long h = hh > (long long)ed.w ? hh : (long long)ed.w;
+    long long peak = h;
+    if (interior) {
+      const long long hp = gh + (long long)pk.x;
+      peak = hp > (long long)pk.y ? hp : (long long)pk.y;
+    }
+    if (peak > Q.beta) continue;
+    // the previous plan of the run (lower cost) dominates unless h drops
+    if (h >= prev_h) continue;
+    prev_h = h;
+    if (front_dominates(w, xd, &i, c, h)) continue;
+    mask |= 1u << j;
+  }
+  return mask;
+}
+
+__device__ __forceinline__ void write_run(const WS& w, const QueryDev& Q, uint32_t q, uint32_t u, const GroupSmem& gs,
+                                          uint32_t mask, const int4& ed, uint32_t gx, uint32_t s, uint32_t oi) {
+  for (uint32_t m = mask; m; m &= m - 1u) {
+    const uint32_t j = (uint32_t)__ffs(m) - 1u;
+    Cand cd;
+    cd.cost = gs.c[j] + (long long)ed.y;
+    const long long hh = gs.h[j] + (long long)ed.z;
+    cd.h = hh > (long long)ed.w ? hh : (long long)ed.w;
+    cd.pp = gs.p[j];
+    cd.tb = 1u + u;
+    cd.g = 0;
+    cd.i = 0;
+    put_cand(w, Q, q, gx, s++, oi, cd);
+  }
+}
+
+// Small groups: lanes on the out-edges of u (two edges per lane per step, all
+// their loads in flight together), each lane walking the group plans (cost
+// order) and the target's front together.
 __device__ __forceinline__ void expand_edges(const WS& w, const QueryDev& Q, uint32_t q, uint32_t u, uint32_t e_beg,
                                              uint32_t e_end, const GroupSmem& gs, uint32_t cnt, bool interior) {
   const unsigned lane = lane_id();
-  for (uint32_t e0 = e_beg; e0 < e_end; e0 += 32) {
-    const uint32_t e = e0 + lane;
-    uint32_t mask = 0, gx = 0;
-    int4 ed = make_int4(0, 0, 0, 0);
-    if (e < e_end) {
-      ed = __ldg(&Q.fwd_edge[e]);
-      int2 pk = make_int2(0, 0);
-      if (interior) pk = __ldg(&Q.fwd_peak[e]);
-      gx = Q.base + (uint32_t)ed.x;
-      const uint4 xd = w.fdesc[gx];
-      const size_t xo = xd.x;
-      const uint32_t xn = xd.y;
-      uint32_t i = 0;
-      long long prev_h = LLONG_MAX;
-      for (uint32_t j = 0; j < cnt; ++j) {
-        const long long gh = gs.h[j];
-        const long long c = gs.c[j] + (long long)ed.y;
-        const long long hh = gh + (long long)ed.z;
-        const long long h = hh > (long long)ed.w ? hh : (long long)ed.w;
-        long long peak = h;
-        if (interior) {
-          const long long hp = gh + (long long)pk.x;
-          peak = hp > (long long)pk.y ? hp : (long long)pk.y;
-        }
-        if (peak > Q.beta) continue;
-        // the previous plan of the run (lower cost) dominates unless h drops
-        if (h >= prev_h) continue;
-        prev_h = h;
-        i = front_upper(w, xo, xn, i, c);
-        if (i > 0 && w.f_h[xo + i - 1] <= h) continue;   // an old plan wins every tie
-        mask |= 1u << j;
-      }
+  for (uint32_t e0 = e_beg; e0 < e_end; e0 += 64) {
+    const uint32_t ea = e0 + lane, eb = ea + 32;
+    const bool va = ea < e_end, vb = eb < e_end;
+    int4 eda = make_int4(0, 0, 0, 0), edb = make_int4(0, 0, 0, 0);
+    int2 pka = make_int2(0, 0), pkb = make_int2(0, 0);
+    if (va) eda = __ldg(&Q.fwd_edge[ea]);
+    if (vb) edb = __ldg(&Q.fwd_edge[eb]);
+    if (interior) {
+      if (va) pka = __ldg(&Q.fwd_peak[ea]);
+      if (vb) pkb = __ldg(&Q.fwd_peak[eb]);
     }
-    uint32_t oi = 0;
-    uint32_t s = take_slots(w, q, gx, (uint32_t)__popc(mask), &oi);
-    for (uint32_t m = mask; m; m &= m - 1u) {
-      const uint32_t j = (uint32_t)__ffs(m) - 1u;
-      Cand cd;
-      cd.cost = gs.c[j] + (long long)ed.y;
-      const long long hh = gs.h[j] + (long long)ed.z;
-      cd.h = hh > (long long)ed.w ? hh : (long long)ed.w;
-      cd.pp = gs.p[j];
-      cd.tb = 1u + u;
-      cd.g = 0;
-      cd.i = 0;
-      put_cand(w, Q, q, gx, s++, oi, cd);
-    }
+    const uint32_t gxa = Q.base + (uint32_t)eda.x, gxb = Q.base + (uint32_t)edb.x;
+    FDesc xa, xb;
+    xa.d = make_uint4(0, 0, 0, 0);
+    xa.last = make_longlong2(0, 0);
+    xb = xa;
+    if (va) xa = w.fdesc[gxa];
+    if (vb) xb = w.fdesc[gxb];
+    const uint32_t ma = va ? filter_run(w, Q, gs, cnt, eda, pka, interior, xa) : 0u;
+    const uint32_t mb = vb ? filter_run(w, Q, gs, cnt, edb, pkb, interior, xb) : 0u;
+    const uint32_t ra = (uint32_t)__popc(ma), rb = (uint32_t)__popc(mb);
+    const uint32_t sa = ra ? atomicAdd(&w.cand_n[gxa], ra) : 0u;
+    const uint32_t sb = rb ? atomicAdd(&w.cand_n[gxb], rb) : 0u;
+    uint32_t oa = 0, ob = 0;
+    slot_book(w, q, gxa, ra, sa, &oa);
+    if (__any_sync(kFull, vb)) slot_book(w, q, gxb, rb, sb, &ob);
+    write_run(w, Q, q, u, gs, ma, eda, gxa, sa, oa);
+    write_run(w, Q, q, u, gs, mb, edb, gxb, sb, ob);
   }
 }
 
@@ -954,9 +1008,7 @@ __device__ __forceinline__ void expand_plans(const WS& w, const QueryDev& Q, uin
     int2 pk = make_int2(0, 0);
     if (interior) pk = __ldg(&Q.fwd_peak[e]);
     const uint32_t gx = Q.base + (uint32_t)ed.x;
-    const uint4 xd = w.fdesc[gx];
-    const size_t xo = xd.x;
-    const uint32_t xn = xd.y;
+    const FDesc xd = w.fdesc[gx];
     long long carry_h = 0;
     bool carry_ok = false;
     for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
@@ -987,22 +1039,21 @@ __device__ __forceinline__ void expand_plans(const WS& w, const QueryDev& Q, uin
       carry_h = shfl_i64(h, 31);
       carry_ok = __shfl_sync(kFull, ok, 31);
       if (ok && pok && ph <= h) ok = false;
-      if (ok) {
-        const uint32_t L = front_upper(w, xo, xn, 0, c);
-        if (L > 0 && w.f_h[xo + L - 1] <= h) ok = false;
-      }
+      uint32_t i0 = 0;
+      if (ok && front_dominates(w, xd, &i0, c, h)) ok = false;
       const unsigned bal = __ballot_sync(kFull, ok);
       if (!bal) continue;
       const uint32_t r = (uint32_t)__popc(bal);
-      // one lane takes the run's slots; the others follow it
-      uint32_t oi = 0;
-      uint32_t s = take_slots(w, q, gx, lane == 0 ? r : 0u, &oi);
+      // lane 0 takes the run's slots; the others follow it
+      uint32_t s = 0, oi = 0;
+      if (lane == 0) s = atomicAdd(&w.cand_n[gx], r);
+      slot_book(w, q, gx, lane == 0 ? r : 0u, s, &oi);
       s = __shfl_sync(kFull, s, 0);
       oi = __shfl_sync(kFull, oi, 0);
       if (ok) {
         const uint32_t k = (uint32_t)__popc(bal & lt);
         const uint32_t sk = s + k;
-        // overflow indices: records before this one in the run that overflowed
+        // overflow index: the run's records before this one that overflowed
         uint32_t ok_i = oi + (sk >= kSlots ? sk - max(s, kSlots) : 0u);
         Cand cd;
         cd.cost = c;
@@ -1017,6 +1068,18 @@ __device__ __forceinline__ void expand_plans(const WS& w, const QueryDev& Q, uin
   }
 }
 
+// Dynamic distribution of a phase's nodes over warps: a warp takes the next
+// `chunk` list entries from the phase's counter (about 16 grabs per warp and
+// phase), so warps that drew heavy nodes take fewer.
+__device__ __forceinline__ uint32_t grab_chunk(uint32_t n_list, uint32_t warps) {
+  return max(1u, n_list / (warps * 16u));
+}
+__device__ __forceinline__ uint32_t grab(uint32_t* ctr, uint32_t chunk) {
+  uint32_t k = 0;
+  if (lane_id() == 0) k = atomicAdd(ctr, chunk);
+  return __shfl_sync(kFull, k, 0);
+}
+
 __device__ void phase_expand(const WS& w, WarpCtx& cx, GroupSmem& gs) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
@@ -1025,14 +1088,16 @@ __device__ void phase_expand(const WS& w, WarpCtx& cx, GroupSmem& gs) {
   const uint32_t lanes_from = w.ctl->lanes_from;
   const uint2* list = w.oh_list + (size_t)(it & 1) * w.NV;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_list; k += warps) {
+  const uint32_t chunk = grab_chunk(n_list, warps);
+  for (uint32_t k0 = grab(&w.ctl->grab[0], chunk); k0 < n_list; k0 = grab(&w.ctl->grab[0], chunk))
+  for (uint32_t k = k0; k < min(k0 + chunk, n_list); ++k) {
     const uint2 gq = list[k];
     const uint32_t g = gq.x, q = gq.y;
     if (w.qs[q].done) continue;
     const QueryDev& Q = w.qd[q];
     const uint32_t u = g - Q.base;
     const uint32_t e_beg = __ldg(&Q.fwd_ptr[u]), e_end = __ldg(&Q.fwd_ptr[u + 1]);
-    const uint4 fd = w.fdesc[g];
+    const uint4 fd = w.fdesc[g].d;
     const uint32_t n = fd.y;
     const size_t o = fd.x;
     const long long thr = (long long)it * Q.Lambda, thr2 = thr + Q.Lambda;
@@ -1273,14 +1338,12 @@ __device__ __forceinline__ void merge_small(FrontCursor& fc, WarpSmem& sm, uint3
 // ---------------------------------------------------------------------------
 // Merge (RemoveDominated, Sec. 3, for every node that received candidates).
 // ---------------------------------------------------------------------------
-__device__ void phase_merge(const WS& w, WarpCtx& cx, WarpSmem& sm) {
+// One node's merge with the whole warp (any front and candidate count).
+__device__ __forceinline__ void merge_node(const WS& w, WarpCtx& cx, WarpSmem& sm, const uint2 gq) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t it = cx.it;
-  const uint32_t n_m = ld_vol(&w.ctl->m_n);
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_m; k += warps) {
-    const uint2 gq = w.m_list[k];
+  {
     const uint32_t g = gq.x, q = gq.y;
     const QueryDev& Q = w.qd[q];
     const uint32_t x = g - Q.base;
@@ -1288,7 +1351,7 @@ __device__ void phase_merge(const WS& w, WarpCtx& cx, WarpSmem& sm) {
     const uint32_t so = nc > kSlots ? w.segoff[g] : 0u;
     FrontCursor fc;
     {
-      const uint4 fd = w.fdesc[g];
+      const uint4 fd = w.fdesc[g].d;
       fc.off = fd.x;
       fc.n = fd.y;
       fc.off2 = fd.z;
@@ -1393,12 +1456,231 @@ __device__ void phase_merge(const WS& w, WarpCtx& cx, WarpSmem& sm) {
           gnext = gnext || __any_sync(kFull, hit);
         }
       }
-      commit_tail(w, cx, q, g, fc, n_new);
+      long long lc, lh;
+      if (fc.reg) {
+        lc = shfl_i64(fc.rc, (int)fc.n - 1);
+        lh = shfl_i64(fc.rh, (int)fc.n - 1);
+      } else {
+        lc = w.f_cost[(size_t)fc.off + fc.n - 1];
+        lh = w.f_h[(size_t)fc.off + fc.n - 1];
+      }
+      commit_tail(w, cx, q, g, fc, n_new, lc, lh);
       // an open plan of the next group at a goal node ends the query at the
       // top of the next iteration (the loop condition of Alg. 3)
       if (lane == 0 && gnext && Q.is_goal[x]) w.qs[q].goal_next = 1u;
     }
     if (lane == 0) w.cand_n[g] = 0;
+  }
+}
+
+__device__ __forceinline__ long long shfl16_i64(long long v, uint32_t src) {
+  return __shfl_sync(kFull, v, (int)src, 16);
+}
+
+// Two small merges at once, one per half-warp: lanes 16 s .. 16 s + 15 serve
+// node gq of half s, whose front (n entries) and candidates (nc) fit 16 lanes
+// together.  Within each half the one-pass merge of merge_small: sort (cost, h,
+// tie key), keep the strict prefix minimum of h; then each half commits its
+// node (pool block, arena records, descriptor, counters, next open list).
+__device__ __forceinline__ void merge_pair16(const WS& w, WarpCtx& cx, WarpSmem& sm, const uint2 gq, const uint4 fd,
+                                             uint32_t nc) {
+  const unsigned lane = lane_id();
+  const unsigned sl = lane & 15u, hb = lane & 16u;
+  const unsigned llt = (1u << sl) - 1u;
+  const uint32_t it = cx.it;
+  const uint32_t g = gq.x, q = gq.y;
+  const QueryDev& Q = w.qd[q];
+  const uint32_t x = g - Q.base;
+  const uint32_t n = fd.y, t = n + nc;
+  const bool isf = sl < n, isc = sl >= n && sl < t;
+  long long kc = LLONG_MAX, vh = LLONG_MAX;
+  uint32_t vt = 0xFFFFFFFFu, vp = 0u, va = 0u;
+  if (isf) {
+    const size_t o = (size_t)fd.x + sl;
+    kc = w.f_cost[o];
+    vh = w.f_h[o];
+    vp = w.f_pid[o];
+    va = w.f_aux[o];
+    vt = 0u;
+  } else if (isc) {
+    const Cand cd = w.slot[(size_t)g * kSlots + (sl - n)];
+    kc = cd.cost;
+    vh = cd.h;
+    vt = cd.tb;
+    vp = cd.pp | kNew;
+    va = cd.tb;
+  }
+  uint32_t W = 2;
+  const uint32_t tm = max(t, (uint32_t)__shfl_xor_sync(kFull, t, 16));
+  while (W < tm) W <<= 1;
+  // 1. sort on (cost, source lane) within each half (W <= 16 keeps every
+  //    exchange inside its half)
+  uint32_t ks = sl;
+  for (uint32_t k = 2; k <= W; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      const long long oc = shfl_xor_i64(kc, (int)j);
+      const uint32_t os = __shfl_xor_sync(kFull, ks, (int)j);
+      const bool up = (sl & k) == 0;
+      const bool lower = (sl & j) == 0;
+      const bool o_less = oc < kc || (oc == kc && os < ks);
+      if ((lower == up) ? o_less : !o_less) {
+        kc = oc;
+        ks = os;
+      }
+    }
+  }
+  long long kh = shfl16_i64(vh, ks);
+  uint32_t kt = __shfl_sync(kFull, vt, (int)ks, 16);
+  uint32_t kp = __shfl_sync(kFull, vp, (int)ks, 16);
+  uint32_t ka = __shfl_sync(kFull, va, (int)ks, 16);
+  // 2. equal costs: sort again on the full key (rare)
+  {
+    const long long pc = __shfl_up_sync(kFull, kc, 1, 16);
+    if (__any_sync(kFull, sl > 0 && kt != 0xFFFFFFFFu && pc == kc)) {
+      for (uint32_t k = 2; k <= W; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+          const long long oc = shfl_xor_i64(kc, (int)j), oh = shfl_xor_i64(kh, (int)j);
+          const uint32_t ot = __shfl_xor_sync(kFull, kt, (int)j), op = __shfl_xor_sync(kFull, kp, (int)j);
+          const uint32_t oa = __shfl_xor_sync(kFull, ka, (int)j);
+          const bool up = (sl & k) == 0;
+          const bool lower = (sl & j) == 0;
+          const bool o_less = key_less(oc, oh, ot, kc, kh, kt);
+          const bool m_less = key_less(kc, kh, kt, oc, oh, ot);
+          if ((lower == up) ? o_less : m_less) {
+            kc = oc;
+            kh = oh;
+            kt = ot;
+            kp = op;
+            ka = oa;
+          }
+        }
+      }
+    }
+  }
+  // 3. skyline within the half
+  long long pm = kh;
+  for (uint32_t o = 1; o < W; o <<= 1) {
+    const long long y = __shfl_up_sync(kFull, pm, o, 16);
+    if (sl >= o && y < pm) pm = y;
+  }
+  long long excl = __shfl_up_sync(kFull, pm, 1, 16);
+  if (sl == 0) excl = LLONG_MAX;
+  const bool valid = sl < W && kt != 0xFFFFFFFFu;
+  const bool surv = valid && kh < excl;
+  const uint32_t my = (__ballot_sync(kFull, surv) >> hb) & 0xFFFFu;
+  const uint32_t removed =
+      (uint32_t)__popc((__ballot_sync(kFull, valid && !surv && kt == 0u && (kp & kOpen)) >> hb) & 0xFFFFu);
+  const bool any_new = ((__ballot_sync(kFull, surv && (kp & kNew)) >> hb) & 0xFFFFu) != 0u;
+  if (surv) {
+    const uint32_t r = hb + (uint32_t)__popc(my & llt);
+    sm.st_cost[r] = kc;
+    sm.st_h[r] = kh;
+    sm.st_pid[r] = kp;
+    sm.st_aux[r] = ka;
+  }
+  __syncwarp();
+  const uint32_t nn = (uint32_t)__popc(my);
+  long long rc = 0, rh = 0;
+  uint32_t rp = 0;
+  if (sl < nn) {
+    rc = sm.st_cost[hb + sl];
+    rh = sm.st_h[hb + sl];
+    rp = sm.st_pid[hb + sl];
+  }
+  __syncwarp();
+  // 4. commit, per half
+  uint32_t off = fd.x, lg = fd.w & 0xFFu;
+  const uint32_t off2 = fd.z, lg2 = (fd.w >> 8) & 0xFFu;
+  bool ok = any_new;
+  {
+    const bool need = ok && (lg == 0 || (1u << lg) < nn);
+    const uint32_t nlg = max(kMinLg, ceil_lg(nn));
+    uint32_t o = 0;
+    if (need && sl == 0) o = pool_alloc(w, q, nlg);
+    o = __shfl_sync(kFull, o, (int)hb);
+    if (need) {
+      if (o == kNoBlock) {
+        if (sl == 0) query_error(w, q, kErrFront);
+        ok = false;
+      } else {
+        off = o;
+        lg = nlg;
+      }
+    }
+  }
+  const bool isnew = ok && sl < nn && (rp & kNew);
+  const uint32_t bal = (__ballot_sync(kFull, isnew) >> hb) & 0xFFFFu;
+  uint32_t a0 = kNone;
+  if (sl == 0 && bal) a0 = arena_take(w, q, (uint32_t)__popc(bal));
+  a0 = __shfl_sync(kFull, a0, (int)hb);
+  if (isnew) {
+    if (a0 != kNone) {
+      const uint32_t a = a0 + (uint32_t)__popc(bal & llt);
+      w.a_head[a] = x;
+      w.a_parent[a] = rp & kPidMask;
+      w.a_iter[a] = it + 1;
+      w.a_cost[a] = rc;
+      rp = a | kOpen;
+    } else {
+      rp = kOpen;
+    }
+  }
+  if (ok && sl < nn) {
+    const size_t o = (size_t)off + sl;
+    w.f_cost[o] = rc;
+    w.f_h[o] = rh;
+    w.f_pid[o] = rp;
+    w.f_aux[o] = 0u;
+  }
+  const long long thr2 = (long long)(it + 1) * Q.Lambda;
+  const bool gnext = ((__ballot_sync(kFull, ok && sl < nn && (rp & kOpen) && rc <= thr2) >> hb) & 0xFFFFu) != 0u;
+  const long long lc = __shfl_sync(kFull, rc, (int)(hb + (nn ? nn - 1 : 0)));
+  const long long lh = __shfl_sync(kFull, rh, (int)(hb + (nn ? nn - 1 : 0)));
+  if (sl == 0) {
+    if (ok) {
+      FDesc d;
+      d.d = make_uint4(off, nn, off2, lg | (lg2 << 8));
+      d.last = make_longlong2(lc, lh);
+      w.fdesc[g] = d;
+      const uint32_t n_new = (uint32_t)__popc(bal);
+      acc_open(w, cx, q, (long long)n_new - (long long)removed);
+      acc_plans(w, cx, q, n_new);
+      if (nn > ld_vol(&w.ctl->max_front)) atomicMax(&w.ctl->max_front, nn);
+      if (gnext && Q.is_goal[x]) w.qs[q].goal_next = 1u;
+    }
+    w.cand_n[g] = 0;
+  }
+  // both halves' nodes to the next open list (warp-uniform calls)
+  for (uint32_t h = 0; h < 32; h += 16) {
+    const bool pk = __shfl_sync(kFull, ok, (int)h);
+    const uint32_t pg = __shfl_sync(kFull, g, (int)h), pq = __shfl_sync(kFull, q, (int)h);
+    if (pk) push_next(w, cx, pg, pq);
+  }
+}
+
+__device__ void phase_merge(const WS& w, WarpCtx& cx, WarpSmem& sm) {
+  const uint32_t n_m = ld_vol(&w.ctl->m_n);
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t chunk = max(2u, grab_chunk(n_m, warps));
+  const unsigned half = lane_id() >> 4;
+  for (uint32_t k0 = grab(&w.ctl->grab[1], chunk); k0 < n_m; k0 = grab(&w.ctl->grab[1], chunk)) {
+    const uint32_t k1 = min(k0 + chunk, n_m);
+    uint32_t k = k0;
+    while (k < k1) {
+      if (k + 1 < k1) {
+        // two nodes whose fronts and candidates fit half a warp each go together
+        const uint2 gq = w.m_list[k + half];
+        const uint32_t nc = w.cand_n[gq.x];
+        const uint4 fd = w.fdesc[gq.x].d;
+        if (__all_sync(kFull, fd.y <= 16u && fd.y + nc <= 16u)) {
+          merge_pair16(w, cx, sm, gq, fd, nc);
+          k += 2;
+          continue;
+        }
+      }
+      merge_node(w, cx, sm, w.m_list[k]);
+      ++k;
+    }
   }
   flush_next(w, cx);
 }
@@ -1460,6 +1742,8 @@ __device__ void epi_end(const WS& w) {
     c->m_n = 0;
     c->g_n = 0;
     c->ov_any = 0;
+    c->grab[0] = 0;
+    c->grab[1] = 0;
     c->it = it + 1;
     c->waves += 1;
   }
@@ -1467,7 +1751,7 @@ __device__ void epi_end(const WS& w) {
 }
 
 // The persistent wavefront loop (Alg. 3): one cooperative launch per search.
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_wave(WS w) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_wave(WS w) {
   __shared__ WarpSmem smem[kWarpsPerBlock];
   __shared__ GroupSmem gsm[kWarpsPerBlock];
   __shared__ WaveSmem ws;
@@ -1541,7 +1825,7 @@ __global__ void k_finalize(WS w, uint32_t nq) {
     for (uint32_t i = threadIdx.x; i < Q.n_goal; i += blockDim.x) {
       const uint32_t v = Q.goal_list[i];
       const uint32_t g = Q.base + v;
-      const uint4 fd = w.fdesc[g];
+      const uint4 fd = w.fdesc[g].d;
       const uint32_t n = fd.y;
       const size_t o = fd.x;
       for (uint32_t j = 0; j < n; ++j) {
@@ -1670,7 +1954,7 @@ __global__ void __launch_bounds__(256) k_candidates(WS w, uint32_t q0, uint32_t 
     for (uint32_t i = threadIdx.x; i < Q.n_goal; i += blockDim.x) {
       const uint32_t v = Q.goal_list[i];
       const uint32_t g = Q.base + v;
-      const uint4 fd = w.fdesc[g];
+      const uint4 fd = w.fdesc[g].d;
       const uint32_t n = fd.y;
       const size_t off = fd.x;
       if (r == 0) mine += n;
@@ -1730,7 +2014,7 @@ __global__ void k_gather_fronts(WS w, uint32_t base, uint32_t V, const uint32_t*
                                 long long* __restrict__ oc, long long* __restrict__ oh) {
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < V; v += warps) {
-    const uint4 fd = w.fdesc[base + v];
+    const uint4 fd = w.fdesc[base + v].d;
     for (uint32_t j = lane_id(); j < fd.y; j += 32) {
       oc[ptr[v] + j] = w.f_cost[(size_t)fd.x + j];
       oh[ptr[v] + j] = w.f_h[(size_t)fd.x + j];
@@ -1959,7 +2243,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   const bool prof = profile_enabled();
   const unsigned long long wait_ns = (unsigned long long)(wait_us ? wait_us : kDefaultWaitUs) * 1000ull;
   MPAP_CK(cudaMemcpyAsync(w.qd, qd.data(), sizeof(QueryDev) * nq, cudaMemcpyHostToDevice, st));
-  MPAP_CK(cudaMemsetAsync(w.fdesc, 0, sizeof(uint4) * NVu, st));
+  MPAP_CK(cudaMemsetAsync(w.fdesc, 0, sizeof(FDesc) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.cand_n, 0, sizeof(uint32_t) * NVu, st));
   MPAP_CK(cudaMemsetAsync(w.oh_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
   {
@@ -1968,13 +2252,12 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     k_init_done<<<1, 256, 0, st>>>(w, nq);
   }
   MPAP_CK(cudaGetLastError());
+  const int grid = std::max(1, std::min<int>((int)tun.wave_blocks_per_sm, wave_occupancy())) * sms();
   {
     // the whole wavefront loop: one cooperative launch, every block resident
-    const int per_sm = std::max(1, std::min<int>((int)tun.wave_blocks_per_sm, wave_occupancy()));
     void* args[] = {&w};
     LaunchScope ls(st, "k_wave");
-    MPAP_CK(cudaLaunchCooperativeKernel((const void*)k_wave, dim3(per_sm * sms()), dim3(kWarpsPerBlock * 32), args, 0,
-                                        st));
+    MPAP_CK(cudaLaunchCooperativeKernel((const void*)k_wave, dim3(grid), dim3(kWarpsPerBlock * 32), args, 0, st));
   }
   {
     LaunchScope ls(st, "k_finalize");
@@ -1997,6 +2280,8 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   if (prof) {
     const char* names[4] = {"k_wave.expand", "k_wave.regroup", "k_wave.merge", "k_wave.end"};
     for (int k = 0; k < 4; ++k) profile_add(names[k], hc.waves, (double)hc.ph_ns[k] * 1e-6);
+    // mean time a block of the grid spent waiting at barriers
+    profile_add("k_wave.idle", hc.waves, (double)hc.idle_ns * 1e-6 / (double)grid);
   }
   rc = MPAP_OK;
   uint32_t lmax = 0;     // longest plan to return
@@ -2060,14 +2345,14 @@ int32_t search_fronts_impl(mpap_workspace* ws, uint32_t index, uint32_t* front_p
     return MPAP_ERR_INVALID_ARG;
   }
   const uint32_t V = ws->last_V[index], base = ws->last_base[index];
-  std::vector<uint4> fd(V);
-  MPAP_CK(cudaMemcpyAsync(fd.data(), w.fdesc + base, sizeof(uint4) * V, cudaMemcpyDeviceToHost, st));
+  std::vector<FDesc> fd(V);
+  MPAP_CK(cudaMemcpyAsync(fd.data(), w.fdesc + base, sizeof(FDesc) * V, cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaStreamSynchronize(st));
   std::vector<uint32_t> ptr(V + 1);
   uint64_t t = 0;
   for (uint32_t v = 0; v < V; ++v) {
     ptr[v] = (uint32_t)t;
-    t += fd[v].y;
+    t += fd[v].d.y;
   }
   ptr[V] = (uint32_t)t;
   if (front_ptr) std::memcpy(front_ptr, ptr.data(), 4 * ((size_t)V + 1));
