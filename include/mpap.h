@@ -274,8 +274,8 @@ void mpap_roadmap_free(mpap_roadmap* rm);
  * so a query that runs out of its share fails alone whatever the others do.  A
  * query that runs out of pool, plan arena (max_plans) or group array (max_plans)
  * ends with MPAP_ERR_CAPACITY in its own result; the other queries of the batch
- * run on.  Candidates of one wavefront wait in 32 slots of 32 bytes per node
- * (1 KiB per node); a node's candidates beyond 32 go to two overflow areas of
+ * run on.  Candidates of one wavefront wait in 64 slots of 32 bytes per node
+ * (2 KiB per node); a node's candidates beyond 64 go to two overflow areas of
  * max_plans records, shared out among the queries of a call like the pool.
  * Allocates with cudaMalloc; reused by every search call. */
 int32_t mpap_workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans,

@@ -33,8 +33,8 @@
 //            one atomic add and replaced by a block twice the needed size when
 //            too small (the old block is abandoned: at most as much again)
 //   fdesc    [NV] {live block, count, other block, log2 sizes}
-//   slots    [NV][32] candidates of the current wavefront {cost, h, parent, tie}
-//            (32 B), count per node; more than 32 go to an overflow area in
+//   slots    [NV][64] candidates of the current wavefront {cost, h, parent, tie}
+//            (32 B), count per node; more than 64 go to an overflow area in
 //            arrival order and are regrouped per node before the merge
 //   group    [cap] {cost, h, ref}: groups of more than 32 plans
 //   arena    [cap] {head u32, parent u32, iter u32, cost i64} for back-tracing
@@ -49,7 +49,7 @@
 
 namespace mpap {
 
-constexpr uint32_t kSlots = 32;          // inline candidate slots per node and wavefront
+constexpr uint32_t kSlots = 64;          // inline candidate slots per node and wavefront
 constexpr uint32_t kDefaultWaitUs = 20000000;  // barrier wait limit when no query sets one
 
 struct QueryDev {
@@ -139,6 +139,8 @@ struct Ctl {
   unsigned long long idle_ns;  // block time spent waiting at grid barriers, summed over blocks
   uint32_t waves;
   uint32_t grab[2];      // work counters of the expansion and the merge (nodes handed out)
+  uint32_t ovl_n;        // nodes with overflow records this wavefront
+  uint32_t ov_total;     // overflow records of all queries this wavefront
 };
 
 struct WS {
@@ -156,6 +158,8 @@ struct WS {
   Cand* ov;                // [ocap] overflow candidates in arrival order (per-query shares)
   Cand* ov2;               // [ocap] the same regrouped per node
   uint32_t* segoff;        // [NV] start of a node's regrouped overflow
+  uint2* ovl;              // [NV] {node, query} with overflow records this wavefront
+  uint32_t* ov_pref;       // [max_q + 1] exclusive prefix of the queries' overflow records
   uint32_t* oh_stamp;
   long long* g_cost;       // [gcap] groups of more than 32 plans
   long long* g_h;
@@ -322,6 +326,8 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from
     c.waves = 0;
     c.grab[0] = 0;
     c.grab[1] = 0;
+    c.ovl_n = 0;
+    c.ov_total = 0;
   }
   if (q >= nq) return;
   const QueryDev& Q = w.qd[q];
@@ -715,13 +721,15 @@ struct WaveSmem {
   long long open[kAccQ];
   unsigned long long plans[kAccQ];
   unsigned long long exps[kAccQ];
-  uint2 lbuf[kWarpsPerBlock][32];
+  uint2 lbuf[kWarpsPerBlock][32];   // bound for the next open list
+  uint2 mbuf[kWarpsPerBlock][32];   // bound for this wavefront's merge list
 };
 
 struct WarpCtx {
   WaveSmem* s;
   uint2* next;        // open list of the next wavefront
-  uint32_t lb_n;      // nodes in this warp's buffer (warp-uniform)
+  uint32_t lb_n;      // nodes in this warp's open-list buffer (warp-uniform)
+  uint32_t mb_n;      // nodes in this warp's merge-list buffer (warp-uniform)
   uint32_t nq;
   uint32_t it;
 };
@@ -770,16 +778,26 @@ __device__ __forceinline__ void flush_next(const WS& w, WarpCtx& cx) {
   cx.lb_n = 0;
 }
 
-// Puts node g of query q on the next open list unless it is there already
-// (its stamp); warp-uniform arguments.
+// Puts node g of query q on the next open list (warp-uniform arguments).  A
+// node gets there at most once per wavefront: the expansion, which visits every
+// listed node once, stamps the nodes it keeps on the list, and the merge, which
+// visits every node once, skips stamped ones (no atomics needed).
 __device__ __forceinline__ void push_next(const WS& w, WarpCtx& cx, uint32_t g, uint32_t q) {
-  const unsigned lane = lane_id();
-  uint32_t fresh = 0;
-  if (lane == 0) fresh = atomicExch(&w.oh_stamp[g], cx.it + 1) != cx.it + 1 ? 1u : 0u;
-  fresh = __shfl_sync(kFull, fresh, 0);
-  if (!fresh) return;
-  if (lane == 0) cx.s->lbuf[threadIdx.x >> 5][cx.lb_n] = make_uint2(g, q);
+  if (lane_id() == 0) cx.s->lbuf[threadIdx.x >> 5][cx.lb_n] = make_uint2(g, q);
   if (++cx.lb_n == 32) flush_next(w, cx);
+}
+
+// Moves this warp's buffered nodes to the merge list (one atomic).
+__device__ __forceinline__ void flush_merge(const WS& w, WarpCtx& cx) {
+  if (!cx.mb_n) return;
+  const unsigned lane = lane_id();
+  __syncwarp();
+  uint32_t b = 0;
+  if (lane == 0) b = atomicAdd(&w.ctl->m_n, cx.mb_n);
+  b = __shfl_sync(kFull, b, 0);
+  if (lane < cx.mb_n) w.m_list[b + lane] = cx.s->mbuf[threadIdx.x >> 5][lane];
+  __syncwarp();
+  cx.mb_n = 0;
 }
 
 // Arena records for the new entries of a block-mode front (marked open);
@@ -820,7 +838,7 @@ __device__ __forceinline__ uint32_t arena_block(const WS& w, uint32_t q, uint32_
 
 // The node's new descriptor and counters, and its place in the next open list.
 __device__ __forceinline__ void commit_tail(const WS& w, WarpCtx& cx, uint32_t q, uint32_t g, const FrontCursor& fc,
-                                            uint32_t n_new, long long last_c, long long last_h) {
+                                            uint32_t n_new, long long last_c, long long last_h, bool listed) {
   if (lane_id() == 0) {
     FDesc fd;
     fd.d = make_uint4(fc.off, fc.n, fc.off2, fc.lg | (fc.lg2 << 8));
@@ -830,7 +848,7 @@ __device__ __forceinline__ void commit_tail(const WS& w, WarpCtx& cx, uint32_t q
     acc_plans(w, cx, q, n_new);
     if (fc.n > ld_vol(&w.ctl->max_front)) atomicMax(&w.ctl->max_front, fc.n);
   }
-  push_next(w, cx, g, q);
+  if (!listed) push_next(w, cx, g, q);
 }
 
 // ---------------------------------------------------------------------------
@@ -865,16 +883,17 @@ __device__ __forceinline__ uint32_t front_upper(const WS& w, size_t o, uint32_t 
 // new candidates of node gx: the lane that opened gx this wavefront puts it on
 // the merge list; slots from kSlots on are overflow records, whose indices in
 // query q's overflow share come back in *ov (warp-aggregated).  Warp-collective.
-__device__ __forceinline__ void slot_book(const WS& w, uint32_t q, uint32_t gx, uint32_t r, uint32_t s, uint32_t* ov) {
+__device__ __forceinline__ void slot_book(const WS& w, WarpCtx& cx, uint32_t q, uint32_t gx, uint32_t r, uint32_t s,
+                                          uint32_t* ov) {
   const unsigned lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   const bool first = r && s == 0;
   const unsigned fb = __ballot_sync(kFull, first);
   if (fb) {
-    uint32_t b = 0;
-    if (lane == 0) b = atomicAdd(&w.ctl->m_n, (uint32_t)__popc(fb));
-    b = __shfl_sync(kFull, b, 0);
-    if (first) w.m_list[b + __popc(fb & lt)] = make_uint2(gx, q);
+    const uint32_t nf = (uint32_t)__popc(fb);
+    if (cx.mb_n + nf > 32) flush_merge(w, cx);
+    if (first) cx.s->mbuf[threadIdx.x >> 5][cx.mb_n + __popc(fb & lt)] = make_uint2(gx, q);
+    cx.mb_n += nf;
   }
   const uint32_t nov = (s + r > kSlots) ? s + r - max(s, kSlots) : 0u;
   const uint32_t incl = warp_incl_scan(nov);
@@ -894,6 +913,8 @@ __device__ __forceinline__ void put_cand(const WS& w, const QueryDev& Q, uint32_
   if (s < kSlots) {
     w.slot[(size_t)gx * kSlots + s] = cd;
   } else {
+    // the first overflow record of a node lists it for the regrouping
+    if (s == kSlots) w.ovl[atomicAdd(&w.ctl->ovl_n, 1u)] = make_uint2(gx, q);
     if (oi < Q.ov_cap) {
       cd.g = gx;
       cd.i = s - kSlots;
@@ -962,7 +983,7 @@ __device__ __forceinline__ void write_run(const WS& w, const QueryDev& Q, uint32
 // Small groups: lanes on the out-edges of u (two edges per lane per step, all
 // their loads in flight together), each lane walking the group plans (cost
 // order) and the target's front together.
-__device__ __forceinline__ void expand_edges(const WS& w, const QueryDev& Q, uint32_t q, uint32_t u, uint32_t e_beg,
+__device__ __forceinline__ void expand_edges(const WS& w, WarpCtx& cx, const QueryDev& Q, uint32_t q, uint32_t u, uint32_t e_beg,
                                              uint32_t e_end, const GroupSmem& gs, uint32_t cnt, bool interior) {
   const unsigned lane = lane_id();
   for (uint32_t e0 = e_beg; e0 < e_end; e0 += 64) {
@@ -989,8 +1010,8 @@ __device__ __forceinline__ void expand_edges(const WS& w, const QueryDev& Q, uin
     const uint32_t sa = ra ? atomicAdd(&w.cand_n[gxa], ra) : 0u;
     const uint32_t sb = rb ? atomicAdd(&w.cand_n[gxb], rb) : 0u;
     uint32_t oa = 0, ob = 0;
-    slot_book(w, q, gxa, ra, sa, &oa);
-    if (__any_sync(kFull, vb)) slot_book(w, q, gxb, rb, sb, &ob);
+    slot_book(w, cx, q, gxa, ra, sa, &oa);
+    if (__any_sync(kFull, vb)) slot_book(w, cx, q, gxb, rb, sb, &ob);
     write_run(w, Q, q, u, gs, ma, eda, gxa, sa, oa);
     write_run(w, Q, q, u, gs, mb, edb, gxb, sb, ob);
   }
@@ -998,7 +1019,7 @@ __device__ __forceinline__ void expand_edges(const WS& w, const QueryDev& Q, uin
 
 // Large groups: one out-edge at a time, lanes on the group plans (a cost-sorted
 // run of candidates per edge).
-__device__ __forceinline__ void expand_plans(const WS& w, const QueryDev& Q, uint32_t q, uint32_t u, uint32_t e_beg,
+__device__ __forceinline__ void expand_plans(const WS& w, WarpCtx& cx, const QueryDev& Q, uint32_t q, uint32_t u, uint32_t e_beg,
                                              uint32_t e_end, const long long* gc, const long long* gh,
                                              const uint32_t* gp, uint32_t cnt, bool interior) {
   const unsigned lane = lane_id();
@@ -1047,7 +1068,7 @@ __device__ __forceinline__ void expand_plans(const WS& w, const QueryDev& Q, uin
       // lane 0 takes the run's slots; the others follow it
       uint32_t s = 0, oi = 0;
       if (lane == 0) s = atomicAdd(&w.cand_n[gx], r);
-      slot_book(w, q, gx, lane == 0 ? r : 0u, s, &oi);
+      slot_book(w, cx, q, gx, lane == 0 ? r : 0u, s, &oi);
       s = __shfl_sync(kFull, s, 0);
       oi = __shfl_sync(kFull, oi, 0);
       if (ok) {
@@ -1106,10 +1127,11 @@ __device__ void phase_expand(const WS& w, WarpCtx& cx, GroupSmem& gs) {
     uint32_t goff = 0;
     if (n <= 32) {
       uint32_t pid = 0;
-      long long c = 0;
+      long long c = 0, hv = 0;
       if (lane < n) {
         pid = w.f_pid[o + lane];
         c = w.f_cost[o + lane];
+        hv = w.f_h[o + lane];
       }
       const bool open = lane < n && (pid & kOpen);
       const bool isg = open && c <= thr;
@@ -1120,7 +1142,7 @@ __device__ void phase_expand(const WS& w, WarpCtx& cx, GroupSmem& gs) {
       if (isg) {
         const uint32_t r = (uint32_t)__popc(gb & lt);
         gs.c[r] = c;
-        gs.h[r] = w.f_h[o + lane];
+        gs.h[r] = hv;
         gs.p[r] = pid & kPidMask;
         w.f_pid[o + lane] = pid & ~kOpen;
       }
@@ -1184,20 +1206,25 @@ __device__ void phase_expand(const WS& w, WarpCtx& cx, GroupSmem& gs) {
       // (the loop condition of the next iteration)
       if (rgoal && Q.is_goal[u]) w.qs[q].goal_next = 1u;
     }
-    // plans left open keep the node on the open list
-    if (rest) push_next(w, cx, g, q);
+    // plans left open keep the node on the open list (stamped: the merge of
+    // this wavefront will not list it again)
+    if (rest) {
+      if (lane == 0) w.oh_stamp[g] = it + 1;
+      push_next(w, cx, g, q);
+    }
     if (cnt) {
       const bool interior = (Q.flags & MPAP_QUERY_CHECK_INTERIOR) != 0;
       if (!global_group && cnt < lanes_from)
-        expand_edges(w, Q, q, u, e_beg, e_end, gs, cnt, interior);
+        expand_edges(w, cx, Q, q, u, e_beg, e_end, gs, cnt, interior);
       else if (global_group)
-        expand_plans(w, Q, q, u, e_beg, e_end, w.g_cost + goff, w.g_h + goff, w.g_pid + goff, cnt, interior);
+        expand_plans(w, cx, Q, q, u, e_beg, e_end, w.g_cost + goff, w.g_h + goff, w.g_pid + goff, cnt, interior);
       else
-        expand_plans(w, Q, q, u, e_beg, e_end, gs.c, gs.h, gs.p, cnt, interior);
+        expand_plans(w, cx, Q, q, u, e_beg, e_end, gs.c, gs.h, gs.p, cnt, interior);
     }
     __syncwarp();
   }
   flush_next(w, cx);
+  flush_merge(w, cx);
 }
 
 // ---------------------------------------------------------------------------
@@ -1208,10 +1235,10 @@ __device__ void phase_expand(const WS& w, WarpCtx& cx, GroupSmem& gs) {
 // function.
 // ---------------------------------------------------------------------------
 __device__ void phase_segments(const WS& w) {
-  const uint32_t n_m = ld_vol(&w.ctl->m_n);
+  const uint32_t n_o = ld_vol(&w.ctl->ovl_n);
   const uint32_t nt = gridDim.x * blockDim.x;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_m; k += nt) {
-    const uint2 gq = w.m_list[k];
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_o; k += nt) {
+    const uint2 gq = w.ovl[k];
     const uint32_t nc = w.cand_n[gq.x];
     if (nc <= kSlots) continue;
     const QueryDev& Q = w.qd[gq.y];
@@ -1228,16 +1255,19 @@ __device__ void phase_segments(const WS& w) {
 
 __device__ void phase_scatter(const WS& w) {
   const uint32_t nq = w.ctl->nq;
+  const uint32_t total = ld_vol(&w.ctl->ov_total);
   const uint32_t nt = gridDim.x * blockDim.x;
-  const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
-  for (uint32_t q = 0; q < nq; ++q) {
-    const QueryDev& Q = w.qd[q];
-    const uint32_t cnt = (uint32_t)min((uint64_t)w.qs[q].ov_n, Q.ov_cap);
-    for (uint32_t r = t0; r < cnt; r += nt) {
-      const Cand cd = w.ov[Q.ov_base + r];
-      const uint32_t so = w.segoff[cd.g];
-      if (so != kNone) w.ov2[(size_t)so + cd.i] = cd;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += nt) {
+    // the query of record r: last q with ov_pref[q] <= r
+    uint32_t lo = 0, hi = nq;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (w.ov_pref[mid] <= r) lo = mid; else hi = mid;
     }
+    const QueryDev& Q = w.qd[lo];
+    const Cand cd = w.ov[Q.ov_base + (r - w.ov_pref[lo])];
+    const uint32_t so = w.segoff[cd.g];
+    if (so != kNone) w.ov2[(size_t)so + cd.i] = cd;
   }
 }
 
@@ -1349,6 +1379,7 @@ __device__ __forceinline__ void merge_node(const WS& w, WarpCtx& cx, WarpSmem& s
     const uint32_t x = g - Q.base;
     const uint32_t nc = w.cand_n[g];
     const uint32_t so = nc > kSlots ? w.segoff[g] : 0u;
+    const bool listed = w.oh_stamp[g] == it + 1;   // kept on the open list by the expansion
     FrontCursor fc;
     {
       const uint4 fd = w.fdesc[g].d;
@@ -1464,7 +1495,7 @@ __device__ __forceinline__ void merge_node(const WS& w, WarpCtx& cx, WarpSmem& s
         lc = w.f_cost[(size_t)fc.off + fc.n - 1];
         lh = w.f_h[(size_t)fc.off + fc.n - 1];
       }
-      commit_tail(w, cx, q, g, fc, n_new, lc, lh);
+      commit_tail(w, cx, q, g, fc, n_new, lc, lh, listed);
       // an open plan of the next group at a goal node ends the query at the
       // top of the next iteration (the loop condition of Alg. 3)
       if (lane == 0 && gnext && Q.is_goal[x]) w.qs[q].goal_next = 1u;
@@ -1492,6 +1523,7 @@ __device__ __forceinline__ void merge_pair16(const WS& w, WarpCtx& cx, WarpSmem&
   const QueryDev& Q = w.qd[q];
   const uint32_t x = g - Q.base;
   const uint32_t n = fd.y, t = n + nc;
+  const bool listed = w.oh_stamp[g] == it + 1;   // kept on the open list by the expansion
   const bool isf = sl < n, isc = sl >= n && sl < t;
   long long kc = LLONG_MAX, vh = LLONG_MAX;
   uint32_t vt = 0xFFFFFFFFu, vp = 0u, va = 0u;
@@ -1652,7 +1684,7 @@ __device__ __forceinline__ void merge_pair16(const WS& w, WarpCtx& cx, WarpSmem&
   }
   // both halves' nodes to the next open list (warp-uniform calls)
   for (uint32_t h = 0; h < 32; h += 16) {
-    const bool pk = __shfl_sync(kFull, ok, (int)h);
+    const bool pk = __shfl_sync(kFull, ok && !listed, (int)h);
     const uint32_t pg = __shfl_sync(kFull, g, (int)h), pq = __shfl_sync(kFull, q, (int)h);
     if (pk) push_next(w, cx, pg, pq);
   }
@@ -1688,16 +1720,21 @@ __device__ void phase_merge(const WS& w, WarpCtx& cx, WarpSmem& sm) {
 // ---------------------------------------------------------------------------
 // Work of the last block at the barriers.
 // ---------------------------------------------------------------------------
-// After the expansion: does any query need its overflow regrouped?
+// After the expansion: does any query need its overflow regrouped?  The
+// exclusive prefix of the queries' overflow records (kept within each share)
+// maps a flat record index to its query.
 __device__ void epi_mid(const WS& w) {
-  __shared__ uint32_t s_any;
-  if (threadIdx.x == 0) s_any = 0;
-  __syncthreads();
-  const uint32_t nq = w.ctl->nq;
-  for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x)
-    if (w.qs[q].ov_n) s_any = 1u;
-  __syncthreads();
-  if (threadIdx.x == 0) w.ctl->ov_any = s_any;
+  if (threadIdx.x == 0) {
+    const uint32_t nq = w.ctl->nq;
+    uint32_t acc = 0;
+    for (uint32_t q = 0; q < nq; ++q) {
+      w.ov_pref[q] = acc;
+      acc += (uint32_t)min((uint64_t)w.qs[q].ov_n, w.qd[q].ov_cap);
+    }
+    w.ov_pref[nq] = acc;
+    w.ctl->ov_total = acc;
+    w.ctl->ov_any = acc ? 1u : 0u;
+  }
   phase_mark(w, 0);
 }
 
@@ -1744,6 +1781,7 @@ __device__ void epi_end(const WS& w) {
     c->ov_any = 0;
     c->grab[0] = 0;
     c->grab[1] = 0;
+    c->ovl_n = 0;
     c->it = it + 1;
     c->waves += 1;
   }
@@ -1767,6 +1805,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_wave(WS w) {
   WarpCtx cx;
   cx.s = &ws;
   cx.lb_n = 0;
+  cx.mb_n = 0;
   cx.nq = nq;
   if (blockIdx.x == 0 && threadIdx.x == 0) w.ctl->t_mark = global_timer();
   for (;;) {
@@ -2088,7 +2127,8 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
   bool ok = walloc(&w.f_cost, slots) && walloc(&w.f_h, slots) && walloc(&w.f_pid, slots) &&
             walloc(&w.f_aux, slots) && walloc(&w.fdesc, w.NV) && walloc(&w.slot, w.NV * kSlots) &&
             walloc(&w.cand_n, w.NV) && walloc(&w.ov, w.ocap) && walloc(&w.ov2, w.ocap) &&
-            walloc(&w.segoff, w.NV) && walloc(&w.oh_stamp, w.NV) && walloc(&w.g_cost, w.gcap) &&
+            walloc(&w.segoff, w.NV) && walloc(&w.ovl, w.NV) && walloc(&w.ov_pref, (size_t)max_q + 1) &&
+            walloc(&w.oh_stamp, w.NV) && walloc(&w.g_cost, w.gcap) &&
             walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) && walloc(&w.oh_list, 2 * w.NV) &&
             walloc(&w.m_list, w.NV) && walloc(&w.a_head, w.acap) && walloc(&w.a_parent, w.acap) &&
             walloc(&w.a_iter, w.acap) && walloc(&w.a_cost, w.acap) && walloc(&w.ctl, 1) && walloc(&w.qd, max_q) &&
@@ -2105,7 +2145,7 @@ void workspace_free(mpap_workspace* ws) {
   if (!ws) return;
   WS& w = ws->w;
   void* ptrs[] = {w.f_cost, w.f_h,     w.f_pid,  w.f_aux,  w.fdesc,  w.slot,     w.cand_n, w.ov,
-                  w.ov2,    w.segoff,  w.oh_stamp, w.g_cost, w.g_h,  w.g_pid,    w.oh_list, w.m_list,
+                  w.ov2,    w.segoff,  w.ovl,    w.ov_pref, w.oh_stamp, w.g_cost, w.g_h,  w.g_pid,    w.oh_list, w.m_list,
                   w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl,    w.qd,       w.qs,     w.res,
                   w.path};
   for (void* p : ptrs) cudaFree(p);
