@@ -896,13 +896,13 @@ __device__ __forceinline__ void slot_book(const WS& w, WarpCtx& cx, uint32_t q, 
     cx.mb_n += nf;
   }
   const uint32_t nov = (s + r > kSlots) ? s + r - max(s, kSlots) : 0u;
+  *ov = 0;
+  if (!__any_sync(kFull, nov != 0u)) return;    // the common case: every record fits its slots
   const uint32_t incl = warp_incl_scan(nov);
   const uint32_t tot = __shfl_sync(kFull, incl, 31);
   uint32_t b = 0;
-  if (tot) {
-    if (lane == 0) b = atomicAdd(&w.qs[q].ov_n, tot);
-    b = __shfl_sync(kFull, b, 0);
-  }
+  if (lane == 0) b = atomicAdd(&w.qs[q].ov_n, tot);
+  b = __shfl_sync(kFull, b, 0);
   *ov = b + incl - nov;
 }
 
