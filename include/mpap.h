@@ -335,9 +335,10 @@ int32_t mpap_certify_batch(mpap_roadmap* const* rms, const uint32_t* const* path
  * tables) and the output struct as for mpap_certify, and gets identical counts.
  * Limits: path_len <= 4096 nodes, (path_len - 1) * M <= 65536 checkpoints,
  * K + 1 <= 256 levels, at most 512 boxes; larger inputs return
- * MPAP_ERR_INVALID_ARG with the reason in mpap_last_error().  The first call on a
- * device looks up the array's device address (make it before any stream capture
- * on that device).  Every call on a device shares the one array and clears the
+ * MPAP_ERR_INVALID_ARG with the reason in mpap_last_error().  Every call looks up
+ * the array's device address on the current device (so it stays right after a
+ * device reset); the first call on a device may load the library's device code
+ * there, so make it before any stream capture on that device.  Every call on a device shares the one array and clears the
  * counters it needs, so calls that overlap on the GPU (other streams or threads)
  * race: serialise them.  Calls no cudaMalloc, cudaFree or allocating routine. */
 int32_t mpap_certify_noalloc(const mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,

@@ -334,24 +334,14 @@ static __device__ __align__(256) unsigned char g_certify_scratch[kNoAllocBytes];
 
 namespace {
 
-// Device address of g_certify_scratch on the current device, looked up once
-// per device (with that device current) and cached.
+// Device address of g_certify_scratch on the current device.
 int32_t noalloc_scratch(char** out) {
-  static std::mutex mu;
-  static void* addr[64] = {};
-  int dev = 0;
-  MPAP_CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    set_error("certify_noalloc: device ordinal %d out of range", dev);
-    return MPAP_ERR_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> g(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    MPAP_CK(cudaGetSymbolAddress(&p, g_certify_scratch));
-    addr[dev] = p;
-  }
-  *out = static_cast<char*>(addr[dev]);
+  // Looked up on every call (a host-side table lookup): after a device reset,
+  // or a primary-context reset by another framework, the library's module is
+  // loaded again and the array may sit at another address.
+  void* p = nullptr;
+  MPAP_CK(cudaGetSymbolAddress(&p, g_certify_scratch));
+  *out = static_cast<char*>(p);
   return MPAP_OK;
 }
 

@@ -159,13 +159,22 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(GemmArgs g) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
     }
     any = true;
-    // bounded wait for the tile's MMAs (shared-memory reuse and the result)
+    // bounded wait for the tile's MMAs (shared-memory reuse and the result):
+    // one second of GPU timer time, far beyond any healthy tile, so that it
+    // only ends a kernel whose MMAs never complete.  This is a last resort: the
+    // teardown below then frees tensor memory that MMAs still in flight may
+    // write, so it reports MPAP_ERR_TIMEOUT rather than recovering.
     uint32_t done = 0;
-    for (uint32_t tries = 0; tries < (1u << 22) && !done; ++tries) {
+    unsigned long long t0 = 0, t = 0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (!done) {
       asm volatile(
           "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
           : "=r"(done)
           : "r"(mb), "r"(phase));
+      if (done) break;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > 1000000000ull) break;
     }
     phase ^= 1u;
     // one decision for the whole CTA, so every thread leaves the loop together

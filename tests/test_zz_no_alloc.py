@@ -54,3 +54,20 @@ def test_noalloc_rejects_inputs_beyond_its_fixed_size(mp):
         mp.certify_noalloc(rg, too_long, 16, sc.mc_seed, 0, sc.delta_fx, sc.sigma_fx, sc.shift)
     assert e.value.status == mp.MPAP_ERR_INVALID_ARG
     assert "4096" in str(e.value)
+
+
+def test_noalloc_rejects_too_many_checkpoints(mp):
+    """A plan within the node limit whose edges hold more checkpoints than the
+    fixed array has room for: (3000 - 1) edges x 32 sub-steps > 65536.  (The
+    level-table limit, K + 1 <= 256, always holds: a roadmap's K is at most
+    255.)"""
+    sc = scenegen.make_scene("2d", 2, query_id=2)
+    rg = mp.build_roadmap_for_scene(sc, n=500, M=32)
+    ws = mp.Workspace(rg.V, front_cap=1024, max_plans=1 << 22)
+    res = mp.search(ws, rg, BIG, lam=0.5)
+    assert res.status == 0
+    plan = np.resize(res.path, 3000).astype(np.uint32)
+    with pytest.raises(mp.MpapError) as e:
+        mp.certify_noalloc(rg, plan, 16, sc.mc_seed, 0, sc.delta_fx, sc.sigma_fx, sc.shift)
+    assert e.value.status == mp.MPAP_ERR_INVALID_ARG
+    assert "65536" in str(e.value)
