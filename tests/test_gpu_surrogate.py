@@ -131,9 +131,15 @@ def test_mlp_gradients_match_oracle(mp, n):
     lo, go = omlp.loss_and_grad(p, x, y, rounding=True)
     assert loss == pytest.approx(lo, rel=1e-4, abs=1e-6)
     gd, od = omlp.unpack(g.astype(np.float64)), omlp.unpack(go)
+    # element by element: every entry of every parameter gradient within
+    # 1e-2 of that tensor's largest oracle magnitude (fp32 accumulation in
+    # another order can move a bfloat16 rounding of an activation by one unit,
+    # 2^-8 relative, which reaches the gradients through the layers above)
     for k, _ in omlp.SHAPES:
-        err = np.linalg.norm(gd[k] - od[k])
-        assert err <= 1e-2 * np.linalg.norm(od[k]) + 1e-9, (k, err, np.linalg.norm(od[k]))
+        tol = 1e-2 * np.max(np.abs(od[k])) + 1e-6
+        err = np.abs(gd[k] - od[k])
+        worst = np.unravel_index(np.argmax(err), err.shape)
+        assert err[worst] <= tol, (k, worst, gd[k][worst], od[k][worst], tol)
     # apply = False leaves the parameters alone
     np.testing.assert_array_equal(net.get_params(), p.astype(np.float32))
 
