@@ -247,9 +247,8 @@ def run_gpu(args, rank, world, local):
     for _ in range(args.warmup):
         arm.step()
     log("timed region")
-    # timed region: K steps, device events, profiler on, clocks sampled
-    mp.profile_reset()
-    mp.profile_enable(True)
+    # timed region: K steps, device events, library profiler off, clocks sampled
+    mp.profile_enable(False)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -263,9 +262,18 @@ def run_gpu(args, rank, world, local):
     barrier()
     launches = mp.launch_count() - launches0
     ck = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    # per-kernel breakdown in a separate pass over the same steps, with CUDA
+    # events around every launch (the library profiler), so that the timed
+    # value above carries no profiling overhead
+    log("breakdown pass")
+    mp.profile_reset()
+    mp.profile_enable(True)
+    for _ in range(args.steps):
+        arm.step()
+    torch.cuda.synchronize()
     mp.profile_enable(False)
     kern = mp.profile_read()
-    ms_total = e0.elapsed_time(e1)
     ms = ms_total / args.steps
     if world > 1:
         ms_total, exps = reduce_over_ranks(ms_total, exps, device)
@@ -282,7 +290,8 @@ def run_gpu(args, rank, world, local):
                       "parallelism": f"queries sharded over {world} GPU(s)"},
            "ms_per_query": ms / per_query,
            "gpu_launches": int(launches),
-           "tuning": tuning}
+           "tuning": tuning,
+           "breakdown": "per-kernel times from a second pass of the same steps with per-launch CUDA events"}
     # breakdown from the live kernel timers (timed region)
     search_k = {"k_init", "k_wave", "k_finalize", "k_candidates"}
     certify_k = {"k_mc_checkpoints", "k_mc_rollouts"}
@@ -296,9 +305,10 @@ def run_gpu(args, rank, world, local):
     out["expansions_per_step"] = exps / args.steps
     out["solved"] = sum(1 for r in res if r.status == 0)
     out["certified_failure_rate"] = sum(c["hits_any"] for c in certs) / max(1, sum(c["rollouts"] for c in certs))
-    out["roofline"] = roofline(kern, arm, res, args.steps)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    out["roofline"] = roofline(kern, arm, res, args.steps, sms=sms)
     # the two kernels that share most of the step, each against its own bound
-    out["roofline_by_kernel"] = [roofline(kern, arm, res, args.steps, name=k) for k in ("k_wave", "k_edges")
+    out["roofline_by_kernel"] = [roofline(kern, arm, res, args.steps, name=k, sms=sms) for k in ("k_wave", "k_edges")
                                  if k in kern]
     if ck:
         out["clocks"] = ck
@@ -319,7 +329,7 @@ def run_gpu(args, rank, world, local):
         log("surrogate")
         out["surrogate"] = surrogate_report(args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(scenes[:2])
+        out["cpu_baseline"] = cpu_baseline(scenes[:2], scenes[2:2 + 16])
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
@@ -348,7 +358,7 @@ def _traffic(kernel, units, key="bytes_per_roadmap"):
     return t[key] * units
 
 
-def roofline(kern, arm, res, steps, name=None):
+def roofline(kern, arm, res, steps, name=None, sms=152):
     """Roofline of one kernel (default: the dominant one) from the live
     CUDA-event timers."""
     peaks = {}
@@ -379,14 +389,15 @@ def roofline(kern, arm, res, steps, name=None):
         ops_per_launch = (39.0 * tests + 943.0 * edges) * steps / max(1, launches)
         achieved = ops_per_launch / (ms / launches / 1e3) / 1e12
         sm_max = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * sm_max * 1e6 / 1e12
+        peak = sms * 128 * sm_max * 1e6 / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": _traffic(name, B * steps / max(1, launches)),
                 "traffic_unit": "DRAM bytes per launch (ncu, scaled from an 8-roadmap capture)",
                 "near_tests_per_step": tests, "edges_per_step": edges,
                 "ops_per_step": 39.0 * tests + 943.0 * edges,
                 "all_pairs_per_step": V * V * B,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
+                "peak_source": f"derived: {sms} SMs (device) x 128 FP32 lanes x max SM clock "
+                               "(MEASURED_PEAKS.json sm_max_mhz)"}
     # HBM-bound search kernels: algorithmic bytes per step, the 16-byte reverse edge
     # record per plan-edge expansion and a 24-byte front entry per plan
     bytes_step = 16.0 * exps + 24.0 * plans
@@ -449,8 +460,7 @@ def e2e(arm, args, stream):
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     exps = 0
-    k = max(1, min(args.steps, 3))
-    for _ in range(k):
+    for _ in range(args.steps):
         exps += arm.step(host=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -790,15 +800,52 @@ def oracle_query(sc):
     return res.expansions
 
 
-def cpu_baseline(scenes):
+def host_cpu():
+    """(logical cores, CPU model) of the machine the oracle runs on."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def cpu_baseline(scenes, threaded_scenes):
+    """The oracle as it stands on the host cores: one thread over two queries,
+    then one query per thread over all cores (the oracle's calls release the
+    interpreter lock, so the threads run in parallel)."""
+    import concurrent.futures as cf
     import oracle
     oracle.build()
+    ncores, model = host_cpu()
     t0 = time.perf_counter()
     exps = sum(oracle_query(s) for s in scenes)
     dt = time.perf_counter() - t0
-    return {"value": exps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(scenes)} of the benchmark's 6D-16k queries (roadmap + search + 4096-rollout MC), "
-                      f"single thread, {dt:.1f} s", "ms_per_query": dt * 1e3 / len(scenes)}
+    out = {"value": exps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{len(scenes)} of the benchmark's 6D-16k queries (roadmap + search + 4096-rollout MC), "
+                     f"single thread, {dt:.1f} s", "ms_per_query": dt * 1e3 / len(scenes),
+           "host_cores": ncores, "cpu_model": model}
+    nt = min(ncores, len(threaded_scenes))
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=nt) as ex:
+        texps = sum(ex.map(oracle_query, threaded_scenes[:nt]))
+    tdt = time.perf_counter() - t0
+    out["threaded"] = {"value": texps / tdt, "unit": UNIT, "cores": nt, "queries": nt,
+                       "sample": f"{nt} queries, one per thread on {nt} threads, {tdt:.1f} s wall",
+                       "ms_per_query": tdt * 1e3 / nt}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -821,7 +868,8 @@ def run_reference(args, rank, world):
                        "note": "CPU oracle, one query per step (bounded sample)"},
             "ms_per_query": ms,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed 6D-16k queries, one per step"},
+                             "sample": f"{args.steps} timed 6D-16k queries, one per step",
+                             "host_cores": host_cpu()[0], "cpu_model": host_cpu()[1]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
