@@ -741,46 +741,67 @@ def surrogate_report(args, stream):
                           "note": "algorithmic bf16 FLOPs of the 11 products of a step over the tensor-core "
                                   "kernel's time; 128-wide layers leave it latency-bound",
                           "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)" if peaks else "fallback"}}
-    # evaluation: 64 held-out queries, plain vs screened; wall time from the
-    # search to the certified plan of every query (host decisions between rounds)
+    # evaluation on 64 held-out queries at one certified failure bound, wall
+    # time from the search to the certified plan of every query:
+    #   plain_gpu  one mpap_search per query, then its candidates certified in
+    #              solution order one Monte Carlo call at a time
+    #   batched    one batched search, candidates certified in solution order
+    #              in lock-step batched rounds (mpap_surrogate_screen, no network)
+    #   screened   the same with the network's screened order
     ev = {}
     seeds = range(1, 1 + SUR_BATCH)
     rms, res, cands, mcs = _sur_batch(mp, S, ws, cfg, seeds, 0)
     qs = [mp.make_query(1 << 62, scenegen.LAMBDA, goal_stop=False) for _ in rms]
+    ws1 = mp.Workspace(SUR_N + 2, front_cap=128, max_plans=1 << 22)
     sel = {}
-    for mode in ("plain", "screened", "plain", "screened"):      # second pass is the timed one
+    for mode in ("plain_gpu", "batched", "screened") * 2:      # second pass is the timed one
         torch.cuda.synchronize()
         t = time.perf_counter()
-        res = mp.search_batch(ws, rms, qs)
-        cands = S.collect_candidates(ws, res, 64)
-        t1 = time.perf_counter()
-        if mode == "plain":
-            orders = [np.arange(len(c["paths"])) if c else np.zeros(0, np.int64) for c in cands]
+        if mode == "plain_gpu":
+            cq = []
+            for rm, q in zip(rms, qs):
+                r = mp.search(ws1, rm, q.beta, lam=scenegen.LAMBDA, goal_stop=False)
+                cq.append(mp.search_candidates(ws1, 0, cap=64) if r.status == 0 else None)
+            t1 = t2 = time.perf_counter()
+            chosen = np.full(len(rms), -1, np.int64)
+            calls = np.zeros(len(rms), np.int64)
+            for i, c in enumerate(cq):
+                for j, path in enumerate(c["paths"] if c else []):
+                    ro, seed, base, d, sig, sh = mcs[i]
+                    ct = mp.certify(rms[i], path, ro, seed, base + j, d, sig, sh)
+                    calls[i] += 1
+                    if ct["hits_any"] <= SUR_EPS * ct["rollouts"]:
+                        chosen[i] = j
+                        break
+            out = S.Selection(chosen, calls, int(calls.max()) if len(calls) else 0)
         else:
-            pf = S.predicted_failure(net, S.candidate_features(rms, cands))
-            orders = [S.screened_order(p, SUR_TAU) for p in pf]
-        t2 = time.perf_counter()
-        out = S.certify_in_order(rms, cands, mcs, orders, SUR_EPS)
+            res = mp.search_batch(ws, rms, qs)
+            cq = S.collect_candidates(ws, res, 64)
+            t1 = time.perf_counter()
+            out = S.screen(net, rms, cq, mcs, SUR_EPS, SUR_TAU, use_net=(mode == "screened"))
+            t2 = t1
         torch.cuda.synchronize()
         t3 = time.perf_counter()
         dt = t3 - t
         sel[mode] = out
+        cands = cq
         ev[mode] = {"ms_per_batch": dt * 1e3, "ms_per_query": dt * 1e3 / len(rms),
-                    "phase_ms": {"search_and_candidates": (t1 - t) * 1e3, "screen": (t2 - t1) * 1e3,
-                                 "certify_rounds": (t3 - t2) * 1e3},
+                    "phase_ms": {"search_and_candidates": (t1 - t) * 1e3, "certify": (t3 - t2) * 1e3},
                     "mc_calls": int(out.mc_calls.sum()), "mc_rounds": out.rounds,
                     "mc_rollouts": int(out.mc_calls.sum()) * cfg.mc_rollouts,
                     "solved": int((out.chosen >= 0).sum())}
-    a, b = sel["plain"], sel["screened"]
+    a, b = sel["plain_gpu"], sel["screened"]
+    assert np.array_equal(a.chosen >= 0, b.chosen >= 0)
     ratios = [cands[i]["cost"][b.chosen[i]] / cands[i]["cost"][a.chosen[i]]
               for i in range(len(rms)) if a.chosen[i] >= 0]
     return {"workload": f"6D double integrator, {SUR_N} samples, 30 boxes, 32^3 grid, twice the 6D MC noise, "
                         f"beta unbounded, exhaustive search (no goal stop), 64 candidates/query, "
                         f"{cfg.mc_rollouts}-rollout MC judge",
             "queries": len(rms), "certified_failure_bound": SUR_EPS, "screen_threshold": SUR_TAU,
-            "plain": ev["plain"], "screened": ev["screened"],
-            "mc_calls_ratio": ev["screened"]["mc_calls"] / max(1, ev["plain"]["mc_calls"]),
-            "speedup": ev["plain"]["ms_per_batch"] / ev["screened"]["ms_per_batch"],
+            "plain_gpu": ev["plain_gpu"], "batched": ev["batched"], "screened": ev["screened"],
+            "mc_calls_ratio": ev["screened"]["mc_calls"] / max(1, ev["plain_gpu"]["mc_calls"]),
+            "speedup_vs_plain_gpu": ev["plain_gpu"]["ms_per_batch"] / ev["screened"]["ms_per_batch"],
+            "speedup_vs_batched": ev["batched"]["ms_per_batch"] / ev["screened"]["ms_per_batch"],
             "cost_ratio_mean": float(np.mean(ratios)) if ratios else None,
             "cost_ratio_max": float(np.max(ratios)) if ratios else None,
             "train": train}

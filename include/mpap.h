@@ -510,6 +510,103 @@ int32_t mpap_mlp_train_step(mpap_mlp* net, const float* x, const float* y, uint3
                             int32_t apply, float* loss, float* grads, int32_t mem, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Certification-driven choice of plans (Alg. 1 step 4; Sec. 3 on Monte Carlo
+ * certification and the refinement of beta).
+ *
+ * Alg. 1 certifies the plan Explore returns for a bound beta and, from the
+ * Monte Carlo outcome, loosens beta (more aggressive plans) or tightens it (more
+ * conservative ones) and explores again until a robust plan is found.  The
+ * paper leaves the update open; the rule of this library:
+ *   - a plan passes when its any-failure count is at most max_hits;
+ *   - with no failure seen yet, beta becomes 2 beta + 1 (at most 2^62) after a
+ *     pass or after "no plan", and the query stops once a pass brings no
+ *     cheaper plan than the previous pass;
+ *   - with failures but no pass yet, beta becomes floor((b + f) / 2), b the
+ *     largest bound known to give no plan (-1 if none), f the smallest failing
+ *     bound;
+ *   - with both, beta bisects between the largest passing and the smallest
+ *     failing bound;
+ *   - a query stops when no integer lies strictly between its bounds, after
+ *     max_rounds explorations, or when a search ends with an error.
+ * ------------------------------------------------------------------------- */
+#define MPAP_REFINE_PASS 0
+#define MPAP_REFINE_FAIL 1
+#define MPAP_REFINE_NONE 2    /* the search found no plan (MPAP_NO_SOLUTION) */
+#define MPAP_REFINE_ERROR 3   /* the search ended with an error (its status in hits) */
+
+/* The bounds of one query's refinement; -1 marks an unknown bound (bounds are
+ * non-negative).  Start from {-1, 0, -1, -1}. */
+typedef struct {
+  int64_t lo;        /* largest bound that passed */
+  int64_t lo_cost;   /* cost of the plan found at lo */
+  int64_t hi;        /* smallest bound that failed */
+  int64_t none;      /* largest bound that gave no plan */
+} mpap_refine_bounds;
+
+/* Records the outcome (MPAP_REFINE_PASS, _FAIL or _NONE) of exploring at beta
+ * (cost: the plan's cost, for a pass) and sets *next to the bound to explore
+ * next, or -1 when the refinement stops.  Pure host code (no GPU needed).
+ * MPAP_ERR_INVALID_ARG for a null pointer, a negative beta or another outcome. */
+int32_t mpap_refine_advance(mpap_refine_bounds* b, int64_t beta, int32_t outcome, int64_t cost, int64_t* next);
+
+/* One exploration of a refinement. */
+typedef struct {
+  int64_t beta;
+  int64_t cost;      /* plan cost (pass, fail), -1 otherwise */
+  int32_t outcome;   /* MPAP_REFINE_* */
+  int32_t hits;      /* any-failure count (pass, fail), the search status (error), -1 (none) */
+} mpap_refine_round;
+
+/* Result of one query's refinement.  path and history are caller-owned host
+ * arrays of path_cap and hist_cap entries (either may be NULL with cap 0). */
+typedef struct {
+  int32_t certified;        /* 1 if some bound passed */
+  int32_t status;           /* MPAP_OK, or MPAP_ERR_INVALID_ARG if path_cap was too small */
+  int64_t beta;             /* largest passing bound, -1 without a pass */
+  int64_t cost, h;          /* the plan found at beta */
+  uint32_t path_len, path_cap;
+  uint32_t* path;
+  mpap_cert cert;           /* its Monte Carlo certificate */
+  uint32_t rounds;          /* explorations run */
+  uint32_t hist_cap;
+  mpap_refine_round* history;   /* the first min(rounds, hist_cap) explorations */
+} mpap_refine_result;
+
+/* Refines the bound of n queries in lock step: round t is one batched search
+ * (mpap_search_batch) over the queries still refining, each with its current
+ * bound, and one batched certification (mpap_certify_batch) of the plans found,
+ * with call id t.  qs[i] gives query i's initial bound (beta) and its search
+ * parameters; mcs[i] its Monte Carlo model (call_id ignored); max_hits[i] its
+ * pass threshold.  outs[i] receives its result.  ws must hold the nodes of all
+ * n roadmaps.  Returns MPAP_OK, or the first error that is not a search's own
+ * (search errors end only their query, as MPAP_REFINE_ERROR in its history). */
+int32_t mpap_refine_batch(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs,
+                          const mpap_mc_params* mcs, const uint32_t* max_hits, uint32_t n,
+                          uint32_t max_rounds, mpap_refine_result* outs, void* stream);
+
+/* Screened certification of candidate plans (the paper has no counterpart: it
+ * serves the learned surrogate).  Query i (rms[i]) has candidates c =
+ * cand_ptr[i] .. cand_ptr[i+1]-1, usually P_candidates in solution order
+ * (mpap_search_candidates_batch); candidate c is the node sequence
+ * path[path_ptr[c] .. path_ptr[c+1]).  With use_net = 1 the network's
+ * predicted any-failure probability 1 - (1 - p_coll)(1 - p_loc) (binary32,
+ * from the 48 features feat[c][48], computed here when feat is NULL) orders
+ * each query's candidates: those predicted at most tau first, then the others,
+ * each group in index order; with use_net = 0 the order is the index order.
+ * Then, in lock-step rounds (one batched certification per round), every
+ * unresolved query certifies the next candidate of its order with call id
+ * mcs[i].call_id + j (j its index within the query) until one has an
+ * any-failure fraction hits_any / rollouts <= eps, or after max_calls (0: no
+ * limit).  Outputs (host): chosen[i] (index within the query, -1 if none
+ * passed), mc_calls[i], *rounds, and p_fail[c] (may be NULL).  net may be NULL
+ * when use_net = 0.  Host arrays throughout. */
+int32_t mpap_surrogate_screen(mpap_mlp* net, mpap_roadmap* const* rms, uint32_t nq, const uint32_t* cand_ptr,
+                              const uint32_t* path_ptr, const uint32_t* path, const float* feat,
+                              const mpap_mc_params* mcs, double eps, float tau, int32_t use_net,
+                              uint32_t max_calls, int32_t* chosen, uint32_t* mc_calls, uint32_t* rounds,
+                              float* p_fail, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Launch accounting and kernel timing (tracing).  The paper reports per-phase
  * computation times (Table 2); these entry points expose the same information
  * per kernel.  mpap_launch_count() counts every kernel this library has launched

@@ -39,7 +39,8 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_tuning_clear", "mpap_tuning_export", "mpap_autotune_build", "mpap_autotune_search",
            "mpap_search_candidates_batch", "mpap_plan_features_batch", "mpap_roadmap_from_csr_peaks",
            "mpap_roadmap_export_peaks", "mpap_roadmap_export_reverse", "mpap_feature_levels",
-           "mpap_roadmap_update", "mpap_roadmap_update_batch"]
+           "mpap_roadmap_update", "mpap_roadmap_update_batch", "mpap_refine_advance", "mpap_refine_batch",
+           "mpap_surrogate_screen"]
 
 
 class mpap_scene(C.Structure):
@@ -80,6 +81,24 @@ class mpap_tuning(C.Structure):
 class mpap_cert(C.Structure):
     _fields_ = [("hits_loc", C.c_uint32), ("hits_coll", C.c_uint32), ("hits_any", C.c_uint32),
                 ("rollouts", C.c_uint32)]
+
+
+MPAP_REFINE_PASS, MPAP_REFINE_FAIL, MPAP_REFINE_NONE, MPAP_REFINE_ERROR = 0, 1, 2, 3
+
+
+class mpap_refine_bounds(C.Structure):
+    _fields_ = [("lo", C.c_int64), ("lo_cost", C.c_int64), ("hi", C.c_int64), ("none", C.c_int64)]
+
+
+class mpap_refine_round(C.Structure):
+    _fields_ = [("beta", C.c_int64), ("cost", C.c_int64), ("outcome", C.c_int32), ("hits", C.c_int32)]
+
+
+class mpap_refine_result(C.Structure):
+    _fields_ = [("certified", C.c_int32), ("status", C.c_int32), ("beta", C.c_int64), ("cost", C.c_int64),
+                ("h", C.c_int64), ("path_len", C.c_uint32), ("path_cap", C.c_uint32),
+                ("path", C.POINTER(C.c_uint32)), ("cert", mpap_cert), ("rounds", C.c_uint32),
+                ("hist_cap", C.c_uint32), ("history", C.POINTER(mpap_refine_round))]
 
 
 _NP_SCALAR = {C.c_int32: "i4", C.c_uint32: "u4", C.c_int64: "i8", C.c_uint64: "u8", C.c_float: "f4"}
@@ -209,6 +228,13 @@ def lib():
         L.mpap_mlp_forward.argtypes = [P, P, C.c_uint32, P, i32, P]
         L.mpap_mlp_train_step.restype = i32
         L.mpap_mlp_train_step.argtypes = [P, P, P, C.c_uint32, C.c_float, i32, C.POINTER(C.c_float), P, i32, P]
+        L.mpap_refine_advance.argtypes = [C.POINTER(mpap_refine_bounds), C.c_int64, C.c_int32, C.c_int64,
+                                          C.POINTER(C.c_int64)]
+        L.mpap_refine_batch.argtypes = [P, C.POINTER(P), C.POINTER(mpap_query), C.POINTER(mpap_mc_params),
+                                        P, C.c_uint32, C.c_uint32, C.POINTER(mpap_refine_result), P]
+        L.mpap_surrogate_screen.argtypes = [P, C.POINTER(P), C.c_uint32, P, P, P, P, C.POINTER(mpap_mc_params),
+                                            C.c_double, C.c_float, i32, C.c_uint32, P, P,
+                                            C.POINTER(C.c_uint32), P, P]
         TP = C.POINTER(mpap_tuning)
         L.mpap_tuning_get.restype = i32
         L.mpap_tuning_get.argtypes = [i32, C.c_uint32, TP]

@@ -23,7 +23,7 @@ if not os.path.exists(NVCC):
     NVCC = "nvcc"
 
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
-         "-Xcompiler", "-O2", "-I", os.path.join(ROOT, "include")]
+         "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
 
 
 def sources():

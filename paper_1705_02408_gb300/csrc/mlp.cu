@@ -582,6 +582,8 @@ static int32_t check_err(mpap_mlp* n, cudaStream_t st) {
   return MPAP_OK;
 }
 
+uint32_t mlp_max_batch(const mpap_mlp* nt) { return nt->max_batch; }
+
 int32_t mlp_forward(mpap_mlp* nt, const float* x, uint32_t n, float* prob, int32_t mem, cudaStream_t st) {
   if (n == 0) return MPAP_OK;
   if (n > nt->max_batch) {

@@ -12,7 +12,9 @@ procedures meet the same certified failure bound; the screen only changes how
 many Monte Carlo calls (and lock-step rounds over a batch of queries) that takes.
 
 Every computation runs in libmpap kernels (search, candidate back-tracing,
-features, MLP, Monte Carlo); this module sequences the calls.
+features, MLP, Monte Carlo); the screened certification itself, ordering and
+lock-step rounds included, is one library call (mpap_surrogate_screen).  This
+module marshals arguments and sequences the training steps.
 """
 from __future__ import annotations
 
@@ -20,7 +22,10 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import Mlp, certify_batch, plan_features_batch, search_candidates_batch
+import ctypes as C
+
+from . import (Mlp, _check, _mc_array, _stream, certify_batch, lib, mpap_mc_params,
+               plan_features_batch, search_candidates_batch)
 
 
 def collect_candidates(ws, results, cap=64, path_cap=1 << 14):
@@ -75,66 +80,45 @@ def train(net: Mlp, X, Y, steps=1000, batch=4096, lr=1e-3, seed=0, log_every=0):
     return np.array(losses)
 
 
-def predicted_failure(net: Mlp, feats):
-    """Predicted probability of any failure, 1 - (1 - p_coll)(1 - p_loc), per
-    candidate of every query (one batched forward pass)."""
-    sizes = [len(f) for f in feats]
-    if sum(sizes) == 0:
-        return [np.zeros(0) for _ in feats]
-    X = np.concatenate([f for f in feats if len(f)])
-    P = np.concatenate([net.forward(X[o:o + net.max_batch]) for o in range(0, len(X), net.max_batch)])
-    pa = 1.0 - (1.0 - P[:, 0]) * (1.0 - P[:, 1])
-    out, o = [], 0
-    for s in sizes:
-        out.append(pa[o:o + s])
-        o += s
-    return out
-
-
-def screened_order(p_fail, tau):
-    """Candidates predicted to pass (p_fail <= tau) first, then the rest; each
-    group keeps the cost order."""
-    idx = np.arange(len(p_fail))
-    return np.concatenate([idx[p_fail <= tau], idx[p_fail > tau]]).astype(np.int64)
-
-
 @dataclass
 class Selection:
     chosen: np.ndarray      # per query: candidate index that passed, -1 if none did
     mc_calls: np.ndarray    # per query: Monte Carlo certifications spent
     rounds: int             # lock-step rounds (batched certification launches)
+    p_fail: list = None     # per query: predicted any-failure probability of each candidate
 
 
-def certify_in_order(rms, cands, mcs, orders, eps, max_calls=None):
-    """Lock-step over the batch: in round t every unresolved query certifies the
-    t-th candidate of its order (one batched launch per round) and is resolved by
-    the first candidate whose any-failure fraction is at most eps.  Candidate j of
-    query i always uses call_id j, so a candidate's certificate does not depend on
-    the order it is tried in."""
+def screen(net, rms, cands, mcs, eps, tau=0.1, use_net=True, feats=None, max_calls=0, stream=None):
+    """mpap_surrogate_screen: certifies the candidates of every query in lock-step
+    rounds until one passes (any-failure fraction <= eps), in the network's
+    screened order (predicted any-failure <= tau first) when use_net, else in
+    index (solution) order.  cands: per query a dict with "paths" (or None);
+    mcs[i] = (rollouts, seed, call_base, delta_fx, sigma_fx, shift), candidate j
+    certified with call id call_base + j; feats: per query [k_i, 48] float32, or
+    None to compute them on the GPU."""
     nq = len(rms)
-    chosen = np.full(nq, -1, np.int64)
-    calls = np.zeros(nq, np.int64)
-    live = [i for i in range(nq) if cands[i]]
-    rounds = 0
-    t = 0
-    while live:
-        batch = [i for i in live if t < len(orders[i]) and (max_calls is None or t < max_calls)]
-        if not batch:
-            break
-        jobs = []
-        for i in batch:
-            j = int(orders[i][t])
-            ro, seed, _, delta, sig, sh = mcs[i]
-            jobs.append((i, j, (ro, seed, j, delta, sig, sh)))
-        certs = certify_batch([rms[i] for i, _, _ in jobs], [cands[i]["paths"][j] for i, j, _ in jobs],
-                              [m for _, _, m in jobs])
-        rounds += 1
-        done = set()
-        for (i, j, _), ct in zip(jobs, certs):
-            calls[i] += 1
-            if ct["hits_any"] <= eps * ct["rollouts"]:
-                chosen[i] = j
-                done.add(i)
-        live = [i for i in live if i not in done and t + 1 < len(orders[i])]
-        t += 1
-    return Selection(chosen, calls, rounds)
+    counts = [len(c["paths"]) if c else 0 for c in cands]
+    cand_ptr = np.zeros(nq + 1, np.uint32)
+    cand_ptr[1:] = np.cumsum(counts)
+    paths = [p for c in cands if c for p in c["paths"]]
+    total = len(paths)
+    path_ptr = np.zeros(total + 1, np.uint32)
+    path_ptr[1:] = np.cumsum([len(p) for p in paths])
+    flat = np.ascontiguousarray(np.concatenate(paths) if paths else np.zeros(1), np.uint32)
+    fx = None
+    if feats is not None and use_net and total:
+        fx = np.ascontiguousarray(np.concatenate([f for f in feats if len(f)]), np.float32)
+    ms, keep = _mc_array(mcs)
+    chosen = np.zeros(max(nq, 1), np.int32)
+    calls = np.zeros(max(nq, 1), np.uint32)
+    pf = np.zeros(max(total, 1), np.float32)
+    rounds = C.c_uint32()
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(lib().mpap_surrogate_screen(net.h if (use_net and net is not None) else None,
+                                       (C.c_void_p * max(nq, 1))(*[rm.h for rm in rms]), nq, vp(cand_ptr),
+                                       vp(path_ptr), vp(flat), vp(fx) if fx is not None else None,
+                                       ms.ctypes.data_as(C.POINTER(mpap_mc_params)), float(eps), float(tau),
+                                       1 if use_net else 0, int(max_calls), vp(chosen), vp(calls),
+                                       C.byref(rounds), vp(pf), _stream(stream)), "mpap_surrogate_screen")
+    split = [pf[cand_ptr[i]:cand_ptr[i + 1]].copy() for i in range(nq)]
+    return Selection(chosen[:nq].astype(np.int64), calls[:nq].astype(np.int64), int(rounds.value), split)

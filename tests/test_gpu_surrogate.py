@@ -207,3 +207,55 @@ def test_batched_candidates_and_features_match_single_calls(mp, orc):
             np.testing.assert_array_equal(f, mp.plan_features(rg, c["paths"]))
         else:
             assert f.shape == (0, 48)
+
+
+def test_screen_matches_single_certifications(mp):
+    """mpap_surrogate_screen against direct calls: its predicted failure is the
+    network's forward pass combined as 1 - (1 - p_coll)(1 - p_loc) in binary32;
+    its order puts the candidates predicted at most tau first (each group in
+    solution order); and its lock-step selection equals certifying each query's
+    candidates one by one in that order (call id base + j) until one passes.
+    Features computed by the screen equal the ones given to it."""
+    from paper_1705_02408_gb300 import surrogate as S
+    cfg = scenegen.surrogate_config(3000)
+    scs = [scenegen.make_scene(cfg, s, query_id=s) for s in (1, 2, 3, 4, 5)]
+    rms = mp.build_roadmaps([mp.scene_spec(sc) for sc in scs])
+    wsb = mp.Workspace(sum(r.V for r in rms), front_cap=128, max_plans=1 << 22)
+    res = mp.search_batch(wsb, rms, [mp.make_query(BIG, 0.5, goal_stop=False) for _ in scs])
+    cands = S.collect_candidates(wsb, res, 16)
+    assert sum(1 for c in cands if c) >= 4
+    feats = S.candidate_features(rms, cands)
+    mcs = [(256, sc.mc_seed, 5, sc.delta_fx, sc.sigma_fx * 3, sc.shift) for sc in scs]
+    net = mp.Mlp(seed=7, max_batch=512)
+    eps, tau = 0.05, 0.5
+    one = np.float32(1)
+    for use_net in (False, True):
+        sel = S.screen(net, rms, cands, mcs, eps, tau, use_net=use_net, feats=feats if use_net else None)
+        for i, c in enumerate(cands):
+            k = len(c["paths"]) if c else 0
+            order = list(range(k))
+            if use_net and k:
+                P = net.forward(feats[i])
+                pf = one - (one - P[:, 0]) * (one - P[:, 1])
+                np.testing.assert_array_equal(sel.p_fail[i], pf)
+                order = [j for j in range(k) if pf[j] <= np.float32(tau)] + \
+                        [j for j in range(k) if pf[j] > np.float32(tau)]
+            want, calls = -1, 0
+            for j in order:
+                ro, seed, base, d, sig, sh = mcs[i]
+                ct = mp.certify(rms[i], c["paths"][j], ro, seed, base + j, d, sig, sh)
+                calls += 1
+                if ct["hits_any"] <= eps * ct["rollouts"]:
+                    want = j
+                    break
+            assert (int(sel.chosen[i]), int(sel.mc_calls[i])) == (want, calls), (use_net, i)
+        assert sel.rounds == int(max(sel.mc_calls))
+    # features computed inside the screen give the same decisions
+    a = S.screen(net, rms, cands, mcs, eps, tau, use_net=True, feats=feats)
+    b = S.screen(net, rms, cands, mcs, eps, tau, use_net=True)
+    np.testing.assert_array_equal(a.chosen, b.chosen)
+    for x, y in zip(a.p_fail, b.p_fail):
+        np.testing.assert_array_equal(x, y)
+    # at most one call per query
+    c1 = S.screen(net, rms, cands, mcs, eps, tau, use_net=True, feats=feats, max_calls=1)
+    assert int(c1.mc_calls.max()) <= 1 and c1.rounds <= 1

@@ -58,10 +58,12 @@ def test_screen_needs_fewer_monte_carlo_calls(mp):
     costs = []
     for o in range(0, 64, B):
         rms, cands, feats, mcs = _batch(mp, S, ws, cfg, range(1 + o, 1 + o + B), 1024, 0)
-        plain = [np.arange(len(c["paths"])) if c else np.zeros(0, np.int64) for c in cands]
-        screened = [S.screened_order(p, TAU) for p in S.predicted_failure(net, feats)]
-        a = S.certify_in_order(rms, cands, mcs, plain, EPS)
-        b = S.certify_in_order(rms, cands, mcs, screened, EPS)
+        # both procedures through the library's screened certification
+        # (mpap_surrogate_screen): solution order, and the network's order
+        a = S.screen(None, rms, cands, mcs, EPS, use_net=False)
+        b = S.screen(net, rms, cands, mcs, EPS, TAU, use_net=True, feats=feats)
+        # the screen's order: candidates predicted at most TAU first
+        assert sum(int((p <= np.float32(TAU)).sum()) for p in b.p_fail) > 0
         np.testing.assert_array_equal(a.chosen >= 0, b.chosen >= 0)
         # every returned plan is certified: re-check both selections by Monte Carlo
         for sel in (a, b):

@@ -143,12 +143,3 @@ def test_feature_bins_for_uneven_counts(orc):
     assert list(counts) == [2, 1, 1, 1, 2, 1, 1, 1, 2, 1, 1, 1, 2, 1, 1, 1]
     np.testing.assert_allclose(f[16:32], counts * 5 / (64 * K), rtol=1e-7)
     np.testing.assert_allclose(f[:16], 5 / K, rtol=1e-7)
-
-
-def test_screened_order_keeps_cost_order_within_groups():
-    from paper_1705_02408_gb300.surrogate import screened_order
-    p = np.array([0.3, 0.01, 0.2, 0.05, 0.5, 0.0])
-    assert list(screened_order(p, 0.1)) == [1, 3, 5, 0, 2, 4]
-    assert list(screened_order(p, 1.0)) == list(range(6))
-    assert list(screened_order(p, -1.0)) == list(range(6))
-    assert screened_order(np.zeros(0), 0.1).size == 0

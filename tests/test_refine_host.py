@@ -1,85 +1,69 @@
-"""Host logic of the GPU refinement driver (no GPU): its bound bookkeeping takes
-the same steps as the oracle's on random outcome sequences, and the lock-step
-driver sequences library calls as the oracle's loop does, with the searches and
-certifications replaced by deterministic fakes."""
+"""Host logic of the library's refinement (no GPU): its bound rule
+(mpap_refine_advance, the step mpap_refine_batch takes after every
+certification) takes the same steps as the oracle's on random outcome sequences
+and at the edges of the integer range, and the batch entry point rejects bad
+arguments before touching a device."""
+import ctypes as C
+
 import numpy as np
+import pytest
 
 from oracle import refine as orf
 
 
-def _gpu_bounds():
-    from paper_1705_02408_gb300.refine import _Bounds
-    return _Bounds()
+@pytest.fixture(scope="module")
+def gref():
+    from paper_1705_02408_gb300 import build
+    build.build()
+    from paper_1705_02408_gb300 import refine
+    return refine
 
 
-def test_bounds_follow_the_oracle_rule():
+def _walk(gref, beta, outcomes, costs):
+    b = gref.Bounds()
+    lo = lo_cost = hi = none = None
+    for outcome, cost in zip(outcomes, costs):
+        got = b.advance(beta, outcome, cost)
+        lo, lo_cost, hi, none, want = orf.next_beta(beta, outcome, cost, lo, lo_cost, hi, none)
+        assert got == want, (beta, outcome, cost)
+        assert b.state == (lo, lo_cost, hi, none)
+        if want is None:
+            return
+        beta = want
+
+
+def test_bounds_follow_the_oracle_rule(gref):
     rng = np.random.default_rng(5)
     for trial in range(300):
-        b = _gpu_bounds()
-        lo = lo_cost = hi = none = None
         beta = int(rng.integers(0, 1 << int(rng.integers(1, 40))))
-        cost = 10 ** 9
-        for step in range(40):
-            outcome = rng.choice([orf.PASS, orf.FAIL, orf.NONE], p=[0.45, 0.4, 0.15])
-            if outcome == orf.PASS:
-                cost -= int(rng.integers(0, 3))
-            got = b.advance(beta, outcome, cost)
-            lo, lo_cost, hi, none, want = orf.next_beta(beta, outcome, cost, lo, lo_cost, hi, none)
-            assert got == want, (trial, step)
-            assert (b.lo, b.lo_cost, b.hi, b.none) == (lo, lo_cost, hi, none)
-            if want is None:
-                break
-            beta = want
+        outcomes = rng.choice([orf.PASS, orf.FAIL, orf.NONE], size=40, p=[0.45, 0.4, 0.15])
+        costs = 10 ** 9 - np.cumsum(rng.integers(0, 3, 40))
+        _walk(gref, beta, list(outcomes), [int(c) for c in costs])
 
 
-def test_lock_step_driver_with_fake_library(monkeypatch):
-    """refine_batch against the oracle's sequential loop, with searches and
-    certifications replaced by deterministic functions of (query, beta, call)."""
+def test_bounds_at_the_edges(gref):
+    """Loosening saturates at 2^62 (2 beta + 1 would overflow 64 bits near it);
+    tightening from a failure at 0 stops (floor((-1 + 0) / 2) = -1 leaves no
+    integer in between); bisection of bounds near 2^62 does not overflow."""
+    cap = 1 << 62
+    for beta in (cap // 2 - 1, cap // 2, cap // 2 + 1, cap - 1, cap):
+        _walk(gref, beta, [orf.NONE, orf.NONE], [0, 0])
+    _walk(gref, 0, [orf.FAIL], [0])
+    _walk(gref, 5, [orf.FAIL, orf.NONE, orf.FAIL, orf.NONE], [0] * 4)
+    _walk(gref, cap - 3, [orf.PASS, orf.PASS], [10, 9])
+    _walk(gref, cap - 3, [orf.PASS, orf.FAIL, orf.PASS, orf.FAIL], [10, 0, 9, 0])
+
+
+def test_advance_rejects_bad_arguments(gref):
     import paper_1705_02408_gb300 as mp
-    from paper_1705_02408_gb300 import refine as gref
-
-    class R:
-        def __init__(self, status, cost, h, path):
-            self.status, self.cost, self.h, self.path = status, cost, h, path
-
-    def fake_search(q, beta):
-        if beta < 3 * q:
-            return R(mp.MPAP_NO_SOLUTION, 0, 0, np.zeros(0, np.uint32))
-        cost = 1000 - min(beta, 200 + 50 * q)
-        return R(mp.MPAP_OK, cost, beta // 2, np.array([q, beta % 7], np.uint32))
-
-    def fake_cert(q, path, call_id):
-        beta_rt = int(path[1])
-        hits = (q * 7 + call_id * 3 + beta_rt) % 11
-        return {"hits_loc": hits, "hits_coll": 0, "hits_any": hits, "rollouts": 10}
-
-    nq = 6
-    rms = [object() for _ in range(nq)]
-    qid = {id(r): i for i, r in enumerate(rms)}
-
-    def search_batch(ws, rr, queries, path_cap=4096, stream=None, check=True):
-        return [fake_search(qid[id(r)], q.beta) for r, q in zip(rr, queries)]
-
-    def certify_batch(rr, paths, mcs, stream=None):
-        return [fake_cert(qid[id(r)], p, m[2]) for r, p, m in zip(rr, paths, mcs)]
-
-    monkeypatch.setattr(gref, "search_batch", search_batch)
-    monkeypatch.setattr(gref, "certify_batch", certify_batch)
-    beta0 = [10, 50, 3, 400, 0, 77]
-    mcs = [(10, 1, 0, 1, None, None)] * nq
-    got = gref.refine_batch(None, rms, beta0, mcs, 5, max_rounds=9)
-    for q in range(nq):
-        def s(beta, q=q):
-            r = fake_search(q, beta)
-            return r.status, r.cost, r.h, r.path
-
-        def c(path, call_id, q=q):
-            return fake_cert(q, path, call_id)
-
-        want = orf.refine_with(s, c, beta0[q], 5, 9)
-        g = got[q]
-        assert g.history == want.history
-        assert (g.certified, g.beta, g.cost, g.h, g.rounds) == (want.certified, want.beta, want.cost, want.h,
-                                                                 want.rounds)
-        np.testing.assert_array_equal(g.path, want.path)
-        assert g.cert == want.cert
+    b = mp.mpap_refine_bounds(-1, 0, -1, -1)
+    nxt = C.c_int64()
+    assert mp.lib().mpap_refine_advance(C.byref(b), -1, mp.MPAP_REFINE_PASS, 0, C.byref(nxt)) == \
+        mp.MPAP_ERR_INVALID_ARG
+    assert mp.lib().mpap_refine_advance(C.byref(b), 5, mp.MPAP_REFINE_ERROR, 0, C.byref(nxt)) == \
+        mp.MPAP_ERR_INVALID_ARG
+    assert mp.lib().mpap_refine_advance(None, 5, mp.MPAP_REFINE_PASS, 0, C.byref(nxt)) == mp.MPAP_ERR_INVALID_ARG
+    # a batch without a workspace is rejected on the host
+    assert mp.lib().mpap_refine_batch(None, None, None, None, None, 1, 4, None, None) == mp.MPAP_ERR_INVALID_ARG
+    assert mp.lib().mpap_surrogate_screen(None, None, 1, None, None, None, None, None, 0.05, 0.1, 0, 0, None,
+                                          None, None, None, None) == mp.MPAP_ERR_INVALID_ARG
