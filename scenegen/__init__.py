@@ -304,3 +304,42 @@ def load_calibration() -> dict:
 
 def calib_key(cfg: Config, seed: int) -> str:
     return f"{cfg.name}:{cfg.dim_kind}:{cfg.n}:{seed}"
+
+
+# ---------------------------------------------------------------------------
+# Synthetic observations for the learned error-rate heuristic.  The paper fits
+# its network to error rates of a real visual-inertial estimator measured
+# against motion capture; that data is not available, so observations come from
+# an invented sensor model: the rate r of the position-error magnitude is
+# Gaussian with mean 0.02 (1 + 0.5 |v| + 0.3 |w|) (1 - n / 12) (negative when
+# more than 12 features are visible: the estimate relocalises) and standard
+# deviation 0.004 (1 + |v|) + 0.002 |w|, for speed |v| <= 1, angular rate
+# |w| <= 2 and n = 0 .. 24 visible features.
+# ---------------------------------------------------------------------------
+def vio_samples(n: int, seed: int):
+    """(X [n, 7] float32 = (v, w, n_visible), r [n] float32) drawn from the model above."""
+    rng = np.random.default_rng([int(seed), 0x710])
+    d = rng.normal(0.0, 1.0, (n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    v = d * rng.uniform(0.0, 1.0, (n, 1))
+    a = rng.normal(0.0, 1.0, (n, 3))
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    w = a * rng.uniform(0.0, 2.0, (n, 1))
+    nv = rng.integers(0, 25, (n, 1)).astype(np.float64)
+    sv, sw = np.linalg.norm(v, axis=1), np.linalg.norm(w, axis=1)
+    mean = 0.02 * (1 + 0.5 * sv + 0.3 * sw) * (1 - nv[:, 0] / 12.0)
+    std = 0.004 * (1 + sv) + 0.002 * sw
+    r = mean + std * rng.normal(0.0, 1.0, n)
+    return np.concatenate([v, w, nv], 1).astype(np.float32), r.astype(np.float32)
+
+
+def mapped_states(n: int, seed: int):
+    """[n, 7] float32 mapped states (position in the unit cube, velocity in the
+    unit ball, yaw in [-pi, pi)) for the heuristic map."""
+    rng = np.random.default_rng([int(seed), 0x3A9])
+    p = rng.uniform(0.0, 1.0, (n, 3))
+    d = rng.normal(0.0, 1.0, (n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    v = d * rng.uniform(0.0, 1.0, (n, 1)) ** (1.0 / 3.0)
+    y = rng.uniform(-np.pi, np.pi, (n, 1))
+    return np.concatenate([p, v, y], 1).astype(np.float32)
