@@ -510,6 +510,60 @@ int32_t mpap_mlp_train_step(mpap_mlp* net, const float* x, const float* y, uint3
                             int32_t apply, float* loss, float* grads, int32_t mem, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned error-rate heuristic (Sec. 5.1).  A feedforward network with two
+ * hidden layers of eight ReLU units maps x = (v_x, v_y, v_z, w_x, w_y, w_z, n)
+ * (linear and angular velocity, visible-feature count) to the mean and the
+ * standard deviation of the Gaussian rate of the position-error magnitude:
+ *   z = W3 relu(W2 relu(W1 x + b1) + b2) + b3,  mean = z0,
+ *   std = softplus(z1) + 1e-3,
+ * fitted by maximum likelihood: loss = mean over the batch of
+ * log std + (r - mean)^2 / (2 std^2).  Packed parameters (fp32,
+ * MPAP_ERRNET_PARAMS): W1[8][7], b1[8], W2[8][8], b2[8], W3[2][8], b3[2].
+ * mpap_errnet_create draws weights uniform in +-1/sqrt(fan in) from seed, biases
+ * zero.  All arithmetic is binary32 on the CUDA cores; batch gradients are
+ * summed in a fixed order, so training is deterministic.
+ * ------------------------------------------------------------------------- */
+#define MPAP_ERRNET_PARAMS 154
+#define MPAP_ERRNET_INPUTS 7
+typedef struct mpap_errnet mpap_errnet;
+int32_t mpap_errnet_create(uint64_t seed, uint32_t max_batch, mpap_errnet** out);
+void mpap_errnet_free(mpap_errnet* net);
+int32_t mpap_errnet_get_params(mpap_errnet* net, float* params, void* stream);
+/* Sets the parameters and clears the Adam state. */
+int32_t mpap_errnet_set_params(mpap_errnet* net, const float* params, void* stream);
+/* out[n][2] = (mean, std) of the inputs x[n][7]; host arrays, or device arrays
+ * with mem = MPAP_MEM_DEVICE.  n <= max_batch. */
+int32_t mpap_errnet_forward(mpap_errnet* net, const float* x, uint32_t n, float* out, int32_t mem, void* stream);
+/* One maximum-likelihood step on observed rates r[n]: *loss (optional) is the
+ * loss before the step, grads (optional, MPAP_ERRNET_PARAMS floats) its
+ * gradient; if apply, one Adam step (beta1 0.9, beta2 0.999, eps 1e-8,
+ * bias-corrected) with learning rate lr.  1 <= n <= max_batch. */
+int32_t mpap_errnet_train_step(mpap_errnet* net, const float* x, const float* r, uint32_t n, float lr, int32_t apply,
+                               float* loss, float* grads, int32_t mem, void* stream);
+
+/* The heuristic map: values (mean, std) map_val[n_map][2] known at mapped
+ * states map_state[n_map][7] = (position 3, velocity 3, yaw) are interpolated
+ * at query states q[n_q][7] by their k <= 16 nearest mapped states under
+ *   d^2 = w[0] |dp|^2 + w[1] |dv|^2 + w[2] wrap(dyaw)^2,
+ *   wrap(a) = a - 2 pi rint(a / 2 pi),
+ * ties to the lower index, weighted by 1 / (d + 1e-6): out[n_q][2].  k larger
+ * than n_map uses all mapped states.  mem: MPAP_MEM_HOST (copies in and out,
+ * synchronises) or MPAP_MEM_DEVICE for all arrays but w (asynchronous). */
+int32_t mpap_errmap_query(const float* map_state, const float* map_val, uint32_t n_map, const float* q, uint32_t n_q,
+                          uint32_t k, const float* w, float* out, int32_t mem, void* stream);
+
+/* The mapped mean rate at the centres ((2 i + 1) / (2 G), ...) of a G^Dp grid
+ * (Dp = 2 for dim_kind 2, else 3; x fastest), for one velocity vel[3] and yaw,
+ * as a quality level of the grid form of the heuristic, so that a roadmap built
+ * on it accumulates the learned rate: the grid form gains dt (1 - k / n_f) per
+ * sub-step, the learned one dt mean / mu_ref, so
+ *   level = clamp(floor(n_f (1 - mean / mu_ref) + 1/2), 0, K)
+ * (uint8 levels[G^Dp]).  Map arguments and mem as for mpap_errmap_query. */
+int32_t mpap_errmap_levels(const float* map_state, const float* map_val, uint32_t n_map, uint32_t k, const float* w,
+                           int32_t dim_kind, int32_t grid_G, const float* vel, float yaw, float mu_ref, int32_t n_f,
+                           int32_t K, uint8_t* levels, int32_t mem, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Certification-driven choice of plans (Alg. 1 step 4; Sec. 3 on Monte Carlo
  * certification and the refinement of beta).
  *

@@ -40,7 +40,9 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_search_candidates_batch", "mpap_plan_features_batch", "mpap_roadmap_from_csr_peaks",
            "mpap_roadmap_export_peaks", "mpap_roadmap_export_reverse", "mpap_feature_levels",
            "mpap_roadmap_update", "mpap_roadmap_update_batch", "mpap_refine_advance", "mpap_refine_batch",
-           "mpap_surrogate_screen"]
+           "mpap_surrogate_screen", "mpap_errnet_create", "mpap_errnet_free", "mpap_errnet_get_params",
+           "mpap_errnet_set_params", "mpap_errnet_forward", "mpap_errnet_train_step", "mpap_errmap_query",
+           "mpap_errmap_levels"]
 
 
 class mpap_scene(C.Structure):
@@ -228,6 +230,16 @@ def lib():
         L.mpap_mlp_forward.argtypes = [P, P, C.c_uint32, P, i32, P]
         L.mpap_mlp_train_step.restype = i32
         L.mpap_mlp_train_step.argtypes = [P, P, P, C.c_uint32, C.c_float, i32, C.POINTER(C.c_float), P, i32, P]
+        L.mpap_errnet_create.argtypes = [C.c_uint64, C.c_uint32, C.POINTER(P)]
+        L.mpap_errnet_free.argtypes = [P]
+        L.mpap_errnet_free.restype = None
+        L.mpap_errnet_get_params.argtypes = [P, P, P]
+        L.mpap_errnet_set_params.argtypes = [P, P, P]
+        L.mpap_errnet_forward.argtypes = [P, P, C.c_uint32, P, i32, P]
+        L.mpap_errnet_train_step.argtypes = [P, P, P, C.c_uint32, C.c_float, i32, C.POINTER(C.c_float), P, i32, P]
+        L.mpap_errmap_query.argtypes = [P, P, C.c_uint32, P, C.c_uint32, C.c_uint32, P, P, i32, P]
+        L.mpap_errmap_levels.argtypes = [P, P, C.c_uint32, C.c_uint32, P, i32, i32, P, C.c_float, C.c_float, i32,
+                                         i32, P, i32, P]
         L.mpap_refine_advance.argtypes = [C.POINTER(mpap_refine_bounds), C.c_int64, C.c_int32, C.c_int64,
                                           C.POINTER(C.c_int64)]
         L.mpap_refine_batch.argtypes = [P, C.POINTER(P), C.POINTER(mpap_query), C.POINTER(mpap_mc_params),
@@ -898,6 +910,117 @@ class Mlp:
         _check(lib().mpap_mlp_train_step(self.h, xp, yp, n, float(lr), 1 if apply else 0, C.byref(loss), gp,
                                          1 if dev else 0, _stream(stream)), "mpap_mlp_train_step")
         return loss.value, g
+
+
+# ---------------------------------------------------------------------------
+# Learned error-rate heuristic (Sec. 5.1)
+# ---------------------------------------------------------------------------
+ERRNET_PARAMS = 154
+
+
+class ErrNet:
+    """An mpap_errnet: the 7-8-8-2 error-rate network (mean and standard
+    deviation of the Gaussian rate of the position error), trained by maximum
+    likelihood on the GPU.  Arrays are numpy (host) or contiguous CUDA tensors."""
+
+    def __init__(self, seed=0, max_batch=1 << 16):
+        h = C.c_void_p()
+        _check(lib().mpap_errnet_create(int(seed), int(max_batch), C.byref(h)), "mpap_errnet_create")
+        self.h = h
+        self.max_batch = int(max_batch)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.mpap_errnet_free(self.h)
+            self.h = None
+
+    def get_params(self, stream=None) -> np.ndarray:
+        out = np.zeros(ERRNET_PARAMS, np.float32)
+        _check(lib().mpap_errnet_get_params(self.h, out.ctypes.data_as(C.c_void_p), _stream(stream)),
+               "mpap_errnet_get_params")
+        return out
+
+    def set_params(self, params, stream=None):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == ERRNET_PARAMS
+        _check(lib().mpap_errnet_set_params(self.h, p.ctypes.data_as(C.c_void_p), _stream(stream)),
+               "mpap_errnet_set_params")
+
+    def forward(self, x, stream=None):
+        """[n, 2] (mean, std) of inputs x [n, 7]."""
+        xp, xk, dev = _ptr(x, np.float32)
+        n = int(x.shape[0])
+        if dev:
+            import torch
+            out = torch.empty((n, 2), dtype=torch.float32, device=x.device)
+            op = C.c_void_p(out.data_ptr())
+        else:
+            out = np.zeros((n, 2), np.float32)
+            op = out.ctypes.data_as(C.c_void_p)
+        _check(lib().mpap_errnet_forward(self.h, xp, n, op, 1 if dev else 0, _stream(stream)), "mpap_errnet_forward")
+        return out
+
+    def train_step(self, x, r, lr=1e-3, apply=True, want_grads=False, stream=None):
+        """One maximum-likelihood step on rates r [n]; returns (loss, grads or None)."""
+        xp, xk, dev = _ptr(x, np.float32)
+        rp, rk, _ = _ptr(r, np.float32)
+        n = int(x.shape[0])
+        loss = C.c_float()
+        g, gp = None, None
+        if want_grads:
+            if dev:
+                import torch
+                g = torch.empty(ERRNET_PARAMS, dtype=torch.float32, device=x.device)
+                gp = C.c_void_p(g.data_ptr())
+            else:
+                g = np.zeros(ERRNET_PARAMS, np.float32)
+                gp = g.ctypes.data_as(C.c_void_p)
+        _check(lib().mpap_errnet_train_step(self.h, xp, rp, n, float(lr), 1 if apply else 0, C.byref(loss), gp,
+                                            1 if dev else 0, _stream(stream)), "mpap_errnet_train_step")
+        return loss.value, g
+
+
+def errmap_query(map_state, map_val, q, k=8, w=(1.0, 1.0, 1.0), stream=None):
+    """mpap_errmap_query: (mean, std) [Q, 2] at query states q [Q, 7] from the
+    mapped states [N, 7] and their values [N, 2] (host or device arrays)."""
+    sp, sk, dev = _ptr(map_state, np.float32)
+    vp, vk, _ = _ptr(map_val, np.float32)
+    qp, qk, _ = _ptr(q, np.float32)
+    ww = np.ascontiguousarray(w, np.float32)
+    nq = int(q.shape[0])
+    if dev:
+        import torch
+        out = torch.empty((nq, 2), dtype=torch.float32, device=q.device)
+        op = C.c_void_p(out.data_ptr())
+    else:
+        out = np.zeros((nq, 2), np.float32)
+        op = out.ctypes.data_as(C.c_void_p)
+    _check(lib().mpap_errmap_query(sp, vp, int(map_state.shape[0]), qp, nq, int(k), ww.ctypes.data_as(C.c_void_p),
+                                   op, 1 if dev else 0, _stream(stream)), "mpap_errmap_query")
+    return out
+
+
+def errmap_levels(map_state, map_val, dim_kind, grid_G, vel=(0.0, 0.0, 0.0), yaw=0.0, mu_ref=0.02, k=8,
+                  w=(1.0, 1.0, 1.0), n_f=12, K=24, stream=None):
+    """mpap_errmap_levels: uint8 quality levels [G^Dp] of the mapped mean rate at
+    the grid's cell centres (host arrays)."""
+    sp, sk, dev = _ptr(map_state, np.float32)
+    vp, vk, _ = _ptr(map_val, np.float32)
+    ww = np.ascontiguousarray(w, np.float32)
+    vv = np.ascontiguousarray(vel, np.float32)
+    cells = grid_G ** (2 if dim_kind == 2 else 3)     # 2: the unit square, else the unit cube
+    if dev:
+        import torch
+        out = torch.empty(cells, dtype=torch.uint8, device=map_state.device)
+        op = C.c_void_p(out.data_ptr())
+    else:
+        out = np.zeros(cells, np.uint8)
+        op = out.ctypes.data_as(C.c_void_p)
+    _check(lib().mpap_errmap_levels(sp, vp, int(map_state.shape[0]), int(k), ww.ctypes.data_as(C.c_void_p),
+                                    int(dim_kind), int(grid_G), vv.ctypes.data_as(C.c_void_p), float(yaw),
+                                    float(mu_ref), int(n_f), int(K), op, 1 if dev else 0, _stream(stream)),
+           "mpap_errmap_levels")
+    return out
 
 
 # ---------------------------------------------------------------------------

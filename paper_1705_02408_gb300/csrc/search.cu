@@ -2316,7 +2316,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   MPAP_CK(cudaMemcpyAsync(ws->h_hdr + o_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   MPAP_CK(cudaStreamSynchronize(st));
   ws->last_max_front = hc.max_front;
-  launch_count_add(3);
+  launch_count_add(1);   // k_init_done (k_init, k_wave and k_finalize count through their scopes)
   if (prof) {
     const char* names[4] = {"k_wave.expand", "k_wave.regroup", "k_wave.merge", "k_wave.end"};
     for (int k = 0; k < 4; ++k) profile_add(names[k], hc.waves, (double)hc.ph_ns[k] * 1e-6);
