@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-perception", action="store_true")
     ap.add_argument("--no-update", action="store_true")
+    ap.add_argument("--no-errnet", action="store_true")
     ap.add_argument("--sur-train-plans", type=int, default=200000,
                     help="Monte Carlo-labelled candidate plans to train the surrogate on")
     ap.add_argument("--sur-train-steps", type=int, default=2000)
@@ -323,6 +324,8 @@ def run_gpu(args, rank, world, local):
         out["perception_levels"] = perception_report(arm)
     if rank == 0 and not args.no_update:
         out["online_update"] = update_report(arm)
+    if rank == 0 and not args.no_errnet:
+        out["learned_heuristic"] = errnet_report(arm)
     if rank == 0 and world == 1 and not args.no_mixed:
         out["mixed_batch"] = mixed_report(args, stream)
     if rank == 0 and world == 1 and not args.no_surrogate:
@@ -500,6 +503,63 @@ def perception_report(arm, features=256, reps=10):
         pairs = Y * G ** 3 * features
         out[key] = {"ms_per_table": ms, "cell_feature_pairs_per_s": pairs / (ms / 1e3),
                     "mean_level": float(lv.float().mean().item())}
+    return out
+
+
+def errnet_report(arm, n_train=200000, steps=400, batch=8192, n_map=20000):
+    """The learned error-rate heuristic (Sec. 5.1): maximum-likelihood training of
+    the 7-8-8-2 network on synthetic observations, its forward pass over the mapped
+    states, the weighted 8-nearest-neighbour map queried at the benchmark scenes'
+    6D roadmap nodes, and the level grid (32^3) for a roadmap build; CUDA events."""
+    import torch
+    mp = arm.mp
+    X, r = scenegen.vio_samples(n_train, 11)
+    Xd, rd = torch.from_numpy(X).cuda(), torch.from_numpy(r).cuda()
+    net = mp.ErrNet(seed=5, max_batch=max(batch, n_map))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    idx = torch.randint(0, n_train, (steps, batch), device="cuda", generator=g)
+    for t in range(5):
+        net.train_step(Xd[idx[t]], rd[idx[t]], lr=3e-3)
+    out = {"network": "7-8-8-2 ReLU, Gaussian mean and std, maximum likelihood (binary32)"}
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for t in range(steps):
+        loss, _ = net.train_step(Xd[idx[t]], rd[idx[t]], lr=3e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["train"] = {"steps": steps, "batch": batch, "ms_per_step": ms / steps,
+                    "samples_per_s": steps * batch / (ms / 1e3), "final_loss": float(loss)}
+    # the map: network evaluated at mapped states (synthetic inputs), queried at roadmap nodes
+    M = torch.from_numpy(scenegen.mapped_states(n_map, 12)).cuda()
+    Xm = torch.from_numpy(scenegen.vio_samples(n_map, 13)[0]).cuda()
+    e0.record()
+    vals = net.forward(Xm)
+    e1.record()
+    torch.cuda.synchronize()
+    out["forward_ms_per_map"] = e0.elapsed_time(e1)
+    rms = arm.rms
+    xs = [rm.export()["x"] for rm in rms[:4]]
+    q = np.concatenate([np.concatenate([x.T, np.zeros((x.shape[1], 1), np.float32)], 1) for x in xs])
+    qd = torch.from_numpy(np.ascontiguousarray(q, np.float32)).cuda()
+    for _ in range(2):
+        mp.errmap_query(M, vals, qd, k=8, w=(4.0, 1.0, 0.25))
+    torch.cuda.synchronize()
+    e0.record()
+    mp.errmap_query(M, vals, qd, k=8, w=(4.0, 1.0, 0.25))
+    e1.record()
+    torch.cuda.synchronize()
+    qms = e0.elapsed_time(e1)
+    out["map_query"] = {"map_states": n_map, "queries": int(len(q)), "k": 8, "ms": qms,
+                        "pairs_per_s": n_map * len(q) / (qms / 1e3)}
+    e0.record()
+    lv = mp.errmap_levels(M, vals, 6, 32, vel=(0.5, 0.0, 0.0), yaw=0.0, mu_ref=0.02, k=8)
+    e1.record()
+    torch.cuda.synchronize()
+    out["levels_32cubed_ms"] = e0.elapsed_time(e1)
+    out["levels_mean"] = float(lv.float().mean().item())
     return out
 
 

@@ -271,8 +271,10 @@ void mpap_roadmap_free(mpap_roadmap* rm);
  * and up, replaced by blocks twice the needed size as its front grows, so single
  * fronts may be far larger than front_cap as long as the pool lasts.  Each
  * query of a call gets its own share of the pool, in proportion to its nodes,
- * so a query that runs out of its share fails alone whatever the others do.  A
- * query that runs out of pool, plan arena (max_plans) or group array (max_plans)
+ * so a query that runs out of its share fails alone whatever the others do.  Half
+ * of the plan arena (max_plans records) is shared out the same way; a query that
+ * fills its share draws on the other half, which all queries of the call share.
+ * A query that runs out of pool, of plan arena or of group array (max_plans)
  * ends with MPAP_ERR_CAPACITY in its own result; the other queries of the batch
  * run on.  Candidates of one wavefront wait in 64 slots of 32 bytes per node
  * (2 KiB per node); a node's candidates beyond 64 go to two overflow areas of

@@ -141,13 +141,16 @@ struct Ctl {
   uint32_t grab[2];      // work counters of the expansion and the merge (nodes handed out)
   uint32_t ovl_n;        // nodes with overflow records this wavefront
   uint32_t ov_total;     // overflow records of all queries this wavefront
+  unsigned long long arena_common_n;   // records of the arena's common half handed out
+  unsigned long long tmp_n;            // bulk-merge scratch entries handed out this wavefront
 };
 
 struct WS {
   uint64_t NV;
   uint32_t fcap;           // front pool entries per node (pool = NV fcap)
   uint64_t pcap;           // front pool entries
-  uint64_t acap, gcap, ocap;
+  uint64_t acap, gcap, ocap, tcap;
+  uint64_t arena_common_base, arena_common_cap;   // the arena's half that all queries share
   long long* f_cost;       // [pcap] front pool
   long long* f_h;
   uint32_t* f_pid;
@@ -158,6 +161,11 @@ struct WS {
   Cand* ov;                // [ocap] overflow candidates in arrival order (per-query shares)
   Cand* ov2;               // [ocap] the same regrouped per node
   uint32_t* segoff;        // [NV] start of a node's regrouped overflow
+  long long* t_cost;       // [tcap] bulk-merge scratch (reset every wavefront): candidate
+  long long* t_h;          //   skylines {cost, h, parent, tie key} and insertion indices
+  uint32_t* t_pp;
+  uint32_t* t_tb;
+  uint32_t* t_m;
   uint2* ovl;              // [NV] {node, query} with overflow records this wavefront
   uint32_t* ov_pref;       // [max_q + 1] exclusive prefix of the queries' overflow records
   uint32_t* oh_stamp;
@@ -328,6 +336,8 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from
     c.grab[1] = 0;
     c.ovl_n = 0;
     c.ov_total = 0;
+    c.arena_common_n = 0;
+    c.tmp_n = 0;
   }
   if (q >= nq) return;
   const QueryDev& Q = w.qd[q];
@@ -699,16 +709,17 @@ __device__ __forceinline__ void merge_chunk_reg(const WS& w, uint32_t q, FrontCu
   __syncwarp();
 }
 
-// r arena records of query q's share (call from one lane); kNone when the share
-// is used up (the query then fails alone).
+// r arena records for query q (call from one lane): from the query's own share
+// while it lasts, then from the arena's common half, which every query of the
+// batch draws on; kNone when both are used up (the query then fails).
 __device__ __forceinline__ uint32_t arena_take(const WS& w, uint32_t q, uint32_t r) {
   const unsigned long long o = atomicAdd(&w.qs[q].arena_n, (unsigned long long)r);
   const QueryDev& Q = w.qd[q];
-  if (o + r > Q.arena_cap) {
-    query_error(w, q, kErrArena);
-    return kNone;
-  }
-  return (uint32_t)(Q.arena_base + o);
+  if (o + r <= Q.arena_cap) return (uint32_t)(Q.arena_base + o);
+  const unsigned long long c = atomicAdd(&w.ctl->arena_common_n, (unsigned long long)r);
+  if (c + r <= w.arena_common_cap) return (uint32_t)(w.arena_common_base + c);
+  query_error(w, q, kErrArena);
+  return kNone;
 }
 
 // Per-block shared state of the wavefront kernel: per-query counter
@@ -1368,6 +1379,197 @@ __device__ __forceinline__ void merge_small(FrontCursor& fc, WarpSmem& sm, uint3
 // ---------------------------------------------------------------------------
 // Merge (RemoveDominated, Sec. 3, for every node that received candidates).
 // ---------------------------------------------------------------------------
+// Bulk merge of a node's nc candidates (many) into its front, linear in the
+// front's size: the candidates' own skyline S is built in this wavefront's
+// scratch, 32 candidates at a time (each chunk filtered against S, reduced to
+// its skyline and merged into S between two scratch regions); then one sweep
+// over the front keeps the entries no survivor dominates and interleaves the
+// survivors (no survivor is dominated by the front: the expansion dropped those).
+// O(nc / 32 |S| / 32 + n / 32 + |S| log n / 32) warp steps instead of
+// O(nc / 32 n / 32).  Returns false, changing nothing, when the scratch is
+// used up; the caller then merges in chunks.
+template <class Load>
+__device__ bool merge_bulk(const WS& w, uint32_t q, FrontCursor& fc, WarpSmem& sm, uint32_t nc, Load load) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long T = 0;
+  if (lane == 0) T = atomicAdd(&w.ctl->tmp_n, 2ull * nc);
+  T = __shfl_sync(kFull, T, 0);
+  if (T + 2ull * nc > w.tcap) return false;
+  size_t A = T, B = T + nc;
+  uint32_t sn = 0;
+  for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
+    long long cc = 0, ch = 0;
+    uint32_t tb = 0, pp = 0;
+    bool ok = c0 + lane < nc && load(c0 + lane, cc, ch, tb, pp);
+    // 1. candidates dominated by the skyline so far (its last entry of cost <= cc)
+    if (ok && sn) {
+      uint32_t L = 0, R = sn;
+      while (L < R) {
+        const uint32_t mid = (L + R) >> 1;
+        if (w.t_cost[A + mid] <= cc) L = mid + 1; else R = mid;
+      }
+      if (L > 0) {
+        const long long sc = w.t_cost[A + L - 1], sh = w.t_h[A + L - 1];
+        if (sh <= ch && (sc < cc || sh < ch || w.t_tb[A + L - 1] < tb)) ok = false;
+      }
+    }
+    if (!__any_sync(kFull, ok)) continue;
+    // 2. skyline of the chunk (sorted, in sm.s_*)
+    const uint32_t m = chunk_skyline(sm, ok, cc, ch, tb, pp);
+    sm.bins[lane] = 0;
+    if (lane == 0) sm.bins[32] = 0;
+    __syncwarp();
+    // 3. S entries dominated by a chunk survivor drop out; the rest go to B at
+    //    (kept rank + chunk survivors before them)
+    uint32_t kept = 0;
+    for (uint32_t j0 = 0; j0 < sn; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      const bool valid = j < sn;
+      long long fcost = 0, fh = 0;
+      uint32_t fpp = 0, ftb = 0;
+      if (valid) {
+        fcost = w.t_cost[A + j];
+        fh = w.t_h[A + j];
+        fpp = w.t_pp[A + j];
+        ftb = w.t_tb[A + j];
+      }
+      uint32_t L = 0, R = m;
+      while (L < R) {
+        const uint32_t mid = (L + R) >> 1;
+        if (sm.s_cost[mid] <= fcost) L = mid + 1; else R = mid;
+      }
+      bool dom = false;
+      if (valid && L > 0) {
+        const long long scost = sm.s_cost[L - 1], sh = sm.s_h[L - 1];
+        dom = sh <= fh && (scost < fcost || sh < fh || sm.s_tb[L - 1] < ftb);
+      }
+      const bool keep = valid && !dom;
+      const unsigned kb = __ballot_sync(kFull, keep);
+      if (keep) {
+        const size_t pos = B + kept + __popc(kb & lt) + L;
+        w.t_cost[pos] = fcost;
+        w.t_h[pos] = fh;
+        w.t_pp[pos] = fpp;
+        w.t_tb[pos] = ftb;
+        atomicAdd(&sm.bins[L], 1u);
+      }
+      kept += __popc(kb);
+    }
+    __syncwarp();
+    const uint32_t before = warp_incl_scan(lane < m ? sm.bins[lane] : 0u);
+    if (lane < m) {
+      const size_t pos = B + lane + before;
+      w.t_cost[pos] = sm.s_cost[lane];
+      w.t_h[pos] = sm.s_h[lane];
+      w.t_pp[pos] = sm.s_pp[lane];
+      w.t_tb[pos] = sm.s_tb[lane];
+    }
+    __syncwarp();
+    const size_t t = A;
+    A = B;
+    B = t;
+    sn = kept + m;
+  }
+  if (sn == 0) return true;
+  const size_t o = fc.off;
+  const uint32_t n = fc.n;
+  // 4. insertion index of every survivor: front entries of lower or equal cost
+  for (uint32_t s0 = 0; s0 < sn; s0 += 32) {
+    const uint32_t s = s0 + lane;
+    if (s < sn) {
+      const long long sc = w.t_cost[A + s];
+      uint32_t L = 0, R = n;
+      while (L < R) {
+        const uint32_t mid = (L + R) >> 1;
+        if (w.f_cost[o + mid] <= sc) L = mid + 1; else R = mid;
+      }
+      w.t_m[A + s] = L;
+    }
+  }
+  if (!ensure_other(w, q, fc, n + sn)) return true;
+  __syncwarp();
+  // 5. one sweep over the front
+  const size_t on = fc.off2;
+  uint32_t K = 0, sp = 0, rem_open = 0;
+  for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    const bool valid = j < n;
+    long long fcost = 0, fh = 0;
+    uint32_t fpid = 0, faux = 0;
+    if (valid) {
+      fcost = w.f_cost[o + j];
+      fh = w.f_h[o + j];
+      fpid = w.f_pid[o + j];
+      faux = w.f_aux[o + j];
+    }
+    // survivors of lower or equal cost; the last of them alone can dominate (old plans win ties)
+    uint32_t lo = 0, hi = sn;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (w.t_cost[A + mid] <= fcost) lo = mid + 1; else hi = mid;
+    }
+    bool dom = false;
+    if (valid && lo > 0) {
+      const long long sc = w.t_cost[A + lo - 1], sh = w.t_h[A + lo - 1];
+      dom = sh <= fh && (sc < fcost || sh < fh);
+    }
+    const bool keep = valid && !dom;
+    if (dom && (fpid & kOpen)) rem_open++;
+    const unsigned kb = __ballot_sync(kFull, keep);
+    if (keep) {
+      const size_t pos = on + K + __popc(kb & lt) + lo;
+      w.f_cost[pos] = fcost;
+      w.f_h[pos] = fh;
+      w.f_pid[pos] = fpid;
+      w.f_aux[pos] = faux;
+    }
+    // survivors that go before a front entry of this chunk
+    const uint32_t jend = min(j0 + 32u, n);
+    for (;;) {
+      const uint32_t s = sp + lane;
+      bool emit = false;
+      uint32_t mm = 0;
+      if (s < sn) {
+        mm = w.t_m[A + s];
+        emit = mm < jend;
+      }
+      const unsigned eb = __ballot_sync(kFull, emit);
+      if (emit) {
+        const uint32_t d = mm - j0;   // 0 .. 31: earlier chunks emitted every index below j0
+        const size_t pos = on + s + K + __popc(kb & ((1u << d) - 1u));
+        w.f_cost[pos] = w.t_cost[A + s];
+        w.f_h[pos] = w.t_h[A + s];
+        w.f_pid[pos] = w.t_pp[A + s] | kNew;
+        w.f_aux[pos] = w.t_tb[A + s];
+      }
+      const uint32_t c = __popc(eb);
+      sp += c;
+      if (c < 32) break;
+    }
+    K += __popc(kb);
+  }
+  // survivors after every front entry
+  for (uint32_t s0 = sp; s0 < sn; s0 += 32) {
+    const uint32_t s = s0 + lane;
+    if (s < sn) {
+      const size_t pos = on + s + K;
+      w.f_cost[pos] = w.t_cost[A + s];
+      w.f_h[pos] = w.t_h[A + s];
+      w.f_pid[pos] = w.t_pp[A + s] | kNew;
+      w.f_aux[pos] = w.t_tb[A + s];
+    }
+  }
+  for (int sft = 16; sft > 0; sft >>= 1) rem_open += __shfl_xor_sync(kFull, rem_open, sft);
+  fc.removed_open += rem_open;
+  swap_blocks(fc);
+  fc.n = K + sn;
+  fc.reg = false;
+  fc.any_new = true;
+  __syncwarp();
+  return true;
+}
+
 // One node's merge with the whole warp (any front and candidate count).
 __device__ __forceinline__ void merge_node(const WS& w, WarpCtx& cx, WarpSmem& sm, const uint2 gq) {
   const unsigned lane = lane_id();
@@ -1421,7 +1623,10 @@ __device__ __forceinline__ void merge_node(const WS& w, WarpCtx& cx, WarpSmem& s
       if (lane >= fc.n && lane < fc.n + nc) load(lane - fc.n, cc, ch, tb, pp);
       merge_small(fc, sm, nc, cc, ch, tb, pp);
     } else {
-      for (uint32_t c0 = 0; c0 < nc && !fc.err; c0 += 32) {
+      // many candidates into a front that does not fit a warp: linear bulk merge
+      // (chunks of 32 against the whole front when its scratch is used up)
+      const bool bulk = nc > 32 && fc.n + nc > 64 && merge_bulk(w, q, fc, sm, nc, load);
+      for (uint32_t c0 = 0; !bulk && c0 < nc && !fc.err; c0 += 32) {
         const uint32_t i = c0 + lane;
         bool ok = false;
         long long cc = 0, ch = 0;
@@ -1782,6 +1987,7 @@ __device__ void epi_end(const WS& w) {
     c->grab[0] = 0;
     c->grab[1] = 0;
     c->ovl_n = 0;
+    c->tmp_n = 0;
     c->it = it + 1;
     c->waves += 1;
   }
@@ -2121,13 +2327,15 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
   w.acap = max_plans;
   w.gcap = max_plans;
   w.ocap = max_plans;
+  w.tcap = max_plans;
   w.path_cap = 4096;
   ws->max_q = max_q;
   const size_t slots = (size_t)w.pcap;
   bool ok = walloc(&w.f_cost, slots) && walloc(&w.f_h, slots) && walloc(&w.f_pid, slots) &&
             walloc(&w.f_aux, slots) && walloc(&w.fdesc, w.NV) && walloc(&w.slot, w.NV * kSlots) &&
             walloc(&w.cand_n, w.NV) && walloc(&w.ov, w.ocap) && walloc(&w.ov2, w.ocap) &&
-            walloc(&w.segoff, w.NV) && walloc(&w.ovl, w.NV) && walloc(&w.ov_pref, (size_t)max_q + 1) &&
+            walloc(&w.segoff, w.NV) && walloc(&w.t_cost, w.tcap) && walloc(&w.t_h, w.tcap) &&
+            walloc(&w.t_pp, w.tcap) && walloc(&w.t_tb, w.tcap) && walloc(&w.t_m, w.tcap) && walloc(&w.ovl, w.NV) && walloc(&w.ov_pref, (size_t)max_q + 1) &&
             walloc(&w.oh_stamp, w.NV) && walloc(&w.g_cost, w.gcap) &&
             walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) && walloc(&w.oh_list, 2 * w.NV) &&
             walloc(&w.m_list, w.NV) && walloc(&w.a_head, w.acap) && walloc(&w.a_parent, w.acap) &&
@@ -2145,7 +2353,7 @@ void workspace_free(mpap_workspace* ws) {
   if (!ws) return;
   WS& w = ws->w;
   void* ptrs[] = {w.f_cost, w.f_h,     w.f_pid,  w.f_aux,  w.fdesc,  w.slot,     w.cand_n, w.ov,
-                  w.ov2,    w.segoff,  w.ovl,    w.ov_pref, w.oh_stamp, w.g_cost, w.g_h,  w.g_pid,    w.oh_list, w.m_list,
+                  w.ov2,    w.segoff,  w.t_cost, w.t_h,    w.t_pp,   w.t_tb,    w.t_m,    w.ovl,    w.ov_pref, w.oh_stamp, w.g_cost, w.g_h,  w.g_pid,    w.oh_list, w.m_list,
                   w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl,    w.qd,       w.qs,     w.res,
                   w.path};
   for (void* p : ptrs) cudaFree(p);
@@ -2244,7 +2452,11 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
     return MPAP_ERR_INVALID_ARG;
   }
   // every query gets a share of the front pool, of the candidate overflow
-  // areas and of the plan arena in proportion to its nodes
+  // areas and of one half of the plan arena in proportion to its nodes; the
+  // arena's other half is common to the batch
+  const uint64_t a_shared = w.acap - w.acap / 2;
+  w.arena_common_base = a_shared;
+  w.arena_common_cap = w.acap / 2;
   {
     uint64_t acc = 0, acc_o = 0, acc_a = 0;
     for (uint32_t i = 0; i < nq; ++i) {
@@ -2252,7 +2464,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
       const double f = (double)qd[i].V / (double)total;
       const uint64_t cap = last ? w.pcap - acc : (uint64_t)((double)w.pcap * f);
       const uint64_t ocap = last ? w.ocap - acc_o : (uint64_t)((double)w.ocap * f);
-      const uint64_t acap = last ? w.acap - acc_a : (uint64_t)((double)w.acap * f);
+      const uint64_t acap = last ? a_shared - acc_a : (uint64_t)((double)a_shared * f);
       if (cap < 16 || acap < 1) {
         set_error("search: query %u's share of the front pool (below 16 entries) or of the plan arena is too small",
                   i);
