@@ -353,8 +353,9 @@ int32_t mpap_certify_noalloc(const mpap_roadmap* rm, const uint32_t* path, uint3
  * roadmap of a batch.  mpap_build_roadmaps reads edge_warps for each dimension
  * group of its batch; mpap_search / mpap_search_batch read the wavefront
  * kernel's blocks per SM and the group size from which its expansion runs its
- * lanes over a node's group plans instead of its out-edges.  Keys without an
- * entry use the defaults (8, 8, 8, 64).  The results of every call are
+ * lanes over a node's group plans instead of its out-edges, and the size from
+ * which a node's merge is spread over the whole grid.  Keys without an entry use
+ * the defaults (8, 8, 8, 64, 8192).  The results of every call are
  * identical for every valid shape; only the time changes.  The table is
  * process-wide and guarded by a mutex.
  * ------------------------------------------------------------------------- */
@@ -365,6 +366,8 @@ typedef struct {
   uint32_t plan_lanes_from;       /* group size from which the expansion puts its
                                      lanes on the group plans: 1 .. 64 */
   uint32_t front_cap;             /* advisory pool entries per node for mpap_workspace_create */
+  uint32_t grid_merge_from;       /* front + candidates of one node from which its merge
+                                     runs on every warp of the grid: 33 .. 2^30 */
 } mpap_tuning;
 
 /* The entry the library uses for (dim_kind, V): a stored one or the defaults. */

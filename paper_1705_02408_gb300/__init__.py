@@ -77,7 +77,8 @@ class mpap_mc_params(C.Structure):
 
 class mpap_tuning(C.Structure):
     _fields_ = [("edge_warps", C.c_uint32), ("wave_blocks_per_sm", C.c_uint32),
-                ("plan_lanes_from", C.c_uint32), ("front_cap", C.c_uint32)]
+                ("plan_lanes_from", C.c_uint32), ("front_cap", C.c_uint32),
+                ("grid_merge_from", C.c_uint32)]
 
 
 class mpap_cert(C.Structure):
@@ -1028,7 +1029,7 @@ def errmap_levels(map_state, map_val, dim_kind, grid_G, vel=(0.0, 0.0, 0.0), yaw
 # ---------------------------------------------------------------------------
 def _tuning_dict(t):
     return dict(edge_warps=t.edge_warps, wave_blocks_per_sm=t.wave_blocks_per_sm,
-                plan_lanes_from=t.plan_lanes_from, front_cap=t.front_cap)
+                plan_lanes_from=t.plan_lanes_from, front_cap=t.front_cap, grid_merge_from=t.grid_merge_from)
 
 
 def tuning_get(dim_kind, V):
@@ -1037,8 +1038,9 @@ def tuning_get(dim_kind, V):
     return _tuning_dict(t)
 
 
-def tuning_set(dim_kind, V, edge_warps=8, wave_blocks_per_sm=8, plan_lanes_from=8, front_cap=64):
-    t = mpap_tuning(edge_warps, wave_blocks_per_sm, plan_lanes_from, front_cap)
+def tuning_set(dim_kind, V, edge_warps=8, wave_blocks_per_sm=8, plan_lanes_from=8, front_cap=64,
+               grid_merge_from=8192):
+    t = mpap_tuning(edge_warps, wave_blocks_per_sm, plan_lanes_from, front_cap, grid_merge_from)
     _check(lib().mpap_tuning_set(int(dim_kind), int(V), C.byref(t)), "mpap_tuning_set")
 
 

@@ -51,6 +51,8 @@ namespace mpap {
 
 constexpr uint32_t kSlots = 64;          // inline candidate slots per node and wavefront
 constexpr uint32_t kDefaultWaitUs = 20000000;  // barrier wait limit when no query sets one
+constexpr uint32_t kHugeMax = 1024;       // grid-wide merges per wavefront (further nodes: one warp each)
+constexpr uint32_t kTile = 1024;          // cost buckets per warp tile of the grid-wide merge
 
 struct QueryDev {
   const uint32_t* fwd_ptr;
@@ -127,6 +129,7 @@ struct Ctl {
   uint32_t iter_cap;     // loop bound (max over queries of max_iters, plus 2)
   uint32_t max_front;    // largest front committed by any node
   uint32_t lanes_from;   // group size from which the expansion puts lanes on plans
+  uint32_t huge_from;    // front + candidates from which a node's merge is grid-wide
   uint32_t ov_any;       // some query overflowed its slots this wavefront
   // grid barrier
   uint32_t bar_count;
@@ -143,6 +146,27 @@ struct Ctl {
   uint32_t ov_total;     // overflow records of all queries this wavefront
   unsigned long long arena_common_n;   // records of the arena's common half handed out
   unsigned long long tmp_n;            // bulk-merge scratch entries handed out this wavefront
+  // grid-wide merges of huge nodes (this wavefront)
+  uint32_t hg_n;         // huge nodes handed to the grid-wide merge
+  uint32_t hg_live;      // the grid-wide merge runs before the end of this wavefront
+  uint32_t hg_nm;        // their members (front entries and candidates), flat
+  uint32_t hg_nt;        // their bucket tiles, flat
+  unsigned long long hg_ents;   // members reserved (bounds the flat index space)
+};
+
+// A node merged by the whole grid (see the grid-wide merge below).
+struct HugeDesc {
+  uint32_t g, q, n, nc;        // node, query, front entries, candidates
+  uint32_t off, so;            // live front block; regrouped overflow segment (kNone: none)
+  uint32_t lg_old;             // lg of the live block's size
+  uint32_t out, lg_out;        // block the merged front goes to, lg of its size (0: none yet)
+  uint32_t nb, shift;          // cost buckets (a power of two, at least kTile) and cost shift
+  uint32_t ent0, tile0;        // first flat member and tile index
+  uint32_t ok;                 // 0: skipped (its query failed for capacity)
+  unsigned long long mem;      // scratch: members [mem, mem + n + nc)
+  unsigned long long bkt;      //          buckets [bkt, bkt + nb)
+  long long lo, hi;            // cost range of the members
+  uint32_t n_out, n_new, removed_open, pad;
 };
 
 struct WS {
@@ -174,6 +198,7 @@ struct WS {
   uint32_t* g_pid;
   uint2* oh_list;          // [2][NV] {node, query} with open plans (this / next wavefront)
   uint2* m_list;           // [NV] {node, query} with candidates this wavefront
+  HugeDesc* hg;             // [kHugeMax] huge nodes of this wavefront
   uint32_t* a_head;
   uint32_t* a_parent;
   uint32_t* a_iter;
@@ -309,7 +334,8 @@ __device__ __forceinline__ void phase_mark(const WS& w, int k) {
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from, unsigned long long wait_ns) {
+__global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from, uint32_t huge_from,
+                       unsigned long long wait_ns) {
   const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q == 0) {
     Ctl& c = *w.ctl;
@@ -323,6 +349,7 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from
     c.iter_cap = iter_cap;
     c.max_front = 1;
     c.lanes_from = lanes_from;
+    c.huge_from = huge_from;
     c.ov_any = 0;
     c.bar_count = 0;
     c.bar_gen = 0;
@@ -338,6 +365,11 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from
     c.ov_total = 0;
     c.arena_common_n = 0;
     c.tmp_n = 0;
+    c.hg_n = 0;
+    c.hg_live = 0;
+    c.hg_nm = 0;
+    c.hg_nt = 0;
+    c.hg_ents = 0;
   }
   if (q >= nq) return;
   const QueryDev& Q = w.qd[q];
@@ -743,6 +775,7 @@ struct WarpCtx {
   uint32_t mb_n;      // nodes in this warp's merge-list buffer (warp-uniform)
   uint32_t nq;
   uint32_t it;
+  uint32_t huge_from;  // front + candidates from which a node's merge is grid-wide
 };
 
 __device__ __forceinline__ void acc_open(const WS& w, WarpCtx& cx, uint32_t q, long long v) {
@@ -1570,6 +1603,73 @@ __device__ bool merge_bulk(const WS& w, uint32_t q, FrontCursor& fc, WarpSmem& s
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Grid-wide merge of huge nodes (RemoveDominated for a node whose front and
+// candidates together hold at least ctl->huge_from entries, 8192 by default).  One warp would take time
+// linear in the front, or worse, and hold every other block at the next
+// barrier; instead every warp of the grid takes part.  The node's members
+// (front entries, tie key 0, and candidates) are bucketed by cost into nb
+// buckets of equal width.  A member is dominated by a member of a lower bucket
+// (strictly lower cost) iff the minimum h over all lower buckets is at most its
+// own, which an exclusive prefix minimum over the buckets gives; and by a member
+// of its own bucket iff one before it in the (cost, h, tie key) order has an h
+// at most its own.  Domination is transitive, so testing against every member,
+// dominated or not, is exact.  The survivors of each bucket are counted, and an
+// exclusive prefix sum over the buckets places them in the new front in cost
+// order.  Every step is a grid-stride loop over members or over tiles of kTile
+// buckets (a warp each); grid barriers separate the steps.
+// ---------------------------------------------------------------------------
+
+// Hands node g to this wavefront's grid-wide merge (warp-collective).  False,
+// with nothing changed that the caller relies on, when the merge has no room
+// left: the caller then merges the node itself.
+__device__ __forceinline__ bool defer_huge(const WS& w, uint32_t g, uint32_t q, const FrontCursor& fc,
+                                           uint32_t nc, uint32_t so) {
+  uint32_t ok = 0;
+  if (lane_id() == 0) {
+    const uint32_t N = fc.n + nc;
+    const uint32_t nb = max(kTile, 1u << ceil_lg(N));
+    Ctl* c = w.ctl;
+    uint32_t idx = kNone;
+    unsigned long long T = 0;
+    if (atomicAdd(&c->hg_ents, (unsigned long long)N) + N <= (1ull << 31)) {
+      T = atomicAdd(&c->tmp_n, (unsigned long long)N + nb);
+      if (T + N + nb <= w.tcap) {
+        idx = atomicAdd(&c->hg_n, 1u);
+        if (idx >= kHugeMax) idx = kNone;
+      }
+    }
+    if (idx != kNone) {
+      HugeDesc d;
+      d.g = g;
+      d.q = q;
+      d.n = fc.n;
+      d.nc = nc;
+      d.off = fc.off;
+      d.so = so;
+      d.lg_old = fc.lg;
+      d.out = fc.off2;      // the merged front goes to the node's other block, grown
+      d.lg_out = fc.lg2;    // once the survivors are counted if it is too small
+      d.ok = 1;
+      d.nb = nb;
+      d.shift = 0;
+      d.ent0 = 0;
+      d.tile0 = 0;
+      d.mem = T;
+      d.bkt = T + N;
+      d.lo = fc.n ? w.f_cost[fc.off] : LLONG_MAX;
+      d.hi = fc.n ? w.f_cost[(size_t)fc.off + fc.n - 1] : LLONG_MIN;
+      d.n_out = 0;
+      d.n_new = 0;
+      d.removed_open = 0;
+      d.pad = 0;
+      w.hg[idx] = d;
+      ok = 1;
+    }
+  }
+  return __shfl_sync(kFull, ok, 0) != 0;
+}
+
 // One node's merge with the whole warp (any front and candidate count).
 __device__ __forceinline__ void merge_node(const WS& w, WarpCtx& cx, WarpSmem& sm, const uint2 gq) {
   const unsigned lane = lane_id();
@@ -1591,6 +1691,8 @@ __device__ __forceinline__ void merge_node(const WS& w, WarpCtx& cx, WarpSmem& s
       fc.lg = fd.w & 0xFFu;
       fc.lg2 = (fd.w >> 8) & 0xFFu;
     }
+    // huge nodes are merged by the whole grid after this phase
+    if (nc && fc.n + nc >= cx.huge_from && fc.n + nc <= (1u << 30) && defer_huge(w, g, q, fc, nc, so)) return;
     fc.err = false;
     fc.removed_open = 0;
     fc.any_new = false;
@@ -1922,6 +2024,537 @@ __device__ void phase_merge(const WS& w, WarpCtx& cx, WarpSmem& sm) {
   flush_next(w, cx);
 }
 
+// Steps of the grid-wide merge (whole grid unless noted).
+constexpr uint32_t kSurv = 0x80000000u;   // survivor mark on a placed member's tie key
+
+__device__ __forceinline__ uint32_t gwarp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ uint32_t nwarps() { return (gridDim.x * blockDim.x) >> 5; }
+
+// The huge node holding flat member (tiles: tile) index x: the last one whose
+// first index is <= x (skipped nodes hold no index).
+__device__ __forceinline__ uint32_t huge_find(const WS& w, uint32_t nh, uint32_t x, bool tiles) {
+  uint32_t lo = 0, hi = nh;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((tiles ? w.hg[mid].tile0 : w.hg[mid].ent0) <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+struct Member {
+  long long c, h;
+  uint32_t p, tb;   // pid (front entries) or parent plan (candidates); tie key
+};
+
+// Member i of huge node d: front entry i (tie key 0: older than any candidate)
+// or candidate i - n; false when the candidate's record was lost to a full
+// overflow share (its query has failed).
+__device__ __forceinline__ bool huge_member(const WS& w, const HugeDesc& d, uint32_t i, Member& m) {
+  if (i < d.n) {
+    const size_t o = (size_t)d.off + i;
+    m.c = w.f_cost[o];
+    m.h = w.f_h[o];
+    m.p = w.f_pid[o];
+    m.tb = 0;
+    return true;
+  }
+  const uint32_t k = i - d.n;
+  const Cand* src;
+  if (k < kSlots) src = &w.slot[(size_t)d.g * kSlots + k];
+  else if (d.so != kNone) src = &w.ov2[(size_t)d.so + (k - kSlots)];
+  else return false;
+  const Cand cd = *src;
+  m.c = cd.cost;
+  m.h = cd.h;
+  m.p = cd.pp;
+  m.tb = cd.tb;
+  return true;
+}
+
+__device__ __forceinline__ size_t huge_bucket(const HugeDesc& d, long long c) {
+  return (size_t)d.bkt + (size_t)((unsigned long long)(c - d.lo) >> d.shift);
+}
+
+// Barrier after the merges, last block: flat member and tile numbering of the
+// huge nodes (serial: they are few).
+__device__ void huge_setup(const WS& w) {
+  if (threadIdx.x == 0) {
+    Ctl* c = w.ctl;
+    const uint32_t nh = min(c->hg_n, kHugeMax);
+    uint32_t m = 0, t = 0;
+    for (uint32_t k = 0; k < nh; ++k) {
+      HugeDesc& d = w.hg[k];
+      d.ent0 = m;
+      d.tile0 = t;
+      if (d.ok) {
+        m += d.n + d.nc;
+        t += d.nb / kTile;
+      }
+    }
+    c->hg_nm = m;
+    c->hg_nt = t;
+    c->hg_live = 1;
+  }
+}
+
+// 1. Cost range of the candidates (the front's is its first and last entry);
+//    bucket counters and cursors to 0, bucket minima to +infinity.
+__device__ void huge_range(const WS& w) {
+  const unsigned lane = lane_id();
+  const uint32_t nh = min(ld_vol(&w.ctl->hg_n), kHugeMax), nm = ld_vol(&w.ctl->hg_nm), nt = ld_vol(&w.ctl->hg_nt);
+  for (uint32_t b0 = gwarp() * 32u; b0 < nm; b0 += nwarps() * 32u) {
+    const uint32_t x = b0 + lane;
+    uint32_t k = kNone;
+    bool v = false;
+    long long c = 0;
+    if (x < nm) {
+      k = huge_find(w, nh, x, false);
+      const HugeDesc& d = w.hg[k];
+      const uint32_t i = x - d.ent0;
+      Member m;
+      if (i >= d.n && huge_member(w, d, i, m)) {
+        v = true;
+        c = m.c;
+      }
+    }
+    const uint32_t k0 = __shfl_sync(kFull, k, 0);
+    if (__all_sync(kFull, !v || k == k0)) {
+      long long mn = v ? c : LLONG_MAX, mx = v ? c : LLONG_MIN;
+      for (int s = 16; s > 0; s >>= 1) {
+        mn = min(mn, (long long)shfl_xor_i64(mn, s));
+        mx = max(mx, (long long)shfl_xor_i64(mx, s));
+      }
+      if (lane == 0 && mn <= mx) {
+        atomicMin(&w.hg[k0].lo, mn);
+        atomicMax(&w.hg[k0].hi, mx);
+      }
+    } else if (v) {
+      atomicMin(&w.hg[k].lo, c);
+      atomicMax(&w.hg[k].hi, c);
+    }
+  }
+  for (uint32_t t = gwarp(); t < nt; t += nwarps()) {
+    const HugeDesc& d = w.hg[huge_find(w, nh, t, true)];
+    const size_t b0 = d.bkt + (size_t)(t - d.tile0) * kTile;
+    for (uint32_t j = lane; j < kTile; j += 32) {
+      w.t_m[b0 + j] = 0;
+      w.t_tb[b0 + j] = 0;
+      w.t_cost[b0 + j] = LLONG_MAX;
+    }
+  }
+}
+
+// Last block: the cost shift that maps each node's range onto its nb buckets.
+__device__ void huge_shift(const WS& w) {
+  const uint32_t nh = min(w.ctl->hg_n, kHugeMax);
+  for (uint32_t k = threadIdx.x; k < nh; k += blockDim.x) {
+    HugeDesc& d = w.hg[k];
+    if (!d.ok || d.lo > d.hi) continue;
+    const unsigned long long range = (unsigned long long)(d.hi - d.lo);
+    uint32_t s = 0;
+    while ((range >> s) >= d.nb) ++s;
+    d.shift = s;
+  }
+}
+
+// 2. Members per bucket and each bucket's minimum h.
+__device__ void huge_count(const WS& w) {
+  const unsigned lane = lane_id();
+  const uint32_t nh = min(ld_vol(&w.ctl->hg_n), kHugeMax), nm = ld_vol(&w.ctl->hg_nm);
+  for (uint32_t b0 = gwarp() * 32u; b0 < nm; b0 += nwarps() * 32u) {
+    const uint32_t x = b0 + lane;
+    if (x >= nm) continue;
+    const HugeDesc& d = w.hg[huge_find(w, nh, x, false)];
+    Member m;
+    if (!huge_member(w, d, x - d.ent0, m)) continue;
+    const size_t b = huge_bucket(d, m.c);
+    atomicAdd(&w.t_m[b], 1u);
+    atomicMin(&w.t_cost[b], m.h);
+  }
+}
+
+// 3. Per tile (a warp each): its member count and minimum h, kept in the
+//    bucket area's h column (minima at [0, ntl), counts at [ntl, 2 ntl)).
+__device__ void huge_tile_agg(const WS& w) {
+  const unsigned lane = lane_id();
+  const uint32_t nh = min(ld_vol(&w.ctl->hg_n), kHugeMax), nt = ld_vol(&w.ctl->hg_nt);
+  for (uint32_t t = gwarp(); t < nt; t += nwarps()) {
+    const HugeDesc& d = w.hg[huge_find(w, nh, t, true)];
+    const uint32_t tl = t - d.tile0, ntl = d.nb / kTile;
+    const size_t b0 = d.bkt + (size_t)tl * kTile;
+    long long mn = LLONG_MAX;
+    uint32_t sum = 0;
+    for (uint32_t j = lane; j < kTile; j += 32) {
+      sum += w.t_m[b0 + j];
+      mn = min(mn, w.t_cost[b0 + j]);
+    }
+    for (int s = 16; s > 0; s >>= 1) {
+      sum += __shfl_xor_sync(kFull, sum, s);
+      mn = min(mn, (long long)shfl_xor_i64(mn, s));
+    }
+    if (lane == 0) {
+      w.t_h[d.bkt + tl] = mn;
+      w.t_h[d.bkt + ntl + tl] = (long long)sum;
+    }
+  }
+}
+
+// Exclusive scan (minimum, or sum) of a[0, n) in place by the whole block;
+// returns the total.
+template <bool kMin>
+__device__ long long block_scan_excl(long long* a, uint32_t n) {
+  __shared__ long long s_w[kWarpsPerBlock];
+  __shared__ long long s_carry;
+  const long long id = kMin ? LLONG_MAX : 0;
+  const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
+  __syncthreads();   // every thread has read the previous call's total
+  if (threadIdx.x == 0) s_carry = id;
+  __syncthreads();
+  for (uint32_t i0 = 0; i0 < n; i0 += blockDim.x) {
+    const uint32_t i = i0 + threadIdx.x;
+    long long x = i < n ? a[i] : id;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = shfl_up_i64(x, o);
+      if (lane >= (unsigned)o) x = kMin ? min(x, y) : x + y;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    long long pre = s_carry;
+    for (unsigned k = 0; k < wid; ++k) pre = kMin ? min(pre, s_w[k]) : pre + s_w[k];
+    long long ex = shfl_up_i64(x, 1);
+    if (lane == 0) ex = id;
+    if (i < n) a[i] = kMin ? min(pre, ex) : pre + ex;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = kMin ? min(pre, x) : pre + x;
+    __syncthreads();
+  }
+  return s_carry;
+}
+
+// Last block: exclusive prefixes over each node's tiles, of the minima and
+// counts (counts = true), or of the survivor counts, whose total is the size of
+// the merged front; its block is then grown if needed (a node whose query's
+// pool share is used up is skipped: the query fails).
+__device__ void huge_tile_scan(const WS& w, bool counts) {
+  const uint32_t nh = min(w.ctl->hg_n, kHugeMax);
+  for (uint32_t k = 0; k < nh; ++k) {
+    HugeDesc& d = w.hg[k];
+    if (!d.ok) continue;
+    const uint32_t ntl = d.nb / kTile;
+    if (counts) block_scan_excl<true>(w.t_h + d.bkt, ntl);
+    const long long tot = block_scan_excl<false>(w.t_h + d.bkt + ntl, ntl);
+    if (!counts && threadIdx.x == 0) {
+      d.n_out = (uint32_t)tot;
+      if (d.lg_out == 0 || (1u << d.lg_out) < d.n_out) {
+        d.lg_out = max(kMinLg, ceil_lg(d.n_out) + 1u);
+        d.out = pool_alloc(w, d.q, d.lg_out);
+        if (d.out == kNoBlock) {
+          query_error(w, d.q, kErrFront);
+          d.ok = 0;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// 4. Per tile: each bucket's first member slot (exclusive prefix of the counts)
+//    and the minimum h of all lower buckets (exclusive prefix minimum).
+__device__ void huge_bucket_scan(const WS& w) {
+  const unsigned lane = lane_id();
+  const uint32_t nh = min(ld_vol(&w.ctl->hg_n), kHugeMax), nt = ld_vol(&w.ctl->hg_nt);
+  for (uint32_t t = gwarp(); t < nt; t += nwarps()) {
+    const HugeDesc& d = w.hg[huge_find(w, nh, t, true)];
+    const uint32_t tl = t - d.tile0, ntl = d.nb / kTile;
+    const size_t b0 = d.bkt + (size_t)tl * kTile;
+    uint32_t cs = (uint32_t)w.t_h[d.bkt + ntl + tl];
+    long long cm = w.t_h[d.bkt + tl];
+    for (uint32_t j0 = 0; j0 < kTile; j0 += 32) {
+      const size_t b = b0 + j0 + lane;
+      const uint32_t cnt = w.t_m[b];
+      long long im = w.t_cost[b];
+      const uint32_t incl = warp_incl_scan(cnt);
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = shfl_up_i64(im, o);
+        if (lane >= (unsigned)o) im = min(im, y);
+      }
+      long long em = shfl_up_i64(im, 1);
+      if (lane == 0) em = LLONG_MAX;
+      w.t_m[b] = cs + incl - cnt;
+      w.t_cost[b] = min(cm, em);
+      cs += __shfl_sync(kFull, incl, 31);
+      cm = min(cm, (long long)shfl_i64(im, 31));
+    }
+  }
+}
+
+// 5. Members dominated through a lower bucket drop out (open front entries
+//    among them leave P_open); the rest are placed in their bucket's slots.
+__device__ void huge_place(const WS& w) {
+  const unsigned lane = lane_id();
+  const uint32_t nh = min(ld_vol(&w.ctl->hg_n), kHugeMax), nm = ld_vol(&w.ctl->hg_nm);
+  for (uint32_t b0 = gwarp() * 32u; b0 < nm; b0 += nwarps() * 32u) {
+    const uint32_t x = b0 + lane;
+    uint32_t k = kNone;
+    bool rem = false;
+    if (x < nm) {
+      k = huge_find(w, nh, x, false);
+      const HugeDesc& d = w.hg[k];
+      const uint32_t i = x - d.ent0;
+      Member m;
+      if (huge_member(w, d, i, m)) {
+        const size_t b = huge_bucket(d, m.c);
+        if (w.t_cost[b] <= m.h) {
+          rem = i < d.n && (m.p & kOpen);
+        } else {
+          const size_t pos = d.mem + w.t_m[b] + atomicAdd(&w.t_tb[b], 1u);
+          w.t_cost[pos] = m.c;
+          w.t_h[pos] = m.h;
+          w.t_pp[pos] = m.p;
+          w.t_tb[pos] = m.tb;
+        }
+      }
+    }
+    const uint32_t k0 = __shfl_sync(kFull, k, 0);
+    if (__all_sync(kFull, x >= nm || k == k0)) {
+      const uint32_t r = (uint32_t)__popc(__ballot_sync(kFull, rem));
+      if (lane == 0 && r) atomicAdd(&w.hg[k0].removed_open, r);
+    } else if (rem) {
+      atomicAdd(&w.hg[k].removed_open, 1u);
+    }
+  }
+}
+
+// Is placed member i of a bucket at s dominated by another of the same bucket?
+__device__ __forceinline__ bool bucket_dominated(const WS& w, size_t s, uint32_t k, uint32_t i, long long c,
+                                                 long long h, uint32_t tb) {
+  for (uint32_t j = 0; j < k; ++j) {
+    if (j == i) continue;
+    const long long hj = w.t_h[s + j];
+    if (hj > h) continue;
+    if (key_less(w.t_cost[s + j], hj, w.t_tb[s + j] & ~kSurv, c, h, tb)) return true;
+  }
+  return false;
+}
+
+// 6. Per tile: the survivors of each bucket (marked on their tie keys) and
+//    their count; open front entries dominated inside their bucket leave
+//    P_open.  Buckets of more than 32 members take the whole warp.
+__device__ void huge_resolve(const WS& w) {
+  const unsigned lane = lane_id();
+  const uint32_t nh = min(ld_vol(&w.ctl->hg_n), kHugeMax), nt = ld_vol(&w.ctl->hg_nt);
+  for (uint32_t t = gwarp(); t < nt; t += nwarps()) {
+    const uint32_t hk = huge_find(w, nh, t, true);
+    const HugeDesc& d = w.hg[hk];
+    const uint32_t tl = t - d.tile0, ntl = d.nb / kTile;
+    const size_t b0 = d.bkt + (size_t)tl * kTile;
+    uint32_t tile_sv = 0, tile_rem = 0;
+    for (uint32_t j0 = 0; j0 < kTile; j0 += 32) {
+      const size_t b = b0 + j0 + lane;
+      const uint32_t k = w.t_tb[b];
+      const size_t s = d.mem + w.t_m[b];
+      uint32_t sv = 0;
+      const bool big = k > 32;
+      if (!big) {
+        for (uint32_t i = 0; i < k; ++i) {
+          const long long c = w.t_cost[s + i], h = w.t_h[s + i];
+          const uint32_t tb = w.t_tb[s + i] & ~kSurv;
+          if (!bucket_dominated(w, s, k, i, c, h, tb)) {
+            w.t_tb[s + i] = tb | kSurv;
+            ++sv;
+          } else if (tb == 0 && (w.t_pp[s + i] & kOpen)) {
+            ++tile_rem;
+          }
+        }
+      }
+      for (unsigned bb = __ballot_sync(kFull, big); bb; bb &= bb - 1u) {
+        const int L = __ffs(bb) - 1;
+        const size_t sL = (size_t)__shfl_sync(kFull, (unsigned long long)s, L);
+        const uint32_t kL = __shfl_sync(kFull, k, L);
+        uint32_t cnt = 0;
+        for (uint32_t i0 = 0; i0 < kL; i0 += 32) {
+          const uint32_t i = i0 + lane;
+          bool keep = false;
+          uint32_t tb = 0;
+          if (i < kL) {
+            const long long c = w.t_cost[sL + i], h = w.t_h[sL + i];
+            tb = w.t_tb[sL + i] & ~kSurv;
+            keep = !bucket_dominated(w, sL, kL, i, c, h, tb);
+          }
+          __syncwarp();
+          if (keep) w.t_tb[sL + i] = tb | kSurv;
+          else if (i < kL && tb == 0 && (w.t_pp[sL + i] & kOpen)) ++tile_rem;
+          cnt += (uint32_t)__popc(__ballot_sync(kFull, keep));
+        }
+        if (lane == (unsigned)L) sv = cnt;
+      }
+      w.t_pp[b] = sv;
+      tile_sv += sv;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      tile_sv += __shfl_xor_sync(kFull, tile_sv, o);
+      tile_rem += __shfl_xor_sync(kFull, tile_rem, o);
+    }
+    if (lane == 0) {
+      w.t_h[d.bkt + ntl + tl] = (long long)tile_sv;
+      if (tile_rem) atomicAdd(&w.hg[hk].removed_open, tile_rem);
+    }
+  }
+}
+
+// Rank of survivor i among the survivors of its bucket (cost order: survivors
+// of one bucket have distinct costs).
+__device__ __forceinline__ uint32_t survivor_rank(const WS& w, size_t s, uint32_t k, long long c) {
+  uint32_t r = 0;
+  for (uint32_t j = 0; j < k; ++j)
+    if ((w.t_tb[s + j] & kSurv) && w.t_cost[s + j] < c) ++r;
+  return r;
+}
+
+// Writes one survivor to the merged front; a new plan gets arena record a
+// (kNone: none left) and is open.  Returns its pid.
+__device__ __forceinline__ uint32_t huge_emit(const WS& w, size_t pos, uint32_t x, uint32_t it, long long c,
+                                              long long h, uint32_t p, bool isnew, uint32_t a) {
+  uint32_t pid = p;
+  if (isnew) {
+    pid = kOpen;
+    if (a != kNone) {
+      w.a_head[a] = x;
+      w.a_parent[a] = p & kPidMask;
+      w.a_iter[a] = it + 1;
+      w.a_cost[a] = c;
+      pid = a | kOpen;
+    }
+  }
+  w.f_cost[pos] = c;
+  w.f_h[pos] = h;
+  w.f_pid[pos] = pid;
+  w.f_aux[pos] = 0;
+  return pid;
+}
+
+// 7. Per tile: survivors to their places in the merged front (exclusive prefix
+//    of the survivor counts; cost order inside a bucket), new plans to arena
+//    records (one range per 32 buckets), and the goal test of the next group.
+__device__ void huge_write(const WS& w) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t nh = min(ld_vol(&w.ctl->hg_n), kHugeMax), nt = ld_vol(&w.ctl->hg_nt), it = ld_vol(&w.ctl->it);
+  for (uint32_t t = gwarp(); t < nt; t += nwarps()) {
+    const uint32_t hk = huge_find(w, nh, t, true);
+    const HugeDesc& d = w.hg[hk];
+    if (!d.ok) continue;   // no block for the merged front: the query failed
+    const QueryDev& Q = w.qd[d.q];
+    const uint32_t x = d.g - Q.base;
+    const long long thr2 = (long long)(it + 1) * Q.Lambda;
+    const bool goal = Q.is_goal[x] != 0;
+    const uint32_t tl = t - d.tile0, ntl = d.nb / kTile;
+    const size_t b0 = d.bkt + (size_t)tl * kTile;
+    uint32_t carry = (uint32_t)w.t_h[d.bkt + ntl + tl];
+    uint32_t tile_new = 0;
+    bool gnext = false;
+    for (uint32_t j0 = 0; j0 < kTile; j0 += 32) {
+      const size_t b = b0 + j0 + lane;
+      const uint32_t k = w.t_tb[b];
+      const size_t s = d.mem + w.t_m[b];
+      const uint32_t sv = w.t_pp[b];
+      const uint32_t incl = warp_incl_scan(sv);
+      const uint32_t o0 = carry + incl - sv;
+      carry += __shfl_sync(kFull, incl, 31);
+      if (!__any_sync(kFull, sv != 0u)) continue;
+      // new survivors of this lane's bucket, then one arena range for the step
+      uint32_t nn = 0;
+      for (uint32_t i = 0; i < k; ++i) {
+        const uint32_t tb = w.t_tb[s + i];
+        if ((tb & kSurv) && (tb & ~kSurv)) ++nn;
+      }
+      const uint32_t nincl = warp_incl_scan(nn);
+      const uint32_t ntot = __shfl_sync(kFull, nincl, 31);
+      uint32_t a0 = kNone;
+      if (lane == 0 && ntot) a0 = arena_take(w, d.q, ntot);
+      a0 = __shfl_sync(kFull, a0, 0);
+      tile_new += ntot;
+      uint32_t an = nincl - nn;   // this bucket's first record within the range
+      const bool big = k > 32;
+      if (!big) {
+        for (uint32_t i = 0; i < k; ++i) {
+          const uint32_t tb = w.t_tb[s + i];
+          if (!(tb & kSurv)) continue;
+          const long long c = w.t_cost[s + i], h = w.t_h[s + i];
+          const bool isnew = (tb & ~kSurv) != 0;
+          const size_t pos = (size_t)d.out + o0 + survivor_rank(w, s, k, c);
+          const uint32_t pid = huge_emit(w, pos, x, it, c, h, w.t_pp[s + i], isnew,
+                                         (isnew && a0 != kNone) ? a0 + an : kNone);
+          if (isnew) ++an;
+          gnext = gnext || ((pid & kOpen) && c <= thr2);
+        }
+      }
+      for (unsigned bb = __ballot_sync(kFull, big); bb; bb &= bb - 1u) {
+        const int L = __ffs(bb) - 1;
+        const size_t sL = (size_t)__shfl_sync(kFull, (unsigned long long)s, L);
+        const uint32_t kL = __shfl_sync(kFull, k, L);
+        const uint32_t oL = __shfl_sync(kFull, o0, L);
+        uint32_t aL = __shfl_sync(kFull, an, L);
+        for (uint32_t i0 = 0; i0 < kL; i0 += 32) {
+          const uint32_t i = i0 + lane;
+          uint32_t tb = 0;
+          if (i < kL) tb = w.t_tb[sL + i];
+          const bool surv = (tb & kSurv) != 0;
+          const bool isnew = surv && (tb & ~kSurv) != 0;
+          const unsigned nb_ = __ballot_sync(kFull, isnew);
+          if (surv) {
+            const long long c = w.t_cost[sL + i], h = w.t_h[sL + i];
+            const size_t pos = (size_t)d.out + oL + survivor_rank(w, sL, kL, c);
+            const uint32_t pid = huge_emit(w, pos, x, it, c, h, w.t_pp[sL + i], isnew,
+                                           (isnew && a0 != kNone) ? a0 + aL + (uint32_t)__popc(nb_ & lt) : kNone);
+            gnext = gnext || ((pid & kOpen) && c <= thr2);
+          }
+          aL += (uint32_t)__popc(nb_);
+        }
+      }
+    }
+    if (lane == 0 && tile_new) atomicAdd(&w.hg[hk].n_new, tile_new);   // warp-uniform
+    // an open plan of the next group at a goal node ends the query at the top of
+    // the next iteration (the loop condition of Alg. 3)
+    if (goal && __any_sync(kFull, gnext) && lane == 0) w.qs[d.q].goal_next = 1u;
+  }
+}
+
+// Last block, after step 7: each node's new descriptor (the merged front is
+// live, the old block becomes the other), its query's counters and its place in
+// the next open list; then the grid-wide merge is closed for this wavefront.
+__device__ void huge_finish(const WS& w) {
+  Ctl* c = w.ctl;
+  const uint32_t nh = min(c->hg_n, kHugeMax), it = c->it;
+  for (uint32_t k = threadIdx.x; k < nh; k += blockDim.x) {
+    const HugeDesc& d = w.hg[k];
+    if (d.ok) {
+      FDesc fd;
+      fd.d = make_uint4(d.out, d.n_out, d.off, d.lg_out | (d.lg_old << 8));
+      const size_t l = (size_t)d.out + d.n_out - 1;
+      fd.last = d.n_out ? make_longlong2(w.f_cost[l], w.f_h[l]) : make_longlong2(0, 0);
+      w.fdesc[d.g] = fd;
+      atomic_add_i64(&w.qs[d.q].open_cnt, (long long)d.n_new - (long long)d.removed_open);
+      atomicAdd(&w.qs[d.q].plans, (unsigned long long)d.n_new);
+      atomicMax(&c->max_front, d.n_out);
+      if (d.n_new && w.oh_stamp[d.g] != it + 1) {
+        const uint32_t slot = atomicAdd(&c->oh_n[(it + 1) & 1], 1u);
+        w.oh_list[(size_t)((it + 1) & 1) * w.NV + slot] = make_uint2(d.g, d.q);
+      }
+    }
+    w.cand_n[d.g] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c->hg_n = 0;
+    c->hg_live = 0;
+    c->hg_nm = 0;
+    c->hg_nt = 0;
+    c->hg_ents = 0;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Work of the last block at the barriers.
 // ---------------------------------------------------------------------------
@@ -2013,6 +2646,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_wave(WS w) {
   cx.lb_n = 0;
   cx.mb_n = 0;
   cx.nq = nq;
+  cx.huge_from = w.ctl->huge_from;
   if (blockIdx.x == 0 && threadIdx.x == 0) w.ctl->t_mark = global_timer();
   for (;;) {
     const uint32_t it = ld_vol(&w.ctl->it);
@@ -2031,10 +2665,36 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_wave(WS w) {
     phase_merge(w, cx, sm);
     flush_acc(w, ws, nq);
     if (!grid_barrier(w, [&] {
-          phase_mark(w, 2);
-          epi_end(w);
+          if (ld_vol(&w.ctl->hg_n)) {
+            huge_setup(w);
+          } else {
+            phase_mark(w, 2);
+            epi_end(w);
+          }
         }))
       return;
+    if (ld_vol(&w.ctl->hg_live)) {
+      // grid-wide merge of the huge nodes, then the end of the wavefront
+      huge_range(w);
+      if (!grid_barrier(w, [&] { huge_shift(w); })) return;
+      huge_count(w);
+      if (!grid_barrier(w, [] {})) return;
+      huge_tile_agg(w);
+      if (!grid_barrier(w, [&] { huge_tile_scan(w, true); })) return;
+      huge_bucket_scan(w);
+      if (!grid_barrier(w, [] {})) return;
+      huge_place(w);
+      if (!grid_barrier(w, [] {})) return;
+      huge_resolve(w);
+      if (!grid_barrier(w, [&] { huge_tile_scan(w, false); })) return;
+      huge_write(w);
+      if (!grid_barrier(w, [&] {
+            huge_finish(w);
+            phase_mark(w, 2);
+            epi_end(w);
+          }))
+        return;
+    }
   }
 }
 
@@ -2339,7 +2999,7 @@ int32_t workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_
             walloc(&w.oh_stamp, w.NV) && walloc(&w.g_cost, w.gcap) &&
             walloc(&w.g_h, w.gcap) && walloc(&w.g_pid, w.gcap) && walloc(&w.oh_list, 2 * w.NV) &&
             walloc(&w.m_list, w.NV) && walloc(&w.a_head, w.acap) && walloc(&w.a_parent, w.acap) &&
-            walloc(&w.a_iter, w.acap) && walloc(&w.a_cost, w.acap) && walloc(&w.ctl, 1) && walloc(&w.qd, max_q) &&
+            walloc(&w.a_iter, w.acap) && walloc(&w.a_cost, w.acap) && walloc(&w.hg, kHugeMax) && walloc(&w.ctl, 1) && walloc(&w.qd, max_q) &&
             walloc(&w.qs, max_q) && walloc(&w.res, max_q) && walloc(&w.path, (size_t)max_q * w.path_cap);
   if (!ok) {
     workspace_free(ws);
@@ -2354,7 +3014,7 @@ void workspace_free(mpap_workspace* ws) {
   WS& w = ws->w;
   void* ptrs[] = {w.f_cost, w.f_h,     w.f_pid,  w.f_aux,  w.fdesc,  w.slot,     w.cand_n, w.ov,
                   w.ov2,    w.segoff,  w.t_cost, w.t_h,    w.t_pp,   w.t_tb,    w.t_m,    w.ovl,    w.ov_pref, w.oh_stamp, w.g_cost, w.g_h,  w.g_pid,    w.oh_list, w.m_list,
-                  w.a_head, w.a_parent, w.a_iter, w.a_cost, w.ctl,    w.qd,       w.qs,     w.res,
+                  w.a_head, w.a_parent, w.a_iter, w.a_cost, w.hg,     w.ctl,    w.qd,       w.qs,     w.res,
                   w.path};
   for (void* p : ptrs) cudaFree(p);
   if (ws->h_hdr) cudaFreeHost(ws->h_hdr);
@@ -2500,7 +3160,8 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   MPAP_CK(cudaMemsetAsync(w.oh_stamp, 0xFF, sizeof(uint32_t) * NVu, st));
   {
     LaunchScope ls(st, "k_init");
-    k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq, max_iters + 2u, tun.plan_lanes_from, wait_ns);
+    k_init<<<(nq + 127) / 128, 128, 0, st>>>(w, nq, max_iters + 2u, tun.plan_lanes_from, tun.grid_merge_from,
+                                             wait_ns);
     k_init_done<<<1, 256, 0, st>>>(w, nq);
   }
   MPAP_CK(cudaGetLastError());

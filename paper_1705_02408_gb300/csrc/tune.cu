@@ -33,12 +33,14 @@ mpap_tuning default_tuning() {
   t.wave_blocks_per_sm = 8;
   t.plan_lanes_from = 8;
   t.front_cap = 64;
+  t.grid_merge_from = 8192;
   return t;
 }
 
 bool tuning_valid(const mpap_tuning& t) {
   return (t.edge_warps == 4 || t.edge_warps == 8) && t.wave_blocks_per_sm >= 1 && t.wave_blocks_per_sm <= 64 &&
-         t.plan_lanes_from >= 1 && t.plan_lanes_from <= 64 && t.front_cap >= 1;
+         t.plan_lanes_from >= 1 && t.plan_lanes_from <= 64 && t.front_cap >= 1 &&
+         t.grid_merge_from >= 33 && t.grid_merge_from <= (1u << 30);
 }
 
 mpap_tuning tuning_for(int dim, uint32_t V) {
