@@ -346,6 +346,11 @@ NCU_TRAFFIC = {
     "k_edges": {"bytes_per_roadmap": (13.236736e6 + 90.364672e6) / 8,
                 "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "d62482682c7dcca7902214d7f5b830d779e07767",
                             "paper_1705_02408_gb300/csrc/common.cuh": "f42dfc54d3c1a7692a7b0b6e1943805b4fb67da4"}},
+    # one k_wave launch of the 8-query 6D-16k step: 169.29 MB read + 61.54 MB written
+    # for 12,658,585 plan-edge expansions (profiles/k_wave_6d16k_8queries.md)
+    "k_wave": {"bytes_per_expansion": (169.289216e6 + 61.544448e6) / 12658585.0,
+               "sources": {"paper_1705_02408_gb300/csrc/search.cu": "eb8d2718e6dbb92e69d6baa632fffd30080a7cc7",
+                           "paper_1705_02408_gb300/csrc/common.cuh": "f42dfc54d3c1a7692a7b0b6e1943805b4fb67da4"}},
 }
 
 
@@ -631,13 +636,17 @@ def refine_report(arm, eps=0.05, rounds=8):
 
 def mixed_report(args, stream, count=256):
     """The batched workload: 256 queries, each on its own roadmap (dimension
-    uniform over 2D/3D/6D; n log-uniform in [1000, 32000] for 3D/6D and [1000,
-    4000] for 2D), obstacles and grids seeded per query, beta from the stored
-    oracle calibration: built in one call, searched in one lock-step launch with
-    autotuned shapes and certified in one launch.  Every query owns a share of
-    the front pool in proportion to its nodes (1024 entries per node); the few
-    2D queries whose Pareto fronts outgrow it (single fronts above 10^5 plans)
-    end with a capacity status of their own, which the report counts."""
+    uniform over 2D/3D/6D, n log-uniform in [1000, 32000] for 3D/6D and [1000,
+    4000] for 2D), obstacles and grids
+    seeded per query, beta from the stored oracle calibration: built in one
+    call, searched in one lock-step launch with autotuned shapes and certified in
+    one launch.  The front pool holds 2048 entries per node of the batch, half of
+    it shared out among the queries in proportion to their nodes; every query
+    draws on its own share only (MPAP_QUERY_OWN_SHARE), so whether it runs out
+    does not depend on the rest of the batch, and the few 2D queries whose exact
+    Pareto fronts outgrow it (single fronts above 10^5 plans) end with a capacity
+    status of their own, which the report counts.  The plain arm searches the
+    queries that finished in the batch one call each."""
     import torch
     import paper_1705_02408_gb300 as mp
     calib = scenegen.load_calibration()
@@ -657,12 +666,12 @@ def mixed_report(args, stream, count=256):
     def run_group(name, idx, front_cap, tune, timed_reps, plain):
         grp = [scenes[i] for i in idx]
         specs = [mp.scene_spec(sc) for sc in grp]
-        queries = [mp.make_query(sc.extra["beta"], scenegen.LAMBDA) for sc in grp]
+        queries = [mp.make_query(sc.extra["beta"], scenegen.LAMBDA, own_share=True) for sc in grp]
         mcs = [(sc.cfg.mc_rollouts, sc.mc_seed, 0, sc.delta_fx, sc.sigma_fx, sc.shift) for sc in grp]
         total = sum(sc.cfg.n + 2 for sc in grp)
         t0 = time.perf_counter()
         log(f"mixed {name}: {len(grp)} queries, {total} nodes")
-        ws = mp.Workspace(total, front_cap=front_cap, max_plans=1 << 27)
+        ws = mp.Workspace(total, front_cap=front_cap, max_plans=1 << 29)
         tuning = None
         if tune:
             tb, build_ms, rms = mp.autotune_build(specs, reps=1)
@@ -704,27 +713,36 @@ def mixed_report(args, stream, count=256):
              "status": {str(k): int(v) for k, v in zip(*np.unique([r.status for r in res], return_counts=True))},
              "status_by_dim": by_dim,
              "max_wavefronts": max(r.wavefronts for r in res), "front_cap": front_cap, "tuning": tuning}
+        mf, pu = ws.stats()
+        g["max_front"], g["pool_entries_used"], g["pool_entries"] = mf, pu, total * front_cap
+        g["plans"] = int(sum(r.plans for r in res))
         if plain:
+            # the same set of queries both ways: those that finished in the batch
+            done = [i for i, r in enumerate(res) if r.status in (0, 1)]
+            sub_rms = [holder["rms"][i] for i in done]
+            sub_q = [queries[i] for i in done]
             e0.record(stream)
-            mp.search_batch(ws, holder["rms"], queries, check=False)
+            mp.search_batch(ws, sub_rms, sub_q, check=False)
             e1.record(stream)
             torch.cuda.synchronize()
             ms_b = e0.elapsed_time(e1)
-            ws1 = mp.Workspace(max(sc.cfg.n + 2 for sc in grp), front_cap=1024, max_plans=1 << 25)
+            vmax = max(grp[i].cfg.n + 2 for i in done)
+            ws1 = mp.Workspace(vmax, front_cap=min(16384, ((1 << 32) - 16) // vmax), max_plans=1 << 27)
             e0.record(stream)
-            for rm, q in zip(holder["rms"], queries):
+            for rm, q in zip(sub_rms, sub_q):
                 try:
                     mp.search(ws1, rm, q.beta, lam=scenegen.LAMBDA)
                 except mp.MpapError:
-                    pass            # a query out of its pool share: counted in the batched status
+                    pass            # the status is the batched one's (same fronts, same result)
             e1.record(stream)
             torch.cuda.synchronize()
             ms_p = e0.elapsed_time(e1)
-            g["search_only"] = {"batched_ms_per_query": ms_b / len(grp), "plain_ms_per_query": ms_p / len(grp),
-                                "speedup": ms_p / ms_b}
+            del ws1
+            g["search_only"] = {"queries": len(done), "batched_ms_per_query": ms_b / len(done),
+                                "plain_ms_per_query": ms_p / len(done), "speedup": ms_p / ms_b}
         return g
 
-    g = run_group("all", list(range(count)), 1024, True, 2, True)
+    g = run_group("all", list(range(count)), 2048, True, 2, True)
     out.update(g)
     return out
 

@@ -114,6 +114,10 @@ typedef struct {
  *               Eq. 2 for all t: a candidate is cut when the heuristic exceeds
  *               beta at any sub-step of its last edge (max(Cmax, h + Smax) >
  *               beta), not only at its head (Alg. 3).
+ *               bit 2 MPAP_QUERY_OWN_SHARE: the query draws only on its own
+ *               share of the front pool and of the plan arena, never on the
+ *               halves common to the batch, so whether it runs out of capacity
+ *               does not depend on the other queries of the call.
  *   wait_us     limit of one grid-barrier wait of the device wavefront loop, in
  *               microseconds of GPU timer time (0: 20 s).  A batch uses the
  *               smallest non-zero value of its queries.  A wait that runs out
@@ -121,6 +125,7 @@ typedef struct {
  *               the call returns it; the workspace stays usable. */
 #define MPAP_QUERY_NO_GOAL_STOP 1u
 #define MPAP_QUERY_CHECK_INTERIOR 2u
+#define MPAP_QUERY_OWN_SHARE 4u
 typedef struct {
   int64_t beta;
   int64_t group_width_q;
@@ -269,11 +274,11 @@ void mpap_roadmap_free(mpap_roadmap* rm);
  * entries (24 bytes each; the product must not exceed 2^32 - 16): every node
  * draws two blocks from it (its live front and a merge target), of 16 entries
  * and up, replaced by blocks twice the needed size as its front grows, so single
- * fronts may be far larger than front_cap as long as the pool lasts.  Each
- * query of a call gets its own share of the pool, in proportion to its nodes,
- * so a query that runs out of its share fails alone whatever the others do.  Half
- * of the plan arena (max_plans records) is shared out the same way; a query that
- * fills its share draws on the other half, which all queries of the call share.
+ * fronts may be far larger than front_cap as long as the pool lasts.  Half of
+ * the pool is shared out among the queries of a call in proportion to their
+ * nodes; a query that fills its share draws on the other half, which all
+ * queries of the call share (where a block lies changes no result).  Half of
+ * the plan arena (max_plans records) is shared out the same way.
  * A query that runs out of pool, of plan arena or of group array (max_plans)
  * ends with MPAP_ERR_CAPACITY in its own result; the other queries of the batch
  * run on.  Candidates of one wavefront wait in 64 slots of 32 bytes per node
@@ -283,6 +288,13 @@ void mpap_roadmap_free(mpap_roadmap* rm);
 int32_t mpap_workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t max_plans,
                               mpap_workspace** out);
 void mpap_workspace_free(mpap_workspace* ws);
+
+/* Sizes reached by the last search call on `ws` (the paper has no counterpart:
+ * this sizes workspaces): *max_front = the largest Pareto front any node held,
+ * *pool_used = front-pool entries handed out (blocks of every size, summed over
+ * the queries of the call and the pool's common half).  Either pointer may be
+ * NULL.  Host only; MPAP_ERR_INVALID_ARG for a NULL workspace. */
+int32_t mpap_workspace_stats(const mpap_workspace* ws, uint32_t* max_front, uint64_t* pool_used);
 
 /* Alg. 3 Explore for one query on one roadmap.  The whole group loop is one
  * persistent kernel (cooperative launch, grid barriers between the expansion
@@ -394,7 +406,7 @@ int32_t mpap_autotune_build(uint32_t n, const mpap_scene* scenes, const mpap_roa
  * untimed one.  Stores the fastest for the batch key and
  * sets best->front_cap to twice the front-pool entries per node the search
  * used, rounded up to a power of two (at least 16).  Queries that run out of
- * their pool share keep that status (it is part of the compared results).  Fails
+ * the pool keep that status (it is part of the compared results).  Fails
  * with MPAP_ERR_CUDA (and stores nothing) if two shapes give different results. */
 int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const mpap_query* qs,
                              uint32_t nq, uint32_t reps, mpap_tuning* best, double* best_ms,

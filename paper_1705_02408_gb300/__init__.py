@@ -27,6 +27,7 @@ MPAP_ERR_ITER_LIMIT, MPAP_ERR_CUDA, MPAP_ERR_SAMPLING = -4, -5, -6
 MPAP_MEM_HOST, MPAP_MEM_DEVICE = 0, 1
 MPAP_QUERY_NO_GOAL_STOP = 1
 MPAP_QUERY_CHECK_INTERIOR = 2
+MPAP_QUERY_OWN_SHARE = 4
 
 EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_build_roadmaps",
            "mpap_build_roadmap_from_points", "mpap_roadmap_from_csr", "mpap_roadmap_info",
@@ -42,7 +43,7 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_roadmap_update", "mpap_roadmap_update_batch", "mpap_refine_advance", "mpap_refine_batch",
            "mpap_surrogate_screen", "mpap_errnet_create", "mpap_errnet_free", "mpap_errnet_get_params",
            "mpap_errnet_set_params", "mpap_errnet_forward", "mpap_errnet_train_step", "mpap_errmap_query",
-           "mpap_errmap_levels"]
+           "mpap_errmap_levels", "mpap_workspace_stats"]
 
 
 class mpap_scene(C.Structure):
@@ -174,6 +175,8 @@ def lib():
         L.mpap_workspace_create.restype = i32
         L.mpap_workspace_create.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.POINTER(P)]
         L.mpap_workspace_free.argtypes = [P]
+        L.mpap_workspace_stats.restype = i32
+        L.mpap_workspace_stats.argtypes = [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]
         L.mpap_search.restype = i32
         L.mpap_search.argtypes = [P, P, C.POINTER(mpap_query), C.POINTER(mpap_result), P]
         L.mpap_search_batch.restype = i32
@@ -683,6 +686,12 @@ class Workspace:
             _lib.mpap_workspace_free(self.h)
             self.h = None
 
+    def stats(self):
+        """mpap_workspace_stats: (largest front, pool entries used) of the last search."""
+        mf = C.c_uint32(); pu = C.c_uint64()
+        _check(lib().mpap_workspace_stats(self.h, C.byref(mf), C.byref(pu)), "mpap_workspace_stats")
+        return mf.value, pu.value
+
     def fronts(self, index=0, stream=None):
         """Final (cost, h) fronts of query `index` of the last search: (ptr, cost, h)."""
         tot = C.c_uint64()
@@ -708,8 +717,10 @@ class SearchResult:
     plans: int
 
 
-def make_query(beta, lam=0.5, group_width_q=0, max_iters=100000, goal_stop=True, interior=False, wait_us=0):
-    flags = (0 if goal_stop else MPAP_QUERY_NO_GOAL_STOP) | (MPAP_QUERY_CHECK_INTERIOR if interior else 0)
+def make_query(beta, lam=0.5, group_width_q=0, max_iters=100000, goal_stop=True, interior=False, wait_us=0,
+               own_share=False):
+    flags = (0 if goal_stop else MPAP_QUERY_NO_GOAL_STOP) | (MPAP_QUERY_CHECK_INTERIOR if interior else 0) | \
+        (MPAP_QUERY_OWN_SHARE if own_share else 0)
     return mpap_query(beta=int(beta), group_width_q=int(group_width_q), lambda_=float(lam),
                       max_iters=int(max_iters), flags=flags, wait_us=int(wait_us))
 
@@ -1039,7 +1050,7 @@ def tuning_get(dim_kind, V):
 
 
 def tuning_set(dim_kind, V, edge_warps=8, wave_blocks_per_sm=8, plan_lanes_from=8, front_cap=64,
-               grid_merge_from=8192):
+               grid_merge_from=2048):
     t = mpap_tuning(edge_warps, wave_blocks_per_sm, plan_lanes_from, front_cap, grid_merge_from)
     _check(lib().mpap_tuning_set(int(dim_kind), int(V), C.byref(t)), "mpap_tuning_set")
 

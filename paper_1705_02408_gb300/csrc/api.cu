@@ -423,6 +423,16 @@ int32_t mpap_workspace_create(uint64_t total_nodes, uint32_t front_cap, uint64_t
 
 void mpap_workspace_free(mpap_workspace* ws) { mpap::workspace_free(ws); }
 
+int32_t mpap_workspace_stats(const mpap_workspace* ws, uint32_t* max_front, uint64_t* pool_used) {
+  if (!ws) {
+    set_error("mpap_workspace_stats: null workspace");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  if (max_front) *max_front = mpap::workspace_last_max_front(ws);
+  if (pool_used) *pool_used = mpap::workspace_last_pool_used(ws);
+  return MPAP_OK;
+}
+
 int32_t mpap_search(mpap_workspace* ws, mpap_roadmap* rm, const mpap_query* q, mpap_result* out, void* stream) {
   if (!ws || !rm || !q || !out) {
     set_error("null argument");

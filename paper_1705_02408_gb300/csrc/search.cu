@@ -51,7 +51,7 @@ namespace mpap {
 
 constexpr uint32_t kSlots = 64;          // inline candidate slots per node and wavefront
 constexpr uint32_t kDefaultWaitUs = 20000000;  // barrier wait limit when no query sets one
-constexpr uint32_t kHugeMax = 1024;       // grid-wide merges per wavefront (further nodes: one warp each)
+constexpr uint32_t kHugeMax = 8192;       // grid-wide merges per wavefront (further nodes: one warp each)
 constexpr uint32_t kTile = 1024;          // cost buckets per warp tile of the grid-wide merge
 
 struct QueryDev {
@@ -145,6 +145,7 @@ struct Ctl {
   uint32_t ovl_n;        // nodes with overflow records this wavefront
   uint32_t ov_total;     // overflow records of all queries this wavefront
   unsigned long long arena_common_n;   // records of the arena's common half handed out
+  unsigned long long pool_common_n;    // entries of the front pool's common half handed out
   unsigned long long tmp_n;            // bulk-merge scratch entries handed out this wavefront
   // grid-wide merges of huge nodes (this wavefront)
   uint32_t hg_n;         // huge nodes handed to the grid-wide merge
@@ -175,6 +176,7 @@ struct WS {
   uint64_t pcap;           // front pool entries
   uint64_t acap, gcap, ocap, tcap;
   uint64_t arena_common_base, arena_common_cap;   // the arena's half that all queries share
+  uint64_t pool_common_base, pool_common_cap;     // the front pool's half that all queries share
   long long* f_cost;       // [pcap] front pool
   long long* f_h;
   uint32_t* f_pid;
@@ -250,14 +252,19 @@ __device__ __forceinline__ uint32_t ceil_lg(uint32_t n) {
   return n <= 1 ? 0u : 32u - (uint32_t)__clz(n - 1u);
 }
 
-// One block of 2^lg entries of query q's pool share (call from one lane);
-// kNoBlock when the share is used up.  Shares are disjoint, so a query that
-// runs out fails alone, whatever the others do.
+// One block of 2^lg entries for query q (call from one lane): from the query's
+// own pool share while it lasts, then from the pool's common half, which every
+// query of the batch draws on (a query whose fronts outgrow its share borrows
+// what the others leave); kNoBlock when both are used up.  Where a block lies
+// does not change any result.
 __device__ __forceinline__ uint32_t pool_alloc(const WS& w, uint32_t q, uint32_t lg) {
   const unsigned long long sz = 1ull << lg;
   const unsigned long long o = atomicAdd(&w.qs[q].pool_n, sz);
   const QueryDev& Q = w.qd[q];
-  return (o + sz <= Q.pool_cap) ? (uint32_t)(Q.pool_base + o) : kNoBlock;
+  if (o + sz <= Q.pool_cap) return (uint32_t)(Q.pool_base + o);
+  if (Q.flags & MPAP_QUERY_OWN_SHARE) return kNoBlock;
+  const unsigned long long c = atomicAdd(&w.ctl->pool_common_n, sz);
+  return (c + sz <= w.pool_common_cap) ? (uint32_t)(w.pool_common_base + c) : kNoBlock;
 }
 
 // Records a capacity error of query q (it ends at the end of the wavefront).
@@ -364,6 +371,7 @@ __global__ void k_init(WS w, uint32_t nq, uint32_t iter_cap, uint32_t lanes_from
     c.ovl_n = 0;
     c.ov_total = 0;
     c.arena_common_n = 0;
+    c.pool_common_n = 0;
     c.tmp_n = 0;
     c.hg_n = 0;
     c.hg_live = 0;
@@ -748,6 +756,10 @@ __device__ __forceinline__ uint32_t arena_take(const WS& w, uint32_t q, uint32_t
   const unsigned long long o = atomicAdd(&w.qs[q].arena_n, (unsigned long long)r);
   const QueryDev& Q = w.qd[q];
   if (o + r <= Q.arena_cap) return (uint32_t)(Q.arena_base + o);
+  if (Q.flags & MPAP_QUERY_OWN_SHARE) {
+    query_error(w, q, kErrArena);
+    return kNone;
+  }
   const unsigned long long c = atomicAdd(&w.ctl->arena_common_n, (unsigned long long)r);
   if (c + r <= w.arena_common_cap) return (uint32_t)(w.arena_common_base + c);
   query_error(w, q, kErrArena);
@@ -1153,16 +1165,18 @@ __device__ void phase_expand(const WS& w, WarpCtx& cx, GroupSmem& gs) {
   const uint32_t lanes_from = w.ctl->lanes_from;
   const uint2* list = w.oh_list + (size_t)(it & 1) * w.NV;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t chunk = grab_chunk(n_list, warps);
+  const uint32_t chunk = max(grab_chunk(n_list, warps), n_list / (warps * 4u));
   for (uint32_t k0 = grab(&w.ctl->grab[0], chunk); k0 < n_list; k0 = grab(&w.ctl->grab[0], chunk))
   for (uint32_t k = k0; k < min(k0 + chunk, n_list); ++k) {
     const uint2 gq = list[k];
     const uint32_t g = gq.x, q = gq.y;
-    if (w.qs[q].done) continue;
+    // the node's loads go out together, before the test of its query's state
     const QueryDev& Q = w.qd[q];
+    const uint4 fd = w.fdesc[g].d;
+    const uint32_t q_done = w.qs[q].done;
     const uint32_t u = g - Q.base;
     const uint32_t e_beg = __ldg(&Q.fwd_ptr[u]), e_end = __ldg(&Q.fwd_ptr[u + 1]);
-    const uint4 fd = w.fdesc[g].d;
+    if (q_done) continue;
     const uint32_t n = fd.y;
     const size_t o = fd.x;
     const long long thr = (long long)it * Q.Lambda, thr2 = thr + Q.Lambda;
@@ -1605,7 +1619,7 @@ __device__ bool merge_bulk(const WS& w, uint32_t q, FrontCursor& fc, WarpSmem& s
 
 // ---------------------------------------------------------------------------
 // Grid-wide merge of huge nodes (RemoveDominated for a node whose front and
-// candidates together hold at least ctl->huge_from entries, 8192 by default).  One warp would take time
+// candidates together hold at least ctl->huge_from entries, 2048 by default).  One warp would take time
 // linear in the front, or worse, and hold every other block at the next
 // barrier; instead every warp of the grid takes part.  The node's members
 // (front entries, tie key 0, and candidates) are bucketed by cost into nb
@@ -2075,25 +2089,51 @@ __device__ __forceinline__ size_t huge_bucket(const HugeDesc& d, long long c) {
   return (size_t)d.bkt + (size_t)((unsigned long long)(c - d.lo) >> d.shift);
 }
 
-// Barrier after the merges, last block: flat member and tile numbering of the
-// huge nodes (serial: they are few).
+// Barrier after the merges, last block (all its threads): flat member and tile
+// numbering of the huge nodes, an exclusive prefix sum over them (each thread
+// sums a contiguous run of nodes, the runs' totals are scanned in order).
 __device__ void huge_setup(const WS& w) {
-  if (threadIdx.x == 0) {
-    Ctl* c = w.ctl;
-    const uint32_t nh = min(c->hg_n, kHugeMax);
-    uint32_t m = 0, t = 0;
-    for (uint32_t k = 0; k < nh; ++k) {
-      HugeDesc& d = w.hg[k];
-      d.ent0 = m;
-      d.tile0 = t;
-      if (d.ok) {
-        m += d.n + d.nc;
-        t += d.nb / kTile;
-      }
+  __shared__ uint32_t s_m[kWarpsPerBlock * 32], s_t[kWarpsPerBlock * 32];
+  Ctl* c = w.ctl;
+  const uint32_t nh = min(c->hg_n, kHugeMax);
+  const uint32_t nt_ = blockDim.x;
+  const uint32_t per = (nh + nt_ - 1) / nt_;
+  const uint32_t k0 = min(nh, threadIdx.x * per), k1 = min(nh, k0 + per);
+  uint32_t m = 0, t = 0;
+  for (uint32_t k = k0; k < k1; ++k) {
+    const HugeDesc& d = w.hg[k];
+    if (d.ok) {
+      m += d.n + d.nc;
+      t += d.nb / kTile;
     }
-    c->hg_nm = m;
-    c->hg_nt = t;
+  }
+  s_m[threadIdx.x] = m;
+  s_t[threadIdx.x] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t am = 0, at = 0;
+    for (uint32_t i = 0; i < nt_; ++i) {
+      const uint32_t a = s_m[i], b = s_t[i];
+      s_m[i] = am;
+      s_t[i] = at;
+      am += a;
+      at += b;
+    }
+    c->hg_nm = am;
+    c->hg_nt = at;
     c->hg_live = 1;
+  }
+  __syncthreads();
+  m = s_m[threadIdx.x];
+  t = s_t[threadIdx.x];
+  for (uint32_t k = k0; k < k1; ++k) {
+    HugeDesc& d = w.hg[k];
+    d.ent0 = m;
+    d.tile0 = t;
+    if (d.ok) {
+      m += d.n + d.nc;
+      t += d.nb / kTile;
+    }
   }
 }
 
@@ -3111,18 +3151,21 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
               (unsigned long long)w.NV);
     return MPAP_ERR_INVALID_ARG;
   }
-  // every query gets a share of the front pool, of the candidate overflow
-  // areas and of one half of the plan arena in proportion to its nodes; the
-  // arena's other half is common to the batch
+  // every query gets a share of the candidate overflow areas, of one half of
+  // the front pool and of one half of the plan arena in proportion to its
+  // nodes; the other halves of the pool and the arena are common to the batch
   const uint64_t a_shared = w.acap - w.acap / 2;
   w.arena_common_base = a_shared;
   w.arena_common_cap = w.acap / 2;
+  const uint64_t p_shared = w.pcap - w.pcap / 2;
+  w.pool_common_base = p_shared;
+  w.pool_common_cap = w.pcap / 2;
   {
     uint64_t acc = 0, acc_o = 0, acc_a = 0;
     for (uint32_t i = 0; i < nq; ++i) {
       const bool last = i + 1 == nq;
       const double f = (double)qd[i].V / (double)total;
-      const uint64_t cap = last ? w.pcap - acc : (uint64_t)((double)w.pcap * f);
+      const uint64_t cap = last ? p_shared - acc : (uint64_t)((double)p_shared * f);
       const uint64_t ocap = last ? w.ocap - acc_o : (uint64_t)((double)w.ocap * f);
       const uint64_t acap = last ? a_shared - acc_a : (uint64_t)((double)a_shared * f);
       if (cap < 16 || acap < 1) {
@@ -3233,6 +3276,7 @@ int32_t search_batch_impl(mpap_workspace* ws, mpap_roadmap* const* rms, const mp
   {
     unsigned long long used = 0;
     for (uint32_t i = 0; i < nq; ++i) used += std::min<unsigned long long>(qsh[i].pool_n, qd[i].pool_cap);
+    used += std::min<unsigned long long>(hc.pool_common_n, w.pool_common_cap);
     ws->last_pool_used = used;
   }
   if (hc.timeout) {

@@ -33,7 +33,7 @@ mpap_tuning default_tuning() {
   t.wave_blocks_per_sm = 8;
   t.plan_lanes_from = 8;
   t.front_cap = 64;
-  t.grid_merge_from = 8192;
+  t.grid_merge_from = 2048;
   return t;
 }
 

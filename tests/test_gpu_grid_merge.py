@@ -4,7 +4,7 @@ exclusive prefix minimum of h over the buckets, exact resolution inside each
 bucket, an exclusive prefix sum placing the survivors) against the oracle and
 against the one-warp merge.  With the threshold lowered to 33 entries nearly
 every merge of the parity cases runs grid-wide; on 2D queries whose single
-fronts pass 10^4 plans the default threshold (8192) takes it, and the results
+fronts pass 10^4 plans a threshold of 8192 takes it, and the results
 equal those with the grid-wide merge switched off.  Fronts, solutions and
 counters bit-exact."""
 import numpy as np

@@ -177,9 +177,10 @@ def test_query_error_stays_with_its_query(mp, orc):
 
 
 def test_pool_share_exhaustion_stays_with_its_query(mp, orc):
-    """Every query of a batch owns a share of the front pool in proportion to its
-    nodes: a 2D query whose fronts outgrow its share fails, deterministically and
-    alone, and the 6D query beside it is still exact."""
+    """Every query of a batch owns a share of half the front pool in proportion
+    to its nodes, and may borrow from the other half: a 2D query whose fronts
+    outgrow both fails, and the 6D query beside it (within its share) is still
+    exact."""
     s2 = scenegen.make_scene("2d", 2, query_id=2)
     s6 = scenegen.make_scene("6d", 3, query_id=3)
     r2 = mp.build_roadmap_for_scene(s2)
@@ -193,6 +194,50 @@ def test_pool_share_exhaustion_stays_with_its_query(mp, orc):
         res = mp.search_batch(wsb, [r2, r6], qs, check=False)
         assert res[0].status == mp.MPAP_ERR_CAPACITY
         assert_same_search(res[1], orc.explore(o6, b6, orc.group_width(0.5, 18.0)), wsb, index=1)
+
+
+def test_pool_common_half_and_own_share(mp, orc):
+    """Half of the front pool is shared out among the queries of a batch in
+    proportion to their nodes and half is common to the batch: a query whose
+    fronts outgrow its share borrows from the common half, and its result (and
+    every front) equals that of a run on its own.  With MPAP_QUERY_OWN_SHARE the
+    same query ends with a capacity status instead, and the query beside it is
+    exact either way."""
+    cfg = scenegen.scaled_config(scenegen.DIM_2D, 1000)
+    sb = scenegen.make_scene(cfg, 2, query_id=2)     # fronts of hundreds of plans
+    ss = scenegen.make_scene(cfg, 1, query_id=1)
+    rb, rs = mp.build_roadmaps([mp.scene_spec(sb), mp.scene_spec(ss)])
+    bb = orc.beta_percentile(orc.build_roadmap(sb))
+    bs = orc.beta_percentile(orc.build_roadmap(ss))
+    big = mp.Workspace(rb.V, front_cap=4096, max_plans=1 << 24)
+    ref_b = mp.search(big, rb, bb, lam=0.5)
+    fr_b = big.fronts(0)
+    used_b = big.stats()[1]
+    ref_s = mp.search(big, rs, bs, lam=0.5)
+    fr_s = big.fronts(0)
+    total = rb.V + rs.V
+    fc = -(-2 * used_b // total)           # pool ~ 2x what the big query uses alone
+    assert (fc * total // 2) * rb.V // total < used_b     # its share alone is too small
+    wsb = mp.Workspace(total, front_cap=fc, max_plans=1 << 24)
+
+    def same(a, b, fr, index):
+        assert (a.status, a.cost, a.h, a.wavefronts, a.expansions, a.plans) == \
+            (b.status, b.cost, b.h, b.wavefronts, b.expansions, b.plans)
+        np.testing.assert_array_equal(a.path, b.path)
+        ptr, cost, h = wsb.fronts(index)
+        V = rb.V
+        np.testing.assert_array_equal(ptr[:V + 1], fr[0][:V + 1])
+        np.testing.assert_array_equal(cost, fr[1])
+        np.testing.assert_array_equal(h, fr[2])
+
+    res = mp.search_batch(wsb, [rb, rs], [mp.make_query(bb, 0.5), mp.make_query(bs, 0.5)], check=False)
+    assert res[0].status == 0
+    same(res[0], ref_b, fr_b, 0)
+    same(res[1], ref_s, fr_s, 1)
+    res = mp.search_batch(wsb, [rb, rs], [mp.make_query(bb, 0.5, own_share=True), mp.make_query(bs, 0.5)],
+                          check=False)
+    assert res[0].status == mp.MPAP_ERR_CAPACITY
+    same(res[1], ref_s, fr_s, 1)
 
 
 def test_barrier_timeout_is_reported(mp, orc, ws):

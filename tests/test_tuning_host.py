@@ -12,14 +12,14 @@ def mp():
     m.tuning_clear()
 
 
-DEFAULT = dict(edge_warps=8, wave_blocks_per_sm=8, plan_lanes_from=8, front_cap=64, grid_merge_from=8192)
+DEFAULT = dict(edge_warps=8, wave_blocks_per_sm=8, plan_lanes_from=8, front_cap=64, grid_merge_from=2048)
 
 
 def test_defaults_and_buckets(mp):
     mp.tuning_clear()
     assert mp.tuning_get(6, 16002) == DEFAULT
     mp.tuning_set(6, 16002, edge_warps=4, wave_blocks_per_sm=2, plan_lanes_from=8, front_cap=128)
-    want = dict(edge_warps=4, wave_blocks_per_sm=2, plan_lanes_from=8, front_cap=128, grid_merge_from=8192)
+    want = dict(edge_warps=4, wave_blocks_per_sm=2, plan_lanes_from=8, front_cap=128, grid_merge_from=2048)
     # the key is (dimension, floor(log2 V)): 8192 <= V < 16384 share bucket 13
     assert mp.tuning_get(6, 8192) == want and mp.tuning_get(6, 16383) == want
     assert mp.tuning_get(6, 16384) == DEFAULT and mp.tuning_get(6, 8191) == DEFAULT
