@@ -568,36 +568,50 @@ def errnet_report(arm, n_train=200000, steps=400, batch=8192, n_map=20000):
     return out
 
 
-def update_report(arm, k=3):
-    """Online update (mpap_roadmap_update_batch) of the benchmark's roadmaps: k
-    added boxes each and a replaced quality grid, in one call, against rebuilding
-    all of them in one batched build; CUDA events around each."""
+def update_report(arm, k=3, side=0.3):
+    """Online update (mpap_roadmap_update_batch) of the benchmark's roadmaps in one
+    call, against rebuilding all of them in one batched build; CUDA events around
+    each.  Two map changes: k added boxes each with the levels of the cells inside
+    one cube of the given side replaced (new features mapped there: only the edges
+    near the boxes and that cube are re-tested and re-transferred), and k added
+    boxes with an entirely new grid (every edge is re-transferred)."""
     import torch
-    rms = arm.build()
     rng = np.random.default_rng(7)
-    adds = []
-    for _ in rms:
+    G = arm.cfg.grid_G
+    cen = (np.arange(G) + 0.5) / G
+    adds, local, fresh = [], [], []
+    for s in arm.scenes:
         c = rng.uniform(0.2, 0.8, (k, 3)); sz = rng.uniform(0.04, 0.12, (k, 3))
         adds.append(((c - sz / 2).astype(np.float32), (c + sz / 2).astype(np.float32)))
-    grids = [scenegen.make_scene(arm.cfg, s.seed + 1000).grid for s in arm.scenes]
-    E0 = sum(rm.E for rm in rms)
-    torch.cuda.synchronize()
+        other = scenegen.make_scene(arm.cfg, s.seed + 1000).grid
+        lo = rng.uniform(0.0, 1.0 - side, 3)
+        ins = [(cen >= lo[i]) & (cen < lo[i] + side) for i in range(3)]
+        m = (ins[2][:, None, None] & ins[1][None, :, None] & ins[0][None, None, :]).ravel()
+        g = s.grid.copy()
+        g[m] = other[m]
+        local.append(g)
+        fresh.append(other)
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    arm.mp.roadmap_update_batch(rms, [a[0] for a in adds], [a[1] for a in adds], grids)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_update = e0.elapsed_time(e1)
-    E1 = sum(rm.E for rm in rms)
+    out = {"workload": f"{len(arm.scenes)} roadmaps of {arm.cfg.n + 2} nodes, one batched update call"}
+    for name, grids in (("boxes_and_local_grid", local), ("boxes_and_new_grid", fresh)):
+        rms = arm.build()
+        E0 = sum(rm.E for rm in rms)
+        torch.cuda.synchronize()
+        e0.record()
+        arm.mp.roadmap_update_batch(rms, [a[0] for a in adds], [a[1] for a in adds], grids)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_update = e0.elapsed_time(e1)
+        E1 = sum(rm.E for rm in rms)
+        out[name] = {"change": f"{k} added boxes each and " + (f"the cells inside one cube of side {side} given "
+                                                                 "new levels" if grids is local else "a new grid"),
+                     "ms_per_roadmap_update": ms_update / len(rms), "edges_before": E0, "edges_after": E1}
     e0.record()
     arm.build()
     e1.record()
     torch.cuda.synchronize()
-    ms_build = e0.elapsed_time(e1)
-    return {"workload": f"{len(rms)} roadmaps of {arm.cfg.n + 2} nodes, {k} added boxes each and a new grid, "
-                        "one batched update call",
-            "ms_per_roadmap_update": ms_update / len(rms), "ms_per_roadmap_rebuild": ms_build / len(rms),
-            "edges_before": E0, "edges_after": E1}
+    out["ms_per_roadmap_rebuild"] = e0.elapsed_time(e1) / len(arm.scenes)
+    return out
 
 
 def refine_report(arm, eps=0.05, rounds=8):

@@ -240,10 +240,14 @@ int32_t mpap_roadmap_export_reverse(const mpap_roadmap* rm, uint32_t* rev_ptr, u
 /* Online update of a built roadmap (the map changes, the nodes stay; Sec. 3 on
  * use within a mapping framework): nb_add boxes float[nb_add][3] are appended to
  * the roadmap's obstacles and, when grid is not NULL, its quality levels
- * uint8[G^Dp] are replaced.  Every edge is tested against the added boxes only
- * (an added box can only remove edges) and the transfers and their peaks are
- * recomputed only when the grid changed; the forward and reverse CSR are then
- * compacted.  The roadmap afterwards is the one mpap_build_roadmap_from_points
+ * uint8[G^Dp] are replaced.  An added box can only remove edges, so an edge is
+ * tested against the added boxes only, and only when a conservative box around
+ * its checkpoints (2D/3D: the segment's bounding box; 6D: the segment from p0 to
+ * p0 + v0 T grown by sqrt(T^3 J / 3), J = cost - T, which bounds the connection's
+ * deviation from it) meets one of them; its transfer and peaks are recomputed
+ * only when that box meets a cell whose level the new grid changes.  The
+ * forward and reverse CSR are then compacted.  The roadmap afterwards is the one
+ * mpap_build_roadmap_from_points
  * builds from the same nodes on the updated scene.  mem: MPAP_MEM_HOST or
  * MPAP_MEM_DEVICE for add_lo, add_hi and grid.  Synchronises the stream.
  * Returns MPAP_ERR_INVALID_ARG for a roadmap without geometry, more than 1024

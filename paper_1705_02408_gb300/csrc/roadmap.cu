@@ -737,10 +737,45 @@ __global__ void k_reverse_fill(const BuildJob* __restrict__ jobs) {
 // ---------------------------------------------------------------------------
 // Online update of a built roadmap (the map changes, the nodes stay): boxes are
 // added and the quality grid may be replaced.  An added box can only remove
-// edges, so every edge is tested against the added boxes alone; the transfers
-// are recomputed only when the grid changed.  The result is the roadmap the
-// build would make from the same nodes on the updated scene.
+// edges, so an edge is tested against the added boxes alone, and only when a
+// box of a bound on the edge's checkpoints meets one of them; its transfer is
+// recomputed only when that bound meets a cell whose level the new grid
+// changed.  The result is the roadmap the build would make from the same nodes
+// on the updated scene.
+//
+// The bound.  2D/3D: the segment's bounding box.  6D: every position of the
+// fixed-time double-integrator connection satisfies
+//   |p(t) - (p0 + v0 t)| = |int_0^t (t - s) u(s) ds| <= sqrt(t^3 / 3) sqrt(J)
+// (Cauchy-Schwarz, J = int |u|^2 = cost - T), so the connection stays within
+// sqrt(T^3 J / 3) of the segment from p0 to p0 + v0 T; J comes from the edge's
+// own quantised cost.  Both are grown by a margin far above the rounding of the
+// floating-point checkpoints, so skipping an edge outside every added box and
+// every changed cell changes no result.
 // ---------------------------------------------------------------------------
+constexpr float kReachMargin = 1e-3f;
+
+template <int DIM>
+__device__ __forceinline__ void edge_reach_box(const Geom& g, const float a[6], const float b[6], int cost_q,
+                                               float lo[3], float hi[3]) {
+  if (DIM != 6) {
+    constexpr int DP = (DIM == 2) ? 2 : 3;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      lo[i] = (i < DP) ? fminf(a[i], b[i]) - kReachMargin : -INFINITY;
+      hi[i] = (i < DP) ? fmaxf(a[i], b[i]) + kReachMargin : INFINITY;
+    }
+    return;
+  }
+  const float J = fmaxf(0.0f, (float)cost_q * (1.0f / 16777216.0f) - g.T) * 1.001f + 1e-3f;
+  const float rho = sqrtf(g.T * g.T * g.T * J * (1.0f / 3.0f)) * 1.001f + kReachMargin;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float e = a[i] + a[3 + i] * g.T;
+    lo[i] = fminf(a[i], e) - rho;
+    hi[i] = fmaxf(a[i], e) + rho;
+  }
+}
+
 struct UpdateJob {
   Geom g;                  // the updated scene (all boxes, the current grid)
   Geom g_add;              // the added boxes only
@@ -758,8 +793,41 @@ struct UpdateJob {
   uint32_t* dst_out;
   int2* peak_out;
   uint32_t* status;        // error bits
-  int retransfer;          // the grid changed
+  int retransfer;          // the grid was replaced
+  const int* creg;         // [6] index range of the cells whose level changed {min x, y, z, max x, y, z}
 };
+
+// Index range per axis of the cells whose level the new grid changes (one
+// roadmap per blockIdx.y; creg starts at {INT_MAX x3, INT_MIN x3}).
+struct GridDiffJob {
+  const uint8_t* old_g;
+  const uint8_t* new_g;
+  int G, dp;
+  int* creg;
+};
+
+__global__ void k_grid_diff(const GridDiffJob* __restrict__ jobs) {
+  const GridDiffJob J = jobs[blockIdx.y];
+  const size_t cells = (size_t)J.G * J.G * (J.dp == 3 ? J.G : 1);
+  int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
+    if (J.old_g[i] != J.new_g[i]) {
+      const int c[3] = {(int)(i % J.G), (int)((i / J.G) % J.G), J.dp == 3 ? (int)(i / ((size_t)J.G * J.G)) : 0};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        mn[k] = min(mn[k], c[k]);
+        mx[k] = max(mx[k], c[k]);
+      }
+    }
+  }
+  if (mn[0] != INT_MAX) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&J.creg[k], mn[k]);
+      atomicMax(&J.creg[3 + k], mx[k]);
+    }
+  }
+}
 
 // One warp per source: collision of each out-edge against the added boxes and,
 // when the grid changed, the edge's transfer on the new grid.  blockIdx.y picks
@@ -776,6 +844,21 @@ __global__ void k_update_edges(const UpdateJob* __restrict__ jobs, const uint32_
   }
   __syncthreads();
   constexpr int nc = (DIM == 6) ? 6 : DIM;
+  constexpr int DP = (DIM == 2) ? 2 : 3;
+  // the changed cells as a closed region of positions (open towards a grid
+  // border: positions beyond it fall into the border cells), grown by the margin
+  float rlo[3] = {0, 0, 0}, rhi[3] = {0, 0, 0};
+  bool any_changed = false;
+  if (J.retransfer) {
+    any_changed = J.creg[0] <= J.creg[3];
+    const float Gf = (float)J.g.G;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int cmin = J.creg[i], cmax = J.creg[3 + i];
+      rlo[i] = (i >= DP || cmin <= 0) ? -INFINITY : (float)cmin / Gf - kReachMargin;
+      rhi[i] = (i >= DP || cmax >= J.g.G - 1) ? INFINITY : (float)(cmax + 1) / Gf + kReachMargin;
+    }
+  }
   const unsigned lane = lane_id();
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < J.V; v += warps) {
@@ -791,19 +874,36 @@ __global__ void k_update_edges(const UpdateJob* __restrict__ jobs, const uint32_
         int4 rec = J.edge[e];
         int2 pk = J.peak[e];
         float b[6] = {0, 0, 0, 0, 0, 0};
+        if (DIM != 6) {
 #pragma unroll
-        for (int c = 0; c < nc; ++c) b[c] = J.x[(size_t)c * J.V + (uint32_t)rec.x];
-        Conn cn;
-        conn_setup_t<DIM>(J.g, a, b, cn);
-        ok = !conn_collides_t<DIM>(J.g_add, cn, s_lo, s_hi, nullptr);
-        if (ok && J.retransfer) {
-          int64_t S, C, Smax, Cmax;
-          conn_transfer_t<DIM>(J.g, cn, (int64_t)rec.y, S, C, Smax, Cmax);
-          if (S > INT32_MAX || S < INT32_MIN || C > INT32_MAX || Smax > INT32_MAX || Cmax > INT32_MAX)
-            atomicOr(&J.status[0], kErrEdge);
-          rec.z = (int)S;
-          rec.w = (int)C;
-          pk = make_int2((int)Smax, (int)Cmax);
+          for (int c = 0; c < nc; ++c) b[c] = J.x[(size_t)c * J.V + (uint32_t)rec.x];
+        }
+        float blo[3], bhi[3];
+        edge_reach_box<DIM>(J.g, a, b, rec.y, blo, bhi);
+        bool hit_box = false;
+        for (int k = 0; k < J.g_add.nb && !hit_box; ++k)
+          hit_box = blo[0] <= s_hi[3 * k] && bhi[0] >= s_lo[3 * k] && blo[1] <= s_hi[3 * k + 1] &&
+                    bhi[1] >= s_lo[3 * k + 1] && blo[2] <= s_hi[3 * k + 2] && bhi[2] >= s_lo[3 * k + 2];
+        const bool hit_cells = any_changed && blo[0] <= rhi[0] && bhi[0] >= rlo[0] && blo[1] <= rhi[1] &&
+                               bhi[1] >= rlo[1] && blo[2] <= rhi[2] && bhi[2] >= rlo[2];
+        ok = true;
+        if (hit_box || hit_cells) {
+          if (DIM == 6) {
+#pragma unroll
+            for (int c = 0; c < nc; ++c) b[c] = J.x[(size_t)c * J.V + (uint32_t)rec.x];
+          }
+          Conn cn;
+          conn_setup_t<DIM>(J.g, a, b, cn);
+          if (hit_box) ok = !conn_collides_t<DIM>(J.g_add, cn, s_lo, s_hi, nullptr);
+          if (ok && hit_cells) {
+            int64_t S, C, Smax, Cmax;
+            conn_transfer_t<DIM>(J.g, cn, (int64_t)rec.y, S, C, Smax, Cmax);
+            if (S > INT32_MAX || S < INT32_MIN || C > INT32_MAX || Smax > INT32_MAX || Cmax > INT32_MAX)
+              atomicOr(&J.status[0], kErrEdge);
+            rec.z = (int)S;
+            rec.w = (int)C;
+            pk = make_int2((int)Smax, (int)Cmax);
+          }
         }
         J.edge_upd[e] = rec;
         J.peak_upd[e] = pk;
@@ -1519,9 +1619,7 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
     if (rc) return rc;
     MPAP_CK(cudaMemcpyAsync(rm->box_lo, lo[j].data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
     MPAP_CK(cudaMemcpyAsync(rm->box_hi, hi[j].data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
-    if (grids && grids[j])
-      MPAP_CK(cudaMemcpyAsync(rm->grid, grids[j], cells, device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                              st));
+    // a new grid goes to the roadmap after it is compared with the old one (below)
     rm->nb = nb;
     fill_geom_constants(rm->geom, rm->dim, rm->nb, rm->G, rm->n_f, rm->M, rm->r, rm->T);
     rm->geom.box_lo = rm->box_lo;
@@ -1538,9 +1636,16 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
   // 2. one scratch block: per roadmap old pointers, kept counts, reverse counters,
   //    updated records and keep flags; the job tables
   char* blk = nullptr;
+  size_t grid_bytes = 0;
+  for (uint32_t j = 0; j < n; ++j)
+    if (grids && grids[j]) {
+      const mpap_roadmap* rm = rms[j];
+      grid_bytes += 256 + (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G) + 256 + 6 * sizeof(int);
+    }
   const size_t bytes = 256 * (10 * (size_t)n + 8) + 16 * (size_t)n + 16 * V_sum +
                        (sizeof(int4) + sizeof(int2) + 1) * (size_t)E_sum +
-                       (sizeof(UpdateJob) + sizeof(BuildJob) + sizeof(ScanSeg) + 4) * (size_t)n;
+                       (sizeof(UpdateJob) + sizeof(BuildJob) + sizeof(ScanSeg) + sizeof(GridDiffJob) + 4) * (size_t)n +
+                       grid_bytes;
   MPAP_CK(scratch_alloc((void**)&blk, bytes, st));
   auto bail = [&](int32_t r) {
     scratch_free(blk, st);
@@ -1552,6 +1657,10 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
   BuildJob* d_bj = cv.take<BuildJob>(n);
   ScanSeg* d_seg = cv.take<ScanSeg>(n);
   uint32_t* d_ids = cv.take<uint32_t>(n);
+  GridDiffJob* d_gd = cv.take<GridDiffJob>(n);
+  std::vector<GridDiffJob> gd;
+  std::vector<uint8_t*> new_grid(n, nullptr);
+  std::vector<int*> creg(n, nullptr);
   std::vector<UpdateJob> uj(n);
   std::vector<BuildJob> bj(n);
   std::vector<ScanSeg> segs(n);
@@ -1582,6 +1691,13 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
     J.peak_out = rm->fwd_peak;
     J.status = d_status + 4 * j;
     J.retransfer = (grids && grids[j]) ? 1 : 0;
+    if (J.retransfer) {
+      const size_t cells = (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G);
+      new_grid[j] = cv.take<uint8_t>(cells);
+      creg[j] = cv.take<int>(6);
+      J.creg = creg[j];
+      gd.push_back(GridDiffJob{rm->grid, new_grid[j], (int)rm->G, rm->dim == 2 ? 2 : 3, creg[j]});
+    }
     segs[j] = ScanSeg{J.kept, rm->fwd_ptr, V, d_status + 4 * j + 2};
     BuildJob& B = bj[j];
     std::memset(&B, 0, sizeof(B));
@@ -1612,6 +1728,34 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
       (rc = upload(d_bj, bj.data(), sizeof(BuildJob) * n, st)) ||
       (rc = upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st)))
     return bail(rc);
+  // new grids: the cells whose level changes (their index range bounds the
+  // edges whose transfers are recomputed), then the grid itself
+  if (!gd.empty()) {
+    const int init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+    uint32_t gmax = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+      if (!new_grid[j]) continue;
+      mpap_roadmap* rm = rms[j];
+      const size_t cells = (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G);
+      gmax = std::max<uint32_t>(gmax, (uint32_t)((cells + 255) / 256));
+      if (!cuda_ok(cudaMemcpyAsync(new_grid[j], grids[j], cells,
+                                   device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "copy") ||
+          (rc = upload(creg[j], init, sizeof(init), st)))
+        return bail(rc ? rc : MPAP_ERR_CUDA);
+    }
+    if ((rc = upload(d_gd, gd.data(), sizeof(GridDiffJob) * gd.size(), st))) return bail(rc);
+    {
+      LaunchScope ls(st, "k_grid_diff");
+      k_grid_diff<<<dim3(std::min<uint32_t>(gmax, 64u), (uint32_t)gd.size()), 256, 0, st>>>(d_gd);
+    }
+    for (uint32_t j = 0; j < n; ++j) {
+      if (!new_grid[j]) continue;
+      mpap_roadmap* rm = rms[j];
+      const size_t cells = (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G);
+      if (!cuda_ok(cudaMemcpyAsync(rm->grid, new_grid[j], cells, cudaMemcpyDeviceToDevice, st), "copy"))
+        return bail(MPAP_ERR_CUDA);
+    }
+  }
   // 3. edges against the added boxes (one launch per dimension), new row
   //    pointers, compaction into the CSR
   std::vector<uint32_t> ids;

@@ -67,6 +67,62 @@ def test_update_equals_construction_from_the_same_nodes(mp, orc, name, seed, n, 
         assert mp.certify(rg, a.path, *m) == orc.certify(ro, b.path, *m)
 
 
+def _local_grid(sc, seed, side=0.3):
+    """The scene's grid with the levels of the cells inside one cube of the given
+    side replaced by those of another seeded grid (new features mapped there)."""
+    rng = np.random.default_rng(seed + 991)
+    G = sc.cfg.grid_G
+    g = sc.grid.copy()
+    other = scenegen.make_scene(sc.cfg, seed + 200).grid
+    dp = 2 if sc.cfg.dim_kind == 2 else 3
+    lo = rng.uniform(0.0, 1.0 - side, dp)
+    idx = [np.arange(G)] * dp
+    cen = (np.arange(G) + 0.5) / G
+    inside = [(cen >= lo[i]) & (cen < lo[i] + side) for i in range(dp)]
+    if dp == 2:
+        m = inside[1][:, None] & inside[0][None, :]
+    else:
+        m = inside[2][:, None, None] & inside[1][None, :, None] & inside[0][None, None, :]
+    g.reshape(m.shape)[m] = other.reshape(m.shape)[m]
+    return g
+
+
+@pytest.mark.parametrize("name,seed,n,r,k,mode", [
+    ("2d", 3, 900, None, 3, "local"),
+    ("3d", 4, 1500, None, 2, "local"),
+    ("6d", 2, 2000, 18.0, 3, "local"),
+    ("6d", 6, 2000, 18.0, 0, "local"),    # grid only, a local change
+    ("6d", 7, 2000, 18.0, 2, "same"),     # the same grid again: no transfer changes
+    ("3d", 8, 1500, None, 0, "same"),
+])
+def test_update_skips_edges_away_from_the_changes(mp, orc, name, seed, n, r, k, mode):
+    """The update re-tests only the edges whose checkpoint bound meets an added box
+    and re-transfers only those whose bound meets a changed cell; with a local
+    grid change (or the same grid again) the result must still equal the
+    construction from the same nodes on the updated scene."""
+    sc = scenegen.make_scene(name, seed, query_id=seed)
+    rr = sc.cfg.r if r is None else r
+    rg = mp.build_roadmap_for_scene(sc, n=n, r=rr)
+    x = orc.build_roadmap(sc, n=n, r=rr).graph().x
+    lo, hi = _added_boxes(name, seed, k)
+    grid = _local_grid(sc, seed) if mode == "local" else sc.grid.copy()
+    if mode == "local":
+        assert (grid != sc.grid).any()
+    before = rg.export()
+    rg.update(lo if k else None, hi if k else None, grid)
+    ro = orc.build_roadmap_from_points(sc.cfg.dim_kind, np.concatenate([sc.box_lo, lo]),
+                                       np.concatenate([sc.box_hi, hi]), grid, sc.cfg.grid_G, x, rr,
+                                       T=sc.cfg.T_edge, M=sc.cfg.M)
+    g = ro.graph()
+    assert_same_graph(rg.export(), g)
+    np.testing.assert_array_equal(np.stack(rg.peaks()), np.stack([g.Smax, g.Cmax]))
+    assert_reverse_is_transpose(rg)
+    if mode == "same" and k == 0:
+        after = rg.export()
+        for key in ("row_ptr", "dst", "cost_q", "S", "C"):
+            np.testing.assert_array_equal(after[key], before[key])
+
+
 def test_update_with_device_arrays_and_repeated(mp, orc):
     import torch
     sc = scenegen.make_scene("3d", 6, query_id=6)
