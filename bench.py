@@ -606,6 +606,15 @@ def update_report(arm, k=3, side=0.3):
         out[name] = {"change": f"{k} added boxes each and " + (f"the cells inside one cube of side {side} given "
                                                                  "new levels" if grids is local else "a new grid"),
                      "ms_per_roadmap_update": ms_update / len(rms), "edges_before": E0, "edges_after": E1}
+        # the same update once more with per-launch events (a separate pass)
+        rms = arm.build()
+        torch.cuda.synchronize()
+        arm.mp.profile_reset()
+        arm.mp.profile_enable(True)
+        arm.mp.roadmap_update_batch(rms, [a[0] for a in adds], [a[1] for a in adds], grids)
+        torch.cuda.synchronize()
+        arm.mp.profile_enable(False)
+        out[name]["kernel_ms"] = {kk: round(v[1], 4) for kk, v in sorted(arm.mp.profile_read().items())}
     e0.record()
     arm.build()
     e1.record()

@@ -246,7 +246,10 @@ int32_t mpap_roadmap_export_reverse(const mpap_roadmap* rm, uint32_t* rev_ptr, u
  * p0 + v0 T grown by sqrt(T^3 J / 3), J = cost - T, which bounds the connection's
  * deviation from it) meets one of them; its transfer and peaks are recomputed
  * only when that box meets a cell whose level the new grid changes.  The
- * forward and reverse CSR are then compacted.  The roadmap afterwards is the one
+ * forward and reverse CSR are then compacted.  The host inputs are staged in one
+ * upload and the call synchronises the stream once, at its end; the box arrays
+ * keep room for 64 more boxes than the scene had, so an update that adds no more
+ * allocates nothing for them.  The roadmap afterwards is the one
  * mpap_build_roadmap_from_points
  * builds from the same nodes on the updated scene.  mem: MPAP_MEM_HOST or
  * MPAP_MEM_DEVICE for add_lo, add_hi and grid.  Synchronises the stream.

@@ -792,15 +792,20 @@ struct UpdateJob {
   int4* edge_out;          // compacted forward CSR
   uint32_t* dst_out;
   int2* peak_out;
-  uint32_t* status;        // error bits
+  uint32_t* status;        // [4] error bits, edges after the update, scan overflow, -
   int retransfer;          // the grid was replaced
   const int* creg;         // [6] index range of the cells whose level changed {min x, y, z, max x, y, z}
+  float* box_lo_dst;       // where the added boxes go in the roadmap's box arrays
+  float* box_hi_dst;
+  uint32_t* ptr_out;       // [V+1] the roadmap's row pointers (ptr until the compaction, then ptr_new)
 };
 
 // Index range per axis of the cells whose level the new grid changes (one
 // roadmap per blockIdx.y; creg starts at {INT_MAX x3, INT_MIN x3}).
+// The roadmap's grid takes the new levels in the same pass (each cell is read
+// and written by one thread only).
 struct GridDiffJob {
-  const uint8_t* old_g;
+  uint8_t* old_g;
   const uint8_t* new_g;
   int G, dp;
   int* creg;
@@ -811,7 +816,9 @@ __global__ void k_grid_diff(const GridDiffJob* __restrict__ jobs) {
   const size_t cells = (size_t)J.G * J.G * (J.dp == 3 ? J.G : 1);
   int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
-    if (J.old_g[i] != J.new_g[i]) {
+    const uint8_t nv = J.new_g[i];
+    if (J.old_g[i] != nv) {
+      J.old_g[i] = nv;
       const int c[3] = {(int)(i % J.G), (int)((i / J.G) % J.G), J.dp == 3 ? (int)(i / ((size_t)J.G * J.G)) : 0};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -841,6 +848,11 @@ __global__ void k_update_edges(const UpdateJob* __restrict__ jobs, const uint32_
   for (int i = threadIdx.x; i < 3 * J.g_add.nb; i += blockDim.x) {
     s_lo[i] = J.g_add.box_lo[i];
     s_hi[i] = J.g_add.box_hi[i];
+    if (blockIdx.x == 0) {
+      // the added boxes join the roadmap's obstacles (read from their source here)
+      J.box_lo_dst[i] = s_lo[i];
+      J.box_hi_dst[i] = s_hi[i];
+    }
   }
   __syncthreads();
   constexpr int nc = (DIM == 6) ? 6 : DIM;
@@ -938,6 +950,17 @@ __global__ void k_update_compact(const UpdateJob* __restrict__ jobs) {
       }
       out += __popc(bal);
     }
+  }
+}
+
+// After the compaction: the new row pointers become the roadmap's, and the new
+// edge count goes to the job's status word 1 (blockIdx.y: roadmap).
+__global__ void k_update_ptrs(const UpdateJob* __restrict__ jobs) {
+  const UpdateJob& J = jobs[blockIdx.y];
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v <= J.V; v += gridDim.x * blockDim.x) {
+    const uint32_t p = J.ptr_new[v];
+    J.ptr_out[v] = p;
+    if (v == J.V) J.status[1] = p;
   }
 }
 
@@ -1160,6 +1183,10 @@ int32_t ensure_edges(mpap_roadmap* rm, uint64_t E) {
   return MPAP_OK;
 }
 
+// Box arrays hold room for kBoxRoom boxes beyond the scene's, so that an online
+// update that adds a few needs no new allocation.
+constexpr size_t kBoxRoom = 64;
+
 int32_t ensure_scene(mpap_roadmap* rm, size_t nb, size_t cells) {
   if (!rm->box_lo || rm->cap_nb < 3 * nb + 3) {
     cudaFree(rm->box_lo);
@@ -1167,14 +1194,42 @@ int32_t ensure_scene(mpap_roadmap* rm, size_t nb, size_t cells) {
     rm->box_lo = nullptr;
     rm->box_hi = nullptr;
     rm->cap_nb = 0;
-    MPAP_CK(cudaMalloc((void**)&rm->box_lo, sizeof(float) * (3 * nb + 3)));
-    MPAP_CK(cudaMalloc((void**)&rm->box_hi, sizeof(float) * (3 * nb + 3)));
-    rm->cap_nb = 3 * nb + 3;
+    const size_t cap = 3 * (nb + kBoxRoom) + 3;
+    MPAP_CK(cudaMalloc((void**)&rm->box_lo, sizeof(float) * cap));
+    MPAP_CK(cudaMalloc((void**)&rm->box_hi, sizeof(float) * cap));
+    rm->cap_nb = cap;
   }
   size_t c = rm->cap_cells;
   int32_t rc = grow(&rm->grid, c, cells);
   rm->cap_cells = c;
   return rc;
+}
+
+// Box arrays with room for nb boxes that keep the first nb_old (grown with room
+// to spare; the old arrays are freed once the stream has copied them).
+int32_t ensure_boxes_kept(mpap_roadmap* rm, size_t nb_old, size_t nb, cudaStream_t st) {
+  if (rm->box_lo && rm->cap_nb >= 3 * nb + 3) return MPAP_OK;
+  const size_t cap = 3 * (nb + kBoxRoom) + 3;
+  float* lo = nullptr;
+  float* hi = nullptr;
+  if (cudaMalloc((void**)&lo, sizeof(float) * cap) != cudaSuccess ||
+      cudaMalloc((void**)&hi, sizeof(float) * cap) != cudaSuccess) {
+    cudaFree(lo);
+    cudaFree(hi);
+    set_error("roadmap_update: cudaMalloc of the box arrays failed");
+    return MPAP_ERR_CUDA;
+  }
+  if (nb_old && rm->box_lo) {
+    MPAP_CK(cudaMemcpyAsync(lo, rm->box_lo, sizeof(float) * 3 * nb_old, cudaMemcpyDeviceToDevice, st));
+    MPAP_CK(cudaMemcpyAsync(hi, rm->box_hi, sizeof(float) * 3 * nb_old, cudaMemcpyDeviceToDevice, st));
+  }
+  MPAP_CK(cudaStreamSynchronize(st));
+  cudaFree(rm->box_lo);
+  cudaFree(rm->box_hi);
+  rm->box_lo = lo;
+  rm->box_hi = hi;
+  rm->cap_nb = cap;
+  return MPAP_OK;
 }
 
 }  // namespace
@@ -1587,39 +1642,19 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
       return MPAP_ERR_INVALID_ARG;
     }
   }
-  // 1. the scenes: old boxes kept, added boxes appended, grids replaced
-  std::vector<std::vector<float>> lo(n), hi(n);
-  for (uint32_t j = 0; j < n; ++j) {
-    mpap_roadmap* rm = rms[j];
-    const int nb = rm->nb + nb_add[j];
-    lo[j].assign(3 * (size_t)nb + 3, 0.0f);
-    hi[j].assign(3 * (size_t)nb + 3, 0.0f);
-    if (rm->nb) {
-      MPAP_CK(cudaMemcpyAsync(lo[j].data(), rm->box_lo, sizeof(float) * 3 * rm->nb, cudaMemcpyDeviceToHost, st));
-      MPAP_CK(cudaMemcpyAsync(hi[j].data(), rm->box_hi, sizeof(float) * 3 * rm->nb, cudaMemcpyDeviceToHost, st));
-    }
-    if (nb_add[j]) {
-      const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-      MPAP_CK(cudaMemcpyAsync(lo[j].data() + 3 * rm->nb, add_lo[j], sizeof(float) * 3 * nb_add[j], kind, st));
-      MPAP_CK(cudaMemcpyAsync(hi[j].data() + 3 * rm->nb, add_hi[j], sizeof(float) * 3 * nb_add[j], kind, st));
-    }
-  }
-  MPAP_CK(cudaStreamSynchronize(st));
+  auto cells_of = [](const mpap_roadmap* rm) { return (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G); };
+  // 1. box capacity (the old boxes stay where they are; the added ones are
+  //    appended on the device), the updated geometry constants, sizes
   std::vector<int> nb_old(n);
-  uint64_t E_sum = 0, V_sum = 0;
-  uint32_t Vmax = 0;
+  uint64_t E_sum = 0, V_sum = 0, add_sum = 0, cell_sum = 0;
+  uint32_t Vmax = 0, n_grid = 0;
   int max_add = 0;
   for (uint32_t j = 0; j < n; ++j) {
     mpap_roadmap* rm = rms[j];
-    const int dp = (rm->dim == 2) ? 2 : 3;
-    const size_t cells = (size_t)rm->G * rm->G * (dp == 3 ? rm->G : 1);
     nb_old[j] = rm->nb;
     const int nb = rm->nb + nb_add[j];
-    int32_t rc = ensure_scene(rm, (size_t)nb, cells);
+    int32_t rc = ensure_boxes_kept(rm, (size_t)rm->nb, (size_t)nb, st);
     if (rc) return rc;
-    MPAP_CK(cudaMemcpyAsync(rm->box_lo, lo[j].data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
-    MPAP_CK(cudaMemcpyAsync(rm->box_hi, hi[j].data(), sizeof(float) * 3 * (size_t)nb, cudaMemcpyHostToDevice, st));
-    // a new grid goes to the roadmap after it is compared with the old one (below)
     rm->nb = nb;
     fill_geom_constants(rm->geom, rm->dim, rm->nb, rm->G, rm->n_f, rm->M, rm->r, rm->T);
     rm->geom.box_lo = rm->box_lo;
@@ -1632,20 +1667,20 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
     V_sum += (uint64_t)rm->V + 1;
     Vmax = std::max(Vmax, rm->V);
     max_add = std::max(max_add, nb_add[j]);
-  }
-  // 2. one scratch block: per roadmap old pointers, kept counts, reverse counters,
-  //    updated records and keep flags; the job tables
-  char* blk = nullptr;
-  size_t grid_bytes = 0;
-  for (uint32_t j = 0; j < n; ++j)
+    add_sum += (uint64_t)nb_add[j];
     if (grids && grids[j]) {
-      const mpap_roadmap* rm = rms[j];
-      grid_bytes += 256 + (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G) + 256 + 6 * sizeof(int);
+      ++n_grid;
+      cell_sum += cells_of(rm);
     }
-  const size_t bytes = 256 * (10 * (size_t)n + 8) + 16 * (size_t)n + 16 * V_sum +
-                       (sizeof(int4) + sizeof(int2) + 1) * (size_t)E_sum +
-                       (sizeof(UpdateJob) + sizeof(BuildJob) + sizeof(ScanSeg) + sizeof(GridDiffJob) + 4) * (size_t)n +
-                       grid_bytes;
+  }
+  // 2. one scratch block: job tables, status words, changed-cell ranges, the
+  //    host inputs staged in one upload, and per roadmap the updated records,
+  //    keep flags, kept counts, new row pointers and reverse counters
+  const size_t stage_bytes = device ? 0 : (2 * 12 * (size_t)add_sum + cell_sum);
+  const size_t bytes = 256 * (8 * (size_t)n + 16) + 16 * (size_t)n + 24 * (size_t)n + stage_bytes +
+                       16 * V_sum + (sizeof(int4) + sizeof(int2) + 1) * (size_t)E_sum +
+                       (sizeof(UpdateJob) + sizeof(BuildJob) + sizeof(ScanSeg) + sizeof(GridDiffJob) + 4) * (size_t)n;
+  char* blk = nullptr;
   MPAP_CK(scratch_alloc((void**)&blk, bytes, st));
   auto bail = [&](int32_t r) {
     scratch_free(blk, st);
@@ -1653,52 +1688,80 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
   };
   Carve cv{blk, 0};
   uint32_t* d_status = cv.take<uint32_t>(4 * (size_t)n);
+  int* d_creg = cv.take<int>(6 * (size_t)n);
   UpdateJob* d_uj = cv.take<UpdateJob>(n);
   BuildJob* d_bj = cv.take<BuildJob>(n);
   ScanSeg* d_seg = cv.take<ScanSeg>(n);
   uint32_t* d_ids = cv.take<uint32_t>(n);
   GridDiffJob* d_gd = cv.take<GridDiffJob>(n);
+  uint32_t* d_counts = cv.take<uint32_t>(2 * V_sum);     // reverse counters and fill cursors, all roadmaps
+  uint8_t* d_stage = stage_bytes ? cv.take<uint8_t>(stage_bytes) : nullptr;
+  std::vector<uint8_t> stage(stage_bytes);
+  size_t st_box = 0, st_grid = 2 * 12 * (size_t)add_sum;
   std::vector<GridDiffJob> gd;
-  std::vector<uint8_t*> new_grid(n, nullptr);
-  std::vector<int*> creg(n, nullptr);
+  std::vector<int> creg_init(6 * (size_t)n);
   std::vector<UpdateJob> uj(n);
   std::vector<BuildJob> bj(n);
   std::vector<ScanSeg> segs(n);
+  size_t cnt_off = 0;
   for (uint32_t j = 0; j < n; ++j) {
     mpap_roadmap* rm = rms[j];
     const uint32_t V = rm->V;
     const uint64_t E = rm->E;
     UpdateJob& J = uj[j];
     std::memset(&J, 0, sizeof(J));
-    uint32_t* ptr_old = cv.take<uint32_t>((size_t)V + 1);
     J.g = rm->geom;
     J.g_add = rm->geom;
     J.g_add.nb = nb_add[j];
-    J.g_add.box_lo = rm->box_lo + 3 * nb_old[j];
-    J.g_add.box_hi = rm->box_hi + 3 * nb_old[j];
+    if (nb_add[j]) {
+      const size_t nbytes = 12 * (size_t)nb_add[j];
+      if (device) {
+        J.g_add.box_lo = add_lo[j];
+        J.g_add.box_hi = add_hi[j];
+      } else {
+        std::memcpy(stage.data() + st_box, add_lo[j], nbytes);
+        std::memcpy(stage.data() + st_box + nbytes, add_hi[j], nbytes);
+        J.g_add.box_lo = reinterpret_cast<const float*>(d_stage + st_box);
+        J.g_add.box_hi = reinterpret_cast<const float*>(d_stage + st_box + nbytes);
+        st_box += 2 * nbytes;
+      }
+    }
+    J.box_lo_dst = rm->box_lo + 3 * nb_old[j];
+    J.box_hi_dst = rm->box_hi + 3 * nb_old[j];
     J.x = rm->x;
     J.V = V;
-    J.ptr = ptr_old;
+    J.ptr = rm->fwd_ptr;
+    J.ptr_out = rm->fwd_ptr;
     J.edge = rm->fwd_edge;
     J.peak = rm->fwd_peak;
     J.edge_upd = cv.take<int4>(E);
     J.peak_upd = cv.take<int2>(E);
     J.keep = cv.take<uint8_t>(E);
     J.kept = cv.take<uint32_t>((size_t)V + 1);
-    J.ptr_new = rm->fwd_ptr;
+    uint32_t* ptr_new = cv.take<uint32_t>((size_t)V + 1);
+    J.ptr_new = ptr_new;
     J.edge_out = rm->fwd_edge;
     J.dst_out = rm->fwd_dst;
     J.peak_out = rm->fwd_peak;
     J.status = d_status + 4 * j;
     J.retransfer = (grids && grids[j]) ? 1 : 0;
-    if (J.retransfer) {
-      const size_t cells = (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G);
-      new_grid[j] = cv.take<uint8_t>(cells);
-      creg[j] = cv.take<int>(6);
-      J.creg = creg[j];
-      gd.push_back(GridDiffJob{rm->grid, new_grid[j], (int)rm->G, rm->dim == 2 ? 2 : 3, creg[j]});
+    int* cr = d_creg + 6 * (size_t)j;
+    for (int k = 0; k < 3; ++k) {
+      creg_init[6 * (size_t)j + k] = INT_MAX;
+      creg_init[6 * (size_t)j + 3 + k] = INT_MIN;
     }
-    segs[j] = ScanSeg{J.kept, rm->fwd_ptr, V, d_status + 4 * j + 2};
+    if (J.retransfer) {
+      const size_t cells = cells_of(rm);
+      const uint8_t* src = grids[j];
+      if (!device) {
+        std::memcpy(stage.data() + st_grid, grids[j], cells);
+        src = d_stage + st_grid;
+        st_grid += cells;
+      }
+      J.creg = cr;
+      gd.push_back(GridDiffJob{rm->grid, src, (int)rm->G, rm->dim == 2 ? 2 : 3, cr});
+    }
+    segs[j] = ScanSeg{J.kept, ptr_new, V, d_status + 4 * j + 2};
     BuildJob& B = bj[j];
     std::memset(&B, 0, sizeof(B));
     B.V = V;
@@ -1708,56 +1771,14 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
     B.rev_edge = rm->rev_edge;
     B.fwd_peak = rm->fwd_peak;
     B.rev_peak = rm->rev_peak;
-    B.counts = cv.take<uint32_t>((size_t)V + 1);
-    B.fill = cv.take<uint32_t>((size_t)V + 1);
+    B.counts = d_counts + cnt_off;
+    B.fill = d_counts + V_sum + cnt_off;
+    cnt_off += (size_t)V + 1;
   }
   if (cv.off > bytes) {
     set_error("roadmap_update: scratch layout overflow");
     return bail(MPAP_ERR_CUDA);
   }
-  int32_t rc = MPAP_OK;
-  if (!cuda_ok(cudaMemsetAsync(d_status, 0, 16 * (size_t)n, st), "memset")) return bail(MPAP_ERR_CUDA);
-  for (uint32_t j = 0; j < n; ++j) {
-    if (!cuda_ok(cudaMemcpyAsync(const_cast<uint32_t*>(uj[j].ptr), rms[j]->fwd_ptr, 4 * ((size_t)rms[j]->V + 1),
-                                 cudaMemcpyDeviceToDevice, st), "copy") ||
-        !cuda_ok(cudaMemsetAsync(bj[j].counts, 0, 4 * ((size_t)rms[j]->V + 1), st), "memset") ||
-        !cuda_ok(cudaMemsetAsync(bj[j].fill, 0, 4 * ((size_t)rms[j]->V + 1), st), "memset"))
-      return bail(MPAP_ERR_CUDA);
-  }
-  if ((rc = upload(d_uj, uj.data(), sizeof(UpdateJob) * n, st)) ||
-      (rc = upload(d_bj, bj.data(), sizeof(BuildJob) * n, st)) ||
-      (rc = upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st)))
-    return bail(rc);
-  // new grids: the cells whose level changes (their index range bounds the
-  // edges whose transfers are recomputed), then the grid itself
-  if (!gd.empty()) {
-    const int init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-    uint32_t gmax = 0;
-    for (uint32_t j = 0; j < n; ++j) {
-      if (!new_grid[j]) continue;
-      mpap_roadmap* rm = rms[j];
-      const size_t cells = (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G);
-      gmax = std::max<uint32_t>(gmax, (uint32_t)((cells + 255) / 256));
-      if (!cuda_ok(cudaMemcpyAsync(new_grid[j], grids[j], cells,
-                                   device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "copy") ||
-          (rc = upload(creg[j], init, sizeof(init), st)))
-        return bail(rc ? rc : MPAP_ERR_CUDA);
-    }
-    if ((rc = upload(d_gd, gd.data(), sizeof(GridDiffJob) * gd.size(), st))) return bail(rc);
-    {
-      LaunchScope ls(st, "k_grid_diff");
-      k_grid_diff<<<dim3(std::min<uint32_t>(gmax, 64u), (uint32_t)gd.size()), 256, 0, st>>>(d_gd);
-    }
-    for (uint32_t j = 0; j < n; ++j) {
-      if (!new_grid[j]) continue;
-      mpap_roadmap* rm = rms[j];
-      const size_t cells = (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G);
-      if (!cuda_ok(cudaMemcpyAsync(rm->grid, new_grid[j], cells, cudaMemcpyDeviceToDevice, st), "copy"))
-        return bail(MPAP_ERR_CUDA);
-    }
-  }
-  // 3. edges against the added boxes (one launch per dimension), new row
-  //    pointers, compaction into the CSR
   std::vector<uint32_t> ids;
   const int dims[3] = {2, 3, 6};
   uint32_t off[4] = {0, 0, 0, 0};
@@ -1767,8 +1788,30 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
       if (rms[j]->dim == dims[di]) ids.push_back(j);
   }
   off[3] = (uint32_t)ids.size();
-  if ((rc = upload(d_ids, ids.data(), sizeof(uint32_t) * n, st))) return bail(rc);
+  int32_t rc = MPAP_OK;
+  if (!cuda_ok(cudaMemsetAsync(d_status, 0, 16 * (size_t)n, st), "memset") ||
+      !cuda_ok(cudaMemsetAsync(d_counts, 0, sizeof(uint32_t) * 2 * V_sum, st), "memset"))
+    return bail(MPAP_ERR_CUDA);
+  if ((stage_bytes && (rc = upload(d_stage, stage.data(), stage_bytes, st))) ||
+      (rc = upload(d_creg, creg_init.data(), sizeof(int) * 6 * (size_t)n, st)) ||
+      (rc = upload(d_uj, uj.data(), sizeof(UpdateJob) * n, st)) ||
+      (rc = upload(d_bj, bj.data(), sizeof(BuildJob) * n, st)) ||
+      (rc = upload(d_seg, segs.data(), sizeof(ScanSeg) * n, st)) ||
+      (rc = upload(d_ids, ids.data(), sizeof(uint32_t) * n, st)) ||
+      (!gd.empty() && (rc = upload(d_gd, gd.data(), sizeof(GridDiffJob) * gd.size(), st))))
+    return bail(rc);
   const int sms = sm_count();
+  // 3. new grids: the cells whose level changes (their index range bounds the
+  //    edges whose transfers are recomputed), written into the roadmaps' grids
+  if (!gd.empty()) {
+    uint32_t gmax = 0;
+    for (const GridDiffJob& d : gd)
+      gmax = std::max<uint32_t>(gmax, (uint32_t)(((size_t)d.G * d.G * (d.dp == 3 ? d.G : 1) + 255) / 256));
+    LaunchScope ls(st, "k_grid_diff");
+    k_grid_diff<<<dim3(std::min<uint32_t>(gmax, 64u), (uint32_t)gd.size()), 256, 0, st>>>(d_gd);
+  }
+  // 4. edges near the changes (one launch per dimension), new row pointers,
+  //    compaction into the CSR, the row pointers and edge counts in place
   const uint32_t gx = std::min<uint32_t>((Vmax + 7) / 8, 4u * sms);
   const size_t sm = sizeof(float) * 6 * (size_t)max_add;
   {
@@ -1790,19 +1833,19 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
     LaunchScope ls(st, "k_update_compact");
     k_update_compact<<<dim3(gx, n), 256, 0, st>>>(d_uj);
   }
+  {
+    LaunchScope ls(st, "k_update_ptrs");
+    k_update_ptrs<<<dim3(std::min<uint32_t>((Vmax + 256) / 256, 4u * sms), n), 256, 0, st>>>(d_uj);
+  }
   if (!cuda_ok(cudaGetLastError(), "update kernels")) return bail(MPAP_ERR_CUDA);
-  // 4. edge counts back, then the reverse CSR of every updated roadmap
-  std::vector<uint32_t> hs(4 * (size_t)n), e_new(n);
+  // 5. the reverse CSR of every updated roadmap, then the status words back
+  if ((rc = build_reverse(n, bj, d_bj, d_seg, Vmax, st))) return bail(rc);
+  std::vector<uint32_t> hs(4 * (size_t)n);
   if (!cuda_ok(cudaMemcpyAsync(hs.data(), d_status, 16 * (size_t)n, cudaMemcpyDeviceToHost, st), "copy"))
     return bail(MPAP_ERR_CUDA);
-  for (uint32_t j = 0; j < n; ++j)
-    if (!cuda_ok(cudaMemcpyAsync(&e_new[j], rms[j]->fwd_ptr + rms[j]->V, 4, cudaMemcpyDeviceToHost, st), "copy"))
-      return bail(MPAP_ERR_CUDA);
-  if (!cuda_ok(cudaStreamSynchronize(st), "sync")) return bail(MPAP_ERR_CUDA);
-  for (uint32_t j = 0; j < n; ++j) rms[j]->E = e_new[j];
-  if ((rc = build_reverse(n, bj, d_bj, d_seg, Vmax, st))) return bail(rc);
   scratch_free(blk, st);
   if (!cuda_ok(cudaStreamSynchronize(st), "sync")) return MPAP_ERR_CUDA;
+  for (uint32_t j = 0; j < n; ++j) rms[j]->E = hs[4 * j + 1];
   for (uint32_t j = 0; j < n; ++j)
     if (hs[4 * j]) {
       set_error("roadmap_update: an edge transfer of roadmap %u does not fit int32", j);
