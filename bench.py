@@ -341,10 +341,10 @@ def run_gpu(args, rank, world, local):
 # DRAM traffic from ncu captures, per unit of work, valid only while the kernel
 # sources are the ones that were captured.
 NCU_TRAFFIC = {
-    # one row-pass launch over 8 roadmaps: 13.24 MB read + 90.36 MB written (roadmap.cu
-    # has only gained the online-update kernels since; the row pass is unchanged)
-    "k_edges": {"bytes_per_roadmap": (13.236736e6 + 90.364672e6) / 8,
-                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "d62482682c7dcca7902214d7f5b830d779e07767",
+    # one row-pass launch over 8 roadmaps: 13.22 MB read + 89.78 MB written
+    # (profiles/k_edges_6d16k.md)
+    "k_edges": {"bytes_per_roadmap": (13.224192e6 + 89.782272e6) / 8,
+                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "10e96881fc43d35abe455134208faed84bb55602",
                             "paper_1705_02408_gb300/csrc/common.cuh": "f42dfc54d3c1a7692a7b0b6e1943805b4fb67da4"}},
     # one k_wave launch of the 8-query 6D-16k step: 169.29 MB read + 61.54 MB written
     # for 12,658,585 plan-edge expansions (profiles/k_wave_6d16k_8queries.md)
