@@ -82,6 +82,10 @@ def lib():
         L.orc_certify.argtypes = [P, u32p, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32,
                                   C.c_int64, i32p, i32p, u32p]
         L.orc_straight_line_h.argtypes = [P, i64p]
+        L.orc_certify_vio.restype = C.c_int
+        L.orc_certify_vio.argtypes = [P, u32p, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32, C.c_int64,
+                                      C.c_int32, C.c_int32, C.c_int32, i32p, u32p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]
         L.orc_result_candidates.restype = C.c_int
         L.orc_result_candidates.argtypes = [P, C.c_uint32, i64p, i64p, u32p, u32p, C.c_uint32,
                                             C.POINTER(C.c_uint32)]
@@ -278,6 +282,35 @@ def certify(rm: Roadmap, path, rollouts: int, seed: int, call_id: int, delta_fx:
                       hits)
     return dict(hits_loc=int(hits[0]), hits_coll=int(hits[1]), hits_any=int(hits[2]),
                 rollouts=int(hits[3]))
+
+
+def certify_vio(rm: Roadmap, path, rollouts: int, seed: int, call_id: int, delta_fx: int, q_a: int,
+                kp_q16: int, kv_q16: int, r_fx, trace: bool = False):
+    """Closed-loop VIO Monte Carlo certification (LQR tracking, inertial
+    prediction, Kalman position fixes; see certify_vio in mpap_oracle.cpp).  With
+    trace: also the final axis-0 estimation error of every rollout, the Q16 Kalman
+    gains (Lp, Lw) and the posterior position variance of every step, and the
+    final axis-0 executed deviation of every rollout."""
+    hits = np.zeros(4, np.uint32)
+    path = np.ascontiguousarray(path, np.uint32)
+    plen = path.size
+    if plen == 0:
+        path = np.zeros(1, np.uint32)
+    r_fx = np.ascontiguousarray(r_fx, np.int32)
+    ep = gains = p00 = None
+    ptrs = [None, None, None]
+    if trace and plen >= 2:
+        steps = (plen - 1) * rm.M
+        ep = np.zeros((max(rollouts, 1), 2), np.int64)
+        gains = np.zeros((steps, 2), np.int32)
+        p00 = np.zeros(steps, np.float64)
+        ptrs = [ep.ctypes.data, gains.ctypes.data, p00.ctypes.data]
+    lib().orc_certify_vio(rm.h, path, plen, rollouts, seed, call_id, int(delta_fx), int(q_a), int(kp_q16),
+                          int(kv_q16), r_fx, hits, *ptrs)
+    out = dict(hits_loc=int(hits[0]), hits_coll=int(hits[1]), hits_any=int(hits[2]), rollouts=int(hits[3]))
+    if trace:
+        out.update(ep_last=ep[:, 0].copy(), p_last=ep[:, 1].copy(), gains=gains, p00=p00)
+    return out
 
 
 def feature_levels(dp: int, box_lo, box_hi, features, G: int, headings=None, cos_half: float = -2.0,

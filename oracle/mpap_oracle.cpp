@@ -683,6 +683,169 @@ int certify(const Roadmap& rm, const uint32_t* path, uint32_t path_len, uint32_t
 }
 
 // ----------------------------------------------------------------------------
+// Closed-loop VIO Monte Carlo model (Sec. 4.1: the nominal trajectory is tracked
+// by an LQR controller; the state estimate fuses an inertial prediction from a
+// noisy accelerometer with position fixes from the features in view through a
+// Kalman filter).  The paper gives no parameters; every quantity below is this
+// build's reading.  Per position axis, in 2^-20 units and per checkpoint step:
+// true deviation (p, w) from the nominal (w = velocity x step) and estimation
+// error (ep, ew) = estimate - truth.  At checkpoint s with quality level k:
+//   a  = -round((kp (p + ep) + kv (w + ew)) / 2^16)   LQR control from the estimate
+//   p += w + (a >> 1);  w += a                          the executed deviation
+//   na = (q_a xi1) >> 16;  ep += ew + (na >> 1);  ew += na     inertial prediction
+//   if r_k > 0:  nu = (r_k xi2) >> 16;  t = nu - ep;
+//                ep += round(Lp_s t / 2^16);  ew += round(Lw_s t / 2^16)   position fix
+// all clamped to |x| <= 2^30; round(x / 2^16) = (x + 2^15) >> 16.  (Lp_s, Lw_s)
+// are the Kalman gains of step s from the covariance recursion in double (P_0 = 0;
+// prediction A P A^T + q_a^2 B B^T with A = [1 1; 0 1], B = (1/2, 1); update
+// with measurement noise r_k^2 when r_k > 0), quantised to Q16.  xi1, xi2 are
+// the Irwin-Hall normals of certify(): axis i takes u16 words 24 i .. 24 i + 11
+// and 24 i + 12 .. 24 i + 23 of Philox with counter (rollout, step, call, call_id),
+// calls 0 .. ceil(3 dp) - 1.  Failures as in certify(): |ep| >= delta
+// (localisation, Eq. 1) and the executed position nom + p outside the map or in a
+// closed box (the robust problem).
+// ----------------------------------------------------------------------------
+void vio_gains(const std::vector<int>& lev, int32_t q_a, const int32_t* r_fx, std::vector<int32_t>& Lp,
+               std::vector<int32_t>& Lw, std::vector<double>& P00) {
+  double p00 = 0.0, p01 = 0.0, p11 = 0.0;
+  const double q2 = (double)q_a * (double)q_a;
+  const size_t n = lev.size();
+  Lp.assign(n, 0);
+  Lw.assign(n, 0);
+  P00.assign(n, 0.0);
+  for (size_t s = 0; s < n; ++s) {
+    const double a00 = p00 + 2.0 * p01 + p11 + 0.25 * q2;
+    const double a01 = p01 + p11 + 0.5 * q2;
+    const double a11 = p11 + q2;
+    const int32_t r = r_fx[lev[s]];
+    double lp = 0.0, lw = 0.0;
+    if (r > 0) {
+      const double S = a00 + (double)r * (double)r;
+      lp = a00 / S;
+      lw = a01 / S;
+      p00 = (1.0 - lp) * a00;
+      p01 = (1.0 - lp) * a01;
+      p11 = a11 - lw * a01;
+    } else {
+      p00 = a00;
+      p01 = a01;
+      p11 = a11;
+    }
+    Lp[s] = (int32_t)llrint(lp * 65536.0);
+    Lw[s] = (int32_t)llrint(lw * 65536.0);
+    P00[s] = p00;
+  }
+}
+
+static inline int64_t clamp30(int64_t x) {
+  const int64_t lim = (int64_t)1 << 30;
+  return x > lim ? lim : (x < -lim ? -lim : x);
+}
+
+static inline int64_t round16(int64_t x) { return (x + 32768) >> 16; }
+
+int certify_vio(const Roadmap& rm, const uint32_t* path, uint32_t path_len, uint32_t rollouts, uint64_t seed,
+                uint32_t call_id, int64_t delta_fx, int32_t q_a, int32_t kp, int32_t kv, const int32_t* r_fx,
+                CertOut& out, int64_t* ep_last, int32_t* gains, double* p00_out) {
+  const Scene& sc = rm.sc;
+  const int dp = sc.dp();
+  out = CertOut{};
+  out.rollouts = rollouts;
+  if (path_len < 2) return 0;
+  std::vector<int64_t> nom;
+  std::vector<int> lev;
+  for (uint32_t j = 0; j + 1 < path_len; ++j) {
+    EdgeGeom g = edge_geom(rm, path[j], path[j + 1]);
+    for (int m = 1; m <= rm.M; ++m) {
+      float p[3];
+      checkpoint(rm, g, m, p);
+      for (int i = 0; i < 3; ++i) nom.push_back((int64_t)llrintf(p[i] * kTwo20));
+      lev.push_back(level_at(sc, p));
+    }
+  }
+  const uint32_t steps = (uint32_t)lev.size();
+  std::vector<int32_t> Lp, Lw;
+  std::vector<double> P00;
+  vio_gains(lev, q_a, r_fx, Lp, Lw, P00);
+  if (gains)
+    for (uint32_t s = 0; s < steps; ++s) {
+      gains[2 * s] = Lp[s];
+      gains[2 * s + 1] = Lw[s];
+    }
+  if (p00_out)
+    for (uint32_t s = 0; s < steps; ++s) p00_out[s] = P00[s];
+  std::vector<int64_t> blo(3 * sc.nb), bhi(3 * sc.nb);
+  for (int b = 0; b < 3 * sc.nb; ++b) {
+    blo[b] = (int64_t)llrintf(sc.lo[b] * kTwo20);
+    bhi[b] = (int64_t)llrintf(sc.hi[b] * kTwo20);
+  }
+  const int64_t one = (int64_t)1 << 20;
+  const int64_t delta2 = delta_fx * delta_fx;
+  const uint32_t ncalls = (uint32_t)(24 * dp + 7) / 8;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (uint32_t ro = 0; ro < rollouts; ++ro) {
+    int64_t p[3] = {0, 0, 0}, w[3] = {0, 0, 0}, ep[3] = {0, 0, 0}, ew[3] = {0, 0, 0};
+    bool loc = false, coll = false;
+    for (uint32_t s = 0; s < steps; ++s) {
+      const int k = lev[s];
+      uint32_t words[36];
+      for (uint32_t c = 0; c < ncalls; ++c) {
+        uint32_t ctr[4] = {ro, s, c, call_id};
+        philox4x32_10(ctr, key, words + 4 * c);
+      }
+      auto normal = [&](int first) {
+        int64_t xi = 0;
+        for (int j = 0; j < 12; ++j) {
+          const int idx = first + j;
+          const uint32_t wd = words[idx >> 1];
+          xi += (idx & 1) ? (int64_t)(wd >> 16) : (int64_t)(wd & 0xFFFFu);
+        }
+        return xi - 6 * 65536;
+      };
+      for (int i = 0; i < dp; ++i) {
+        const int64_t a = -round16((int64_t)kp * (p[i] + ep[i]) + (int64_t)kv * (w[i] + ew[i]));
+        p[i] = clamp30(p[i] + w[i] + (a >> 1));
+        w[i] = clamp30(w[i] + a);
+        const int64_t na = ((int64_t)q_a * normal(24 * i)) >> 16;
+        ep[i] = clamp30(ep[i] + ew[i] + (na >> 1));
+        ew[i] = clamp30(ew[i] + na);
+        if (r_fx[k] > 0) {
+          const int64_t nu = ((int64_t)r_fx[k] * normal(24 * i + 12)) >> 16;
+          const int64_t t = nu - ep[i];
+          ep[i] = clamp30(ep[i] + round16((int64_t)Lp[s] * t));
+          ew[i] = clamp30(ew[i] + round16((int64_t)Lw[s] * t));
+        }
+      }
+      int64_t ee = 0;
+      for (int i = 0; i < dp; ++i) ee += ep[i] * ep[i];
+      if (ee >= delta2) loc = true;
+      int64_t q[3];
+      bool out_ws = false;
+      for (int i = 0; i < dp; ++i) {
+        q[i] = nom[3 * s + i] + p[i];
+        if (q[i] < 0 || q[i] > one) out_ws = true;
+      }
+      bool in_box = false;
+      for (int b = 0; b < sc.nb && !in_box; ++b) {
+        bool inside = true;
+        for (int i = 0; i < dp; ++i)
+          if (q[i] < blo[3 * b + i] || q[i] > bhi[3 * b + i]) { inside = false; break; }
+        in_box = inside;
+      }
+      if (out_ws || in_box) coll = true;
+    }
+    if (ep_last) {
+      ep_last[2 * (size_t)ro] = ep[0];
+      ep_last[2 * (size_t)ro + 1] = p[0];
+    }
+    out.hits_loc += loc;
+    out.hits_coll += coll;
+    out.hits_any += (loc || coll);
+  }
+  return 0;
+}
+
+// ----------------------------------------------------------------------------
 // Trajectory features of a plan (input of the certification surrogate, which is
 // not in the paper).  The plan's Monte Carlo checkpoints s = 0 .. steps-1 (the M
 // sub-steps of every edge, exactly as certify() visits them) are split into 16
@@ -1000,6 +1163,19 @@ int orc_certify(const orc_roadmap* h, const uint32_t* path, uint32_t path_len, u
                 const int32_t* shift, uint32_t* hits /* loc, coll, any, rollouts */) {
   CertOut c;
   int rc = certify(h->rm, path, path_len, rollouts, seed, call_id, delta_fx, sigma_fx, shift, c);
+  hits[0] = c.hits_loc;
+  hits[1] = c.hits_coll;
+  hits[2] = c.hits_any;
+  hits[3] = c.rollouts;
+  return rc;
+}
+
+int orc_certify_vio(const orc_roadmap* h, const uint32_t* path, uint32_t path_len, uint32_t rollouts,
+                    uint64_t seed, uint32_t call_id, int64_t delta_fx, int32_t q_a, int32_t kp, int32_t kv,
+                    const int32_t* r_fx, uint32_t* hits, int64_t* ep_last, int32_t* gains, double* p00) {
+  CertOut c;
+  int rc = certify_vio(h->rm, path, path_len, rollouts, seed, call_id, delta_fx, q_a, kp, kv, r_fx, c, ep_last,
+                       gains, p00);
   hits[0] = c.hits_loc;
   hits[1] = c.hits_coll;
   hits[2] = c.hits_any;
