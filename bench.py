@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-perception", action="store_true")
     ap.add_argument("--no-update", action="store_true")
     ap.add_argument("--no-errnet", action="store_true")
+    ap.add_argument("--no-vio", action="store_true")
     ap.add_argument("--sur-train-plans", type=int, default=200000,
                     help="Monte Carlo-labelled candidate plans to train the surrogate on")
     ap.add_argument("--sur-train-steps", type=int, default=2000)
@@ -320,6 +321,8 @@ def run_gpu(args, rank, world, local):
     log("timed region done")
     if rank == 0 and not args.no_refine:
         out["refine"] = refine_report(arm)
+    if rank == 0 and not args.no_vio:
+        out["vio_certify"] = vio_report(arm)
     if rank == 0 and not args.no_perception:
         out["perception_levels"] = perception_report(arm)
     if rank == 0 and not args.no_update:
@@ -621,6 +624,49 @@ def update_report(arm, k=3, side=0.3):
     torch.cuda.synchronize()
     out["ms_per_roadmap_rebuild"] = e0.elapsed_time(e1) / len(arm.scenes)
     return out
+
+
+# closed-loop VIO model parameters (per checkpoint step, 2^-20 units): inertial
+# noise, position-fix noise at the lowest level with a fix (falling as
+# 1/sqrt(level)), LQR weights (q_p, q_w, r)
+VIO_Q_A, VIO_R_MAX, VIO_FIX_FROM, VIO_LQR_WEIGHTS = 60, 2048, 3, (1.0, 0.5, 20.0)
+
+
+def vio_report(arm):
+    """The benchmark's 64 plans certified under the closed-loop VIO model (LQR
+    tracking, inertial prediction, Kalman fixes) in one batched call, beside the
+    error-walk certification of the same plans; CUDA events around each."""
+    import torch
+    mp = arm.mp
+    rms, res, _ = arm._last
+    paths = [r.path for r in res]
+    kp, kv = mp.vio_lqr_gains(*VIO_LQR_WEIGHTS)
+    lev = np.arange(25)
+    table = np.where(lev >= VIO_FIX_FROM, np.rint(VIO_R_MAX * np.sqrt(VIO_FIX_FROM / np.maximum(lev, 1))),
+                     0).astype(np.int32)
+    mcs = [(m[0], m[1], m[2], m[3]) for m in arm.mc]
+    vios = [(VIO_Q_A, kp, kv, table)] * len(rms)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    mp.certify_vio_batch(rms, paths, mcs, vios)          # warm-up
+    torch.cuda.synchronize()
+    e0.record()
+    out = mp.certify_vio_batch(rms, paths, mcs, vios)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_vio = e0.elapsed_time(e1)
+    e0.record()
+    mp.certify_batch(rms, paths, arm.mc)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_walk = e0.elapsed_time(e1)
+    R = sum(o["rollouts"] for o in out)
+    return {"workload": f"{len(rms)} plans of the benchmark step, {arm.cfg.mc_rollouts} rollouts each",
+            "model": {"q_a_fx": VIO_Q_A, "lqr_weights": VIO_LQR_WEIGHTS, "kp_q16": kp, "kv_q16": kv,
+                      "r_fx_max": VIO_R_MAX, "fix_from_level": VIO_FIX_FROM},
+            "ms_per_batch": ms_vio, "ms_per_batch_error_walk": ms_walk,
+            "failure_rate": sum(o["hits_any"] for o in out) / max(1, R),
+            "localisation_rate": sum(o["hits_loc"] for o in out) / max(1, R),
+            "collision_rate": sum(o["hits_coll"] for o in out) / max(1, R)}
 
 
 def refine_report(arm, eps=0.05, rounds=8):

@@ -345,6 +345,52 @@ int32_t mpap_certify_batch(mpap_roadmap* const* rms, const uint32_t* const* path
                            const uint32_t* path_lens, const mpap_mc_params* mcs, uint32_t n,
                            mpap_cert* outs, void* stream);
 
+/* Closed-loop VIO Monte Carlo model (Sec. 4.1: the nominal trajectory tracked by
+ * an LQR controller, the state estimated by a Kalman filter that fuses an
+ * inertial prediction with position fixes from the features in view).  The
+ * paper gives no parameters; this is the library's reading.  Per position axis,
+ * in 2^-20 units and per checkpoint step, the executed deviation (p, w) from the
+ * nominal (w = velocity x step) and the estimation error (ep, ew): at checkpoint
+ * s with quality level k,
+ *   a  = -round((kp_q16 (p + ep) + kv_q16 (w + ew)) / 2^16)     LQR from the estimate
+ *   p += w + (a >> 1);  w += a
+ *   na = (q_a xi1) >> 16;  ep += ew + (na >> 1);  ew += na       inertial prediction
+ *   if r_fx[k] > 0:  nu = (r_fx[k] xi2) >> 16;  t = nu - ep;
+ *     ep += round(Lp_s t / 2^16);  ew += round(Lw_s t / 2^16)    position fix
+ * all clamped to |x| <= 2^30, round(x / 2^16) = (x + 2^15) >> 16.  (Lp_s, Lw_s)
+ * are the Kalman gains of step s from the covariance recursion in double (P_0 =
+ * 0; prediction A P A^T + q_a^2 B B^T, A = [1 1; 0 1], B = (1/2, 1); update with
+ * variance r_fx[k]^2 when r_fx[k] > 0) rounded to Q16.  xi1 and xi2 are sums of 12
+ * uniform 16-bit draws minus 6 * 2^16: axis i takes the u16 halves (low first)
+ * of Philox4x32-10 calls 3 i .. 3 i + 2 with counter (rollout, step, call,
+ * call_id) and key seed, xi1 from the first six words and xi2 from the last six.
+ * Localisation fails when ep.ep >= delta_fx^2 (Eq. 1); the executed position
+ * nom + p fails when it leaves the unit map or enters a closed box.  r_fx is a
+ * host array of K+1 entries (0: no fix at that level); kp_q16, kv_q16 are the
+ * LQR gains per step in Q16 (a = -(kp p + kv w)). */
+typedef struct {
+  int32_t q_a;             /* inertial noise per step, 2^-20 units */
+  int32_t kp_q16;
+  int32_t kv_q16;
+  const int32_t* r_fx;     /* [K+1] position-fix noise per quality level */
+} mpap_vio_params;
+
+/* The LQR gains of the VIO model for state cost diag(q_p, q_w) and control cost
+ * r (> 0): per position axis x' = A x + B a with A = [1 1; 0 1], B = (1/2, 1)
+ * over one checkpoint step, a = -(kp p + kv w) with (kp, kv) = (r + B^T P B)^-1
+ * B^T P A, P the fixed point of the discrete Riccati recursion started at
+ * diag(q_p, q_w) (double), returned in Q16.  Host only; MPAP_ERR_INVALID_ARG for
+ * negative weights, r <= 0 or NULL outputs. */
+int32_t mpap_vio_lqr_gains(double q_p, double q_w, double r, int32_t* kp_q16, int32_t* kv_q16);
+
+/* n certifications under the VIO model in one launch: paths[i] (host) on rms[i]
+ * with mcs[i] (rollouts, call_id, seed, delta_fx; its sigma_fx and shift are not
+ * used and may be NULL) and vps[i].  Errors as for mpap_certify_batch, and
+ * MPAP_ERR_INVALID_ARG for a null r_fx. */
+int32_t mpap_certify_vio_batch(mpap_roadmap* const* rms, const uint32_t* const* paths,
+                               const uint32_t* path_lens, const mpap_mc_params* mcs,
+                               const mpap_vio_params* vps, uint32_t n, mpap_cert* outs, void* stream);
+
 /* mpap_certify without any device allocation (the paper has no counterpart;
  * this serves deployment).  For callers that must not allocate device memory
  * while running -- a planner inside a robot's real-time control loop, where an

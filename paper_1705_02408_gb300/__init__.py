@@ -43,7 +43,8 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_roadmap_update", "mpap_roadmap_update_batch", "mpap_refine_advance", "mpap_refine_batch",
            "mpap_surrogate_screen", "mpap_errnet_create", "mpap_errnet_free", "mpap_errnet_get_params",
            "mpap_errnet_set_params", "mpap_errnet_forward", "mpap_errnet_train_step", "mpap_errmap_query",
-           "mpap_errmap_levels", "mpap_workspace_stats"]
+           "mpap_errmap_levels", "mpap_workspace_stats", "mpap_certify_vio_batch",
+           "mpap_vio_lqr_gains"]
 
 
 class mpap_scene(C.Structure):
@@ -80,6 +81,11 @@ class mpap_tuning(C.Structure):
     _fields_ = [("edge_warps", C.c_uint32), ("wave_blocks_per_sm", C.c_uint32),
                 ("plan_lanes_from", C.c_uint32), ("front_cap", C.c_uint32),
                 ("grid_merge_from", C.c_uint32)]
+
+
+class mpap_vio_params(C.Structure):
+    _fields_ = [("q_a", C.c_int32), ("kp_q16", C.c_int32), ("kv_q16", C.c_int32),
+                ("r_fx", C.POINTER(C.c_int32))]
 
 
 class mpap_cert(C.Structure):
@@ -194,6 +200,12 @@ def lib():
         L.mpap_certify_batch.restype = i32
         L.mpap_certify_batch.argtypes = [C.POINTER(P), C.POINTER(P), P, C.POINTER(mpap_mc_params),
                                          C.c_uint32, C.POINTER(mpap_cert), P]
+        L.mpap_vio_lqr_gains.restype = i32
+        L.mpap_vio_lqr_gains.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_int32)]
+        L.mpap_certify_vio_batch.restype = i32
+        L.mpap_certify_vio_batch.argtypes = [C.POINTER(P), C.POINTER(P), P, C.POINTER(mpap_mc_params),
+                                             C.POINTER(mpap_vio_params), C.c_uint32, C.POINTER(mpap_cert), P]
         L.mpap_profile_enable.restype = i32
         L.mpap_profile_enable.argtypes = [i32]
         L.mpap_profile_reset.restype = i32
@@ -822,6 +834,45 @@ def certify_batch(rms, paths, mcs, stream=None):
            "mpap_certify_batch")
     cols = [outs[k].tolist() for k in ("hits_loc", "hits_coll", "hits_any", "rollouts")]
     return [dict(hits_loc=a, hits_coll=b, hits_any=c, rollouts=d) for a, b, c, d in zip(*cols)]
+
+
+def certify_vio_batch(rms, paths, mcs, vios, stream=None):
+    """mpap_certify_vio_batch: the closed-loop VIO model.  mcs: list of (rollouts,
+    seed, call_id, delta_fx); vios: list of (q_a, kp_q16, kv_q16, r_fx)."""
+    n = len(rms)
+    hs = (C.c_void_p * n)(*[rm.h for rm in rms])
+    arrs = [np.ascontiguousarray(p, np.uint32) if len(p) else np.zeros(1, np.uint32) for p in paths]
+    pp = np.array([a.__array_interface__["data"][0] for a in arrs], np.uint64)
+    lens = np.array([len(p) for p in paths], np.uint32)
+    ms = (mpap_mc_params * n)()
+    vs = (mpap_vio_params * n)()
+    keep = []
+    for i, (m, v) in enumerate(zip(mcs, vios)):
+        ms[i].rollouts, ms[i].seed, ms[i].call_id, ms[i].delta_fx = int(m[0]), int(m[1]), int(m[2]), int(m[3])
+        r = np.ascontiguousarray(v[3], np.int32)
+        keep.append(r)
+        vs[i].q_a, vs[i].kp_q16, vs[i].kv_q16 = int(v[0]), int(v[1]), int(v[2])
+        vs[i].r_fx = r.ctypes.data_as(C.POINTER(C.c_int32))
+    outs = (mpap_cert * n)()
+    _check(lib().mpap_certify_vio_batch(hs, pp.ctypes.data_as(C.POINTER(C.c_void_p)),
+                                        lens.ctypes.data_as(C.c_void_p), ms, vs, n, outs, _stream(stream)),
+           "mpap_certify_vio_batch")
+    return [dict(hits_loc=o.hits_loc, hits_coll=o.hits_coll, hits_any=o.hits_any, rollouts=o.rollouts)
+            for o in outs]
+
+
+def vio_lqr_gains(q_p, q_w, r):
+    """mpap_vio_lqr_gains: (kp_q16, kv_q16) of the VIO model's LQR tracker."""
+    kp = C.c_int32(); kv = C.c_int32()
+    _check(lib().mpap_vio_lqr_gains(float(q_p), float(q_w), float(r), C.byref(kp), C.byref(kv)),
+           "mpap_vio_lqr_gains")
+    return kp.value, kv.value
+
+
+def certify_vio(rm: Roadmap, path, rollouts, seed, call_id, delta_fx, q_a, kp_q16, kv_q16, r_fx, stream=None):
+    """One plan under the closed-loop VIO model (a batch of one)."""
+    return certify_vio_batch([rm], [path], [(rollouts, seed, call_id, delta_fx)],
+                             [(q_a, kp_q16, kv_q16, r_fx)], stream)[0]
 
 
 # ---------------------------------------------------------------------------

@@ -22,6 +22,9 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
 int32_t feature_levels_impl(int dp, int nb, const float* lo, const float* hi, uint32_t nf, const float* feat,
                             uint32_t G, uint32_t Y, const float* head, float cos_half, float range, int K,
                             uint8_t* out, bool device, cudaStream_t st);
+int32_t certify_vio_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,
+                               const mpap_mc_params* mcs, const mpap_vio_params* vps, uint32_t n, mpap_cert* outs,
+                               cudaStream_t st);
 int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,
                            const mpap_mc_params* mcs, uint32_t n, mpap_cert* outs, cudaStream_t st);
 int32_t certify_noalloc_impl(const mpap_roadmap* rm, const uint32_t* path, uint32_t path_len,
@@ -486,6 +489,50 @@ int32_t mpap_certify_batch(mpap_roadmap* const* rms, const uint32_t* const* path
     return MPAP_ERR_INVALID_ARG;
   }
   return mpap::certify_batch_impl(rms, paths, path_lens, mcs, n, outs, S(stream));
+}
+
+int32_t mpap_vio_lqr_gains(double q_p, double q_w, double r, int32_t* kp_q16, int32_t* kv_q16) {
+  if (!kp_q16 || !kv_q16 || !(q_p >= 0.0) || !(q_w >= 0.0) || !(r > 0.0)) {
+    set_error("mpap_vio_lqr_gains: weights must be q_p, q_w >= 0 and r > 0, outputs non-null");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  // P <- Q + A^T P A - A^T P B (r + B^T P B)^-1 B^T P A, A = [1 1; 0 1], B = (1/2, 1)
+  double p00 = q_p, p01 = 0.0, p11 = q_w;
+  double k0 = 0.0, k1 = 0.0;
+  for (int it = 0; it < 1000000; ++it) {
+    // B^T P = (p00/2 + p01, p01/2 + p11); B^T P B; B^T P A
+    const double bp0 = 0.5 * p00 + p01, bp1 = 0.5 * p01 + p11;
+    const double bpb = 0.5 * bp0 + bp1;
+    const double g0 = bp0, g1 = bp0 + bp1;            // B^T P A
+    const double s = r + bpb;
+    k0 = g0 / s;
+    k1 = g1 / s;
+    // A^T P A
+    const double a00 = p00, a01 = p00 + p01, a11 = p00 + 2.0 * p01 + p11;
+    const double n00 = q_p + a00 - g0 * k0;
+    const double n01 = a01 - g0 * k1;
+    const double n11 = q_w + a11 - g1 * k1;
+    const double d = std::max(std::fabs(n00 - p00), std::max(std::fabs(n01 - p01), std::fabs(n11 - p11)));
+    p00 = n00;
+    p01 = n01;
+    p11 = n11;
+    if (d <= 1e-14 * std::max(1.0, std::max(std::fabs(p00), std::fabs(p11)))) break;
+  }
+  const double bp0 = 0.5 * p00 + p01, bp1 = 0.5 * p01 + p11;
+  const double s = r + 0.5 * bp0 + bp1;
+  *kp_q16 = (int32_t)llrint(bp0 / s * 65536.0);
+  *kv_q16 = (int32_t)llrint((bp0 + bp1) / s * 65536.0);
+  return MPAP_OK;
+}
+
+int32_t mpap_certify_vio_batch(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,
+                               const mpap_mc_params* mcs, const mpap_vio_params* vps, uint32_t n, mpap_cert* outs,
+                               void* stream) {
+  if (n && (!rms || !paths || !path_lens || !mcs || !vps || !outs)) {
+    set_error("null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  return mpap::certify_vio_batch_impl(rms, paths, path_lens, mcs, vps, n, outs, S(stream));
 }
 
 int32_t mpap_search_candidates(mpap_workspace* ws, uint32_t index, uint32_t cap, int64_t* cost, int64_t* h,

@@ -11,6 +11,12 @@
 //                     checkpoints (relocalisation contraction, Irwin-Hall(12)
 //                     noise from Philox4x32-10), counting localisation and
 //                     collision/leave-map failures.
+// and, for the closed-loop VIO model of Sec. 4.1 (mpap_certify_vio_batch),
+//   k_vio_gains       one thread per plan: the Kalman gains of every checkpoint
+//                     step from the covariance recursion (double, then Q16);
+//   k_vio_rollouts    one thread per rollout: LQR tracking from the estimate,
+//                     inertial prediction and Kalman position fixes per axis in
+//                     integer arithmetic, the same failure events.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -286,6 +292,264 @@ int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* path
     {
       ::mpap::LaunchScope ls_(st, "k_mc_rollouts");
       k_mc_rollouts<<<gro, 256, 0, st>>>(d_jobs);
+    }
+  }
+  MPAP_CK(cudaGetLastError());
+  std::vector<uint32_t> hh(3 * n);
+  MPAP_CK(cudaMemcpyAsync(hh.data(), d_hits, b_hits, cudaMemcpyDeviceToHost, st));
+  scratch_free(blk, st);
+  MPAP_CK(cudaStreamSynchronize(st));
+  for (uint32_t i = 0; i < n; ++i) {
+    outs[i].hits_loc = hh[3 * i];
+    outs[i].hits_coll = hh[3 * i + 1];
+    outs[i].hits_any = hh[3 * i + 2];
+    outs[i].rollouts = mcs[i].rollouts;
+  }
+  return MPAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Closed-loop VIO model (Sec. 4.1: LQR tracking of the nominal from the state
+// estimate, inertial prediction, Kalman position fixes; the recurrences are
+// stated with mpap_certify_vio_batch).  Three kernels per batch: the
+// checkpoints (k_mc_checkpoints, shared with the error walk), the Kalman gains
+// of every step (k_vio_gains: one thread per plan walks the covariance recursion
+// in double, rounded to Q16 as the rollouts use them) and the rollouts
+// (k_vio_rollouts: one thread per rollout, the three axes' integer states).
+// ---------------------------------------------------------------------------
+struct VioJob {
+  McJob mc;                // checkpoints, rollouts, keys, delta, hit counters (sigma/shift unused)
+  int32_t q_a, kp, kv;
+  const int32_t* r;        // [K+1] position-fix noise per level
+  int2* gains;             // [steps] {Lp, Lw} in Q16
+};
+
+__global__ void k_vio_gains(const VioJob* jobs, uint32_t n) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const VioJob& J = jobs[j];
+  double p00 = 0.0, p01 = 0.0, p11 = 0.0;
+  const double q2 = (double)J.q_a * (double)J.q_a;
+  for (uint32_t s = 0; s < J.mc.steps; ++s) {
+    const double a00 = p00 + 2.0 * p01 + p11 + 0.25 * q2;
+    const double a01 = p01 + p11 + 0.5 * q2;
+    const double a11 = p11 + q2;
+    const int32_t r = J.r[J.mc.ckpt[s].w];
+    double lp = 0.0, lw = 0.0;
+    if (r > 0) {
+      const double S = a00 + (double)r * (double)r;
+      lp = a00 / S;
+      lw = a01 / S;
+      p00 = (1.0 - lp) * a00;
+      p01 = (1.0 - lp) * a01;
+      p11 = a11 - lw * a01;
+    } else {
+      p00 = a00;
+      p01 = a01;
+      p11 = a11;
+    }
+    J.gains[s] = make_int2((int)__double2ll_rn(lp * 65536.0), (int)__double2ll_rn(lw * 65536.0));
+  }
+}
+
+__device__ __forceinline__ long long vio_clamp(long long x) {
+  const long long lim = 1ll << 30;
+  return x > lim ? lim : (x < -lim ? -lim : x);
+}
+
+__device__ __forceinline__ long long vio_round16(long long x) { return (x + 32768ll) >> 16; }
+
+// Irwin-Hall normal from six Philox words (both 16-bit halves of each).
+__device__ __forceinline__ long long vio_normal(const uint32_t* w) {
+  long long xi = 0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) xi += (long long)(w[j] & 0xFFFFu) + (long long)(w[j] >> 16);
+  return xi - 6ll * 65536ll;
+}
+
+__global__ void __launch_bounds__(256) k_vio_rollouts(const VioJob* jobs) {
+  const VioJob& V = jobs[blockIdx.y];
+  const McJob& J = V.mc;
+  __shared__ int s_lo[3 * kMcMaxBoxes], s_hi[3 * kMcMaxBoxes];
+  const int nb = J.g.nb < kMcMaxBoxes ? J.g.nb : kMcMaxBoxes;
+  for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) {
+    s_lo[i] = (int)__float2ll_rn(__fmul_rn(J.g.box_lo[i], kTwo20));
+    s_hi[i] = (int)__float2ll_rn(__fmul_rn(J.g.box_hi[i], kTwo20));
+  }
+  __syncthreads();
+  const int dp = J.g.dp;
+  const uint32_t ro = blockIdx.x * blockDim.x + threadIdx.x;
+  bool loc = false, coll = false;
+  if (ro < J.rollouts) {
+    long long p[3] = {0, 0, 0}, w[3] = {0, 0, 0}, ep[3] = {0, 0, 0}, ew[3] = {0, 0, 0};
+    const long long one = 1ll << 20;
+    const long long kp = V.kp, kv = V.kv, qa = V.q_a;
+    for (uint32_t s = 0; s < J.steps; ++s) {
+      const int4 ck = J.ckpt[s];
+      const long long r = (long long)__ldg(V.r + ck.w);
+      const int2 L = V.gains[s];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (i < dp) {
+          uint32_t wd[12];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            uint32_t w0 = ro, w1 = s, w2 = (uint32_t)(3 * i + c), w3 = J.call_id;
+            philox4x32_10(w0, w1, w2, w3, J.key0, J.key1);
+            wd[4 * c + 0] = w0;
+            wd[4 * c + 1] = w1;
+            wd[4 * c + 2] = w2;
+            wd[4 * c + 3] = w3;
+          }
+          const long long a = -vio_round16(kp * (p[i] + ep[i]) + kv * (w[i] + ew[i]));
+          p[i] = vio_clamp(p[i] + w[i] + (a >> 1));
+          w[i] = vio_clamp(w[i] + a);
+          const long long na = (qa * vio_normal(wd)) >> 16;
+          ep[i] = vio_clamp(ep[i] + ew[i] + (na >> 1));
+          ew[i] = vio_clamp(ew[i] + na);
+          if (r > 0) {
+            const long long nu = (r * vio_normal(wd + 6)) >> 16;
+            const long long t = nu - ep[i];
+            ep[i] = vio_clamp(ep[i] + vio_round16((long long)L.x * t));
+            ew[i] = vio_clamp(ew[i] + vio_round16((long long)L.y * t));
+          }
+        }
+      }
+      long long ee = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < dp) ee += ep[i] * ep[i];
+      if (ee >= J.delta2) loc = true;
+      const long long qx = (long long)ck.x + p[0], qy = (long long)ck.y + p[1], qz = (long long)ck.z + p[2];
+      bool bad = qx < 0 || qx > one || qy < 0 || qy > one || (dp == 3 && (qz < 0 || qz > one));
+      for (int b = 0; b < nb && !bad; ++b) {
+        bool in = qx >= s_lo[3 * b] && qx <= s_hi[3 * b] && qy >= s_lo[3 * b + 1] && qy <= s_hi[3 * b + 1];
+        if (dp == 3) in = in && qz >= s_lo[3 * b + 2] && qz <= s_hi[3 * b + 2];
+        bad = in;
+      }
+      if (bad) coll = true;
+    }
+  }
+  const unsigned nl = __reduce_add_sync(0xFFFFFFFFu, loc ? 1u : 0u);
+  const unsigned nc = __reduce_add_sync(0xFFFFFFFFu, coll ? 1u : 0u);
+  const unsigned na = __reduce_add_sync(0xFFFFFFFFu, (loc || coll) ? 1u : 0u);
+  if ((threadIdx.x & 31) == 0) {
+    if (nl) atomicAdd(J.hits + 0, nl);
+    if (nc) atomicAdd(J.hits + 1, nc);
+    if (na) atomicAdd(J.hits + 2, na);
+  }
+}
+
+int32_t certify_vio_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* paths, const uint32_t* path_lens,
+                               const mpap_mc_params* mcs, const mpap_vio_params* vps, uint32_t n, mpap_cert* outs,
+                               cudaStream_t st) {
+  if (n == 0) return MPAP_OK;
+  std::vector<VioJob> jobs(n);
+  size_t total_steps = 0, total_path = 0, total_tab = 0;
+  uint32_t max_ro = 0, max_steps = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const mpap_roadmap* rm = rms[i];
+    if (!rm || !rm->has_geometry) {
+      set_error("certify_vio: roadmap %u has no geometry", i);
+      return MPAP_ERR_INVALID_ARG;
+    }
+    if (rm->nb > kMcMaxBoxes) {
+      set_error("certify_vio: at most %d boxes", kMcMaxBoxes);
+      return MPAP_ERR_INVALID_ARG;
+    }
+    if (!vps[i].r_fx || (path_lens[i] && !paths[i])) {
+      set_error("certify_vio: null table or path");
+      return MPAP_ERR_INVALID_ARG;
+    }
+    for (uint32_t j = 0; j < path_lens[i]; ++j)
+      if (paths[i][j] >= rm->V) {
+        set_error("certify_vio: path node %u out of range", paths[i][j]);
+        return MPAP_ERR_INVALID_ARG;
+      }
+    const uint32_t steps = path_lens[i] >= 2 ? (path_lens[i] - 1) * (uint32_t)rm->M : 0u;
+    VioJob& V = jobs[i];
+    std::memset(&V, 0, sizeof(V));
+    McJob& J = V.mc;
+    J.g = rm->geom;
+    J.x = rm->x;
+    J.V = rm->V;
+    J.path_len = path_lens[i];
+    J.steps = steps;
+    J.rollouts = mcs[i].rollouts;
+    J.call_id = mcs[i].call_id;
+    J.K = rm->K;
+    J.key0 = (uint32_t)mcs[i].seed;
+    J.key1 = (uint32_t)(mcs[i].seed >> 32);
+    J.delta2 = (long long)mcs[i].delta_fx * (long long)mcs[i].delta_fx;
+    V.q_a = vps[i].q_a;
+    V.kp = vps[i].kp_q16;
+    V.kv = vps[i].kv_q16;
+    total_steps += steps;
+    total_path += path_lens[i];
+    total_tab += (size_t)(rm->K + 1);
+    max_ro = std::max(max_ro, mcs[i].rollouts);
+    max_steps = std::max(max_steps, steps);
+  }
+  // one device scratch block: jobs | hits | paths | r tables | checkpoints | gains
+  const size_t b_jobs = sizeof(VioJob) * n;
+  const size_t b_hits = sizeof(uint32_t) * 3 * n;
+  const size_t b_path = sizeof(uint32_t) * (total_path + 1);
+  const size_t b_tab = sizeof(int32_t) * (total_tab + 1);
+  const size_t b_ck = sizeof(int4) * (total_steps + 1);
+  const size_t b_gain = sizeof(int2) * (total_steps + 1);
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t o_hits = up(b_jobs), o_path = o_hits + up(b_hits), o_tab = o_path + up(b_path);
+  const size_t o_ck = o_tab + up(b_tab), o_gain = o_ck + up(b_ck);
+  const size_t bytes = o_gain + up(b_gain);
+  char* blk = nullptr;
+  MPAP_CK(scratch_alloc((void**)&blk, bytes, st));
+  VioJob* d_jobs = (VioJob*)blk;
+  uint32_t* d_hits = (uint32_t*)(blk + o_hits);
+  uint32_t* d_path = (uint32_t*)(blk + o_path);
+  int32_t* d_tab = (int32_t*)(blk + o_tab);
+  int4* d_ck = (int4*)(blk + o_ck);
+  int2* d_gain = (int2*)(blk + o_gain);
+  // host image of jobs | zeroed hit counters | paths | tables: one upload
+  std::vector<char> himg(o_ck, 0);
+  uint32_t* hpath = (uint32_t*)(himg.data() + o_path);
+  int32_t* htab = (int32_t*)(himg.data() + o_tab);
+  size_t po = 0, to = 0, co = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const int K1 = rms[i]->K + 1;
+    for (uint32_t j = 0; j < path_lens[i]; ++j) hpath[po + j] = paths[i][j];
+    for (int k = 0; k < K1; ++k) htab[to + k] = vps[i].r_fx[k];
+    McJob& J = jobs[i].mc;
+    J.path = d_path + po;
+    J.ckpt = d_ck + co;
+    J.hits = d_hits + 3 * i;
+    jobs[i].r = d_tab + to;
+    jobs[i].gains = d_gain + co;
+    po += path_lens[i];
+    to += (size_t)K1;
+    co += J.steps;
+  }
+  std::memcpy(himg.data(), jobs.data(), b_jobs);
+  MPAP_CK(cudaMemcpyAsync(blk, himg.data(), o_ck, cudaMemcpyHostToDevice, st));
+  // k_mc_checkpoints takes an array of McJob: a compact copy of the jobs'
+  // checkpoint parts
+  if (max_steps) {
+    std::vector<McJob> mj(n);
+    for (uint32_t i = 0; i < n; ++i) mj[i] = jobs[i].mc;
+    McJob* d_mj = nullptr;
+    MPAP_CK(scratch_alloc((void**)&d_mj, sizeof(McJob) * n, st));
+    MPAP_CK(cudaMemcpyAsync(d_mj, mj.data(), sizeof(McJob) * n, cudaMemcpyHostToDevice, st));
+    {
+      ::mpap::LaunchScope ls_(st, "k_mc_checkpoints");
+      k_mc_checkpoints<<<dim3((max_steps + 255) / 256, n), 256, 0, st>>>(d_mj);
+    }
+    scratch_free(d_mj, st);
+    {
+      ::mpap::LaunchScope ls_(st, "k_vio_gains");
+      k_vio_gains<<<(n + 127) / 128, 128, 0, st>>>(d_jobs, n);
+    }
+    if (max_ro) {
+      ::mpap::LaunchScope ls_(st, "k_vio_rollouts");
+      k_vio_rollouts<<<dim3((max_ro + 255) / 256, n), 256, 0, st>>>(d_jobs);
     }
   }
   MPAP_CK(cudaGetLastError());
