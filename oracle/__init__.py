@@ -55,6 +55,16 @@ def lib():
         L.orc_build_roadmap_from_points.argtypes = [C.c_int, C.c_int, f32p, f32p, C.c_int, u8p,
                                                     C.c_int, C.c_int, C.c_uint32, f32p,
                                                     C.c_float, C.c_float, C.c_int, C.c_float]
+        L.orc_build_roadmap_heading.restype = P
+        L.orc_build_roadmap_heading.argtypes = [C.c_int, C.c_int, f32p, f32p, C.c_int, u8p, C.c_int,
+                                                C.c_int, C.c_uint32, C.c_uint64, C.c_uint32, C.c_float,
+                                                C.c_float, C.c_int, f32p, f32p, C.c_float, C.c_int, u8p]
+        L.orc_build_roadmap_from_points_heading.restype = P
+        L.orc_build_roadmap_from_points_heading.argtypes = [C.c_int, C.c_int, f32p, f32p, C.c_int, u8p,
+                                                            C.c_int, C.c_int, C.c_uint32, f32p, C.c_float,
+                                                            C.c_float, C.c_int, C.c_float, C.c_int, u8p,
+                                                            C.c_void_p]
+        L.orc_roadmap_yaw.argtypes = [P, f32p]
         L.orc_roadmap_from_csr.restype = P
         L.orc_roadmap_from_csr.argtypes = [C.c_uint32, u32p, u32p, i32p, i32p, i32p, u8p]
         L.orc_roadmap_free.argtypes = [P]
@@ -161,27 +171,39 @@ class Roadmap:
         return dict(cost=float(cost[0]), J=float(J[0]), ckpt=ck.reshape(M, 3), d=d,
                     a0=a0, jerk=jk, collides=bool(hit))
 
+    def yaw(self) -> np.ndarray:
+        out = np.zeros(self.V, np.float32)
+        lib().orc_roadmap_yaw(self.h, out)
+        return out
+
     def straight_line_h(self) -> np.ndarray:
         out = np.zeros(self.V, np.int64)
         lib().orc_straight_line_h(self.h, out)
         return out
 
 
-def build_roadmap(scene, n=None, r=None, M=None) -> Roadmap:
+def build_roadmap(scene, n=None, r=None, M=None, heading=None) -> Roadmap:
+    """heading: None (grid form) or a uint8 array [Y][G^Dp] of level tables, table y
+    for the camera heading 2 pi y / Y (the camera-heading form: node yaws drawn
+    from Philox, yaw interpolated along every edge)."""
     cfg = scene.cfg
     n = cfg.n if n is None else n
     r = cfg.r if r is None else r
     M = cfg.M if M is None else M
     from scenegen import N_F, K_LEVELS, GOAL_RADIUS
-    h = lib().orc_build_roadmap(cfg.dim_kind, cfg.nb, scene.box_lo.reshape(-1), scene.box_hi.reshape(-1),
-                                cfg.grid_G, scene.grid, N_F, K_LEVELS, n, scene.sample_seed,
-                                scene.query_id, r, cfg.T_edge, M, scene.x_init, scene.x_goal,
-                                GOAL_RADIUS)
+    args = (cfg.dim_kind, cfg.nb, scene.box_lo.reshape(-1), scene.box_hi.reshape(-1), cfg.grid_G, scene.grid,
+            N_F, K_LEVELS, n, scene.sample_seed, scene.query_id, r, cfg.T_edge, M, scene.x_init, scene.x_goal,
+            GOAL_RADIUS)
+    if heading is None:
+        h = lib().orc_build_roadmap(*args)
+    else:
+        head = np.ascontiguousarray(heading, np.uint8)
+        h = lib().orc_build_roadmap_heading(*args, head.shape[0], head.reshape(-1))
     return Roadmap(h, cfg.dim_kind, M)
 
 
 def build_roadmap_from_points(dim, box_lo, box_hi, grid, G, x, r, T=0.25, M=16,
-                              goal_radius=0.05, n_f=12, K=24) -> Roadmap:
+                              goal_radius=0.05, n_f=12, K=24, heading=None, yaw=None) -> Roadmap:
     box_lo = np.ascontiguousarray(box_lo, np.float32).reshape(-1)
     box_hi = np.ascontiguousarray(box_hi, np.float32).reshape(-1)
     if box_lo.size == 0:
@@ -191,9 +213,17 @@ def build_roadmap_from_points(dim, box_lo, box_hi, grid, G, x, r, T=0.25, M=16,
         nb = box_lo.size // 3
     x = np.ascontiguousarray(x, np.float32)
     V = x.shape[1]
-    h = lib().orc_build_roadmap_from_points(dim, nb, box_lo, box_hi, G,
-                                            np.ascontiguousarray(grid, np.uint8), n_f, K, V,
-                                            x.reshape(-1), r, T, M, goal_radius)
+    if heading is None:
+        h = lib().orc_build_roadmap_from_points(dim, nb, box_lo, box_hi, G,
+                                                np.ascontiguousarray(grid, np.uint8), n_f, K, V,
+                                                x.reshape(-1), r, T, M, goal_radius)
+    else:
+        head = np.ascontiguousarray(heading, np.uint8)
+        yw = None if yaw is None else np.ascontiguousarray(yaw, np.float32)
+        h = lib().orc_build_roadmap_from_points_heading(dim, nb, box_lo, box_hi, G,
+                                                        np.ascontiguousarray(grid, np.uint8), n_f, K, V,
+                                                        x.reshape(-1), r, T, M, goal_radius, head.shape[0],
+                                                        head.reshape(-1), None if yw is None else yw.ctypes.data)
     return Roadmap(h, dim, M)
 
 

@@ -68,6 +68,22 @@ void philox4x32_10(const uint32_t in_ctr[4], const uint32_t in_key[2], uint32_t 
 // A 32-bit word to a float uniform in [0, 1): the top 24 bits times 2^-24 (exact).
 float word_to_unit(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
 
+// Yaw (Sec. 4.1: a single-integrator yaw state tracked exactly).  Constants are
+// rounded once from double.
+const float kTwoPiF = (float)(2.0 * 3.14159265358979323846);
+const float kPiF = (float)3.14159265358979323846;
+const float kInvTwoPiF = (float)(1.0 / (2.0 * 3.14159265358979323846));
+
+// Node v's yaw, uniform in [-pi, pi): Philox counter (v, 2, query_id, 0), key seed.
+float node_yaw(uint64_t seed, uint32_t query_id, uint32_t v) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t ctr[4] = {v, 2u, query_id, 0u};
+  uint32_t w[4];
+  philox4x32_10(ctr, key, w);
+  float t = word_to_unit(w[0]) * kTwoPiF;
+  return t - kPiF;
+}
+
 const float kTwo24 = 16777216.0f;   // cost quantum is 2^-24
 const float kTwo20 = 1048576.0f;    // Monte Carlo fixed point is 2^-20
 
@@ -81,6 +97,10 @@ struct Scene {
   int G = 1;
   std::vector<uint8_t> level;// [G^Dp], x fastest
   int n_f = 12, K = 24;
+  // camera-heading form (Sec. 4.1: features in the field of view of the yaw):
+  // Y level tables, table y for the heading 2 pi y / Y; 0 = one table (level)
+  int Y = 0;
+  std::vector<uint8_t> head;  // [Y][G^Dp]
   int dp() const { return dim == 2 ? 2 : 3; }
 };
 
@@ -95,6 +115,7 @@ struct Roadmap {
   std::vector<uint32_t> dst;
   std::vector<int32_t> cost_q, S, C;  // per edge: quantised cost, max-plus transfer
   std::vector<int32_t> Smax, Cmax;    // per edge: peak of the transfer over its sub-steps
+  std::vector<float> yaw;             // [V] node yaw (camera-heading form only)
   // 6D steering constants, computed once in double and rounded to float.
   float c1 = 0, c2 = 0, c3 = 0, e1 = 0, e2 = 0, inv6 = 0, dtm = 0, Tq_f = 0;
   int64_t Tq = 0;
@@ -142,6 +163,19 @@ int level_at(const Scene& sc, const float p[3]) {
   return sc.level[idx];
 }
 
+// Grid cell index of a position (as level_at).
+size_t cell_index(const Scene& sc, const float p[3]) {
+  int c[3] = {0, 0, 0};
+  for (int i = 0; i < sc.dp(); ++i) {
+    float s = p[i] * (float)sc.G;
+    int ci = (int)std::floor(s);
+    if (ci < 0) ci = 0;
+    if (ci > sc.G - 1) ci = sc.G - 1;
+    c[i] = ci;
+  }
+  return (sc.dp() == 2) ? ((size_t)c[1] * sc.G + c[0]) : (((size_t)c[2] * sc.G + c[1]) * sc.G + c[0]);
+}
+
 // ----------------------------------------------------------------------------
 // SampleFree(n) (Sec. 3): candidates come from Philox with counter
 // (attempt, 0|1, query_id, 0) and key = seed; a candidate is kept iff it is in free
@@ -186,6 +220,10 @@ bool sample_free(Roadmap& rm, uint32_t n, uint64_t seed, uint32_t query_id,
     for (int i = 0; i < 3; ++i) rm.x[3 + i][id] = v[i];
     ++kept;
   }
+  if (sc.Y > 0) {
+    rm.yaw.assign(rm.V, 0.0f);
+    for (uint32_t v = 0; v < rm.V; ++v) rm.yaw[v] = node_yaw(seed, query_id, v);
+  }
   return true;
 }
 
@@ -220,10 +258,18 @@ struct EdgeGeom {
   float v0[3] = {0, 0, 0}, q2[3] = {0, 0, 0}, q3[3] = {0, 0, 0};
   float J = 0;
   float a0[3] = {0, 0, 0}, jk[3] = {0, 0, 0};
+  float psi0 = 0, dpsi = 0;                      // yaw at the start and its wrapped change
 };
 
 EdgeGeom edge_geom(const Roadmap& rm, uint32_t u, uint32_t v) {
   EdgeGeom g;
+  if (rm.sc.Y > 0) {
+    // yaw moves at a constant rate along the shorter way round
+    const float d = rm.yaw[v] - rm.yaw[u];
+    const float turns = std::nearbyint(d * kInvTwoPiF);
+    g.psi0 = rm.yaw[u];
+    g.dpsi = d - turns * kTwoPiF;
+  }
   if (rm.sc.dim != 6) {
     const int dp = rm.sc.dp();
     float s = 0.0f;
@@ -272,6 +318,22 @@ void checkpoint(const Roadmap& rm, const EdgeGeom& g, int m, float p[3]) {
     float mid = g.v0[i] + t * in;
     p[i] = g.a[i] + t * mid;
   }
+}
+
+// Quality level at checkpoint m of an edge (position p).  Grid form: the level of
+// p's cell.  Camera-heading form: the yaw at the checkpoint, psi0 + (m / M) dpsi,
+// picks the nearest of the Y headings 2 pi y / Y, whose table gives the level
+// of p's cell.
+int checkpoint_level(const Roadmap& rm, const EdgeGeom& g, int m, const float p[3]) {
+  const Scene& sc = rm.sc;
+  if (sc.Y == 0) return level_at(sc, p);
+  const float t = (float)m * (1.0f / (float)rm.M);
+  const float psi = g.psi0 + t * g.dpsi;
+  const float cbin = (float)((double)sc.Y / (2.0 * 3.14159265358979323846));
+  int y = (int)std::nearbyint(psi * cbin);
+  y = ((y % sc.Y) + sc.Y) % sc.Y;
+  const size_t cells = (sc.dim == 2) ? (size_t)sc.G * sc.G : (size_t)sc.G * sc.G * sc.G;
+  return sc.head[(size_t)y * cells + cell_index(sc, p)];
 }
 
 // Exact-in-FP32 slab test of the closed segment a + t d, t in [0, 1], against a
@@ -327,7 +389,7 @@ void edge_steps(const Roadmap& rm, const EdgeGeom& g, int64_t cost_q, std::vecto
   for (int m = 1; m <= rm.M; ++m) {
     float p[3];
     checkpoint(rm, g, m, p);
-    int k = level_at(rm.sc, p);
+    int k = checkpoint_level(rm, g, m, p);
     d[m - 1] = inc * (int64_t)(rm.sc.n_f - k);
   }
 }
@@ -620,7 +682,7 @@ int certify(const Roadmap& rm, const uint32_t* path, uint32_t path_len, uint32_t
       float p[3];
       checkpoint(rm, g, m, p);
       for (int i = 0; i < 3; ++i) nom.push_back((int64_t)llrintf(p[i] * kTwo20));
-      lev.push_back(level_at(sc, p));
+      lev.push_back(checkpoint_level(rm, g, m, p));
     }
   }
   const uint32_t steps = (uint32_t)lev.size();
@@ -760,7 +822,7 @@ int certify_vio(const Roadmap& rm, const uint32_t* path, uint32_t path_len, uint
       float p[3];
       checkpoint(rm, g, m, p);
       for (int i = 0; i < 3; ++i) nom.push_back((int64_t)llrintf(p[i] * kTwo20));
-      lev.push_back(level_at(sc, p));
+      lev.push_back(checkpoint_level(rm, g, m, p));
     }
   }
   const uint32_t steps = (uint32_t)lev.size();
@@ -865,7 +927,7 @@ void plan_features(const Roadmap& rm, const uint32_t* path, uint32_t len, float*
     for (int m = 1; m <= rm.M; ++m) {
       float p[3];
       checkpoint(rm, g, m, p);
-      int k = level_at(sc, p);
+      int k = checkpoint_level(rm, g, m, p);
       lev.push_back(k > sc.K ? sc.K : k);
       float c = INFINITY;
       for (int i = 0; i < dp; ++i) c = std::fmin(c, std::fmin(p[i], 1.0f - p[i]));
@@ -895,6 +957,14 @@ void plan_features(const Roadmap& rm, const uint32_t* path, uint32_t len, float*
     f[j] = any ? (float)lmax / Kf : 0.0f;
     f[16 + j] = any ? (float)lsum / (64.0f * Kf) : 0.0f;
     f[32 + j] = any ? 4.0f * std::fmin(0.25f, cmin) : 1.0f;
+  }
+}
+
+void set_heading(Scene& sc, int Y, const uint8_t* head) {
+  sc.Y = Y > 0 ? Y : 0;
+  if (sc.Y) {
+    const size_t cells = (sc.dim == 2) ? (size_t)sc.G * sc.G : (size_t)sc.G * sc.G * sc.G;
+    sc.head.assign(head, head + (size_t)sc.Y * cells);
   }
 }
 
@@ -930,6 +1000,23 @@ void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) 
 // Build V = {x_init, x_goal} + SampleFree(n) and the r-disc graph (Alg. 2).
 // Returns null on failure (sampling budget exhausted or an edge field overflowing
 // int32).
+orc_roadmap* orc_build_roadmap_heading(int dim, int nb, const float* lo, const float* hi, int G,
+                                       const uint8_t* level, int n_f, int K, uint32_t n,
+                                       uint64_t seed, uint32_t query_id, float r, float T, int M,
+                                       const float* x_init, const float* x_goal, float goal_radius,
+                                       int Y, const uint8_t* head) {
+  orc_roadmap* h = new orc_roadmap();
+  Roadmap& rm = h->rm;
+  rm.sc = make_scene(dim, nb, lo, hi, G, level, n_f, K);
+  set_heading(rm.sc, Y, head);
+  rm.r = r; rm.T = T; rm.M = M; rm.goal_radius = goal_radius;
+  set_di6_constants(rm);
+  if (!sample_free(rm, n, seed, query_id, x_init, x_goal)) { delete h; return nullptr; }
+  mark_goal(rm);
+  if (!build_graph(rm)) { delete h; return nullptr; }
+  return h;
+}
+
 orc_roadmap* orc_build_roadmap(int dim, int nb, const float* lo, const float* hi, int G,
                                const uint8_t* level, int n_f, int K, uint32_t n,
                                uint64_t seed, uint32_t query_id, float r, float T, int M,
@@ -945,7 +1032,30 @@ orc_roadmap* orc_build_roadmap(int dim, int nb, const float* lo, const float* hi
   return h;
 }
 
-// Same graph construction on caller-given node states (x: [6][V] SoA).
+// Same graph construction on caller-given node states (x: [6][V] SoA) and, in the
+// camera-heading form, yaws (yaw: [V], NULL for all zero).
+orc_roadmap* orc_build_roadmap_from_points_heading(int dim, int nb, const float* lo, const float* hi,
+                                                   int G, const uint8_t* level, int n_f, int K,
+                                                   uint32_t V, const float* x, float r, float T, int M,
+                                                   float goal_radius, int Y, const uint8_t* head,
+                                                   const float* yaw) {
+  orc_roadmap* h = new orc_roadmap();
+  Roadmap& rm = h->rm;
+  rm.sc = make_scene(dim, nb, lo, hi, G, level, n_f, K);
+  set_heading(rm.sc, Y, head);
+  rm.r = r; rm.T = T; rm.M = M; rm.goal_radius = goal_radius;
+  set_di6_constants(rm);
+  rm.V = V;
+  for (int a = 0; a < 6; ++a) rm.x[a].assign(x + (size_t)a * V, x + (size_t)(a + 1) * V);
+  if (Y > 0) {
+    if (yaw) rm.yaw.assign(yaw, yaw + V);
+    else rm.yaw.assign(V, 0.0f);
+  }
+  mark_goal(rm);
+  if (!build_graph(rm)) { delete h; return nullptr; }
+  return h;
+}
+
 orc_roadmap* orc_build_roadmap_from_points(int dim, int nb, const float* lo, const float* hi,
                                            int G, const uint8_t* level, int n_f, int K,
                                            uint32_t V, const float* x, float r, float T, int M,
@@ -1181,6 +1291,11 @@ int orc_certify_vio(const orc_roadmap* h, const uint32_t* path, uint32_t path_le
   hits[2] = c.hits_any;
   hits[3] = c.rollouts;
   return rc;
+}
+
+void orc_roadmap_yaw(const orc_roadmap* h, float* out) {
+  const Roadmap& rm = h->rm;
+  for (uint32_t v = 0; v < rm.V; ++v) out[v] = rm.yaw.empty() ? 0.0f : rm.yaw[v];
 }
 
 // Straight-line heuristic from node 0 to every node: F_{x_init -> v}(0) for the
