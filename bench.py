@@ -344,16 +344,16 @@ def run_gpu(args, rank, world, local):
 # DRAM traffic from ncu captures, per unit of work, valid only while the kernel
 # sources are the ones that were captured.
 NCU_TRAFFIC = {
-    # one row-pass launch over 8 roadmaps: 13.22 MB read + 89.78 MB written
+    # one row-pass launch over 8 roadmaps: 13.24 MB read + 89.72 MB written
     # (profiles/k_edges_6d16k.md)
-    "k_edges": {"bytes_per_roadmap": (13.224192e6 + 89.782272e6) / 8,
-                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "10e96881fc43d35abe455134208faed84bb55602",
-                            "paper_1705_02408_gb300/csrc/common.cuh": "f42dfc54d3c1a7692a7b0b6e1943805b4fb67da4"}},
-    # one k_wave launch of the 8-query 6D-16k step: 169.29 MB read + 61.54 MB written
+    "k_edges": {"bytes_per_roadmap": (13.243392e6 + 89.717504e6) / 8,
+                "sources": {"paper_1705_02408_gb300/csrc/roadmap.cu": "19dc98e00769a158323b00e07af135847edc6571",
+                            "paper_1705_02408_gb300/csrc/common.cuh": "c0e30decd0d668ce9cb5dd6fa1e41da2e91baa84"}},
+    # one k_wave launch of the 8-query 6D-16k step: 169.44 MB read + 58.48 MB written
     # for 12,658,585 plan-edge expansions (profiles/k_wave_6d16k_8queries.md)
-    "k_wave": {"bytes_per_expansion": (169.289216e6 + 61.544448e6) / 12658585.0,
+    "k_wave": {"bytes_per_expansion": (169.441024e6 + 58.480896e6) / 12658585.0,
                "sources": {"paper_1705_02408_gb300/csrc/search.cu": "eb8d2718e6dbb92e69d6baa632fffd30080a7cc7",
-                           "paper_1705_02408_gb300/csrc/common.cuh": "f42dfc54d3c1a7692a7b0b6e1943805b4fb67da4"}},
+                           "paper_1705_02408_gb300/csrc/common.cuh": "c0e30decd0d668ce9cb5dd6fa1e41da2e91baa84"}},
 }
 
 

@@ -79,7 +79,20 @@ typedef struct {
   int32_t n_f;
   int32_t K;
   int32_t mem;
+  int32_t n_heading;               /* 0, or Y tables for the camera-heading form */
+  const uint8_t* heading_levels;   /* [Y][G^Dp] (same memory kind as the grid) */
 } mpap_scene;
+/* The camera-heading form of the perception heuristic (Sec. 4.1: features count
+ * only in the field of view of the yaw, a single-integrator state tracked
+ * exactly).  With n_heading = Y > 0 every node carries a yaw (see
+ * mpap_roadmap_export_yaw), the yaw moves at a constant rate along each edge the
+ * shorter way round (psi(t) = psi_a + (m / M) wrap(psi_b - psi_a) at checkpoint m,
+ * wrap(d) = d - 2 pi rint(d / (2 pi)), binary32), and checkpoint m reads its level
+ * from table y = rint(psi n_heading / (2 pi)) mod Y (the heading 2 pi y / Y
+ * nearest to the yaw; mpap_feature_levels computes such tables) instead of
+ * grid_level, in the edge transfers, the certification and the plan features.
+ * Levels must lie in 0..K as for the grid.  Such a roadmap's levels cannot be
+ * replaced by mpap_roadmap_update (boxes can be added). */
 
 /* Roadmap construction parameters (Alg. 2).
  *   n           free samples drawn by SampleFree; V = n + 2 nodes with
@@ -228,6 +241,13 @@ int32_t mpap_roadmap_export(const mpap_roadmap* rm, float* x, uint8_t* is_goal, 
  * is at most max(Cmax, h + Smax), with equality at some sub-step (Sec. 4.1
  * heuristic; used by the interior check of Eq. 2). */
 int32_t mpap_roadmap_export_peaks(const mpap_roadmap* rm, int32_t* Smax, int32_t* Cmax, void* stream);
+
+/* Copies the node yaws of a roadmap in the camera-heading form (Sec. 4.1: a
+ * single-integrator yaw state; drawn uniform in [-pi, pi) from Philox4x32-10
+ * with counter (v, 2, query_id, 0) and key seed for sampled roadmaps, 0 for given
+ * node states) to a host array of V floats; all zero for the grid form.
+ * Synchronises the stream. */
+int32_t mpap_roadmap_export_yaw(const mpap_roadmap* rm, float* yaw, void* stream);
 
 /* Copies the reverse CSR the search reads (in-edges of every node, Alg. 3's
  * predecessor sets) to host arrays (any pointer may be NULL): rev_ptr[V+1];

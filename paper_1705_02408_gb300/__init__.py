@@ -44,13 +44,14 @@ EXPORTS = ["mpap_status_string", "mpap_last_error", "mpap_build_roadmap", "mpap_
            "mpap_surrogate_screen", "mpap_errnet_create", "mpap_errnet_free", "mpap_errnet_get_params",
            "mpap_errnet_set_params", "mpap_errnet_forward", "mpap_errnet_train_step", "mpap_errmap_query",
            "mpap_errmap_levels", "mpap_workspace_stats", "mpap_certify_vio_batch",
-           "mpap_vio_lqr_gains"]
+           "mpap_vio_lqr_gains", "mpap_roadmap_export_yaw"]
 
 
 class mpap_scene(C.Structure):
     _fields_ = [("dim_kind", C.c_int32), ("nb", C.c_int32), ("box_lo", C.c_void_p),
                 ("box_hi", C.c_void_p), ("grid_G", C.c_int32), ("grid_level", C.c_void_p),
-                ("n_f", C.c_int32), ("K", C.c_int32), ("mem", C.c_int32)]
+                ("n_f", C.c_int32), ("K", C.c_int32), ("mem", C.c_int32), ("n_heading", C.c_int32),
+                ("heading_levels", C.c_void_p)]
 
 
 class mpap_roadmap_params(C.Structure):
@@ -200,6 +201,8 @@ def lib():
         L.mpap_certify_batch.restype = i32
         L.mpap_certify_batch.argtypes = [C.POINTER(P), C.POINTER(P), P, C.POINTER(mpap_mc_params),
                                          C.c_uint32, C.POINTER(mpap_cert), P]
+        L.mpap_roadmap_export_yaw.restype = i32
+        L.mpap_roadmap_export_yaw.argtypes = [P, P, P]
         L.mpap_vio_lqr_gains.restype = i32
         L.mpap_vio_lqr_gains.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int32),
                                          C.POINTER(C.c_int32)]
@@ -359,18 +362,26 @@ def _addr(a, dtype):
     return arr.__array_interface__["data"][0], arr, False, arr.size
 
 
-def make_scene_struct(dim_kind, box_lo, box_hi, grid, grid_G, n_f=12, K=24):
-    """An mpap_scene over numpy (host) or CUDA tensor (device) arrays."""
+def make_scene_struct(dim_kind, box_lo, box_hi, grid, grid_G, n_f=12, K=24, heading=None):
+    """An mpap_scene over numpy (host) or CUDA tensor (device) arrays.  heading:
+    None, or the camera-heading form's level tables [Y][G^Dp] (uint8, same
+    memory kind as the grid)."""
     lo_p, lo_k, lo_d = _ptr(box_lo, np.float32)
     hi_p, hi_k, hi_d = _ptr(box_hi, np.float32)
     g_p, g_k, g_d = _ptr(grid, np.uint8)
     nb = (lo_k.numel() if hasattr(lo_k, "numel") else lo_k.size) // 3
-    if len({lo_d, hi_d, g_d}) != 1:
+    kinds = {lo_d, hi_d, g_d}
+    h_p, h_k, Y = None, None, 0
+    if heading is not None:
+        h_p, h_k, h_d = _ptr(heading, np.uint8)
+        kinds.add(h_d)
+        Y = int(heading.shape[0])
+    if len(kinds) != 1:
         raise ValueError("scene arrays must all be on the host or all on the device")
     s = mpap_scene(dim_kind=dim_kind, nb=nb, box_lo=lo_p if nb else None,
                    box_hi=hi_p if nb else None, grid_G=grid_G, grid_level=g_p, n_f=n_f, K=K,
-                   mem=MPAP_MEM_DEVICE if g_d else MPAP_MEM_HOST)
-    return s, (lo_k, hi_k, g_k)
+                   mem=MPAP_MEM_DEVICE if g_d else MPAP_MEM_HOST, n_heading=Y, heading_levels=h_p)
+    return s, (lo_k, hi_k, g_k, h_k)
 
 
 class Roadmap:
@@ -456,6 +467,13 @@ class Roadmap:
                "mpap_roadmap_update")
         return self
 
+    def yaw(self, stream=None):
+        """mpap_roadmap_export_yaw: node yaws (camera-heading form; zeros otherwise)."""
+        out = np.zeros(self.V, np.float32)
+        _check(lib().mpap_roadmap_export_yaw(self.h, out.ctypes.data_as(C.c_void_p), _stream(stream)),
+               "mpap_roadmap_export_yaw")
+        return out
+
     def peaks(self, stream=None):
         """(Smax, Cmax) per edge, in the order of export()."""
         E = self.info()[1]
@@ -467,9 +485,9 @@ class Roadmap:
 
 
 def build_roadmap(dim_kind, box_lo, box_hi, grid, grid_G, n, seed, r, x_init, x_goal,
-                  goal_radius=0.05, T=0.25, M=16, query_id=0, n_f=12, K=24, stream=None) -> Roadmap:
+                  goal_radius=0.05, T=0.25, M=16, query_id=0, n_f=12, K=24, heading=None, stream=None) -> Roadmap:
     """mpap_build_roadmap: V = {x_init, x_goal} + SampleFree(n), r-disc graph (Alg. 2)."""
-    sc, keep = make_scene_struct(dim_kind, box_lo, box_hi, grid, grid_G, n_f, K)
+    sc, keep = make_scene_struct(dim_kind, box_lo, box_hi, grid, grid_G, n_f, K, heading)
     p = mpap_roadmap_params(n=n, query_id=query_id, seed=seed, r=r, T_edge=T, M=M,
                             goal_radius=goal_radius)
     for i in range(6):
@@ -494,14 +512,23 @@ def _batch_structs(specs):
     scenes = np.zeros(n, SCENE_DT)
     params = np.zeros(n, PARAMS_DT)
     keep = []
-    lo, hi, gl, nb, mem = [], [], [], [], []
+    lo, hi, gl, nb, mem, heads = [], [], [], [], [], []
     for sp in specs:
         a_lo, k_lo, d_lo, n_lo = _addr(sp["box_lo"], np.float32)
         a_hi, k_hi, d_hi, _ = _addr(sp["box_hi"], np.float32)
         a_g, k_g, d_g, _ = _addr(sp["grid"], np.uint8)
         if not (d_lo == d_hi == d_g):
             raise ValueError("scene arrays must all be on the host or all on the device")
-        keep.append((k_lo, k_hi, k_g))
+        hd = sp.get("heading")
+        if hd is not None:
+            a_h, k_h, d_h, _ = _addr(hd, np.uint8)
+            if d_h != d_g:
+                raise ValueError("scene arrays must all be on the host or all on the device")
+            heads.append((int(hd.shape[0]), a_h))
+        else:
+            k_h = None
+            heads.append((0, 0))
+        keep.append((k_lo, k_hi, k_g, k_h))
         nb.append(n_lo // 3)
         lo.append(a_lo if n_lo else 0)
         hi.append(a_hi if n_lo else 0)
@@ -517,6 +544,8 @@ def _batch_structs(specs):
     scenes["n_f"] = g("n_f", 12)
     scenes["K"] = g("K", 24)
     scenes["mem"] = mem
+    scenes["n_heading"] = [h[0] for h in heads]
+    scenes["heading_levels"] = [h[1] for h in heads]
     params["n"] = [sp["n"] for sp in specs]
     params["query_id"] = g("query_id", 0)
     params["seed"] = [sp["seed"] for sp in specs]
@@ -622,15 +651,16 @@ def roadmap_update_batch(rms, adds_lo, adds_hi, grids=None, stream=None):
     return rms
 
 
-def scene_spec(scene, n=None, r=None, M=None, device_inputs=None):
+def scene_spec(scene, n=None, r=None, M=None, device_inputs=None, heading=None):
     """Keyword arguments of build_roadmap for a scenegen.Scene (device_inputs: a
-    (box_lo, box_hi, grid) triple of CUDA tensors to read in place)."""
+    (box_lo, box_hi, grid) triple of CUDA tensors to read in place; heading: the
+    camera-heading form's level tables [Y][G^Dp], or None)."""
     cfg = scene.cfg
     lo, hi, grid = (scene.box_lo, scene.box_hi, scene.grid) if device_inputs is None else device_inputs
     return dict(dim_kind=cfg.dim_kind, box_lo=lo, box_hi=hi, grid=grid, grid_G=cfg.grid_G,
                 n=cfg.n if n is None else n, seed=scene.sample_seed, r=cfg.r if r is None else r,
                 x_init=scene.x_init, x_goal=scene.x_goal, T=cfg.T_edge, M=cfg.M if M is None else M,
-                query_id=scene.query_id)
+                query_id=scene.query_id, heading=heading)
 
 
 def build_roadmap_from_points(dim_kind, box_lo, box_hi, grid, grid_G, x, r, T=0.25, M=16,
@@ -666,8 +696,10 @@ def roadmap_from_csr(row_ptr, dst, cost_q, S, Cc, is_goal, Smax=None, Cmax=None,
     return Roadmap(h)
 
 
-def build_roadmap_for_scene(scene, n=None, r=None, M=None, device_inputs=False, stream=None) -> Roadmap:
-    """Convenience: build from a scenegen.Scene (host arrays, or device copies)."""
+def build_roadmap_for_scene(scene, n=None, r=None, M=None, device_inputs=False, heading=None,
+                            stream=None) -> Roadmap:
+    """Convenience: build from a scenegen.Scene (host arrays, or device copies;
+    heading: the camera-heading form's level tables [Y][G^Dp], or None)."""
     cfg = scene.cfg
     lo, hi, grid = scene.box_lo, scene.box_hi, scene.grid
     if device_inputs:
@@ -675,10 +707,12 @@ def build_roadmap_for_scene(scene, n=None, r=None, M=None, device_inputs=False, 
         lo = torch.from_numpy(np.ascontiguousarray(lo)).cuda()
         hi = torch.from_numpy(np.ascontiguousarray(hi)).cuda()
         grid = torch.from_numpy(np.ascontiguousarray(grid)).cuda()
+        if heading is not None:
+            heading = torch.from_numpy(np.ascontiguousarray(heading)).cuda()
     return build_roadmap(cfg.dim_kind, lo, hi, grid, cfg.grid_G, cfg.n if n is None else n,
                          scene.sample_seed, cfg.r if r is None else r, scene.x_init, scene.x_goal,
                          T=cfg.T_edge, M=cfg.M if M is None else M, query_id=scene.query_id,
-                         stream=stream)
+                         heading=heading, stream=stream)
 
 
 class Workspace:

@@ -249,6 +249,21 @@ int32_t mpap_roadmap_from_csr_peaks(uint32_t V, const uint32_t* row_ptr, const u
   return mpap::roadmap_from_csr_impl(V, row_ptr, dst, cost_q, Sv, C, Smax, Cmax, is_goal, out, S(stream));
 }
 
+int32_t mpap_roadmap_export_yaw(const mpap_roadmap* rm, float* yaw, void* stream) {
+  if (!rm || !yaw) {
+    set_error("null argument");
+    return MPAP_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = S(stream);
+  if (rm->n_head && rm->yaw && rm->V) {
+    MPAP_CK(cudaMemcpyAsync(yaw, rm->yaw, sizeof(float) * (size_t)rm->V, cudaMemcpyDeviceToHost, st));
+    MPAP_CK(cudaStreamSynchronize(st));
+  } else {
+    std::memset(yaw, 0, sizeof(float) * (size_t)rm->V);
+  }
+  return MPAP_OK;
+}
+
 int32_t mpap_roadmap_export_peaks(const mpap_roadmap* rm, int32_t* Smax, int32_t* Cmax, void* stream) {
   if (!rm) {
     set_error("null roadmap");

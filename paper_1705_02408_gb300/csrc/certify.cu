@@ -59,9 +59,11 @@ __global__ void k_mc_checkpoints(const McJob* jobs) {
     }
     Conn cn;
     conn_setup(J.g, xa, xb, cn);
+    conn_yaw(J.g, cn, a, b);
     float p[3];
     conn_point(J.g, cn, m, p);
-    int lev = level_at(J.g, p);
+    const float yaw_c[2] = {cn.psi0, cn.dpsi};
+    int lev = J.g.dp == 2 ? level_ck_t<2>(J.g, yaw_c, m, p) : level_ck_t<3>(J.g, yaw_c, m, p);
     lev = lev > J.K ? J.K : lev;
     J.ckpt[t] = make_int4((int)__float2ll_rn(__fmul_rn(p[0], kTwo20)), (int)__float2ll_rn(__fmul_rn(p[1], kTwo20)),
                           (int)__float2ll_rn(__fmul_rn(p[2], kTwo20)), lev);
@@ -742,10 +744,12 @@ __global__ void k_plan_features(const FeatJob* __restrict__ jobs) {
         xb[c] = J.x[(size_t)c * J.V + b];
       }
       conn_setup(J.g, xa, xb, cn);
+      conn_yaw(J.g, cn, a, b);
     }
     float p[3];
     conn_point(J.g, cn, (int)(s % M) + 1, p);
-    int lev = level_at(J.g, p);
+    const float yaw_c[2] = {cn.psi0, cn.dpsi};
+    int lev = dp == 2 ? level_ck_t<2>(J.g, yaw_c, (int)(s % M) + 1, p) : level_ck_t<3>(J.g, yaw_c, (int)(s % M) + 1, p);
     lev = lev > J.K ? J.K : lev;
     lmax = lev > lmax ? lev : lmax;
     lsum += (uint32_t)lev;

@@ -51,7 +51,19 @@ struct Geom {
   // 1 when M inc max(n_f, K - n_f) < 2^31 for every edge's increment inc (levels
   // 0..K): the transfer's partial sums then fit 32-bit integers exactly
   int narrow;
+  // camera-heading form (Sec. 4.1, features in the field of view of the yaw):
+  // n_head level tables [n_head][G^dp], table y for the heading 2 pi y / n_head,
+  // node yaws [V]; n_head = 0: the one grid above
+  int n_head;
+  const uint8_t* head_levels;
+  const float* yaw;
+  float cbin;             // n_head / (2 pi), rounded once from double
 };
+
+// Yaw constants, rounded once from double.
+constexpr float kTwoPiF = (float)(2.0 * 3.14159265358979323846);
+constexpr float kPiF = (float)3.14159265358979323846;
+constexpr float kInvTwoPiF = (float)(1.0 / (2.0 * 3.14159265358979323846));
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
@@ -110,6 +122,30 @@ __device__ __forceinline__ int level_at(const Geom& g, const float p[3]) {
   return g.dp == 2 ? level_at_t<2>(g, p) : level_at_t<3>(g, p);
 }
 
+// Quality level at checkpoint m (position p) of connection c: the grid's level of
+// p's cell, or in the heading form the level of p's cell in the table of the
+// heading nearest to the checkpoint's yaw.
+template <int DP>
+__device__ __forceinline__ int level_ck_t(const Geom& g, const float* yaw_c, int m, const float p[3]) {
+  if (g.n_head == 0) return level_at_t<DP>(g, p);
+  const float t = __fmul_rn((float)m, g.invM);
+  const float psi = __fadd_rn(yaw_c[0], __fmul_rn(t, yaw_c[1]));
+  int y = __float2int_rn(__fmul_rn(psi, g.cbin));
+  y = ((y % g.n_head) + g.n_head) % g.n_head;
+  int c[3] = {0, 0, 0};
+  const float Gf = (float)g.G;
+#pragma unroll
+  for (int i = 0; i < DP; ++i) {
+    int ci = (int)floorf(__fmul_rn(p[i], Gf));
+    ci = ci < 0 ? 0 : ci;
+    ci = ci > g.G - 1 ? g.G - 1 : ci;
+    c[i] = ci;
+  }
+  const size_t cells = (size_t)g.G * g.G * (DP == 3 ? g.G : 1);
+  const size_t idx = (DP == 2) ? ((size_t)c[1] * g.G + c[0]) : (((size_t)c[2] * g.G + c[1]) * g.G + c[0]);
+  return (int)__ldg(g.head_levels + (size_t)y * cells + idx);
+}
+
 // The optimal connection from state a to state b.
 //   2D/3D: straight segment a + t d, t in [0, 1] (unit speed); cost = |d|.
 //   6D:    p(t) = p0 + t (v0 + t (a0/2 + t j/6)) with a0 = 6 dp/T^2 - 2 dv/T and
@@ -119,7 +155,22 @@ struct Conn {
   float p0[3], v0[3], q2[3], q3[3];   // 6D cubic (q2 = a0/2, q3 = j/6)
   float d[3];                         // 2D/3D direction (p0 holds the start)
   float cost;
+  float psi0, dpsi;                   // yaw at the start and its wrapped change (heading form)
 };
+
+// The yaw of the connection from node va to node vb (heading form): a constant
+// rate along the shorter way round, psi(t) = psi0 + t dpsi, t = m / M.
+__device__ __forceinline__ void conn_yaw(const Geom& g, Conn& c, uint32_t va, uint32_t vb) {
+  c.psi0 = 0.0f;
+  c.dpsi = 0.0f;
+  if (g.n_head > 0) {
+    const float ya = g.yaw[va], yb = g.yaw[vb];
+    const float d = __fsub_rn(yb, ya);
+    const float turns = rintf(__fmul_rn(d, kInvTwoPiF));
+    c.psi0 = ya;
+    c.dpsi = __fsub_rn(d, __fmul_rn(turns, kTwoPiF));
+  }
+}
 
 // Cost only (the Near test), same operations and order as conn_setup.
 template <int DIM>
@@ -167,6 +218,8 @@ __device__ __forceinline__ void conn_setup_t(const Geom& g, const float a[6], co
       }
     }
     c.cost = __fsqrt_rn(s);
+    c.psi0 = 0.0f;
+    c.dpsi = 0.0f;
     return;
   }
   float jsum = 0.0f;
@@ -187,6 +240,8 @@ __device__ __forceinline__ void conn_setup_t(const Geom& g, const float a[6], co
     c.q3[i] = __fmul_rn(jk, g.inv6);
   }
   c.cost = __fadd_rn(g.T, jsum);
+  c.psi0 = 0.0f;
+  c.dpsi = 0.0f;
 }
 
 __device__ __forceinline__ void conn_setup(const Geom& g, const float a[6], const float b[6], Conn& c) {
@@ -384,16 +439,18 @@ __device__ __forceinline__ int64_t quantise_cost(float cost) {
 // steps the heuristic is max(C_m, h + S_m), so its peak along the edge (the "for
 // all t" form of Eq. 2) is max(Cmax, h + Smax) with Smax = max_m S_m and
 // Cmax = max_m C_m.
-template <typename I, int DIM>
+template <typename I, int DIM, bool HEAD>
 __device__ __forceinline__ void conn_transfer_i(const Geom& g, const Conn& c, int64_t cost_q, int64_t& S,
                                                 int64_t& C, int64_t& Smax, int64_t& Cmax) {
   constexpr int DP = (DIM == 2) ? 2 : 3;
   const I inc = (I)((DIM == 6) ? g.Tq : cost_q);
   I s = 0, h = 0, smax = (sizeof(I) == 4) ? (I)INT32_MIN : (I)INT64_MIN, cmax = 0;
+  const float yaw_c[2] = {c.psi0, c.dpsi};
   for (int m = 1; m <= g.M; ++m) {
     float p[3];
     conn_point_t<DIM>(g, c, m, p);
-    const I dm = inc * (I)(g.n_f - level_at_t<DP>(g, p));
+    const int lev = HEAD ? level_ck_t<DP>(g, yaw_c, m, p) : level_at_t<DP>(g, p);
+    const I dm = inc * (I)(g.n_f - lev);
     s += dm;
     h += dm;
     h = h < 0 ? 0 : h;
@@ -407,12 +464,13 @@ __device__ __forceinline__ void conn_transfer_i(const Geom& g, const Conn& c, in
 }
 
 // 32-bit partial sums where Geom::narrow proves them exact, 64-bit otherwise
-// (the same values either way).
-template <int DIM>
+// (the same values either way).  HEAD: the camera-heading form (levels from the
+// table of the checkpoint's yaw; the caller has set the yaw with conn_yaw).
+template <int DIM, bool HEAD = false>
 __device__ __forceinline__ void conn_transfer_t(const Geom& g, const Conn& c, int64_t cost_q, int64_t& S,
                                                 int64_t& C, int64_t& Smax, int64_t& Cmax) {
-  if (g.narrow) conn_transfer_i<int32_t, DIM>(g, c, cost_q, S, C, Smax, Cmax);
-  else conn_transfer_i<int64_t, DIM>(g, c, cost_q, S, C, Smax, Cmax);
+  if (g.narrow) conn_transfer_i<int32_t, DIM, HEAD>(g, c, cost_q, S, C, Smax, Cmax);
+  else conn_transfer_i<int64_t, DIM, HEAD>(g, c, cost_q, S, C, Smax, Cmax);
 }
 
 // ---------------------------------------------------------------------------

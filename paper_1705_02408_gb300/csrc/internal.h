@@ -34,6 +34,10 @@ struct mpap_roadmap {
   float* box_lo = nullptr;     // [nb][3]
   float* box_hi = nullptr;
   uint8_t* grid = nullptr;
+  int n_head = 0;              // camera-heading form: level tables per heading and node yaws
+  uint8_t* head = nullptr;     // [n_head][G^Dp]
+  float* yaw = nullptr;        // [V]
+  size_t cap_head = 0, cap_yaw = 0;
   size_t cap_V = 0, cap_E = 0, cap_nb = 0, cap_cells = 0;
   uint64_t near_tests = 0;     // Cost < r tests evaluated by the last build
 };

@@ -74,6 +74,14 @@ void fill_geom_constants(Geom& g, int dim, int nb, int G, int n_f, int M, float 
   g.Tq = (int64_t)llrintf(T * 16777216.0f);
 }
 
+// The camera-heading part of a roadmap's geometry (after fill_geom_constants).
+void set_heading_geom(mpap_roadmap* rm) {
+  rm->geom.n_head = rm->n_head;
+  rm->geom.head_levels = rm->head;
+  rm->geom.yaw = rm->yaw;
+  rm->geom.cbin = (float)((double)rm->n_head / (2.0 * 3.14159265358979323846));
+}
+
 // Per-roadmap descriptor read by every build kernel.
 struct BuildJob {
   Geom g;
@@ -267,7 +275,26 @@ __global__ void k_check_levels(const BuildJob* __restrict__ jobs) {
   bool bad = false;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += gridDim.x * blockDim.x)
     bad = bad || (int)J.g.grid[i] > J.K;
+  // and every table of the camera-heading form
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cells * (uint32_t)J.g.n_head;
+       i += gridDim.x * blockDim.x)
+    bad = bad || (int)J.g.head_levels[i] > J.K;
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&J.status[0], kErrLevel);
+}
+
+// Node yaws of the camera-heading form (Sec. 4.1, a single-integrator yaw):
+// node v's yaw is uniform in [-pi, pi) from Philox4x32-10 with counter
+// (v, 2, query_id, 0), key = seed (sampled roadmaps; given node states keep 0).
+__global__ void k_node_yaw(const BuildJob* __restrict__ jobs) {
+  const BuildJob& J = jobs[blockIdx.y];
+  if (J.g.n_head == 0 || J.n == 0) return;
+  float* yaw = const_cast<float*>(J.g.yaw);
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < J.V; v += gridDim.x * blockDim.x) {
+    uint32_t w0 = v, w1 = 2u, w2 = J.qid, w3 = 0u;
+    philox4x32_10(w0, w1, w2, w3, J.key0, J.key1);
+    const float u = __fmul_rn((float)(w0 >> 8), 1.0f / 16777216.0f);
+    yaw[v] = __fsub_rn(__fmul_rn(u, kTwoPiF), kPiF);
+  }
 }
 
 // X_goal: nodes within goal_radius (position) of node 1.
@@ -345,7 +372,7 @@ enum EdgeMode { kFillCsr = 1, kRow = 2 };
 
 // Overflow pass: one flush of source v's queue, written straight into the CSR
 // (forward row from out_base in discovery order, reverse records by cursor).
-template <int DIM>
+template <int DIM, bool HEAD>
 __device__ __forceinline__ void edge_flush_csr(const BuildJob& J, uint32_t v, const float a[6], const uint32_t* q,
                                                int k, const float* s_lo, const float* s_hi, const uint32_t* s_bins,
                                                uint32_t out_base, uint32_t& running) {
@@ -368,7 +395,8 @@ __device__ __forceinline__ void edge_flush_csr(const BuildJob& J, uint32_t v, co
     const uint32_t rank = running + __popc(bal & ((1u << lane) - 1u));
     const int64_t cq = quantise_cost(cn.cost);
     int64_t S, C, Smax, Cmax;
-    conn_transfer_t<DIM>(g, cn, cq, S, C, Smax, Cmax);
+    if constexpr (HEAD) conn_yaw(g, cn, v, u);
+    conn_transfer_t<DIM, HEAD>(g, cn, cq, S, C, Smax, Cmax);
     if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX || Smax > INT32_MAX || Cmax > INT32_MAX)
       atomicOr(&J.status[0], kErrEdge);
     const int4 rec = make_int4((int)u, (int)cq, (int)S, (int)C);
@@ -424,7 +452,7 @@ __device__ __forceinline__ void neighbour_run(const BuildJob& J, uint32_t rr, ui
 // lanes of one source are contiguous and in discovery order, so one atomic add on
 // the source's edge count per group hands out its ranks; the group that carries
 // the count past kRowCap puts the source on the overflow list.
-template <int DIM>
+template <int DIM, bool HEAD>
 __device__ __forceinline__ void edge_flush_rows(const BuildJob& J, const uint32_t* qu, const uint32_t* qv, int k,
                                                 const float* s_lo, const float* s_hi, const uint32_t* s_bins) {
   const Geom& g = J.g;
@@ -462,7 +490,8 @@ __device__ __forceinline__ void edge_flush_rows(const BuildJob& J, const uint32_
     if (rank < kRowCap) {
       const int64_t cq = quantise_cost(cn.cost);
       int64_t S, C, Smax, Cmax;
-      conn_transfer_t<DIM>(g, cn, cq, S, C, Smax, Cmax);
+      if constexpr (HEAD) conn_yaw(g, cn, v, u);
+      conn_transfer_t<DIM, HEAD>(g, cn, cq, S, C, Smax, Cmax);
       if (cq > INT32_MAX || S > INT32_MAX || S < INT32_MIN || C > INT32_MAX || Smax > INT32_MAX || Cmax > INT32_MAX)
         atomicOr(&J.status[0], kErrEdge);
       J.rows[(size_t)v * kRowCap + rank] = make_int4((int)u, (int)cq, (int)S, (int)C);
@@ -478,7 +507,7 @@ constexpr uint32_t kSourcesPerWarp = 8;
 // pass).  A warp takes kSourcesPerWarp consecutive sources in cell order and
 // feeds their Near candidates through one queue, so collision tests and
 // transfers run on full warps across source boundaries.
-template <int DIM, int WARPS>
+template <int DIM, int WARPS, bool HEAD>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_rows(const BuildJob* __restrict__ jobs,
                                                                     const uint32_t* __restrict__ job_ids) {
   const BuildJob& J = jobs[job_ids[blockIdx.y]];
@@ -566,7 +595,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_rows(const Bui
         qn += __popc(bal);
         if (qn >= 32) {
           __syncwarp();
-          edge_flush_rows<DIM>(J, qu, qv, 32, s_lo, s_hi, binned ? s_bins : nullptr);
+          edge_flush_rows<DIM, HEAD>(J, qu, qv, 32, s_lo, s_hi, binned ? s_bins : nullptr);
           const bool mv = 32 + (int)lane < qn;
           const uint32_t ru = mv ? qu[32 + lane] : 0u, rv = mv ? qv[32 + lane] : 0u;
           __syncwarp();
@@ -581,13 +610,13 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_rows(const Bui
     }
   }
   __syncwarp();
-  if (qn > 0) edge_flush_rows<DIM>(J, qu, qv, qn, s_lo, s_hi, binned ? s_bins : nullptr);
+  if (qn > 0) edge_flush_rows<DIM, HEAD>(J, qu, qv, qn, s_lo, s_hi, binned ? s_bins : nullptr);
   if (lane == 0) atomicAdd(J.near_tests, (unsigned long long)tests);
 }
 
 // Overflow pass: the sources whose rows outgrew kRowCap, one warp per source,
 // edges written straight into the CSR at the source's row pointer.
-template <int DIM, int WARPS>
+template <int DIM, int WARPS, bool HEAD>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_csr(const BuildJob* __restrict__ jobs,
                                                                    const uint32_t* __restrict__ job_ids) {
   const BuildJob& J = jobs[job_ids[blockIdx.y]];
@@ -673,7 +702,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_csr(const Buil
       qn += __popc(bal);
       if (qn >= 32) {
         __syncwarp();
-        edge_flush_csr<DIM>(J, v, a, q, 32, s_lo, s_hi, binned ? s_bins : nullptr, out_base, running);
+        edge_flush_csr<DIM, HEAD>(J, v, a, q, 32, s_lo, s_hi, binned ? s_bins : nullptr, out_base, running);
         const uint32_t rest = (32 + (int)lane < qn) ? q[32 + lane] : 0u;
         __syncwarp();
         if (32 + (int)lane < qn) q[lane] = rest;
@@ -683,7 +712,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_edges_csr(const Buil
     }
   }
   __syncwarp();
-  if (qn > 0) edge_flush_csr<DIM>(J, v, a, q, qn, s_lo, s_hi, binned ? s_bins : nullptr, out_base, running);
+  if (qn > 0) edge_flush_csr<DIM, HEAD>(J, v, a, q, qn, s_lo, s_hi, binned ? s_bins : nullptr, out_base, running);
   (void)tests;   // counted by the row pass
 }
 
@@ -906,10 +935,12 @@ __global__ void k_update_edges(const UpdateJob* __restrict__ jobs, const uint32_
           }
           Conn cn;
           conn_setup_t<DIM>(J.g, a, b, cn);
+          conn_yaw(J.g, cn, v, (uint32_t)rec.x);
           if (hit_box) ok = !conn_collides_t<DIM>(J.g_add, cn, s_lo, s_hi, nullptr);
           if (ok && hit_cells) {
             int64_t S, C, Smax, Cmax;
-            conn_transfer_t<DIM>(J.g, cn, (int64_t)rec.y, S, C, Smax, Cmax);
+            if (J.g.n_head) conn_transfer_t<DIM, true>(J.g, cn, (int64_t)rec.y, S, C, Smax, Cmax);
+            else conn_transfer_t<DIM, false>(J.g, cn, (int64_t)rec.y, S, C, Smax, Cmax);
             if (S > INT32_MAX || S < INT32_MIN || C > INT32_MAX || Smax > INT32_MAX || Cmax > INT32_MAX)
               atomicOr(&J.status[0], kErrEdge);
             rec.z = (int)S;
@@ -964,18 +995,27 @@ __global__ void k_update_ptrs(const UpdateJob* __restrict__ jobs) {
   }
 }
 
-template <int MODE, int WARPS>
-void launch_edges_w(int dim, dim3 grid, size_t smem, cudaStream_t st, const BuildJob* jobs, const uint32_t* ids) {
+template <int MODE, int WARPS, bool HEAD>
+void launch_edges_h(int dim, dim3 grid, size_t smem, cudaStream_t st, const BuildJob* jobs, const uint32_t* ids) {
   const dim3 block(WARPS * 32);
   if (MODE == kRow) {
-    if (dim == 6) k_edges_rows<6, WARPS><<<grid, block, smem, st>>>(jobs, ids);
-    else if (dim == 3) k_edges_rows<3, WARPS><<<grid, block, smem, st>>>(jobs, ids);
-    else k_edges_rows<2, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+    if (dim == 6) k_edges_rows<6, WARPS, HEAD><<<grid, block, smem, st>>>(jobs, ids);
+    else if (dim == 3) k_edges_rows<3, WARPS, HEAD><<<grid, block, smem, st>>>(jobs, ids);
+    else k_edges_rows<2, WARPS, HEAD><<<grid, block, smem, st>>>(jobs, ids);
   } else {
-    if (dim == 6) k_edges_csr<6, WARPS><<<grid, block, smem, st>>>(jobs, ids);
-    else if (dim == 3) k_edges_csr<3, WARPS><<<grid, block, smem, st>>>(jobs, ids);
-    else k_edges_csr<2, WARPS><<<grid, block, smem, st>>>(jobs, ids);
+    if (dim == 6) k_edges_csr<6, WARPS, HEAD><<<grid, block, smem, st>>>(jobs, ids);
+    else if (dim == 3) k_edges_csr<3, WARPS, HEAD><<<grid, block, smem, st>>>(jobs, ids);
+    else k_edges_csr<2, WARPS, HEAD><<<grid, block, smem, st>>>(jobs, ids);
   }
+}
+
+// dim: 2, 3, 6 for the grid form, plus kHeadDim for the camera-heading form
+constexpr int kHeadDim = 100;
+
+template <int MODE, int WARPS>
+void launch_edges_w(int dim, dim3 grid, size_t smem, cudaStream_t st, const BuildJob* jobs, const uint32_t* ids) {
+  if (dim > kHeadDim) launch_edges_h<MODE, WARPS, true>(dim - kHeadDim, grid, smem, st, jobs, ids);
+  else launch_edges_h<MODE, WARPS, false>(dim, grid, smem, st, jobs, ids);
 }
 
 // One launch per dimension group; `warps` (4 or 8 warps per block) comes from
@@ -1236,6 +1276,8 @@ int32_t ensure_boxes_kept(mpap_roadmap* rm, size_t nb_old, size_t nb, cudaStream
 
 void roadmap_free_impl(mpap_roadmap* rm) {
   if (!rm) return;
+  cudaFree(rm->head);
+  cudaFree(rm->yaw);
   cudaFree(rm->x);
   cudaFree(rm->is_goal);
   cudaFree(rm->goal_list);
@@ -1307,7 +1349,20 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     MPAP_BTRY(copy_in(rm->box_hi, sc->box_hi, 12 * (size_t)rm->nb, dev, st));
     MPAP_BTRY(copy_in(rm->grid, sc->grid_level, cells, dev, st));
     if (sp.points) MPAP_BTRY(copy_in(rm->x, sp.points, sizeof(float) * 6 * (size_t)V, false, st));
+    rm->n_head = (sc->n_heading > 0 && sc->heading_levels) ? sc->n_heading : 0;
+    if (rm->n_head) {
+      size_t ch = rm->cap_head, cy = rm->cap_yaw;
+      MPAP_BTRY(grow(&rm->head, ch, (size_t)rm->n_head * cells));
+      rm->cap_head = ch;
+      MPAP_BTRY(grow(&rm->yaw, cy, (size_t)V));
+      rm->cap_yaw = cy;
+      MPAP_BTRY(copy_in(rm->head, sc->heading_levels, (size_t)rm->n_head * cells, dev, st));
+      if (sp.points)
+        MPAP_BTRY(cuda_ok(cudaMemsetAsync(rm->yaw, 0, sizeof(float) * (size_t)V, st), "memset") ? MPAP_OK
+                                                                                               : MPAP_ERR_CUDA);
+    }
     fill_geom_constants(rm->geom, rm->dim, rm->nb, rm->G, rm->n_f, sp.M, sp.r, sp.T);
+    set_heading_geom(rm);
     rm->geom.box_lo = rm->box_lo;
     rm->geom.box_hi = rm->box_hi;
     rm->geom.grid = rm->grid;
@@ -1453,7 +1508,15 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
   }
   MPAP_BTRY(upload(d_jobs, hj.data(), sizeof(BuildJob) * n, st));
 
-  // 4. level check, goal region and spatial binning
+  // 4. node yaws (camera-heading form), level check, goal region and spatial binning
+  {
+    bool any_head = false;
+    for (uint32_t j = 0; j < n; ++j) any_head = any_head || (hj[j].g.n_head > 0 && hj[j].n > 0);
+    if (any_head) {
+      LaunchScope ls(st, "k_node_yaw");
+      k_node_yaw<<<dim3(std::min<uint32_t>((Vmax + 255) / 256, 2u * sms), n), 256, 0, st>>>(d_jobs);
+    }
+  }
   {
     LaunchScope ls(st, "k_check_levels");
     k_check_levels<<<dim3((uint32_t)std::min<size_t>((max_qcells + 255) / 256, 2u * sms), n), 256, 0, st>>>(d_jobs);
@@ -1480,25 +1543,26 @@ int32_t build_roadmaps_impl(uint32_t n, const BuildSpec* specs, mpap_roadmap** r
     k_bin_scatter<<<gridv, 256, 0, st>>>(d_jobs);
   }
 
-  // 5. Near + Collision: count pass, row pointers, fill pass (one launch per dim)
+  // 5. Near + Collision: count pass, row pointers, fill pass (one launch per
+  //    dimension and form: grid, or camera heading)
   std::vector<uint32_t> ids;
-  const int dims[3] = {2, 3, 6};
-  uint32_t id_off[4] = {0, 0, 0, 0};
-  for (int di = 0; di < 3; ++di) {
+  const int dims[6] = {2, 3, 6, kHeadDim + 2, kHeadDim + 3, kHeadDim + 6};
+  uint32_t id_off[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int di = 0; di < 6; ++di) {
     id_off[di] = (uint32_t)ids.size();
     for (uint32_t j = 0; j < n; ++j)
-      if (hj[j].g.dim == dims[di]) ids.push_back(j);
+      if (hj[j].g.dim + (hj[j].g.n_head ? kHeadDim : 0) == dims[di]) ids.push_back(j);
   }
-  id_off[3] = (uint32_t)ids.size();
+  id_off[6] = (uint32_t)ids.size();
   MPAP_BTRY(upload(d_ids, ids.data(), sizeof(uint32_t) * n, st));
   const size_t box_smem = sizeof(float) * 6 * max_nb;
   auto edges_pass = [&](int mode) {
-    for (int di = 0; di < 3; ++di) {
+    for (int di = 0; di < 6; ++di) {
       const uint32_t cnt = id_off[di + 1] - id_off[di];
       if (!cnt) continue;
       uint32_t vmax = 0;
       for (uint32_t k = id_off[di]; k < id_off[di + 1]; ++k) vmax = std::max(vmax, hj[ids[k]].V);
-      const uint32_t warps = tuning_for(dims[di], vmax).edge_warps;
+      const uint32_t warps = tuning_for(dims[di] % kHeadDim, vmax).edge_warps;
       if (mode == kFillCsr) {
         vmax = 0;
         for (uint32_t k = id_off[di]; k < id_off[di + 1]; ++k) vmax = std::max(vmax, hg[6 * ids[k] + 5]);
@@ -1641,6 +1705,10 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
       set_error("roadmap_update: roadmap %u would have more than 1024 boxes", j);
       return MPAP_ERR_INVALID_ARG;
     }
+    if (rms[j]->n_head && grids && grids[j]) {
+      set_error("roadmap_update: roadmap %u is in the camera-heading form; its levels cannot be replaced", j);
+      return MPAP_ERR_INVALID_ARG;
+    }
   }
   auto cells_of = [](const mpap_roadmap* rm) { return (size_t)rm->G * rm->G * (rm->dim == 2 ? 1 : rm->G); };
   // 1. box capacity (the old boxes stay where they are; the added ones are
@@ -1657,6 +1725,7 @@ int32_t roadmap_update_batch_impl(uint32_t n, mpap_roadmap* const* rms, const in
     if (rc) return rc;
     rm->nb = nb;
     fill_geom_constants(rm->geom, rm->dim, rm->nb, rm->G, rm->n_f, rm->M, rm->r, rm->T);
+    set_heading_geom(rm);
     rm->geom.box_lo = rm->box_lo;
     rm->geom.box_hi = rm->box_hi;
     rm->geom.grid = rm->grid;
