@@ -92,3 +92,21 @@ def test_roadmap_update_argument_checks(libpath):
     import paper_1705_02408_gb300 as mp
     L = mp.lib()
     assert L.mpap_roadmap_update(None, 0, None, None, None, 0, None) == mp.MPAP_ERR_INVALID_ARG
+
+
+def test_new_entry_points_argument_checks(libpath):
+    """Null handles and arrays of the workspace statistics, yaw export and VIO
+    certification are rejected on the host before any device work."""
+    import ctypes as C
+    import paper_1705_02408_gb300 as mp
+    L = mp.lib()
+    mf, pu = C.c_uint32(), C.c_uint64()
+    assert L.mpap_workspace_stats(None, C.byref(mf), C.byref(pu)) == mp.MPAP_ERR_INVALID_ARG
+    assert L.mpap_roadmap_export_yaw(None, None, None) == mp.MPAP_ERR_INVALID_ARG
+    out = mp.mpap_cert()
+    assert L.mpap_certify_vio_batch(None, None, None, None, None, 1, C.byref(out), None) == mp.MPAP_ERR_INVALID_ARG
+    assert L.mpap_certify_vio_batch(None, None, None, None, None, 0, None, None) == mp.MPAP_OK
+    kp, kv = C.c_int32(), C.c_int32()
+    assert L.mpap_vio_lqr_gains(1.0, 1.0, 1.0, None, C.byref(kv)) == mp.MPAP_ERR_INVALID_ARG
+    assert L.mpap_vio_lqr_gains(1.0, 1.0, 1.0, C.byref(kp), C.byref(kv)) == mp.MPAP_OK
+    assert kp.value > 0 and kv.value > 0
