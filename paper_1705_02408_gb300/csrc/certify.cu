@@ -27,6 +27,16 @@
 
 namespace mpap {
 
+// A CUDA check after a scratch block `blk` was taken on stream `st`: on failure
+// the block goes back before the error is returned.
+#define MPAP_CK_FREE(call)                                   \
+  do {                                                       \
+    if (!::mpap::cuda_ok((call), #call)) {                   \
+      scratch_free(blk, st);                                 \
+      return MPAP_ERR_CUDA;                                  \
+    }                                                        \
+  } while (0)
+
 struct McJob {
   Geom g;
   const float* x;          // roadmap node states [6][V]
@@ -279,7 +289,7 @@ int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* path
     co += jobs[i].steps;
   }
   std::memcpy(himg.data(), jobs.data(), b_jobs);
-  MPAP_CK(cudaMemcpyAsync(blk, himg.data(), o_ck, cudaMemcpyHostToDevice, st));
+  MPAP_CK_FREE(cudaMemcpyAsync(blk, himg.data(), o_ck, cudaMemcpyHostToDevice, st));
   uint32_t max_steps = 0;
   for (auto& J : jobs) max_steps = max_steps > J.steps ? max_steps : J.steps;
   if (max_steps) {
@@ -296,9 +306,9 @@ int32_t certify_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* path
       k_mc_rollouts<<<gro, 256, 0, st>>>(d_jobs);
     }
   }
-  MPAP_CK(cudaGetLastError());
+  MPAP_CK_FREE(cudaGetLastError());
   std::vector<uint32_t> hh(3 * n);
-  MPAP_CK(cudaMemcpyAsync(hh.data(), d_hits, b_hits, cudaMemcpyDeviceToHost, st));
+  MPAP_CK_FREE(cudaMemcpyAsync(hh.data(), d_hits, b_hits, cudaMemcpyDeviceToHost, st));
   scratch_free(blk, st);
   MPAP_CK(cudaStreamSynchronize(st));
   for (uint32_t i = 0; i < n; ++i) {
@@ -531,15 +541,23 @@ int32_t certify_vio_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* 
     co += J.steps;
   }
   std::memcpy(himg.data(), jobs.data(), b_jobs);
-  MPAP_CK(cudaMemcpyAsync(blk, himg.data(), o_ck, cudaMemcpyHostToDevice, st));
+  MPAP_CK_FREE(cudaMemcpyAsync(blk, himg.data(), o_ck, cudaMemcpyHostToDevice, st));
   // k_mc_checkpoints takes an array of McJob: a compact copy of the jobs'
   // checkpoint parts
   if (max_steps) {
     std::vector<McJob> mj(n);
     for (uint32_t i = 0; i < n; ++i) mj[i] = jobs[i].mc;
     McJob* d_mj = nullptr;
-    MPAP_CK(scratch_alloc((void**)&d_mj, sizeof(McJob) * n, st));
-    MPAP_CK(cudaMemcpyAsync(d_mj, mj.data(), sizeof(McJob) * n, cudaMemcpyHostToDevice, st));
+    if (scratch_alloc((void**)&d_mj, sizeof(McJob) * n, st) != cudaSuccess) {
+      scratch_free(blk, st);
+      set_error("certify_vio: scratch allocation failed");
+      return MPAP_ERR_CUDA;
+    }
+    if (!cuda_ok(cudaMemcpyAsync(d_mj, mj.data(), sizeof(McJob) * n, cudaMemcpyHostToDevice, st), "copy")) {
+      scratch_free(d_mj, st);
+      scratch_free(blk, st);
+      return MPAP_ERR_CUDA;
+    }
     {
       ::mpap::LaunchScope ls_(st, "k_mc_checkpoints");
       k_mc_checkpoints<<<dim3((max_steps + 255) / 256, n), 256, 0, st>>>(d_mj);
@@ -554,9 +572,9 @@ int32_t certify_vio_batch_impl(mpap_roadmap* const* rms, const uint32_t* const* 
       k_vio_rollouts<<<dim3((max_ro + 255) / 256, n), 256, 0, st>>>(d_jobs);
     }
   }
-  MPAP_CK(cudaGetLastError());
+  MPAP_CK_FREE(cudaGetLastError());
   std::vector<uint32_t> hh(3 * n);
-  MPAP_CK(cudaMemcpyAsync(hh.data(), d_hits, b_hits, cudaMemcpyDeviceToHost, st));
+  MPAP_CK_FREE(cudaMemcpyAsync(hh.data(), d_hits, b_hits, cudaMemcpyDeviceToHost, st));
   scratch_free(blk, st);
   MPAP_CK(cudaStreamSynchronize(st));
   for (uint32_t i = 0; i < n; ++i) {
