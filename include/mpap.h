@@ -440,7 +440,7 @@ int32_t mpap_certify_noalloc(const mpap_roadmap* rm, const uint32_t* path, uint3
  * kernel's blocks per SM and the group size from which its expansion runs its
  * lanes over a node's group plans instead of its out-edges, and the size from
  * which a node's merge is spread over the whole grid.  Keys without an entry use
- * the defaults (8, 8, 8, 64, 8192).  The results of every call are
+ * the defaults (8, 8, 8, 64, 2048).  The results of every call are
  * identical for every valid shape; only the time changes.  The table is
  * process-wide and guarded by a mutex.
  * ------------------------------------------------------------------------- */
