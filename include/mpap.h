@@ -494,8 +494,8 @@ int32_t mpap_autotune_search(mpap_workspace* ws, mpap_roadmap* const* rms, const
  * the whole candidate set and a learned screen of it, so that a caller can try
  * the candidates in cost order but skip those a small network predicts will fail
  * certification, and spend Monte Carlo only on likely winners.  The network is
- * not in the paper (the paper learns nothing); Monte Carlo stays the judge of
- * every plan returned.
+ * not in the paper (its only learned part is the error-rate heuristic of Sec.
+ * 5.1, mpap_errnet_*); Monte Carlo stays the judge of every plan returned.
  * ------------------------------------------------------------------------- */
 
 /* Candidates of query `index` of the last search on ws (Alg. 3 final lines), in
